@@ -1,0 +1,347 @@
+"""Benchmark: dual gradient evaluations per second of group-sparse OT on GB300.
+
+One step = one evaluation of the dual objective D and its gradient (Eq. 4-5)
+over the whole workload, through the library's C ABI.  Default workload: m = n
+= 20000, 1000 classes with Zipf(1.1) sizes (min 2), d = 512 Gaussian-mixture
+features, C FP32 (1.6 GB) squared-Euclidean scaled to max 1, gamma = 1,
+mu = 0.5, synthetic and seeded.  C is larger than L2, so no flush is needed.
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
+of the workload on its GPU (the single-problem path is not sharded).
+``--impl reference`` times the FP64 CPU oracle on host cores instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "dual grad evals/s"
+UNIT = "evals/s"
+
+WORKLOADS = {
+    "large": dict(m=20000, n=20000, L=1000, d=512, gamma=1.0, mu=0.5),
+    "mid": dict(m=4000, n=4000, L=100, d=256, gamma=1.0, mu=0.1),
+    "tiny": dict(m=200, n=200, L=10, d=10, gamma=1.0, mu=0.1),
+}
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _make_workload(name, seed, device):
+    import torch
+    cfg = WORKLOADS[name]
+    if name == "tiny":
+        p = synth.tiny(seed=seed)
+    elif name == "mid":
+        p = synth.mid(seed=seed, device=device)
+    else:
+        p = synth.large(seed=seed, device=device)
+    C = torch.from_numpy(p.C).to(device)
+    return p, C, cfg
+
+
+def _eval_point(C, k):
+    """A dual point like those met mid-solve: alpha = 0 and beta_j just above
+    the k-th smallest cost of column j, so about k entries of f are positive
+    per column (input construction, not part of the method)."""
+    import torch
+    beta = torch.kthvalue(C.double(), k, dim=0).values + 1e-3
+    alpha = torch.zeros(C.shape[0], dtype=torch.float64, device=C.device)
+    return alpha, beta.contiguous()
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+
+    def __enter__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.uuid:
+            cmd += ["-i", self.uuid]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        self.f.flush()
+
+    def summary(self):
+        try:
+            rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+            os.unlink(self.f.name)
+        except Exception:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = max(mx, float(r[1]))
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_for(kernel_src_hash, workload):
+    """Per-launch DRAM bytes of the evaluation kernel from a committed ncu
+    summary, only when it was taken on the current kernel source."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as fh:
+            t = json.load(fh)
+        e = t.get(workload)
+        if e and e.get("src_sha1") == kernel_src_hash:
+            return e.get("bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+def _src_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2303_07597_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.startswith("otgs_eval") or name == "otgs_internal.cuh":
+            h.update(open(os.path.join(csrc, name), "rb").read())
+    return h.hexdigest()
+
+
+def cpu_baseline(p, alpha, beta, gamma, mu, budget_s=10.0, ncols=None):
+    """FP64 oracle dense evaluation on a column sample (all rows, the first
+    ncols columns; the cost is linear in columns), scaled to the workload."""
+    import oracle
+    n = p.n
+    if ncols is None:
+        ncols = max(1, min(n, int(4e7 // p.m)))
+    o = oracle.Oracle(np.ascontiguousarray(p.C[:, :ncols]), p.labels, p.a, p.b[:ncols], p.L, gamma, mu)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o.dual(alpha, beta[:ncols])
+        reps += 1
+        el = time.perf_counter() - t0
+        if el >= budget_s or reps >= 1000:
+            break
+    per = el / reps * (n / ncols)
+    return {"value": 1.0 / per, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{reps} dense FP64 evaluations on all {p.m} rows x {ncols} of {n} columns "
+                      f"({el:.1f} s), scaled by n/{ncols}"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cfg = WORKLOADS[args.workload]
+    p = {"tiny": synth.tiny, "mid": synth.mid, "large": synth.large}[args.workload](seed=args.seed)
+    Cn = p.C
+    k = 20 if args.workload != "tiny" else 5
+    beta = np.sort(Cn, axis=0)[k - 1].astype(np.float64) + 1e-3
+    alpha = np.zeros(p.m)
+    per_step = max(2.0, 30.0 / max(1, args.steps + args.warmup))
+    cb = None
+    vals = []
+    for s in range(args.warmup + args.steps):
+        cb = cpu_baseline(p, alpha, beta, cfg["gamma"], cfg["mu"], budget_s=per_step)
+        if s >= args.warmup:
+            vals.append(cb["value"])
+    v = float(np.mean(vals))
+    cb["value"] = v
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": f"{args.workload}: m=n={cfg['m']}, L={cfg['L']}, gamma={cfg['gamma']}, "
+                                   f"mu={cfg['mu']}", "l2": "inputs > L2"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2303_07597_gb300 as pk
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p, C, cfg = _make_workload(args.workload, args.seed, str(dev))
+    a = torch.from_numpy(p.a).to(dev)
+    b = torch.from_numpy(p.b).to(dev)
+    lab = torch.from_numpy(p.labels).to(dev)
+    solver = pk.GroupSparseOT(C, a, b, lab, p.L, cfg["gamma"], cfg["mu"])
+    k = 20 if args.workload != "tiny" else 5
+    alpha, beta = _eval_point(C, k)
+    out = torch.empty(1 + p.m + p.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        pk.ot_gs_grad(solver.h, alpha, beta, out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    pk.ot_gs_set_timing(solver.h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(uuid) as cs:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    pk.ot_gs_set_timing(solver.h, False)
+    launches, kern_ms = pk.ot_gs_get_timing(solver.h)
+    el_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([el_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        el_ms = float(t.item())
+        dist.barrier()
+    clocks = cs.summary()
+
+    # end to end: host inputs in pinned memory, copies inside the timed region
+    h_alpha = alpha.cpu().pin_memory()
+    h_beta = beta.cpu().pin_memory()
+    h_out = torch.empty(out.shape, dtype=torch.float64).pin_memory()
+    d_alpha, d_beta = torch.empty_like(alpha), torch.empty_like(beta)
+
+    def step_e2e():
+        d_alpha.copy_(h_alpha, non_blocking=True)
+        d_beta.copy_(h_beta, non_blocking=True)
+        pk.ot_gs_grad(solver.h, d_alpha, d_beta, out)
+        h_out.copy_(out, non_blocking=True)
+
+    for _ in range(args.warmup):
+        step_e2e()
+    torch.cuda.synchronize()
+    k_e2e = max(1, args.steps // 2)
+    e0.record(stream)
+    for _ in range(k_e2e):
+        step_e2e()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    if rank == 0:
+        m, n = p.m, p.n
+        value = args.steps * world / (el_ms / 1000.0)
+        kern_avg_s = kern_ms / max(1, launches) / 1000.0
+        alg_bytes = 4.0 * m * n + 8.0 * (m + n)
+        peak, peak_kind = _peaks()
+        achieved = alg_bytes / kern_avg_s / 1e9
+        cb = None
+        if world == 1 and not args.no_cpu_baseline:
+            hp = p
+            cb = cpu_baseline(hp, alpha.cpu().numpy(), beta.cpu().numpy(), cfg["gamma"], cfg["mu"],
+                              budget_s=args.cpu_budget)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el_ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"{args.workload}: m=n={cfg['m']}, L={cfg['L']} "
+                                   f"({'Zipf(1.1) sizes, min 2' if args.workload == 'large' else 'classes'}), "
+                                   f"d={cfg['d']}, gamma={cfg['gamma']}, mu={cfg['mu']}, dense evaluation",
+                       "l2": "inputs > L2 (C is 4mn bytes)" if args.workload == "large" else "C may be L2-resident",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": peak_kind,
+                         "kernel": "k_eval", "alg_bytes_per_launch": alg_bytes,
+                         "kernel_ms": kern_avg_s * 1000.0,
+                         "traffic": _traffic_for(_src_hash(), args.workload)},
+            "cpu_baseline": cb,
+            "e2e": {"value": k_e2e * world / (e2e_ms / 1000.0), "unit": UNIT,
+                    "h2d_bytes_per_step": 8 * (m + n), "d2h_bytes_per_step": 8 * (1 + m + n)},
+            "gpu_launches": 3 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--cpu-budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,213 @@
+/*
+ * otgs.h -- C ABI of the GB300 (sm_103a) solver for discrete optimal
+ * transport with the squared-L2 + group-lasso regulariser.
+ *
+ * Method: Ida et al., "Fast Regularized Discrete Optimal Transport with
+ * Group-Sparse Regularizers" (AAAI 2023).  The library maximises the smooth
+ * relaxed dual (Eq. 4)
+ *
+ *     D(alpha, beta) = alpha.a + beta.b - sum_j psi(alpha + beta_j 1_m - c_j)
+ *
+ * whose gradient comes from the group soft-threshold of Eq. 5,
+ *
+ *     grad psi(f)_[l] = ([z - mu gamma]_+ / (gamma z)) [f_[l]]_+,
+ *     z = ||[f_[l]]_+||,   psi_[l] = [z - mu gamma]_+^2 / (2 gamma),
+ *
+ * with the safe skipping of zero blocks (Def. 1, Eq. 6, Lemma 2), the set of
+ * surely-nonzero blocks (Def. 2-3, Eq. 7-8) and the driver of Alg. 1 around an
+ * L-BFGS loop that runs entirely on the device.
+ *
+ * Conventions for every entry point:
+ *  - Pointers documented "device" must be device memory of the current CUDA
+ *    device (e.g. PyTorch tensors' data_ptr()); "host" pointers are ordinary
+ *    host memory.  Nothing takes ownership of caller memory.
+ *  - Every call enqueues its work on the handle's stream (a cudaStream_t
+ *    passed as void*; NULL = the legacy default stream) and, unless stated
+ *    otherwise, returns without synchronising.
+ *  - Return value: OTGS_OK (0) or a negative ot_gs_status.  The message of
+ *    the last failure on a handle is available from ot_gs_last_error().
+ *  - Floating point: C is FP32; a, b, alpha, beta, gradients and D are FP64.
+ *    Kernels compute in FP32 with error-free (double-float) transformations
+ *    where cancellation demands it, and accumulate in FP64.
+ */
+#ifndef OTGS_H
+#define OTGS_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define OTGS_API __attribute__((visibility("default")))
+#else
+#define OTGS_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ot_gs ot_gs; /* opaque handle */
+
+typedef enum {
+    OTGS_OK = 0,
+    OTGS_EINVAL = -1,        /* invalid argument (sizes, labels, gamma, mu, marginals, NULL) */
+    OTGS_ECUDA = -2,         /* a CUDA runtime call failed (message in ot_gs_last_error) */
+    OTGS_ENOMEM = -3,        /* device or host allocation failed */
+    OTGS_ENOTCONV = -4,      /* ot_gs_solve stopped at maxit before ||grad D||_inf <= tol */
+    OTGS_ETIMEOUT = -5,      /* ot_gs_solve stopped at its time budget */
+    OTGS_ELINESEARCH = -6,   /* the line search found no acceptable step */
+    OTGS_ENONFINITE = -7     /* non-finite input (C, a, b, alpha, beta) */
+} ot_gs_status;
+
+/* Solver parameters (ot_gs_set_params / ot_gs_get_params). */
+typedef struct {
+    double gamma;          /* gamma > 0 of Eq. 3 */
+    double mu;             /* mu >= 0 of Eq. 3; the threshold is theta = mu gamma */
+    int32_t r;             /* accepted iterations between snapshot refreshes (Alg. 1; paper: 10) */
+    int32_t lbfgs_m;       /* L-BFGS memory (pairs), 1..32, default 10 */
+    int32_t use_screening; /* 1: Alg. 1/2 screened evaluations in ot_gs_solve; 0: dense */
+    int32_t use_lower_bound; /* 1: build the set N of Def. 3 every r iterations */
+    double time_budget_ms; /* <= 0: none; else ot_gs_solve stops with OTGS_ETIMEOUT */
+} ot_gs_params;
+
+/* Counters, cumulative since create (or since ot_gs_reset_stats). */
+typedef struct {
+    int64_t evals;            /* dual evaluations (line-search trials included) */
+    int64_t iters;            /* accepted L-BFGS iterations of the last solve */
+    int64_t blocks_total;     /* (l, j) blocks visited by all evaluations = evals * L * n */
+    int64_t blocks_in_N;      /* blocks computed because (l, j) in N (Alg. 2, first loop) */
+    int64_t blocks_skipped;   /* blocks with zbar <= theta (Alg. 2, zero without computing) */
+    int64_t blocks_checked;   /* upper bounds evaluated (blocks outside N) */
+    int64_t units_total;      /* (group, 32-column tile) units visited = evals * L * ceil(n/32) */
+    int64_t units_computed;   /* units whose C tile was streamed */
+    int64_t snapshots;        /* snapshot refreshes (dense passes) */
+    double  c_bytes;          /* bytes of C streamed by evaluation kernels */
+} ot_gs_stats;
+
+/*
+ * Create a problem (Sec. 2.1-2.3).
+ *   h       out: new handle
+ *   C       device, FP32, m x n, row i at C + i*ldc (ldc >= n), c_ij >= 0, finite.
+ *           Borrowed when the labels are non-decreasing, n % 4 == 0, ldc % 4 == 0
+ *           and C is 16-byte aligned; the caller then keeps it alive and unchanged until
+ *           ot_gs_destroy.  Otherwise the library keeps a class-sorted copy.
+ *   a, b    device, FP64, m and n positive marginals with |sum a - sum b| <=
+ *           1e-12 max(sum a, 1) (Sec. 2.1 uses 1/m and 1/n); copied.
+ *   labels  device, int32, m class labels in [0, L) (the groups of Eq. 3); copied.
+ *   gamma, mu  regularisation of Eq. 3 (gamma > 0, mu >= 0)
+ *   stream  cudaStream_t (as void*) on which all later work is enqueued
+ * Synchronises the stream once (validation and the group plan are built on
+ * the host).  Errors: OTGS_EINVAL, OTGS_ENONFINITE, OTGS_ENOMEM, OTGS_ECUDA;
+ * *h is NULL on failure.
+ */
+OTGS_API int ot_gs_create(ot_gs **h, const float *C, int64_t ldc, const double *a, const double *b,
+                 const int32_t *labels, int64_t m, int64_t n, int32_t L, double gamma,
+                 double mu, void *stream);
+
+/* Release every resource of the handle (synchronises its stream).  NULL is a no-op. */
+OTGS_API int ot_gs_destroy(ot_gs *h);
+
+/* Replace the stream used by later calls. */
+OTGS_API int ot_gs_set_stream(ot_gs *h, void *stream);
+
+OTGS_API int ot_gs_set_params(ot_gs *h, const ot_gs_params *p); /* host struct; validates */
+OTGS_API int ot_gs_get_params(const ot_gs *h, ot_gs_params *p); /* host struct */
+
+/*
+ * One dense evaluation of the dual objective and its gradient (Eq. 4, Eq. 5;
+ * gradient by Danskin's theorem, Sec. 2.3):
+ *   alpha   device FP64 [m], caller's row order
+ *   beta    device FP64 [n]
+ *   out     device FP64 [1 + m + n]: out[0] = D(alpha, beta),
+ *           out[1 + i] = dD/dalpha_i = a_i - sum_j t_ij,
+ *           out[1 + m + j] = dD/dbeta_j = b_j - sum_i t_ij
+ * Asynchronous.  Reads all of C once.  Errors: OTGS_EINVAL, OTGS_ECUDA.
+ */
+OTGS_API int ot_gs_grad(ot_gs *h, const double *alpha, const double *beta, double *out);
+
+/*
+ * Same evaluation, screened by the upper bound of Eq. 6 against the handle's
+ * current snapshot and set N (Alg. 2): blocks with zbar <= theta are not read
+ * and contribute exact zeros.  The result equals ot_gs_grad bit for bit
+ * (Thm. 2; the skip test keeps a margin that covers the kernels' rounding).
+ * skip_mask (device, optional, NULL to ignore) receives the per-block skip
+ * decisions as L x ceil(n/32) uint32 words, bit (j % 32) of word
+ * [l * ceil(n/32) + j / 32] set when block (l, j) was skipped.
+ */
+OTGS_API int ot_gs_grad_screened(ot_gs *h, const double *alpha, const double *beta, double *out,
+                        uint32_t *skip_mask);
+
+/*
+ * Refresh the snapshot at (alpha, beta) (Alg. 1, line 15): one dense pass that
+ * also stores z~_{l,j} (rounded up to FP32) and o~_{l,j}, and alpha~ = alpha,
+ * beta~ = beta.  When build_N != 0 the set N (Def. 3, Eq. 8) is first rebuilt
+ * from the lower bound of Eq. 7 against the previous snapshot (Alg. 1, lines
+ * 4-14).  Writes D and the gradient to out like ot_gs_grad when out != NULL.
+ */
+OTGS_API int ot_gs_snapshot(ot_gs *h, const double *alpha, const double *beta, int build_N, double *out);
+
+/*
+ * Copy the screening state for inspection (any pointer may be NULL); all are
+ * device pointers.  zt, ot: FP32 [L * ceil(n/32)*32] (row l = group, padded
+ * columns undefined); alpha_s: FP64 [m] caller order; beta_s: FP64 [n];
+ * N_mask: uint32 [L * ceil(n/32)] bitmask of the set N.
+ */
+OTGS_API int ot_gs_get_screen_state(ot_gs *h, float *zt, float *ot, double *alpha_s, double *beta_s,
+                           uint32_t *N_mask);
+
+/*
+ * Solve max D with L-BFGS (memory lbfgs_m) and a strong-Wolfe line search,
+ * from the handle's current iterate (zero after create, Alg. 1 line 1; or the
+ * point given to ot_gs_set_state).  With use_screening = 1 each evaluation is
+ * screened (Alg. 2) and every r accepted iterations N and the snapshot are
+ * rebuilt (Alg. 1).  The whole iteration -- line search, evaluation, the
+ * L-BFGS update and the convergence test -- runs on the device; the host
+ * waits once at the end.  Stops when ||grad D||_inf <= tol.
+ * Returns OTGS_OK, OTGS_ENOTCONV (maxit), OTGS_ETIMEOUT, OTGS_ELINESEARCH, or
+ * an error.  Synchronises the stream.
+ */
+OTGS_API int ot_gs_solve(ot_gs *h, double tol, int32_t maxit);
+
+/*
+ * Current iterate: alpha (device FP64 [m], caller order), beta (device FP64
+ * [n]); D, grad_inf (host, FP64) and iters (host) may be NULL.  Synchronises.
+ */
+OTGS_API int ot_gs_get_solution(ot_gs *h, double *alpha, double *beta, double *D, double *grad_inf,
+                       int32_t *iters);
+
+/* Set the iterate used by the next ot_gs_solve (warm start or resume) and
+ * clear the L-BFGS memory.  alpha, beta: device FP64 [m], [n], caller order. */
+OTGS_API int ot_gs_set_state(ot_gs *h, const double *alpha, const double *beta);
+
+OTGS_API int ot_gs_get_stats(ot_gs *h, ot_gs_stats *s); /* host struct; synchronises */
+OTGS_API int ot_gs_reset_stats(ot_gs *h);
+
+/*
+ * Kernel timing for benchmarks: while enabled (enable != 0), every launch of
+ * the evaluation kernel is bracketed by CUDA events on the handle's stream.
+ * ot_gs_get_timing synchronises the stream and returns the number of timed
+ * launches and their summed device time in milliseconds, then clears them.
+ */
+OTGS_API int ot_gs_set_timing(ot_gs *h, int enable);
+OTGS_API int ot_gs_get_timing(ot_gs *h, int64_t *launches, double *total_ms);
+
+/* Message of the last failure on h (or of the last failed ot_gs_create when
+ * h is NULL).  Never NULL; valid until the next call on the handle. */
+OTGS_API const char *ot_gs_last_error(const ot_gs *h);
+
+/* Library version string, e.g. "otgs 0.1 sm_103a". */
+OTGS_API const char *ot_gs_version(void);
+
+/*
+ * Host-only inspection of the group plan the library builds at create (no
+ * GPU needed): for m labels in [0, L) and n columns, writes the number of
+ * panels and of (panel, column chunk) work items.  Returns OTGS_EINVAL on bad
+ * input.  Used to test the host-side work decomposition.
+ */
+OTGS_API int ot_gs_plan_info(const int32_t *labels_host, int64_t m, int64_t n, int32_t L,
+                    int64_t *n_panels, int64_t *n_items, int64_t *rowpart_len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* OTGS_H */

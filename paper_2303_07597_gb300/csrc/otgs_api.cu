@@ -1,0 +1,403 @@
+// otgs_api.cu -- the C ABI (include/otgs.h): handle life cycle, validation,
+// device buffers, and the host side of one evaluation.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "otgs_handle.cuh"
+
+using namespace otgs;
+
+static thread_local std::string g_create_error;
+
+namespace otgs {
+
+bool Handle::fail(int code, const std::string& msg)
+{
+    err = msg;
+    last_code = code;
+    return false;
+}
+
+bool Handle::ck(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return true;
+    err = std::string(what) + ": " + cudaGetErrorString(e);
+    last_code = OTGS_ECUDA;
+    return false;
+}
+
+void* Handle::dalloc(size_t bytes, const char* what)
+{
+    void* p = nullptr;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        err = std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) + " B): " + cudaGetErrorString(e);
+        last_code = e == cudaErrorMemoryAllocation ? OTGS_ENOMEM : OTGS_ECUDA;
+        cudaGetLastError();
+        return nullptr;
+    }
+    allocs.push_back(p);
+    return p;
+}
+
+Handle::~Handle()
+{
+    if (st_synced_ok) cudaStreamSynchronize(st);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (void* p : allocs) cudaFree(p);
+    if (host_scal) cudaFreeHost(host_scal);
+}
+
+template <class T>
+static T* upload(Handle* h, const std::vector<T>& v, const char* what)
+{
+    T* d = (T*)h->dalloc(sizeof(T) * (v.empty() ? 1 : v.size()), what);
+    if (!d) return nullptr;
+    if (!v.empty() && !h->ck(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, h->st), what))
+        return nullptr;
+    return d;
+}
+
+bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double* b_, const int32_t* labels_,
+                  int64_t m_, int64_t n_, int32_t L_, double gamma_, double mu_, cudaStream_t st_)
+{
+    st = st_;
+    m = m_; n = n_; L = L_;
+    prm.gamma = gamma_; prm.mu = mu_;
+    prm.r = 10; prm.lbfgs_m = 10; prm.use_screening = 0; prm.use_lower_bound = 1;
+    prm.time_budget_ms = 0.0;
+    std::vector<int32_t> lab(m);
+    if (!ck(cudaMemcpyAsync(lab.data(), labels_, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st), "labels D2H"))
+        return false;
+    if (!ck(cudaStreamSynchronize(st), "labels sync")) return false;
+    st_synced_ok = true;
+    std::string pe = build_plan(lab.data(), m, n, L, hp);
+    if (!pe.empty()) return fail(OTGS_EINVAL, pe);
+    ntiles = hp.ntiles;
+    unit_words = (ntiles + 31) / 32;
+    // validation of C, a, b on the device
+    {
+        double* sums = (double*)dalloc(2 * sizeof(double), "check sums");
+        int* flags = (int*)dalloc(4 * sizeof(int), "check flags");
+        if (!sums || !flags) return false;
+        if (!ck(cudaMemsetAsync(sums, 0, 2 * sizeof(double), st), "memset")) return false;
+        if (!ck(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st), "memset")) return false;
+        launch_check_finite(C_, ldc_, (int32_t)m, (int32_t)n, a_, b_, sums, flags, st);
+        double hs[2];
+        int hf[4];
+        if (!ck(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st), "check D2H")) return false;
+        if (!ck(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st), "check D2H")) return false;
+        if (!ck(cudaStreamSynchronize(st), "check sync")) return false;
+        if (hf[0]) return fail(OTGS_ENONFINITE, "C has a non-finite entry");
+        if (hf[1]) return fail(OTGS_EINVAL, "C has a negative entry");
+        if (hf[2]) return fail(OTGS_EINVAL, "a and b must be positive and finite");
+        if (!(std::fabs(hs[0] - hs[1]) <= 1e-12 * std::fmax(1.0, std::fmax(hs[0], hs[1]))))
+            return fail(OTGS_EINVAL, "sum(a) != sum(b)");
+    }
+    // C: borrow when class-sorted and float4-aligned (every float4 that starts
+    // below column n then ends below n), else a sorted, padded copy
+    bool aligned = (reinterpret_cast<uintptr_t>(C_) % 16 == 0) && (ldc_ % 4 == 0) && (n % 4 == 0);
+    dp.perm = upload(this, hp.perm, "perm");
+    if (!dp.perm) return false;
+    if (hp.sorted_identity && aligned) {
+        C = C_;
+        ldc = ldc_;
+        own_C = false;
+    } else {
+        ldc = (n + 3) / 4 * 4;
+        float* Cs = (float*)dalloc(sizeof(float) * (size_t)(m * ldc), "sorted C");
+        if (!Cs) return false;
+        launch_gather_rows(C_, ldc_, dp.perm, (int32_t)m, (int32_t)n, Cs, ldc, st);
+        C = Cs;
+        own_C = true;
+    }
+    // plan arrays
+    dp.goff = upload(this, hp.goff, "goff");
+    dp.rgroup = upload(this, hp.rgroup, "rgroup");
+    dp.pkind = upload(this, hp.pkind, "pkind");
+    dp.prows = upload(this, hp.prows, "prows");
+    dp.pW = upload(this, hp.pW, "pW");
+    dp.pnch = upload(this, hp.pnch, "pnch");
+    dp.pitem = upload(this, hp.pitem, "pitem");
+    dp.pw_off = upload(this, hp.pw_off, "pw_off");
+    dp.pgrp = upload(this, hp.pgrp, "pgrp");
+    dp.gpanel = upload(this, hp.gpanel, "gpanel");
+    dp.gsrow = upload(this, hp.gsrow, "gsrow");
+    dp.prp = upload(this, hp.prp, "prp");
+    dp.item_panel = upload(this, hp.item_panel, "item_panel");
+    dp.item_chunk = upload(this, hp.item_chunk, "item_chunk");
+    dp.exec_order = upload(this, hp.exec_order, "exec_order");
+    if (!dp.goff || !dp.rgroup || !dp.pkind || !dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.pw_off ||
+        !dp.pgrp || !dp.gpanel || !dp.gsrow || !dp.prp || !dp.item_panel || !dp.item_chunk || !dp.exec_order)
+        return false;
+    std::vector<uint8_t> ones(hp.nitems(), 1);
+    item_all_active = upload(this, ones, "item_active");
+    if (!item_all_active) return false;
+    // marginals (a in sorted order)
+    a_sorted = (double*)dalloc(sizeof(double) * m, "a_sorted");
+    b = (double*)dalloc(sizeof(double) * n, "b");
+    if (!a_sorted || !b) return false;
+    launch_permute_f64(a_, dp.perm, (int32_t)m, a_sorted, true, st);
+    if (!ck(cudaMemcpyAsync(b, b_, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "b copy")) return false;
+    // evaluation buffers
+    A2 = (float2*)dalloc(sizeof(float2) * m, "A2");
+    B2 = (float2*)dalloc(sizeof(float2) * (size_t)ntiles * TW, "B2");
+    alpha_eval = (double*)dalloc(sizeof(double) * m, "alpha_eval");
+    rowpart = (double*)dalloc(sizeof(double) * (size_t)hp.rowpart_len, "rowpart");
+    colpart = (double*)dalloc(sizeof(double) * (size_t)hp.npanels() * n, "colpart");
+    psipart = (double*)dalloc(sizeof(double) * (size_t)hp.nitems(), "psipart");
+    nred = reduce_blocks((int32_t)m, (int32_t)n);
+    block_part = (double*)dalloc(sizeof(double) * 3 * (size_t)nred, "block_part");
+    counter = (unsigned*)dalloc(sizeof(unsigned) * 4, "counter");
+    scal = (double*)dalloc(sizeof(double) * 8, "scal");
+    if (!A2 || !B2 || !alpha_eval || !rowpart || !colpart || !psipart || !block_part || !counter || !scal)
+        return false;
+    if (!ck(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, st), "memset counter")) return false;
+    if (!ck(cudaMallocHost(&host_scal, sizeof(double) * 8), "cudaMallocHost")) return false;
+    // kernels use up to eval_smem_bytes() of dynamic shared memory
+    if (!ck(cudaStreamSynchronize(st), "create sync")) return false;
+    stats_host = ot_gs_stats();
+    return true;
+}
+
+EvalArgs Handle::eval_args(const int32_t* items, const uint8_t* active, const uint32_t* need, bool snap)
+{
+    EvalArgs e;
+    memset(&e, 0, sizeof(e));
+    e.C = C; e.ldc = ldc;
+    e.m = (int32_t)m; e.n = (int32_t)n; e.L = L; e.ntiles = ntiles;
+    e.npanels = hp.npanels(); e.nitems = hp.nitems();
+    e.A2 = A2; e.B2 = B2;
+    e.plan = dp;
+    e.items = items;
+    e.item_active = active;
+    e.unit_need = need;
+    e.unit_words = unit_words;
+    e.rowpart = rowpart; e.colpart = colpart; e.psipart = psipart;
+    e.zt = snap ? zt : nullptr;
+    e.ot = snap ? ot : nullptr;
+    const double theta = prm.mu * prm.gamma;
+    e.theta_hi = (float)theta;
+    e.theta_lo = (float)(theta - (double)e.theta_hi);
+    double cut = theta * theta * (1.0 - std::ldexp(1.0, -20));
+    float fc = (float)cut;
+    if ((double)fc > cut) fc = std::nextafter(fc, 0.f);
+    e.th2_cut = fc;
+    e.gamma = (float)prm.gamma;
+    e.inv2g = 1.0 / (2.0 * prm.gamma);
+    return e;
+}
+
+ReduceArgs Handle::reduce_args(const uint8_t* active, double* out_caller, double* G_sorted, const double* dir,
+                               const double* beta_ptr)
+{
+    ReduceArgs r;
+    memset(&r, 0, sizeof(r));
+    r.m = (int32_t)m; r.n = (int32_t)n; r.npanels = hp.npanels(); r.nitems = hp.nitems();
+    r.plan = dp;
+    r.item_active = active;
+    r.rowpart = rowpart; r.colpart = colpart; r.psipart = psipart;
+    r.a_sorted = a_sorted; r.b = b;
+    r.alpha_sorted = alpha_eval; r.beta = beta_ptr;
+    r.out_caller = out_caller; r.G_sorted = G_sorted; r.dir = dir;
+    r.scal = scal;
+    r.block_part = block_part;
+    r.counter = counter;
+    return r;
+}
+
+// Launch of the evaluation kernel, optionally bracketed by timing events.
+void Handle::eval_launch(const EvalArgs& e, int n_ctas)
+{
+    if (timing) {
+        while (ev_pool.size() < ev_used + 2) {
+            cudaEvent_t ev;
+            if (cudaEventCreate(&ev) != cudaSuccess) { timing = false; break; }
+            ev_pool.push_back(ev);
+        }
+    }
+    if (timing) cudaEventRecord(ev_pool[ev_used], st);
+    launch_eval(e, n_ctas, st);
+    if (timing) {
+        cudaEventRecord(ev_pool[ev_used + 1], st);
+        ev_used += 2;
+    }
+}
+
+// Dense evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.
+bool Handle::eval_dense(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
+                        double* G_sorted, const double* dir, bool snap)
+{
+    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, alpha_eval, st);
+    EvalArgs e = eval_args(dp.exec_order, item_all_active, nullptr, snap);
+    eval_launch(e, hp.nitems());
+    ReduceArgs r = reduce_args(item_all_active, out_caller, G_sorted, dir, beta);
+    launch_reduce(r, st);
+    stats_host.evals++;
+    stats_host.blocks_total += (int64_t)L * n;
+    stats_host.units_total += (int64_t)L * ntiles;
+    stats_host.units_computed += nonempty_units();
+    stats_host.c_bytes += 4.0 * (double)m * (double)n;
+    return ck(cudaGetLastError(), "eval launch");
+}
+
+int64_t Handle::nonempty_units() const
+{
+    int64_t ne = 0;
+    for (int32_t l = 0; l < L; l++) ne += hp.goff[l + 1] > hp.goff[l];
+    return ne * ntiles;
+}
+
+}  // namespace otgs
+
+// ================================================================== C ABI
+#define H_CHECK(h)                                                            \
+    do {                                                                      \
+        if (!(h)) return OTGS_EINVAL;                                         \
+    } while (0)
+
+extern "C" {
+
+int ot_gs_create(ot_gs** out, const float* C, int64_t ldc, const double* a, const double* b,
+                 const int32_t* labels, int64_t m, int64_t n, int32_t L, double gamma, double mu, void* stream)
+{
+    g_create_error.clear();
+    if (!out) { g_create_error = "h is NULL"; return OTGS_EINVAL; }
+    *out = nullptr;
+    if (!C || !a || !b || !labels) { g_create_error = "NULL input pointer"; return OTGS_EINVAL; }
+    if (m <= 0 || n <= 0 || L <= 0 || ldc < n) { g_create_error = "need m, n, L > 0 and ldc >= n"; return OTGS_EINVAL; }
+    if (!(gamma > 0.0) || !std::isfinite(gamma) || !(mu >= 0.0) || !std::isfinite(mu)) {
+        g_create_error = "need gamma > 0 and mu >= 0, finite";
+        return OTGS_EINVAL;
+    }
+    Handle* h = new (std::nothrow) Handle();
+    if (!h) { g_create_error = "out of host memory"; return OTGS_ENOMEM; }
+    if (!h->init(C, ldc, a, b, labels, m, n, L, gamma, mu, (cudaStream_t)stream)) {
+        g_create_error = h->err;
+        int code = h->last_code ? h->last_code : OTGS_ECUDA;
+        delete h;
+        return code;
+    }
+    *out = reinterpret_cast<ot_gs*>(h);
+    return OTGS_OK;
+}
+
+int ot_gs_destroy(ot_gs* hh)
+{
+    if (!hh) return OTGS_OK;
+    delete reinterpret_cast<Handle*>(hh);
+    return OTGS_OK;
+}
+
+int ot_gs_set_stream(ot_gs* hh, void* stream)
+{
+    H_CHECK(hh);
+    reinterpret_cast<Handle*>(hh)->st = (cudaStream_t)stream;
+    return OTGS_OK;
+}
+
+int ot_gs_set_params(ot_gs* hh, const ot_gs_params* p)
+{
+    H_CHECK(hh);
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!p) { h->fail(OTGS_EINVAL, "params is NULL"); return OTGS_EINVAL; }
+    if (!(p->gamma > 0.0) || !std::isfinite(p->gamma) || !(p->mu >= 0.0) || !std::isfinite(p->mu) || p->r < 1 ||
+        p->lbfgs_m < 1 || p->lbfgs_m > 32) {
+        h->fail(OTGS_EINVAL, "invalid params (gamma > 0, mu >= 0, r >= 1, 1 <= lbfgs_m <= 32)");
+        return OTGS_EINVAL;
+    }
+    bool reg_changed = p->gamma != h->prm.gamma || p->mu != h->prm.mu;
+    h->prm = *p;
+    if (reg_changed) h->invalidate_screen();
+    return OTGS_OK;
+}
+
+int ot_gs_get_params(const ot_gs* hh, ot_gs_params* p)
+{
+    H_CHECK(hh);
+    if (!p) return OTGS_EINVAL;
+    *p = reinterpret_cast<const Handle*>(hh)->prm;
+    return OTGS_OK;
+}
+
+int ot_gs_grad(ot_gs* hh, const double* alpha, const double* beta, double* out)
+{
+    H_CHECK(hh);
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!alpha || !beta || !out) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
+    if (!h->eval_dense(alpha, false, beta, out, nullptr, nullptr, false)) return h->last_code;
+    return OTGS_OK;
+}
+
+int ot_gs_get_stats(ot_gs* hh, ot_gs_stats* s)
+{
+    H_CHECK(hh);
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!s) return OTGS_EINVAL;
+    if (!h->ck(cudaStreamSynchronize(h->st), "stats sync")) return OTGS_ECUDA;
+    if (!h->collect_stats()) return h->last_code;
+    *s = h->stats_host;
+    return OTGS_OK;
+}
+
+int ot_gs_reset_stats(ot_gs* hh)
+{
+    H_CHECK(hh);
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->ck(cudaStreamSynchronize(h->st), "stats sync")) return OTGS_ECUDA;
+    h->stats_host = ot_gs_stats();
+    h->reset_device_stats();
+    return OTGS_OK;
+}
+
+int ot_gs_set_timing(ot_gs* hh, int enable)
+{
+    H_CHECK(hh);
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    h->timing = enable != 0;
+    return OTGS_OK;
+}
+
+int ot_gs_get_timing(ot_gs* hh, int64_t* launches, double* total_ms)
+{
+    H_CHECK(hh);
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->ck(cudaStreamSynchronize(h->st), "timing sync")) return OTGS_ECUDA;
+    double tot = 0.0;
+    for (size_t k = 0; k + 1 < h->ev_used; k += 2) {
+        float ms = 0.f;
+        if (!h->ck(cudaEventElapsedTime(&ms, h->ev_pool[k], h->ev_pool[k + 1]), "cudaEventElapsedTime"))
+            return OTGS_ECUDA;
+        tot += ms;
+    }
+    if (launches) *launches = (int64_t)(h->ev_used / 2);
+    if (total_ms) *total_ms = tot;
+    h->ev_used = 0;
+    return OTGS_OK;
+}
+
+const char* ot_gs_last_error(const ot_gs* hh)
+{
+    if (!hh) return g_create_error.c_str();
+    return reinterpret_cast<const Handle*>(hh)->err.c_str();
+}
+
+const char* ot_gs_version(void) { return "otgs 0.1 sm_103a"; }
+
+int ot_gs_plan_info(const int32_t* labels_host, int64_t m, int64_t n, int32_t L, int64_t* n_panels,
+                    int64_t* n_items, int64_t* rowpart_len)
+{
+    if (!labels_host) return OTGS_EINVAL;
+    HostPlan hp;
+    if (!build_plan(labels_host, m, n, L, hp).empty()) return OTGS_EINVAL;
+    if (n_panels) *n_panels = hp.npanels();
+    if (n_items) *n_items = hp.nitems();
+    if (rowpart_len) *rowpart_len = hp.rowpart_len;
+    return OTGS_OK;
+}
+
+}  // extern "C"

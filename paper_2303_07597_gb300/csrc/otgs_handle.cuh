@@ -1,0 +1,93 @@
+// otgs_handle.cuh -- the state behind an ot_gs* handle.
+#pragma once
+
+#include <string>
+#include <vector>
+
+#include "otgs_internal.cuh"
+
+namespace otgs {
+
+struct Handle {
+    cudaStream_t st = nullptr;
+    int64_t m = 0, n = 0;
+    int32_t L = 0, ntiles = 0, unit_words = 0;
+    ot_gs_params prm;
+    HostPlan hp;
+    DevPlan dp;
+    std::vector<void*> allocs;
+    std::string err;
+    int last_code = 0;
+    bool st_synced_ok = false;
+
+    // problem
+    const float* C = nullptr;
+    int64_t ldc = 0;
+    bool own_C = false;
+    double* a_sorted = nullptr;
+    double* b = nullptr;
+    float cmax = 0.f;
+
+    // one evaluation
+    float2* A2 = nullptr;
+    float2* B2 = nullptr;
+    double* alpha_eval = nullptr;   // sorted alpha of the last evaluation
+    double* rowpart = nullptr;
+    double* colpart = nullptr;
+    double* psipart = nullptr;
+    uint8_t* item_all_active = nullptr;
+    int nred = 0;
+    double* block_part = nullptr;
+    unsigned* counter = nullptr;
+    double* scal = nullptr;
+    double* host_scal = nullptr;
+
+    // screening (Sec. 3): allocated on first use
+    bool screen_alloc = false;
+    bool snap_valid = false;      // zt/ot/alpha_snap/beta_snap describe a snapshot
+    float* zt = nullptr;          // z~ (rounded up), L x ntiles*TW
+    float* ot = nullptr;          // o~, L x ntiles*TW
+    double* alpha_snap = nullptr; // sorted
+    double* beta_snap = nullptr;
+    uint32_t* Nmask = nullptr;    // set N, one word per unit (bit = column within tile)
+    uint32_t* skipmask = nullptr; // last screened evaluation's skip decisions, same layout
+    uint32_t* unit_need = nullptr;// L x unit_words
+    uint8_t* item_active = nullptr;
+    float* gstat = nullptr;       // per group: npos, nabs, nneg, theta_skip
+    float* cstat = nullptr;       // per column: dbp, dbabs, dbneg
+    unsigned* gmax = nullptr;     // float bits: max|alpha|, max|beta|, max|alpha~|, max|beta~|
+    unsigned long long* dcount = nullptr; // device counters: in_N, checked, skipped, units
+    ot_gs_stats stats_host;
+
+    // optional event timing of evaluation-kernel launches
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    void eval_launch(const EvalArgs& e, int n_ctas);
+
+    ~Handle();
+    bool init(const float* C, int64_t ldc, const double* a, const double* b, const int32_t* labels, int64_t m,
+              int64_t n, int32_t L, double gamma, double mu, cudaStream_t st);
+    bool fail(int code, const std::string& msg);
+    bool ck(cudaError_t e, const char* what);
+    void* dalloc(size_t bytes, const char* what);
+
+    EvalArgs eval_args(const int32_t* items, const uint8_t* active, const uint32_t* need, bool snap);
+    ReduceArgs reduce_args(const uint8_t* active, double* out_caller, double* G_sorted, const double* dir,
+                           const double* beta_ptr);
+    bool eval_dense(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
+                    double* G_sorted, const double* dir, bool snap);
+    int64_t nonempty_units() const;
+
+    // screening (otgs_screen_host.cu)
+    bool ensure_screen();
+    void invalidate_screen() { snap_valid = false; }
+    bool snapshot_at(const double* alpha, bool alpha_sorted, const double* beta, bool build_N,
+                     double* out_caller, double* G_sorted, const double* dir);
+    bool eval_screened(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
+                       double* G_sorted, const double* dir);
+    bool collect_stats();
+    void reset_device_stats();
+};
+
+}  // namespace otgs
