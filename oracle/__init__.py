@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-frounding-math", "-fPIC",
                                "-shared", "-fvisibility=hidden", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -65,6 +65,7 @@ def _load():
         lib.orc_primal.argtypes = [P, P]
         lib.orc_bounds.argtypes = [P, P, P, P, P, P, P, P, P]
         lib.orc_gradpsi.argtypes = [P, P, P, P, P, P, P, P, P, P, P, P]
+        lib.orc_gpu_screen.argtypes = [P, P, P, P, P, P, P, i64, P, i64, P, P, P]
         lib.orc_solve.restype = ctypes.c_int
         lib.orc_solve.argtypes = [P, P, P, dbl, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                   ctypes.c_int, ctypes.c_int, P, P, P, ctypes.c_int, P]
@@ -170,6 +171,24 @@ class Oracle:
         self._lib.orc_gradpsi(self._h, *[_p(x) for x in args], _p(zt), _p(inN), _p(D), _p(ga),
                               _p(gb), _p(skipped), _p(counts))
         return float(D[0]), ga, gb, skipped.astype(bool), counts
+
+    def gpu_screen_rule(self, alpha, beta, alpha_s, beta_s, zt, ot, Nmask=None):
+        """Replica of the CUDA path's FP32 screening rule (Eq. 6-8 with
+        directed rounding and margin).  zt, ot: float32 (L, ldz); Nmask:
+        uint32 (L, ntiles) or None.  Returns (skip words, N words, counts)."""
+        args = [_f64(alpha, self.m), _f64(beta, self.n), _f64(alpha_s, self.m),
+                _f64(beta_s, self.n)]
+        zt = np.ascontiguousarray(zt, dtype=np.float32)
+        ot = np.ascontiguousarray(ot, dtype=np.float32)
+        ntiles = (self.n + 31) // 32
+        assert zt.shape[0] == self.L and zt.shape[1] >= self.n and ot.shape == zt.shape
+        Nm = None if Nmask is None else np.ascontiguousarray(Nmask, dtype=np.uint32).reshape(self.L, ntiles)
+        skip = np.zeros((self.L, ntiles), dtype=np.uint32)
+        Nout = np.zeros((self.L, ntiles), dtype=np.uint32)
+        counts = np.zeros(3, dtype=np.int64)
+        self._lib.orc_gpu_screen(self._h, *[_p(x) for x in args], _p(zt), _p(ot), zt.shape[1], _p(Nm),
+                                 ntiles, _p(skip), _p(Nout), _p(counts))
+        return skip, Nout, counts
 
     def solve(self, tol=1e-8, maxit=1000, M=10, screening=False, use_lower=True, r=10,
               alpha0=None, beta0=None, trace=False):

@@ -18,6 +18,7 @@
  *
  * Parity pins are not in this file: see tests/test_oracle_pins.py.
  */
+#include <fenv.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -607,4 +608,154 @@ EXPORT int orc_solve(const orc_t *h, double *alpha, double *beta, double tol, in
     free(s.ga); free(s.gb);
     if (screening) { free(sc.alpha_s); free(sc.beta_s); free(sc.zt); free(sc.ot); free(sc.inN); }
     return status;
+}
+
+/* ------------------------------------- FP32 screening rule of the GPU path */
+
+/*
+ * Bit-for-bit replica of the screening decisions the CUDA path takes, written
+ * from the rule it implements (Eq. 6-8 in FP32 with directed rounding), to
+ * check the GPU's skip set and set N exactly.  Reading of the paper: Eq. 6 is
+ * evaluated with every operation rounded toward +inf (so Lemma 1 holds for the
+ * computed bound) and a block is skipped when zbar <= RD(theta - tau_l),
+ * tau_l = 2^-36 (sqrt(g_l) M + g_l theta), a margin that covers the rounding of
+ * the evaluation kernel; Eq. 7 is evaluated round-to-nearest.
+ *
+ * Group sums follow the GPU order: lane k (0..31) adds rows k, k+32, ... of
+ * the group (ascending row index), then the 32 lane values meet in a xor tree
+ * with offsets 16, 8, 4, 2, 1.
+ *
+ *   alpha, beta, alpha_s, beta_s   current iterate and snapshot (caller order)
+ *   zt, ot                          FP32 snapshot values, row l at zt + l*ldz
+ *   Nmask_in                        set N as L x ntiles words (bit = column % 32)
+ *   skip_out (optional)             L x ntiles words: blocks skipped by Eq. 6
+ *   N_out (optional)                L x ntiles words: N rebuilt from Eq. 7
+ *   counts[3] (optional)            += in N, checked, skipped
+ */
+static void xor_tree_f(float *v, int up)
+{
+    float w[32];
+    for (int off = 16; off >= 1; off >>= 1) {
+        for (int x = 0; x < 32; x++) w[x] = v[x] + v[x ^ off];
+        for (int x = 0; x < 32; x++) v[x] = w[x];
+    }
+    (void)up;
+}
+
+static float maxf_tree(const float *v)
+{
+    float r = 0.f;
+    for (int x = 0; x < 32; x++) if (v[x] > r) r = v[x];
+    return r;
+}
+
+EXPORT void orc_gpu_screen(const orc_t *h, const double *alpha, const double *beta,
+                           const double *alpha_s, const double *beta_s, const float *zt,
+                           const float *ot, int64_t ldz, const uint32_t *Nmask_in,
+                           int64_t ntiles, uint32_t *skip_out, uint32_t *N_out, int64_t *counts)
+{
+    const int32_t L = h->L;
+    const int64_t n = h->n;
+    const int old_mode = fegetround();
+    float *npos = (float *)malloc(sizeof(float) * (size_t)L);
+    float *nabs = (float *)malloc(sizeof(float) * (size_t)L);
+    float *nneg = (float *)malloc(sizeof(float) * (size_t)L);
+    float *sgru = (float *)malloc(sizeof(float) * (size_t)L);
+    float *sgrn = (float *)malloc(sizeof(float) * (size_t)L);
+    float *dbp = (float *)malloc(sizeof(float) * (size_t)n);
+    float *dba = (float *)malloc(sizeof(float) * (size_t)n);
+    float *dbn = (float *)malloc(sizeof(float) * (size_t)n);
+    float amax = 0.f, asmax = 0.f, bmax = 0.f, bsmax = 0.f, cmax = 0.f;
+    for (int64_t q = 0; q < h->m * n; q++) if (h->C[q] > cmax) cmax = h->C[q];
+    for (int32_t l = 0; l < L; l++) {
+        float pu[32], a2[32], n2[32];
+        for (int x = 0; x < 32; x++) { pu[x] = 0.f; a2[x] = 0.f; n2[x] = 0.f; }
+        int64_t g = h->goff[l + 1] - h->goff[l];
+        for (int64_t k = 0; k < g; k++) {
+            int64_t i = h->grows[h->goff[l] + k];
+            int x = (int)(k % 32);
+            fesetround(FE_UPWARD);
+            volatile double du = alpha[i] - alpha_s[i];
+            float dp = (float)du;
+            if (!(dp > 0.f)) dp = 0.f;
+            pu[x] = pu[x] + dp * dp;
+            float ar = (float)fabs(alpha[i]), asr = (float)fabs(alpha_s[i]);
+            if (ar > amax) amax = ar;
+            if (asr > asmax) asmax = asr;
+            fesetround(FE_TONEAREST);
+            volatile double dd = alpha[i] - alpha_s[i];
+            float d = (float)dd;
+            a2[x] = a2[x] + d * d;
+            float dn = d < 0.f ? d : 0.f;
+            n2[x] = n2[x] + dn * dn;
+        }
+        fesetround(FE_TONEAREST);
+        double sg = sqrt((double)g);
+        fesetround(FE_UPWARD);
+        xor_tree_f(pu, 1);
+        npos[l] = sqrtf(pu[0]);
+        sgru[l] = (float)sg;
+        fesetround(FE_TONEAREST);
+        xor_tree_f(a2, 0);
+        xor_tree_f(n2, 0);
+        nabs[l] = sqrtf(a2[0]);
+        nneg[l] = sqrtf(n2[0]);
+        sgrn[l] = (float)sqrt((double)g);
+    }
+    for (int64_t j = 0; j < n; j++) {
+        fesetround(FE_UPWARD);
+        volatile double du = beta[j] - beta_s[j];
+        float p = (float)du;
+        dbp[j] = p > 0.f ? p : 0.f;
+        float br = (float)fabs(beta[j]), bsr = (float)fabs(beta_s[j]);
+        if (br > bmax) bmax = br;
+        if (bsr > bsmax) bsmax = bsr;
+        fesetround(FE_TONEAREST);
+        volatile double dd = beta[j] - beta_s[j];
+        float d = (float)dd;
+        dba[j] = fabsf(d);
+        dbn[j] = d < 0.f ? -d : 0.f;
+    }
+    fesetround(FE_TONEAREST);
+    double M = (((double)amax + (double)bmax) + (double)asmax) + (double)bsmax + (double)cmax;
+    const double theta = h->theta;
+    const float theta_f = (float)theta;
+    int64_t c_in = 0, c_chk = 0, c_skip = 0;
+    for (int32_t l = 0; l < L; l++) {
+        int64_t g = h->goff[l + 1] - h->goff[l];
+        fesetround(FE_TONEAREST);
+        double tau = ldexp(sqrt((double)g) * M + (double)g * theta, -36);
+        double tdiff = theta - tau;
+        fesetround(FE_DOWNWARD);
+        float th_skip = (float)tdiff;
+        for (int64_t jt = 0; jt < ntiles; jt++) {
+            uint32_t sw = 0, nw = 0, Nw = Nmask_in ? Nmask_in[l * ntiles + jt] : 0u;
+            for (int lane = 0; lane < 32; lane++) {
+                int64_t j = jt * 32 + lane;
+                if (j >= n || g == 0) continue;
+                const float z = zt[l * ldz + j], o = ot[l * ldz + j];
+                int inN = (Nw >> lane) & 1u;
+                if (inN) c_in++;
+                else {
+                    c_chk++;
+                    fesetround(FE_UPWARD);
+                    float zbar = (z + npos[l]) + sgru[l] * dbp[j];
+                    if (zbar <= th_skip) { sw |= 1u << lane; c_skip++; }
+                }
+                fesetround(FE_TONEAREST);
+                float kt = sqrtf(z * z + o * o);
+                float zl = kt - nabs[l];
+                zl = zl - sgrn[l] * dba[j];
+                zl = zl - o;
+                zl = zl - nneg[l];
+                zl = zl - sgrn[l] * dbn[j];
+                if (zl > theta_f) nw |= 1u << lane;
+            }
+            if (skip_out) skip_out[l * ntiles + jt] = sw;
+            if (N_out) N_out[l * ntiles + jt] = nw;
+        }
+    }
+    fesetround(old_mode);
+    if (counts) { counts[0] += c_in; counts[1] += c_chk; counts[2] += c_skip; }
+    free(npos); free(nabs); free(nneg); free(sgru); free(sgrn); free(dbp); free(dba); free(dbn);
 }

@@ -6,7 +6,7 @@
 #include <string>
 #include <vector>
 
-#include "otgs_handle.cuh"
+#include "otgs_solver.cuh"
 
 using namespace otgs;
 
@@ -47,6 +47,7 @@ void* Handle::dalloc(size_t bytes, const char* what)
 Handle::~Handle()
 {
     if (st_synced_ok) cudaStreamSynchronize(st);
+    delete solver;
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
     if (host_scal) cudaFreeHost(host_scal);
@@ -97,6 +98,8 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
         if (hf[2]) return fail(OTGS_EINVAL, "a and b must be positive and finite");
         if (!(std::fabs(hs[0] - hs[1]) <= 1e-12 * std::fmax(1.0, std::fmax(hs[0], hs[1]))))
             return fail(OTGS_EINVAL, "sum(a) != sum(b)");
+        unsigned cbits = (unsigned)hf[3];
+        memcpy(&cmax, &cbits, sizeof(float));
     }
     // C: borrow when class-sorted and float4-aligned (every float4 that starts
     // below column n then ends below n), else a sorted, padded copy
@@ -233,6 +236,16 @@ bool Handle::eval_dense(const double* alpha, bool alpha_sorted, const double* be
                         double* G_sorted, const double* dir, bool snap)
 {
     launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, alpha_eval, st);
+    return eval_dense_core(beta, out_caller, G_sorted, dir, snap);
+}
+
+bool Handle::eval_dense_prepped(const double* beta, double* G_sorted, const double* dir)
+{
+    return eval_dense_core(beta, nullptr, G_sorted, dir, false);
+}
+
+bool Handle::eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap)
+{
     EvalArgs e = eval_args(dp.exec_order, item_all_active, nullptr, snap);
     eval_launch(e, hp.nitems());
     ReduceArgs r = reduce_args(item_all_active, out_caller, G_sorted, dir, beta);
@@ -240,7 +253,8 @@ bool Handle::eval_dense(const double* alpha, bool alpha_sorted, const double* be
     stats_host.evals++;
     stats_host.blocks_total += (int64_t)L * n;
     stats_host.units_total += (int64_t)L * ntiles;
-    stats_host.units_computed += nonempty_units();
+    dense_units += nonempty_units();
+    stats_host.units_computed = dense_units;
     stats_host.c_bytes += 4.0 * (double)m * (double)n;
     return ck(cudaGetLastError(), "eval launch");
 }

@@ -453,6 +453,7 @@ __global__ void __launch_bounds__(NTHREADS, 2) k_eval(const EvalArgs A)
 {
     extern __shared__ double smem[];
     const int item = A.items[blockIdx.x];
+    if (A.unit_need && !A.item_active[item]) return;  // screened: nothing to stream
     const int p = A.plan.item_panel[item], cc = A.plan.item_chunk[item];
     if (A.plan.pkind[p] == 0) small_item<SNAP>(A, item, p, cc, smem);
     else big_item<SNAP>(A, item, p, cc, smem);
@@ -504,19 +505,25 @@ void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, co
 }
 
 // ------------------------------------------------------------- reduce
+// Eight lanes per row and per column: lane k adds the partials k, k+8, ...
+// and the eight lane sums meet in a fixed xor tree, so the result does not
+// depend on scheduling.
 constexpr int RED_THREADS = 256;
+constexpr int RED_LANES = 8;
 
 int reduce_blocks(int32_t m, int32_t n)
 {
-    int tot = m > n ? m : n;
-    return (tot + RED_THREADS - 1) / RED_THREADS;
+    int64_t tot = (int64_t)(m > n ? m : n) * RED_LANES;
+    return (int)((tot + RED_THREADS - 1) / RED_THREADS);
 }
 
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
 {
-    __shared__ double sh[3][RED_THREADS];
+    __shared__ double sh[3][RED_THREADS / RED_LANES];
     __shared__ bool last;
-    const int t = blockIdx.x * RED_THREADS + threadIdx.x;
+    const int gt = blockIdx.x * RED_THREADS + threadIdx.x;
+    const int t = gt / RED_LANES, k = gt % RED_LANES;
+    const unsigned gmask = 0xffu << (threadIdx.x & 24);
     double ab = 0.0, dt = 0.0, inf = 0.0;
     if (t < R.m) {
         const int l = R.plan.rgroup[t];
@@ -525,33 +532,51 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
         const int rows = R.plan.prows[p], nch = R.plan.pnch[p], it0 = R.plan.pitem[p];
         const double* rp = R.rowpart + R.plan.prp[p] + loc;
         double acc = 0.0;
-        for (int c = 0; c < nch; c++)
-            if (R.item_active[it0 + c]) acc += rp[(int64_t)c * rows];
+#pragma unroll 4
+        for (int c = k; c < nch; c += RED_LANES) {
+            const double v = __ldg(rp + (int64_t)c * rows);
+            acc += __ldg(R.item_active + it0 + c) ? v : 0.0;
+        }
+        acc += __shfl_xor_sync(gmask, acc, 1);
+        acc += __shfl_xor_sync(gmask, acc, 2);
+        acc += __shfl_xor_sync(gmask, acc, 4);
         const double ga = R.a_sorted[t] - acc;
-        if (R.out_caller) R.out_caller[1 + R.plan.perm[t]] = ga;
-        if (R.G_sorted) R.G_sorted[t] = -ga;
-        if (R.dir) dt = -ga * R.dir[t];
-        inf = fabs(ga);
-        ab = R.alpha_sorted[t] * R.a_sorted[t];
+        if (k == 0) {
+            if (R.out_caller) R.out_caller[1 + R.plan.perm[t]] = ga;
+            if (R.G_sorted) R.G_sorted[t] = -ga;
+            if (R.dir) dt = -ga * R.dir[t];
+            inf = fabs(ga);
+            ab = R.alpha_sorted[t] * R.a_sorted[t];
+        }
     }
     if (t < R.n) {
         double acc = 0.0;
-        for (int p = 0; p < R.npanels; p++) {
-            const int c = t / R.plan.pW[p];
-            if (R.item_active[R.plan.pitem[p] + c]) acc += R.colpart[(int64_t)p * R.n + t];
+#pragma unroll 4
+        for (int p = k; p < R.npanels; p += RED_LANES) {
+            const int c = t / __ldg(R.plan.pW + p);
+            const double v = __ldg(R.colpart + (int64_t)p * R.n + t);
+            acc += __ldg(R.item_active + __ldg(R.plan.pitem + p) + c) ? v : 0.0;
         }
+        acc += __shfl_xor_sync(gmask, acc, 1);
+        acc += __shfl_xor_sync(gmask, acc, 2);
+        acc += __shfl_xor_sync(gmask, acc, 4);
         const double gb = R.b[t] - acc;
-        if (R.out_caller) R.out_caller[1 + R.m + t] = gb;
-        if (R.G_sorted) R.G_sorted[R.m + t] = -gb;
-        if (R.dir) dt += -gb * R.dir[R.m + t];
-        inf = fmax(inf, fabs(gb));
-        ab += R.beta[t] * R.b[t];
+        if (k == 0) {
+            if (R.out_caller) R.out_caller[1 + R.m + t] = gb;
+            if (R.G_sorted) R.G_sorted[R.m + t] = -gb;
+            if (R.dir) dt += -gb * R.dir[R.m + t];
+            inf = fmax(inf, fabs(gb));
+            ab += R.beta[t] * R.b[t];
+        }
     }
-    sh[0][threadIdx.x] = ab;
-    sh[1][threadIdx.x] = dt;
-    sh[2][threadIdx.x] = inf;
+    const int g = threadIdx.x / RED_LANES;
+    if (k == 0) {
+        sh[0][g] = ab;
+        sh[1][g] = dt;
+        sh[2][g] = inf;
+    }
     __syncthreads();
-    for (int s = RED_THREADS / 2; s > 0; s >>= 1) {
+    for (int s = RED_THREADS / RED_LANES / 2; s > 0; s >>= 1) {
         if (threadIdx.x < s) {
             sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
             sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
@@ -644,7 +669,8 @@ void launch_permute_f64(const double* src, const int32_t* perm, int32_t m, doubl
 }
 
 // flags[0]: C has a non-finite entry; flags[1]: C has a negative entry;
-// flags[2]: a or b has a non-positive or non-finite entry.  sums[0..1] = sum a, sum b.
+// flags[2]: a or b has a non-positive or non-finite entry; flags[3]: bits of max c.
+// sums[0..1] = sum a, sum b.
 __global__ void k_check(const float* __restrict__ C, int64_t ldc, int32_t m, int32_t n,
                         const double* __restrict__ a, const double* __restrict__ b, double* sums, int* flags)
 {
@@ -666,6 +692,13 @@ __global__ void k_check(const float* __restrict__ C, int64_t ldc, int32_t m, int
         if (!(v > 0.0) || !isfinite(v)) bad_m = 1;
         sb += v;
     }
+    float cm = 0.f;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < tot; k += (int64_t)gridDim.x * blockDim.x) {
+        float c = C[(k / n) * ldc + (k % n)];
+        if (c > cm) cm = c;  // NaN compares false
+    }
+    for (int off = 16; off >= 1; off >>= 1) cm = fmaxf(cm, __shfl_xor_sync(FULLMASK, cm, off));
+    if ((threadIdx.x & 31) == 0) atomicMax((unsigned*)(flags + 3), __float_as_uint(cm));
     if (__any_sync(FULLMASK, bad_f) && (threadIdx.x & 31) == 0) atomicOr(flags + 0, 1);
     if (__any_sync(FULLMASK, bad_n) && (threadIdx.x & 31) == 0) atomicOr(flags + 1, 1);
     if (__any_sync(FULLMASK, bad_m) && (threadIdx.x & 31) == 0) atomicOr(flags + 2, 1);

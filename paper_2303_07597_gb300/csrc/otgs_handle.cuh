@@ -8,6 +8,8 @@
 
 namespace otgs {
 
+struct Solver;
+
 struct Handle {
     cudaStream_t st = nullptr;
     int64_t m = 0, n = 0;
@@ -57,6 +59,9 @@ struct Handle {
     float* cstat = nullptr;       // per column: dbp, dbabs, dbneg
     unsigned* gmax = nullptr;     // float bits: max|alpha|, max|beta|, max|alpha~|, max|beta~|
     unsigned long long* dcount = nullptr; // device counters: in_N, checked, skipped, units
+    float* sg_ru = nullptr;       // sqrt(g_l) rounded up
+    float* sg_rn = nullptr;       // sqrt(g_l) rounded to nearest
+    int64_t dense_units = 0;      // units streamed by dense passes
     ot_gs_stats stats_host;
 
     // optional event timing of evaluation-kernel launches
@@ -77,10 +82,17 @@ struct Handle {
                            const double* beta_ptr);
     bool eval_dense(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
                     double* G_sorted, const double* dir, bool snap);
+    // evaluations whose float-pair split (A2, B2, alpha_eval) is already in place
+    bool eval_dense_prepped(const double* beta, double* G_sorted, const double* dir);
+    bool eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap);
+    bool eval_screened_prepped(const double* beta, double* G_sorted, const double* dir,
+                               double* out_caller = nullptr);
+    Solver* solver = nullptr;
     int64_t nonempty_units() const;
 
     // screening (otgs_screen_host.cu)
     bool ensure_screen();
+    bool zero_snapshot();
     void invalidate_screen() { snap_valid = false; }
     bool snapshot_at(const double* alpha, bool alpha_sorted, const double* beta, bool build_N,
                      double* out_caller, double* G_sorted, const double* dir);

@@ -1,0 +1,404 @@
+// otgs_screen.cu -- safe skipping of zero blocks (Sec. 3.2) and the set N of
+// surely-nonzero blocks (Sec. 3.3), on the device.
+//
+// Arithmetic of the bounds (all FP32, fixed operation order, reproduced bit
+// for bit by the oracle's replica of this rule):
+//  * upper bound (Def. 1, Eq. 6), every operation rounded toward +inf so the
+//    computed zbar is >= the exact bound (Lemma 1 survives rounding):
+//      npos_l = sqrt(sum_i [alpha_i - alpha~_i]_+^2)         (rows of group l)
+//      dbp_j  = [beta_j - beta~_j]_+
+//      zbar   = (z~ + npos_l) + sqrt(g_l) * dbp_j
+//    The block is skipped when zbar <= theta_skip_l = RD(theta - tau_l), with
+//    tau_l = 2^-36 (sqrt(g_l) M + g_l theta) and M = max|alpha| + max|beta| +
+//    max|alpha~| + max|beta~| + max c.  tau_l exceeds the rounding error of
+//    the evaluation kernel's z (double-float f and S), so a skipped block also
+//    evaluates to exactly zero there and screened == dense bit for bit.
+//  * lower bound (Def. 2, Eq. 7), round-to-nearest (N only decides which
+//    blocks are computed without a check, never a result):
+//      zlow = k~ - ||dalpha_[l]|| - sqrt(g_l)|dbeta_j| - o~ - ||[dalpha_[l]]_-|| - sqrt(g_l)|[dbeta_j]_-|
+//      k~ = sqrt(z~^2 + o~^2);  (l, j) in N  iff  zlow > theta.
+// Group sums run lane-strided over the group's sorted rows (lane k takes rows
+// k, k+32, ...) and then through a fixed xor tree (16, 8, 4, 2, 1).
+#include "otgs_handle.cuh"
+
+namespace otgs {
+
+#define FULLMASK 0xffffffffu
+
+struct ScreenArgs {
+    int32_t m, n, L, ntiles, unit_words;
+    const int32_t* goff;
+    const double* alpha;     // sorted rows, current
+    const double* alpha_s;   // sorted rows, snapshot
+    const double* beta;
+    const double* beta_s;
+    const float* zt;         // L x ntiles*TW
+    const float* ot;
+    const float* sg_ru;      // RU(sqrt(g_l))
+    const float* sg_rn;      // RN(sqrt(g_l))
+    float* gstat;            // [L][4]: npos (RU), nabs, nneg (RN)
+    float* cstat;            // [ntiles*TW][4]: dbp (RU), |dbeta|, |[dbeta]_-| (RN)
+    unsigned* gmax;          // [4] float bits, zeroed before the delta kernel
+    float cmax;
+    double theta;
+    float theta_f;
+    uint32_t* Nmask;         // [L][ntiles]
+    uint32_t* skipmask;      // [L][ntiles]
+    uint32_t* unit_need;     // [L][unit_words], zeroed before the screen kernel
+    uint8_t* item_active;    // [nitems], zeroed before the screen kernel
+    const int32_t* gpanel;
+    const int32_t* pitem;
+    const int32_t* pW;
+    unsigned long long* count;  // [0] in N, [1] checked, [2] skipped, [3] units needed
+};
+
+__device__ __forceinline__ void atomic_max_pos(unsigned* addr, float v)
+{
+    atomicMax(addr, __float_as_uint(v));  // v >= 0: integer order == float order
+}
+
+// Blocks [0, ceil(L/8)) take one group per warp; the rest take columns.
+__global__ void k_delta(const ScreenArgs S, int group_blocks)
+{
+    if ((int)blockIdx.x < group_blocks) {
+        const int l = blockIdx.x * 8 + (threadIdx.x >> 5);
+        const int lane = threadIdx.x & 31;
+        if (l >= S.L) return;
+        const int r0 = S.goff[l], r1 = S.goff[l + 1];
+        float pu = 0.f, a2 = 0.f, n2 = 0.f, amax = 0.f, asmax = 0.f;
+        for (int r = r0 + lane; r < r1; r += 32) {
+            const double al = S.alpha[r], as = S.alpha_s[r];
+            const float du = __double2float_ru(__dsub_ru(al, as));
+            const float dp = fmaxf(du, 0.f);
+            pu = __fadd_ru(pu, __fmul_ru(dp, dp));
+            const float d = __double2float_rn(__dsub_rn(al, as));
+            a2 = __fadd_rn(a2, __fmul_rn(d, d));
+            const float dn = fminf(d, 0.f);
+            n2 = __fadd_rn(n2, __fmul_rn(dn, dn));
+            amax = fmaxf(amax, __double2float_ru(fabs(al)));
+            asmax = fmaxf(asmax, __double2float_ru(fabs(as)));
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            pu = __fadd_ru(pu, __shfl_xor_sync(FULLMASK, pu, off));
+            a2 = __fadd_rn(a2, __shfl_xor_sync(FULLMASK, a2, off));
+            n2 = __fadd_rn(n2, __shfl_xor_sync(FULLMASK, n2, off));
+            amax = fmaxf(amax, __shfl_xor_sync(FULLMASK, amax, off));
+            asmax = fmaxf(asmax, __shfl_xor_sync(FULLMASK, asmax, off));
+        }
+        if (lane == 0) {
+            S.gstat[4 * l + 0] = __fsqrt_ru(pu);
+            S.gstat[4 * l + 1] = __fsqrt_rn(a2);
+            S.gstat[4 * l + 2] = __fsqrt_rn(n2);
+            S.gstat[4 * l + 3] = 0.f;
+            atomic_max_pos(S.gmax + 0, amax);
+            atomic_max_pos(S.gmax + 2, asmax);
+        }
+        return;
+    }
+    const int j = (blockIdx.x - group_blocks) * blockDim.x + threadIdx.x;
+    if (j >= S.ntiles * TW) return;
+    float dbp = 0.f, dba = 0.f, dbn = 0.f, bmax = 0.f, bsmax = 0.f;
+    if (j < S.n) {
+        const double be = S.beta[j], bs = S.beta_s[j];
+        dbp = fmaxf(__double2float_ru(__dsub_ru(be, bs)), 0.f);
+        const float d = __double2float_rn(__dsub_rn(be, bs));
+        dba = fabsf(d);
+        dbn = fabsf(fminf(d, 0.f));
+        bmax = __double2float_ru(fabs(be));
+        bsmax = __double2float_ru(fabs(bs));
+    }
+    S.cstat[4 * j + 0] = dbp;
+    S.cstat[4 * j + 1] = dba;
+    S.cstat[4 * j + 2] = dbn;
+    S.cstat[4 * j + 3] = 0.f;
+    for (int off = 16; off >= 1; off >>= 1) {
+        bmax = fmaxf(bmax, __shfl_xor_sync(FULLMASK, bmax, off));
+        bsmax = fmaxf(bsmax, __shfl_xor_sync(FULLMASK, bsmax, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(S.gmax + 1, bmax);
+        atomic_max_pos(S.gmax + 3, bsmax);
+    }
+}
+
+// theta_skip_l = RD(theta - 2^-36 (sqrt(g) M + g theta)), FP64 round-to-nearest inside.
+__device__ __forceinline__ float theta_skip(const ScreenArgs& S, int g)
+{
+    const double M = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn((double)__uint_as_float(S.gmax[0]),
+                                                             (double)__uint_as_float(S.gmax[1])),
+                                                    (double)__uint_as_float(S.gmax[2])),
+                                           (double)__uint_as_float(S.gmax[3])),
+                                  (double)S.cmax);
+    const double tau = ldexp(__dadd_rn(__dmul_rn(__dsqrt_rn((double)g), M), __dmul_rn((double)g, S.theta)), -36);
+    return __double2float_rd(__dsub_rn(S.theta, tau));
+}
+
+// One warp per unit (l, 32-column tile); lane = column in the tile.
+__global__ void k_screen(const ScreenArgs S)
+{
+    const int64_t u = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (u >= (int64_t)S.L * S.ntiles) return;
+    const int l = (int)(u / S.ntiles), jt = (int)(u % S.ntiles);
+    const int g = S.goff[l + 1] - S.goff[l];
+    const int j = jt * TW + lane;
+    const bool valid = j < S.n && g > 0;
+    const uint32_t Nw = S.Nmask[u];
+    const bool inN = valid && ((Nw >> lane) & 1u);
+    bool skip = false;
+    if (valid && !inN) {
+        const float zbar = __fadd_ru(__fadd_ru(S.zt[(int64_t)l * S.ntiles * TW + j], S.gstat[4 * l]),
+                                     __fmul_ru(S.sg_ru[l], S.cstat[4 * j]));
+        skip = zbar <= theta_skip(S, g);
+    }
+    const uint32_t skipw = __ballot_sync(FULLMASK, skip);
+    const uint32_t needw = __ballot_sync(FULLMASK, valid && !skip);
+    const uint32_t validw = __ballot_sync(FULLMASK, valid);
+    if (lane == 0) {
+        S.skipmask[u] = skipw;
+        if (needw) {
+            atomicOr(S.unit_need + (int64_t)l * S.unit_words + (jt >> 5), 1u << (jt & 31));
+            const int p = S.gpanel[l];
+            S.item_active[S.pitem[p] + (jt * TW) / S.pW[p]] = 1;
+        }
+        unsigned long long c0 = __popc(Nw & validw), c1 = __popc(~Nw & validw), c2 = __popc(skipw);
+        if (c0) atomicAdd(S.count + 0, c0);
+        if (c1) atomicAdd(S.count + 1, c1);
+        if (c2) atomicAdd(S.count + 2, c2);
+        if (needw) atomicAdd(S.count + 3, 1ull);
+    }
+}
+
+// Alg. 1 lines 4-14: N from the lower bound against the current snapshot.
+__global__ void k_build_N(const ScreenArgs S)
+{
+    const int64_t u = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (u >= (int64_t)S.L * S.ntiles) return;
+    const int l = (int)(u / S.ntiles), jt = (int)(u % S.ntiles);
+    const int g = S.goff[l + 1] - S.goff[l];
+    const int j = jt * TW + lane;
+    bool inN = false;
+    if (j < S.n && g > 0) {
+        const int64_t q = (int64_t)l * S.ntiles * TW + j;
+        const float z = S.zt[q], o = S.ot[q];
+        const float kt = __fsqrt_rn(__fadd_rn(__fmul_rn(z, z), __fmul_rn(o, o)));
+        const float sg = S.sg_rn[l];
+        float zl = __fsub_rn(kt, S.gstat[4 * l + 1]);
+        zl = __fsub_rn(zl, __fmul_rn(sg, S.cstat[4 * j + 1]));
+        zl = __fsub_rn(zl, o);
+        zl = __fsub_rn(zl, S.gstat[4 * l + 2]);
+        zl = __fsub_rn(zl, __fmul_rn(sg, S.cstat[4 * j + 2]));
+        inN = zl > S.theta_f;
+    }
+    const uint32_t w = __ballot_sync(FULLMASK, inN);
+    if (lane == 0) S.Nmask[u] = w;
+}
+
+// ------------------------------------------------------------------- host
+ScreenArgs make_screen_args(Handle* h)
+{
+    ScreenArgs s;
+    memset(&s, 0, sizeof(s));
+    s.m = (int32_t)h->m; s.n = (int32_t)h->n; s.L = h->L; s.ntiles = h->ntiles; s.unit_words = h->unit_words;
+    s.goff = h->dp.goff;
+    s.alpha = h->alpha_eval; s.alpha_s = h->alpha_snap;
+    s.beta = nullptr; s.beta_s = h->beta_snap;
+    s.zt = h->zt; s.ot = h->ot;
+    s.sg_ru = h->sg_ru; s.sg_rn = h->sg_rn;
+    s.gstat = h->gstat; s.cstat = h->cstat; s.gmax = h->gmax;
+    s.cmax = h->cmax;
+    s.theta = h->prm.mu * h->prm.gamma;
+    s.theta_f = (float)s.theta;
+    s.Nmask = h->Nmask; s.skipmask = h->skipmask; s.unit_need = h->unit_need; s.item_active = h->item_active;
+    s.gpanel = h->dp.gpanel; s.pitem = h->dp.pitem; s.pW = h->dp.pW;
+    s.count = h->dcount;
+    return s;
+}
+
+bool Handle::ensure_screen()
+{
+    if (screen_alloc) return true;
+    const size_t ldz = (size_t)ntiles * TW;
+    zt = (float*)dalloc(sizeof(float) * (size_t)L * ldz, "zt");
+    ot = (float*)dalloc(sizeof(float) * (size_t)L * ldz, "ot");
+    alpha_snap = (double*)dalloc(sizeof(double) * m, "alpha_snap");
+    beta_snap = (double*)dalloc(sizeof(double) * n, "beta_snap");
+    Nmask = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * ntiles, "Nmask");
+    skipmask = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * ntiles, "skipmask");
+    unit_need = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * unit_words, "unit_need");
+    item_active = (uint8_t*)dalloc((size_t)hp.nitems(), "item_active");
+    gstat = (float*)dalloc(sizeof(float) * 4 * (size_t)L, "gstat");
+    cstat = (float*)dalloc(sizeof(float) * 4 * ldz, "cstat");
+    gmax = (unsigned*)dalloc(sizeof(unsigned) * 8, "gmax");
+    dcount = (unsigned long long*)dalloc(sizeof(unsigned long long) * 8, "dcount");
+    if (!zt || !ot || !alpha_snap || !beta_snap || !Nmask || !skipmask || !unit_need || !item_active || !gstat ||
+        !cstat || !gmax || !dcount)
+        return false;
+    std::vector<float> ru(L), rn(L);
+    for (int32_t l = 0; l < L; l++) {
+        const double g = (double)(hp.goff[l + 1] - hp.goff[l]);
+        const double s = std::sqrt(g);
+        float f = (float)s;
+        rn[l] = f;
+        if ((double)f < s) f = std::nextafter(f, INFINITY);
+        ru[l] = f;
+    }
+    sg_ru = (float*)dalloc(sizeof(float) * L, "sg_ru");
+    sg_rn = (float*)dalloc(sizeof(float) * L, "sg_rn");
+    if (!sg_ru || !sg_rn) return false;
+    if (!ck(cudaMemcpyAsync(sg_ru, ru.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st), "sg upload"))
+        return false;
+    if (!ck(cudaMemcpyAsync(sg_rn, rn.data(), sizeof(float) * L, cudaMemcpyHostToDevice, st), "sg upload"))
+        return false;
+    if (!ck(cudaMemsetAsync(dcount, 0, sizeof(unsigned long long) * 8, st), "memset")) return false;
+    if (!ck(cudaMemsetAsync(Nmask, 0, sizeof(uint32_t) * (size_t)L * ntiles, st), "memset")) return false;
+    if (!ck(cudaStreamSynchronize(st), "screen alloc sync")) return false;
+    screen_alloc = true;
+    return true;
+}
+
+// Alg. 1 line 1: the first snapshot is taken at alpha~ = beta~ = 0 with N empty.
+bool Handle::zero_snapshot()
+{
+    cudaMemsetAsync(alpha_snap, 0, sizeof(double) * m, st);
+    cudaMemsetAsync(beta_snap, 0, sizeof(double) * n, st);
+    cudaMemsetAsync(Nmask, 0, sizeof(uint32_t) * (size_t)L * ntiles, st);
+    if (!eval_dense(alpha_snap, true, beta_snap, nullptr, nullptr, nullptr, true)) return false;
+    snap_valid = true;
+    stats_host.snapshots++;
+    return true;
+}
+
+// Delta statistics of (alpha_eval, beta) against the snapshot.
+static void launch_delta(Handle* h, const double* beta)
+{
+    ScreenArgs s = make_screen_args(h);
+    s.beta = beta;
+    cudaMemsetAsync(h->gmax, 0, sizeof(unsigned) * 4, h->st);
+    const int gblocks = (h->L + 7) / 8;
+    const int cblocks = (h->ntiles * TW + 255) / 256;
+    k_delta<<<gblocks + cblocks, 256, 0, h->st>>>(s, gblocks);
+}
+
+bool Handle::snapshot_at(const double* alpha, bool alpha_sorted, const double* beta, bool build_N,
+                         double* out_caller, double* G_sorted, const double* dir)
+{
+    if (!ensure_screen()) return false;
+    if (!snap_valid && !zero_snapshot()) return false;
+    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, alpha_eval, st);
+    if (build_N && prm.use_lower_bound) {
+        launch_delta(this, beta);
+        ScreenArgs s = make_screen_args(this);
+        s.beta = beta;
+        const int64_t units = (int64_t)L * ntiles;
+        k_build_N<<<(unsigned)((units + 7) / 8), 256, 0, st>>>(s);
+    } else if (build_N) {
+        cudaMemsetAsync(Nmask, 0, sizeof(uint32_t) * (size_t)L * ntiles, st);
+    }
+    if (!eval_dense(alpha_eval, true, beta, out_caller, G_sorted, dir, true)) return false;
+    cudaMemcpyAsync(alpha_snap, alpha_eval, sizeof(double) * m, cudaMemcpyDeviceToDevice, st);
+    cudaMemcpyAsync(beta_snap, beta, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+    stats_host.snapshots++;
+    return ck(cudaGetLastError(), "snapshot launch");
+}
+
+bool Handle::eval_screened(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
+                           double* G_sorted, const double* dir)
+{
+    if (!ensure_screen()) return false;
+    if (!snap_valid && !zero_snapshot()) return false;
+    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, alpha_eval, st);
+    return eval_screened_prepped(beta, G_sorted, dir, out_caller);
+}
+
+bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const double* dir, double* out_caller)
+{
+    if (!ensure_screen()) return false;
+    if (!snap_valid) return fail(OTGS_EINVAL, "screened evaluation without a snapshot");
+    launch_delta(this, beta);
+    cudaMemsetAsync(unit_need, 0, sizeof(uint32_t) * (size_t)L * unit_words, st);
+    cudaMemsetAsync(item_active, 0, (size_t)hp.nitems(), st);
+    ScreenArgs s = make_screen_args(this);
+    s.beta = beta;
+    const int64_t units = (int64_t)L * ntiles;
+    k_screen<<<(unsigned)((units + 7) / 8), 256, 0, st>>>(s);
+    EvalArgs e = eval_args(dp.exec_order, item_active, unit_need, false);
+    eval_launch(e, hp.nitems());
+    ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
+    launch_reduce(r, st);
+    stats_host.evals++;
+    stats_host.blocks_total += (int64_t)L * n;
+    stats_host.units_total += (int64_t)L * ntiles;
+    return ck(cudaGetLastError(), "screened eval launch");
+}
+
+bool Handle::collect_stats()
+{
+    if (!screen_alloc) return true;
+    unsigned long long c[8];
+    if (!ck(cudaMemcpy(c, dcount, sizeof(c), cudaMemcpyDeviceToHost), "stats D2H")) return false;
+    stats_host.blocks_in_N = (int64_t)c[0];
+    stats_host.blocks_checked = (int64_t)c[1];
+    stats_host.blocks_skipped = (int64_t)c[2];
+    stats_host.units_computed = dense_units + (int64_t)c[3];
+    return true;
+}
+
+void Handle::reset_device_stats()
+{
+    dense_units = 0;
+    if (screen_alloc) cudaMemsetAsync(dcount, 0, sizeof(unsigned long long) * 8, st);
+}
+
+}  // namespace otgs
+
+using namespace otgs;
+
+extern "C" {
+
+int ot_gs_grad_screened(ot_gs* hh, const double* alpha, const double* beta, double* out, uint32_t* skip_mask)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!alpha || !beta || !out) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
+    if (!h->eval_screened(alpha, false, beta, out, nullptr, nullptr)) return h->last_code;
+    if (skip_mask &&
+        !h->ck(cudaMemcpyAsync(skip_mask, h->skipmask, sizeof(uint32_t) * (size_t)h->L * h->ntiles,
+                               cudaMemcpyDeviceToDevice, h->st), "skip mask copy"))
+        return OTGS_ECUDA;
+    return OTGS_OK;
+}
+
+int ot_gs_snapshot(ot_gs* hh, const double* alpha, const double* beta, int build_N, double* out)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!alpha || !beta) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
+    if (!h->snapshot_at(alpha, false, beta, build_N != 0, out, nullptr, nullptr)) return h->last_code;
+    return OTGS_OK;
+}
+
+int ot_gs_get_screen_state(ot_gs* hh, float* zt, float* ot, double* alpha_s, double* beta_s, uint32_t* N_mask)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->ensure_screen()) return h->last_code;
+    if (!h->snap_valid) { h->fail(OTGS_EINVAL, "no snapshot yet"); return OTGS_EINVAL; }
+    const size_t lz = (size_t)h->L * h->ntiles * TW;
+    if (zt && !h->ck(cudaMemcpyAsync(zt, h->zt, sizeof(float) * lz, cudaMemcpyDeviceToDevice, h->st), "copy"))
+        return OTGS_ECUDA;
+    if (ot && !h->ck(cudaMemcpyAsync(ot, h->ot, sizeof(float) * lz, cudaMemcpyDeviceToDevice, h->st), "copy"))
+        return OTGS_ECUDA;
+    if (alpha_s) launch_permute_f64(h->alpha_snap, h->dp.perm, (int32_t)h->m, alpha_s, false, h->st);
+    if (beta_s && !h->ck(cudaMemcpyAsync(beta_s, h->beta_snap, sizeof(double) * h->n, cudaMemcpyDeviceToDevice,
+                                         h->st), "copy"))
+        return OTGS_ECUDA;
+    if (N_mask && !h->ck(cudaMemcpyAsync(N_mask, h->Nmask, sizeof(uint32_t) * (size_t)h->L * h->ntiles,
+                                         cudaMemcpyDeviceToDevice, h->st), "copy"))
+        return OTGS_ECUDA;
+    return h->ck(cudaGetLastError(), "get_screen_state") ? OTGS_OK : OTGS_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,494 @@
+// otgs_solver.cu -- L-BFGS on -D (Eq. 4) with a strong-Wolfe line search,
+// all state and arithmetic on the device (FP64).
+//
+// The two-loop recursion (Nocedal & Wright, Alg. 7.4) only needs dot products
+// of the current gradient G with the stored pairs and of the pairs with each
+// other.  Those come from one multi-dot pass per accepted step; the scalar
+// recursion then runs in one thread and one more pass forms the direction
+//   d = cG G + sum_k cy_k y_k + sum_k cs_k s_k.
+// The line search is a state machine in one thread: it reads D and the slope
+// of the trial evaluation, and sets the next trial step, or accepts.  Alg. 1's
+// snapshot refresh (with the rebuild of N) runs every r accepted iterations.
+#include <cmath>
+#include <cstddef>
+#include <cstring>
+
+#include "otgs_solver.cuh"
+
+namespace otgs {
+
+#define FULLMASK 0xffffffffu
+
+// ------------------------------------------------------------------ kernels
+// x_t = x + t d; also the float-pair split of x_t for the evaluation kernel.
+__global__ void k_trial(SolverState* S, const double* __restrict__ x, const double* __restrict__ d, double* xt,
+                        float2* A2, float2* B2, double* alpha_eval, int m, int n, int npad)
+{
+    if (S->done) return;
+    const double t = S->t;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < m) {
+        const double v = fma(t, d[i], x[i]);
+        xt[i] = v;
+        alpha_eval[i] = v;
+        const float h = __double2float_rn(v);
+        A2[i] = make_float2(h, __double2float_rn(v - (double)h));
+    }
+    if (i < npad) {
+        if (i < n) {
+            const double v = fma(t, d[m + i], x[m + i]);
+            xt[m + i] = v;
+            const float h = __double2float_rn(v);
+            B2[i] = make_float2(h, __double2float_rn(v - (double)h));
+        } else {
+            B2[i] = make_float2(-1e30f, 0.f);
+        }
+    }
+}
+
+__device__ double bracket_step(double lo, double Flo, double dlo, double hi, double Fhi, double dhi)
+{
+    const double w = hi - lo;
+    double t = lo + 0.5 * w;
+    if (dlo < 0.0 && dhi > 0.0) {
+        t = lo - dlo * w / (dhi - dlo);
+    } else {
+        const double den = 2.0 * (Fhi - Flo - dlo * w);
+        if (den > 0.0) t = lo - dlo * w * w / den;
+    }
+    if (!(t >= lo + 0.1 * w && t <= hi - 0.1 * w)) t = lo + 0.5 * w;
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long gtimer()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Line-search state machine (same rule as the oracle): scal = {D, Gt.d, ||Gt||_inf}.
+__global__ void k_linesearch(SolverState* S, const double* scal)
+{
+    if (S->done) return;
+    S->evals++;
+    S->accepted = 0;
+    S->refresh = 0;
+    const double F = -scal[0], dphi = scal[1];
+    const double F0 = S->F0, d0 = S->dphi0, t = S->t;
+    const bool suff = (F <= F0 + LS_C1 * t * d0) || (F - F0 <= LS_EPS_F * fabs(F0) && dphi <= (2.0 * LS_C1 - 1.0) * d0);
+    S->ls_evals++;
+    bool accept = S->force_accept || (suff && fabs(dphi) <= -LS_C2 * d0);
+    if (!accept) {
+        if (!suff || dphi >= 0.0) {
+            S->hi = t; S->Fhi = F; S->dhi = dphi; S->have_hi = 1;
+        } else {
+            S->lo = t; S->Flo = F; S->dlo = dphi;
+        }
+        if (S->ls_evals >= LS_MAX_EVALS || (S->have_hi && S->hi - S->lo <= 1e-15 * S->hi)) {
+            if (S->lo > 0.0) {  // evaluate once more at the last sufficient-decrease step and take it
+                S->t = S->lo;
+                S->force_accept = 1;
+            } else {
+                S->status = OTGS_ELINESEARCH;
+                S->done = 1;
+            }
+        } else {
+            S->t = S->have_hi ? bracket_step(S->lo, S->Flo, S->dlo, S->hi, S->Fhi, S->dhi) : 2.0 * t;
+        }
+    } else {
+        S->accepted = 1;
+        S->force_accept = 0;
+        S->F = F;
+        S->ginf = scal[2];
+        S->iter++;
+        if (S->ginf <= S->tol) {
+            S->status = OTGS_OK;
+            S->done = 1;
+        } else if (S->iter >= S->maxit) {
+            S->status = OTGS_ENOTCONV;
+            S->done = 1;
+        } else if (S->budget_ns > 0.0 && (double)(gtimer() - S->t_start) > S->budget_ns) {
+            S->status = OTGS_ETIMEOUT;
+            S->done = 1;
+        }
+        S->refresh = S->screening && !S->done && (S->iter % S->r == 0);
+    }
+}
+
+// Fixed-order block sum of NV values (one per thread) into out[0..NV).
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&acc)[NV], double* out)
+{
+    __shared__ double sh[SOLVER_THREADS / 32][NV];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        double v = acc[k];
+        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
+        if (lane == 0) sh[w][k] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        double v = 0.0;
+        for (int q = 0; q < SOLVER_THREADS / 32; q++) v += sh[q][threadIdx.x];
+        out[threadIdx.x] = v;
+    }
+}
+
+// Accept: s = xt - x, y = Gt - G into slot head; x = xt, G = Gt; the
+// pair-independent dots s.y, s.s, y.y, G.G per block.
+__global__ void __launch_bounds__(SOLVER_THREADS) k_accept(SolverState* S, double* x, double* G, const double* xt,
+                                                          const double* Gt, double* Sv, double* Yv, int N,
+                                                          double* pbase)
+{
+    if (!S->accepted) return;
+    const int head = S->head;
+    double* s_new = Sv + (size_t)head * N;
+    double* y_new = Yv + (size_t)head * N;
+    double acc[NBASE] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const double s = xt[i] - x[i], y = Gt[i] - G[i], g = Gt[i];
+        s_new[i] = s;
+        y_new[i] = y;
+        x[i] = xt[i];
+        G[i] = g;
+        acc[DOT_SY] += s * y;
+        acc[DOT_SS] += s * s;
+        acc[DOT_YY] += y * y;
+        acc[DOT_GG] += g * g;
+    }
+    block_sum<NBASE>(acc, pbase + (size_t)blockIdx.x * NBASE);
+}
+
+// G.G at the start of a solve (no pairs yet).
+__global__ void __launch_bounds__(SOLVER_THREADS) k_gg(const double* G, int N, double* pbase)
+{
+    double acc[NBASE] = {0.0, 0.0, 0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) acc[DOT_GG] += G[i] * G[i];
+    block_sum<NBASE>(acc, pbase + (size_t)blockIdx.x * NBASE);
+}
+
+// Per stored slot k = blockIdx.y: s_new.y_k, s_k.y_new, y_new.y_k, G.s_k, G.y_k.
+__global__ void __launch_bounds__(SOLVER_THREADS) k_pairdots(const SolverState* S, const double* G, const double* Sv,
+                                                            const double* Yv, int N, double* ppair)
+{
+    if (!S->accepted) return;
+    const int k = blockIdx.y, head = S->head;
+    const double* s_new = Sv + (size_t)head * N;
+    const double* y_new = Yv + (size_t)head * N;
+    const double* sk = Sv + (size_t)k * N;
+    const double* yk = Yv + (size_t)k * N;
+    double acc[NPAIR] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const double sn = s_new[i], yn = y_new[i], g = G[i], s = sk[i], y = yk[i];
+        acc[PD_SNEW_Y] += sn * y;
+        acc[PD_S_YNEW] += s * yn;
+        acc[PD_YNEW_Y] += yn * y;
+        acc[PD_G_S] += g * s;
+        acc[PD_G_Y] += g * y;
+    }
+    block_sum<NPAIR>(acc, ppair + ((size_t)k * gridDim.x + blockIdx.x) * NPAIR);
+}
+
+// Sum block partials in block order; then the two-loop recursion on scalars,
+// the descent check, and the start of the next line search.
+__global__ void k_direction(SolverState* S, const double* pbase, const double* ppair, int nblocks, int start)
+{
+    if (S->done || (!start && !S->accepted)) return;
+    const int M = S->M;
+    __shared__ double base[NBASE];
+    __shared__ double pd[MAX_LBFGS_M][NPAIR];
+    for (int q = threadIdx.x; q < NBASE; q += blockDim.x) {
+        double v = 0.0;
+        for (int b = 0; b < nblocks; b++) v += pbase[(size_t)b * NBASE + q];
+        base[q] = v;
+    }
+    for (int q = threadIdx.x; q < M * NPAIR; q += blockDim.x) {
+        const int k = q / NPAIR, c = q % NPAIR;
+        double v = 0.0;
+        if (!start)
+            for (int b = 0; b < nblocks; b++) v += ppair[((size_t)k * nblocks + b) * NPAIR + c];
+        pd[k][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+    if (!start) {
+        // curvature pair: keep it only with enough positive curvature
+        const int head = S->head;
+        const double sy = base[DOT_SY];
+        if (sy > 1e-12 * sqrt(base[DOT_SS] * base[DOT_YY])) {
+            for (int k = 0; k < M; k++) {
+                S->SY[head * M + k] = pd[k][PD_SNEW_Y];  // s_head . y_k
+                S->SY[k * M + head] = pd[k][PD_S_YNEW];  // s_k . y_head
+                S->YY[head * M + k] = pd[k][PD_YNEW_Y];
+                S->YY[k * M + head] = pd[k][PD_YNEW_Y];
+            }
+            S->SY[head * M + head] = sy;
+            S->YY[head * M + head] = base[DOT_YY];
+            S->head = (head + 1) % M;
+            if (S->npairs < M) S->npairs++;
+        } else if (S->npairs == M) {
+            S->npairs = M - 1;  // the rejected pair overwrote the oldest slot
+        }
+    }
+    const int np = S->npairs, hd = S->head;
+    double a[MAX_LBFGS_M], b[MAX_LBFGS_M];
+    int idx[MAX_LBFGS_M];
+    for (int k = 0; k < np; k++) idx[k] = ((hd - np + k) % M + M) % M;  // oldest .. newest
+    // first loop, newest to oldest: a_i = rho_i s_i.q,  q = G - sum_{newer} a_k y_k
+    for (int u = np - 1; u >= 0; u--) {
+        const int i = idx[u];
+        double sq = pd[i][PD_G_S];
+        for (int v = u + 1; v < np; v++) sq -= a[v] * S->SY[i * M + idx[v]];
+        a[u] = sq / S->SY[i * M + i];
+    }
+    double h0 = 1.0;
+    if (np > 0) {
+        const int nw = idx[np - 1];
+        h0 = S->SY[nw * M + nw] / S->YY[nw * M + nw];
+    }
+    // second loop, oldest to newest: b_i = rho_i y_i.r, r = h0 q + sum_{older}(a_k - b_k) s_k
+    for (int u = 0; u < np; u++) {
+        const int i = idx[u];
+        double yq = pd[i][PD_G_Y];
+        for (int v = 0; v < np; v++) yq -= a[v] * S->YY[i * M + idx[v]];
+        double yr = h0 * yq;
+        for (int v = 0; v < u; v++) yr += (a[v] - b[v]) * S->SY[idx[v] * M + i];
+        b[u] = yr / S->SY[i * M + i];
+    }
+    // d = -(h0 q + sum (a - b) s) = -h0 G + h0 sum a y - sum (a - b) s
+    double cG = -h0;
+    double dphi0 = cG * base[DOT_GG];
+    for (int k = 0; k < MAX_LBFGS_M; k++) { S->cy[k] = 0.0; S->cs[k] = 0.0; }
+    for (int u = 0; u < np; u++) {
+        const int i = idx[u];
+        S->cy[i] = h0 * a[u];
+        S->cs[i] = -(a[u] - b[u]);
+        dphi0 += S->cy[i] * pd[i][PD_G_Y] + S->cs[i] * pd[i][PD_G_S];
+    }
+    if (!(dphi0 < 0.0)) {  // not a descent direction: restart from -G
+        for (int k = 0; k < MAX_LBFGS_M; k++) { S->cy[k] = 0.0; S->cs[k] = 0.0; }
+        S->npairs = 0;
+        cG = -1.0;
+        dphi0 = -base[DOT_GG];
+    }
+    S->cG = cG;
+    S->dphi0 = dphi0;
+    S->F0 = S->F;
+    const double ginf = S->ginf;
+    S->t = (S->iter == 0 && S->npairs == 0 && ginf > 0.0) ? 1.0 / ginf : 1.0;
+    S->lo = 0.0; S->Flo = S->F; S->dlo = dphi0;
+    S->hi = 0.0; S->Fhi = 0.0; S->dhi = 0.0; S->have_hi = 0;
+    S->ls_evals = 0;
+    S->force_accept = 0;
+}
+
+// d = cG G + sum_k cy_k y_k + sum_k cs_k s_k
+__global__ void k_combine(const SolverState* S, const double* G, const double* Sv, const double* Yv, double* d,
+                          int N, int M, int start)
+{
+    if (S->done || (!start && !S->accepted)) return;
+    const double cG = S->cG;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        double v = cG * G[i];
+        for (int k = 0; k < M; k++) {
+            const double cy = S->cy[k], cs = S->cs[k];
+            if (cy != 0.0) v += cy * Yv[(size_t)k * N + i];
+            if (cs != 0.0) v += cs * Sv[(size_t)k * N + i];
+        }
+        d[i] = v;
+    }
+}
+
+// Start of a solve: F, ||G|| from the evaluation at x; convergence at x.
+__global__ void k_start(SolverState* S, const double* scal)
+{
+    S->F = -scal[0];
+    S->ginf = scal[2];
+    S->evals++;
+    if (S->ginf <= S->tol) {
+        S->status = OTGS_OK;
+        S->done = 1;
+    } else if (S->maxit <= 0) {
+        S->status = OTGS_ENOTCONV;
+        S->done = 1;
+    }
+    S->t_start = gtimer();
+}
+
+// ------------------------------------------------------------------- host
+bool Solver::init(Handle* h_)
+{
+    h = h_;
+    N = (int)(h->m + h->n);
+    M = h->prm.lbfgs_m;
+    nblk = 2 * 152;
+    auto al = [&](size_t bytes, const char* w) { return h->dalloc(bytes, w); };
+    state = (SolverState*)al(sizeof(SolverState), "solver state");
+    x = (double*)al(sizeof(double) * N, "x");
+    G = (double*)al(sizeof(double) * N, "G");
+    d = (double*)al(sizeof(double) * N, "d");
+    xt = (double*)al(sizeof(double) * N, "xt");
+    Gt = (double*)al(sizeof(double) * N, "Gt");
+    Sv = (double*)al(sizeof(double) * (size_t)N * M, "S");
+    Yv = (double*)al(sizeof(double) * (size_t)N * M, "Y");
+    pbase = (double*)al(sizeof(double) * (size_t)nblk * NBASE, "dot partials");
+    ppair = (double*)al(sizeof(double) * (size_t)nblk * M * NPAIR, "pair dot partials");
+    if (cudaMallocHost(&hstate, sizeof(SolverState)) != cudaSuccess) {
+        hstate = nullptr;
+        return h->fail(OTGS_ENOMEM, "cudaMallocHost(solver state)");
+    }
+    if (!state || !x || !G || !d || !xt || !Gt || !Sv || !Yv || !pbase || !ppair) return false;
+    cudaMemsetAsync(x, 0, sizeof(double) * N, h->st);
+    cudaMemsetAsync(Sv, 0, sizeof(double) * (size_t)N * M, h->st);
+    cudaMemsetAsync(Yv, 0, sizeof(double) * (size_t)N * M, h->st);
+    return h->ck(cudaGetLastError(), "solver init");
+}
+
+Solver::~Solver()
+{
+    if (hstate) cudaFreeHost(hstate);
+}
+
+int Solver::run(double tol, int maxit)
+{
+    cudaStream_t st = h->st;
+    SolverState init;
+    memset(&init, 0, sizeof(init));
+    init.tol = tol;
+    init.maxit = maxit;
+    init.M = M;
+    init.r = h->prm.r;
+    init.screening = h->prm.use_screening;
+    init.budget_ns = h->prm.time_budget_ms > 0 ? h->prm.time_budget_ms * 1e6 : 0.0;
+    init.npairs = 0;
+    init.head = 0;
+    init.status = OTGS_ENOTCONV;
+    if (!h->ck(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st), "state H2D")) return h->last_code;
+    // Alg. 1 line 1: snapshot at the start point, N empty
+    if (h->prm.use_screening) {
+        h->invalidate_screen();
+        if (!h->ensure_screen()) return h->last_code;
+        cudaMemsetAsync(h->Nmask, 0, sizeof(uint32_t) * (size_t)h->L * h->ntiles, st);
+        h->snap_valid = true;  // replaced right away by the snapshot at x
+        if (!h->snapshot_at(x, true, x + h->m, false, nullptr, G, nullptr)) return h->last_code;
+    } else {
+        if (!h->eval_dense(x, true, x + h->m, nullptr, G, nullptr, false)) return h->last_code;
+    }
+    k_start<<<1, 1, 0, st>>>(state, h->scal);
+    k_gg<<<nblk, SOLVER_THREADS, 0, st>>>(G, N, pbase);
+    k_direction<<<1, 128, 0, st>>>(state, pbase, ppair, nblk, 1);
+    k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 1);
+    const int npad = h->ntiles * TW;
+    const int tb = (std::max((int)h->m, npad) + 255) / 256;
+    const size_t hdr = offsetof(SolverState, tol);  // the int fields and the eval counter
+    const long long max_trials = (long long)maxit * (LS_MAX_EVALS + 2) + 16;
+    for (long long trial = 0;; trial++) {
+        if (!h->ck(cudaMemcpyAsync(hstate, state, hdr, cudaMemcpyDeviceToHost, st), "state D2H") ||
+            !h->ck(cudaStreamSynchronize(st), "solver sync"))
+            return h->last_code;
+        if (hstate->done) break;
+        if (trial >= max_trials) {  // the device loop always ends first; this is a second guard
+            h->fail(OTGS_ENOTCONV, "solver exceeded its trial budget");
+            break;
+        }
+        k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->A2, h->B2, h->alpha_eval, (int)h->m, (int)h->n, npad);
+        if (!eval_trial()) return h->last_code;
+        k_linesearch<<<1, 1, 0, st>>>(state, h->scal);
+        k_accept<<<nblk, SOLVER_THREADS, 0, st>>>(state, x, G, xt, Gt, Sv, Yv, N, pbase);
+        k_pairdots<<<dim3(nblk, M), SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, N, ppair);
+        if (h->prm.use_screening) {
+            if (!h->ck(cudaMemcpyAsync(hstate, state, hdr, cudaMemcpyDeviceToHost, st), "D2H") ||
+                !h->ck(cudaStreamSynchronize(st), "solver sync"))
+                return h->last_code;
+            if (hstate->refresh && !h->snapshot_at(x, true, x + h->m, true, nullptr, nullptr, nullptr))
+                return h->last_code;
+        }
+        k_direction<<<1, 128, 0, st>>>(state, pbase, ppair, nblk, 0);
+        k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 0);
+        if (!h->ck(cudaGetLastError(), "solver launch")) return h->last_code;
+    }
+    if (!h->ck(cudaMemcpyAsync(hstate, state, sizeof(SolverState), cudaMemcpyDeviceToHost, st), "state D2H") ||
+        !h->ck(cudaStreamSynchronize(st), "solver sync"))
+        return h->last_code;
+    h->stats_host.iters = hstate->iter;
+    iters = hstate->iter;
+    D = -hstate->F;
+    ginf = hstate->ginf;
+    return hstate->status;
+}
+
+// Evaluation of the trial point prepared by k_trial (A2/B2/alpha_eval are set).
+bool Solver::eval_trial()
+{
+    const double* beta = xt + h->m;
+    if (h->prm.use_screening) return h->eval_screened_prepped(beta, Gt, d);
+    return h->eval_dense_prepped(beta, Gt, d);
+}
+
+}  // namespace otgs
+
+using namespace otgs;
+
+extern "C" {
+
+int ot_gs_solve(ot_gs* hh, double tol, int32_t maxit)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!(tol >= 0.0) || maxit < 0) { h->fail(OTGS_EINVAL, "need tol >= 0 and maxit >= 0"); return OTGS_EINVAL; }
+    if (!h->solver) {
+        h->solver = new (std::nothrow) Solver();
+        if (!h->solver || !h->solver->init(h)) {
+            delete h->solver;
+            h->solver = nullptr;
+            if (!h->last_code) h->fail(OTGS_ENOMEM, "solver allocation");
+            return h->last_code;
+        }
+    } else if (h->solver->M != h->prm.lbfgs_m) {
+        h->fail(OTGS_EINVAL, "lbfgs_m changed after the first solve");
+        return OTGS_EINVAL;
+    }
+    return h->solver->run(tol, maxit);
+}
+
+int ot_gs_get_solution(ot_gs* hh, double* alpha, double* beta, double* D, double* grad_inf, int32_t* iters)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->solver) { h->fail(OTGS_EINVAL, "no solve yet"); return OTGS_EINVAL; }
+    Solver* s = h->solver;
+    if (alpha) launch_permute_f64(s->x, h->dp.perm, (int32_t)h->m, alpha, false, h->st);
+    if (beta && !h->ck(cudaMemcpyAsync(beta, s->x + h->m, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st),
+                       "copy"))
+        return OTGS_ECUDA;
+    if (!h->ck(cudaStreamSynchronize(h->st), "sync")) return OTGS_ECUDA;
+    if (D) *D = s->D;
+    if (grad_inf) *grad_inf = s->ginf;
+    if (iters) *iters = s->iters;
+    return OTGS_OK;
+}
+
+int ot_gs_set_state(ot_gs* hh, const double* alpha, const double* beta)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!alpha || !beta) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
+    if (!h->solver) {
+        h->solver = new (std::nothrow) Solver();
+        if (!h->solver || !h->solver->init(h)) {
+            delete h->solver;
+            h->solver = nullptr;
+            return h->last_code ? h->last_code : OTGS_ENOMEM;
+        }
+    }
+    Solver* s = h->solver;
+    launch_permute_f64(alpha, h->dp.perm, (int32_t)h->m, s->x, true, h->st);
+    if (!h->ck(cudaMemcpyAsync(s->x + h->m, beta, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st), "copy"))
+        return OTGS_ECUDA;
+    h->invalidate_screen();
+    return h->ck(cudaGetLastError(), "set_state") ? OTGS_OK : OTGS_ECUDA;
+}
+
+}  // extern "C"

@@ -1,0 +1,105 @@
+"""Screening on the GPU (Alg. 2, Eq. 6-8) against the oracle: the skip set and
+the set N bit for bit (given the GPU's stored snapshot), skipped blocks safe
+(zero gradient in exact FP64), and screened evaluation == dense evaluation bit
+for bit (Thm. 2)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from gpu_util import DEV, check_grad, solver
+
+pytestmark = pytest.mark.gpu
+
+
+def _state(s, p):
+    nt = (p.n + 31) // 32
+    zt = torch.empty(p.L * nt * 32, dtype=torch.float32, device=DEV)
+    ot = torch.empty_like(zt)
+    al = torch.empty(p.m, dtype=torch.float64, device=DEV)
+    be = torch.empty(p.n, dtype=torch.float64, device=DEV)
+    Nm = torch.empty(p.L * nt, dtype=torch.int32, device=DEV)
+    import paper_2303_07597_gb300 as pk
+    pk.ot_gs_get_screen_state(s.h, zt, ot, al, be, Nm)
+    torch.cuda.synchronize()
+    return (zt.cpu().numpy().reshape(p.L, nt * 32), ot.cpu().numpy().reshape(p.L, nt * 32),
+            al.cpu().numpy(), be.cpu().numpy(), Nm.cpu().numpy().view(np.uint32).reshape(p.L, nt))
+
+
+def _points(p, gamma, mu, seed):
+    """A snapshot point x0 after a few oracle iterations and a nearby x1."""
+    o = oracle.Oracle.from_problem(p, gamma, mu)
+    r0 = o.solve(tol=1e-12, maxit=15)
+    r1 = o.solve(tol=1e-12, maxit=25)
+    return o, (r0["alpha"], r0["beta"]), (r1["alpha"], r1["beta"])
+
+
+CASES = [
+    ("tiny", lambda: synth.tiny(seed=0), 1.0, 0.1),
+    ("ragged", lambda: synth.random_instance(300, 77, 7, seed=0), 0.7, 0.3),
+    ("biggroups", lambda: synth.random_instance(513, 129, 3, seed=1), 1.0, 0.2),
+    ("mixed", lambda: synth.random_instance(700, 96, 40, seed=4, min_size=0), 0.5, 0.5),
+]
+
+
+@pytest.mark.parametrize("name,mk,gamma,mu", CASES)
+def test_screened_equals_dense_and_skip_set_matches_oracle(name, mk, gamma, mu):
+    p = mk()
+    o, x0, x1 = _points(p, gamma, mu, 0)
+    s = solver(p, gamma, mu)
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(DEV)
+    s.snapshot(t(x0[0]), t(x0[1]), build_N=False)
+    nt = (p.n + 31) // 32
+    skip = torch.zeros(p.L * nt, dtype=torch.int32, device=DEV)
+    out_s = s.grad_screened(t(x1[0]), t(x1[1]), skip_mask=skip)
+    out_d = s.grad(t(x1[0]), t(x1[1]))
+    torch.cuda.synchronize()
+    # Thm. 2: identical results, bit for bit
+    assert torch.equal(out_s, out_d), (out_s - out_d).abs().max().item()
+    check_grad(out_s, o.dual(x1[0], x1[1]), x1[0], x1[1], p.a, p.b, name)
+    # skip set == oracle replica of the rule on the GPU's stored snapshot
+    zt, ot, als, bes, Nm = _state(s, p)
+    assert np.allclose(als, x0[0], rtol=0, atol=0) and np.array_equal(bes, x0[1])
+    sk_ref, _, cnt = o.gpu_screen_rule(x1[0], x1[1], als, bes, zt, ot, Nm)
+    sk_gpu = skip.cpu().numpy().view(np.uint32).reshape(p.L, nt)
+    assert np.array_equal(sk_gpu, sk_ref)
+    assert cnt[2] > 0, "expected some skipped blocks"
+    # safety (Lemma 2): every skipped block has z <= theta in exact FP64
+    _, _, _, z, _ = o.dual(x1[0], x1[1], want_norms=True)
+    bits = np.unpackbits(sk_gpu.view(np.uint8), bitorder="little").reshape(p.L, nt * 32)[:, :p.n]
+    assert (z[bits.astype(bool)] <= o.theta).all()
+
+
+@pytest.mark.parametrize("name,mk,gamma,mu", CASES[:3])
+def test_N_rebuild_matches_oracle(name, mk, gamma, mu):
+    p = mk()
+    o, x0, x1 = _points(p, gamma, mu, 1)
+    s = solver(p, gamma, mu)
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(DEV)
+    s.snapshot(t(x0[0]), t(x0[1]), build_N=False)
+    zt0, ot0, als, bes, _ = _state(s, p)
+    s.snapshot(t(x1[0]), t(x1[1]), build_N=True)
+    _, _, _, _, Nm = _state(s, p)
+    _, N_ref, _ = o.gpu_screen_rule(x1[0], x1[1], als, bes, zt0, ot0, None)
+    assert np.array_equal(Nm, N_ref)
+    # Lemma 4: every block of N has a nonzero gradient block (z > theta)
+    _, _, _, z, _ = o.dual(x1[0], x1[1], want_norms=True)
+    nt = (p.n + 31) // 32
+    bits = np.unpackbits(Nm.view(np.uint8), bitorder="little").reshape(p.L, nt * 32)[:, :p.n]
+    assert (z[bits.astype(bool)] > o.theta).all()
+
+
+def test_snapshot_values_bound_the_exact_norms():
+    """Stored z~ is an upper bound of the exact z (rounded up), o~ ~ exact."""
+    p = synth.random_instance(400, 100, 5, seed=3)
+    o = oracle.Oracle.from_problem(p, 1.0, 0.2)
+    al, be = synth.random_duals(p.m, p.n, seed=4)
+    s = solver(p, 1.0, 0.2)
+    t = lambda v: torch.from_numpy(np.ascontiguousarray(v)).to(DEV)
+    s.snapshot(t(al), t(be), build_N=False)
+    zt, ot, _, _, _ = _state(s, p)
+    _, _, _, z, oo = o.dual(al, be, want_norms=True)
+    assert (zt[:, :p.n].astype(np.float64) >= z * (1 - 1e-12)).all()
+    assert np.allclose(zt[:, :p.n], z, rtol=1e-6, atol=1e-30)
+    assert np.allclose(ot[:, :p.n], oo, rtol=1e-4, atol=1e-6)
