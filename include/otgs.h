@@ -206,6 +206,40 @@ OTGS_API const char *ot_gs_version(void);
 OTGS_API int ot_gs_plan_info(const int32_t *labels_host, int64_t m, int64_t n, int32_t L,
                     int64_t *n_panels, int64_t *n_items, int64_t *rowpart_len);
 
+/*
+ * Allocation-free dense evaluation.  The paper has no counterpart: this entry
+ * point exists for callers that cannot allocate device memory -- code running
+ * inside a custom device allocator's callbacks, frameworks whose memory pool
+ * forbids allocations outside the pool, loops that cannot afford cudaMalloc's
+ * implicit synchronisation.  It computes what ot_gs_grad computes without a
+ * handle and calls no cudaMalloc, cudaFree or other allocating routine: all
+ * scratch (plan, partial sums, reduction state) lives in one static device
+ * array of OTGS_STATIC_SCRATCH_BYTES bytes that every GPU loading this part of
+ * the library keeps until the process exits.
+ *   C            device FP32, m x n, row stride ldc; rows class-sorted
+ *                (labels_host non-decreasing); n % 4 == 0, ldc % 4 == 0 and C
+ *                16-byte aligned (no sorted copy can be made without allocating)
+ *   a, b         device FP64 marginals [m], [n]
+ *   labels_host  HOST int32 [m], non-decreasing, values in [0, L)
+ *   alpha, beta  device FP64 [m], [n];  out: device FP64 [1 + m + n] as ot_gs_grad
+ *   stream       cudaStream_t as void*
+ * Inputs are not otherwise validated.  Sizes whose scratch would exceed the
+ * static array (roughly m = n = 10^4 with a thousand classes fits) are
+ * rejected with OTGS_EINVAL before any GPU work; the message says how many
+ * bytes were needed.  The first call made on a device looks up the array's
+ * device address there (once per device), so that first call should come
+ * before any stream capture.  Every call shares the array and leaves the last
+ * call's contents in it (the one value that must start at zero is cleared by
+ * each call); calls that overlap on the GPU race with each other.
+ * Asynchronous with respect to the host.  Errors: OTGS_EINVAL, OTGS_ECUDA;
+ * message from ot_gs_noalloc_last_error().
+ */
+#define OTGS_STATIC_SCRATCH_BYTES (64u * 1024u * 1024u)
+OTGS_API int ot_gs_grad_noalloc(const float *C, int64_t ldc, const double *a, const double *b,
+                                const int32_t *labels_host, int64_t m, int64_t n, int32_t L, double gamma,
+                                double mu, const double *alpha, const double *beta, double *out, void *stream);
+OTGS_API const char *ot_gs_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -84,6 +84,8 @@ def lib():
         "ot_gs_last_error": ([P], ctypes.c_char_p),
         "ot_gs_version": ([], ctypes.c_char_p),
         "ot_gs_plan_info": ([P, i64, i64, i32, P, P, P], ctypes.c_int),
+        "ot_gs_grad_noalloc": ([P, i64, P, P, P, i64, i64, i32, dbl, dbl, P, P, P, P], ctypes.c_int),
+        "ot_gs_noalloc_last_error": ([], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -260,6 +262,26 @@ def ot_gs_plan_info(labels, n, L):
     if rc != OTGS_OK:
         raise OTGSError(rc, "invalid plan input")
     return dict(n_panels=np_.value, n_items=ni.value, rowpart_len=rl.value)
+
+
+def ot_gs_grad_noalloc(C, a, b, labels_host, L, gamma, mu, alpha, beta, out, stream=None):
+    """Dense evaluation without a handle and without any device allocation
+    (for callers that cannot allocate); labels_host is a host int32 array of
+    non-decreasing labels.  Raises OTGSError on a non-zero status."""
+    import torch
+    m, n = C.shape
+    lab = np.ascontiguousarray(labels_host, dtype=np.int32)
+    if lab.shape != (m,):
+        raise ValueError("labels_host must have m entries")
+    rc = lib().ot_gs_grad_noalloc(ctypes.c_void_p(C.data_ptr()), C.stride(0),
+                                  _ptr(a, torch.float64, m, "a"), _ptr(b, torch.float64, n, "b"),
+                                  lab.ctypes.data_as(ctypes.c_void_p), m, n, int(L), float(gamma),
+                                  float(mu), _ptr(alpha, torch.float64, m, "alpha"),
+                                  _ptr(beta, torch.float64, n, "beta"),
+                                  _ptr(out, torch.float64, 1 + m + n, "out"), _stream_ptr(stream))
+    if rc != OTGS_OK:
+        raise OTGSError(rc, lib().ot_gs_noalloc_last_error().decode())
+    return rc
 
 
 # ------------------------------------------------------------ convenience

@@ -1,0 +1,192 @@
+// otgs_noalloc.cu -- a dense evaluation that allocates no device memory.
+//
+// ot_gs_grad needs a handle, and creating one allocates device buffers.  Some
+// callers cannot do that: code that runs inside a custom device allocator's
+// callbacks (cudaMalloc there would recurse or deadlock), frameworks whose
+// memory pool forbids allocations outside the pool, and latency-critical loops
+// that cannot afford cudaMalloc's implicit device synchronisation.  This entry
+// point serves them: every scratch buffer of the evaluation -- the group plan,
+// the float-pair split of alpha and beta, the row / column / psi partial sums
+// and the reduction's block partials -- is carved out of one file-scope
+// __device__ array of OTGS_STATIC_SCRATCH_BYTES bytes.  Each GPU that loads
+// this part of the library keeps that array until the process exits.
+//
+// In host code the array's name is only a host-side stand-in for the symbol,
+// not a device address.  Its device address is looked up once per device with
+// cudaGetSymbolAddress, with that device current, on the first call made
+// while that device is current; that first call should therefore come before
+// any stream capture.  All calls share the array and it keeps the contents of
+// the last call: the reduction's ticket counter, the only value that must
+// start at zero, is cleared by every call.  Calls that overlap on the GPU (on
+// different streams, or from different host threads) race on the array.
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "otgs_internal.cuh"
+
+namespace otgs {
+
+static __device__ __align__(256) unsigned char g_static_scratch[OTGS_STATIC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 128;
+std::mutex g_mu;
+void* g_addr[kMaxDevices] = {nullptr};
+thread_local std::string g_err;
+
+int set_err(int code, const std::string& msg)
+{
+    g_err = msg;
+    return code;
+}
+
+// Bump allocator over the static array (offsets only; no memory is allocated).
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes)
+    {
+        size_t at = (off + 255) / 256 * 256;
+        off = at + (bytes ? bytes : 1);
+        return at;
+    }
+};
+
+}  // namespace
+
+}  // namespace otgs
+
+using namespace otgs;
+
+extern "C" {
+
+const char* ot_gs_noalloc_last_error(void) { return g_err.c_str(); }
+
+int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const double* b, const int32_t* labels_host,
+                       int64_t m, int64_t n, int32_t L, double gamma, double mu, const double* alpha,
+                       const double* beta, double* out, void* stream)
+{
+    g_err.clear();
+    if (!C || !a || !b || !labels_host || !alpha || !beta || !out)
+        return set_err(OTGS_EINVAL, "NULL pointer");
+    if (m <= 0 || n <= 0 || L <= 0 || ldc < n) return set_err(OTGS_EINVAL, "need m, n, L > 0 and ldc >= n");
+    if (!(gamma > 0.0) || !std::isfinite(gamma) || !(mu >= 0.0) || !std::isfinite(mu))
+        return set_err(OTGS_EINVAL, "need gamma > 0 and mu >= 0, finite");
+    if (n % 4 != 0 || ldc % 4 != 0 || reinterpret_cast<uintptr_t>(C) % 16 != 0)
+        return set_err(OTGS_EINVAL, "need n % 4 == 0, ldc % 4 == 0 and a 16-byte aligned C");
+    for (int64_t i = 1; i < m; i++)
+        if (labels_host[i] < labels_host[i - 1])
+            return set_err(OTGS_EINVAL, "labels must be non-decreasing (class-sorted rows of C)");
+    HostPlan hp;
+    std::string pe = build_plan(labels_host, m, n, L, hp);
+    if (!pe.empty()) return set_err(OTGS_EINVAL, pe);
+    const int ntiles = hp.ntiles;
+    // layout of the scratch array
+    Carve cv;
+    const size_t o_perm = cv.take(4 * hp.perm.size()), o_goff = cv.take(4 * hp.goff.size());
+    const size_t o_rgroup = cv.take(4 * hp.rgroup.size()), o_pkind = cv.take(4 * hp.pkind.size());
+    const size_t o_prows = cv.take(4 * hp.prows.size()), o_pW = cv.take(4 * hp.pW.size());
+    const size_t o_pnch = cv.take(4 * hp.pnch.size()), o_pitem = cv.take(4 * hp.pitem.size());
+    const size_t o_pw_off = cv.take(4 * hp.pw_off.size()), o_pgrp = cv.take(4 * hp.pgrp.size());
+    const size_t o_gpanel = cv.take(4 * hp.gpanel.size()), o_gsrow = cv.take(4 * hp.gsrow.size());
+    const size_t o_prp = cv.take(8 * hp.prp.size());
+    const size_t o_ipanel = cv.take(4 * hp.item_panel.size()), o_ichunk = cv.take(4 * hp.item_chunk.size());
+    const size_t o_exec = cv.take(4 * hp.exec_order.size()), o_active = cv.take((size_t)hp.nitems());
+    const size_t o_A2 = cv.take(8 * (size_t)m), o_B2 = cv.take(8 * (size_t)ntiles * TW);
+    const size_t o_aeval = cv.take(8 * (size_t)m);
+    const size_t o_rowpart = cv.take(8 * (size_t)hp.rowpart_len);
+    const size_t o_colpart = cv.take(8 * (size_t)hp.npanels() * (size_t)n);
+    const size_t o_psipart = cv.take(8 * (size_t)hp.nitems());
+    const int nred = reduce_blocks((int32_t)m, (int32_t)n);
+    const size_t o_bpart = cv.take(8 * 3 * (size_t)nred), o_counter = cv.take(16), o_scal = cv.take(64);
+    if (cv.off > OTGS_STATIC_SCRATCH_BYTES)
+        return set_err(OTGS_EINVAL, "problem needs " + std::to_string(cv.off) + " bytes of scratch, above the " +
+                                        std::to_string((size_t)OTGS_STATIC_SCRATCH_BYTES) +
+                                        " bytes of the static buffer");
+    // per-device set-up: the device address of the static array
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return set_err(OTGS_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return set_err(OTGS_EINVAL, "device index out of range");
+    unsigned char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_addr[dev]) {
+            void* p = nullptr;
+            e = cudaGetSymbolAddress(&p, g_static_scratch);
+            if (e != cudaSuccess || !p)
+                return set_err(OTGS_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+            g_addr[dev] = p;
+        }
+        base = static_cast<unsigned char*>(g_addr[dev]);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    auto up = [&](size_t off, const void* src, size_t bytes) {
+        return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    std::vector<uint8_t> ones(hp.nitems(), 1);
+    const std::pair<size_t, const std::vector<int32_t>*> i32s[] = {
+        {o_perm, &hp.perm}, {o_goff, &hp.goff}, {o_rgroup, &hp.rgroup}, {o_pkind, &hp.pkind},
+        {o_prows, &hp.prows}, {o_pW, &hp.pW}, {o_pnch, &hp.pnch}, {o_pitem, &hp.pitem},
+        {o_pw_off, &hp.pw_off}, {o_pgrp, &hp.pgrp}, {o_gpanel, &hp.gpanel}, {o_gsrow, &hp.gsrow},
+        {o_ipanel, &hp.item_panel}, {o_ichunk, &hp.item_chunk}, {o_exec, &hp.exec_order}};
+    for (const auto& pr : i32s)
+        if ((e = up(pr.first, pr.second->data(), 4 * pr.second->size())) != cudaSuccess) break;
+    if (e == cudaSuccess) e = up(o_prp, hp.prp.data(), 8 * hp.prp.size());
+    if (e == cudaSuccess) e = up(o_active, ones.data(), ones.size());
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_counter, 0, 16, st);
+    if (e != cudaSuccess) return set_err(OTGS_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
+    DevPlan dp;
+    dp.perm = (int32_t*)(base + o_perm); dp.goff = (int32_t*)(base + o_goff); dp.rgroup = (int32_t*)(base + o_rgroup);
+    dp.pkind = (int32_t*)(base + o_pkind); dp.prows = (int32_t*)(base + o_prows); dp.pW = (int32_t*)(base + o_pW);
+    dp.pnch = (int32_t*)(base + o_pnch); dp.pitem = (int32_t*)(base + o_pitem); dp.pw_off = (int32_t*)(base + o_pw_off);
+    dp.pgrp = (int32_t*)(base + o_pgrp); dp.gpanel = (int32_t*)(base + o_gpanel); dp.gsrow = (int32_t*)(base + o_gsrow);
+    dp.prp = (int64_t*)(base + o_prp);
+    dp.item_panel = (int32_t*)(base + o_ipanel); dp.item_chunk = (int32_t*)(base + o_ichunk);
+    dp.exec_order = (int32_t*)(base + o_exec);
+    const uint8_t* active = base + o_active;
+    float2* A2 = (float2*)(base + o_A2);
+    float2* B2 = (float2*)(base + o_B2);
+    double* aeval = (double*)(base + o_aeval);
+    // the caller's a is already in class-sorted order (labels non-decreasing)
+    launch_prep(alpha, true, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, aeval, st);
+    EvalArgs ea;
+    memset(&ea, 0, sizeof(ea));
+    ea.C = C; ea.ldc = ldc;
+    ea.m = (int32_t)m; ea.n = (int32_t)n; ea.L = L; ea.ntiles = ntiles;
+    ea.npanels = hp.npanels(); ea.nitems = hp.nitems();
+    ea.A2 = A2; ea.B2 = B2; ea.plan = dp;
+    ea.items = dp.exec_order; ea.item_active = active; ea.unit_need = nullptr;
+    ea.unit_words = (ntiles + 31) / 32;
+    ea.rowpart = (double*)(base + o_rowpart);
+    ea.colpart = (double*)(base + o_colpart);
+    ea.psipart = (double*)(base + o_psipart);
+    const double theta = mu * gamma;
+    ea.theta_hi = (float)theta;
+    ea.theta_lo = (float)(theta - (double)ea.theta_hi);
+    const double cut = theta * theta * (1.0 - std::ldexp(1.0, -20));
+    float fc = (float)cut;
+    if ((double)fc > cut) fc = std::nextafter(fc, 0.f);
+    ea.th2_cut = fc;
+    ea.gamma = (float)gamma;
+    ea.inv2g = 1.0 / (2.0 * gamma);
+    launch_eval(ea, hp.nitems(), st);
+    ReduceArgs ra;
+    memset(&ra, 0, sizeof(ra));
+    ra.m = (int32_t)m; ra.n = (int32_t)n; ra.npanels = hp.npanels(); ra.nitems = hp.nitems();
+    ra.plan = dp; ra.item_active = active;
+    ra.rowpart = ea.rowpart; ra.colpart = ea.colpart; ra.psipart = ea.psipart;
+    ra.a_sorted = a; ra.b = b; ra.alpha_sorted = aeval; ra.beta = beta;
+    ra.out_caller = out; ra.scal = (double*)(base + o_scal);
+    ra.block_part = (double*)(base + o_bpart);
+    ra.counter = (unsigned*)(base + o_counter);
+    launch_reduce(ra, st);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return set_err(OTGS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));
+    return OTGS_OK;
+}
+
+}  // extern "C"
