@@ -146,7 +146,7 @@ def _src_hash():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2303_07597_gb300", "csrc")
     for name in sorted(os.listdir(csrc)):
-        if name.startswith("otgs_eval") or name == "otgs_internal.cuh":
+        if name in ("otgs_eval.cu", "otgs_stream.cu", "otgs_plan.cu", "otgs_internal.cuh"):
             h.update(open(os.path.join(csrc, name), "rb").read())
     return h.hexdigest()
 
@@ -309,7 +309,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
-                         "kernel": "k_eval", "alg_bytes_per_launch": alg_bytes,
+                         "kernel": "k_stream", "alg_bytes_per_launch": alg_bytes,
                          "kernel_ms": kern_avg_s * 1000.0,
                          "traffic": _traffic_for(_src_hash(), args.workload)},
             "cpu_baseline": cb,

@@ -1,5 +1,6 @@
 // otgs_api.cu -- the C ABI (include/otgs.h): handle life cycle, validation,
 // device buffers, and the host side of one evaluation.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -134,6 +135,14 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     dp.item_panel = upload(this, hp.item_panel, "item_panel");
     dp.item_chunk = upload(this, hp.item_chunk, "item_chunk");
     dp.exec_order = upload(this, hp.exec_order, "exec_order");
+    dp.prow0 = upload(this, hp.prow0, "prow0");
+    dp.pginfo = upload(this, hp.pginfo, "pginfo");
+    dp.desc = upload(this, hp.desc, "item descriptors");
+    if (!dp.prow0 || !dp.pginfo || !dp.desc) return false;
+    {
+        std::string te = make_tmaps(C, ldc, m, n, tmaps);
+        if (!te.empty()) return fail(OTGS_ECUDA, te);
+    }
     if (!dp.goff || !dp.rgroup || !dp.pkind || !dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.pw_off ||
         !dp.pgrp || !dp.gpanel || !dp.gsrow || !dp.prp || !dp.item_panel || !dp.item_chunk || !dp.exec_order)
         return false;
@@ -147,8 +156,19 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     launch_permute_f64(a_, dp.perm, (int32_t)m, a_sorted, true, st);
     if (!ck(cudaMemcpyAsync(b, b_, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "b copy")) return false;
     // evaluation buffers
-    A2 = (float2*)dalloc(sizeof(float2) * m, "A2");
-    B2 = (float2*)dalloc(sizeof(float2) * (size_t)ntiles * TW, "B2");
+    A2 = (float2*)dalloc(sizeof(float2) * ((size_t)m + 2), "A2");  // padded: copied in 16-byte blocks
+    B2 = (float2*)dalloc(sizeof(float2) * (size_t)padded_cols(ntiles), "B2");
+    Bp = (float*)dalloc(sizeof(float) * (size_t)padded_cols(ntiles), "Bp");
+    work = (int*)dalloc(sizeof(int) * 4, "work");
+    kerr = (int*)dalloc(sizeof(int) * 4, "kernel error");
+    if (!Bp || !work || !kerr) return false;
+    if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
+    if (!ck(cudaMemsetAsync(A2, 0, sizeof(float2) * ((size_t)m + 2), st), "memset A2")) return false;
+    {
+        int dev = 0;
+        if (!ck(cudaGetDevice(&dev), "cudaGetDevice")) return false;
+        if (!ck(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "SM count")) return false;
+    }
     alpha_eval = (double*)dalloc(sizeof(double) * m, "alpha_eval");
     rowpart = (double*)dalloc(sizeof(double) * (size_t)hp.rowpart_len, "rowpart");
     colpart = (double*)dalloc(sizeof(double) * (size_t)hp.npanels() * n, "colpart");
@@ -161,7 +181,6 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
         return false;
     if (!ck(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, st), "memset counter")) return false;
     if (!ck(cudaMallocHost(&host_scal, sizeof(double) * 8), "cudaMallocHost")) return false;
-    // kernels use up to eval_smem_bytes() of dynamic shared memory
     if (!ck(cudaStreamSynchronize(st), "create sync")) return false;
     stats_host = ot_gs_stats();
     return true;
@@ -175,6 +194,9 @@ EvalArgs Handle::eval_args(const int32_t* items, const uint8_t* active, const ui
     e.m = (int32_t)m; e.n = (int32_t)n; e.L = L; e.ntiles = ntiles;
     e.npanels = hp.npanels(); e.nitems = hp.nitems();
     e.A2 = A2; e.B2 = B2;
+    e.Bp = Bp;
+    e.work = work; e.err = kerr;
+    e.nlist = hp.nitems();
     e.plan = dp;
     e.items = items;
     e.item_active = active;
@@ -210,6 +232,7 @@ ReduceArgs Handle::reduce_args(const uint8_t* active, double* out_caller, double
     r.scal = scal;
     r.block_part = block_part;
     r.counter = counter;
+    r.err = kerr;
     return r;
 }
 
@@ -223,8 +246,9 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
             ev_pool.push_back(ev);
         }
     }
+    cudaMemsetAsync(work, 0, sizeof(int), st);
     if (timing) cudaEventRecord(ev_pool[ev_used], st);
-    launch_eval(e, n_ctas, st);
+    launch_stream(e, tmaps, n_ctas, st);
     if (timing) {
         cudaEventRecord(ev_pool[ev_used + 1], st);
         ev_used += 2;
@@ -235,7 +259,7 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
 bool Handle::eval_dense(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
                         double* G_sorted, const double* dir, bool snap)
 {
-    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, alpha_eval, st);
+    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, Bp, alpha_eval, st);
     return eval_dense_core(beta, out_caller, G_sorted, dir, snap);
 }
 
@@ -247,7 +271,7 @@ bool Handle::eval_dense_prepped(const double* beta, double* G_sorted, const doub
 bool Handle::eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap)
 {
     EvalArgs e = eval_args(dp.exec_order, item_all_active, nullptr, snap);
-    eval_launch(e, hp.nitems());
+    eval_launch(e, std::min(n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_all_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     stats_host.evals++;

@@ -33,6 +33,11 @@ struct Handle {
     // one evaluation
     float2* A2 = nullptr;
     float2* B2 = nullptr;
+    float* Bp = nullptr;            // bound_up(beta hi), padded columns
+    TmaMaps tmaps;                  // TMA descriptors of C
+    int* work = nullptr;            // evaluation kernel work counter
+    int* kerr = nullptr;            // evaluation kernel error word
+    int n_sm = 0;
     double* alpha_eval = nullptr;   // sorted alpha of the last evaluation
     double* rowpart = nullptr;
     double* colpart = nullptr;

@@ -6,8 +6,9 @@
 // memory pool forbids allocations outside the pool, and latency-critical loops
 // that cannot afford cudaMalloc's implicit device synchronisation.  This entry
 // point serves them: every scratch buffer of the evaluation -- the group plan,
-// the float-pair split of alpha and beta, the row / column / psi partial sums
-// and the reduction's block partials -- is carved out of one file-scope
+// the float-pair split of alpha and beta and its bounds, the row / column / psi
+// partial sums, the work counter, the error word and the reduction's block
+// partials -- is carved out of one file-scope
 // __device__ array of OTGS_STATIC_SCRATCH_BYTES bytes.  Each GPU that loads
 // this part of the library keeps that array until the process exits.
 //
@@ -16,8 +17,9 @@
 // cudaGetSymbolAddress, with that device current, on the first call made
 // while that device is current; that first call should therefore come before
 // any stream capture.  All calls share the array and it keeps the contents of
-// the last call: the reduction's ticket counter, the only value that must
-// start at zero, is cleared by every call.  Calls that overlap on the GPU (on
+// the last call: the values that must start at zero (the reduction's ticket
+// counter, the evaluation's work counter and error word) are cleared by every
+// call.  Calls that overlap on the GPU (on
 // different streams, or from different host threads) race on the array.
 #include <cmath>
 #include <cstring>
@@ -95,7 +97,12 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const size_t o_prp = cv.take(8 * hp.prp.size());
     const size_t o_ipanel = cv.take(4 * hp.item_panel.size()), o_ichunk = cv.take(4 * hp.item_chunk.size());
     const size_t o_exec = cv.take(4 * hp.exec_order.size()), o_active = cv.take((size_t)hp.nitems());
-    const size_t o_A2 = cv.take(8 * (size_t)m), o_B2 = cv.take(8 * (size_t)ntiles * TW);
+    const size_t o_prow0 = cv.take(4 * hp.prow0.size());
+    const size_t o_pginfo = cv.take(16 * hp.pginfo.size());
+    const size_t o_desc = cv.take(sizeof(ItemDesc) * hp.desc.size());
+    const size_t o_A2 = cv.take(8 * ((size_t)m + 2)), o_B2 = cv.take(8 * (size_t)padded_cols(ntiles));
+    const size_t o_Bp = cv.take(4 * (size_t)padded_cols(ntiles));
+    const size_t o_work = cv.take(16), o_err = cv.take(16);
     const size_t o_aeval = cv.take(8 * (size_t)m);
     const size_t o_rowpart = cv.take(8 * (size_t)hp.rowpart_len);
     const size_t o_colpart = cv.take(8 * (size_t)hp.npanels() * (size_t)n);
@@ -132,12 +139,19 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
         {o_perm, &hp.perm}, {o_goff, &hp.goff}, {o_rgroup, &hp.rgroup}, {o_pkind, &hp.pkind},
         {o_prows, &hp.prows}, {o_pW, &hp.pW}, {o_pnch, &hp.pnch}, {o_pitem, &hp.pitem},
         {o_pw_off, &hp.pw_off}, {o_pgrp, &hp.pgrp}, {o_gpanel, &hp.gpanel}, {o_gsrow, &hp.gsrow},
-        {o_ipanel, &hp.item_panel}, {o_ichunk, &hp.item_chunk}, {o_exec, &hp.exec_order}};
+        {o_ipanel, &hp.item_panel}, {o_ichunk, &hp.item_chunk}, {o_exec, &hp.exec_order},
+        {o_prow0, &hp.prow0}};
     for (const auto& pr : i32s)
         if ((e = up(pr.first, pr.second->data(), 4 * pr.second->size())) != cudaSuccess) break;
     if (e == cudaSuccess) e = up(o_prp, hp.prp.data(), 8 * hp.prp.size());
+    if (e == cudaSuccess) e = up(o_pginfo, hp.pginfo.data(), 16 * hp.pginfo.size());
+    if (e == cudaSuccess) e = up(o_desc, hp.desc.data(), sizeof(ItemDesc) * hp.desc.size());
     if (e == cudaSuccess) e = up(o_active, ones.data(), ones.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_counter, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_work, 0, 16, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_err, 0, 16, st);
+    int n_sm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return set_err(OTGS_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
     DevPlan dp;
     dp.perm = (int32_t*)(base + o_perm); dp.goff = (int32_t*)(base + o_goff); dp.rgroup = (int32_t*)(base + o_rgroup);
@@ -147,18 +161,25 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     dp.prp = (int64_t*)(base + o_prp);
     dp.item_panel = (int32_t*)(base + o_ipanel); dp.item_chunk = (int32_t*)(base + o_ichunk);
     dp.exec_order = (int32_t*)(base + o_exec);
+    dp.prow0 = (int32_t*)(base + o_prow0);
+    dp.pginfo = (int4*)(base + o_pginfo);
+    dp.desc = (ItemDesc*)(base + o_desc);
     const uint8_t* active = base + o_active;
     float2* A2 = (float2*)(base + o_A2);
     float2* B2 = (float2*)(base + o_B2);
     double* aeval = (double*)(base + o_aeval);
     // the caller's a is already in class-sorted order (labels non-decreasing)
-    launch_prep(alpha, true, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, aeval, st);
+    float* Bp = (float*)(base + o_Bp);
+    launch_prep(alpha, true, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, Bp, aeval, st);
     EvalArgs ea;
     memset(&ea, 0, sizeof(ea));
     ea.C = C; ea.ldc = ldc;
     ea.m = (int32_t)m; ea.n = (int32_t)n; ea.L = L; ea.ntiles = ntiles;
     ea.npanels = hp.npanels(); ea.nitems = hp.nitems();
     ea.A2 = A2; ea.B2 = B2; ea.plan = dp;
+    ea.Bp = Bp;
+    ea.work = (int*)(base + o_work); ea.err = (int*)(base + o_err);
+    ea.nlist = hp.nitems();
     ea.items = dp.exec_order; ea.item_active = active; ea.unit_need = nullptr;
     ea.unit_words = (ntiles + 31) / 32;
     ea.rowpart = (double*)(base + o_rowpart);
@@ -173,7 +194,12 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     ea.th2_cut = fc;
     ea.gamma = (float)gamma;
     ea.inv2g = 1.0 / (2.0 * gamma);
-    launch_eval(ea, hp.nitems(), st);
+    TmaMaps tm;
+    {
+        const std::string te = make_tmaps(C, ldc, m, n, tm);
+        if (!te.empty()) return set_err(OTGS_ECUDA, te);
+    }
+    launch_stream(ea, tm, n_sm < hp.nitems() ? n_sm : hp.nitems(), st);
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.m = (int32_t)m; ra.n = (int32_t)n; ra.npanels = hp.npanels(); ra.nitems = hp.nitems();
@@ -183,6 +209,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     ra.out_caller = out; ra.scal = (double*)(base + o_scal);
     ra.block_part = (double*)(base + o_bpart);
     ra.counter = (unsigned*)(base + o_counter);
+    ra.err = ea.err;
     launch_reduce(ra, st);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_err(OTGS_ECUDA, std::string("launch: ") + cudaGetErrorString(e));

@@ -19,6 +19,10 @@
 //      k~ = sqrt(z~^2 + o~^2);  (l, j) in N  iff  zlow > theta.
 // Group sums run lane-strided over the group's sorted rows (lane k takes rows
 // k, k+32, ...) and then through a fixed xor tree (16, 8, 4, 2, 1).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
 #include "otgs_handle.cuh"
 
 namespace otgs {
@@ -287,7 +291,7 @@ bool Handle::snapshot_at(const double* alpha, bool alpha_sorted, const double* b
 {
     if (!ensure_screen()) return false;
     if (!snap_valid && !zero_snapshot()) return false;
-    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, alpha_eval, st);
+    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, Bp, alpha_eval, st);
     if (build_N && prm.use_lower_bound) {
         launch_delta(this, beta);
         ScreenArgs s = make_screen_args(this);
@@ -309,7 +313,7 @@ bool Handle::eval_screened(const double* alpha, bool alpha_sorted, const double*
 {
     if (!ensure_screen()) return false;
     if (!snap_valid && !zero_snapshot()) return false;
-    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, alpha_eval, st);
+    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, Bp, alpha_eval, st);
     return eval_screened_prepped(beta, G_sorted, dir, out_caller);
 }
 
@@ -325,7 +329,7 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     const int64_t units = (int64_t)L * ntiles;
     k_screen<<<(unsigned)((units + 7) / 8), 256, 0, st>>>(s);
     EvalArgs e = eval_args(dp.exec_order, item_active, unit_need, false);
-    eval_launch(e, hp.nitems());
+    eval_launch(e, std::min(n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     stats_host.evals++;

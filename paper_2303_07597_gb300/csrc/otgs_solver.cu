@@ -9,6 +9,7 @@
 // The line search is a state machine in one thread: it reads D and the slope
 // of the trial evaluation, and sets the next trial step, or accepts.  Alg. 1's
 // snapshot refresh (with the rebuild of N) runs every r accepted iterations.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstring>
@@ -22,7 +23,7 @@ namespace otgs {
 // ------------------------------------------------------------------ kernels
 // x_t = x + t d; also the float-pair split of x_t for the evaluation kernel.
 __global__ void k_trial(SolverState* S, const double* __restrict__ x, const double* __restrict__ d, double* xt,
-                        float2* A2, float2* B2, double* alpha_eval, int m, int n, int npad)
+                        float2* A2, float2* B2, float* Bp, double* alpha_eval, int m, int n, int npad)
 {
     if (S->done) return;
     const double t = S->t;
@@ -40,8 +41,10 @@ __global__ void k_trial(SolverState* S, const double* __restrict__ x, const doub
             xt[m + i] = v;
             const float h = __double2float_rn(v);
             B2[i] = make_float2(h, __double2float_rn(v - (double)h));
+            Bp[i] = bound_up(h);
         } else {
             B2[i] = make_float2(-1e30f, 0.f);
+            Bp[i] = -INFINITY;
         }
     }
 }
@@ -380,7 +383,7 @@ int Solver::run(double tol, int maxit)
     k_gg<<<nblk, SOLVER_THREADS, 0, st>>>(G, N, pbase);
     k_direction<<<1, 128, 0, st>>>(state, pbase, ppair, nblk, 1);
     k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 1);
-    const int npad = h->ntiles * TW;
+    const int npad = padded_cols(h->ntiles);
     const int tb = (std::max((int)h->m, npad) + 255) / 256;
     const size_t hdr = offsetof(SolverState, tol);  // the int fields and the eval counter
     const long long max_trials = (long long)maxit * (LS_MAX_EVALS + 2) + 16;
@@ -393,7 +396,8 @@ int Solver::run(double tol, int maxit)
             h->fail(OTGS_ENOTCONV, "solver exceeded its trial budget");
             break;
         }
-        k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->A2, h->B2, h->alpha_eval, (int)h->m, (int)h->n, npad);
+        k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->A2, h->B2, h->Bp, h->alpha_eval, (int)h->m,
+                                    (int)h->n, npad);
         if (!eval_trial()) return h->last_code;
         k_linesearch<<<1, 1, 0, st>>>(state, h->scal);
         k_accept<<<nblk, SOLVER_THREADS, 0, st>>>(state, x, G, xt, Gt, Sv, Yv, N, pbase);
