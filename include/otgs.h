@@ -87,9 +87,10 @@ typedef struct {
  * Create a problem (Sec. 2.1-2.3).
  *   h       out: new handle
  *   C       device, FP32, m x n, row i at C + i*ldc (ldc >= n), c_ij >= 0, finite.
- *           Borrowed when the labels are non-decreasing, n % 4 == 0, ldc % 4 == 0
- *           and C is 16-byte aligned; the caller then keeps it alive and unchanged until
- *           ot_gs_destroy.  Otherwise the library keeps a class-sorted copy.
+ *           Borrowed when the labels are non-decreasing, ldc % 4 == 0 and C is
+ *           16-byte aligned (the layout TMA reads); the caller then keeps it alive
+ *           and unchanged until ot_gs_destroy.  Otherwise the library keeps a
+ *           class-sorted copy.
  *   a, b    device, FP64, m and n positive marginals with |sum a - sum b| <=
  *           1e-12 max(sum a, 1) (Sec. 2.1 uses 1/m and 1/n); copied.
  *   labels  device, int32, m class labels in [0, L) (the groups of Eq. 3); copied.
@@ -200,11 +201,13 @@ OTGS_API const char *ot_gs_version(void);
 /*
  * Host-only inspection of the group plan the library builds at create (no
  * GPU needed): for m labels in [0, L) and n columns, writes the number of
- * panels and of (panel, column chunk) work items.  Returns OTGS_EINVAL on bad
- * input.  Used to test the host-side work decomposition.
+ * panels (row ranges of whole groups), of (panel, 256-column chunk) work
+ * items, and of the 32-row shared-memory stages one dense evaluation streams.
+ * Returns OTGS_EINVAL on bad input.  Used to test the host-side work
+ * decomposition.
  */
 OTGS_API int ot_gs_plan_info(const int32_t *labels_host, int64_t m, int64_t n, int32_t L,
-                    int64_t *n_panels, int64_t *n_items, int64_t *rowpart_len);
+                    int64_t *n_panels, int64_t *n_items, int64_t *n_stages);
 
 /*
  * Allocation-free dense evaluation.  The paper has no counterpart: this entry
@@ -217,14 +220,15 @@ OTGS_API int ot_gs_plan_info(const int32_t *labels_host, int64_t m, int64_t n, i
  * array of OTGS_STATIC_SCRATCH_BYTES bytes that every GPU loading this part of
  * the library keeps until the process exits.
  *   C            device FP32, m x n, row stride ldc; rows class-sorted
- *                (labels_host non-decreasing); n % 4 == 0, ldc % 4 == 0 and C
- *                16-byte aligned (no sorted copy can be made without allocating)
+ *                (labels_host non-decreasing); ldc % 4 == 0 and C 16-byte
+ *                aligned (no sorted copy can be made without allocating)
  *   a, b         device FP64 marginals [m], [n]
  *   labels_host  HOST int32 [m], non-decreasing, values in [0, L)
  *   alpha, beta  device FP64 [m], [n];  out: device FP64 [1 + m + n] as ot_gs_grad
  *   stream       cudaStream_t as void*
  * Inputs are not otherwise validated.  Sizes whose scratch would exceed the
- * static array (roughly m = n = 10^4 with a thousand classes fits) are
+ * static array (about 44 bytes per row, 20 per column and 96 per work item
+ * of up to 512 rows x 256 columns: m = n = 2 x 10^5 fits) are
  * rejected with OTGS_EINVAL before any GPU work; the message says how many
  * bytes were needed.  The first call made on a device looks up the array's
  * device address there (once per device), so that first call should come

@@ -261,7 +261,7 @@ def ot_gs_plan_info(labels, n, L):
                                ctypes.byref(np_), ctypes.byref(ni), ctypes.byref(rl))
     if rc != OTGS_OK:
         raise OTGSError(rc, "invalid plan input")
-    return dict(n_panels=np_.value, n_items=ni.value, rowpart_len=rl.value)
+    return dict(n_panels=np_.value, n_items=ni.value, n_stages=rl.value)
 
 
 def ot_gs_grad_noalloc(C, a, b, labels_host, L, gamma, mu, alpha, beta, out, stream=None):

@@ -102,9 +102,9 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
         unsigned cbits = (unsigned)hf[3];
         memcpy(&cmax, &cbits, sizeof(float));
     }
-    // C: borrow when class-sorted and float4-aligned (every float4 that starts
-    // below column n then ends below n), else a sorted, padded copy
-    bool aligned = (reinterpret_cast<uintptr_t>(C_) % 16 == 0) && (ldc_ % 4 == 0) && (n % 4 == 0);
+    // C: borrow when class-sorted and laid out as TMA needs (16-byte aligned
+    // base and row stride), else a sorted, padded copy
+    bool aligned = (reinterpret_cast<uintptr_t>(C_) % 16 == 0) && (ldc_ % 4 == 0);
     dp.perm = upload(this, hp.perm, "perm");
     if (!dp.perm) return false;
     if (hp.sorted_identity && aligned) {
@@ -122,33 +122,23 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     // plan arrays
     dp.goff = upload(this, hp.goff, "goff");
     dp.rgroup = upload(this, hp.rgroup, "rgroup");
-    dp.pkind = upload(this, hp.pkind, "pkind");
+    dp.rowg = upload(this, hp.rowg, "row groups");
     dp.prows = upload(this, hp.prows, "prows");
     dp.pW = upload(this, hp.pW, "pW");
     dp.pnch = upload(this, hp.pnch, "pnch");
     dp.pitem = upload(this, hp.pitem, "pitem");
-    dp.pw_off = upload(this, hp.pw_off, "pw_off");
-    dp.pgrp = upload(this, hp.pgrp, "pgrp");
     dp.gpanel = upload(this, hp.gpanel, "gpanel");
-    dp.gsrow = upload(this, hp.gsrow, "gsrow");
-    dp.prp = upload(this, hp.prp, "prp");
     dp.item_panel = upload(this, hp.item_panel, "item_panel");
     dp.item_chunk = upload(this, hp.item_chunk, "item_chunk");
     dp.exec_order = upload(this, hp.exec_order, "exec_order");
-    dp.prow0 = upload(this, hp.prow0, "prow0");
-    dp.pginfo = upload(this, hp.pginfo, "pginfo");
     dp.desc = upload(this, hp.desc, "item descriptors");
-    if (!dp.prow0 || !dp.pginfo || !dp.desc) return false;
+    if (!dp.goff || !dp.rgroup || !dp.rowg || !dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.gpanel ||
+        !dp.item_panel || !dp.item_chunk || !dp.exec_order || !dp.desc)
+        return false;
     {
         std::string te = make_tmaps(C, ldc, m, n, tmaps);
         if (!te.empty()) return fail(OTGS_ECUDA, te);
     }
-    if (!dp.goff || !dp.rgroup || !dp.pkind || !dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.pw_off ||
-        !dp.pgrp || !dp.gpanel || !dp.gsrow || !dp.prp || !dp.item_panel || !dp.item_chunk || !dp.exec_order)
-        return false;
-    std::vector<uint8_t> ones(hp.nitems(), 1);
-    item_all_active = upload(this, ones, "item_active");
-    if (!item_all_active) return false;
     // marginals (a in sorted order)
     a_sorted = (double*)dalloc(sizeof(double) * m, "a_sorted");
     b = (double*)dalloc(sizeof(double) * n, "b");
@@ -156,29 +146,27 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     launch_permute_f64(a_, dp.perm, (int32_t)m, a_sorted, true, st);
     if (!ck(cudaMemcpyAsync(b, b_, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "b copy")) return false;
     // evaluation buffers
-    A2 = (float2*)dalloc(sizeof(float2) * ((size_t)m + 2), "A2");  // padded: copied in 16-byte blocks
-    B2 = (float2*)dalloc(sizeof(float2) * (size_t)padded_cols(ntiles), "B2");
-    Bp = (float*)dalloc(sizeof(float) * (size_t)padded_cols(ntiles), "Bp");
-    work = (int*)dalloc(sizeof(int) * 4, "work");
+    rowA = (float4*)dalloc(sizeof(float4) * (size_t)m, "rowA");
+    B2 = (float2*)dalloc(sizeof(float2) * (size_t)padded_cols(n), "B2");
+    Bp = (float*)dalloc(sizeof(float) * (size_t)padded_cols(n), "Bp");
+    ctl = (EvalCtl*)dalloc(sizeof(EvalCtl), "evaluation control");
     kerr = (int*)dalloc(sizeof(int) * 4, "kernel error");
-    if (!Bp || !work || !kerr) return false;
+    alpha_eval = (double*)dalloc(sizeof(double) * m, "alpha_eval");
+    rowfx = (unsigned long long*)dalloc(sizeof(unsigned long long) * (size_t)m, "row sums");
+    colfx = (unsigned long long*)dalloc(sizeof(unsigned long long) * (size_t)n, "column sums");
+    psipart = (double*)dalloc(sizeof(double) * (size_t)hp.nitems() * NWARPS, "psipart");
+    if (!rowA || !B2 || !Bp || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !psipart) return false;
     if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
-    if (!ck(cudaMemsetAsync(A2, 0, sizeof(float2) * ((size_t)m + 2), st), "memset A2")) return false;
     {
         int dev = 0;
         if (!ck(cudaGetDevice(&dev), "cudaGetDevice")) return false;
         if (!ck(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "SM count")) return false;
     }
-    alpha_eval = (double*)dalloc(sizeof(double) * m, "alpha_eval");
-    rowpart = (double*)dalloc(sizeof(double) * (size_t)hp.rowpart_len, "rowpart");
-    colpart = (double*)dalloc(sizeof(double) * (size_t)hp.npanels() * n, "colpart");
-    psipart = (double*)dalloc(sizeof(double) * (size_t)hp.nitems(), "psipart");
     nred = reduce_blocks((int32_t)m, (int32_t)n);
-    block_part = (double*)dalloc(sizeof(double) * 3 * (size_t)nred, "block_part");
+    block_part = (double*)dalloc(sizeof(double) * 4 * (size_t)nred, "block_part");
     counter = (unsigned*)dalloc(sizeof(unsigned) * 4, "counter");
     scal = (double*)dalloc(sizeof(double) * 8, "scal");
-    if (!A2 || !B2 || !alpha_eval || !rowpart || !colpart || !psipart || !block_part || !counter || !scal)
-        return false;
+    if (!block_part || !counter || !scal) return false;
     if (!ck(cudaMemsetAsync(counter, 0, sizeof(unsigned) * 4, st), "memset counter")) return false;
     if (!ck(cudaMallocHost(&host_scal, sizeof(double) * 8), "cudaMallocHost")) return false;
     if (!ck(cudaStreamSynchronize(st), "create sync")) return false;
@@ -186,23 +174,22 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     return true;
 }
 
-EvalArgs Handle::eval_args(const int32_t* items, const uint8_t* active, const uint32_t* need, bool snap)
+EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool snap)
 {
     EvalArgs e;
     memset(&e, 0, sizeof(e));
     e.C = C; e.ldc = ldc;
     e.m = (int32_t)m; e.n = (int32_t)n; e.L = L; e.ntiles = ntiles;
-    e.npanels = hp.npanels(); e.nitems = hp.nitems();
-    e.A2 = A2; e.B2 = B2;
-    e.Bp = Bp;
-    e.work = work; e.err = kerr;
+    e.nitems = hp.nitems();
+    e.rowA = rowA; e.rowg = dp.rowg;
+    e.B2 = B2; e.Bp = Bp;
+    e.ctl = ctl; e.err = kerr;
     e.nlist = hp.nitems();
-    e.plan = dp;
-    e.items = items;
+    e.desc = dp.desc;
     e.item_active = active;
     e.unit_need = need;
     e.unit_words = unit_words;
-    e.rowpart = rowpart; e.colpart = colpart; e.psipart = psipart;
+    e.rowfx = rowfx; e.colfx = colfx; e.psipart = psipart;
     e.zt = snap ? zt : nullptr;
     e.ot = snap ? ot : nullptr;
     const double theta = prm.mu * prm.gamma;
@@ -222,10 +209,12 @@ ReduceArgs Handle::reduce_args(const uint8_t* active, double* out_caller, double
 {
     ReduceArgs r;
     memset(&r, 0, sizeof(r));
-    r.m = (int32_t)m; r.n = (int32_t)n; r.npanels = hp.npanels(); r.nitems = hp.nitems();
-    r.plan = dp;
+    r.m = (int32_t)m; r.n = (int32_t)n; r.nitems = hp.nitems();
+    r.perm = dp.perm;
     r.item_active = active;
-    r.rowpart = rowpart; r.colpart = colpart; r.psipart = psipart;
+    r.rowfx = rowfx; r.colfx = colfx; r.psipart = psipart;
+    r.ctl = ctl;
+    r.gamma = (float)prm.gamma;
     r.a_sorted = a_sorted; r.b = b;
     r.alpha_sorted = alpha_eval; r.beta = beta_ptr;
     r.out_caller = out_caller; r.G_sorted = G_sorted; r.dir = dir;
@@ -234,6 +223,13 @@ ReduceArgs Handle::reduce_args(const uint8_t* active, double* out_caller, double
     r.counter = counter;
     r.err = kerr;
     return r;
+}
+
+// Preparation of an evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.
+void Handle::prep(const double* alpha, bool alpha_sorted, const double* beta)
+{
+    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, rowA, B2, Bp, alpha_eval, rowfx, colfx,
+                ctl, st);
 }
 
 // Launch of the evaluation kernel, optionally bracketed by timing events.
@@ -246,7 +242,6 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
             ev_pool.push_back(ev);
         }
     }
-    cudaMemsetAsync(work, 0, sizeof(int), st);
     if (timing) cudaEventRecord(ev_pool[ev_used], st);
     launch_stream(e, tmaps, n_ctas, st);
     if (timing) {
@@ -259,7 +254,7 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
 bool Handle::eval_dense(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
                         double* G_sorted, const double* dir, bool snap)
 {
-    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, Bp, alpha_eval, st);
+    prep(alpha, alpha_sorted, beta);
     return eval_dense_core(beta, out_caller, G_sorted, dir, snap);
 }
 
@@ -270,9 +265,9 @@ bool Handle::eval_dense_prepped(const double* beta, double* G_sorted, const doub
 
 bool Handle::eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap)
 {
-    EvalArgs e = eval_args(dp.exec_order, item_all_active, nullptr, snap);
+    EvalArgs e = eval_args(nullptr, nullptr, snap);
     eval_launch(e, std::min(n_sm, hp.nitems()));
-    ReduceArgs r = reduce_args(item_all_active, out_caller, G_sorted, dir, beta);
+    ReduceArgs r = reduce_args(nullptr, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     stats_host.evals++;
     stats_host.blocks_total += (int64_t)L * n;
@@ -427,14 +422,14 @@ const char* ot_gs_last_error(const ot_gs* hh)
 const char* ot_gs_version(void) { return "otgs 0.1 sm_103a"; }
 
 int ot_gs_plan_info(const int32_t* labels_host, int64_t m, int64_t n, int32_t L, int64_t* n_panels,
-                    int64_t* n_items, int64_t* rowpart_len)
+                    int64_t* n_items, int64_t* n_stages)
 {
     if (!labels_host) return OTGS_EINVAL;
     HostPlan hp;
     if (!build_plan(labels_host, m, n, L, hp).empty()) return OTGS_EINVAL;
     if (n_panels) *n_panels = hp.npanels();
     if (n_items) *n_items = hp.nitems();
-    if (rowpart_len) *rowpart_len = hp.rowpart_len;
+    if (n_stages) *n_stages = hp.nstages;
     return OTGS_OK;
 }
 

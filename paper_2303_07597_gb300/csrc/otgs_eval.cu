@@ -1,14 +1,15 @@
 // otgs_eval.cu -- the kernels around the evaluation of the dual (Eq. 4):
-// the float-pair split of alpha and beta, the fixed-order reduction of the
-// per-item partial sums into D and its gradient, and input utilities.
+// the preparation of alpha and beta, the reduction of the evaluation
+// kernel's sums into D and its gradient, and input utilities.
 //
 // Precision (the evaluation kernel is in otgs_stream.cu): near the optimum
 // z - theta is tiny next to z, so z must be exact to ~1e-13 relative.  alpha
 // and beta reach the kernel as FP32 (hi, lo) pairs plus an upper bound of each
 // (bound_up) for the cheap rejection test; f is formed with error-free
-// transformations where it may be positive.  The reduction is FP64 in a fixed
-// order, so results are deterministic and screened evaluations (skipped
-// units are exact zeros) equal dense ones bit for bit.
+// transformations where it may be positive.  Row and column sums of T arrive
+// as fixed-point integers and psi as per-(item, warp) partials added here in
+// a fixed order, so results are deterministic and screened evaluations
+// (skipped units are exact zeros) equal dense ones bit for bit.
 #include "otgs_internal.cuh"
 
 namespace otgs {
@@ -16,147 +17,125 @@ namespace otgs {
 #define FULLMASK 0xffffffffu
 
 // --------------------------------------------------------------- prep
-__device__ __forceinline__ float2 split2(double x)
-{
-    float h = __double2float_rn(x);
-    return make_float2(h, __double2float_rn(x - (double)h));
-}
-
 __global__ void k_prep(const double* __restrict__ alpha, int alpha_sorted, const int32_t* __restrict__ perm,
-                       const double* __restrict__ beta, int m, int n, int npad, float2* A2, float2* B2, float* Bp,
-                       double* alpha_s_out)
+                       const double* __restrict__ beta, int m, int n, int npad, float4* rowA, float2* B2, float* Bp,
+                       double* alpha_s_out, unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl)
 {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    float apos = 0.f, bpos = 0.f;
     if (t < m) {
-        double a = alpha_sorted ? alpha[t] : alpha[perm[t]];
-        const float2 s = split2(a);
-        A2[t] = s;
+        const double a = alpha_sorted ? alpha[t] : alpha[perm[t]];
+        apos = prep_row(a, rowA + t);
+        rowfx[t] = 0ull;
         if (alpha_s_out) alpha_s_out[t] = a;
     }
     if (t < npad) {
-        if (t < n) {
-            const float2 s = split2(beta[t]);
-            B2[t] = s;
-            Bp[t] = bound_up(s.x);
-        } else {
-            B2[t] = make_float2(-1e30f, 0.f);
-            Bp[t] = -INFINITY;  // never passes c < A' + B', whatever c
-        }
+        bpos = prep_col(t < n, t < n ? beta[t] : 0.0, B2 + t, Bp + t);
+        if (t < n) colfx[t] = 0ull;
     }
+    record_max(ctl, apos, bpos);
 }
 
 void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, const double* beta,
-                 int32_t m, int32_t n, int32_t ntiles, float2* A2, float2* B2, float* Bp,
-                 double* alpha_s_out, cudaStream_t st)
+                 int32_t m, int32_t n, float4* rowA, float2* B2, float* Bp, double* alpha_s_out,
+                 unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl, cudaStream_t st)
 {
-    int npad = padded_cols(ntiles);
-    int tot = m > npad ? m : npad;
-    k_prep<<<(tot + 255) / 256, 256, 0, st>>>(alpha, alpha_sorted ? 1 : 0, perm, beta, m, n, npad, A2, B2, Bp,
-                                             alpha_s_out);
+    const int npad = padded_cols(n);
+    const int tot = m > npad ? m : npad;
+    cudaMemsetAsync(ctl, 0, sizeof(EvalCtl), st);
+    k_prep<<<(tot + 255) / 256, 256, 0, st>>>(alpha, alpha_sorted ? 1 : 0, perm, beta, m, n, npad, rowA, B2, Bp,
+                                             alpha_s_out, rowfx, colfx, ctl);
 }
 
 // ------------------------------------------------------------- reduce
-// Eight lanes per row and per column: lane k adds the partials k, k+8, ...
-// and the eight lane sums meet in a fixed xor tree, so the result does not
-// depend on scheduling.
+// One thread per sorted row and per column; the psi partials are split into
+// one contiguous range per block.  Block sums meet in fixed trees and the
+// last block to finish adds the block sums in block order, so the result does
+// not depend on scheduling.
 constexpr int RED_THREADS = 256;
-constexpr int RED_LANES = 8;
+constexpr int RED_WARPS = RED_THREADS / 32;
 
 int reduce_blocks(int32_t m, int32_t n)
 {
-    int64_t tot = (int64_t)(m > n ? m : n) * RED_LANES;
+    const int64_t tot = m > n ? m : n;
     return (int)((tot + RED_THREADS - 1) / RED_THREADS);
 }
 
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
 {
-    __shared__ double sh[3][RED_THREADS / RED_LANES];
+    __shared__ double sh[4][RED_WARPS];
     __shared__ bool last;
-    const int gt = blockIdx.x * RED_THREADS + threadIdx.x;
-    const int t = gt / RED_LANES, k = gt % RED_LANES;
-    const unsigned gmask = 0xffu << (threadIdx.x & 24);
-    double ab = 0.0, dt = 0.0, inf = 0.0;
+    const FxScale fx = fx_scale(R.ctl->amax, R.ctl->bmax, R.m, R.n, R.gamma);
+    const int t = blockIdx.x * RED_THREADS + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double ab = 0.0, dt = 0.0, inf = 0.0, psi = 0.0;
     if (t < R.m) {
-        const int l = R.plan.rgroup[t];
-        const int p = R.plan.gpanel[l];
-        const int loc = R.plan.gsrow[l] + (t - R.plan.goff[l]);
-        const int rows = R.plan.prows[p], nch = R.plan.pnch[p], it0 = R.plan.pitem[p];
-        const double* rp = R.rowpart + R.plan.prp[p] + loc;
-        double acc = 0.0;
-#pragma unroll 4
-        for (int c = k; c < nch; c += RED_LANES) {
-            const double v = __ldg(rp + (int64_t)c * rows);
-            acc += __ldg(R.item_active + it0 + c) ? v : 0.0;
-        }
-        acc += __shfl_xor_sync(gmask, acc, 1);
-        acc += __shfl_xor_sync(gmask, acc, 2);
-        acc += __shfl_xor_sync(gmask, acc, 4);
-        const double ga = R.a_sorted[t] - acc;
-        if (k == 0) {
-            if (R.out_caller) R.out_caller[1 + R.plan.perm[t]] = ga;
-            if (R.G_sorted) R.G_sorted[t] = -ga;
-            if (R.dir) dt = -ga * R.dir[t];
-            inf = fabs(ga);
-            ab = R.alpha_sorted[t] * R.a_sorted[t];
-        }
+        const double rs = (double)(long long)R.rowfx[t] * fx.from_r;
+        const double ga = R.a_sorted[t] - rs;
+        if (R.out_caller) R.out_caller[1 + R.perm[t]] = ga;
+        if (R.G_sorted) R.G_sorted[t] = -ga;
+        if (R.dir) dt = -ga * R.dir[t];
+        inf = fabs(ga);
+        ab = R.alpha_sorted[t] * R.a_sorted[t];
     }
     if (t < R.n) {
-        double acc = 0.0;
-#pragma unroll 4
-        for (int p = k; p < R.npanels; p += RED_LANES) {
-            const int c = t / __ldg(R.plan.pW + p);
-            const double v = __ldg(R.colpart + (int64_t)p * R.n + t);
-            acc += __ldg(R.item_active + __ldg(R.plan.pitem + p) + c) ? v : 0.0;
-        }
-        acc += __shfl_xor_sync(gmask, acc, 1);
-        acc += __shfl_xor_sync(gmask, acc, 2);
-        acc += __shfl_xor_sync(gmask, acc, 4);
-        const double gb = R.b[t] - acc;
-        if (k == 0) {
-            if (R.out_caller) R.out_caller[1 + R.m + t] = gb;
-            if (R.G_sorted) R.G_sorted[R.m + t] = -gb;
-            if (R.dir) dt += -gb * R.dir[R.m + t];
-            inf = fmax(inf, fabs(gb));
-            ab += R.beta[t] * R.b[t];
-        }
+        const double cs = (double)(long long)R.colfx[t] * fx.from_c;
+        const double gb = R.b[t] - cs;
+        if (R.out_caller) R.out_caller[1 + R.m + t] = gb;
+        if (R.G_sorted) R.G_sorted[R.m + t] = -gb;
+        if (R.dir) dt += -gb * R.dir[R.m + t];
+        inf = fmax(inf, fabs(gb));
+        ab += R.beta[t] * R.b[t];
     }
-    const int g = threadIdx.x / RED_LANES;
-    if (k == 0) {
-        sh[0][g] = ab;
-        sh[1][g] = dt;
-        sh[2][g] = inf;
+    {
+        const int64_t E = (int64_t)R.nitems * NWARPS;
+        const int64_t per = (E + gridDim.x - 1) / gridDim.x;
+        const int64_t e0 = (int64_t)blockIdx.x * per, e1 = e0 + per < E ? e0 + per : E;
+        for (int64_t e = e0 + threadIdx.x; e < e1; e += RED_THREADS)
+            if (!R.item_active || R.item_active[e / NWARPS]) psi += R.psipart[e];
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        ab += __shfl_xor_sync(FULLMASK, ab, off);
+        dt += __shfl_xor_sync(FULLMASK, dt, off);
+        psi += __shfl_xor_sync(FULLMASK, psi, off);
+        inf = fmax(inf, __shfl_xor_sync(FULLMASK, inf, off));
+    }
+    if (lane == 0) {
+        sh[0][warp] = ab;
+        sh[1][warp] = dt;
+        sh[2][warp] = inf;
+        sh[3][warp] = psi;
     }
     __syncthreads();
-    for (int s = RED_THREADS / RED_LANES / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + s];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + s];
-            sh[2][threadIdx.x] = fmax(sh[2][threadIdx.x], sh[2][threadIdx.x + s]);
-        }
-        __syncthreads();
-    }
     if (threadIdx.x == 0) {
-        R.block_part[3 * blockIdx.x + 0] = sh[0][0];
-        R.block_part[3 * blockIdx.x + 1] = sh[1][0];
-        R.block_part[3 * blockIdx.x + 2] = sh[2][0];
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        for (int w = 0; w < RED_WARPS; w++) {
+            v0 += sh[0][w];
+            v1 += sh[1][w];
+            v2 = fmax(v2, sh[2][w]);
+            v3 += sh[3][w];
+        }
+        R.block_part[4 * blockIdx.x + 0] = v0;
+        R.block_part[4 * blockIdx.x + 1] = v1;
+        R.block_part[4 * blockIdx.x + 2] = v2;
+        R.block_part[4 * blockIdx.x + 3] = v3;
         __threadfence();
-        unsigned ticket = atomicAdd(R.counter, 1u);
+        const unsigned ticket = atomicAdd(R.counter, 1u);
         last = ticket == gridDim.x - 1;
     }
     __syncthreads();
     if (!last || threadIdx.x >= 32) return;
     __threadfence();
-    // last block, first warp: fixed-order sums over blocks and items
-    const int lane = threadIdx.x;
+    // last block, first warp: fixed-order sums over blocks
     const volatile double* bp = R.block_part;
     double s_ab = 0.0, s_dt = 0.0, s_inf = 0.0, s_psi = 0.0;
     for (int b = lane; b < (int)gridDim.x; b += 32) {
-        s_ab += bp[3 * b];
-        s_dt += bp[3 * b + 1];
-        s_inf = fmax(s_inf, bp[3 * b + 2]);
+        s_ab += bp[4 * b];
+        s_dt += bp[4 * b + 1];
+        s_inf = fmax(s_inf, bp[4 * b + 2]);
+        s_psi += bp[4 * b + 3];
     }
-    for (int it = lane; it < R.nitems; it += 32)
-        if (R.item_active[it]) s_psi += R.psipart[it];
     for (int off = 16; off >= 1; off >>= 1) {
         s_ab += __shfl_xor_sync(FULLMASK, s_ab, off);
         s_dt += __shfl_xor_sync(FULLMASK, s_dt, off);

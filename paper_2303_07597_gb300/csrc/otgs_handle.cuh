@@ -31,18 +31,17 @@ struct Handle {
     float cmax = 0.f;
 
     // one evaluation
-    float2* A2 = nullptr;
-    float2* B2 = nullptr;
+    float4* rowA = nullptr;         // sorted rows: (alpha hi, lo, bound_up(hi), 0)
+    float2* B2 = nullptr;           // (beta hi, lo), padded columns
     float* Bp = nullptr;            // bound_up(beta hi), padded columns
     TmaMaps tmaps;                  // TMA descriptors of C
-    int* work = nullptr;            // evaluation kernel work counter
+    EvalCtl* ctl = nullptr;         // evaluation control word (work counter, scale maxima)
     int* kerr = nullptr;            // evaluation kernel error word
     int n_sm = 0;
     double* alpha_eval = nullptr;   // sorted alpha of the last evaluation
-    double* rowpart = nullptr;
-    double* colpart = nullptr;
-    double* psipart = nullptr;
-    uint8_t* item_all_active = nullptr;
+    unsigned long long* rowfx = nullptr;  // fixed-point row sums of T
+    unsigned long long* colfx = nullptr;  // fixed-point column sums of T
+    double* psipart = nullptr;      // per (item, consumer warp) psi sums
     int nred = 0;
     double* block_part = nullptr;
     unsigned* counter = nullptr;
@@ -82,12 +81,13 @@ struct Handle {
     bool ck(cudaError_t e, const char* what);
     void* dalloc(size_t bytes, const char* what);
 
-    EvalArgs eval_args(const int32_t* items, const uint8_t* active, const uint32_t* need, bool snap);
+    EvalArgs eval_args(const uint8_t* active, const uint32_t* need, bool snap);
+    void prep(const double* alpha, bool alpha_sorted, const double* beta);
     ReduceArgs reduce_args(const uint8_t* active, double* out_caller, double* G_sorted, const double* dir,
                            const double* beta_ptr);
     bool eval_dense(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
                     double* G_sorted, const double* dir, bool snap);
-    // evaluations whose float-pair split (A2, B2, alpha_eval) is already in place
+    // evaluations whose preparation (rowA, B2, Bp, alpha_eval, ctl) is already in place
     bool eval_dense_prepped(const double* beta, double* G_sorted, const double* dir);
     bool eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap);
     bool eval_screened_prepped(const double* beta, double* G_sorted, const double* dir,

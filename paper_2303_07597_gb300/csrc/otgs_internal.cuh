@@ -4,7 +4,9 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <cmath>
 #include <cstdint>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -13,45 +15,74 @@
 namespace otgs {
 
 // ---------------------------------------------------------------- geometry
-// A "unit" is (group l, tile of TW consecutive target columns): g_l rows of C
-// by TW columns, one 128-byte line per row.  A warp reads a unit four rows
-// at a time, eight lanes per row, one float4 per lane.
+// A "unit" is (group l, tile of TW consecutive target columns): the
+// granularity of the screening decisions (Sec. 3) and of their bitmasks.
 constexpr int TW = 32;
+// The evaluation kernel has NWARPS consumer warps; warp w owns tile w of an
+// item's ITEM_COLS columns (one column per lane) and walks every row.
 constexpr int NWARPS = 8;
-constexpr int NTHREADS = NWARPS * 32;
-// The evaluation kernel streams C through shared-memory stages of STAGE_ROWS
-// rows x STAGE_COLS columns (two tiles; 256-byte rows keep the TMA engine at
-// full rate).  Groups of at most SMALL_MAX_ROWS rows are packed into "small"
-// panels (one stage per tile pair; each consumer warp owns a contiguous range
-// of whole groups); larger groups form a "big" panel of their own
-// (ceil(g / STAGE_ROWS) stages per tile pair, rows split over the warps).
-constexpr int STAGE_ROWS = 128;
-constexpr int STAGE_COLS = 2 * TW;
-constexpr int NSTAGES = 5;
-constexpr int SMALL_MAX_ROWS = STAGE_ROWS;
-constexpr int PANEL_ROWS = STAGE_ROWS;  // row budget of a small panel
-constexpr int PANEL_MAX_GROUPS = 64;    // group budget of a small panel
-constexpr int SMALL_CHUNK = 256;        // columns per small-panel work item (multiple of STAGE_COLS)
-constexpr int BIG_MAX_CHUNK = 256;      // columns per big-panel work item (max, multiple of STAGE_COLS)
-constexpr int BIG_SMEM_ROWS = 4096;     // big groups up to this size sum rows in shared memory
-constexpr double ITEM_BYTES = 2.0 * (1 << 20);  // target C bytes per big-panel item
+constexpr int ITEM_COLS = NWARPS * TW;  // columns of a work item: 1 KB of each row of C
+// C streams through a ring of NSTAGES shared-memory stages of STAGE_ROWS rows
+// x ITEM_COLS columns (32 KB), loaded by 2D TMA boxes.
+constexpr int STAGE_ROWS = 32;
+constexpr int NSTAGES = 6;
+// Consecutive groups are packed into "panels" of whole groups up to
+// PANEL_ROWS rows; a larger group is a panel of its own.  A work item is
+// (panel, column chunk of ITEM_COLS).
+constexpr int PANEL_ROWS = 512;
 
-// Columns of the float-pair split of beta, padded to whole stages.
-inline int32_t padded_cols(int32_t ntiles) { return (ntiles + 1) / 2 * STAGE_COLS; }
+// Columns of the per-column float-pair split of beta, padded to whole items.
+inline int32_t padded_cols(int64_t n) { return (int32_t)((n + ITEM_COLS - 1) / ITEM_COLS * ITEM_COLS); }
 
-// alpha_i (resp. beta_j) rounded up by a relative 2^-22: c_ij < A'_i + B'_j
-// (FP32, round to nearest) holds whenever alpha_i + beta_j - c_ij > 0, so the
-// test rejects only elements whose f is certainly <= 0.
+// alpha_i (resp. beta_j) rounded up by a relative 2^-22: with A' and B' so
+// rounded, fl(fl(A'_i - c_ij) + B'_j) > 0 whenever alpha_i + beta_j - c_ij >= 0
+// (the FP32 representation and rounding errors are below 2^-23 of |alpha| +
+// |beta| + c <= 2 (|alpha| + |beta|)), so the test rejects only elements
+// whose f is certainly <= 0.
 __device__ __forceinline__ float bound_up(float h) { return __fadd_ru(h, __fmul_ru(fabsf(h), 0x1p-22f)); }
 
-// A work item as the evaluation kernel sees it, in execution order (128 B).
+// FP32 (hi, lo) split of an FP64 value: hi + lo = x to ~2^-48 relative.
+__device__ __forceinline__ float2 split2(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+struct EvalCtl;
+// Preparation of one sorted row: (alpha hi, alpha lo, bound_up(alpha hi), 0).
+// Returns [alpha hi]_+ for the fixed-point scale.
+__device__ __forceinline__ float prep_row(double a, float4* rowA)
+{
+    const float2 s = split2(a);
+    *rowA = make_float4(s.x, s.y, bound_up(s.x), 0.f);
+    return fmaxf(s.x, 0.f);
+}
+
+// Preparation of one (padded) column: (beta hi, lo) and bound_up(beta hi); a
+// padding column gets a bound of -inf, which no element passes.
+__device__ __forceinline__ float prep_col(bool real, double b, float2* B2, float* Bp)
+{
+    if (!real) {
+        *B2 = make_float2(-1e30f, 0.f);
+        *Bp = -INFINITY;
+        return 0.f;
+    }
+    const float2 s = split2(b);
+    *B2 = s;
+    *Bp = bound_up(s.x);
+    return fmaxf(s.x, 0.f);
+}
+
+// A work item as the evaluation kernel sees it, in execution order (32 B).
 struct ItemDesc {
-    int item, p, cc, kind;   // item id, panel, column chunk, 0 small / 1 big panel
-    int W, rows, r0, l;      // columns per item; panel (small) or group (big) rows; first sorted row; group (big)
-    int nst, nt, t0, ncols;  // stages per tile (big), tiles, first tile, columns of this item
-    int rb_lo, rb_hi, col0, ngroups;  // row-partial base (int64 halves), first column, groups of the panel
-    int pw[NWARPS + 1];      // first pginfo entry of each consumer warp (small panels), then the end
-    int pad[7];
+    int item;   // item id (index of its psi partials and active flag)
+    int p;      // panel
+    int r0;     // first sorted row
+    int rows;   // rows (whole groups)
+    int col0;   // first column (multiple of ITEM_COLS)
+    int ncols;  // columns of C in the item (<= ITEM_COLS)
+    int nst;    // stages: ceil(rows / STAGE_ROWS)
+    int pad;
 };
 
 // ------------------------------------------------------------------ host plan
@@ -63,26 +94,21 @@ struct HostPlan {
     std::vector<int32_t> perm;    // sorted r -> caller row
     std::vector<int32_t> goff;    // L+1 offsets (sorted rows)
     std::vector<int32_t> rgroup;  // sorted r -> group
-    // panels
-    std::vector<int32_t> pkind;   // 0 small, 1 big
-    std::vector<int32_t> prows;   // rows of the panel
-    std::vector<int32_t> pW;      // columns per work item (multiple of TW)
+    std::vector<int2> rowg;       // sorted r -> {group, end of the group}; 2 padding entries
+    // panels: row ranges of whole groups
+    std::vector<int32_t> prow0;   // first sorted row
+    std::vector<int32_t> prows;   // rows
+    std::vector<int32_t> pW;      // columns per work item (ITEM_COLS)
     std::vector<int32_t> pnch;    // work items (column chunks) of the panel
-    std::vector<int64_t> prp;     // base of the panel's row partials
     std::vector<int32_t> pitem;   // first work-item id of the panel
-    std::vector<int32_t> pw_off;  // [npanels * NWARPS + 1] offsets into pgrp
-    std::vector<int32_t> pgrp;    // groups of each (panel, warp), LPT-balanced
     std::vector<int32_t> gpanel;  // group -> panel (-1 for empty groups)
-    std::vector<int32_t> gsrow;   // group -> first local row in its panel
-    std::vector<int32_t> prow0;   // first sorted row of the panel (rows are contiguous)
-    std::vector<int4> pginfo;     // per pgrp entry: {group, first sorted row, rows, row in panel}
-    std::vector<ItemDesc> desc;   // work items in execution order
     // work items, id = pitem[p] + chunk
     std::vector<int32_t> item_panel, item_chunk;
     std::vector<int32_t> exec_order;  // item ids, largest first
-    int64_t rowpart_len = 0;
-    bool sorted_identity = true;  // labels already non-decreasing
-    int npanels() const { return (int)pkind.size(); }
+    std::vector<ItemDesc> desc;       // work items in execution order
+    int64_t nstages = 0;              // stages streamed by one dense evaluation
+    bool sorted_identity = true;      // labels already non-decreasing
+    int npanels() const { return (int)prows.size(); }
     int nitems() const { return (int)item_panel.size(); }
 };
 
@@ -92,33 +118,91 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
 // ---------------------------------------------------------------- device plan
 struct DevPlan {
     int32_t *perm, *goff, *rgroup;
-    int32_t *pkind, *prows, *pW, *pnch, *pitem, *pw_off, *pgrp, *gpanel, *gsrow;
-    int64_t *prp;
+    int2* rowg;
+    int32_t *prows, *pW, *pnch, *pitem, *gpanel;
     int32_t *item_panel, *item_chunk, *exec_order;
-    int32_t *prow0;
-    int4 *pginfo;
-    ItemDesc *desc;
+    ItemDesc* desc;
 };
+
+// ------------------------------------------------- per-evaluation control word
+// Zeroed before each evaluation's preparation kernel.
+struct EvalCtl {
+    int work;           // work-item counter of the evaluation kernel
+    unsigned amax;      // float bits of max_i [alpha_i hi]_+
+    unsigned bmax;      // float bits of max_j [beta_j hi]_+
+    int pad;
+};
+
+// Adds this warp's maxima of [alpha hi]_+ and [beta hi]_+ into ctl (all
+// lanes of the warp must call it).  Non-negative floats order as their bits.
+__device__ __forceinline__ void record_max(EvalCtl* ctl, float apos, float bpos)
+{
+    const unsigned ma = __reduce_max_sync(0xffffffffu, __float_as_uint(apos));
+    const unsigned mb = __reduce_max_sync(0xffffffffu, __float_as_uint(bpos));
+    if ((threadIdx.x & 31) == 0) {
+        if (ma) atomicMax(&ctl->amax, ma);
+        if (mb) atomicMax(&ctl->bmax, mb);
+    }
+}
+
+// Row and column sums of T (Eq. 5) are accumulated as int64 multiples of 2^-k,
+// so their value does not depend on the order of the additions.  k comes from
+// a bound on the sums: t_ij = s f_ij with s <= 1 / gamma and f_ij <= [alpha_i]_+
+// + [beta_j]_+ (c >= 0), so a row sum is at most n F / gamma and a column sum
+// m F / gamma, F = max [alpha]_+ + max [beta]_+; k puts that bound below 2^61.
+struct FxScale {
+    double to_r, from_r;  // row sums: value * to_r -> integer, integer * from_r -> value
+    double to_c, from_c;  // column sums
+};
+
+__host__ __device__ inline int fx_exponent(double bound)
+{
+    if (!(bound > 0.0) || !(bound < 1e300)) return 0;
+    const int e = ilogb(bound) + 2;  // bound < 2^(e-1): a factor 2 of slack for the FP32 split of alpha, beta
+    const int k = 61 - e;
+    return k < -960 ? -960 : (k > 960 ? 960 : k);
+}
+
+__host__ __device__ inline FxScale fx_scale(unsigned amax_bits, unsigned bmax_bits, int64_t m, int64_t n,
+                                            float gamma)
+{
+    float am, bm;
+#ifdef __CUDA_ARCH__
+    am = __uint_as_float(amax_bits);
+    bm = __uint_as_float(bmax_bits);
+#else
+    memcpy(&am, &amax_bits, 4);
+    memcpy(&bm, &bmax_bits, 4);
+#endif
+    const double F = ((double)am + (double)bm) / (double)gamma;
+    const int kr = fx_exponent(F * (double)n), kc = fx_exponent(F * (double)m);
+    FxScale s;
+    s.to_r = ldexp(1.0, kr);
+    s.from_r = ldexp(1.0, -kr);
+    s.to_c = ldexp(1.0, kc);
+    s.from_c = ldexp(1.0, -kc);
+    return s;
+}
 
 // -------------------------------------------------------------- kernel args
 struct EvalArgs {
-    const float* C;
+    const float* C;     // class-sorted rows, row stride ldc
     int64_t ldc;
-    int32_t m, n, L, ntiles, npanels, nitems;
-    const float2* A2;  // sorted rows: (hi, lo) split of alpha, padded by 2 (copied in 16-byte blocks)
-    const float2* B2;  // columns padded to padded_cols(ntiles): (hi, lo) split of beta
-    const float* Bp;   // bound_up(beta hi) per column, -inf in the padding
-    int* work;         // work-item counter, zero at launch
-    int* err;          // error word (0 = ok)
-    int32_t nlist;     // entries of items
-    DevPlan plan;
-    const int32_t* items;         // item ids, one per CTA
-    const uint8_t* item_active;   // per item id: 1 if launched (its partials valid)
-    const uint32_t* unit_need;    // L x unit_words bitmask of units to stream, NULL = all
+    int32_t m, n, L, ntiles, nitems;
+    const float4* rowA;  // sorted rows: (alpha hi, alpha lo, bound_up(alpha hi), 0)
+    const int2* rowg;    // sorted rows: (group, end of group); 2 padding entries
+    const float2* B2;    // columns padded to padded_cols(n): (hi, lo) split of beta
+    const float* Bp;     // bound_up(beta hi) per column, -inf in the padding
+    EvalCtl* ctl;
+    int* err;            // error word (0 = ok)
+    int32_t nlist;       // entries of desc
+    const ItemDesc* desc;
+    const uint8_t* item_active;   // per item id: 1 if it has a unit to evaluate (screened), else NULL
+    const uint32_t* unit_need;    // L x unit_words bitmask of units to evaluate, NULL = all
     int32_t unit_words;           // ceil(ntiles / 32)
-    double* rowpart;
-    double* colpart;   // npanels x n
-    double* psipart;   // per item id
+    unsigned long long* rowfx;    // [m] fixed-point row sums of T (zeroed by the preparation kernel)
+    unsigned long long* colfx;    // [n] fixed-point column sums of T
+    double* psipart;   // [nitems * NWARPS]: per item and consumer warp, sum of psi
     float* zt;         // snapshot outputs (L x ntiles*TW) or NULL
     float* ot;
     // regularisation scalars
@@ -126,16 +210,17 @@ struct EvalArgs {
     float th2_cut;              // S_hi below this: block surely below threshold
     float gamma;
     double inv2g;               // 1 / (2 gamma)
-    unsigned long long* units_done;  // counter of streamed units (may be NULL)
 };
 
 struct ReduceArgs {
-    int32_t m, n, npanels, nitems;
-    DevPlan plan;
-    const uint8_t* item_active;
-    const double* rowpart;
-    const double* colpart;
+    int32_t m, n, nitems;
+    const int32_t* perm;
+    const uint8_t* item_active; // NULL = all items
+    const unsigned long long* rowfx;
+    const unsigned long long* colfx;
     const double* psipart;
+    const EvalCtl* ctl;
+    float gamma;
     const double* a_sorted;     // FP64 [m] sorted order
     const double* b;            // FP64 [n]
     const double* alpha_sorted; // FP64 [m]
@@ -145,23 +230,26 @@ struct ReduceArgs {
     double* G_sorted;     // [m + n] minus gradient (sorted rows, then columns)
     const double* dir;    // [m + n] direction for dot(G, dir), or NULL
     double* scal;         // [4]: D, dot(G, dir), ||G||_inf, psi
-    double* block_part;   // scratch [3 * nblocks]
+    double* block_part;   // scratch [4 * nblocks]
     unsigned int* counter;// scratch, zero on entry, reset by the last block
     const int* err;       // evaluation error word: non-zero makes D NaN
 };
 
 // launchers (otgs_eval.cu)
+// Zeroes ctl, then writes rowA, B2, Bp (and alpha_s_out), zeroes rowfx and
+// colfx and records max [alpha hi]_+, max [beta hi]_+ in ctl.
 void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, const double* beta,
-                 int32_t m, int32_t n, int32_t ntiles, float2* A2, float2* B2, float* Bp,
-                 double* alpha_s_out, cudaStream_t st);
-// TMA descriptors of C: box k is 2^k rows x STAGE_COLS columns (k = 0..TMA_BOXES-1).
-constexpr int TMA_BOXES = 8;
+                 int32_t m, int32_t n, float4* rowA, float2* B2, float* Bp, double* alpha_s_out,
+                 unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl, cudaStream_t st);
+// TMA descriptors of C: box k is 2^k rows x ITEM_COLS columns (k = 0..TMA_BOXES-1).
+constexpr int TMA_BOXES = 6;
+static_assert((1 << (TMA_BOXES - 1)) == STAGE_ROWS, "boxes must compose any stage height");
 struct TmaMaps {
     CUtensorMap box[TMA_BOXES];
 };
 // Encodes the maps for C (m x n, row stride ldc floats); "" on success.
 std::string make_tmaps(const float* C, int64_t ldc, int64_t m, int64_t n, TmaMaps& T);
-// evaluation kernel (otgs_stream.cu): persistent, n_ctas CTAs; a.work must be zero
+// evaluation kernel (otgs_stream.cu): persistent, n_ctas CTAs; a.ctl zeroed by launch_prep
 void launch_stream(const EvalArgs& a, const TmaMaps& T, int n_ctas, cudaStream_t st);
 size_t stream_smem_bytes();
 void launch_reduce(const ReduceArgs& a, cudaStream_t st);

@@ -77,8 +77,8 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     if (m <= 0 || n <= 0 || L <= 0 || ldc < n) return set_err(OTGS_EINVAL, "need m, n, L > 0 and ldc >= n");
     if (!(gamma > 0.0) || !std::isfinite(gamma) || !(mu >= 0.0) || !std::isfinite(mu))
         return set_err(OTGS_EINVAL, "need gamma > 0 and mu >= 0, finite");
-    if (n % 4 != 0 || ldc % 4 != 0 || reinterpret_cast<uintptr_t>(C) % 16 != 0)
-        return set_err(OTGS_EINVAL, "need n % 4 == 0, ldc % 4 == 0 and a 16-byte aligned C");
+    if (ldc % 4 != 0 || reinterpret_cast<uintptr_t>(C) % 16 != 0)
+        return set_err(OTGS_EINVAL, "need ldc % 4 == 0 and a 16-byte aligned C");
     for (int64_t i = 1; i < m; i++)
         if (labels_host[i] < labels_host[i - 1])
             return set_err(OTGS_EINVAL, "labels must be non-decreasing (class-sorted rows of C)");
@@ -88,27 +88,16 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const int ntiles = hp.ntiles;
     // layout of the scratch array
     Carve cv;
-    const size_t o_perm = cv.take(4 * hp.perm.size()), o_goff = cv.take(4 * hp.goff.size());
-    const size_t o_rgroup = cv.take(4 * hp.rgroup.size()), o_pkind = cv.take(4 * hp.pkind.size());
-    const size_t o_prows = cv.take(4 * hp.prows.size()), o_pW = cv.take(4 * hp.pW.size());
-    const size_t o_pnch = cv.take(4 * hp.pnch.size()), o_pitem = cv.take(4 * hp.pitem.size());
-    const size_t o_pw_off = cv.take(4 * hp.pw_off.size()), o_pgrp = cv.take(4 * hp.pgrp.size());
-    const size_t o_gpanel = cv.take(4 * hp.gpanel.size()), o_gsrow = cv.take(4 * hp.gsrow.size());
-    const size_t o_prp = cv.take(8 * hp.prp.size());
-    const size_t o_ipanel = cv.take(4 * hp.item_panel.size()), o_ichunk = cv.take(4 * hp.item_chunk.size());
-    const size_t o_exec = cv.take(4 * hp.exec_order.size()), o_active = cv.take((size_t)hp.nitems());
-    const size_t o_prow0 = cv.take(4 * hp.prow0.size());
-    const size_t o_pginfo = cv.take(16 * hp.pginfo.size());
+    const size_t o_perm = cv.take(4 * hp.perm.size()), o_rowg = cv.take(sizeof(int2) * hp.rowg.size());
     const size_t o_desc = cv.take(sizeof(ItemDesc) * hp.desc.size());
-    const size_t o_A2 = cv.take(8 * ((size_t)m + 2)), o_B2 = cv.take(8 * (size_t)padded_cols(ntiles));
-    const size_t o_Bp = cv.take(4 * (size_t)padded_cols(ntiles));
-    const size_t o_work = cv.take(16), o_err = cv.take(16);
+    const size_t o_rowA = cv.take(sizeof(float4) * (size_t)m);
+    const size_t o_B2 = cv.take(8 * (size_t)padded_cols(n)), o_Bp = cv.take(4 * (size_t)padded_cols(n));
+    const size_t o_ctl = cv.take(sizeof(EvalCtl)), o_err = cv.take(16);
     const size_t o_aeval = cv.take(8 * (size_t)m);
-    const size_t o_rowpart = cv.take(8 * (size_t)hp.rowpart_len);
-    const size_t o_colpart = cv.take(8 * (size_t)hp.npanels() * (size_t)n);
-    const size_t o_psipart = cv.take(8 * (size_t)hp.nitems());
+    const size_t o_rowfx = cv.take(8 * (size_t)m), o_colfx = cv.take(8 * (size_t)n);
+    const size_t o_psipart = cv.take(8 * (size_t)hp.nitems() * NWARPS);
     const int nred = reduce_blocks((int32_t)m, (int32_t)n);
-    const size_t o_bpart = cv.take(8 * 3 * (size_t)nred), o_counter = cv.take(16), o_scal = cv.take(64);
+    const size_t o_bpart = cv.take(8 * 4 * (size_t)nred), o_counter = cv.take(16), o_scal = cv.take(64);
     if (cv.off > OTGS_STATIC_SCRATCH_BYTES)
         return set_err(OTGS_EINVAL, "problem needs " + std::to_string(cv.off) + " bytes of scratch, above the " +
                                         std::to_string((size_t)OTGS_STATIC_SCRATCH_BYTES) +
@@ -134,56 +123,37 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     auto up = [&](size_t off, const void* src, size_t bytes) {
         return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, st);
     };
-    std::vector<uint8_t> ones(hp.nitems(), 1);
-    const std::pair<size_t, const std::vector<int32_t>*> i32s[] = {
-        {o_perm, &hp.perm}, {o_goff, &hp.goff}, {o_rgroup, &hp.rgroup}, {o_pkind, &hp.pkind},
-        {o_prows, &hp.prows}, {o_pW, &hp.pW}, {o_pnch, &hp.pnch}, {o_pitem, &hp.pitem},
-        {o_pw_off, &hp.pw_off}, {o_pgrp, &hp.pgrp}, {o_gpanel, &hp.gpanel}, {o_gsrow, &hp.gsrow},
-        {o_ipanel, &hp.item_panel}, {o_ichunk, &hp.item_chunk}, {o_exec, &hp.exec_order},
-        {o_prow0, &hp.prow0}};
-    for (const auto& pr : i32s)
-        if ((e = up(pr.first, pr.second->data(), 4 * pr.second->size())) != cudaSuccess) break;
-    if (e == cudaSuccess) e = up(o_prp, hp.prp.data(), 8 * hp.prp.size());
-    if (e == cudaSuccess) e = up(o_pginfo, hp.pginfo.data(), 16 * hp.pginfo.size());
+    e = up(o_perm, hp.perm.data(), 4 * hp.perm.size());
+    if (e == cudaSuccess) e = up(o_rowg, hp.rowg.data(), sizeof(int2) * hp.rowg.size());
     if (e == cudaSuccess) e = up(o_desc, hp.desc.data(), sizeof(ItemDesc) * hp.desc.size());
-    if (e == cudaSuccess) e = up(o_active, ones.data(), ones.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_counter, 0, 16, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(base + o_work, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_err, 0, 16, st);
     int n_sm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return set_err(OTGS_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
-    DevPlan dp;
-    dp.perm = (int32_t*)(base + o_perm); dp.goff = (int32_t*)(base + o_goff); dp.rgroup = (int32_t*)(base + o_rgroup);
-    dp.pkind = (int32_t*)(base + o_pkind); dp.prows = (int32_t*)(base + o_prows); dp.pW = (int32_t*)(base + o_pW);
-    dp.pnch = (int32_t*)(base + o_pnch); dp.pitem = (int32_t*)(base + o_pitem); dp.pw_off = (int32_t*)(base + o_pw_off);
-    dp.pgrp = (int32_t*)(base + o_pgrp); dp.gpanel = (int32_t*)(base + o_gpanel); dp.gsrow = (int32_t*)(base + o_gsrow);
-    dp.prp = (int64_t*)(base + o_prp);
-    dp.item_panel = (int32_t*)(base + o_ipanel); dp.item_chunk = (int32_t*)(base + o_ichunk);
-    dp.exec_order = (int32_t*)(base + o_exec);
-    dp.prow0 = (int32_t*)(base + o_prow0);
-    dp.pginfo = (int4*)(base + o_pginfo);
-    dp.desc = (ItemDesc*)(base + o_desc);
-    const uint8_t* active = base + o_active;
-    float2* A2 = (float2*)(base + o_A2);
+    const int32_t* perm = (const int32_t*)(base + o_perm);
+    float4* rowA = (float4*)(base + o_rowA);
     float2* B2 = (float2*)(base + o_B2);
-    double* aeval = (double*)(base + o_aeval);
-    // the caller's a is already in class-sorted order (labels non-decreasing)
     float* Bp = (float*)(base + o_Bp);
-    launch_prep(alpha, true, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, Bp, aeval, st);
+    EvalCtl* ctl = (EvalCtl*)(base + o_ctl);
+    double* aeval = (double*)(base + o_aeval);
+    unsigned long long* rowfx = (unsigned long long*)(base + o_rowfx);
+    unsigned long long* colfx = (unsigned long long*)(base + o_colfx);
+    // the caller's alpha is already in class-sorted order (labels non-decreasing)
+    launch_prep(alpha, true, perm, beta, (int32_t)m, (int32_t)n, rowA, B2, Bp, aeval, rowfx, colfx, ctl, st);
     EvalArgs ea;
     memset(&ea, 0, sizeof(ea));
     ea.C = C; ea.ldc = ldc;
     ea.m = (int32_t)m; ea.n = (int32_t)n; ea.L = L; ea.ntiles = ntiles;
-    ea.npanels = hp.npanels(); ea.nitems = hp.nitems();
-    ea.A2 = A2; ea.B2 = B2; ea.plan = dp;
-    ea.Bp = Bp;
-    ea.work = (int*)(base + o_work); ea.err = (int*)(base + o_err);
+    ea.nitems = hp.nitems();
+    ea.rowA = rowA; ea.rowg = (const int2*)(base + o_rowg);
+    ea.B2 = B2; ea.Bp = Bp;
+    ea.ctl = ctl; ea.err = (int*)(base + o_err);
     ea.nlist = hp.nitems();
-    ea.items = dp.exec_order; ea.item_active = active; ea.unit_need = nullptr;
+    ea.desc = (const ItemDesc*)(base + o_desc);
+    ea.item_active = nullptr; ea.unit_need = nullptr;
     ea.unit_words = (ntiles + 31) / 32;
-    ea.rowpart = (double*)(base + o_rowpart);
-    ea.colpart = (double*)(base + o_colpart);
+    ea.rowfx = rowfx; ea.colfx = colfx;
     ea.psipart = (double*)(base + o_psipart);
     const double theta = mu * gamma;
     ea.theta_hi = (float)theta;
@@ -202,9 +172,10 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     launch_stream(ea, tm, n_sm < hp.nitems() ? n_sm : hp.nitems(), st);
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
-    ra.m = (int32_t)m; ra.n = (int32_t)n; ra.npanels = hp.npanels(); ra.nitems = hp.nitems();
-    ra.plan = dp; ra.item_active = active;
-    ra.rowpart = ea.rowpart; ra.colpart = ea.colpart; ra.psipart = ea.psipart;
+    ra.m = (int32_t)m; ra.n = (int32_t)n; ra.nitems = hp.nitems();
+    ra.perm = perm; ra.item_active = nullptr;
+    ra.rowfx = rowfx; ra.colfx = colfx; ra.psipart = ea.psipart;
+    ra.ctl = ctl; ra.gamma = ea.gamma;
     ra.a_sorted = a; ra.b = b; ra.alpha_sorted = aeval; ra.beta = beta;
     ra.out_caller = out; ra.scal = (double*)(base + o_scal);
     ra.block_part = (double*)(base + o_bpart);

@@ -291,7 +291,7 @@ bool Handle::snapshot_at(const double* alpha, bool alpha_sorted, const double* b
 {
     if (!ensure_screen()) return false;
     if (!snap_valid && !zero_snapshot()) return false;
-    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, Bp, alpha_eval, st);
+    prep(alpha, alpha_sorted, beta);
     if (build_N && prm.use_lower_bound) {
         launch_delta(this, beta);
         ScreenArgs s = make_screen_args(this);
@@ -313,7 +313,7 @@ bool Handle::eval_screened(const double* alpha, bool alpha_sorted, const double*
 {
     if (!ensure_screen()) return false;
     if (!snap_valid && !zero_snapshot()) return false;
-    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, ntiles, A2, B2, Bp, alpha_eval, st);
+    prep(alpha, alpha_sorted, beta);
     return eval_screened_prepped(beta, G_sorted, dir, out_caller);
 }
 
@@ -328,7 +328,7 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     s.beta = beta;
     const int64_t units = (int64_t)L * ntiles;
     k_screen<<<(unsigned)((units + 7) / 8), 256, 0, st>>>(s);
-    EvalArgs e = eval_args(dp.exec_order, item_active, unit_need, false);
+    EvalArgs e = eval_args(item_active, unit_need, false);
     eval_launch(e, std::min(n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);

@@ -21,32 +21,33 @@ namespace otgs {
 #define FULLMASK 0xffffffffu
 
 // ------------------------------------------------------------------ kernels
-// x_t = x + t d; also the float-pair split of x_t for the evaluation kernel.
+// x_t = x + t d; also the preparation of x_t for the evaluation kernel (the
+// same per-row and per-column records as the plain preparation kernel).
 __global__ void k_trial(SolverState* S, const double* __restrict__ x, const double* __restrict__ d, double* xt,
-                        float2* A2, float2* B2, float* Bp, double* alpha_eval, int m, int n, int npad)
+                        float4* rowA, float2* B2, float* Bp, double* alpha_eval, unsigned long long* rowfx,
+                        unsigned long long* colfx, EvalCtl* ctl, int m, int n, int npad)
 {
-    if (S->done) return;
+    if (S->done) return;  // the same for every thread
     const double t = S->t;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    float apos = 0.f, bpos = 0.f;
     if (i < m) {
         const double v = fma(t, d[i], x[i]);
         xt[i] = v;
         alpha_eval[i] = v;
-        const float h = __double2float_rn(v);
-        A2[i] = make_float2(h, __double2float_rn(v - (double)h));
+        apos = prep_row(v, rowA + i);
+        rowfx[i] = 0ull;
     }
     if (i < npad) {
+        double v = 0.0;
         if (i < n) {
-            const double v = fma(t, d[m + i], x[m + i]);
+            v = fma(t, d[m + i], x[m + i]);
             xt[m + i] = v;
-            const float h = __double2float_rn(v);
-            B2[i] = make_float2(h, __double2float_rn(v - (double)h));
-            Bp[i] = bound_up(h);
-        } else {
-            B2[i] = make_float2(-1e30f, 0.f);
-            Bp[i] = -INFINITY;
+            colfx[i] = 0ull;
         }
+        bpos = prep_col(i < n, v, B2 + i, Bp + i);
     }
+    record_max(ctl, apos, bpos);
 }
 
 __device__ double bracket_step(double lo, double Flo, double dlo, double hi, double Fhi, double dhi)
@@ -383,7 +384,7 @@ int Solver::run(double tol, int maxit)
     k_gg<<<nblk, SOLVER_THREADS, 0, st>>>(G, N, pbase);
     k_direction<<<1, 128, 0, st>>>(state, pbase, ppair, nblk, 1);
     k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 1);
-    const int npad = padded_cols(h->ntiles);
+    const int npad = padded_cols(h->n);
     const int tb = (std::max((int)h->m, npad) + 255) / 256;
     const size_t hdr = offsetof(SolverState, tol);  // the int fields and the eval counter
     const long long max_trials = (long long)maxit * (LS_MAX_EVALS + 2) + 16;
@@ -396,8 +397,9 @@ int Solver::run(double tol, int maxit)
             h->fail(OTGS_ENOTCONV, "solver exceeded its trial budget");
             break;
         }
-        k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->A2, h->B2, h->Bp, h->alpha_eval, (int)h->m,
-                                    (int)h->n, npad);
+        cudaMemsetAsync(h->ctl, 0, sizeof(EvalCtl), st);
+        k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->rowA, h->B2, h->Bp, h->alpha_eval, h->rowfx, h->colfx,
+                                    h->ctl, (int)h->m, (int)h->n, npad);
         if (!eval_trial()) return h->last_code;
         k_linesearch<<<1, 1, 0, st>>>(state, h->scal);
         k_accept<<<nblk, SOLVER_THREADS, 0, st>>>(state, x, G, xt, Gt, Sv, Yv, N, pbase);
@@ -423,7 +425,7 @@ int Solver::run(double tol, int maxit)
     return hstate->status;
 }
 
-// Evaluation of the trial point prepared by k_trial (A2/B2/alpha_eval are set).
+// Evaluation of the trial point prepared by k_trial.
 bool Solver::eval_trial()
 {
     const double* beta = xt + h->m;

@@ -2,34 +2,33 @@
 // the dual (Eq. 4) and its gradient (Eq. 5), fed by TMA.
 //
 // Persistent, one CTA per SM, warp-specialised:
-//  * a producer warp takes work items (host-built descriptors, fetched one
-//    item ahead) from a global counter and streams each stage -- up to
-//    STAGE_ROWS rows x STAGE_COLS columns of C as 2D TMA boxes, plus the
-//    rows' alpha pairs and the columns' beta pairs as bulk copies -- into a
-//    ring of NSTAGES shared-memory stages completed by mbarrier transaction
-//    counts;
-//  * eight consumer warps evaluate the stage out of shared memory, lane k
-//    owning columns k and k + 32 of the stage, and release it.
-// A stage holds a small panel (whole groups of <= STAGE_ROWS rows; each warp
-// walks a contiguous run of whole groups) or STAGE_ROWS rows of one big group
-// (each warp takes 16 rows; per-column partial sums meet in shared memory in
-// warp order).  A big group's tile pair spans ceil(g / STAGE_ROWS) stages; they
-// stay in the ring for the second pass when they fit, else the second pass
-// re-reads the rows from L2.
+//  * a producer warp takes work items (a panel of whole groups x ITEM_COLS
+//    columns; host-built descriptors fetched three items ahead) from a global
+//    counter and streams each item's rows, STAGE_ROWS at a time, into a ring
+//    of NSTAGES shared-memory stages: the rows of C as 2D TMA boxes (1 KB per
+//    row), the rows' alpha records and (group, end) records as bulk copies,
+//    and on an item's first stage its columns' beta constants.  Stages
+//    complete on mbarrier transaction counts;
+//  * NWARPS consumer warps: warp w owns the item's columns [32 w, 32 w + 32),
+//    one per lane, and walks every row of every stage, so each block (l, j)
+//    is evaluated start to end by one thread and the warps' work is the same
+//    whatever the group sizes.
 //
 // Per block (group l, column j): pass A forms f = alpha_i + beta_j - c_ij only
-// where the cheap bound c_ij < A'_i + B'_j says f may be positive (A', B' are
-// alpha, beta rounded up by a relative 2^-22, so no positive f is missed), in
-// double-float with TwoSum, and sums S = ||[f_[l]]_+||^2 and P = sum [f_[l]]_+;
-// then the shrink s = [z - theta]_+ / (gamma z) and psi = [z - theta]_+^2 /
-// (2 gamma) of Eq. 5; pass B adds s [f]_+ into the row sums (one warp sum per
-// row).  Row, column and psi partial sums go to per-item buffers that the
+// where the cheap bound says f may be positive -- fl(fl(A'_i - c_ij) + B'_j) > 0
+// with A', B' alpha, beta rounded up by a relative 2^-22, tested on the max
+// over four rows at a time -- in double-float with TwoSum, and sums S =
+// ||[f_[l]]_+||^2 and P = sum [f_[l]]_+.  At the group's last row: the shrink
+// s = [z - theta]_+ / (gamma z) and psi = [z - theta]_+^2 / (2 gamma) of Eq. 5,
+// and, where s > 0, pass B adds s [f]_+ into the row sums (one warp sum per
+// row; rows of earlier stages are re-read from L2).  Row and column sums go
+// to int64 fixed-point accumulators by atomic adds, whose total does not
+// depend on their order; psi goes to per-(item, warp) partials that the
 // reduction kernel adds in a fixed order.
 //
-// Every wait is on an mbarrier and gives up after WAIT_NS (the consumer warps'
-// own barrier is an mbarrier too); on timeout the kernel records an error in
-// A.err, the producer waits (bounded) for the copies it issued, and all warps
-// return.
+// Every wait is on an mbarrier and gives up after WAIT_NS; on timeout the
+// kernel records an error in A.err, the producer waits (bounded) for the
+// copies it issued, and all warps return.
 #include <mutex>
 #include <string>
 
@@ -41,42 +40,39 @@ namespace otgs {
 
 namespace {
 
-constexpr int CONSUMERS = 8;
+constexpr int CONSUMERS = NWARPS;
 constexpr int THREADS = (CONSUMERS + 1) * 32;
-constexpr int SC = STAGE_COLS;                         // columns per stage
-constexpr int WROWS = STAGE_ROWS / CONSUMERS;          // big stages: rows per consumer warp
-constexpr uint32_t ROW_BYTES = SC * 4;                 // a TMA box row, zero-filled past column n
+constexpr int IC = ITEM_COLS;                          // columns of a stage row
+constexpr int SR = STAGE_ROWS;                         // rows of a stage
+constexpr uint32_t ROW_BYTES = IC * 4;                 // a TMA box row, zero-filled past column n
 constexpr unsigned long long WAIT_NS = 2000000000ull;  // give up a wait after 2 s
+constexpr int DESC_WORDS = (int)(sizeof(ItemDesc) / sizeof(int));
+static_assert(DESC_WORDS <= 32, "a descriptor is spread over the producer's lanes");
+static_assert(SR == 32, "the producer maps one lane to each row of a stage");
 
-enum : int { H_FIRST = 1, H_LAST = 2, H_TERM = 4, H_BIG_HELD = 8, H_SKIP = 16 };
+enum : int { H_FIRST = 1, H_LAST = 2, H_TERM = 4 };
 
-// Everything the consumers need about a stage, written by the producer: the
-// item's descriptor plus the stage's own fields.
+// What the consumers need about a stage, written by the producer.
 struct StageHdr {
     ItemDesc d;
-    int tile, sidx, nst, flags;
-    int a_shift;  // offset of the stage's row 0 in arow[]
-    int pad[3];
+    int sidx;     // stage index within the item
+    int flags;
+    int g_shift;  // offset of the stage's row 0 in rowG[]
+    int pad;
 };
 
 struct Smem {
-    float stage[NSTAGES][STAGE_ROWS * SC];   // NSTAGES x 32 KB; stage row r at [r * SC]
-    float2 arow[NSTAGES][STAGE_ROWS + 2];    // (alpha hi, lo) of the stage's rows; row r at [r + a_shift]
-    float2 colB[NSTAGES][SC];                // (beta hi, lo) of the stage's columns
-    float colP[NSTAGES][SC];                 // B' of the stage's columns
-    int4 gstage[NSTAGES][PANEL_MAX_GROUPS];  // first stage of a small item: the panel's group entries
-    int4 ginfo[PANEL_MAX_GROUPS];            // small item: {group, first sorted row, rows, row in panel}
+    float stage[NSTAGES][SR * IC];   // NSTAGES x 32 KB; stage row r at [r * IC]
+    float4 rowA[NSTAGES][SR];        // (alpha hi, alpha lo, A', 0) of the stage's rows
+    int2 rowG[NSTAGES][SR + 2];      // (group, end of group) of the stage's rows, row r at [r + g_shift]
+    float2 colB[NSTAGES][IC];        // item's first stage: (beta hi, lo) of its columns
+    float colP[NSTAGES][IC];         // item's first stage: B' of its columns
+    uint32_t rmask[NSTAGES][SR];     // screened: bit w set = warp w evaluates the row's block
+    StageHdr hdr[NSTAGES];
     uint64_t full[NSTAGES];
     uint64_t empty[NSTAGES];
-    uint64_t cbar;  // barrier of the consumer warps
-    StageHdr hdr[NSTAGES];
-    float colacc[CONSUMERS][SMALL_CHUNK];  // small item: per-warp column sums
-    float rowacc[BIG_SMEM_ROWS];           // row sums of the current item
-    float4 red[CONSUMERS][SC];             // big tiles: per-warp (S_h, S_l, P_h, P_l) per column
-    float redO[CONSUMERS][SC];
-    double psi_w[CONSUMERS];
-    int anyw[CONSUMERS];
 };
+static_assert(sizeof(Smem) + 1024 <= 227 * 1024, "shared memory of one CTA (plus alignment slack)");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -136,7 +132,7 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
         : "memory");
 }
 
-// One TMA box: rows [y, y + 2^k) x columns [x, x + SC) of C into dst.
+// One TMA box: rows [y, y + 2^k) x columns [x, x + IC) of C into dst.
 __device__ __forceinline__ void tma_box(const TmaMaps& T, int k, float* dst, int x, int y, uint64_t* bar)
 {
     asm volatile(
@@ -146,15 +142,15 @@ __device__ __forceinline__ void tma_box(const TmaMaps& T, int k, float* dst, int
         : "memory");
 }
 
-// Rows [y, y + rows) (rows <= 2^(TMA_BOXES-1)) into dst rows [0, rows): one
-// box per set bit of rows, so exactly the requested rows are read.
+// Rows [y, y + rows) (rows <= STAGE_ROWS) into dst rows [0, rows): one box per
+// set bit of rows, so exactly the requested rows are read.
 __device__ __forceinline__ void tma_rows(const TmaMaps& T, float* dst, int x, int y, int rows, uint64_t* bar)
 {
     int off = 0;
 #pragma unroll
     for (int k = TMA_BOXES - 1; k >= 0; k--)
         if (rows & (1 << k)) {
-            tma_box(T, k, dst + off * SC, x, y + off, bar);
+            tma_box(T, k, dst + off * IC, x, y + off, bar);
             off += 1 << k;
         }
 }
@@ -168,7 +164,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
     e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// (h, l) += (oh, ol); symmetric in its arguments bit for bit.
+// (h, l) += (oh, ol)
 __device__ __forceinline__ void df_add(float& h, float& l, float oh, float ol)
 {
     float s, e;
@@ -226,63 +222,63 @@ __device__ __forceinline__ float block_scale(float Sh, float Sl, const EvalArgs&
 // z rounded up (snapshot value z~ of Def. 1, kept as an upper bound).
 __device__ __forceinline__ float z_up(float Sh, float Sl) { return __fsqrt_ru(fmaxf(__fadd_ru(Sh, Sl), 0.f)); }
 
-// This lane's two columns of the stage: k and k + 32.
-struct Col2 {
-    float bh0, bl0, bp0, bh1, bl1, bp1;
-};
-
-__device__ __forceinline__ Col2 load_cols(const Smem& S, int slot, int lane)
+// The cheap test of one element: false only when f_ij is certainly <= 0.
+__device__ __forceinline__ bool maybe_pos(float ap, float c, float bp)
 {
-    Col2 c;
-    const float2 u = S.colB[slot][lane], v = S.colB[slot][lane + 32];
-    c.bh0 = u.x; c.bl0 = u.y; c.bh1 = v.x; c.bl1 = v.y;
-    c.bp0 = S.colP[slot][lane];
-    c.bp1 = S.colP[slot][lane + 32];
-    return c;
+    return __fadd_rn(__fsub_rn(ap, c), bp) > 0.f;
 }
 
-// Pass A for one row: c0, c1 in this lane's columns.
+// One element of pass A.
+__device__ __forceinline__ void elem_exact(const float4& a, float c, float bh, float bl, float bp, Acc& acc,
+                                           bool& any)
+{
+    if (maybe_pos(a.z, c, bp)) {
+        float fh, fl;
+        f_exact(a.x, a.y, bh, bl, c, fh, fl);
+        if (fh > 0.f) {
+            acc_p(fh, fl, acc);
+            any = true;
+        }
+    }
+}
+
+// o~^2 term of Def. 1: [f]_-^2, f in plain FP32 (the snapshot keeps o~ rounded up).
+__device__ __forceinline__ void acc_neg(const float4& a, float c, float bh, float& O)
+{
+    const float x = fminf(__fsub_rn(__fadd_rn(a.x, bh), c), 0.f);
+    O = fmaf(x, x, O);
+}
+
+// Pass A over rows [r, e) of a stage for this lane's column.
 template <bool SNAP>
-__device__ __forceinline__ bool row_a(float2 a2, float c0, float c1, const Col2& cl, Acc& a0, Acc& a1, float& O0,
-                                      float& O1)
+__device__ __forceinline__ void scan_rows(const float* st, const float4* rA, int r, int e, float bh, float bl,
+                                          float bp, Acc& acc, float& O, bool& any)
 {
-    if (SNAP) {
-        const float x0 = fminf(__fsub_rn(__fadd_rn(a2.x, cl.bh0), c0), 0.f);
-        const float x1 = fminf(__fsub_rn(__fadd_rn(a2.x, cl.bh1), c1), 0.f);
-        O0 = fmaf(x0, x0, O0);
-        O1 = fmaf(x1, x1, O1);
+    for (; r + 4 <= e; r += 4) {
+        const float c0 = st[(r + 0) * IC], c1 = st[(r + 1) * IC], c2 = st[(r + 2) * IC], c3 = st[(r + 3) * IC];
+        const float4 a0 = rA[r + 0], a1 = rA[r + 1], a2 = rA[r + 2], a3 = rA[r + 3];
+        if (SNAP) {
+            acc_neg(a0, c0, bh, O);
+            acc_neg(a1, c1, bh, O);
+            acc_neg(a2, c2, bh, O);
+            acc_neg(a3, c3, bh, O);
+        }
+        // rounding is monotonic, so fl(max(x) + B') > 0 iff some fl(x + B') > 0
+        const float mx = fmaxf(fmaxf(__fsub_rn(a0.z, c0), __fsub_rn(a1.z, c1)),
+                               fmaxf(__fsub_rn(a2.z, c2), __fsub_rn(a3.z, c3)));
+        if (__fadd_rn(mx, bp) > 0.f) {
+            elem_exact(a0, c0, bh, bl, bp, acc, any);
+            elem_exact(a1, c1, bh, bl, bp, acc, any);
+            elem_exact(a2, c2, bh, bl, bp, acc, any);
+            elem_exact(a3, c3, bh, bl, bp, acc, any);
+        }
     }
-    const float ap = bound_up(a2.x);
-    bool any = false;
-    if (c0 < __fadd_rn(ap, cl.bp0)) {
-        float fh, fl;
-        f_exact(a2.x, a2.y, cl.bh0, cl.bl0, c0, fh, fl);
-        if (fh > 0.f) { acc_p(fh, fl, a0); any = true; }
+    for (; r < e; r++) {
+        const float c = st[r * IC];
+        const float4 a = rA[r];
+        if (SNAP) acc_neg(a, c, bh, O);
+        elem_exact(a, c, bh, bl, bp, acc, any);
     }
-    if (c1 < __fadd_rn(ap, cl.bp1)) {
-        float fh, fl;
-        f_exact(a2.x, a2.y, cl.bh1, cl.bl1, c1, fh, fl);
-        if (fh > 0.f) { acc_p(fh, fl, a1); any = true; }
-    }
-    return any;
-}
-
-// Pass B for one row: s0 [f]_+ + s1 [f]_+ over this lane's columns.
-__device__ __forceinline__ float row_b(float2 a2, float c0, float c1, const Col2& cl, float s0, float s1)
-{
-    const float ap = bound_up(a2.x);
-    float rs = 0.f;
-    if (s0 > 0.f && c0 < __fadd_rn(ap, cl.bp0)) {
-        float fh, fl;
-        f_exact(a2.x, a2.y, cl.bh0, cl.bl0, c0, fh, fl);
-        if (fh > 0.f) rs = fmaf(s0, fh, rs);
-    }
-    if (s1 > 0.f && c1 < __fadd_rn(ap, cl.bp1)) {
-        float fh, fl;
-        f_exact(a2.x, a2.y, cl.bh1, cl.bl1, c1, fh, fl);
-        if (fh > 0.f) rs = fmaf(s1, fh, rs);
-    }
-    return rs;
 }
 
 __device__ __forceinline__ float warp_sum(float v)
@@ -292,9 +288,9 @@ __device__ __forceinline__ float warp_sum(float v)
     return v;
 }
 
-__device__ __forceinline__ bool unit_bit(const uint32_t* need, int words, int l, int jt)
+__device__ __forceinline__ void red_fx(unsigned long long* p, double v, double to_fx)
 {
-    return (__ldg(need + (int64_t)l * words + (jt >> 5)) >> (jt & 31)) & 1u;
+    atomicAdd(p, (unsigned long long)__double2ll_rn(v * to_fx));
 }
 
 // Snapshot values of block (l, col) (written only for col < n).
@@ -305,43 +301,6 @@ __device__ __forceinline__ void put_snap(const EvalArgs& A, int l, int col, floa
         A.zt[q] = zt;
         A.ot[q] = ot;
     }
-}
-
-// Producer lane: registers the stage's transaction bytes on its full barrier
-// and copies the stage's column constants and the (alpha hi, lo) pairs of rows
-// [ra, ra + rows) -- as the 16-byte aligned superset [ra & ~1, (ra + rows + 1)
-// & ~1) -- into the stage.  Returns the offset of row ra in arow[slot].
-__device__ __forceinline__ int stage_side(const EvalArgs& A, Smem& S, int slot, int ra, int rows, uint32_t extra,
-                                          int col)
-{
-    const uint32_t cb = SC * sizeof(float2) + SC * sizeof(float);
-    int a0 = ra & ~1, a1 = (ra + rows + 1) & ~1;
-    if (rows == 0) a0 = a1 = ra;
-    const uint32_t ab = (uint32_t)(a1 - a0) * (uint32_t)sizeof(float2);
-    mbar_expect(&S.full[slot], extra + ab + cb);
-    bulk_copy(S.colB[slot], A.B2 + col, SC * sizeof(float2), &S.full[slot]);
-    bulk_copy(S.colP[slot], A.Bp + col, SC * sizeof(float), &S.full[slot]);
-    if (ab) bulk_copy(S.arow[slot], A.A2 + a0, ab, &S.full[slot]);
-    return ra - a0;
-}
-
-// Barrier of the eight consumer warps on an mbarrier (bounded wait); phase
-// counts the barriers this warp has passed.
-__device__ __forceinline__ bool consumer_sync(Smem& S, uint32_t& phase)
-{
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) mbar_arrive(&S.cbar);
-    const bool ok = mbar_wait(&S.cbar, phase & 1u);
-    phase++;
-    return ok;
-}
-
-__device__ __forceinline__ void load_desc(const EvalArgs& A, int it, ItemDesc& d)
-{
-    const int4* src = reinterpret_cast<const int4*>(A.plan.desc + it);
-    int4* dst = reinterpret_cast<int4*>(&d);
-#pragma unroll
-    for (int k = 0; k < (int)(sizeof(ItemDesc) / sizeof(int4)); k++) dst[k] = __ldg(src + k);
 }
 
 }  // namespace
@@ -359,13 +318,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
             mbar_init(&S.full[s], 1);
             mbar_init(&S.empty[s], CONSUMERS);
         }
-        mbar_init(&S.cbar, CONSUMERS);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     // ------------------------------------------------------------ producer
     if (warp == CONSUMERS) {
+        const bool screened = A.unit_need != nullptr;
         long long issued = 0;  // stages issued so far
         bool ok = true;
         auto next_slot = [&](int& slot) -> bool {
@@ -373,19 +332,29 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
             const long long use = issued / NSTAGES;
             return use == 0 || mbar_wait(&S.empty[slot], (uint32_t)((use - 1) & 1));
         };
-        // the next item's index and descriptor are fetched one item ahead
-        int nxt = 0;
-        if (lane == 0) nxt = atomicAdd(A.work, 1);
-        nxt = __shfl_sync(FULLMASK, nxt, 0);
-        ItemDesc dn;
-        bool act_n = true;
-        if (nxt < A.nlist) {
-            load_desc(A, nxt, dn);
-            act_n = !A.unit_need || __ldg(A.item_active + dn.item);
-        }
+        // Items flow through a software pipeline so that no load is waited on
+        // right after it is issued: at the start of item k the counter is bumped
+        // for item k+3, the descriptor of item k+2 is loaded (lane w holds word
+        // w) and the active flag of item k+1.
+        auto fetch = [&]() -> int { return lane == 0 ? atomicAdd(&A.ctl->work, 1) : 0; };
+        auto bcast = [&](int v) -> int { return __shfl_sync(FULLMASK, v, 0); };
+        auto load_w = [&](int idx) -> int {
+            return (idx < A.nlist && lane < DESC_WORDS) ? __ldg(reinterpret_cast<const int*>(A.desc + idx) + lane) : 0;
+        };
+        auto load_act = [&](int idx, int w) -> int {
+            const int item = __shfl_sync(FULLMASK, w, 0);
+            if (idx >= A.nlist) return 0;
+            if (!A.item_active) return 1;
+            return lane == 0 ? (int)__ldg(A.item_active + item) : 0;
+        };
+        int i0 = bcast(fetch());
+        int w0 = load_w(i0);
+        int a0 = load_act(i0, w0);
+        int i1 = bcast(fetch());
+        int w1 = load_w(i1);
+        int i2r = fetch();
         for (;;) {
-            const int it = nxt;
-            if (it >= A.nlist) {
+            if (i0 >= A.nlist) {
                 int slot;
                 if (!next_slot(slot)) { ok = false; break; }
                 if (lane == 0) {
@@ -395,73 +364,56 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
                 issued++;
                 break;
             }
-            const ItemDesc d = dn;
-            const bool act = act_n;
-            if (lane == 0) nxt = atomicAdd(A.work, 1);
-            nxt = __shfl_sync(FULLMASK, nxt, 0);
-            if (nxt < A.nlist) {
-                load_desc(A, nxt, dn);
-                act_n = !A.unit_need || __ldg(A.item_active + dn.item);
-            }
-            if (!act) continue;
-            for (int t = 0; t < d.nt && ok; t += 2) {
-                const int jt = d.t0 + t;
-                const int col = jt * TW;
-                const bool two = t + 1 < d.nt;
-                const bool tneed = d.kind == 0 || !A.unit_need || unit_bit(A.unit_need, A.unit_words, d.l, jt) ||
-                                   (two && unit_bit(A.unit_need, A.unit_words, d.l, jt + 1));
-                const int tst = tneed ? d.nst : 1;  // a skipped big tile pair sends one empty stage
-                for (int si = 0; si < tst; si++) {
+            const int a1 = load_act(i1, w1);
+            const int i2 = bcast(i2r);
+            const int w2 = load_w(i2);
+            const int i3r = fetch();
+            if (bcast(a0)) {
+                const int r0 = __shfl_sync(FULLMASK, w0, 2), rows = __shfl_sync(FULLMASK, w0, 3);
+                const int col0 = __shfl_sync(FULLMASK, w0, 4), nst = __shfl_sync(FULLMASK, w0, 6);
+                const int tile0 = col0 / TW;  // a multiple of NWARPS: the item's tiles share one mask word
+                for (int s = 0; s < nst; s++) {
+                    const int ra = r0 + s * SR;
+                    const int nr = min(SR, rows - s * SR);
+                    uint32_t m8 = 0xffu;
+                    uint32_t need = nr == 32 ? FULLMASK : ((1u << nr) - 1u);
+                    if (screened) {
+                        m8 = 0u;
+                        if (lane < nr) {
+                            const int l = __ldg(&A.rowg[ra + lane].x);
+                            const uint32_t word = __ldg(A.unit_need + (int64_t)l * A.unit_words + (tile0 >> 5));
+                            m8 = (word >> (tile0 & 31)) & 0xffu;
+                        }
+                        need = __ballot_sync(FULLMASK, m8 != 0u);
+                    }
                     int slot;
                     if (!next_slot(slot)) { ok = false; break; }
-                    float* dst = S.stage[slot];
-                    // H_LAST marks every stage of the item's last tile pair (consumers
-                    // read the flags of a pair's first stage)
-                    int flags = (t == 0 && si == 0 ? H_FIRST : 0) | (t + 2 >= d.nt ? H_LAST : 0);
-                    if (d.kind && d.nst <= NSTAGES) flags |= H_BIG_HELD;
-                    if (d.kind && !tneed) flags |= H_SKIP;
-                    int ra = d.r0, rows = d.rows;
-                    uint32_t extra = 0;
-                    if (d.kind == 0) {
-                        if (!A.unit_need) {
-                            extra = (uint32_t)rows * ROW_BYTES;
-                        } else {
-                            uint32_t cnt = 0;
-                            for (int gi = d.pw[0] + lane; gi < d.pw[NWARPS]; gi += 32) {
-                                const int4 g4 = __ldg(A.plan.pginfo + gi);
-                                if (unit_bit(A.unit_need, A.unit_words, g4.x, jt) ||
-                                    (two && unit_bit(A.unit_need, A.unit_words, g4.x, jt + 1)))
-                                    cnt += (uint32_t)g4.z;
-                            }
-                            for (int off = 16; off >= 1; off >>= 1) cnt += __shfl_xor_sync(FULLMASK, cnt, off);
-                            extra = cnt * ROW_BYTES;
-                            if (cnt == 0) rows = 0;
-                        }
-                        if (t == 0) extra += (uint32_t)d.ngroups * 16u;
-                    } else {
-                        ra = d.r0 + si * STAGE_ROWS;
-                        rows = tneed ? min(STAGE_ROWS, d.rows - si * STAGE_ROWS) : 0;
-                        extra = (uint32_t)rows * ROW_BYTES;
-                    }
+                    S.rmask[slot][lane] = m8;
+                    if (lane < DESC_WORDS) reinterpret_cast<int*>(&S.hdr[slot].d)[lane] = w0;
                     if (lane == 0) {
-                        const int a_sh = stage_side(A, S, slot, ra, rows, extra, col);
-                        if (d.kind == 0 && t == 0)
-                            bulk_copy(S.gstage[slot], A.plan.pginfo + d.pw[0], (uint32_t)d.ngroups * 16u,
-                                      &S.full[slot]);
+                        const int g0 = ra & ~1;
+                        const int gcnt = ((ra + nr + 1) & ~1) - g0;
+                        const uint32_t abytes = (uint32_t)nr * 16u, gbytes = (uint32_t)gcnt * 8u;
+                        const uint32_t cbytes = s == 0 ? (uint32_t)IC * 12u : 0u;
+                        mbar_expect(&S.full[slot], (uint32_t)__popc(need) * ROW_BYTES + abytes + gbytes + cbytes);
+                        bulk_copy(S.rowA[slot], A.rowA + ra, abytes, &S.full[slot]);
+                        bulk_copy(S.rowG[slot], A.rowg + g0, gbytes, &S.full[slot]);
+                        if (s == 0) {
+                            bulk_copy(S.colB[slot], A.B2 + col0, IC * 8u, &S.full[slot]);
+                            bulk_copy(S.colP[slot], A.Bp + col0, IC * 4u, &S.full[slot]);
+                        }
                         StageHdr& hh = S.hdr[slot];
-                        hh.d = d;
-                        hh.tile = jt; hh.sidx = si; hh.nst = tst; hh.flags = flags; hh.a_shift = a_sh;
-                        if (d.kind == 0 && !A.unit_need) tma_rows(T, dst, col, d.r0, d.rows, &S.full[slot]);
-                        if (d.kind == 1 && rows > 0) tma_rows(T, dst, col, ra, rows, &S.full[slot]);
-                    }
-                    if (d.kind == 0 && A.unit_need) {
-                        __syncwarp();
-                        for (int gi = d.pw[0] + lane; gi < d.pw[NWARPS]; gi += 32) {
-                            const int4 g4 = __ldg(A.plan.pginfo + gi);
-                            if (!(unit_bit(A.unit_need, A.unit_words, g4.x, jt) ||
-                                  (two && unit_bit(A.unit_need, A.unit_words, g4.x, jt + 1))))
-                                continue;
-                            tma_rows(T, dst + (g4.y - d.r0) * SC, col, g4.y, g4.z, &S.full[slot]);
+                        hh.sidx = s;
+                        hh.flags = (s == 0 ? H_FIRST : 0) | (s == nst - 1 ? H_LAST : 0);
+                        hh.g_shift = ra - g0;
+                        // one run of consecutive needed rows at a time
+                        uint32_t rem = need;
+                        while (rem) {
+                            const int a = __ffs(rem) - 1;
+                            const uint32_t x = rem >> a;
+                            const int len = x == FULLMASK ? 32 : __ffs(~x) - 1;
+                            tma_rows(T, S.stage[slot] + a * IC, col0, ra + a, len, &S.full[slot]);
+                            rem &= a + len >= 32 ? 0u : ~((1u << (a + len)) - 1u);
                         }
                     }
                     __syncwarp();
@@ -470,6 +422,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
                 }
             }
             if (!ok) break;
+            i0 = i1; w0 = w1; a0 = a1;
+            i1 = i2; w1 = w2;
+            i2r = i3r;
         }
         if (!ok) {
             if (lane == 0) atomicOr(A.err, 1);
@@ -481,17 +436,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
     }
 
     // ----------------------------------------------------------- consumers
-    uint32_t cphase = 0;
-#define CSYNC()                                    \
-    do {                                           \
-        if (!consumer_sync(S, cphase)) {           \
-            if (lane == 0) atomicOr(A.err, 8);     \
-            return;                                \
-        }                                          \
-    } while (0)
+    const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);
+    const int wc = warp * TW + lane;  // this lane's column within an item
     long long consumed = 0;
-    double psi_acc = 0.0;
-    int gk0 = 0, gk1 = 0;  // small item: this warp's groups are ginfo[gk0, gk1)
+    // item state
+    float bh = 0.f, bl = 0.f, bp = -INFINITY;
+    int colg = 0;
+    double psi_acc = 0.0, cacc = 0.0;
+    // block state
+    int gl = 0, gend = 0, gstart = 0;
+    bool need = false, any = false;
+    Acc acc = {0.f, 0.f, 0.f, 0.f};
+    float O = 0.f;
     for (;;) {
         const int slot = (int)(consumed % NSTAGES);
         if (!mbar_wait(&S.full[slot], (uint32_t)((consumed / NSTAGES) & 1))) {
@@ -501,232 +457,83 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
         const StageHdr& hs = S.hdr[slot];
         const int flags = hs.flags;
         if (flags & H_TERM) return;
-        const int item = hs.d.item, jt = hs.tile, p = hs.d.p, kind = hs.d.kind;
-        const int col0 = hs.d.col0, ncols = hs.d.ncols;
-        const int64_t rbase = (int64_t)(((uint64_t)(uint32_t)hs.d.rb_hi << 32) | (uint32_t)hs.d.rb_lo);
-        const int c0 = jt * TW + lane, c1 = c0 + TW;  // this lane's columns
-        const bool two = jt + 1 < hs.d.t0 + hs.d.nt;
-        const Col2 cl = load_cols(S, slot, lane);
-        if (kind == 0) {
-            // ---------------- small panel: a contiguous run of whole groups per warp
-            const int rows = hs.d.rows;
-            if (flags & H_FIRST) {
-                const int ng = hs.d.ngroups;
-                for (int k = threadIdx.x; k < ng; k += CONSUMERS * 32) S.ginfo[k] = S.gstage[slot][k];
-                for (int i = threadIdx.x; i < rows; i += CONSUMERS * 32) S.rowacc[i] = 0.f;
-                gk0 = hs.d.pw[warp] - hs.d.pw[0];
-                gk1 = hs.d.pw[warp + 1] - hs.d.pw[0];
-                psi_acc = 0.0;
-                CSYNC();
-            }
-            const float* st = S.stage[slot];
-            const float2* ar = S.arow[slot] + hs.a_shift;
-            float cacc0 = 0.f, cacc1 = 0.f;
-            for (int k = gk0; k < gk1; k++) {
-                const int4 gi4 = S.ginfo[k];
-                const int l = gi4.x, g = gi4.z, sr = gi4.w;
-                if (A.unit_need && !(unit_bit(A.unit_need, A.unit_words, l, jt) ||
-                                     (two && unit_bit(A.unit_need, A.unit_words, l, jt + 1))))
-                    continue;
-                Acc a0 = {0.f, 0.f, 0.f, 0.f}, a1 = {0.f, 0.f, 0.f, 0.f};
-                float O0 = 0.f, O1 = 0.f;
-                bool any = false;
-#pragma unroll 2
-                for (int r = sr; r < sr + g; r++)
-                    any |= row_a<SNAP>(ar[r], st[r * SC + lane], st[r * SC + lane + 32], cl, a0, a1, O0, O1);
-                float s0 = 0.f, s1 = 0.f;
-                if (__any_sync(FULLMASK, any)) {
-                    double p0, p1;
-                    s0 = block_scale(a0.Sh, a0.Sl, A, p0);
-                    s1 = block_scale(a1.Sh, a1.Sl, A, p1);
-                    psi_acc += p0 + p1;
-                    cacc0 = fmaf(s0, __fadd_rn(a0.Ph, a0.Pl), cacc0);
-                    cacc1 = fmaf(s1, __fadd_rn(a1.Ph, a1.Pl), cacc1);
-                }
-                if (SNAP) {
-                    put_snap(A, l, c0, z_up(a0.Sh, a0.Sl), __fsqrt_ru(O0));
-                    if (two) put_snap(A, l, c1, z_up(a1.Sh, a1.Sl), __fsqrt_ru(O1));
-                }
-                if (__any_sync(FULLMASK, s0 > 0.f || s1 > 0.f)) {
-                    for (int r = sr; r < sr + g; r++) {
-                        const float rs = warp_sum(row_b(ar[r], st[r * SC + lane], st[r * SC + lane + 32], cl, s0, s1));
-                        if (lane == 0) S.rowacc[r] += rs;
-                    }
-                }
-            }
-            S.colacc[warp][jt * TW - col0 + lane] = cacc0;
-            S.colacc[warp][jt * TW - col0 + lane + TW] = cacc1;
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.empty[slot]);
-            consumed++;
-            if (flags & H_LAST) {
-#pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) psi_acc += __shfl_xor_sync(FULLMASK, psi_acc, off);
-                if (lane == 0) S.psi_w[warp] = psi_acc;
-                CSYNC();
-                const int tid = threadIdx.x;
-                for (int i = tid; i < rows; i += CONSUMERS * 32) A.rowpart[rbase + i] = (double)S.rowacc[i];
-                for (int c = tid; c < ncols; c += CONSUMERS * 32) {
-                    double v = 0.0;
-#pragma unroll
-                    for (int w = 0; w < CONSUMERS; w++) v += (double)S.colacc[w][c];
-                    A.colpart[(int64_t)p * A.n + col0 + c] = v;
-                }
-                if (tid == 0) {
-                    double v = 0.0;
-                    for (int w = 0; w < CONSUMERS; w++) v += S.psi_w[w];
-                    A.psipart[item] = v;
-                }
-                CSYNC();
-            }
-            continue;
-        }
-        // ---------------- big group: this tile pair spans nst stages
-        const int l = hs.d.l, r0 = hs.d.r0, g = hs.d.rows;
-        const int nst = hs.nst;
-        const bool held = (flags & H_BIG_HELD) != 0;
-        const bool need = !(flags & H_SKIP);
-        const bool racc_smem = g <= BIG_SMEM_ROWS;
-        double* racc_g = A.rowpart + rbase;
-        const int wr0 = warp * WROWS;  // this warp's rows of each stage: [wr0, wr0 + WROWS)
+        const int r0 = hs.d.r0, rows = hs.d.rows, sidx = hs.sidx;
         if (flags & H_FIRST) {
-            for (int sb = 0; sb < g; sb += STAGE_ROWS)
-                if (lane < WROWS) {
-                    const int R = sb + wr0 + lane;
-                    if (R < g) {
-                        if (racc_smem) S.rowacc[R] = 0.f;
-                        else racc_g[R] = 0.0;
-                    }
-                }
+            const float2 b2 = S.colB[slot][wc];
+            bh = b2.x;
+            bl = b2.y;
+            bp = S.colP[slot][wc];
+            colg = hs.d.col0 + wc;
             psi_acc = 0.0;
-            __syncwarp();
+            cacc = 0.0;
+            gend = r0;  // the item's first row opens a block
         }
-        Acc a0 = {0.f, 0.f, 0.f, 0.f}, a1 = {0.f, 0.f, 0.f, 0.f};
-        float O0 = 0.f, O1 = 0.f;
-        bool any = false;
-        const long long pair_first = consumed;  // stage index of this pair's first stage
-        if (need) {
-            for (int si = 0; si < nst; si++) {
-                const int sl = (int)(consumed % NSTAGES);
-                if (si > 0 && !mbar_wait(&S.full[sl], (uint32_t)((consumed / NSTAGES) & 1))) {
-                    if (lane == 0) atomicOr(A.err, 4);
-                    return;
-                }
-                const float* st = S.stage[sl];
-                const float2* ar = S.arow[sl] + S.hdr[sl].a_shift;
-                const int rows = min(STAGE_ROWS, g - si * STAGE_ROWS);
-                const int rend = min(wr0 + WROWS, rows);
-#pragma unroll 2
-                for (int r = wr0; r < rend; r++)
-                    any |= row_a<SNAP>(ar[r], st[r * SC + lane], st[r * SC + lane + 32], cl, a0, a1, O0, O1);
-                if (!held) {
-                    __syncwarp();
-                    if (lane == 0) mbar_arrive(&S.empty[sl]);
-                }
-                consumed++;
+        const int ra = r0 + sidx * SR, nr = min(SR, rows - sidx * SR);
+        const float* st = S.stage[slot] + wc;
+        const float4* rA = S.rowA[slot];
+        const int2* rG = S.rowG[slot] + hs.g_shift;
+        int r = 0;
+        while (r < nr) {
+            if (ra + r == gend) {  // a new group starts at row r
+                const int2 g2 = rG[r];
+                gl = g2.x;
+                gend = g2.y;
+                gstart = ra + r;
+                acc = Acc{0.f, 0.f, 0.f, 0.f};
+                O = 0.f;
+                any = false;
+                need = !A.unit_need || ((S.rmask[slot][r] >> warp) & 1u);
             }
-        } else {
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&S.empty[slot]);
-            consumed++;
-        }
-        S.red[warp][lane] = make_float4(a0.Sh, a0.Sl, a0.Ph, a0.Pl);
-        S.red[warp][lane + 32] = make_float4(a1.Sh, a1.Sl, a1.Ph, a1.Pl);
-        if (SNAP) {
-            S.redO[warp][lane] = O0;
-            S.redO[warp][lane + 32] = O1;
-        }
-        const bool wany = __any_sync(FULLMASK, any);
-        if (lane == 0) S.anyw[warp] = wany ? 1 : 0;
-        CSYNC();
-        bool cany = false;
-#pragma unroll
-        for (int w = 0; w < CONSUMERS; w++) cany |= S.anyw[w] != 0;
-        // every warp combines the partials of its two columns in warp order
-        float s[2] = {0.f, 0.f};
-#pragma unroll
-        for (int h = 0; h < 2; h++) {
-            const int c = lane + h * TW, col = jt * TW + c;
-            float zt = 0.f, ot = 0.f;
-            if (SNAP) {
-                float o = S.redO[0][c];
-                for (int w = 1; w < CONSUMERS; w++) o += S.redO[w][c];
-                ot = __fsqrt_ru(o);
-            }
-            float sc = 0.f, pp = 0.f;
-            if (cany) {
-                const float4 v = S.red[0][c];
-                float hh = v.x, hl = v.y, ph = v.z, pl = v.w;
-                for (int w = 1; w < CONSUMERS; w++) {
-                    const float4 u = S.red[w][c];
-                    df_add(hh, hl, u.x, u.y);
-                    df_add(ph, pl, u.z, u.w);
-                }
+            const int e = min(gend - ra, nr);
+            if (need) scan_rows<SNAP>(st, rA, r, e, bh, bl, bp, acc, O, any);
+            r = e;
+            if (ra + r != gend || !need) continue;
+            // ---- the block (gl, colg) is complete
+            float s = 0.f;
+            if (__any_sync(FULLMASK, any)) {
                 double psi;
-                sc = block_scale(hh, hl, A, psi);
-                if (warp == 0) psi_acc += psi;
-                zt = z_up(hh, hl);
-                pp = __fadd_rn(ph, pl);
+                s = block_scale(acc.Sh, acc.Sl, A, psi);
+                psi_acc += psi;
+                if (s > 0.f) cacc += (double)s * ((double)acc.Ph + (double)acc.Pl);
             }
-            s[h] = sc;
-            if (warp == 0 && (h == 0 || two) && col < A.n) {
-                A.colpart[(int64_t)p * A.n + col] = (double)__fmul_rn(sc, pp);
-                if (SNAP && need) put_snap(A, l, col, zt, ot);
-            }
-        }
-        CSYNC();  // red / anyw free for the next pair
-        if (__any_sync(FULLMASK, s[0] > 0.f || s[1] > 0.f)) {
-            for (int si = 0; si < nst; si++) {
-                const int rows = min(STAGE_ROWS, g - si * STAGE_ROWS);
-                const int rend = min(wr0 + WROWS, rows);
-                if (held) {
-                    const int hsl = (int)((pair_first + si) % NSTAGES);
-                    const float* st = S.stage[hsl];
-                    const float2* ar = S.arow[hsl] + S.hdr[hsl].a_shift;
-                    for (int r = wr0; r < rend; r++) {
-                        const float rs = warp_sum(row_b(ar[r], st[r * SC + lane], st[r * SC + lane + 32], cl, s[0], s[1]));
-                        if (lane == 0) {
-                            const int R = si * STAGE_ROWS + r;
-                            if (racc_smem) S.rowacc[R] += rs;
-                            else racc_g[R] += (double)rs;
-                        }
+            if (SNAP) put_snap(A, gl, colg, z_up(acc.Sh, acc.Sl), __fsqrt_ru(O));
+            if (__any_sync(FULLMASK, s > 0.f)) {
+                // pass B: t_ij = s [f_ij]_+ into the row sums
+                for (int R = gstart; R < gend; R++) {
+                    float c;
+                    float4 a;
+                    if (R >= ra) {
+                        c = st[(R - ra) * IC];
+                        a = rA[R - ra];
+                    } else {  // the row's stage has left the ring: re-read it (from L2)
+                        c = colg < A.n ? __ldg(A.C + (int64_t)R * A.ldc + colg) : 0.f;
+                        a = __ldg(A.rowA + R);
                     }
-                } else {
-                    // the stage has left the ring: re-read its rows from L2
-                    for (int r = wr0; r < rend; r++) {
-                        const int R = si * STAGE_ROWS + r;
-                        const float* rowp = A.C + (int64_t)(r0 + R) * A.ldc;
-                        const float x0 = c0 < A.n ? __ldg(rowp + c0) : 0.f;
-                        const float x1 = c1 < A.n ? __ldg(rowp + c1) : 0.f;
-                        const float rs = warp_sum(row_b(__ldg(A.A2 + r0 + R), x0, x1, cl, s[0], s[1]));
-                        if (lane == 0) {
-                            if (racc_smem) S.rowacc[R] += rs;
-                            else racc_g[R] += (double)rs;
-                        }
+                    float t = 0.f;
+                    if (s > 0.f && maybe_pos(a.z, c, bp)) {
+                        float fh, fl;
+                        f_exact(a.x, a.y, bh, bl, c, fh, fl);
+                        if (fh > 0.f) t = __fmul_rn(s, fh);
+                    }
+                    if (__any_sync(FULLMASK, t != 0.f)) {
+                        const float rs = warp_sum(t);
+                        if (lane == 0) red_fx(A.rowfx + R, (double)rs, fx.to_r);
                     }
                 }
             }
-        }
-        if (held && need) {
-            __syncwarp();
-            if (lane == 0)
-                for (int si = 0; si < nst; si++) mbar_arrive(&S.empty[(int)((pair_first + si) % NSTAGES)]);
         }
         if (flags & H_LAST) {
-            if (warp == 0) {
+            double v = psi_acc;
 #pragma unroll
-                for (int off = 16; off >= 1; off >>= 1) psi_acc += __shfl_xor_sync(FULLMASK, psi_acc, off);
-                if (lane == 0) A.psipart[item] = psi_acc;
-            }
-            CSYNC();
-            if (racc_smem)
-                for (int i = threadIdx.x; i < g; i += CONSUMERS * 32) A.rowpart[rbase + i] = (double)S.rowacc[i];
-            CSYNC();
+            for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
+            if (lane == 0) A.psipart[(int64_t)hs.d.item * NWARPS + warp] = v;
+            if (colg < A.n && cacc != 0.0) red_fx(A.colfx + colg, cacc, fx.to_c);
         }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&S.empty[slot]);
+        consumed++;
     }
 }
-
-#undef CSYNC
 
 size_t stream_smem_bytes() { return sizeof(Smem) + 1024; }
 
@@ -772,7 +579,7 @@ std::string make_tmaps(const float* C, int64_t ldc, int64_t m, int64_t n, TmaMap
     const cuuint64_t strides[1] = {(cuuint64_t)ldc * sizeof(float)};
     const cuuint32_t estr[2] = {1, 1};
     for (int k = 0; k < TMA_BOXES; k++) {
-        const cuuint32_t box[2] = {(cuuint32_t)SC, 1u << k};
+        const cuuint32_t box[2] = {(cuuint32_t)IC, 1u << k};
         CUresult r = enc(&T.box[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(C), dims, strides, box, estr,
                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);

@@ -26,27 +26,54 @@ def test_create_rejects_null_without_gpu():
     assert "NULL" in pk.ot_gs_last_error(None)
 
 
+PANEL_ROWS, ITEM_COLS, STAGE_ROWS = 512, 256, 32
+
+
+def expected_plan(sizes, n):
+    """Panels by the packing rule of the plan (consecutive non-empty groups up
+    to PANEL_ROWS rows; a larger group alone), items and stages from them."""
+    panels, cur = [], 0
+    for g in sizes:
+        if g == 0:
+            continue
+        if cur and cur + g > PANEL_ROWS:
+            panels.append(cur)
+            cur = 0
+        cur += g
+        if cur >= PANEL_ROWS:
+            panels.append(cur)
+            cur = 0
+    if cur:
+        panels.append(cur)
+    nch = -(-n // ITEM_COLS)
+    return len(panels), len(panels) * nch, sum(-(-r // STAGE_ROWS) for r in panels) * nch, panels
+
+
 @pytest.mark.parametrize("sizes,n", [
-    ([20] * 10, 200),                 # tiny: equal small groups
-    ([1, 2, 3, 70, 5, 4100, 0, 9], 77),  # small + big + giant + empty, ragged n
-    ([64, 65, 1], 33),                # boundary of the small/big split
+    ([20] * 10, 200),                        # tiny: equal small groups, one ragged chunk
+    ([1, 2, 3, 70, 5, 4100, 0, 9], 77),      # small + giant + empty, ragged n
+    ([512, 511, 1, 513, 2, 510], 257),       # panel-size boundaries, two chunks (one of 1 column)
+    ([3] * 400, 1000),                       # many tiny groups: panels close on rows
 ])
 def test_plan_covers_rows(sizes, n):
     lab = synth.labels_from_sizes(np.array(sizes))
     info = pk.ot_gs_plan_info(lab, n, len(sizes))
-    assert info["n_panels"] >= 1 and info["n_items"] >= info["n_panels"]
-    # every non-empty row appears in exactly one panel per column chunk:
-    # rowpart length = sum over panels of rows * chunks, bounded by m * n / 32
-    m = len(lab)
-    assert m <= info["rowpart_len"] <= m * ((n + 31) // 32)
+    n_panels, n_items, n_stages, panels = expected_plan(sizes, n)
+    assert sum(panels) == len(lab)  # every row in exactly one panel
+    assert (info["n_panels"], info["n_items"], info["n_stages"]) == (n_panels, n_items, n_stages)
 
 
 def test_plan_zipf_large_shape():
     sizes = synth.class_sizes_zipf(20000, 1000, 1.1, 2)
     lab = synth.labels_from_sizes(sizes)
     info = pk.ot_gs_plan_info(lab, 20000, 1000)
-    assert 50 < info["n_panels"] < 400
-    assert info["n_items"] > 1000
+    n_panels, n_items, n_stages, _ = expected_plan(list(sizes), 20000)
+    assert (info["n_panels"], info["n_items"], info["n_stages"]) == (n_panels, n_items, n_stages)
+    assert int((np.asarray(sizes) > PANEL_ROWS).sum()) < info["n_panels"] < 200
+    # streaming one evaluation touches every row once per column chunk, in
+    # 32-row stages: at most one partial stage per panel and chunk
+    nch = -(-20000 // ITEM_COLS)
+    assert info["n_stages"] <= (20000 // STAGE_ROWS + info["n_panels"]) * nch
 
 
 def test_plan_rejects_bad_labels():

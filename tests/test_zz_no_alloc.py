@@ -49,7 +49,8 @@ def test_noalloc_matches_handle_twice(mk, gamma, mu):
 
 def test_noalloc_rejects_oversized_problem_before_gpu_work():
     """The size check runs on the host before any CUDA call."""
-    m, n, L = 40000, 40000, 1000
+    # scratch is about 44 B per row: two million rows do not fit in 64 MB
+    m, n, L = 2_000_000, 1000, 1000
     lab = synth.labels_from_sizes(synth.class_sizes_zipf(m, L, 1.1, 2))
     rc = pk.lib().ot_gs_grad_noalloc(ctypes.c_void_p(16), n, ctypes.c_void_p(16), ctypes.c_void_p(16),
                                      lab.ctypes.data_as(ctypes.c_void_p), m, n, L, 1.0, 0.5,
