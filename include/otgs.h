@@ -175,6 +175,16 @@ OTGS_API int ot_gs_solve(ot_gs *h, double tol, int32_t maxit);
 OTGS_API int ot_gs_get_solution(ot_gs *h, double *alpha, double *beta, double *D, double *grad_inf,
                        int32_t *iters);
 
+/*
+ * Objective trace of the last ot_gs_solve: entry 0 is the start point, entry
+ * k the k-th accepted iteration.  D[k] is the dual objective there, t_ms[k]
+ * the device time (globaltimer) since the solve was launched, including the
+ * host round trips of the line search, evals[k] the evaluations so far.  Up
+ * to cap entries are written to the HOST arrays; *count (may be NULL) gets
+ * the number recorded (at most 65536).  Synchronises.
+ */
+OTGS_API int ot_gs_get_trace(ot_gs *h, double *D, double *t_ms, int64_t *evals, int32_t cap, int32_t *count);
+
 /* Set the iterate used by the next ot_gs_solve (warm start or resume) and
  * clear the L-BFGS memory.  alpha, beta: device FP64 [m], [n], caller order. */
 OTGS_API int ot_gs_set_state(ot_gs *h, const double *alpha, const double *beta);

@@ -77,6 +77,7 @@ def lib():
         "ot_gs_solve": ([P, dbl, i32], ctypes.c_int),
         "ot_gs_get_solution": ([P, P, P, P, P, P], ctypes.c_int),
         "ot_gs_set_state": ([P, P, P], ctypes.c_int),
+        "ot_gs_get_trace": ([P, P, P, P, i32, P], ctypes.c_int),
         "ot_gs_get_stats": ([P, ctypes.POINTER(Stats)], ctypes.c_int),
         "ot_gs_reset_stats": ([P], ctypes.c_int),
         "ot_gs_set_timing": ([P, ctypes.c_int], ctypes.c_int),
@@ -219,6 +220,20 @@ def ot_gs_get_solution(h, alpha, beta):
     return D.value, gi.value, it.value
 
 
+def ot_gs_get_trace(h):
+    """Objective trace of the last solve: (D, t_ms, evals) numpy arrays, entry
+    0 the start point and entry k the k-th accepted iteration; t_ms is device
+    time since the solve was launched."""
+    cnt = ctypes.c_int32()
+    _check(h, lib().ot_gs_get_trace(h, None, None, None, 0, ctypes.byref(cnt)))
+    k = cnt.value
+    D, t, ev = np.empty(k), np.empty(k), np.empty(k, dtype=np.int64)
+    if k:
+        _check(h, lib().ot_gs_get_trace(h, D.ctypes.data_as(ctypes.c_void_p), t.ctypes.data_as(ctypes.c_void_p),
+                                        ev.ctypes.data_as(ctypes.c_void_p), k, ctypes.byref(cnt)))
+    return D, t, ev
+
+
 def ot_gs_set_state(h, alpha, beta):
     import torch
     return _check(h, lib().ot_gs_set_state(h, _ptr(alpha, torch.float64, name="alpha"),
@@ -347,6 +362,9 @@ class GroupSparseOT:
 
     def set_state(self, alpha, beta):
         ot_gs_set_state(self.h, alpha, beta)
+
+    def trace(self):
+        return ot_gs_get_trace(self.h)
 
     def stats(self):
         return ot_gs_get_stats(self.h)

@@ -266,7 +266,7 @@ bool Handle::eval_dense_prepped(const double* beta, double* G_sorted, const doub
 bool Handle::eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap)
 {
     EvalArgs e = eval_args(nullptr, nullptr, snap);
-    eval_launch(e, std::min(n_sm, hp.nitems()));
+    eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(nullptr, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     stats_host.evals++;

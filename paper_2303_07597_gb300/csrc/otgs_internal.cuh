@@ -23,9 +23,11 @@ constexpr int TW = 32;
 constexpr int NWARPS = 8;
 constexpr int ITEM_COLS = NWARPS * TW;  // columns of a work item: 1 KB of each row of C
 // C streams through a ring of NSTAGES shared-memory stages of STAGE_ROWS rows
-// x ITEM_COLS columns (32 KB), loaded by 2D TMA boxes.
+// x ITEM_COLS columns (32 KB) per CTA, loaded by 2D TMA boxes.
 constexpr int STAGE_ROWS = 32;
-constexpr int NSTAGES = 6;
+constexpr int NSTAGES = 3;
+// CTAs of the evaluation kernel per SM (each with its own ring).
+constexpr int CTAS_PER_SM = 2;
 // Consecutive groups are packed into "panels" of whole groups up to
 // PANEL_ROWS rows; a larger group is a panel of its own.  A work item is
 // (panel, column chunk of ITEM_COLS).
@@ -94,7 +96,7 @@ struct HostPlan {
     std::vector<int32_t> perm;    // sorted r -> caller row
     std::vector<int32_t> goff;    // L+1 offsets (sorted rows)
     std::vector<int32_t> rgroup;  // sorted r -> group
-    std::vector<int2> rowg;       // sorted r -> {group, end of the group}; 2 padding entries
+    std::vector<int4> rowg;       // sorted r -> {group, first row, end row of the group, 0}
     // panels: row ranges of whole groups
     std::vector<int32_t> prow0;   // first sorted row
     std::vector<int32_t> prows;   // rows
@@ -118,7 +120,7 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
 // ---------------------------------------------------------------- device plan
 struct DevPlan {
     int32_t *perm, *goff, *rgroup;
-    int2* rowg;
+    int4* rowg;
     int32_t *prows, *pW, *pnch, *pitem, *gpanel;
     int32_t *item_panel, *item_chunk, *exec_order;
     ItemDesc* desc;
@@ -190,7 +192,7 @@ struct EvalArgs {
     int64_t ldc;
     int32_t m, n, L, ntiles, nitems;
     const float4* rowA;  // sorted rows: (alpha hi, alpha lo, bound_up(alpha hi), 0)
-    const int2* rowg;    // sorted rows: (group, end of group); 2 padding entries
+    const int4* rowg;    // sorted rows: (group, first row, end row of the group, 0)
     const float2* B2;    // columns padded to padded_cols(n): (hi, lo) split of beta
     const float* Bp;     // bound_up(beta hi) per column, -inf in the padding
     EvalCtl* ctl;

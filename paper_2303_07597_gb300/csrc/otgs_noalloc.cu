@@ -88,7 +88,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const int ntiles = hp.ntiles;
     // layout of the scratch array
     Carve cv;
-    const size_t o_perm = cv.take(4 * hp.perm.size()), o_rowg = cv.take(sizeof(int2) * hp.rowg.size());
+    const size_t o_perm = cv.take(4 * hp.perm.size()), o_rowg = cv.take(sizeof(int4) * hp.rowg.size());
     const size_t o_desc = cv.take(sizeof(ItemDesc) * hp.desc.size());
     const size_t o_rowA = cv.take(sizeof(float4) * (size_t)m);
     const size_t o_B2 = cv.take(8 * (size_t)padded_cols(n)), o_Bp = cv.take(4 * (size_t)padded_cols(n));
@@ -124,7 +124,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
         return bytes == 0 ? cudaSuccess : cudaMemcpyAsync(base + off, src, bytes, cudaMemcpyHostToDevice, st);
     };
     e = up(o_perm, hp.perm.data(), 4 * hp.perm.size());
-    if (e == cudaSuccess) e = up(o_rowg, hp.rowg.data(), sizeof(int2) * hp.rowg.size());
+    if (e == cudaSuccess) e = up(o_rowg, hp.rowg.data(), sizeof(int4) * hp.rowg.size());
     if (e == cudaSuccess) e = up(o_desc, hp.desc.data(), sizeof(ItemDesc) * hp.desc.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_counter, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_err, 0, 16, st);
@@ -146,7 +146,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     ea.C = C; ea.ldc = ldc;
     ea.m = (int32_t)m; ea.n = (int32_t)n; ea.L = L; ea.ntiles = ntiles;
     ea.nitems = hp.nitems();
-    ea.rowA = rowA; ea.rowg = (const int2*)(base + o_rowg);
+    ea.rowA = rowA; ea.rowg = (const int4*)(base + o_rowg);
     ea.B2 = B2; ea.Bp = Bp;
     ea.ctl = ctl; ea.err = (int*)(base + o_err);
     ea.nlist = hp.nitems();
@@ -169,7 +169,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
         const std::string te = make_tmaps(C, ldc, m, n, tm);
         if (!te.empty()) return set_err(OTGS_ECUDA, te);
     }
-    launch_stream(ea, tm, n_sm < hp.nitems() ? n_sm : hp.nitems(), st);
+    launch_stream(ea, tm, std::min(CTAS_PER_SM * n_sm, hp.nitems()), st);
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.m = (int32_t)m; ra.n = (int32_t)n; ra.nitems = hp.nitems();

@@ -38,13 +38,12 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
         std::vector<int32_t> fill(hp.goff.begin(), hp.goff.end() - 1);
         for (int64_t i = 0; i < m; i++) hp.perm[fill[labels[i]]++] = (int32_t)i;
     }
-    hp.rowg.resize(m + 2);
+    hp.rowg.resize(m);
     for (int32_t l = 0; l < L; l++)
         for (int32_t r = hp.goff[l]; r < hp.goff[l + 1]; r++) {
             hp.rgroup[r] = l;
-            hp.rowg[r] = make_int2(l, hp.goff[l + 1]);
+            hp.rowg[r] = make_int4(l, hp.goff[l], hp.goff[l + 1], 0);
         }
-    hp.rowg[m] = hp.rowg[m + 1] = make_int2(-1, (int32_t)m);
 
     // panels: runs of consecutive non-empty groups in label order, closed
     // before they would exceed PANEL_ROWS rows

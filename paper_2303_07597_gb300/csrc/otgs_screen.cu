@@ -329,7 +329,7 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     const int64_t units = (int64_t)L * ntiles;
     k_screen<<<(unsigned)((units + 7) / 8), 256, 0, st>>>(s);
     EvalArgs e = eval_args(item_active, unit_need, false);
-    eval_launch(e, std::min(n_sm, hp.nitems()));
+    eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     stats_host.evals++;

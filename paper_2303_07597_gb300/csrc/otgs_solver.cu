@@ -71,6 +71,17 @@ __device__ __forceinline__ unsigned long long gtimer()
     return t;
 }
 
+// Entry iter of the objective trace: D = -F, device time since the launch of
+// the solve, evaluations so far.
+__device__ __forceinline__ void trace_put(SolverState* S, double F)
+{
+    if (!S->trace || S->iter >= S->trace_cap) return;
+    double* e = S->trace + 3 * (size_t)S->iter;
+    e[0] = -F;
+    e[1] = (double)(gtimer() - S->t_begin) * 1e-6;
+    e[2] = (double)S->evals;
+}
+
 // Line-search state machine (same rule as the oracle): scal = {D, Gt.d, ||Gt||_inf}.
 __global__ void k_linesearch(SolverState* S, const double* scal)
 {
@@ -106,6 +117,7 @@ __global__ void k_linesearch(SolverState* S, const double* scal)
         S->F = F;
         S->ginf = scal[2];
         S->iter++;
+        trace_put(S, F);
         if (S->ginf <= S->tol) {
             S->status = OTGS_OK;
             S->done = 1;
@@ -319,7 +331,10 @@ __global__ void k_start(SolverState* S, const double* scal)
         S->done = 1;
     }
     S->t_start = gtimer();
+    trace_put(S, S->F);
 }
+
+__global__ void k_begin(SolverState* S) { S->t_begin = gtimer(); }
 
 // ------------------------------------------------------------------- host
 bool Solver::init(Handle* h_)
@@ -339,11 +354,12 @@ bool Solver::init(Handle* h_)
     Yv = (double*)al(sizeof(double) * (size_t)N * M, "Y");
     pbase = (double*)al(sizeof(double) * (size_t)nblk * NBASE, "dot partials");
     ppair = (double*)al(sizeof(double) * (size_t)nblk * M * NPAIR, "pair dot partials");
+    trace = (double*)al(sizeof(double) * 3 * (size_t)TRACE_CAP, "objective trace");
     if (cudaMallocHost(&hstate, sizeof(SolverState)) != cudaSuccess) {
         hstate = nullptr;
         return h->fail(OTGS_ENOMEM, "cudaMallocHost(solver state)");
     }
-    if (!state || !x || !G || !d || !xt || !Gt || !Sv || !Yv || !pbase || !ppair) return false;
+    if (!state || !x || !G || !d || !xt || !Gt || !Sv || !Yv || !pbase || !ppair || !trace) return false;
     cudaMemsetAsync(x, 0, sizeof(double) * N, h->st);
     cudaMemsetAsync(Sv, 0, sizeof(double) * (size_t)N * M, h->st);
     cudaMemsetAsync(Yv, 0, sizeof(double) * (size_t)N * M, h->st);
@@ -369,7 +385,11 @@ int Solver::run(double tol, int maxit)
     init.npairs = 0;
     init.head = 0;
     init.status = OTGS_ENOTCONV;
+    init.trace = trace;
+    init.trace_cap = TRACE_CAP;
+    trace_len = 0;
     if (!h->ck(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st), "state H2D")) return h->last_code;
+    k_begin<<<1, 1, 0, st>>>(state);
     // Alg. 1 line 1: snapshot at the start point, N empty
     if (h->prm.use_screening) {
         h->invalidate_screen();
@@ -419,6 +439,7 @@ int Solver::run(double tol, int maxit)
         !h->ck(cudaStreamSynchronize(st), "solver sync"))
         return h->last_code;
     h->stats_host.iters = hstate->iter;
+    trace_len = std::min(hstate->iter + 1, TRACE_CAP);
     iters = hstate->iter;
     D = -hstate->F;
     ginf = hstate->ginf;
@@ -473,6 +494,29 @@ int ot_gs_get_solution(ot_gs* hh, double* alpha, double* beta, double* D, double
     if (D) *D = s->D;
     if (grad_inf) *grad_inf = s->ginf;
     if (iters) *iters = s->iters;
+    return OTGS_OK;
+}
+
+int ot_gs_get_trace(ot_gs* hh, double* D, double* t_ms, int64_t* evals, int32_t cap, int32_t* count)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!h->solver) { h->fail(OTGS_EINVAL, "no solve yet"); return OTGS_EINVAL; }
+    if (cap < 0 || (cap > 0 && (!D || !t_ms || !evals))) { h->fail(OTGS_EINVAL, "bad trace buffers"); return OTGS_EINVAL; }
+    Solver* s = h->solver;
+    const int k = std::min<int>(cap, s->trace_len);
+    if (count) *count = s->trace_len;
+    if (k == 0) return OTGS_OK;
+    std::vector<double> buf(3 * (size_t)k);
+    if (!h->ck(cudaMemcpyAsync(buf.data(), s->trace, sizeof(double) * buf.size(), cudaMemcpyDeviceToHost, h->st),
+               "trace D2H") ||
+        !h->ck(cudaStreamSynchronize(h->st), "sync"))
+        return OTGS_ECUDA;
+    for (int i = 0; i < k; i++) {
+        D[i] = buf[3 * i];
+        t_ms[i] = buf[3 * i + 1];
+        evals[i] = (int64_t)buf[3 * i + 2];
+    }
     return OTGS_OK;
 }
 

@@ -7,6 +7,7 @@ namespace otgs {
 
 constexpr int MAX_LBFGS_M = 32;
 constexpr int SOLVER_THREADS = 256;
+constexpr int TRACE_CAP = 1 << 16;  // objective trace entries kept per solve
 // line search (same constants as the oracle)
 constexpr double LS_C1 = 1e-4;
 constexpr double LS_C2 = 0.9;
@@ -24,6 +25,10 @@ struct SolverState {
     double tol, t, lo, Flo, dlo, hi, Fhi, dhi;
     double F, F0, dphi0, ginf, cG, budget_ns;
     unsigned long long t_start;
+    unsigned long long t_begin;  // globaltimer when the solve was launched
+    double* trace;               // [trace_cap][3]: D, ms since t_begin, evaluations
+    int trace_cap;
+    int pad_trace;
     double SY[MAX_LBFGS_M * MAX_LBFGS_M];  // SY[i*M + k] = s_i . y_k
     double YY[MAX_LBFGS_M * MAX_LBFGS_M];
     double cy[MAX_LBFGS_M], cs[MAX_LBFGS_M];
@@ -37,6 +42,8 @@ struct Solver {
     double *x = nullptr, *G = nullptr, *d = nullptr, *xt = nullptr, *Gt = nullptr;
     double *Sv = nullptr, *Yv = nullptr;
     double *pbase = nullptr, *ppair = nullptr;  // dot partials
+    double* trace = nullptr;                    // objective trace of the last solve
+    int trace_len = 0;
     double D = 0.0, ginf = 0.0;
     int iters = 0;
     ~Solver();

@@ -14,17 +14,19 @@
 //    is evaluated start to end by one thread and the warps' work is the same
 //    whatever the group sizes.
 //
-// Per block (group l, column j): pass A forms f = alpha_i + beta_j - c_ij only
-// where the cheap bound says f may be positive -- fl(fl(A'_i - c_ij) + B'_j) > 0
-// with A', B' alpha, beta rounded up by a relative 2^-22, tested on the max
-// over four rows at a time -- in double-float with TwoSum, and sums S =
-// ||[f_[l]]_+||^2 and P = sum [f_[l]]_+.  At the group's last row: the shrink
-// s = [z - theta]_+ / (gamma z) and psi = [z - theta]_+^2 / (2 gamma) of Eq. 5,
-// and, where s > 0, pass B adds s [f]_+ into the row sums (one warp sum per
-// row; rows of earlier stages are re-read from L2).  Row and column sums go
-// to int64 fixed-point accumulators by atomic adds, whose total does not
-// depend on their order; psi goes to per-(item, warp) partials that the
-// reduction kernel adds in a fixed order.
+// Per block (group l, column j), dense evaluation: each lane first marks the
+// 4-row chunks of a stage where f may be positive -- fl(fl(A'_i - c_ij) + B'_j)
+// > 0 for the max over the chunk, with A', B' alpha, beta rounded up by a
+// relative 2^-22 -- and only groups with a marked chunk (in any lane of the
+// warp) are visited: f is formed there in double-float with TwoSum, and S =
+// ||[f_[l]]_+||^2 and P = sum [f_[l]]_+ are summed.  At the group's last row:
+// the shrink s = [z - theta]_+ / (gamma z) and psi = [z - theta]_+^2 /
+// (2 gamma) of Eq. 5, and, where s > 0, pass B adds s [f]_+ into the row sums
+// (one warp sum per row; rows of earlier stages are re-read from L2).  A
+// snapshot evaluation also needs z~ and o~ (Def. 1) of every block, so it
+// walks every group.  Row and column sums go to int64 fixed-point accumulators
+// by atomic adds, whose total does not depend on their order; psi goes to
+// per-(item, warp) partials that the reduction kernel adds in a fixed order.
 //
 // Every wait is on an mbarrier and gives up after WAIT_NS; on timeout the
 // kernel records an error in A.err, the producer waits (bounded) for the
@@ -57,22 +59,21 @@ struct StageHdr {
     ItemDesc d;
     int sidx;     // stage index within the item
     int flags;
-    int g_shift;  // offset of the stage's row 0 in rowG[]
-    int pad;
+    int pad[2];
 };
 
 struct Smem {
     float stage[NSTAGES][SR * IC];   // NSTAGES x 32 KB; stage row r at [r * IC]
     float4 rowA[NSTAGES][SR];        // (alpha hi, alpha lo, A', 0) of the stage's rows
-    int2 rowG[NSTAGES][SR + 2];      // (group, end of group) of the stage's rows, row r at [r + g_shift]
+    int4 rowG[NSTAGES][SR];          // (group, first row, end row, 0) of the stage's rows
     float2 colB[NSTAGES][IC];        // item's first stage: (beta hi, lo) of its columns
     float colP[NSTAGES][IC];         // item's first stage: B' of its columns
-    uint32_t rmask[NSTAGES][SR];     // screened: bit w set = warp w evaluates the row's block
+    uint32_t rmaskw[NSTAGES][CONSUMERS];  // screened: bit r set = warp w evaluates row r's block
     StageHdr hdr[NSTAGES];
     uint64_t full[NSTAGES];
     uint64_t empty[NSTAGES];
 };
-static_assert(sizeof(Smem) + 1024 <= 227 * 1024, "shared memory of one CTA (plus alignment slack)");
+static_assert(CTAS_PER_SM * (sizeof(Smem) + 2048) <= 228 * 1024, "shared memory of the CTAs of one SM");
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -249,7 +250,7 @@ __device__ __forceinline__ void acc_neg(const float4& a, float c, float bh, floa
     O = fmaf(x, x, O);
 }
 
-// Pass A over rows [r, e) of a stage for this lane's column.
+// Pass A over rows [r, e) of a stage for this lane's column (snapshot walk).
 template <bool SNAP>
 __device__ __forceinline__ void scan_rows(const float* st, const float4* rA, int r, int e, float bh, float bl,
                                           float bp, Acc& acc, float& O, bool& any)
@@ -281,6 +282,41 @@ __device__ __forceinline__ void scan_rows(const float* st, const float4* rA, int
     }
 }
 
+// Bit q set: chunk q (rows [4q, 4q + 4)) of the stage may hold an f > 0 in
+// this lane's column.  Rows past the stage's end hold stale data and are
+// masked by the caller.
+__device__ __forceinline__ uint32_t chunk_marks(const float* st, const float4* rA, float bp)
+{
+    uint32_t cm = 0u;
+#pragma unroll
+    for (int q = 0; q < SR / 4; q++) {
+        const int r = 4 * q;
+        const float x0 = __fsub_rn(rA[r + 0].z, st[(r + 0) * IC]);
+        const float x1 = __fsub_rn(rA[r + 1].z, st[(r + 1) * IC]);
+        const float x2 = __fsub_rn(rA[r + 2].z, st[(r + 2) * IC]);
+        const float x3 = __fsub_rn(rA[r + 3].z, st[(r + 3) * IC]);
+        const float mx = fmaxf(fmaxf(x0, x1), fmaxf(x2, x3));  // a NaN operand yields the other one
+        if (__fadd_rn(mx, bp) > 0.f) cm |= 1u << q;
+    }
+    return cm;
+}
+
+// Chunks that overlap rows [s, e) (s < e).
+__device__ __forceinline__ uint32_t chunks_in(int s, int e)
+{
+    return ((2u << ((e - 1) >> 2)) - 1u) & ~((1u << (s >> 2)) - 1u);
+}
+
+// Chunks with at least one row set in a 32-row mask.
+__device__ __forceinline__ uint32_t chunks_of_rows(uint32_t rows)
+{
+    uint32_t c = 0u;
+#pragma unroll
+    for (int q = 0; q < SR / 4; q++)
+        if ((rows >> (4 * q)) & 0xfu) c |= 1u << q;
+    return c;
+}
+
 __device__ __forceinline__ float warp_sum(float v)
 {
 #pragma unroll
@@ -303,11 +339,93 @@ __device__ __forceinline__ void put_snap(const EvalArgs& A, int l, int col, floa
     }
 }
 
+// The block of this lane's column that is being accumulated.
+struct Block {
+    int gl, gstart, gend;  // group and its sorted rows [gstart, gend)
+    bool need;             // evaluated by this warp (always, unless screened)
+    bool any;              // some f > 0 seen
+    Acc acc;
+    float O;               // sum of [f]_-^2 (snapshot evaluations)
+};
+
+// Per-lane constants of the current item and the stage being consumed.
+struct Ctx {
+    const float* st;   // stage, offset to this lane's column
+    const float4* rA;  // stage's alpha records
+    int ra, nr;        // first sorted row of the stage, rows in it
+    float bh, bl, bp;  // beta hi, lo, B' of this lane's column
+    int colg;          // this lane's column of C
+    uint32_t U;        // chunks of the stage marked by some lane (dense path)
+};
+
+__device__ __forceinline__ void open_block(Block& b, const int4& g, bool need)
+{
+    b.gl = g.x;
+    b.gstart = g.y;
+    b.gend = g.z;
+    b.need = need;
+    b.any = false;
+    b.acc = Acc{0.f, 0.f, 0.f, 0.f};
+    b.O = 0.f;
+}
+
+// The block is complete: Eq. 5 for it, and pass B where s > 0.
+template <bool SNAP>
+__device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, const FxScale& fx,
+                                             int lane, bool marks, double& psi_acc, double& cacc)
+{
+    float s = 0.f;
+    if (__any_sync(FULLMASK, b.any)) {
+        double psi;
+        s = block_scale(b.acc.Sh, b.acc.Sl, A, psi);
+        psi_acc += psi;
+        if (s > 0.f) cacc += (double)s * ((double)b.acc.Ph + (double)b.acc.Pl);
+    }
+    if (SNAP) put_snap(A, b.gl, x.colg, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
+    if (!__any_sync(FULLMASK, s > 0.f)) return;
+    // pass B: t_ij = s [f_ij]_+ into the row sums
+    for (int R = b.gstart; R < b.gend; R++) {
+        float c;
+        float4 a;
+        if (R >= x.ra) {
+            const int r = R - x.ra;
+            if (marks && !((x.U >> (r >> 2)) & 1u)) continue;  // no f > 0 in this chunk
+            c = x.st[r * IC];
+            a = x.rA[r];
+        } else {  // the row's stage has left the ring: re-read it (from L2)
+            c = x.colg < A.n ? __ldg(A.C + (int64_t)R * A.ldc + x.colg) : 0.f;
+            a = __ldg(A.rowA + R);
+        }
+        float t = 0.f;
+        if (s > 0.f && maybe_pos(a.z, c, x.bp)) {
+            float fh, fl;
+            f_exact(a.x, a.y, x.bh, x.bl, c, fh, fl);
+            if (fh > 0.f) t = __fmul_rn(s, fh);
+        }
+        if (__any_sync(FULLMASK, t != 0.f)) {
+            const float rs = warp_sum(t);
+            if (lane == 0) red_fx(A.rowfx + R, (double)rs, fx.to_r);
+        }
+    }
+}
+
+// Dense path: the marked chunks of rows [s, e) of the block's group.
+__device__ __forceinline__ void block_marked_rows(Block& b, const Ctx& x, int s, int e)
+{
+    uint32_t qm = x.U & chunks_in(s, e);
+    while (qm) {
+        const int q = __ffs(qm) - 1;
+        qm &= qm - 1u;
+        const int r1 = min(4 * q + 4, e);
+        for (int r = max(4 * q, s); r < r1; r++) elem_exact(x.rA[r], x.st[r * IC], x.bh, x.bl, x.bp, b.acc, b.any);
+    }
+}
+
 }  // namespace
 
 // ================================================================= kernel
 template <bool SNAP>
-__global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const __grid_constant__ TmaMaps T)
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs A, const __grid_constant__ TmaMaps T)
 {
     extern __shared__ unsigned char smem_raw[];
     // TMA destinations must be 128-byte aligned: align the layout to 1 KB
@@ -375,7 +493,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
                 for (int s = 0; s < nst; s++) {
                     const int ra = r0 + s * SR;
                     const int nr = min(SR, rows - s * SR);
-                    uint32_t m8 = 0xffu;
+                    uint32_t m8 = 0xffu;  // this lane's row: bit w = warp w evaluates its block
                     uint32_t need = nr == 32 ? FULLMASK : ((1u << nr) - 1u);
                     if (screened) {
                         m8 = 0u;
@@ -386,18 +504,22 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
                         }
                         need = __ballot_sync(FULLMASK, m8 != 0u);
                     }
+                    uint32_t wmask = 0u;  // lane w < CONSUMERS: rows evaluated by warp w
+#pragma unroll
+                    for (int w = 0; w < CONSUMERS; w++) {
+                        const uint32_t bw = __ballot_sync(FULLMASK, (m8 >> w) & 1u);
+                        if (lane == w) wmask = bw;
+                    }
                     int slot;
                     if (!next_slot(slot)) { ok = false; break; }
-                    S.rmask[slot][lane] = m8;
+                    if (lane < CONSUMERS) S.rmaskw[slot][lane] = wmask;
                     if (lane < DESC_WORDS) reinterpret_cast<int*>(&S.hdr[slot].d)[lane] = w0;
                     if (lane == 0) {
-                        const int g0 = ra & ~1;
-                        const int gcnt = ((ra + nr + 1) & ~1) - g0;
-                        const uint32_t abytes = (uint32_t)nr * 16u, gbytes = (uint32_t)gcnt * 8u;
+                        const uint32_t abytes = (uint32_t)nr * 16u;
                         const uint32_t cbytes = s == 0 ? (uint32_t)IC * 12u : 0u;
-                        mbar_expect(&S.full[slot], (uint32_t)__popc(need) * ROW_BYTES + abytes + gbytes + cbytes);
+                        mbar_expect(&S.full[slot], (uint32_t)__popc(need) * ROW_BYTES + 2u * abytes + cbytes);
                         bulk_copy(S.rowA[slot], A.rowA + ra, abytes, &S.full[slot]);
-                        bulk_copy(S.rowG[slot], A.rowg + g0, gbytes, &S.full[slot]);
+                        bulk_copy(S.rowG[slot], A.rowg + ra, abytes, &S.full[slot]);
                         if (s == 0) {
                             bulk_copy(S.colB[slot], A.B2 + col0, IC * 8u, &S.full[slot]);
                             bulk_copy(S.colP[slot], A.Bp + col0, IC * 4u, &S.full[slot]);
@@ -405,7 +527,6 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
                         StageHdr& hh = S.hdr[slot];
                         hh.sidx = s;
                         hh.flags = (s == 0 ? H_FIRST : 0) | (s == nst - 1 ? H_LAST : 0);
-                        hh.g_shift = ra - g0;
                         // one run of consecutive needed rows at a time
                         uint32_t rem = need;
                         while (rem) {
@@ -439,15 +560,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
     const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);
     const int wc = warp * TW + lane;  // this lane's column within an item
     long long consumed = 0;
-    // item state
-    float bh = 0.f, bl = 0.f, bp = -INFINITY;
-    int colg = 0;
+    Ctx x;
+    x.bh = 0.f; x.bl = 0.f; x.bp = -INFINITY; x.colg = 0; x.U = 0u;
     double psi_acc = 0.0, cacc = 0.0;
-    // block state
-    int gl = 0, gend = 0, gstart = 0;
-    bool need = false, any = false;
-    Acc acc = {0.f, 0.f, 0.f, 0.f};
-    float O = 0.f;
+    Block blk;
+    open_block(blk, make_int4(0, 0, 0, 0), false);
     for (;;) {
         const int slot = (int)(consumed % NSTAGES);
         if (!mbar_wait(&S.full[slot], (uint32_t)((consumed / NSTAGES) & 1))) {
@@ -457,69 +574,61 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
         const StageHdr& hs = S.hdr[slot];
         const int flags = hs.flags;
         if (flags & H_TERM) return;
-        const int r0 = hs.d.r0, rows = hs.d.rows, sidx = hs.sidx;
+        const int r0 = hs.d.r0;
         if (flags & H_FIRST) {
             const float2 b2 = S.colB[slot][wc];
-            bh = b2.x;
-            bl = b2.y;
-            bp = S.colP[slot][wc];
-            colg = hs.d.col0 + wc;
+            x.bh = b2.x;
+            x.bl = b2.y;
+            x.bp = S.colP[slot][wc];
+            x.colg = hs.d.col0 + wc;
             psi_acc = 0.0;
             cacc = 0.0;
-            gend = r0;  // the item's first row opens a block
+            blk.gend = r0;  // no block continues into the item
         }
-        const int ra = r0 + sidx * SR, nr = min(SR, rows - sidx * SR);
-        const float* st = S.stage[slot] + wc;
-        const float4* rA = S.rowA[slot];
-        const int2* rG = S.rowG[slot] + hs.g_shift;
-        int r = 0;
-        while (r < nr) {
-            if (ra + r == gend) {  // a new group starts at row r
-                const int2 g2 = rG[r];
-                gl = g2.x;
-                gend = g2.y;
-                gstart = ra + r;
-                acc = Acc{0.f, 0.f, 0.f, 0.f};
-                O = 0.f;
-                any = false;
-                need = !A.unit_need || ((S.rmask[slot][r] >> warp) & 1u);
+        x.ra = r0 + hs.sidx * SR;
+        x.nr = min(SR, hs.d.rows - hs.sidx * SR);
+        x.st = S.stage[slot] + wc;
+        x.rA = S.rowA[slot];
+        const int4* rG = S.rowG[slot];
+        const uint32_t wrows = A.unit_need ? S.rmaskw[slot][warp] : FULLMASK;  // rows this warp evaluates
+        if (SNAP) {
+            // every block: z~ and o~ of Def. 1 for the snapshot
+            int r = 0;
+            while (r < x.nr) {
+                if (x.ra + r == blk.gend) open_block(blk, rG[r], (wrows >> r) & 1u);
+                const int e = min(blk.gend - x.ra, x.nr);
+                if (blk.need) scan_rows<true>(x.st, x.rA, r, e, x.bh, x.bl, x.bp, blk.acc, blk.O, blk.any);
+                r = e;
+                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, fx, lane, false, psi_acc, cacc);
             }
-            const int e = min(gend - ra, nr);
-            if (need) scan_rows<SNAP>(st, rA, r, e, bh, bl, bp, acc, O, any);
-            r = e;
-            if (ra + r != gend || !need) continue;
-            // ---- the block (gl, colg) is complete
-            float s = 0.f;
-            if (__any_sync(FULLMASK, any)) {
-                double psi;
-                s = block_scale(acc.Sh, acc.Sl, A, psi);
-                psi_acc += psi;
-                if (s > 0.f) cacc += (double)s * ((double)acc.Ph + (double)acc.Pl);
+        } else {
+            // only the groups with a marked chunk (and a block that ends here)
+            const uint32_t live = (x.nr >= SR ? 0xffu : (1u << ((x.nr + 3) >> 2)) - 1u) & chunks_of_rows(wrows);
+            x.U = __reduce_or_sync(FULLMASK, chunk_marks(x.st, x.rA, x.bp) & live);
+            int r = 0;
+            if (blk.gend > x.ra) {  // the block open at the end of the last stage continues here
+                const int e = min(blk.gend - x.ra, x.nr);
+                if (blk.need) block_marked_rows(blk, x, 0, e);
+                if (blk.gend <= x.ra + x.nr && blk.need)
+                    finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
+                r = e;
             }
-            if (SNAP) put_snap(A, gl, colg, z_up(acc.Sh, acc.Sl), __fsqrt_ru(O));
-            if (__any_sync(FULLMASK, s > 0.f)) {
-                // pass B: t_ij = s [f_ij]_+ into the row sums
-                for (int R = gstart; R < gend; R++) {
-                    float c;
-                    float4 a;
-                    if (R >= ra) {
-                        c = st[(R - ra) * IC];
-                        a = rA[R - ra];
-                    } else {  // the row's stage has left the ring: re-read it (from L2)
-                        c = colg < A.n ? __ldg(A.C + (int64_t)R * A.ldc + colg) : 0.f;
-                        a = __ldg(A.rowA + R);
-                    }
-                    float t = 0.f;
-                    if (s > 0.f && maybe_pos(a.z, c, bp)) {
-                        float fh, fl;
-                        f_exact(a.x, a.y, bh, bl, c, fh, fl);
-                        if (fh > 0.f) t = __fmul_rn(s, fh);
-                    }
-                    if (__any_sync(FULLMASK, t != 0.f)) {
-                        const float rs = warp_sum(t);
-                        if (lane == 0) red_fx(A.rowfx + R, (double)rs, fx.to_r);
-                    }
+            while (r < x.nr) {
+                const uint32_t Ur = x.U & ~((1u << (r >> 2)) - 1u);
+                if (!Ur) {
+                    // no f > 0 in rows [r, nr): the stage's last group stays open
+                    // (with nothing accumulated) in case it continues
+                    const int last = x.nr - 1;
+                    open_block(blk, rG[last], (wrows >> last) & 1u);
+                    break;
                 }
+                const int rc = max(r, 4 * (__ffs(Ur) - 1));  // the group there starts at or after r
+                open_block(blk, rG[rc], (wrows >> rc) & 1u);
+                const int e = min(blk.gend - x.ra, x.nr);
+                if (blk.need) block_marked_rows(blk, x, blk.gstart - x.ra, e);
+                if (blk.gend <= x.ra + x.nr && blk.need)
+                    finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
+                r = e;
             }
         }
         if (flags & H_LAST) {
@@ -527,7 +636,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_stream(const EvalArgs A, const _
 #pragma unroll
             for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
             if (lane == 0) A.psipart[(int64_t)hs.d.item * NWARPS + warp] = v;
-            if (colg < A.n && cacc != 0.0) red_fx(A.colfx + colg, cacc, fx.to_c);
+            if (x.colg < A.n && cacc != 0.0) red_fx(A.colfx + x.colg, cacc, fx.to_c);
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[slot]);

@@ -81,3 +81,20 @@ def test_unsorted_labels_and_ragged_solve():
     assert rc == pk.OTGS_OK
     D, _, _ = o.dual(sol["alpha"].cpu().numpy(), sol["beta"].cpu().numpy())
     assert abs(D - ref["D"]) <= 1e-9 * abs(ref["D"])
+
+
+def test_objective_trace_follows_the_solve():
+    """ot_gs_get_trace: one entry for the start point and one per accepted
+    iteration; the line search accepts ascent steps of D (or, by its
+    approximate sufficient-decrease rule, a change within 1e-12 |D|), device
+    time grows, and the last entry is the reported optimum."""
+    p = synth.tiny(seed=4)
+    s, rc, sol = _solve(p, 1.0, 0.1, 1e-9)
+    assert rc == pk.OTGS_OK
+    D, t, ev = s.trace()
+    assert len(D) == sol["iters"] + 1
+    assert D[0] == 0.0  # Alg. 1 starts at alpha = beta = 0 where D = 0
+    assert np.all(np.diff(D) >= -1e-12 * np.abs(D[1:]))
+    assert np.all(np.diff(t) >= 0.0) and t[0] >= 0.0
+    assert np.all(np.diff(ev) >= 1) and ev[0] == 1
+    assert D[-1] == sol["D"]
