@@ -148,14 +148,13 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     // evaluation buffers
     rowA = (float4*)dalloc(sizeof(float4) * (size_t)m, "rowA");
     B2 = (float2*)dalloc(sizeof(float2) * (size_t)padded_cols(n), "B2");
-    Bp = (float*)dalloc(sizeof(float) * (size_t)padded_cols(n), "Bp");
     ctl = (EvalCtl*)dalloc(sizeof(EvalCtl), "evaluation control");
     kerr = (int*)dalloc(sizeof(int) * 4, "kernel error");
     alpha_eval = (double*)dalloc(sizeof(double) * m, "alpha_eval");
     rowfx = (unsigned long long*)dalloc(sizeof(unsigned long long) * (size_t)m, "row sums");
     colfx = (unsigned long long*)dalloc(sizeof(unsigned long long) * (size_t)n, "column sums");
     psipart = (double*)dalloc(sizeof(double) * (size_t)hp.nitems() * NWARPS, "psipart");
-    if (!rowA || !B2 || !Bp || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !psipart) return false;
+    if (!rowA || !B2 || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !psipart) return false;
     if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
     {
         int dev = 0;
@@ -182,7 +181,7 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.m = (int32_t)m; e.n = (int32_t)n; e.L = L; e.ntiles = ntiles;
     e.nitems = hp.nitems();
     e.rowA = rowA; e.rowg = dp.rowg;
-    e.B2 = B2; e.Bp = Bp;
+    e.B2 = B2;
     e.ctl = ctl; e.err = kerr;
     e.nlist = hp.nitems();
     e.desc = dp.desc;
@@ -228,7 +227,7 @@ ReduceArgs Handle::reduce_args(const uint8_t* active, double* out_caller, double
 // Preparation of an evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.
 void Handle::prep(const double* alpha, bool alpha_sorted, const double* beta)
 {
-    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, rowA, B2, Bp, alpha_eval, rowfx, colfx,
+    launch_prep(alpha, alpha_sorted, dp.perm, beta, (int32_t)m, (int32_t)n, rowA, B2, alpha_eval, rowfx, colfx,
                 ctl, st);
 }
 

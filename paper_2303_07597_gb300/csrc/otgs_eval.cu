@@ -18,7 +18,7 @@ namespace otgs {
 
 // --------------------------------------------------------------- prep
 __global__ void k_prep(const double* __restrict__ alpha, int alpha_sorted, const int32_t* __restrict__ perm,
-                       const double* __restrict__ beta, int m, int n, int npad, float4* rowA, float2* B2, float* Bp,
+                       const double* __restrict__ beta, int m, int n, int npad, float4* rowA, float2* B2,
                        double* alpha_s_out, unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl)
 {
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -30,20 +30,20 @@ __global__ void k_prep(const double* __restrict__ alpha, int alpha_sorted, const
         if (alpha_s_out) alpha_s_out[t] = a;
     }
     if (t < npad) {
-        bpos = prep_col(t < n, t < n ? beta[t] : 0.0, B2 + t, Bp + t);
+        bpos = prep_col(t < n, t < n ? beta[t] : 0.0, B2 + t);
         if (t < n) colfx[t] = 0ull;
     }
     record_max(ctl, apos, bpos);
 }
 
 void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, const double* beta,
-                 int32_t m, int32_t n, float4* rowA, float2* B2, float* Bp, double* alpha_s_out,
+                 int32_t m, int32_t n, float4* rowA, float2* B2, double* alpha_s_out,
                  unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl, cudaStream_t st)
 {
     const int npad = padded_cols(n);
     const int tot = m > npad ? m : npad;
     cudaMemsetAsync(ctl, 0, sizeof(EvalCtl), st);
-    k_prep<<<(tot + 255) / 256, 256, 0, st>>>(alpha, alpha_sorted ? 1 : 0, perm, beta, m, n, npad, rowA, B2, Bp,
+    k_prep<<<(tot + 255) / 256, 256, 0, st>>>(alpha, alpha_sorted ? 1 : 0, perm, beta, m, n, npad, rowA, B2,
                                              alpha_s_out, rowfx, colfx, ctl);
 }
 

@@ -33,7 +33,6 @@ struct Handle {
     // one evaluation
     float4* rowA = nullptr;         // sorted rows: (alpha hi, lo, bound_up(hi), 0)
     float2* B2 = nullptr;           // (beta hi, lo), padded columns
-    float* Bp = nullptr;            // bound_up(beta hi), padded columns
     TmaMaps tmaps;                  // TMA descriptors of C
     EvalCtl* ctl = nullptr;         // evaluation control word (work counter, scale maxima)
     int* kerr = nullptr;            // evaluation kernel error word
@@ -87,7 +86,7 @@ struct Handle {
                            const double* beta_ptr);
     bool eval_dense(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,
                     double* G_sorted, const double* dir, bool snap);
-    // evaluations whose preparation (rowA, B2, Bp, alpha_eval, ctl) is already in place
+    // evaluations whose preparation (rowA, B2, alpha_eval, ctl) is already in place
     bool eval_dense_prepped(const double* beta, double* G_sorted, const double* dir);
     bool eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap);
     bool eval_screened_prepped(const double* beta, double* G_sorted, const double* dir,

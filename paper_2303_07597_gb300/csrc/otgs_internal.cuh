@@ -60,18 +60,16 @@ __device__ __forceinline__ float prep_row(double a, float4* rowA)
     return fmaxf(s.x, 0.f);
 }
 
-// Preparation of one (padded) column: (beta hi, lo) and bound_up(beta hi); a
-// padding column gets a bound of -inf, which no element passes.
-__device__ __forceinline__ float prep_col(bool real, double b, float2* B2, float* Bp)
+// Preparation of one (padded) column: (beta hi, lo); a padding column gets
+// (-1e30, 0).  Returns [beta hi]_+ for the fixed-point scale.
+__device__ __forceinline__ float prep_col(bool real, double b, float2* B2)
 {
     if (!real) {
         *B2 = make_float2(-1e30f, 0.f);
-        *Bp = -INFINITY;
         return 0.f;
     }
     const float2 s = split2(b);
     *B2 = s;
-    *Bp = bound_up(s.x);
     return fmaxf(s.x, 0.f);
 }
 
@@ -194,7 +192,6 @@ struct EvalArgs {
     const float4* rowA;  // sorted rows: (alpha hi, alpha lo, bound_up(alpha hi), 0)
     const int4* rowg;    // sorted rows: (group, first row, end row of the group, 0)
     const float2* B2;    // columns padded to padded_cols(n): (hi, lo) split of beta
-    const float* Bp;     // bound_up(beta hi) per column, -inf in the padding
     EvalCtl* ctl;
     int* err;            // error word (0 = ok)
     int32_t nlist;       // entries of desc
@@ -238,10 +235,10 @@ struct ReduceArgs {
 };
 
 // launchers (otgs_eval.cu)
-// Zeroes ctl, then writes rowA, B2, Bp (and alpha_s_out), zeroes rowfx and
+// Zeroes ctl, then writes rowA, B2 (and alpha_s_out), zeroes rowfx and
 // colfx and records max [alpha hi]_+, max [beta hi]_+ in ctl.
 void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, const double* beta,
-                 int32_t m, int32_t n, float4* rowA, float2* B2, float* Bp, double* alpha_s_out,
+                 int32_t m, int32_t n, float4* rowA, float2* B2, double* alpha_s_out,
                  unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl, cudaStream_t st);
 // TMA descriptors of C: box k is 2^k rows x ITEM_COLS columns (k = 0..TMA_BOXES-1).
 constexpr int TMA_BOXES = 6;

@@ -91,7 +91,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const size_t o_perm = cv.take(4 * hp.perm.size()), o_rowg = cv.take(sizeof(int4) * hp.rowg.size());
     const size_t o_desc = cv.take(sizeof(ItemDesc) * hp.desc.size());
     const size_t o_rowA = cv.take(sizeof(float4) * (size_t)m);
-    const size_t o_B2 = cv.take(8 * (size_t)padded_cols(n)), o_Bp = cv.take(4 * (size_t)padded_cols(n));
+    const size_t o_B2 = cv.take(8 * (size_t)padded_cols(n));
     const size_t o_ctl = cv.take(sizeof(EvalCtl)), o_err = cv.take(16);
     const size_t o_aeval = cv.take(8 * (size_t)m);
     const size_t o_rowfx = cv.take(8 * (size_t)m), o_colfx = cv.take(8 * (size_t)n);
@@ -134,20 +134,19 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const int32_t* perm = (const int32_t*)(base + o_perm);
     float4* rowA = (float4*)(base + o_rowA);
     float2* B2 = (float2*)(base + o_B2);
-    float* Bp = (float*)(base + o_Bp);
     EvalCtl* ctl = (EvalCtl*)(base + o_ctl);
     double* aeval = (double*)(base + o_aeval);
     unsigned long long* rowfx = (unsigned long long*)(base + o_rowfx);
     unsigned long long* colfx = (unsigned long long*)(base + o_colfx);
     // the caller's alpha is already in class-sorted order (labels non-decreasing)
-    launch_prep(alpha, true, perm, beta, (int32_t)m, (int32_t)n, rowA, B2, Bp, aeval, rowfx, colfx, ctl, st);
+    launch_prep(alpha, true, perm, beta, (int32_t)m, (int32_t)n, rowA, B2, aeval, rowfx, colfx, ctl, st);
     EvalArgs ea;
     memset(&ea, 0, sizeof(ea));
     ea.C = C; ea.ldc = ldc;
     ea.m = (int32_t)m; ea.n = (int32_t)n; ea.L = L; ea.ntiles = ntiles;
     ea.nitems = hp.nitems();
     ea.rowA = rowA; ea.rowg = (const int4*)(base + o_rowg);
-    ea.B2 = B2; ea.Bp = Bp;
+    ea.B2 = B2;
     ea.ctl = ctl; ea.err = (int*)(base + o_err);
     ea.nlist = hp.nitems();
     ea.desc = (const ItemDesc*)(base + o_desc);

@@ -24,7 +24,7 @@ namespace otgs {
 // x_t = x + t d; also the preparation of x_t for the evaluation kernel (the
 // same per-row and per-column records as the plain preparation kernel).
 __global__ void k_trial(SolverState* S, const double* __restrict__ x, const double* __restrict__ d, double* xt,
-                        float4* rowA, float2* B2, float* Bp, double* alpha_eval, unsigned long long* rowfx,
+                        float4* rowA, float2* B2, double* alpha_eval, unsigned long long* rowfx,
                         unsigned long long* colfx, EvalCtl* ctl, int m, int n, int npad)
 {
     if (S->done) return;  // the same for every thread
@@ -45,7 +45,7 @@ __global__ void k_trial(SolverState* S, const double* __restrict__ x, const doub
             xt[m + i] = v;
             colfx[i] = 0ull;
         }
-        bpos = prep_col(i < n, v, B2 + i, Bp + i);
+        bpos = prep_col(i < n, v, B2 + i);
     }
     record_max(ctl, apos, bpos);
 }
@@ -418,7 +418,7 @@ int Solver::run(double tol, int maxit)
             break;
         }
         cudaMemsetAsync(h->ctl, 0, sizeof(EvalCtl), st);
-        k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->rowA, h->B2, h->Bp, h->alpha_eval, h->rowfx, h->colfx,
+        k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->rowA, h->B2, h->alpha_eval, h->rowfx, h->colfx,
                                     h->ctl, (int)h->m, (int)h->n, npad);
         if (!eval_trial()) return h->last_code;
         k_linesearch<<<1, 1, 0, st>>>(state, h->scal);

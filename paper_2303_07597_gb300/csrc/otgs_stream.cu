@@ -22,7 +22,8 @@
 // ||[f_[l]]_+||^2 and P = sum [f_[l]]_+ are summed.  At the group's last row:
 // the shrink s = [z - theta]_+ / (gamma z) and psi = [z - theta]_+^2 /
 // (2 gamma) of Eq. 5, and, where s > 0, pass B adds s [f]_+ into the row sums
-// (one warp sum per row; rows of earlier stages are re-read from L2).  A
+// (each lane adds its nonzero t_ij; only rows in chunks marked in pass A;
+// rows of earlier stages are re-read from L2).  A
 // snapshot evaluation also needs z~ and o~ (Def. 1) of every block, so it
 // walks every group.  Row and column sums go to int64 fixed-point accumulators
 // by atomic adds, whose total does not depend on their order; psi goes to
@@ -52,6 +53,10 @@ constexpr int DESC_WORDS = (int)(sizeof(ItemDesc) / sizeof(int));
 static_assert(DESC_WORDS <= 32, "a descriptor is spread over the producer's lanes");
 static_assert(SR == 32, "the producer maps one lane to each row of a stage");
 
+// Stages of an item whose marked chunks a warp remembers for pass B (items of
+// up to MARK_STAGES * STAGE_ROWS rows; rows beyond are all visited).
+constexpr int MARK_STAGES = 256;
+
 enum : int { H_FIRST = 1, H_LAST = 2, H_TERM = 4 };
 
 // What the consumers need about a stage, written by the producer.
@@ -67,8 +72,8 @@ struct Smem {
     float4 rowA[NSTAGES][SR];        // (alpha hi, alpha lo, A', 0) of the stage's rows
     int4 rowG[NSTAGES][SR];          // (group, first row, end row, 0) of the stage's rows
     float2 colB[NSTAGES][IC];        // item's first stage: (beta hi, lo) of its columns
-    float colP[NSTAGES][IC];         // item's first stage: B' of its columns
     uint32_t rmaskw[NSTAGES][CONSUMERS];  // screened: bit r set = warp w evaluates row r's block
+    uint8_t marks[CONSUMERS][MARK_STAGES];  // per warp: marked chunks of each stage of the item
     StageHdr hdr[NSTAGES];
     uint64_t full[NSTAGES];
     uint64_t empty[NSTAGES];
@@ -317,13 +322,6 @@ __device__ __forceinline__ uint32_t chunks_of_rows(uint32_t rows)
     return c;
 }
 
-__device__ __forceinline__ float warp_sum(float v)
-{
-#pragma unroll
-    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
-    return v;
-}
-
 __device__ __forceinline__ void red_fx(unsigned long long* p, double v, double to_fx)
 {
     atomicAdd(p, (unsigned long long)__double2ll_rn(v * to_fx));
@@ -356,6 +354,8 @@ struct Ctx {
     float bh, bl, bp;  // beta hi, lo, B' of this lane's column
     int colg;          // this lane's column of C
     uint32_t U;        // chunks of the stage marked by some lane (dense path)
+    int r0;            // first sorted row of the item
+    const uint8_t* marks;  // this warp's marked chunks of the item's stages
 };
 
 __device__ __forceinline__ void open_block(Block& b, const int4& g, bool need)
@@ -372,7 +372,7 @@ __device__ __forceinline__ void open_block(Block& b, const int4& g, bool need)
 // The block is complete: Eq. 5 for it, and pass B where s > 0.
 template <bool SNAP>
 __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, const FxScale& fx,
-                                             int lane, bool marks, double& psi_acc, double& cacc)
+                                             bool marks, double& psi_acc, double& cacc)
 {
     float s = 0.f;
     if (__any_sync(FULLMASK, b.any)) {
@@ -383,28 +383,40 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
     }
     if (SNAP) put_snap(A, b.gl, x.colg, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
     if (!__any_sync(FULLMASK, s > 0.f)) return;
-    // pass B: t_ij = s [f_ij]_+ into the row sums
-    for (int R = b.gstart; R < b.gend; R++) {
-        float c;
-        float4 a;
-        if (R >= x.ra) {
-            const int r = R - x.ra;
-            if (marks && !((x.U >> (r >> 2)) & 1u)) continue;  // no f > 0 in this chunk
-            c = x.st[r * IC];
-            a = x.rA[r];
-        } else {  // the row's stage has left the ring: re-read it (from L2)
-            c = x.colg < A.n ? __ldg(A.C + (int64_t)R * A.ldc + x.colg) : 0.f;
-            a = __ldg(A.rowA + R);
-        }
-        float t = 0.f;
-        if (s > 0.f && maybe_pos(a.z, c, x.bp)) {
-            float fh, fl;
-            f_exact(a.x, a.y, x.bh, x.bl, c, fh, fl);
-            if (fh > 0.f) t = __fmul_rn(s, fh);
-        }
-        if (__any_sync(FULLMASK, t != 0.f)) {
-            const float rs = warp_sum(t);
-            if (lane == 0) red_fx(A.rowfx + R, (double)rs, fx.to_r);
+    // pass B: t_ij = s [f_ij]_+ into the row sums, over the block's rows that
+    // can hold an f > 0 (marked chunks; every row on the snapshot walk),
+    // four rows at a time
+    const int sa = (b.gstart - x.r0) / SR, sb = (b.gend - 1 - x.r0) / SR;
+    for (int sg = sa; sg <= sb; sg++) {
+        const int base = x.r0 + sg * SR;
+        const bool here = base == x.ra;  // the stage being consumed is still in shared memory
+        uint32_t qm = 0xffu;
+        if (marks) qm = here ? x.U : (sg < MARK_STAGES ? (uint32_t)x.marks[sg] : 0xffu);
+        qm &= chunks_in(max(b.gstart - base, 0), min(b.gend - base, SR));
+        while (qm) {
+            const int q = __ffs(qm) - 1;
+            qm &= qm - 1u;
+            const int R0 = max(base + 4 * q, b.gstart), R1 = min(base + 4 * q + 4, b.gend);
+            float c[4];
+            float4 a[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int R = min(R0 + k, R1 - 1);
+                if (here) {
+                    c[k] = x.st[(R - base) * IC];
+                    a[k] = x.rA[R - base];
+                } else {  // the row's stage has left the ring: re-read it (from L2)
+                    c[k] = x.colg < A.n ? __ldg(A.C + (int64_t)R * A.ldc + x.colg) : 0.f;
+                    a[k] = __ldg(A.rowA + R);
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (R0 + k >= R1 || !(s > 0.f) || !maybe_pos(a[k].z, c[k], x.bp)) continue;
+                float fh, fl;
+                f_exact(a[k].x, a[k].y, x.bh, x.bl, c[k], fh, fl);
+                if (fh > 0.f) red_fx(A.rowfx + R0 + k, (double)__fmul_rn(s, fh), fx.to_r);
+            }
         }
     }
 }
@@ -516,13 +528,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                     if (lane < DESC_WORDS) reinterpret_cast<int*>(&S.hdr[slot].d)[lane] = w0;
                     if (lane == 0) {
                         const uint32_t abytes = (uint32_t)nr * 16u;
-                        const uint32_t cbytes = s == 0 ? (uint32_t)IC * 12u : 0u;
+                        const uint32_t cbytes = s == 0 ? (uint32_t)IC * 8u : 0u;
                         mbar_expect(&S.full[slot], (uint32_t)__popc(need) * ROW_BYTES + 2u * abytes + cbytes);
                         bulk_copy(S.rowA[slot], A.rowA + ra, abytes, &S.full[slot]);
                         bulk_copy(S.rowG[slot], A.rowg + ra, abytes, &S.full[slot]);
                         if (s == 0) {
                             bulk_copy(S.colB[slot], A.B2 + col0, IC * 8u, &S.full[slot]);
-                            bulk_copy(S.colP[slot], A.Bp + col0, IC * 4u, &S.full[slot]);
                         }
                         StageHdr& hh = S.hdr[slot];
                         hh.sidx = s;
@@ -579,13 +590,15 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             const float2 b2 = S.colB[slot][wc];
             x.bh = b2.x;
             x.bl = b2.y;
-            x.bp = S.colP[slot][wc];
             x.colg = hs.d.col0 + wc;
+            x.bp = x.colg < A.n ? bound_up(x.bh) : -INFINITY;  // B'; no element of a padding column passes
             psi_acc = 0.0;
             cacc = 0.0;
             blk.gend = r0;  // no block continues into the item
         }
+        x.r0 = r0;
         x.ra = r0 + hs.sidx * SR;
+        x.marks = S.marks[warp];
         x.nr = min(SR, hs.d.rows - hs.sidx * SR);
         x.st = S.stage[slot] + wc;
         x.rA = S.rowA[slot];
@@ -599,18 +612,20 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) scan_rows<true>(x.st, x.rA, r, e, x.bh, x.bl, x.bp, blk.acc, blk.O, blk.any);
                 r = e;
-                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, fx, lane, false, psi_acc, cacc);
+                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, fx, false, psi_acc, cacc);
             }
         } else {
             // only the groups with a marked chunk (and a block that ends here)
             const uint32_t live = (x.nr >= SR ? 0xffu : (1u << ((x.nr + 3) >> 2)) - 1u) & chunks_of_rows(wrows);
             x.U = __reduce_or_sync(FULLMASK, chunk_marks(x.st, x.rA, x.bp) & live);
+            if (hs.sidx < MARK_STAGES && lane == 0) S.marks[warp][hs.sidx] = (uint8_t)x.U;
+            __syncwarp();
             int r = 0;
             if (blk.gend > x.ra) {  // the block open at the end of the last stage continues here
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) block_marked_rows(blk, x, 0, e);
                 if (blk.gend <= x.ra + x.nr && blk.need)
-                    finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
+                    finish_block<false>(A, blk, x, fx, true, psi_acc, cacc);
                 r = e;
             }
             while (r < x.nr) {
@@ -627,7 +642,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) block_marked_rows(blk, x, blk.gstart - x.ra, e);
                 if (blk.gend <= x.ra + x.nr && blk.need)
-                    finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
+                    finish_block<false>(A, blk, x, fx, true, psi_acc, cacc);
                 r = e;
             }
         }
