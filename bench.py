@@ -34,6 +34,9 @@ UNIT = "evals/s"
 
 WORKLOADS = {
     "large": dict(m=20000, n=20000, L=1000, d=512, gamma=1.0, mu=0.5),
+    # the large generator at a quarter of the size (C = 400 MB, still larger
+    # than L2): the case profiles are captured on
+    "large10k": dict(m=10000, n=10000, L=500, d=512, gamma=1.0, mu=0.5),
     "mid": dict(m=4000, n=4000, L=100, d=256, gamma=1.0, mu=0.1),
     "tiny": dict(m=200, n=200, L=10, d=10, gamma=1.0, mu=0.1),
 }
@@ -57,7 +60,8 @@ def _make_workload(name, seed, device):
     elif name == "mid":
         p = synth.mid(seed=seed, device=device)
     else:
-        p = synth.large(seed=seed, device=device)
+        c = WORKLOADS[name]
+        p = synth.large(seed=seed, m=c["m"], n=c["n"], L=c["L"], d=c["d"], device=device)
     C = torch.from_numpy(p.C).to(device)
     return p, C, cfg
 
@@ -177,7 +181,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     cfg = WORKLOADS[args.workload]
-    p = {"tiny": synth.tiny, "mid": synth.mid, "large": synth.large}[args.workload](seed=args.seed)
+    if args.workload in ("tiny", "mid"):
+        p = {"tiny": synth.tiny, "mid": synth.mid}[args.workload](seed=args.seed)
+    else:
+        p = synth.large(seed=args.seed, m=cfg["m"], n=cfg["n"], L=cfg["L"], d=cfg["d"])
     Cn = p.C
     k = 20 if args.workload != "tiny" else 5
     beta = np.sort(Cn, axis=0)[k - 1].astype(np.float64) + 1e-3
@@ -303,9 +310,9 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
             "config": {"workload": f"{args.workload}: m=n={cfg['m']}, L={cfg['L']} "
-                                   f"({'Zipf(1.1) sizes, min 2' if args.workload == 'large' else 'classes'}), "
+                                   f"({'Zipf(1.1) sizes, min 2' if args.workload.startswith('large') else 'classes'}), "
                                    f"d={cfg['d']}, gamma={cfg['gamma']}, mu={cfg['mu']}, dense evaluation",
-                       "l2": "inputs > L2 (C is 4mn bytes)" if args.workload == "large" else "C may be L2-resident",
+                       "l2": "inputs > L2 (C is 4mn bytes)" if args.workload.startswith("large") else "C may be L2-resident",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_kind": peak_kind,
@@ -315,7 +322,7 @@ def run_gpu(args):
             "cpu_baseline": cb,
             "e2e": {"value": k_e2e * world / (e2e_ms / 1000.0), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (m + n), "d2h_bytes_per_step": 8 * (1 + m + n)},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": 4 * args.steps,
             "clocks": clocks,
         }
         print(json.dumps(line))

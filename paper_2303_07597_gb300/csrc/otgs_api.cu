@@ -154,6 +154,9 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     rowfx = (unsigned long long*)dalloc(sizeof(unsigned long long) * (size_t)m, "row sums");
     colfx = (unsigned long long*)dalloc(sizeof(unsigned long long) * (size_t)n, "column sums");
     psipart = (double*)dalloc(sizeof(double) * (size_t)hp.nitems() * NWARPS, "psipart");
+    passb_cap = (int)std::min<int64_t>((int64_t)L * ntiles, 65536);
+    passb = (PassB*)dalloc(sizeof(PassB) * (size_t)passb_cap, "pass-B list");
+    if (!passb) return false;
     if (!rowA || !B2 || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !psipart) return false;
     if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
     {
@@ -189,6 +192,7 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.unit_need = need;
     e.unit_words = unit_words;
     e.rowfx = rowfx; e.colfx = colfx; e.psipart = psipart;
+    e.passb = passb; e.passb_cap = passb_cap;
     e.zt = snap ? zt : nullptr;
     e.ot = snap ? ot : nullptr;
     const double theta = prm.mu * prm.gamma;
@@ -247,6 +251,7 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
         cudaEventRecord(ev_pool[ev_used + 1], st);
         ev_used += 2;
     }
+    launch_passb(e, hp.max_group, n_sm, st);
 }
 
 // Dense evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.

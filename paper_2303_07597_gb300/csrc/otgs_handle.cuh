@@ -41,6 +41,8 @@ struct Handle {
     unsigned long long* rowfx = nullptr;  // fixed-point row sums of T
     unsigned long long* colfx = nullptr;  // fixed-point column sums of T
     double* psipart = nullptr;      // per (item, consumer warp) psi sums
+    PassB* passb = nullptr;         // blocks whose pass B the pass-B kernel does
+    int passb_cap = 0;
     int nred = 0;
     double* block_part = nullptr;
     unsigned* counter = nullptr;

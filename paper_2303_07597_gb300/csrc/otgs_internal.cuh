@@ -107,6 +107,7 @@ struct HostPlan {
     std::vector<int32_t> exec_order;  // item ids, largest first
     std::vector<ItemDesc> desc;       // work items in execution order
     int64_t nstages = 0;              // stages streamed by one dense evaluation
+    int32_t max_group = 0;            // rows of the largest group
     bool sorted_identity = true;      // labels already non-decreasing
     int npanels() const { return (int)prows.size(); }
     int nitems() const { return (int)item_panel.size(); }
@@ -130,8 +131,17 @@ struct EvalCtl {
     int work;           // work-item counter of the evaluation kernel
     unsigned amax;      // float bits of max_i [alpha_i hi]_+
     unsigned bmax;      // float bits of max_j [beta_j hi]_+
-    int pad;
+    int npassb;         // deferred pass-B blocks recorded (may exceed the list's capacity)
 };
+
+// A block (group rows [gstart, gend) x the 32 columns [colg0, colg0 + 32))
+// whose pass B (row sums t_ij = s_j [f_ij]_+) is left to the pass-B kernel
+// because its rows have left the evaluation kernel's ring.
+struct PassB {
+    int gstart, gend, colg0, pad;
+    float s[TW];  // shrink factor of each column's block (0: none)
+};
+constexpr int PASSB_ROWS = 128;  // rows of C per warp task of the pass-B kernel
 
 // Adds this warp's maxima of [alpha hi]_+ and [beta hi]_+ into ctl (all
 // lanes of the warp must call it).  Non-negative floats order as their bits.
@@ -202,6 +212,8 @@ struct EvalArgs {
     unsigned long long* rowfx;    // [m] fixed-point row sums of T (zeroed by the preparation kernel)
     unsigned long long* colfx;    // [n] fixed-point column sums of T
     double* psipart;   // [nitems * NWARPS]: per item and consumer warp, sum of psi
+    PassB* passb;      // deferred pass-B blocks (capacity passb_cap)
+    int32_t passb_cap;
     float* zt;         // snapshot outputs (L x ntiles*TW) or NULL
     float* ot;
     // regularisation scalars
@@ -250,6 +262,10 @@ struct TmaMaps {
 std::string make_tmaps(const float* C, int64_t ldc, int64_t m, int64_t n, TmaMaps& T);
 // evaluation kernel (otgs_stream.cu): persistent, n_ctas CTAs; a.ctl zeroed by launch_prep
 void launch_stream(const EvalArgs& a, const TmaMaps& T, int n_ctas, cudaStream_t st);
+// pass-B kernel (otgs_stream.cu): the blocks k_stream deferred; max_rows is
+// the largest group size (bounds the tasks per block).  Launch right after
+// launch_stream with the same arguments.
+void launch_passb(const EvalArgs& a, int max_rows, int n_sm, cudaStream_t st);
 size_t stream_smem_bytes();
 void launch_reduce(const ReduceArgs& a, cudaStream_t st);
 int reduce_blocks(int32_t m, int32_t n);

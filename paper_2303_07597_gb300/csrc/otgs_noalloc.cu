@@ -96,6 +96,8 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const size_t o_aeval = cv.take(8 * (size_t)m);
     const size_t o_rowfx = cv.take(8 * (size_t)m), o_colfx = cv.take(8 * (size_t)n);
     const size_t o_psipart = cv.take(8 * (size_t)hp.nitems() * NWARPS);
+    const int passb_cap = 4096;
+    const size_t o_passb = cv.take(sizeof(PassB) * (size_t)passb_cap);
     const int nred = reduce_blocks((int32_t)m, (int32_t)n);
     const size_t o_bpart = cv.take(8 * 4 * (size_t)nred), o_counter = cv.take(16), o_scal = cv.take(64);
     if (cv.off > OTGS_STATIC_SCRATCH_BYTES)
@@ -154,6 +156,8 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     ea.unit_words = (ntiles + 31) / 32;
     ea.rowfx = rowfx; ea.colfx = colfx;
     ea.psipart = (double*)(base + o_psipart);
+    ea.passb = (PassB*)(base + o_passb);
+    ea.passb_cap = passb_cap;
     const double theta = mu * gamma;
     ea.theta_hi = (float)theta;
     ea.theta_lo = (float)(theta - (double)ea.theta_hi);
@@ -169,6 +173,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
         if (!te.empty()) return set_err(OTGS_ECUDA, te);
     }
     launch_stream(ea, tm, std::min(CTAS_PER_SM * n_sm, hp.nitems()), st);
+    launch_passb(ea, hp.max_group, n_sm, st);
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.m = (int32_t)m; ra.n = (int32_t)n; ra.nitems = hp.nitems();

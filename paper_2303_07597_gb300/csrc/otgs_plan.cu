@@ -31,7 +31,10 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
         if (i > 0 && labels[i] < labels[i - 1]) hp.sorted_identity = false;
     }
     hp.goff.assign(L + 1, 0);
-    for (int32_t l = 0; l < L; l++) hp.goff[l + 1] = hp.goff[l] + (int32_t)cnt[l + 1];
+    for (int32_t l = 0; l < L; l++) {
+        hp.goff[l + 1] = hp.goff[l] + (int32_t)cnt[l + 1];
+        hp.max_group = std::max<int32_t>(hp.max_group, (int32_t)cnt[l + 1]);
+    }
     hp.perm.resize(m);
     hp.rgroup.resize(m);
     {

@@ -372,7 +372,7 @@ __device__ __forceinline__ void open_block(Block& b, const int4& g, bool need)
 // The block is complete: Eq. 5 for it, and pass B where s > 0.
 template <bool SNAP>
 __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, const FxScale& fx,
-                                             bool marks, double& psi_acc, double& cacc)
+                                             int lane, bool marks, double& psi_acc, double& cacc)
 {
     float s = 0.f;
     if (__any_sync(FULLMASK, b.any)) {
@@ -383,6 +383,25 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
     }
     if (SNAP) put_snap(A, b.gl, x.colg, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
     if (!__any_sync(FULLMASK, s > 0.f)) return;
+    if (b.gstart < x.ra) {
+        // some rows have left the ring: leave pass B to the pass-B kernel,
+        // which spreads it over the whole GPU (this warp would hold its CTA's
+        // ring while re-reading them)
+        int idx = 0;
+        if (lane == 0) idx = atomicAdd(&A.ctl->npassb, 1);
+        idx = __shfl_sync(FULLMASK, idx, 0);
+        if (idx < A.passb_cap) {
+            PassB& e = A.passb[idx];
+            e.s[lane] = s;
+            if (lane == 0) {
+                e.gstart = b.gstart;
+                e.gend = b.gend;
+                e.colg0 = x.colg - lane;
+            }
+            return;
+        }
+        // the list is full: pass B here
+    }
     // pass B: t_ij = s [f_ij]_+ into the row sums, over the block's rows that
     // can hold an f > 0 (marked chunks; every row on the snapshot walk),
     // four rows at a time
@@ -612,7 +631,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) scan_rows<true>(x.st, x.rA, r, e, x.bh, x.bl, x.bp, blk.acc, blk.O, blk.any);
                 r = e;
-                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, fx, false, psi_acc, cacc);
+                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, fx, lane, false, psi_acc, cacc);
             }
         } else {
             // only the groups with a marked chunk (and a block that ends here)
@@ -625,7 +644,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) block_marked_rows(blk, x, 0, e);
                 if (blk.gend <= x.ra + x.nr && blk.need)
-                    finish_block<false>(A, blk, x, fx, true, psi_acc, cacc);
+                    finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
                 r = e;
             }
             while (r < x.nr) {
@@ -642,7 +661,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) block_marked_rows(blk, x, blk.gstart - x.ra, e);
                 if (blk.gend <= x.ra + x.nr && blk.need)
-                    finish_block<false>(A, blk, x, fx, true, psi_acc, cacc);
+                    finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
                 r = e;
             }
         }
@@ -657,6 +676,57 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
         if (lane == 0) mbar_arrive(&S.empty[slot]);
         consumed++;
     }
+}
+
+// ================================================================ pass B
+// The blocks k_stream deferred: task u of warp w covers rows
+// [gstart + PASSB_ROWS k, ...) of block e = u / tasks_per_block; each lane
+// re-forms f for its column and adds its nonzero t_ij = s_j [f_ij]_+ to the
+// fixed-point row sum (integer adds: the total does not depend on order).
+__global__ void __launch_bounds__(256) k_passb(const EvalArgs A, int tasks_per_block)
+{
+    const int nb = min(A.ctl->npassb, A.passb_cap);
+    if (nb == 0) return;
+    const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t ntask = (int64_t)nb * tasks_per_block;
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < ntask; u += nw) {
+        const PassB& e = A.passb[u / tasks_per_block];
+        const int k = (int)(u % tasks_per_block);
+        const int R0 = e.gstart + k * PASSB_ROWS;
+        if (R0 >= e.gend) continue;  // warp-uniform
+        const int R1 = min(R0 + PASSB_ROWS, e.gend);
+        const float s = e.s[lane];
+        const int colg = e.colg0 + lane;
+        if (!__any_sync(FULLMASK, s > 0.f)) continue;
+        const bool real = colg < A.n;
+        const float2 b2 = real ? __ldg(A.B2 + colg) : make_float2(0.f, 0.f);
+        const float bp = real ? bound_up(b2.x) : -INFINITY;
+        for (int R = R0; R < R1; R += 4) {
+            float c[4];
+            float4 a[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const int Rq = min(R + q, R1 - 1);
+                c[q] = real ? __ldg(A.C + (int64_t)Rq * A.ldc + colg) : 0.f;
+                a[q] = __ldg(A.rowA + Rq);
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                if (R + q >= R1 || !(s > 0.f) || !maybe_pos(a[q].z, c[q], bp)) continue;
+                float fh, fl;
+                f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
+                if (fh > 0.f) red_fx(A.rowfx + R + q, (double)__fmul_rn(s, fh), fx.to_r);
+            }
+        }
+    }
+}
+
+void launch_passb(const EvalArgs& a, int max_rows, int n_sm, cudaStream_t st)
+{
+    const int tasks = max(1, (max_rows + PASSB_ROWS - 1) / PASSB_ROWS);
+    k_passb<<<4 * n_sm, 256, 0, st>>>(a, tasks);
 }
 
 size_t stream_smem_bytes() { return sizeof(Smem) + 1024; }
