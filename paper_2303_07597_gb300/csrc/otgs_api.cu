@@ -193,6 +193,7 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.unit_words = unit_words;
     e.rowfx = rowfx; e.colfx = colfx; e.psipart = psipart;
     e.passb = passb; e.passb_cap = passb_cap;
+    e.gate = eval_gate;
     e.zt = snap ? zt : nullptr;
     e.ot = snap ? ot : nullptr;
     const double theta = prm.mu * prm.gamma;
@@ -225,6 +226,7 @@ ReduceArgs Handle::reduce_args(const uint8_t* active, double* out_caller, double
     r.block_part = block_part;
     r.counter = counter;
     r.err = kerr;
+    r.gate = eval_gate;
     return r;
 }
 
@@ -273,13 +275,25 @@ bool Handle::eval_dense_core(const double* beta, double* out_caller, double* G_s
     eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(nullptr, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
-    stats_host.evals++;
-    stats_host.blocks_total += (int64_t)L * n;
-    stats_host.units_total += (int64_t)L * ntiles;
-    dense_units += nonempty_units();
-    stats_host.units_computed = dense_units;
-    stats_host.c_bytes += 4.0 * (double)m * (double)n;
+    if (!eval_gate) count_dense_evals(1);
     return ck(cudaGetLastError(), "eval launch");
+}
+
+void Handle::count_dense_evals(int64_t k)
+{
+    stats_host.evals += k;
+    stats_host.blocks_total += k * (int64_t)L * n;
+    stats_host.units_total += k * (int64_t)L * ntiles;
+    dense_units += k * nonempty_units();
+    stats_host.units_computed = dense_units;
+    stats_host.c_bytes += (double)k * 4.0 * (double)m * (double)n;
+}
+
+void Handle::count_screened_evals(int64_t k)
+{
+    stats_host.evals += k;
+    stats_host.blocks_total += k * (int64_t)L * n;
+    stats_host.units_total += k * (int64_t)L * ntiles;
 }
 
 int64_t Handle::nonempty_units() const

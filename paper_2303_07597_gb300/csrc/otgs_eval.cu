@@ -63,6 +63,7 @@ int reduce_blocks(int32_t m, int32_t n)
 
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
 {
+    if (R.gate && !*R.gate) return;  // a skipped solver trial
     __shared__ double sh[4][RED_WARPS];
     __shared__ bool last;
     const FxScale fx = fx_scale(R.ctl->amax, R.ctl->bmax, R.m, R.n, R.gamma);

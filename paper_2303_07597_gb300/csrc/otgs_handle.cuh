@@ -94,7 +94,12 @@ struct Handle {
     bool eval_screened_prepped(const double* beta, double* G_sorted, const double* dir,
                                double* out_caller = nullptr);
     Solver* solver = nullptr;
+    // While set (batched solver trials): evaluations are gated on this device
+    // flag and are counted in the statistics by the solver afterwards.
+    const int* eval_gate = nullptr;
     int64_t nonempty_units() const;
+    void count_dense_evals(int64_t k);     // statistics of k dense evaluations
+    void count_screened_evals(int64_t k);  // (block counts of screened ones come from the device)
 
     // screening (otgs_screen_host.cu)
     bool ensure_screen();

@@ -214,6 +214,7 @@ struct EvalArgs {
     double* psipart;   // [nitems * NWARPS]: per item and consumer warp, sum of psi
     PassB* passb;      // deferred pass-B blocks (capacity passb_cap)
     int32_t passb_cap;
+    const int* gate;   // NULL, or a device flag: 0 = skip this evaluation (batched solver trials)
     float* zt;         // snapshot outputs (L x ntiles*TW) or NULL
     float* ot;
     // regularisation scalars
@@ -244,6 +245,7 @@ struct ReduceArgs {
     double* block_part;   // scratch [4 * nblocks]
     unsigned int* counter;// scratch, zero on entry, reset by the last block
     const int* err;       // evaluation error word: non-zero makes D NaN
+    const int* gate;      // NULL, or a device flag: 0 = skip (batched solver trials)
 };
 
 // launchers (otgs_eval.cu)

@@ -54,6 +54,8 @@ struct ScreenArgs {
     const int32_t* pitem;
     const int32_t* pW;
     unsigned long long* count;  // [0] in N, [1] checked, [2] skipped, [3] units needed
+    int32_t nitems;
+    const int* gate;            // NULL, or a device flag: 0 = skip (batched solver trials)
 };
 
 __device__ __forceinline__ void atomic_max_pos(unsigned* addr, float v)
@@ -64,6 +66,7 @@ __device__ __forceinline__ void atomic_max_pos(unsigned* addr, float v)
 // Blocks [0, ceil(L/8)) take one group per warp; the rest take columns.
 __global__ void k_delta(const ScreenArgs S, int group_blocks)
 {
+    if (S.gate && !*S.gate) return;
     if ((int)blockIdx.x < group_blocks) {
         const int l = blockIdx.x * 8 + (threadIdx.x >> 5);
         const int lane = threadIdx.x & 31;
@@ -138,39 +141,77 @@ __device__ __forceinline__ float theta_skip(const ScreenArgs& S, int g)
     return __double2float_rd(__dsub_rn(S.theta, tau));
 }
 
-// One warp per unit (l, 32-column tile); lane = column in the tile.
-__global__ void k_screen(const ScreenArgs S)
+// theta_skip of every group (it depends on g_l and on the maxima from
+// k_delta); also clears the item-active flags that k_screen sets.
+__global__ void k_theta(const ScreenArgs S)
 {
-    const int64_t u = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (u >= (int64_t)S.L * S.ntiles) return;
-    const int l = (int)(u / S.ntiles), jt = (int)(u % S.ntiles);
-    const int g = S.goff[l + 1] - S.goff[l];
-    const int j = jt * TW + lane;
-    const bool valid = j < S.n && g > 0;
-    const uint32_t Nw = S.Nmask[u];
-    const bool inN = valid && ((Nw >> lane) & 1u);
-    bool skip = false;
-    if (valid && !inN) {
-        const float zbar = __fadd_ru(__fadd_ru(S.zt[(int64_t)l * S.ntiles * TW + j], S.gstat[4 * l]),
-                                     __fmul_ru(S.sg_ru[l], S.cstat[4 * j]));
-        skip = zbar <= theta_skip(S, g);
-    }
-    const uint32_t skipw = __ballot_sync(FULLMASK, skip);
-    const uint32_t needw = __ballot_sync(FULLMASK, valid && !skip);
-    const uint32_t validw = __ballot_sync(FULLMASK, valid);
-    if (lane == 0) {
-        S.skipmask[u] = skipw;
-        if (needw) {
-            atomicOr(S.unit_need + (int64_t)l * S.unit_words + (jt >> 5), 1u << (jt & 31));
-            const int p = S.gpanel[l];
-            S.item_active[S.pitem[p] + (jt * TW) / S.pW[p]] = 1;
+    if (S.gate && !*S.gate) return;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < S.L) S.gstat[4 * t + 3] = theta_skip(S, S.goff[t + 1] - S.goff[t]);
+    if (t < S.nitems) S.item_active[t] = 0;
+}
+
+// Alg. 2's skip test (Eq. 6, Lemma 2) for every block outside N.  A warp
+// takes the 32 units (l, 32-column tile) of one unit_need word, lane = column
+// in the tile, so each need word is written whole; statistics are summed per
+// block before one atomic add each.
+constexpr int SCREEN_WARPS = 8;
+
+__global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S)
+{
+    if (S.gate && !*S.gate) return;
+    __shared__ unsigned long long csum[SCREEN_WARPS][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t ntask = (int64_t)S.L * S.unit_words;
+    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    for (int64_t task = (int64_t)blockIdx.x * SCREEN_WARPS + warp; task < ntask;
+         task += (int64_t)gridDim.x * SCREEN_WARPS) {
+        const int l = (int)(task / S.unit_words), w = (int)(task % S.unit_words);
+        const int g = S.goff[l + 1] - S.goff[l];
+        const float th = S.gstat[4 * l + 3], npos = S.gstat[4 * l], sg = S.sg_ru[l];
+        const int p = g > 0 ? S.gpanel[l] : 0;
+        uint32_t needword = 0u;
+        const int jt1 = min(32 * w + 32, S.ntiles);
+        for (int jt = 32 * w; jt < jt1; jt++) {
+            const int64_t u = (int64_t)l * S.ntiles + jt;
+            const int j = jt * TW + lane;
+            const bool valid = j < S.n && g > 0;
+            const uint32_t Nw = S.Nmask[u];
+            const bool inN = valid && ((Nw >> lane) & 1u);
+            bool skip = false;
+            if (valid && !inN) {
+                const float zbar =
+                    __fadd_ru(__fadd_ru(S.zt[(int64_t)l * S.ntiles * TW + j], npos), __fmul_ru(sg, S.cstat[4 * j]));
+                skip = zbar <= th;
+            }
+            const uint32_t skipw = __ballot_sync(FULLMASK, skip);
+            const uint32_t needw = __ballot_sync(FULLMASK, valid && !skip);
+            const uint32_t validw = __ballot_sync(FULLMASK, valid);
+            if (lane == 0) {
+                S.skipmask[u] = skipw;
+                if (needw) {
+                    needword |= 1u << (jt & 31);
+                    S.item_active[S.pitem[p] + (jt * TW) / S.pW[p]] = 1;  // same value from every writer
+                }
+                c0 += __popc(Nw & validw);
+                c1 += __popc(~Nw & validw);
+                c2 += __popc(skipw);
+                c3 += needw ? 1ull : 0ull;
+            }
         }
-        unsigned long long c0 = __popc(Nw & validw), c1 = __popc(~Nw & validw), c2 = __popc(skipw);
-        if (c0) atomicAdd(S.count + 0, c0);
-        if (c1) atomicAdd(S.count + 1, c1);
-        if (c2) atomicAdd(S.count + 2, c2);
-        if (needw) atomicAdd(S.count + 3, 1ull);
+        if (lane == 0) S.unit_need[(int64_t)l * S.unit_words + w] = needword;
+    }
+    if (lane == 0) {
+        csum[warp][0] = c0;
+        csum[warp][1] = c1;
+        csum[warp][2] = c2;
+        csum[warp][3] = c3;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        unsigned long long v = 0;
+        for (int q = 0; q < SCREEN_WARPS; q++) v += csum[q][threadIdx.x];
+        if (v) atomicAdd(S.count + threadIdx.x, v);
     }
 }
 
@@ -218,6 +259,8 @@ ScreenArgs make_screen_args(Handle* h)
     s.Nmask = h->Nmask; s.skipmask = h->skipmask; s.unit_need = h->unit_need; s.item_active = h->item_active;
     s.gpanel = h->dp.gpanel; s.pitem = h->dp.pitem; s.pW = h->dp.pW;
     s.count = h->dcount;
+    s.nitems = h->hp.nitems();
+    s.gate = h->eval_gate;
     return s;
 }
 
@@ -280,7 +323,7 @@ static void launch_delta(Handle* h, const double* beta)
 {
     ScreenArgs s = make_screen_args(h);
     s.beta = beta;
-    cudaMemsetAsync(h->gmax, 0, sizeof(unsigned) * 4, h->st);
+    if (!h->eval_gate) cudaMemsetAsync(h->gmax, 0, sizeof(unsigned) * 4, h->st);  // else cleared by the trial gate
     const int gblocks = (h->L + 7) / 8;
     const int cblocks = (h->ntiles * TW + 255) / 256;
     k_delta<<<gblocks + cblocks, 256, 0, h->st>>>(s, gblocks);
@@ -322,19 +365,17 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     if (!ensure_screen()) return false;
     if (!snap_valid) return fail(OTGS_EINVAL, "screened evaluation without a snapshot");
     launch_delta(this, beta);
-    cudaMemsetAsync(unit_need, 0, sizeof(uint32_t) * (size_t)L * unit_words, st);
-    cudaMemsetAsync(item_active, 0, (size_t)hp.nitems(), st);
     ScreenArgs s = make_screen_args(this);
     s.beta = beta;
-    const int64_t units = (int64_t)L * ntiles;
-    k_screen<<<(unsigned)((units + 7) / 8), 256, 0, st>>>(s);
+    k_theta<<<(std::max<int>(L, hp.nitems()) + 255) / 256, 256, 0, st>>>(s);
+    const int64_t tasks = (int64_t)L * unit_words;
+    const int sblocks = (int)std::min<int64_t>((tasks + SCREEN_WARPS - 1) / SCREEN_WARPS, 16LL * n_sm);
+    k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s);
     EvalArgs e = eval_args(item_active, unit_need, false);
     eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
-    stats_host.evals++;
-    stats_host.blocks_total += (int64_t)L * n;
-    stats_host.units_total += (int64_t)L * ntiles;
+    if (!eval_gate) count_screened_evals(1);
     return ck(cudaGetLastError(), "screened eval launch");
 }
 

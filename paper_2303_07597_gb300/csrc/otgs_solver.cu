@@ -27,7 +27,7 @@ __global__ void k_trial(SolverState* S, const double* __restrict__ x, const doub
                         float4* rowA, float2* B2, double* alpha_eval, unsigned long long* rowfx,
                         unsigned long long* colfx, EvalCtl* ctl, int m, int n, int npad)
 {
-    if (S->done) return;  // the same for every thread
+    if (!S->go) return;  // the same for every thread
     const double t = S->t;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     float apos = 0.f, bpos = 0.f;
@@ -85,7 +85,7 @@ __device__ __forceinline__ void trace_put(SolverState* S, double F)
 // Line-search state machine (same rule as the oracle): scal = {D, Gt.d, ||Gt||_inf}.
 __global__ void k_linesearch(SolverState* S, const double* scal)
 {
-    if (S->done) return;
+    if (!S->go) return;
     S->evals++;
     S->accepted = 0;
     S->refresh = 0;
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_accept(SolverState* S, doubl
                                                           const double* Gt, double* Sv, double* Yv, int N,
                                                           double* pbase)
 {
-    if (!S->accepted) return;
+    if (!S->go || !S->accepted) return;
     const int head = S->head;
     double* s_new = Sv + (size_t)head * N;
     double* y_new = Yv + (size_t)head * N;
@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_gg(const double* G, int N, d
 __global__ void __launch_bounds__(SOLVER_THREADS) k_pairdots(const SolverState* S, const double* G, const double* Sv,
                                                             const double* Yv, int N, double* ppair)
 {
-    if (!S->accepted) return;
+    if (!S->go || !S->accepted) return;
     const int k = blockIdx.y, head = S->head;
     const double* s_new = Sv + (size_t)head * N;
     const double* y_new = Yv + (size_t)head * N;
@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_pairdots(const SolverState* 
 // the descent check, and the start of the next line search.
 __global__ void k_direction(SolverState* S, const double* pbase, const double* ppair, int nblocks, int start)
 {
-    if (S->done || (!start && !S->accepted)) return;
+    if (S->done || (!start && (!S->go || !S->accepted))) return;
     const int M = S->M;
     __shared__ double base[NBASE];
     __shared__ double pd[MAX_LBFGS_M][NPAIR];
@@ -304,7 +304,7 @@ __global__ void k_direction(SolverState* S, const double* pbase, const double* p
 __global__ void k_combine(const SolverState* S, const double* G, const double* Sv, const double* Yv, double* d,
                           int N, int M, int start)
 {
-    if (S->done || (!start && !S->accepted)) return;
+    if (S->done || (!start && (!S->go || !S->accepted))) return;
     const double cG = S->cG;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         double v = cG * G[i];
@@ -335,6 +335,24 @@ __global__ void k_start(SolverState* S, const double* scal)
 }
 
 __global__ void k_begin(SolverState* S) { S->t_begin = gtimer(); }
+
+// Opens a line-search trial: it runs only while the solve is not done and no
+// snapshot refresh is waiting for the host.  A running trial starts with a
+// cleared evaluation control word (and screening maxima).
+__global__ void k_gate(SolverState* S, EvalCtl* ctl, unsigned* gmax)
+{
+    const int go = !S->done && !S->refresh;
+    S->go = go;
+    if (!go) return;
+    ctl->work = 0;
+    ctl->amax = 0u;
+    ctl->bmax = 0u;
+    ctl->npassb = 0;
+    if (gmax)
+        for (int k = 0; k < 4; k++) gmax[k] = 0u;
+}
+
+__global__ void k_clear_refresh(SolverState* S) { S->refresh = 0; }
 
 // ------------------------------------------------------------------- host
 bool Solver::init(Handle* h_)
@@ -408,38 +426,57 @@ int Solver::run(double tol, int maxit)
     const int tb = (std::max((int)h->m, npad) + 255) / 256;
     const size_t hdr = offsetof(SolverState, tol);  // the int fields and the eval counter
     const long long max_trials = (long long)maxit * (LS_MAX_EVALS + 2) + 16;
-    for (long long trial = 0;; trial++) {
+    // Trials are queued TRIALS_PER_SYNC at a time; each opens with k_gate, so
+    // the ones queued after the solve ended, or after an iteration that asks
+    // for a snapshot refresh (Alg. 1, every r accepted iterations), do
+    // nothing.  The host then takes the snapshot at the accepted iterate and
+    // queues more.
+    h->eval_gate = &state->go;
+    bool ok = true;
+    while (ok) {
         if (!h->ck(cudaMemcpyAsync(hstate, state, hdr, cudaMemcpyDeviceToHost, st), "state D2H") ||
-            !h->ck(cudaStreamSynchronize(st), "solver sync"))
-            return h->last_code;
+            !h->ck(cudaStreamSynchronize(st), "solver sync")) {
+            ok = false;
+            break;
+        }
         if (hstate->done) break;
-        if (trial >= max_trials) {  // the device loop always ends first; this is a second guard
+        if (hstate->refresh) {
+            h->eval_gate = nullptr;
+            ok = h->snapshot_at(x, true, x + h->m, true, nullptr, nullptr, nullptr);
+            h->eval_gate = &state->go;
+            k_clear_refresh<<<1, 1, 0, st>>>(state);
+            if (!ok) break;
+        }
+        if (hstate->evals - 1 >= max_trials) {  // the device loop always ends first; this is a second guard
             h->fail(OTGS_ENOTCONV, "solver exceeded its trial budget");
             break;
         }
-        cudaMemsetAsync(h->ctl, 0, sizeof(EvalCtl), st);
-        k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->rowA, h->B2, h->alpha_eval, h->rowfx, h->colfx,
-                                    h->ctl, (int)h->m, (int)h->n, npad);
-        if (!eval_trial()) return h->last_code;
-        k_linesearch<<<1, 1, 0, st>>>(state, h->scal);
-        k_accept<<<nblk, SOLVER_THREADS, 0, st>>>(state, x, G, xt, Gt, Sv, Yv, N, pbase);
-        k_pairdots<<<dim3(nblk, M), SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, N, ppair);
-        if (h->prm.use_screening) {
-            if (!h->ck(cudaMemcpyAsync(hstate, state, hdr, cudaMemcpyDeviceToHost, st), "D2H") ||
-                !h->ck(cudaStreamSynchronize(st), "solver sync"))
-                return h->last_code;
-            if (hstate->refresh && !h->snapshot_at(x, true, x + h->m, true, nullptr, nullptr, nullptr))
-                return h->last_code;
+        for (int q = 0; q < TRIALS_PER_SYNC; q++) {
+            k_gate<<<1, 1, 0, st>>>(state, h->ctl, h->prm.use_screening ? h->gmax : nullptr);
+            k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->rowA, h->B2, h->alpha_eval, h->rowfx, h->colfx,
+                                        h->ctl, (int)h->m, (int)h->n, npad);
+            if (!eval_trial()) { ok = false; break; }
+            k_linesearch<<<1, 1, 0, st>>>(state, h->scal);
+            k_accept<<<nblk, SOLVER_THREADS, 0, st>>>(state, x, G, xt, Gt, Sv, Yv, N, pbase);
+            k_pairdots<<<dim3(nblk, M), SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, N, ppair);
+            k_direction<<<1, 128, 0, st>>>(state, pbase, ppair, nblk, 0);
+            k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 0);
         }
-        k_direction<<<1, 128, 0, st>>>(state, pbase, ppair, nblk, 0);
-        k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 0);
-        if (!h->ck(cudaGetLastError(), "solver launch")) return h->last_code;
+        if (ok && !h->ck(cudaGetLastError(), "solver launch")) ok = false;
     }
+    h->eval_gate = nullptr;
+    if (!ok) return h->last_code;
     if (!h->ck(cudaMemcpyAsync(hstate, state, sizeof(SolverState), cudaMemcpyDeviceToHost, st), "state D2H") ||
         !h->ck(cudaStreamSynchronize(st), "solver sync"))
         return h->last_code;
     h->stats_host.iters = hstate->iter;
     trace_len = std::min(hstate->iter + 1, TRACE_CAP);
+    // the trial evaluations (all but the first, counted when it was made)
+    const long long trials = hstate->evals - 1;
+    if (trials > 0) {
+        if (h->prm.use_screening) h->count_screened_evals(trials);
+        else h->count_dense_evals(trials);
+    }
     iters = hstate->iter;
     D = -hstate->F;
     ginf = hstate->ginf;

@@ -8,6 +8,7 @@ namespace otgs {
 constexpr int MAX_LBFGS_M = 32;
 constexpr int SOLVER_THREADS = 256;
 constexpr int TRACE_CAP = 1 << 16;  // objective trace entries kept per solve
+constexpr int TRIALS_PER_SYNC = 16;  // line-search trials queued between host checks
 // line search (same constants as the oracle)
 constexpr double LS_C1 = 1e-4;
 constexpr double LS_C2 = 0.9;
@@ -21,6 +22,7 @@ enum { PD_SNEW_Y = 0, PD_S_YNEW, PD_YNEW_Y, PD_G_S, PD_G_Y, NPAIR };
 struct SolverState {
     int status, done, iter, npairs, head, accepted, refresh, force_accept;
     int ls_evals, have_hi, M, r, screening, maxit;
+    int go;  // the current trial runs (set by the trial gate: not done, no refresh pending)
     long long evals;
     double tol, t, lo, Flo, dlo, hi, Fhi, dhi;
     double F, F0, dphi0, ginf, cG, budget_ns;

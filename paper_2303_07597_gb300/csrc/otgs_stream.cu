@@ -458,6 +458,7 @@ __device__ __forceinline__ void block_marked_rows(Block& b, const Ctx& x, int s,
 template <bool SNAP>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs A, const __grid_constant__ TmaMaps T)
 {
+    if (A.gate && !*A.gate) return;  // a skipped solver trial
     extern __shared__ unsigned char smem_raw[];
     // TMA destinations must be 128-byte aligned: align the layout to 1 KB
     Smem& S = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -685,6 +686,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
 // fixed-point row sum (integer adds: the total does not depend on order).
 __global__ void __launch_bounds__(256) k_passb(const EvalArgs A, int tasks_per_block)
 {
+    if (A.gate && !*A.gate) return;
     const int nb = min(A.ctl->npassb, A.passb_cap);
     if (nb == 0) return;
     const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);

@@ -98,3 +98,6 @@ def test_objective_trace_follows_the_solve():
     assert np.all(np.diff(t) >= 0.0) and t[0] >= 0.0
     assert np.all(np.diff(ev) >= 1) and ev[0] == 1
     assert D[-1] == sol["D"]
+    # every evaluation of the (dense) solve is counted once: the start point
+    # and each line-search trial the device ran
+    assert s.stats()["evals"] == ev[-1]
