@@ -253,7 +253,7 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
         cudaEventRecord(ev_pool[ev_used + 1], st);
         ev_used += 2;
     }
-    launch_passb(e, hp.max_group, n_sm, st);
+    launch_passb(e, n_sm, st);
 }
 
 // Dense evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.

@@ -60,6 +60,7 @@ struct Handle {
     uint32_t* skipmask = nullptr; // last screened evaluation's skip decisions, same layout
     uint32_t* unit_need = nullptr;// L x unit_words
     uint8_t* item_active = nullptr;
+    uint8_t* stage_m8 = nullptr;  // [nstages][STAGE_ROWS]: per row, the needed tiles of its item
     float* gstat = nullptr;       // per group: npos, nabs, nneg, theta_skip
     float* cstat = nullptr;       // per column: dbp, dbabs, dbneg
     unsigned* gmax = nullptr;     // float bits: max|alpha|, max|beta|, max|alpha~|, max|beta~|

@@ -28,10 +28,21 @@ constexpr int STAGE_ROWS = 32;
 constexpr int NSTAGES = 3;
 // CTAs of the evaluation kernel per SM (each with its own ring).
 constexpr int CTAS_PER_SM = 2;
-// Consecutive groups are packed into "panels" of whole groups up to
-// PANEL_ROWS rows; a larger group is a panel of its own.  A work item is
-// (panel, column chunk of ITEM_COLS).
-constexpr int PANEL_ROWS = 512;
+// Consecutive groups are packed into "panels" of whole groups up to a panel
+// height; a larger group is a panel of its own.  A work item is (panel,
+// column chunk of ITEM_COLS).  The height is m * ceil(n / ITEM_COLS) /
+// TARGET_ITEMS clamped to [MIN_PANEL_ROWS, MAX_PANEL_ROWS]: large problems get
+// tall panels (long TMA streams per item), small ones enough items to fill
+// every SM.
+constexpr int MAX_PANEL_ROWS = 512;
+constexpr int MIN_PANEL_ROWS = 32;
+constexpr int64_t TARGET_ITEMS = 2048;
+inline int32_t panel_rows(int64_t m, int64_t n)
+{
+    const int64_t nch = (n + ITEM_COLS - 1) / ITEM_COLS;
+    const int64_t h = (m * nch + TARGET_ITEMS - 1) / TARGET_ITEMS;
+    return (int32_t)(h < MIN_PANEL_ROWS ? MIN_PANEL_ROWS : (h > MAX_PANEL_ROWS ? MAX_PANEL_ROWS : h));
+}
 
 // Columns of the per-column float-pair split of beta, padded to whole items.
 inline int32_t padded_cols(int64_t n) { return (int32_t)((n + ITEM_COLS - 1) / ITEM_COLS * ITEM_COLS); }
@@ -82,7 +93,7 @@ struct ItemDesc {
     int col0;   // first column (multiple of ITEM_COLS)
     int ncols;  // columns of C in the item (<= ITEM_COLS)
     int nst;    // stages: ceil(rows / STAGE_ROWS)
-    int pad;
+    int sbase;  // first stage of the item in execution order (index into per-stage tables)
 };
 
 // ------------------------------------------------------------------ host plan
@@ -138,10 +149,10 @@ struct EvalCtl {
 // whose pass B (row sums t_ij = s_j [f_ij]_+) is left to the pass-B kernel
 // because its rows have left the evaluation kernel's ring.
 struct PassB {
-    int gstart, gend, colg0, pad;
+    int gstart, gend, colg0, pad;  // rows [gstart, gend): a piece of at most PASSB_PIECE rows of the block
     float s[TW];  // shrink factor of each column's block (0: none)
 };
-constexpr int PASSB_ROWS = 128;  // rows of C per warp task of the pass-B kernel
+constexpr int PASSB_PIECE = 256;
 
 // Adds this warp's maxima of [alpha hi]_+ and [beta hi]_+ into ctl (all
 // lanes of the warp must call it).  Non-negative floats order as their bits.
@@ -208,6 +219,7 @@ struct EvalArgs {
     const ItemDesc* desc;
     const uint8_t* item_active;   // per item id: 1 if it has a unit to evaluate (screened), else NULL
     const uint32_t* unit_need;    // L x unit_words bitmask of units to evaluate, NULL = all
+    const uint8_t* stage_m8;      // screened: [nstages][STAGE_ROWS] per row, bit w = tile w of its item needed
     int32_t unit_words;           // ceil(ntiles / 32)
     unsigned long long* rowfx;    // [m] fixed-point row sums of T (zeroed by the preparation kernel)
     unsigned long long* colfx;    // [n] fixed-point column sums of T
@@ -254,20 +266,24 @@ struct ReduceArgs {
 void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, const double* beta,
                  int32_t m, int32_t n, float4* rowA, float2* B2, double* alpha_s_out,
                  unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl, cudaStream_t st);
-// TMA descriptors of C: box k is 2^k rows x ITEM_COLS columns (k = 0..TMA_BOXES-1).
+// TMA descriptors of C: box[k] is 2^k rows x ITEM_COLS columns, tile[k] is
+// 2^k rows x TW columns (k = 0..TMA_BOXES-1).
 constexpr int TMA_BOXES = 6;
 static_assert((1 << (TMA_BOXES - 1)) == STAGE_ROWS, "boxes must compose any stage height");
 struct TmaMaps {
     CUtensorMap box[TMA_BOXES];
+    CUtensorMap tile[TMA_BOXES];
 };
 // Encodes the maps for C (m x n, row stride ldc floats); "" on success.
 std::string make_tmaps(const float* C, int64_t ldc, int64_t m, int64_t n, TmaMaps& T);
 // evaluation kernel (otgs_stream.cu): persistent, n_ctas CTAs; a.ctl zeroed by launch_prep
 void launch_stream(const EvalArgs& a, const TmaMaps& T, int n_ctas, cudaStream_t st);
-// pass-B kernel (otgs_stream.cu): the blocks k_stream deferred; max_rows is
-// the largest group size (bounds the tasks per block).  Launch right after
-// launch_stream with the same arguments.
-void launch_passb(const EvalArgs& a, int max_rows, int n_sm, cudaStream_t st);
+// stage-mask kernel (otgs_stream.cu), screened evaluations: fills
+// a.stage_m8 from a.unit_need for the active items.  Launch before launch_stream.
+void launch_stage_masks(const EvalArgs& a, cudaStream_t st);
+// pass-B kernel (otgs_stream.cu): the blocks k_stream deferred.  Launch right
+// after launch_stream with the same arguments.
+void launch_passb(const EvalArgs& a, int n_sm, cudaStream_t st);
 size_t stream_smem_bytes();
 void launch_reduce(const ReduceArgs& a, cudaStream_t st);
 int reduce_blocks(int32_t m, int32_t n);

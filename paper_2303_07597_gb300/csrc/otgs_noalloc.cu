@@ -173,7 +173,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
         if (!te.empty()) return set_err(OTGS_ECUDA, te);
     }
     launch_stream(ea, tm, std::min(CTAS_PER_SM * n_sm, hp.nitems()), st);
-    launch_passb(ea, hp.max_group, n_sm, st);
+    launch_passb(ea, n_sm, st);
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.m = (int32_t)m; ra.n = (int32_t)n; ra.nitems = hp.nitems();

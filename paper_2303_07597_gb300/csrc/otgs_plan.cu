@@ -4,7 +4,7 @@
 // target column j (Sec. 2.3, O(|L| n g) per evaluation).  On the GPU, rows are
 // visited in class-sorted order, so every group is a contiguous range of
 // sorted rows.  Consecutive groups are packed into panels (row ranges of
-// whole groups, up to PANEL_ROWS rows; a larger group is a panel of its own),
+// whole groups, up to panel_rows(m, n) rows; a larger group is a panel of its own),
 // and a work item is (panel, column chunk of ITEM_COLS columns).  Inside an
 // item, each column's blocks are evaluated by one thread walking down the
 // rows, so no block is ever split between threads; items are handed out
@@ -49,7 +49,8 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
         }
 
     // panels: runs of consecutive non-empty groups in label order, closed
-    // before they would exceed PANEL_ROWS rows
+    // before they would exceed the panel height
+    const int32_t PANEL_ROWS = panel_rows(m, n);
     hp.gpanel.assign(L, -1);
     int32_t cur0 = -1, cur_rows = 0;
     auto flush = [&]() {
@@ -103,9 +104,11 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
         d.col0 = cc * ITEM_COLS;
         d.ncols = (int)std::min<int64_t>(ITEM_COLS, n - (int64_t)d.col0);
         d.nst = (d.rows + STAGE_ROWS - 1) / STAGE_ROWS;
+        d.sbase = (int)hp.nstages;
         hp.nstages += d.nst;
         hp.desc[k] = d;
     }
+    if (hp.nstages > INT32_MAX / STAGE_ROWS) return "m x n too large for the stage tables";
     return "";
 }
 

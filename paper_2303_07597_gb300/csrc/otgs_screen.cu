@@ -73,8 +73,9 @@ __global__ void k_delta(const ScreenArgs S, int group_blocks)
         if (l >= S.L) return;
         const int r0 = S.goff[l], r1 = S.goff[l + 1];
         float pu = 0.f, a2 = 0.f, n2 = 0.f, amax = 0.f, asmax = 0.f;
-        for (int r = r0 + lane; r < r1; r += 32) {
-            const double al = S.alpha[r], as = S.alpha_s[r];
+        // each lane visits rows r0 + lane, r0 + lane + 32, ... in that order
+        // (the order the sums are defined in); loads four at a time
+        auto add = [&](double al, double as) {
             const float du = __double2float_ru(__dsub_ru(al, as));
             const float dp = fmaxf(du, 0.f);
             pu = __fadd_ru(pu, __fmul_ru(dp, dp));
@@ -84,7 +85,19 @@ __global__ void k_delta(const ScreenArgs S, int group_blocks)
             n2 = __fadd_rn(n2, __fmul_rn(dn, dn));
             amax = fmaxf(amax, __double2float_ru(fabs(al)));
             asmax = fmaxf(asmax, __double2float_ru(fabs(as)));
+        };
+        int r = r0 + lane;
+        for (; r + 96 < r1; r += 128) {
+            double al[4], as[4];
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                al[q] = S.alpha[r + 32 * q];
+                as[q] = S.alpha_s[r + 32 * q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; q++) add(al[q], as[q]);
         }
+        for (; r < r1; r += 32) add(S.alpha[r], S.alpha_s[r]);
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
             pu = __fadd_ru(pu, __shfl_xor_sync(FULLMASK, pu, off));
@@ -276,6 +289,8 @@ bool Handle::ensure_screen()
     skipmask = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * ntiles, "skipmask");
     unit_need = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * unit_words, "unit_need");
     item_active = (uint8_t*)dalloc((size_t)hp.nitems(), "item_active");
+    stage_m8 = (uint8_t*)dalloc((size_t)hp.nstages * STAGE_ROWS, "stage masks");
+    if (!stage_m8) return false;
     gstat = (float*)dalloc(sizeof(float) * 4 * (size_t)L, "gstat");
     cstat = (float*)dalloc(sizeof(float) * 4 * ldz, "cstat");
     gmax = (unsigned*)dalloc(sizeof(unsigned) * 8, "gmax");
@@ -372,6 +387,8 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     const int sblocks = (int)std::min<int64_t>((tasks + SCREEN_WARPS - 1) / SCREEN_WARPS, 16LL * n_sm);
     k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s);
     EvalArgs e = eval_args(item_active, unit_need, false);
+    e.stage_m8 = stage_m8;
+    launch_stage_masks(e, st);
     eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);

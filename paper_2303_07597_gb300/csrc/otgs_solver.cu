@@ -209,23 +209,35 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_pairdots(const SolverState* 
 
 // Sum block partials in block order; then the two-loop recursion on scalars,
 // the descent check, and the start of the next line search.
-__global__ void k_direction(SolverState* S, const double* pbase, const double* ppair, int nblocks, int start)
+__global__ void __launch_bounds__(SOLVER_THREADS) k_direction(SolverState* S, const double* pbase, const double* ppair,
+                                                             int nblocks, int start)
 {
     if (S->done || (!start && (!S->go || !S->accepted))) return;
     const int M = S->M;
     __shared__ double base[NBASE];
     __shared__ double pd[MAX_LBFGS_M][NPAIR];
-    for (int q = threadIdx.x; q < NBASE; q += blockDim.x) {
-        double v = 0.0;
-        for (int b = 0; b < nblocks; b++) v += pbase[(size_t)b * NBASE + q];
-        base[q] = v;
+    // the curvature matrices, so that the serial recursion below reads shared memory
+    __shared__ double SY[MAX_LBFGS_M * MAX_LBFGS_M], YY[MAX_LBFGS_M * MAX_LBFGS_M];
+    for (int q = threadIdx.x; q < M * M; q += blockDim.x) {
+        SY[q] = S->SY[q];
+        YY[q] = S->YY[q];
     }
-    for (int q = threadIdx.x; q < M * NPAIR; q += blockDim.x) {
-        const int k = q / NPAIR, c = q % NPAIR;
+    // one warp per quantity: lane-strided partial sums, then a fixed xor tree
+    const int lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+    for (int q = threadIdx.x >> 5; q < NBASE + M * NPAIR; q += nwarps) {
         double v = 0.0;
-        if (!start)
-            for (int b = 0; b < nblocks; b++) v += ppair[((size_t)k * nblocks + b) * NPAIR + c];
-        pd[k][c] = v;
+        if (q < NBASE) {
+            for (int b = lane; b < nblocks; b += 32) v += pbase[(size_t)b * NBASE + q];
+        } else if (!start) {
+            const int k = (q - NBASE) / NPAIR, c = (q - NBASE) % NPAIR;
+            for (int b = lane; b < nblocks; b += 32) v += ppair[((size_t)k * nblocks + b) * NPAIR + c];
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
+        if (lane == 0) {
+            if (q < NBASE) base[q] = v;
+            else pd[(q - NBASE) / NPAIR][(q - NBASE) % NPAIR] = v;
+        }
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -235,13 +247,19 @@ __global__ void k_direction(SolverState* S, const double* pbase, const double* p
         const double sy = base[DOT_SY];
         if (sy > 1e-12 * sqrt(base[DOT_SS] * base[DOT_YY])) {
             for (int k = 0; k < M; k++) {
-                S->SY[head * M + k] = pd[k][PD_SNEW_Y];  // s_head . y_k
-                S->SY[k * M + head] = pd[k][PD_S_YNEW];  // s_k . y_head
-                S->YY[head * M + k] = pd[k][PD_YNEW_Y];
-                S->YY[k * M + head] = pd[k][PD_YNEW_Y];
+                SY[head * M + k] = pd[k][PD_SNEW_Y];  // s_head . y_k
+                SY[k * M + head] = pd[k][PD_S_YNEW];  // s_k . y_head
+                YY[head * M + k] = pd[k][PD_YNEW_Y];
+                YY[k * M + head] = pd[k][PD_YNEW_Y];
             }
-            S->SY[head * M + head] = sy;
-            S->YY[head * M + head] = base[DOT_YY];
+            SY[head * M + head] = sy;
+            YY[head * M + head] = base[DOT_YY];
+            for (int k = 0; k < M; k++) {
+                S->SY[head * M + k] = SY[head * M + k];
+                S->SY[k * M + head] = SY[k * M + head];
+                S->YY[head * M + k] = YY[head * M + k];
+                S->YY[k * M + head] = YY[k * M + head];
+            }
             S->head = (head + 1) % M;
             if (S->npairs < M) S->npairs++;
         } else if (S->npairs == M) {
@@ -256,22 +274,22 @@ __global__ void k_direction(SolverState* S, const double* pbase, const double* p
     for (int u = np - 1; u >= 0; u--) {
         const int i = idx[u];
         double sq = pd[i][PD_G_S];
-        for (int v = u + 1; v < np; v++) sq -= a[v] * S->SY[i * M + idx[v]];
-        a[u] = sq / S->SY[i * M + i];
+        for (int v = u + 1; v < np; v++) sq -= a[v] * SY[i * M + idx[v]];
+        a[u] = sq / SY[i * M + i];
     }
     double h0 = 1.0;
     if (np > 0) {
         const int nw = idx[np - 1];
-        h0 = S->SY[nw * M + nw] / S->YY[nw * M + nw];
+        h0 = SY[nw * M + nw] / YY[nw * M + nw];
     }
     // second loop, oldest to newest: b_i = rho_i y_i.r, r = h0 q + sum_{older}(a_k - b_k) s_k
     for (int u = 0; u < np; u++) {
         const int i = idx[u];
         double yq = pd[i][PD_G_Y];
-        for (int v = 0; v < np; v++) yq -= a[v] * S->YY[i * M + idx[v]];
+        for (int v = 0; v < np; v++) yq -= a[v] * YY[i * M + idx[v]];
         double yr = h0 * yq;
-        for (int v = 0; v < u; v++) yr += (a[v] - b[v]) * S->SY[idx[v] * M + i];
-        b[u] = yr / S->SY[i * M + i];
+        for (int v = 0; v < u; v++) yr += (a[v] - b[v]) * SY[idx[v] * M + i];
+        b[u] = yr / SY[i * M + i];
     }
     // d = -(h0 q + sum (a - b) s) = -h0 G + h0 sum a y - sum (a - b) s
     double cG = -h0;
@@ -360,7 +378,8 @@ bool Solver::init(Handle* h_)
     h = h_;
     N = (int)(h->m + h->n);
     M = h->prm.lbfgs_m;
-    nblk = 2 * 152;
+    // blocks of the vector kernels: enough to cover N once (up to two per SM)
+    nblk = (int)std::min<int64_t>(2 * std::max(1, h->n_sm), (N + SOLVER_THREADS - 1) / SOLVER_THREADS);
     auto al = [&](size_t bytes, const char* w) { return h->dalloc(bytes, w); };
     state = (SolverState*)al(sizeof(SolverState), "solver state");
     x = (double*)al(sizeof(double) * N, "x");
@@ -420,7 +439,7 @@ int Solver::run(double tol, int maxit)
     }
     k_start<<<1, 1, 0, st>>>(state, h->scal);
     k_gg<<<nblk, SOLVER_THREADS, 0, st>>>(G, N, pbase);
-    k_direction<<<1, 128, 0, st>>>(state, pbase, ppair, nblk, 1);
+    k_direction<<<1, SOLVER_THREADS, 0, st>>>(state, pbase, ppair, nblk, 1);
     k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 1);
     const int npad = padded_cols(h->n);
     const int tb = (std::max((int)h->m, npad) + 255) / 256;
@@ -459,7 +478,7 @@ int Solver::run(double tol, int maxit)
             k_linesearch<<<1, 1, 0, st>>>(state, h->scal);
             k_accept<<<nblk, SOLVER_THREADS, 0, st>>>(state, x, G, xt, Gt, Sv, Yv, N, pbase);
             k_pairdots<<<dim3(nblk, M), SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, N, ppair);
-            k_direction<<<1, 128, 0, st>>>(state, pbase, ppair, nblk, 0);
+            k_direction<<<1, SOLVER_THREADS, 0, st>>>(state, pbase, ppair, nblk, 0);
             k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 0);
         }
         if (ok && !h->ck(cudaGetLastError(), "solver launch")) ok = false;

@@ -56,19 +56,24 @@ static_assert(SR == 32, "the producer maps one lane to each row of a stage");
 // Stages of an item whose marked chunks a warp remembers for pass B (items of
 // up to MARK_STAGES * STAGE_ROWS rows; rows beyond are all visited).
 constexpr int MARK_STAGES = 256;
+// A block with s > 0 whose rows reach more than this many rows before the
+// current stage leaves its pass B to the pass-B kernel (re-reading them here
+// would hold the CTA's ring).
+constexpr int PASSB_INLINE_ROWS = 0;
 
-enum : int { H_FIRST = 1, H_LAST = 2, H_TERM = 4 };
+enum : int { H_FIRST = 1, H_TERM = 4 };
 
 // What the consumers need about a stage, written by the producer.
 struct StageHdr {
     ItemDesc d;
     int sidx;     // stage index within the item
     int flags;
-    int pad[2];
+    int tiled;    // 0: rows of ITEM_COLS ([row][IC]); 1: per warp tile ([warp][row][TW])
+    int pad;
 };
 
 struct Smem {
-    float stage[NSTAGES][SR * IC];   // NSTAGES x 32 KB; stage row r at [r * IC]
+    float stage[NSTAGES][SR * IC];   // NSTAGES x 32 KB; see StageHdr::tiled
     float4 rowA[NSTAGES][SR];        // (alpha hi, alpha lo, A', 0) of the stage's rows
     int4 rowG[NSTAGES][SR];          // (group, first row, end row, 0) of the stage's rows
     float2 colB[NSTAGES][IC];        // item's first stage: (beta hi, lo) of its columns
@@ -157,6 +162,22 @@ __device__ __forceinline__ void tma_rows(const TmaMaps& T, float* dst, int x, in
     for (int k = TMA_BOXES - 1; k >= 0; k--)
         if (rows & (1 << k)) {
             tma_box(T, k, dst + off * IC, x, y + off, bar);
+            off += 1 << k;
+        }
+}
+
+// The same for one 32-column tile: rows of TW floats at dst + r * TW.
+__device__ __forceinline__ void tma_tile_rows(const TmaMaps& T, float* dst, int x, int y, int rows, uint64_t* bar)
+{
+    int off = 0;
+#pragma unroll
+    for (int k = TMA_BOXES - 1; k >= 0; k--)
+        if (rows & (1 << k)) {
+            asm volatile(
+                "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+                "[%4];" ::"r"(su32(dst + off * TW)),
+                "l"(reinterpret_cast<uint64_t>(&T.tile[k])), "r"(x), "r"(y + off), "r"(su32(bar))
+                : "memory");
             off += 1 << k;
         }
 }
@@ -290,16 +311,17 @@ __device__ __forceinline__ void scan_rows(const float* st, const float4* rA, int
 // Bit q set: chunk q (rows [4q, 4q + 4)) of the stage may hold an f > 0 in
 // this lane's column.  Rows past the stage's end hold stale data and are
 // masked by the caller.
+template <int RS>
 __device__ __forceinline__ uint32_t chunk_marks(const float* st, const float4* rA, float bp)
 {
     uint32_t cm = 0u;
 #pragma unroll
     for (int q = 0; q < SR / 4; q++) {
         const int r = 4 * q;
-        const float x0 = __fsub_rn(rA[r + 0].z, st[(r + 0) * IC]);
-        const float x1 = __fsub_rn(rA[r + 1].z, st[(r + 1) * IC]);
-        const float x2 = __fsub_rn(rA[r + 2].z, st[(r + 2) * IC]);
-        const float x3 = __fsub_rn(rA[r + 3].z, st[(r + 3) * IC]);
+        const float x0 = __fsub_rn(rA[r + 0].z, st[(r + 0) * RS]);
+        const float x1 = __fsub_rn(rA[r + 1].z, st[(r + 1) * RS]);
+        const float x2 = __fsub_rn(rA[r + 2].z, st[(r + 2) * RS]);
+        const float x3 = __fsub_rn(rA[r + 3].z, st[(r + 3) * RS]);
         const float mx = fmaxf(fmaxf(x0, x1), fmaxf(x2, x3));  // a NaN operand yields the other one
         if (__fadd_rn(mx, bp) > 0.f) cm |= 1u << q;
     }
@@ -349,6 +371,7 @@ struct Block {
 // Per-lane constants of the current item and the stage being consumed.
 struct Ctx {
     const float* st;   // stage, offset to this lane's column
+    int rs;            // the stage's row stride (floats)
     const float4* rA;  // stage's alpha records
     int ra, nr;        // first sorted row of the stage, rows in it
     float bh, bl, bp;  // beta hi, lo, B' of this lane's column
@@ -383,24 +406,37 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
     }
     if (SNAP) put_snap(A, b.gl, x.colg, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
     if (!__any_sync(FULLMASK, s > 0.f)) return;
-    if (b.gstart < x.ra) {
-        // some rows have left the ring: leave pass B to the pass-B kernel,
+    if (b.gstart < x.ra - PASSB_INLINE_ROWS) {
+        // many rows have left the ring: leave pass B to the pass-B kernel,
         // which spreads it over the whole GPU (this warp would hold its CTA's
         // ring while re-reading them)
+        // (in pieces of at most PASSB_PIECE rows, so that one long block does
+        // not set the pass-B kernel's duration)
+        const int npieces = (b.gend - b.gstart + PASSB_PIECE - 1) / PASSB_PIECE;
         int idx = 0;
-        if (lane == 0) idx = atomicAdd(&A.ctl->npassb, 1);
+        if (lane == 0) idx = atomicAdd(&A.ctl->npassb, npieces);
         idx = __shfl_sync(FULLMASK, idx, 0);
-        if (idx < A.passb_cap) {
-            PassB& e = A.passb[idx];
-            e.s[lane] = s;
-            if (lane == 0) {
-                e.gstart = b.gstart;
-                e.gend = b.gend;
-                e.colg0 = x.colg - lane;
+        if (idx + npieces <= A.passb_cap) {
+            for (int k = 0; k < npieces; k++) {
+                PassB& e = A.passb[idx + k];
+                e.s[lane] = s;
+                if (lane == 0) {
+                    e.gstart = b.gstart + k * PASSB_PIECE;
+                    e.gend = min(b.gstart + (k + 1) * PASSB_PIECE, b.gend);
+                    e.colg0 = x.colg - lane;
+                }
             }
             return;
         }
-        // the list is full: pass B here
+        // the list is full: the slots taken that fit are left empty, pass B here
+        for (int k = 0; idx + k < A.passb_cap && k < npieces; k++) {
+            PassB& e = A.passb[idx + k];
+            e.s[lane] = 0.f;
+            if (lane == 0) {
+                e.gstart = 0;
+                e.gend = 0;
+            }
+        }
     }
     // pass B: t_ij = s [f_ij]_+ into the row sums, over the block's rows that
     // can hold an f > 0 (marked chunks; every row on the snapshot walk),
@@ -422,7 +458,7 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
             for (int k = 0; k < 4; k++) {
                 const int R = min(R0 + k, R1 - 1);
                 if (here) {
-                    c[k] = x.st[(R - base) * IC];
+                    c[k] = x.st[(R - base) * x.rs];
                     a[k] = x.rA[R - base];
                 } else {  // the row's stage has left the ring: re-read it (from L2)
                     c[k] = x.colg < A.n ? __ldg(A.C + (int64_t)R * A.ldc + x.colg) : 0.f;
@@ -448,7 +484,7 @@ __device__ __forceinline__ void block_marked_rows(Block& b, const Ctx& x, int s,
         const int q = __ffs(qm) - 1;
         qm &= qm - 1u;
         const int r1 = min(4 * q + 4, e);
-        for (int r = max(4 * q, s); r < r1; r++) elem_exact(x.rA[r], x.st[r * IC], x.bh, x.bl, x.bp, b.acc, b.any);
+        for (int r = max(4 * q, s); r < r1; r++) elem_exact(x.rA[r], x.st[r * x.rs], x.bh, x.bl, x.bp, b.acc, b.any);
     }
 }
 
@@ -521,20 +557,20 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             if (bcast(a0)) {
                 const int r0 = __shfl_sync(FULLMASK, w0, 2), rows = __shfl_sync(FULLMASK, w0, 3);
                 const int col0 = __shfl_sync(FULLMASK, w0, 4), nst = __shfl_sync(FULLMASK, w0, 6);
-                const int tile0 = col0 / TW;  // a multiple of NWARPS: the item's tiles share one mask word
+                const int sbase = __shfl_sync(FULLMASK, w0, 7);
+                // screened: this lane's row's needed tiles, one stage ahead
+                uint32_t m8n = screened ? (uint32_t)__ldg(A.stage_m8 + (int64_t)sbase * SR + lane) : 0xffu;
+                bool first = true;  // no stage of this item issued yet
                 for (int s = 0; s < nst; s++) {
                     const int ra = r0 + s * SR;
                     const int nr = min(SR, rows - s * SR);
                     uint32_t m8 = 0xffu;  // this lane's row: bit w = warp w evaluates its block
                     uint32_t need = nr == 32 ? FULLMASK : ((1u << nr) - 1u);
                     if (screened) {
-                        m8 = 0u;
-                        if (lane < nr) {
-                            const int l = __ldg(&A.rowg[ra + lane].x);
-                            const uint32_t word = __ldg(A.unit_need + (int64_t)l * A.unit_words + (tile0 >> 5));
-                            m8 = (word >> (tile0 & 31)) & 0xffu;
-                        }
+                        m8 = m8n;
+                        if (s + 1 < nst) m8n = __ldg(A.stage_m8 + (int64_t)(sbase + s + 1) * SR + lane);
                         need = __ballot_sync(FULLMASK, m8 != 0u);
+                        if (!need) continue;  // no row of this stage is needed: the stage is not sent
                     }
                     uint32_t wmask = 0u;  // lane w < CONSUMERS: rows evaluated by warp w
 #pragma unroll
@@ -542,24 +578,29 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                         const uint32_t bw = __ballot_sync(FULLMASK, (m8 >> w) & 1u);
                         if (lane == w) wmask = bw;
                     }
+                    // When the needed (row, tile) pairs are sparse, load per 32-column
+                    // tile ([warp][row][TW]; 128-byte rows) instead of whole rows.
+                    const uint32_t tiles = __reduce_add_sync(FULLMASK, (uint32_t)__popc(wmask));
+                    const bool tiled = screened && tiles * 2u <= (uint32_t)__popc(need) * CONSUMERS;
                     int slot;
                     if (!next_slot(slot)) { ok = false; break; }
                     if (lane < CONSUMERS) S.rmaskw[slot][lane] = wmask;
                     if (lane < DESC_WORDS) reinterpret_cast<int*>(&S.hdr[slot].d)[lane] = w0;
                     if (lane == 0) {
                         const uint32_t abytes = (uint32_t)nr * 16u;
-                        const uint32_t cbytes = s == 0 ? (uint32_t)IC * 8u : 0u;
-                        mbar_expect(&S.full[slot], (uint32_t)__popc(need) * ROW_BYTES + 2u * abytes + cbytes);
+                        // the item's first stage sent (not necessarily s == 0) carries its beta pairs
+                        const uint32_t cbytes = first ? (uint32_t)IC * 8u : 0u;
+                        const uint32_t cdata = tiled ? tiles * (uint32_t)(TW * 4) : (uint32_t)__popc(need) * ROW_BYTES;
+                        mbar_expect(&S.full[slot], cdata + 2u * abytes + cbytes);
                         bulk_copy(S.rowA[slot], A.rowA + ra, abytes, &S.full[slot]);
                         bulk_copy(S.rowG[slot], A.rowg + ra, abytes, &S.full[slot]);
-                        if (s == 0) {
-                            bulk_copy(S.colB[slot], A.B2 + col0, IC * 8u, &S.full[slot]);
-                        }
+                        if (first) bulk_copy(S.colB[slot], A.B2 + col0, IC * 8u, &S.full[slot]);
                         StageHdr& hh = S.hdr[slot];
                         hh.sidx = s;
-                        hh.flags = (s == 0 ? H_FIRST : 0) | (s == nst - 1 ? H_LAST : 0);
+                        hh.flags = first ? H_FIRST : 0;
+                        hh.tiled = tiled ? 1 : 0;
                         // one run of consecutive needed rows at a time
-                        uint32_t rem = need;
+                        uint32_t rem = tiled ? 0u : need;
                         while (rem) {
                             const int a = __ffs(rem) - 1;
                             const uint32_t x = rem >> a;
@@ -568,9 +609,22 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                             rem &= a + len >= 32 ? 0u : ~((1u << (a + len)) - 1u);
                         }
                     }
+                    __syncwarp();  // the transaction count is registered before the tiles' copies
+                    if (tiled && lane < CONSUMERS) {
+                        uint32_t rem = wmask;
+                        float* dst = S.stage[slot] + lane * SR * TW;
+                        while (rem) {
+                            const int a = __ffs(rem) - 1;
+                            const uint32_t x = rem >> a;
+                            const int len = x == FULLMASK ? 32 : __ffs(~x) - 1;
+                            tma_tile_rows(T, dst + a * TW, col0 + lane * TW, ra + a, len, &S.full[slot]);
+                            rem &= a + len >= 32 ? 0u : ~((1u << (a + len)) - 1u);
+                        }
+                    }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S.full[slot]);
                     issued++;
+                    first = false;
                 }
             }
             if (!ok) break;
@@ -594,8 +648,16 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
     Ctx x;
     x.bh = 0.f; x.bl = 0.f; x.bp = -INFINITY; x.colg = 0; x.U = 0u;
     double psi_acc = 0.0, cacc = 0.0;
+    int item = -1;  // the item being consumed; its sums are written when the next one starts
     Block blk;
     open_block(blk, make_int4(0, 0, 0, 0), false);
+    auto finish_item = [&]() {
+        double v = psi_acc;
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
+        if (lane == 0) A.psipart[(int64_t)item * NWARPS + warp] = v;
+        if (x.colg < A.n && cacc != 0.0) red_fx(A.colfx + x.colg, cacc, fx.to_c);
+    };
     for (;;) {
         const int slot = (int)(consumed % NSTAGES);
         if (!mbar_wait(&S.full[slot], (uint32_t)((consumed / NSTAGES) & 1))) {
@@ -604,9 +666,14 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
         }
         const StageHdr& hs = S.hdr[slot];
         const int flags = hs.flags;
-        if (flags & H_TERM) return;
+        if (flags & H_TERM) {
+            if (item >= 0) finish_item();
+            return;
+        }
         const int r0 = hs.d.r0;
         if (flags & H_FIRST) {
+            if (item >= 0) finish_item();
+            item = hs.d.item;
             const float2 b2 = S.colB[slot][wc];
             x.bh = b2.x;
             x.bl = b2.y;
@@ -620,7 +687,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
         x.ra = r0 + hs.sidx * SR;
         x.marks = S.marks[warp];
         x.nr = min(SR, hs.d.rows - hs.sidx * SR);
-        x.st = S.stage[slot] + wc;
+        const bool tiled = hs.tiled != 0;
+        x.rs = tiled ? TW : IC;
+        x.st = S.stage[slot] + (tiled ? warp * SR * TW + lane : wc);
         x.rA = S.rowA[slot];
         const int4* rG = S.rowG[slot];
         const uint32_t wrows = A.unit_need ? S.rmaskw[slot][warp] : FULLMASK;  // rows this warp evaluates
@@ -637,7 +706,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
         } else {
             // only the groups with a marked chunk (and a block that ends here)
             const uint32_t live = (x.nr >= SR ? 0xffu : (1u << ((x.nr + 3) >> 2)) - 1u) & chunks_of_rows(wrows);
-            x.U = __reduce_or_sync(FULLMASK, chunk_marks(x.st, x.rA, x.bp) & live);
+            const uint32_t cm = tiled ? chunk_marks<TW>(x.st, x.rA, x.bp) : chunk_marks<IC>(x.st, x.rA, x.bp);
+            x.U = __reduce_or_sync(FULLMASK, cm & live);
             if (hs.sidx < MARK_STAGES && lane == 0) S.marks[warp][hs.sidx] = (uint8_t)x.U;
             __syncwarp();
             int r = 0;
@@ -666,57 +736,75 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 r = e;
             }
         }
-        if (flags & H_LAST) {
-            double v = psi_acc;
-#pragma unroll
-            for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
-            if (lane == 0) A.psipart[(int64_t)hs.d.item * NWARPS + warp] = v;
-            if (x.colg < A.n && cacc != 0.0) red_fx(A.colfx + x.colg, cacc, fx.to_c);
-        }
         __syncwarp();
         if (lane == 0) mbar_arrive(&S.empty[slot]);
         consumed++;
     }
 }
 
+// ========================================================== stage masks
+// Screened evaluations: per (item, stage, row) the needed tiles of the item
+// for the row's group (bit w = tile w of the item's 256 columns), from the
+// unit bitmask, so that the evaluation kernel's producer reads them without
+// a chain of dependent loads.  One block per active item.
+__global__ void __launch_bounds__(256) k_stage_masks(const EvalArgs A)
+{
+    if (A.gate && !*A.gate) return;
+    const ItemDesc d = A.desc[blockIdx.x];
+    if (A.item_active && !A.item_active[d.item]) return;
+    const int tile0 = d.col0 / TW;  // a multiple of NWARPS: the item's tiles share one mask word
+    uint8_t* out = const_cast<uint8_t*>(A.stage_m8) + (int64_t)d.sbase * SR;
+    for (int r = threadIdx.x; r < d.nst * SR; r += blockDim.x) {
+        uint32_t m8 = 0u;
+        if (r < d.rows) {
+            const int l = A.rowg[d.r0 + r].x;
+            m8 = (A.unit_need[(int64_t)l * A.unit_words + (tile0 >> 5)] >> (tile0 & 31)) & 0xffu;
+        }
+        out[r] = (uint8_t)m8;
+    }
+}
+
+void launch_stage_masks(const EvalArgs& a, cudaStream_t st)
+{
+    k_stage_masks<<<a.nlist, 256, 0, st>>>(a);
+}
+
 // ================================================================ pass B
-// The blocks k_stream deferred: task u of warp w covers rows
-// [gstart + PASSB_ROWS k, ...) of block e = u / tasks_per_block; each lane
-// re-forms f for its column and adds its nonzero t_ij = s_j [f_ij]_+ to the
-// fixed-point row sum (integer adds: the total does not depend on order).
-__global__ void __launch_bounds__(256) k_passb(const EvalArgs A, int tasks_per_block)
+// The blocks k_stream deferred, one CTA per block at a time: warp w takes
+// rows [gstart + 8 (w + NW t), + 8) for t = 0, 1, ... with the eight rows'
+// loads issued together; each lane re-forms f for its column and adds its
+// nonzero t_ij = s_j [f_ij]_+ to the fixed-point row sum (integer adds: the
+// total does not depend on their order).
+constexpr int PASSB_THREADS = 256;
+
+__global__ void __launch_bounds__(PASSB_THREADS) k_passb(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
     const int nb = min(A.ctl->npassb, A.passb_cap);
     if (nb == 0) return;
     const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);
-    const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t ntask = (int64_t)nb * tasks_per_block;
-    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < ntask; u += nw) {
-        const PassB& e = A.passb[u / tasks_per_block];
-        const int k = (int)(u % tasks_per_block);
-        const int R0 = e.gstart + k * PASSB_ROWS;
-        if (R0 >= e.gend) continue;  // warp-uniform
-        const int R1 = min(R0 + PASSB_ROWS, e.gend);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = PASSB_THREADS / 32;
+    for (int eb = blockIdx.x; eb < nb; eb += gridDim.x) {
+        const PassB& e = A.passb[eb];
+        const int gstart = e.gstart, gend = e.gend;
         const float s = e.s[lane];
         const int colg = e.colg0 + lane;
         if (!__any_sync(FULLMASK, s > 0.f)) continue;
         const bool real = colg < A.n;
         const float2 b2 = real ? __ldg(A.B2 + colg) : make_float2(0.f, 0.f);
         const float bp = real ? bound_up(b2.x) : -INFINITY;
-        for (int R = R0; R < R1; R += 4) {
-            float c[4];
-            float4 a[4];
+        for (int R = gstart + 8 * warp; R < gend; R += 8 * nw) {
+            float c[8];
+            float4 a[8];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                const int Rq = min(R + q, R1 - 1);
+            for (int q = 0; q < 8; q++) {
+                const int Rq = min(R + q, gend - 1);
                 c[q] = real ? __ldg(A.C + (int64_t)Rq * A.ldc + colg) : 0.f;
                 a[q] = __ldg(A.rowA + Rq);
             }
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                if (R + q >= R1 || !(s > 0.f) || !maybe_pos(a[q].z, c[q], bp)) continue;
+            for (int q = 0; q < 8; q++) {
+                if (R + q >= gend || !(s > 0.f) || !maybe_pos(a[q].z, c[q], bp)) continue;
                 float fh, fl;
                 f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
                 if (fh > 0.f) red_fx(A.rowfx + R + q, (double)__fmul_rn(s, fh), fx.to_r);
@@ -725,10 +813,9 @@ __global__ void __launch_bounds__(256) k_passb(const EvalArgs A, int tasks_per_b
     }
 }
 
-void launch_passb(const EvalArgs& a, int max_rows, int n_sm, cudaStream_t st)
+void launch_passb(const EvalArgs& a, int n_sm, cudaStream_t st)
 {
-    const int tasks = max(1, (max_rows + PASSB_ROWS - 1) / PASSB_ROWS);
-    k_passb<<<4 * n_sm, 256, 0, st>>>(a, tasks);
+    k_passb<<<4 * n_sm, PASSB_THREADS, 0, st>>>(a);
 }
 
 size_t stream_smem_bytes() { return sizeof(Smem) + 1024; }
@@ -775,11 +862,14 @@ std::string make_tmaps(const float* C, int64_t ldc, int64_t m, int64_t n, TmaMap
     const cuuint64_t strides[1] = {(cuuint64_t)ldc * sizeof(float)};
     const cuuint32_t estr[2] = {1, 1};
     for (int k = 0; k < TMA_BOXES; k++) {
-        const cuuint32_t box[2] = {(cuuint32_t)IC, 1u << k};
-        CUresult r = enc(&T.box[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(C), dims, strides, box, estr,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        for (int t = 0; t < 2; t++) {
+            const cuuint32_t box[2] = {(cuuint32_t)(t ? TW : IC), 1u << k};
+            CUresult r = enc(t ? &T.tile[k] : &T.box[k], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(C),
+                             dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             t ? CU_TENSOR_MAP_L2_PROMOTION_L2_128B : CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+            if (r != CUDA_SUCCESS) return "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        }
     }
     return "";
 }

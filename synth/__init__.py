@@ -178,6 +178,21 @@ def large(seed: int = 0, m: int = 20000, n: int = 20000, L: int = 1000, d: int =
     return _maybe_shuffle(p, shuffle_rows, rng)
 
 
+def two_band(seed: int = 0, pairs: int = 64, far_rows: int = 40, near_rows: int = 24, n: int = 8192) -> Problem:
+    """Classes alternate between a "far" class of far_rows rows with costs in
+    [0.9, 1) and a "near" class of near_rows rows with costs in [0, 0.5)
+    (independent uniform draws), labels sorted.  At duals around 0.5 the far
+    classes hold no positive part at all, so screening drops them whole."""
+    rng = np.random.default_rng(seed)
+    sizes = np.tile([far_rows, near_rows], pairs)
+    lab = labels_from_sizes(sizes)
+    far = np.repeat(np.tile([True, False], pairs), sizes)
+    m = int(sizes.sum())
+    C = np.where(far[:, None], rng.uniform(0.9, 1.0, (m, n)), rng.uniform(0.0, 0.5, (m, n))).astype(np.float32)
+    return Problem(C=C, labels=lab, a=np.full(m, 1.0 / m), b=np.full(n, 1.0 / n), L=int(2 * pairs),
+                   name="two_band")
+
+
 def paper_synthetic(L: int, g: int = 10, seed: int = 0) -> Problem:
     """The paper's synthetic set (Sec. 5.1): d=2, g rows per class, class
     l (1-based) has source mean (5l, -5) and target mean (5l, 5), unit

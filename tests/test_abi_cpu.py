@@ -26,12 +26,18 @@ def test_create_rejects_null_without_gpu():
     assert "NULL" in pk.ot_gs_last_error(None)
 
 
-PANEL_ROWS, ITEM_COLS, STAGE_ROWS = 512, 256, 32
+ITEM_COLS, STAGE_ROWS = 256, 32
+
+
+def panel_height(m, n):
+    """m * ceil(n / 256) / 2048 rows, clamped to [32, 512]."""
+    return min(512, max(32, -(-m * -(-n // ITEM_COLS) // 2048)))
 
 
 def expected_plan(sizes, n):
     """Panels by the packing rule of the plan (consecutive non-empty groups up
-    to PANEL_ROWS rows; a larger group alone), items and stages from them."""
+    to the panel height; a larger group alone), items and stages from them."""
+    PANEL_ROWS = panel_height(int(np.sum(sizes)), n)
     panels, cur = [], 0
     for g in sizes:
         if g == 0:
@@ -52,7 +58,8 @@ def expected_plan(sizes, n):
 @pytest.mark.parametrize("sizes,n", [
     ([20] * 10, 200),                        # tiny: equal small groups, one ragged chunk
     ([1, 2, 3, 70, 5, 4100, 0, 9], 77),      # small + giant + empty, ragged n
-    ([512, 511, 1, 513, 2, 510], 257),       # panel-size boundaries, two chunks (one of 1 column)
+    ([512, 511, 1, 513, 2, 510], 257),       # groups around the panel height (32 here), two chunks
+    ([3] * 4000 + [700], 40000),             # tall panels (512 rows) and one larger group
     ([3] * 400, 1000),                       # many tiny groups: panels close on rows
 ])
 def test_plan_covers_rows(sizes, n):
@@ -69,7 +76,8 @@ def test_plan_zipf_large_shape():
     info = pk.ot_gs_plan_info(lab, 20000, 1000)
     n_panels, n_items, n_stages, _ = expected_plan(list(sizes), 20000)
     assert (info["n_panels"], info["n_items"], info["n_stages"]) == (n_panels, n_items, n_stages)
-    assert int((np.asarray(sizes) > PANEL_ROWS).sum()) < info["n_panels"] < 200
+    assert panel_height(20000, 20000) == 512
+    assert int((np.asarray(sizes) > 512).sum()) < info["n_panels"] < 200
     # streaming one evaluation touches every row once per column chunk, in
     # 32-row stages: at most one partial stage per panel and chunk
     nch = -(-20000 // ITEM_COLS)

@@ -103,3 +103,34 @@ def test_snapshot_values_bound_the_exact_norms():
     assert (zt[:, :p.n].astype(np.float64) >= z * (1 - 1e-12)).all()
     assert np.allclose(zt[:, :p.n], z, rtol=1e-6, atol=1e-30)
     assert np.allclose(ot[:, :p.n], oo, rtol=1e-4, atol=1e-6)
+
+
+def test_screened_items_whose_first_stages_are_not_sent():
+    """Panels of 64 rows (m ceil(n/256) / 2048 = 64 here): a far class of 40
+    rows, then a near class of 24.  At this point no far block has a positive
+    part, so screening drops them and each work item's first 32-row stage
+    holds no needed row and is not sent; the item's column data must come with
+    its first stage that is.  Screened == dense bit for bit, and dense agrees
+    with the oracle."""
+    import paper_2303_07597_gb300 as pk
+    p = synth.two_band(seed=3)
+    assert pk.ot_gs_plan_info(p.labels, p.n, p.L)["n_panels"] == 64
+    s = solver(p, 1.0, 0.1)
+    rng = np.random.default_rng(5)
+    alpha = rng.uniform(0.0, 0.1, p.m)
+    beta = rng.uniform(0.2, 0.4, p.n)
+    al, be = torch.from_numpy(alpha).to(DEV), torch.from_numpy(beta).to(DEV)
+    out_d = torch.empty(1 + p.m + p.n, dtype=torch.float64, device=DEV)
+    out_s = torch.empty_like(out_d)
+    s.snapshot(al, be, build_N=False, out=out_d)
+    # a nearby point: the snapshot's bounds still drop every far block
+    al2, be2 = al * (1 + 1e-3), be * (1 - 1e-3)
+    pk.ot_gs_grad(s.h, al2, be2, out_d)
+    s.grad_screened(al2, be2, out_s)
+    torch.cuda.synchronize()
+    assert torch.equal(out_d, out_s)
+    st = s.stats()
+    assert st["units_computed"] < st["units_total"]  # far units were skipped
+    o = oracle.Oracle.from_problem(p, 1.0, 0.1)
+    a2, b2 = al2.cpu().numpy(), be2.cpu().numpy()
+    check_grad(out_s, o.dual(a2, b2), a2, b2, p.a, p.b, "two_band")
