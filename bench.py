@@ -368,7 +368,7 @@ def run_gpu(args):
             "cpu_baseline": cb,
             "e2e": {"value": k_e2e * world / (e2e_ms / 1000.0), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (m + n), "d2h_bytes_per_step": 8 * (1 + m + n)},
-            "gpu_launches": 4 * args.steps,
+            "gpu_launches": 5 * args.steps,  # prep, stream, split finish, pass B, reduce
             "clocks": clocks,
         }
         if world == 1 and not args.no_solve:

@@ -237,13 +237,14 @@ OTGS_API int ot_gs_plan_info(const int32_t *labels_host, int64_t m, int64_t n, i
  *   alpha, beta  device FP64 [m], [n];  out: device FP64 [1 + m + n] as ot_gs_grad
  *   stream       cudaStream_t as void*
  * Inputs are not otherwise validated.  Sizes whose scratch would exceed the
- * static array (about 44 bytes per row, 20 per column and 96 per work item
- * of up to 512 rows x 256 columns: m = n = 2 x 10^5 fits) are
+ * static array (about 44 bytes per row, 20 per column, 64 per work item of up
+ * to 512 rows x 256 columns, and 5 KB per 256 rows x 256 columns of classes of
+ * more than 256 rows: m = n = 2 x 10^4 fits) are
  * rejected with OTGS_EINVAL before any GPU work; the message says how many
  * bytes were needed.  The first call made on a device looks up the array's
  * device address there (once per device), so that first call should come
  * before any stream capture.  Every call shares the array and leaves the last
- * call's contents in it (the one value that must start at zero is cleared by
+ * call's contents in it (the values that must start at zero are cleared by
  * each call); calls that overlap on the GPU race with each other.
  * Asynchronous with respect to the host.  Errors: OTGS_EINVAL, OTGS_ECUDA;
  * message from ot_gs_noalloc_last_error().

@@ -127,12 +127,13 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     dp.pW = upload(this, hp.pW, "pW");
     dp.pnch = upload(this, hp.pnch, "pnch");
     dp.pitem = upload(this, hp.pitem, "pitem");
+    dp.psplit = upload(this, hp.psplit, "psplit");
     dp.gpanel = upload(this, hp.gpanel, "gpanel");
     dp.item_panel = upload(this, hp.item_panel, "item_panel");
     dp.item_chunk = upload(this, hp.item_chunk, "item_chunk");
     dp.exec_order = upload(this, hp.exec_order, "exec_order");
     dp.desc = upload(this, hp.desc, "item descriptors");
-    if (!dp.goff || !dp.rgroup || !dp.rowg || !dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.gpanel ||
+    if (!dp.goff || !dp.rgroup || !dp.rowg || !dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.psplit || !dp.gpanel ||
         !dp.item_panel || !dp.item_chunk || !dp.exec_order || !dp.desc)
         return false;
     {
@@ -156,7 +157,9 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     psipart = (double*)dalloc(sizeof(double) * (size_t)hp.nitems() * NWARPS, "psipart");
     passb_cap = (int)std::min<int64_t>((int64_t)L * ntiles, 65536);
     passb = (PassB*)dalloc(sizeof(PassB) * (size_t)passb_cap, "pass-B list");
-    if (!passb) return false;
+    split_part = (float*)dalloc(sizeof(float) * 5 * ITEM_COLS * (size_t)hp.nsplit_slots, "split partial sums");
+    dp.sets = upload(this, hp.sets, "split block sets");
+    if (!passb || !split_part || !dp.sets) return false;
     if (!rowA || !B2 || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !psipart) return false;
     if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
     {
@@ -193,6 +196,8 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.unit_words = unit_words;
     e.rowfx = rowfx; e.colfx = colfx; e.psipart = psipart;
     e.passb = passb; e.passb_cap = passb_cap;
+    e.split_part = split_part;
+    e.sets = dp.sets; e.nsets = (int32_t)hp.sets.size();
     e.gate = eval_gate;
     e.zt = snap ? zt : nullptr;
     e.ot = snap ? ot : nullptr;
@@ -253,6 +258,7 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
         cudaEventRecord(ev_pool[ev_used + 1], st);
         ev_used += 2;
     }
+    launch_split_finish(e, st);
     launch_passb(e, n_sm, st);
 }
 

@@ -43,6 +43,7 @@ struct Handle {
     double* psipart = nullptr;      // per (item, consumer warp) psi sums
     PassB* passb = nullptr;         // blocks whose pass B the pass-B kernel does
     int passb_cap = 0;
+    float* split_part = nullptr;    // partial block sums of the pieces of split groups
     int nred = 0;
     double* block_part = nullptr;
     unsigned* counter = nullptr;

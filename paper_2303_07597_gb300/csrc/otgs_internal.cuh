@@ -84,16 +84,38 @@ __device__ __forceinline__ float prep_col(bool real, double b, float2* B2)
     return fmaxf(s.x, 0.f);
 }
 
-// A work item as the evaluation kernel sees it, in execution order (32 B).
+// Groups taller than SPLIT_ROWS rows are cut into panels of SPLIT_ROWS rows
+// ("pieces"), so that one block is summed by several CTAs in parallel; a
+// second kernel adds the pieces' partial sums in piece order and finishes
+// those blocks.
+constexpr int SPLIT_ROWS = 256;
+
+// A block set: the blocks of one split group against one 256-column chunk.
+struct SplitSet {
+    int l;       // group
+    int col0;    // first column
+    int split;   // pieces
+    int part;    // partial-sum slot of piece 0 (piece k: part + k)
+    int item0;   // item id of piece 0 (holds the set's psi partials)
+    int rstart;  // rows of the group
+    int rend;
+    int pad;
+};
+
+// A work item as the evaluation kernel sees it, in execution order (64 B).
 struct ItemDesc {
     int item;   // item id (index of its psi partials and active flag)
     int p;      // panel
     int r0;     // first sorted row
-    int rows;   // rows (whole groups)
+    int rows;   // rows (whole groups, or one piece of a split group)
     int col0;   // first column (multiple of ITEM_COLS)
     int ncols;  // columns of C in the item (<= ITEM_COLS)
     int nst;    // stages: ceil(rows / STAGE_ROWS)
     int sbase;  // first stage of the item in execution order (index into per-stage tables)
+    int split;  // pieces of the item's group (1: not split)
+    int sub;    // this item's piece
+    int part;   // split groups: partial-sum slot of piece 0 of this block set (piece k: part + k)
+    int pad[5];
 };
 
 // ------------------------------------------------------------------ host plan
@@ -112,12 +134,17 @@ struct HostPlan {
     std::vector<int32_t> pW;      // columns per work item (ITEM_COLS)
     std::vector<int32_t> pnch;    // work items (column chunks) of the panel
     std::vector<int32_t> pitem;   // first work-item id of the panel
-    std::vector<int32_t> gpanel;  // group -> panel (-1 for empty groups)
+    std::vector<int32_t> psplit;  // pieces of the panel's group (1: not a piece of a split group)
+    std::vector<int32_t> psub;    // the panel's piece
+    std::vector<int32_t> pslot;   // pieces of split groups before the panel's group (split panels)
+    std::vector<int32_t> gpanel;  // group -> panel (-1 for empty groups; the first piece if split)
     // work items, id = pitem[p] + chunk
     std::vector<int32_t> item_panel, item_chunk;
     std::vector<int32_t> exec_order;  // item ids, largest first
     std::vector<ItemDesc> desc;       // work items in execution order
     int64_t nstages = 0;              // stages streamed by one dense evaluation
+    int64_t nsplit_slots = 0;         // partial-sum slots of split groups: their pieces x column chunks
+    std::vector<SplitSet> sets;       // block sets of split groups
     int32_t max_group = 0;            // rows of the largest group
     bool sorted_identity = true;      // labels already non-decreasing
     int npanels() const { return (int)prows.size(); }
@@ -131,7 +158,8 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
 struct DevPlan {
     int32_t *perm, *goff, *rgroup;
     int4* rowg;
-    int32_t *prows, *pW, *pnch, *pitem, *gpanel;
+    SplitSet* sets;
+    int32_t *prows, *pW, *pnch, *pitem, *psplit, *gpanel;
     int32_t *item_panel, *item_chunk, *exec_order;
     ItemDesc* desc;
 };
@@ -226,6 +254,9 @@ struct EvalArgs {
     double* psipart;   // [nitems * NWARPS]: per item and consumer warp, sum of psi
     PassB* passb;      // deferred pass-B blocks (capacity passb_cap)
     int32_t passb_cap;
+    float* split_part; // [slots][ITEM_COLS][5]: a piece's (S hi, S lo, P hi, P lo, O) per column
+    const SplitSet* sets;  // block sets of split groups
+    int32_t nsets;
     const int* gate;   // NULL, or a device flag: 0 = skip this evaluation (batched solver trials)
     float* zt;         // snapshot outputs (L x ntiles*TW) or NULL
     float* ot;
@@ -281,8 +312,11 @@ void launch_stream(const EvalArgs& a, const TmaMaps& T, int n_ctas, cudaStream_t
 // stage-mask kernel (otgs_stream.cu), screened evaluations: fills
 // a.stage_m8 from a.unit_need for the active items.  Launch before launch_stream.
 void launch_stage_masks(const EvalArgs& a, cudaStream_t st);
-// pass-B kernel (otgs_stream.cu): the blocks k_stream deferred.  Launch right
-// after launch_stream with the same arguments.
+// split-finish kernel (otgs_stream.cu): adds the pieces' partial sums of the
+// split groups' blocks and finishes them.  Launch right after launch_stream.
+void launch_split_finish(const EvalArgs& a, cudaStream_t st);
+// pass-B kernel (otgs_stream.cu): the blocks k_stream and the split-finish
+// kernel deferred.  Launch after them with the same arguments.
 void launch_passb(const EvalArgs& a, int n_sm, cudaStream_t st);
 size_t stream_smem_bytes();
 void launch_reduce(const ReduceArgs& a, cudaStream_t st);

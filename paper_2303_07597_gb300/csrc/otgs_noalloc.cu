@@ -98,6 +98,8 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const size_t o_psipart = cv.take(8 * (size_t)hp.nitems() * NWARPS);
     const int passb_cap = 4096;
     const size_t o_passb = cv.take(sizeof(PassB) * (size_t)passb_cap);
+    const size_t o_spart = cv.take(sizeof(float) * 5 * ITEM_COLS * (size_t)hp.nsplit_slots);
+    const size_t o_sets = cv.take(sizeof(SplitSet) * hp.sets.size());
     const int nred = reduce_blocks((int32_t)m, (int32_t)n);
     const size_t o_bpart = cv.take(8 * 4 * (size_t)nred), o_counter = cv.take(16), o_scal = cv.take(64);
     if (cv.off > OTGS_STATIC_SCRATCH_BYTES)
@@ -130,6 +132,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     if (e == cudaSuccess) e = up(o_desc, hp.desc.data(), sizeof(ItemDesc) * hp.desc.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_counter, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_err, 0, 16, st);
+    if (e == cudaSuccess) e = up(o_sets, hp.sets.data(), sizeof(SplitSet) * hp.sets.size());
     int n_sm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return set_err(OTGS_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
@@ -158,6 +161,9 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     ea.psipart = (double*)(base + o_psipart);
     ea.passb = (PassB*)(base + o_passb);
     ea.passb_cap = passb_cap;
+    ea.split_part = (float*)(base + o_spart);
+    ea.sets = (const SplitSet*)(base + o_sets);
+    ea.nsets = (int32_t)hp.sets.size();
     const double theta = mu * gamma;
     ea.theta_hi = (float)theta;
     ea.theta_lo = (float)(theta - (double)ea.theta_hi);
@@ -173,6 +179,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
         if (!te.empty()) return set_err(OTGS_ECUDA, te);
     }
     launch_stream(ea, tm, std::min(CTAS_PER_SM * n_sm, hp.nitems()), st);
+    launch_split_finish(ea, st);
     launch_passb(ea, n_sm, st);
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));

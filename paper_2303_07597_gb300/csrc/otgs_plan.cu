@@ -4,7 +4,8 @@
 // target column j (Sec. 2.3, O(|L| n g) per evaluation).  On the GPU, rows are
 // visited in class-sorted order, so every group is a contiguous range of
 // sorted rows.  Consecutive groups are packed into panels (row ranges of
-// whole groups, up to panel_rows(m, n) rows; a larger group is a panel of its own),
+// whole groups, up to panel_rows(m, n) rows; a group taller than SPLIT_ROWS is
+// cut into pieces of SPLIT_ROWS rows, each a panel),
 // and a work item is (panel, column chunk of ITEM_COLS columns).  Inside an
 // item, each column's blocks are evaluated by one thread walking down the
 // rows, so no block is ever split between threads; items are handed out
@@ -52,16 +53,34 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
     // before they would exceed the panel height
     const int32_t PANEL_ROWS = panel_rows(m, n);
     hp.gpanel.assign(L, -1);
-    int32_t cur0 = -1, cur_rows = 0;
+    int32_t cur0 = -1, cur_rows = 0, pieces_before = 0;
     auto flush = [&]() {
         if (cur_rows == 0) return;
         hp.prow0.push_back(cur0);
         hp.prows.push_back(cur_rows);
+        hp.psplit.push_back(1);
+        hp.psub.push_back(0);
+        hp.pslot.push_back(-1);
         cur_rows = 0;
     };
     for (int32_t l = 0; l < L; l++) {
         const int32_t g = hp.goff[l + 1] - hp.goff[l];
         if (g == 0) continue;
+        if (g > SPLIT_ROWS) {
+            // a tall group: panels of SPLIT_ROWS rows of its own
+            flush();
+            hp.gpanel[l] = hp.npanels();
+            const int32_t pieces = (g + SPLIT_ROWS - 1) / SPLIT_ROWS;
+            for (int32_t k = 0; k < pieces; k++) {
+                hp.prow0.push_back(hp.goff[l] + k * SPLIT_ROWS);
+                hp.prows.push_back(std::min(SPLIT_ROWS, g - k * SPLIT_ROWS));
+                hp.psplit.push_back(pieces);
+                hp.psub.push_back(k);
+                hp.pslot.push_back(pieces_before);
+            }
+            pieces_before += pieces;
+            continue;
+        }
         if (cur_rows > 0 && cur_rows + g > PANEL_ROWS) flush();
         if (cur_rows == 0) cur0 = hp.goff[l];
         hp.gpanel[l] = hp.npanels();
@@ -105,10 +124,32 @@ std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, H
         d.ncols = (int)std::min<int64_t>(ITEM_COLS, n - (int64_t)d.col0);
         d.nst = (d.rows + STAGE_ROWS - 1) / STAGE_ROWS;
         d.sbase = (int)hp.nstages;
+        d.split = hp.psplit[p];
+        d.sub = hp.psub[p];
+        // slots of the set (group, chunk cc): pslot * nch + cc * split + [0, split)
+        d.part = d.split > 1 ? hp.pslot[p] * nch + cc * d.split : -1;
         hp.nstages += d.nst;
         hp.desc[k] = d;
     }
     if (hp.nstages > INT32_MAX / STAGE_ROWS) return "m x n too large for the stage tables";
+    hp.nsplit_slots = (int64_t)pieces_before * nch;
+    // block sets of the split groups: (group, chunk)
+    for (int p = 0; p < np; p++) {
+        if (hp.psplit[p] == 1 || hp.psub[p] != 0) continue;
+        const int32_t l = hp.rgroup[hp.prow0[p]];
+        for (int32_t cc = 0; cc < nch; cc++) {
+            SplitSet s;
+            s.l = l;
+            s.col0 = cc * ITEM_COLS;
+            s.split = hp.psplit[p];
+            s.part = hp.pslot[p] * nch + cc * s.split;
+            s.item0 = hp.pitem[p] + cc;
+            s.rstart = hp.goff[l];
+            s.rend = hp.goff[l + 1];
+            s.pad = 0;
+            hp.sets.push_back(s);
+        }
+    }
     return "";
 }
 

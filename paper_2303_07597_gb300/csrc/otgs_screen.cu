@@ -53,6 +53,7 @@ struct ScreenArgs {
     const int32_t* gpanel;
     const int32_t* pitem;
     const int32_t* pW;
+    const int32_t* psplit;      // pieces of a panel's group (1: not split)
     unsigned long long* count;  // [0] in N, [1] checked, [2] skipped, [3] units needed
     int32_t nitems;
     const int* gate;            // NULL, or a device flag: 0 = skip (batched solver trials)
@@ -204,7 +205,8 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
                 S.skipmask[u] = skipw;
                 if (needw) {
                     needword |= 1u << (jt & 31);
-                    S.item_active[S.pitem[p] + (jt * TW) / S.pW[p]] = 1;  // same value from every writer
+                    // the item of (l, tile) in every piece of the group (same value from every writer)
+                    for (int k = 0; k < S.psplit[p]; k++) S.item_active[S.pitem[p + k] + (jt * TW) / S.pW[p]] = 1;
                 }
                 c0 += __popc(Nw & validw);
                 c1 += __popc(~Nw & validw);
@@ -270,7 +272,7 @@ ScreenArgs make_screen_args(Handle* h)
     s.theta = h->prm.mu * h->prm.gamma;
     s.theta_f = (float)s.theta;
     s.Nmask = h->Nmask; s.skipmask = h->skipmask; s.unit_need = h->unit_need; s.item_active = h->item_active;
-    s.gpanel = h->dp.gpanel; s.pitem = h->dp.pitem; s.pW = h->dp.pW;
+    s.gpanel = h->dp.gpanel; s.pitem = h->dp.pitem; s.pW = h->dp.pW; s.psplit = h->dp.psplit;
     s.count = h->dcount;
     s.nitems = h->hp.nitems();
     s.gate = h->eval_gate;

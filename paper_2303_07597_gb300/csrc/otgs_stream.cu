@@ -361,7 +361,9 @@ __device__ __forceinline__ void put_snap(const EvalArgs& A, int l, int col, floa
 
 // The block of this lane's column that is being accumulated.
 struct Block {
-    int gl, gstart, gend;  // group and its sorted rows [gstart, gend)
+    int gl, gstart, gend;  // group and the sorted rows [gstart, gend) summed in this item
+    int rstart, rend;      // all rows of the group (wider than [gstart, gend) for a piece of a split group)
+    bool split;            // a piece of a group cut over several items
     bool need;             // evaluated by this warp (always, unless screened)
     bool any;              // some f > 0 seen
     Acc acc;
@@ -378,25 +380,65 @@ struct Ctx {
     int colg;          // this lane's column of C
     uint32_t U;        // chunks of the stage marked by some lane (dense path)
     int r0;            // first sorted row of the item
+    int rend;          // end row of the item
     const uint8_t* marks;  // this warp's marked chunks of the item's stages
+    int item, split, sub, part;  // the item; its group's pieces, its piece, the set's piece-0 slot
 };
 
-__device__ __forceinline__ void open_block(Block& b, const int4& g, bool need)
+__device__ __forceinline__ void open_block(Block& b, const int4& g, bool need, const Ctx& x)
 {
     b.gl = g.x;
-    b.gstart = g.y;
-    b.gend = g.z;
+    b.rstart = g.y;
+    b.rend = g.z;
+    b.split = g.y < x.r0 || g.z > x.rend;  // a group cut into pieces: this item sums one
+    b.gstart = max(g.y, x.r0);
+    b.gend = min(g.z, x.rend);
     b.need = need;
     b.any = false;
     b.acc = Acc{0.f, 0.f, 0.f, 0.f};
     b.O = 0.f;
 }
 
-// The block is complete: Eq. 5 for it, and pass B where s > 0.
+// Leaves pass B of a block (rows [gstart, gend) x the warp's 32 columns from
+// colg0, shrink factor s per lane) to the pass-B kernel, in pieces of at most
+// PASSB_PIECE rows (so that one long block does not set that kernel's
+// duration); false when the list is full (the slots taken that fit are left
+// empty and the caller does pass B itself).
+__device__ __forceinline__ bool defer_passb(const EvalArgs& A, int gstart, int gend, int colg0, float s, int lane)
+{
+    const int npieces = (gend - gstart + PASSB_PIECE - 1) / PASSB_PIECE;
+    int idx = 0;
+    if (lane == 0) idx = atomicAdd(&A.ctl->npassb, npieces);
+    idx = __shfl_sync(FULLMASK, idx, 0);
+    const bool fits = idx + npieces <= A.passb_cap;
+    for (int k = 0; k < npieces && idx + k < A.passb_cap; k++) {
+        PassB& e = A.passb[idx + k];
+        e.s[lane] = fits ? s : 0.f;
+        if (lane == 0) {
+            e.gstart = fits ? gstart + k * PASSB_PIECE : 0;
+            e.gend = fits ? min(gstart + (k + 1) * PASSB_PIECE, gend) : 0;
+            e.colg0 = colg0;
+        }
+    }
+    return fits;
+}
+
+// The block is complete: Eq. 5 for it, and pass B where s > 0.  A piece of a
+// split group only stores its partial sums; the split-finish kernel adds the
+// pieces in order and finishes the block.
 template <bool SNAP>
 __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, const FxScale& fx,
                                              int lane, bool marks, double& psi_acc, double& cacc)
 {
+    if (b.split) {
+        float* q = A.split_part + ((int64_t)(x.part + x.sub) * ITEM_COLS + (threadIdx.x >> 5) * TW + lane) * 5;
+        q[0] = b.acc.Sh;
+        q[1] = b.acc.Sl;
+        q[2] = b.acc.Ph;
+        q[3] = b.acc.Pl;
+        q[4] = b.O;
+        return;
+    }
     float s = 0.f;
     if (__any_sync(FULLMASK, b.any)) {
         double psi;
@@ -406,38 +448,7 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
     }
     if (SNAP) put_snap(A, b.gl, x.colg, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
     if (!__any_sync(FULLMASK, s > 0.f)) return;
-    if (b.gstart < x.ra - PASSB_INLINE_ROWS) {
-        // many rows have left the ring: leave pass B to the pass-B kernel,
-        // which spreads it over the whole GPU (this warp would hold its CTA's
-        // ring while re-reading them)
-        // (in pieces of at most PASSB_PIECE rows, so that one long block does
-        // not set the pass-B kernel's duration)
-        const int npieces = (b.gend - b.gstart + PASSB_PIECE - 1) / PASSB_PIECE;
-        int idx = 0;
-        if (lane == 0) idx = atomicAdd(&A.ctl->npassb, npieces);
-        idx = __shfl_sync(FULLMASK, idx, 0);
-        if (idx + npieces <= A.passb_cap) {
-            for (int k = 0; k < npieces; k++) {
-                PassB& e = A.passb[idx + k];
-                e.s[lane] = s;
-                if (lane == 0) {
-                    e.gstart = b.gstart + k * PASSB_PIECE;
-                    e.gend = min(b.gstart + (k + 1) * PASSB_PIECE, b.gend);
-                    e.colg0 = x.colg - lane;
-                }
-            }
-            return;
-        }
-        // the list is full: the slots taken that fit are left empty, pass B here
-        for (int k = 0; idx + k < A.passb_cap && k < npieces; k++) {
-            PassB& e = A.passb[idx + k];
-            e.s[lane] = 0.f;
-            if (lane == 0) {
-                e.gstart = 0;
-                e.gend = 0;
-            }
-        }
-    }
+    if (b.gstart < x.ra - PASSB_INLINE_ROWS && defer_passb(A, b.gstart, b.gend, x.colg - lane, s, lane)) return;
     // pass B: t_ij = s [f_ij]_+ into the row sums, over the block's rows that
     // can hold an f > 0 (marked chunks; every row on the snapshot walk),
     // four rows at a time
@@ -445,7 +456,7 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
     for (int sg = sa; sg <= sb; sg++) {
         const int base = x.r0 + sg * SR;
         const bool here = base == x.ra;  // the stage being consumed is still in shared memory
-        uint32_t qm = 0xffu;
+        uint32_t qm = 0xffu;  // rows past the record: all chunks
         if (marks) qm = here ? x.U : (sg < MARK_STAGES ? (uint32_t)x.marks[sg] : 0xffu);
         qm &= chunks_in(max(b.gstart - base, 0), min(b.gend - base, SR));
         while (qm) {
@@ -650,7 +661,13 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
     double psi_acc = 0.0, cacc = 0.0;
     int item = -1;  // the item being consumed; its sums are written when the next one starts
     Block blk;
-    open_block(blk, make_int4(0, 0, 0, 0), false);
+    x.r0 = 0;
+    x.rend = 0;
+    x.item = 0;
+    x.split = 1;
+    x.sub = 0;
+    x.part = -1;
+    open_block(blk, make_int4(0, 0, 0, 0), false, x);
     auto finish_item = [&]() {
         double v = psi_acc;
 #pragma unroll
@@ -674,6 +691,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
         if (flags & H_FIRST) {
             if (item >= 0) finish_item();
             item = hs.d.item;
+            x.item = item;
+            x.split = hs.d.split;
+            x.sub = hs.d.sub;
+            x.part = hs.d.part;
             const float2 b2 = S.colB[slot][wc];
             x.bh = b2.x;
             x.bl = b2.y;
@@ -684,6 +705,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             blk.gend = r0;  // no block continues into the item
         }
         x.r0 = r0;
+        x.rend = r0 + hs.d.rows;
         x.ra = r0 + hs.sidx * SR;
         x.marks = S.marks[warp];
         x.nr = min(SR, hs.d.rows - hs.sidx * SR);
@@ -697,7 +719,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             // every block: z~ and o~ of Def. 1 for the snapshot
             int r = 0;
             while (r < x.nr) {
-                if (x.ra + r == blk.gend) open_block(blk, rG[r], (wrows >> r) & 1u);
+                if (x.ra + r == blk.gend) open_block(blk, rG[r], (wrows >> r) & 1u, x);
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) scan_rows<true>(x.st, x.rA, r, e, x.bh, x.bl, x.bp, blk.acc, blk.O, blk.any);
                 r = e;
@@ -722,13 +744,16 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const uint32_t Ur = x.U & ~((1u << (r >> 2)) - 1u);
                 if (!Ur) {
                     // no f > 0 in rows [r, nr): the stage's last group stays open
-                    // (with nothing accumulated) in case it continues
+                    // (with nothing accumulated) in case it continues; a piece of a
+                    // split group still reports (zero) partial sums at its end
                     const int last = x.nr - 1;
-                    open_block(blk, rG[last], (wrows >> last) & 1u);
+                    open_block(blk, rG[last], (wrows >> last) & 1u, x);
+                    if (blk.split && blk.need && blk.gend <= x.ra + x.nr)
+                        finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
                     break;
                 }
                 const int rc = max(r, 4 * (__ffs(Ur) - 1));  // the group there starts at or after r
-                open_block(blk, rG[rc], (wrows >> rc) & 1u);
+                open_block(blk, rG[rc], (wrows >> rc) & 1u, x);
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) block_marked_rows(blk, x, blk.gstart - x.ra, e);
                 if (blk.gend <= x.ra + x.nr && blk.need)
@@ -770,11 +795,37 @@ void launch_stage_masks(const EvalArgs& a, cudaStream_t st)
 }
 
 // ================================================================ pass B
-// The blocks k_stream deferred, one CTA per block at a time: warp w takes
-// rows [gstart + 8 (w + NW t), + 8) for t = 0, 1, ... with the eight rows'
-// loads issued together; each lane re-forms f for its column and adds its
-// nonzero t_ij = s_j [f_ij]_+ to the fixed-point row sum (integer adds: the
-// total does not depend on their order).
+// Rows [R0, R1) (stepping by `step` from R0) of a block for this lane's
+// column: re-form f and add the nonzero t_ij = s [f_ij]_+ to the fixed-point
+// row sums (integer adds: the total does not depend on their order).  Eight
+// rows' loads are issued together.
+__device__ __forceinline__ void passb_rows(const EvalArgs& A, const FxScale& fx, int R0, int R1, int step,
+                                           int colg, float s)
+{
+    const bool real = colg < A.n;
+    const float2 b2 = real ? __ldg(A.B2 + colg) : make_float2(0.f, 0.f);
+    const float bp = real ? bound_up(b2.x) : -INFINITY;
+    for (int R = R0; R < R1; R += step) {
+        float c[8];
+        float4 a[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int Rq = min(R + q, R1 - 1);
+            c[q] = real ? __ldg(A.C + (int64_t)Rq * A.ldc + colg) : 0.f;
+            a[q] = __ldg(A.rowA + Rq);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if (R + q >= R1 || !(s > 0.f) || !maybe_pos(a[q].z, c[q], bp)) continue;
+            float fh, fl;
+            f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
+            if (fh > 0.f) red_fx(A.rowfx + R + q, (double)__fmul_rn(s, fh), fx.to_r);
+        }
+    }
+}
+
+// The deferred blocks, one CTA per list entry at a time: warp w takes rows
+// [gstart + 8 (w + NW t), + 8) for t = 0, 1, ...
 constexpr int PASSB_THREADS = 256;
 
 __global__ void __launch_bounds__(PASSB_THREADS) k_passb(const EvalArgs A)
@@ -786,36 +837,63 @@ __global__ void __launch_bounds__(PASSB_THREADS) k_passb(const EvalArgs A)
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = PASSB_THREADS / 32;
     for (int eb = blockIdx.x; eb < nb; eb += gridDim.x) {
         const PassB& e = A.passb[eb];
-        const int gstart = e.gstart, gend = e.gend;
         const float s = e.s[lane];
-        const int colg = e.colg0 + lane;
         if (!__any_sync(FULLMASK, s > 0.f)) continue;
-        const bool real = colg < A.n;
-        const float2 b2 = real ? __ldg(A.B2 + colg) : make_float2(0.f, 0.f);
-        const float bp = real ? bound_up(b2.x) : -INFINITY;
-        for (int R = gstart + 8 * warp; R < gend; R += 8 * nw) {
-            float c[8];
-            float4 a[8];
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                const int Rq = min(R + q, gend - 1);
-                c[q] = real ? __ldg(A.C + (int64_t)Rq * A.ldc + colg) : 0.f;
-                a[q] = __ldg(A.rowA + Rq);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; q++) {
-                if (R + q >= gend || !(s > 0.f) || !maybe_pos(a[q].z, c[q], bp)) continue;
-                float fh, fl;
-                f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
-                if (fh > 0.f) red_fx(A.rowfx + R + q, (double)__fmul_rn(s, fh), fx.to_r);
-            }
-        }
+        // warp w: 8-row batches w, w + nw, ... of the entry
+        for (int R = e.gstart + 8 * warp; R < e.gend; R += 8 * nw)
+            passb_rows(A, fx, R, min(R + 8, e.gend), 8, e.colg0 + lane, s);
     }
 }
 
 void launch_passb(const EvalArgs& a, int n_sm, cudaStream_t st)
 {
     k_passb<<<4 * n_sm, PASSB_THREADS, 0, st>>>(a);
+}
+
+// ========================================================== split finish
+// One CTA per block set at a time, warp w = tile w of the set's 256 columns:
+// add the pieces' partial sums in piece order, then Eq. 5 for the block as
+// in the evaluation kernel (psi into piece 0's partials, the column sum, the
+// snapshot values, pass B to the pass-B kernel).
+__global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
+{
+    if (A.gate && !*A.gate) return;
+    const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int si = blockIdx.x; si < A.nsets; si += gridDim.x) {
+        const SplitSet st = A.sets[si];
+        const int tile = st.col0 / TW + warp;
+        if (A.unit_need && !((A.unit_need[(int64_t)st.l * A.unit_words + (tile >> 5)] >> (tile & 31)) & 1u))
+            continue;  // a screened-out unit: its pieces wrote nothing this evaluation
+        const int colg = st.col0 + warp * TW + lane;
+        Acc t = {0.f, 0.f, 0.f, 0.f};
+        float o = 0.f;
+        for (int k = 0; k < st.split; k++) {
+            const float* q = A.split_part + ((int64_t)(st.part + k) * ITEM_COLS + warp * TW + lane) * 5;
+            df_add(t.Sh, t.Sl, q[0], q[1]);
+            df_add(t.Ph, t.Pl, q[2], q[3]);
+            o = __fadd_rn(o, q[4]);
+        }
+        float s = 0.f;
+        double psi = 0.0;
+        if (__any_sync(FULLMASK, t.Ph > 0.f)) {
+            s = block_scale(t.Sh, t.Sl, A, psi);
+            if (s > 0.f && colg < A.n)
+                red_fx(A.colfx + colg, (double)s * ((double)t.Ph + (double)t.Pl), fx.to_c);
+        }
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) psi += __shfl_xor_sync(FULLMASK, psi, off);
+        if (lane == 0 && psi != 0.0) A.psipart[(int64_t)st.item0 * NWARPS + warp] += psi;
+        if (A.zt) put_snap(A, st.l, colg, z_up(t.Sh, t.Sl), __fsqrt_ru(o));
+        if (!__any_sync(FULLMASK, s > 0.f)) continue;
+        if (!defer_passb(A, st.rstart, st.rend, st.col0 + warp * TW, s, lane))
+            passb_rows(A, fx, st.rstart, st.rend, 8, colg, s);  // the list is full
+    }
+}
+
+void launch_split_finish(const EvalArgs& a, cudaStream_t st)
+{
+    if (a.nsets > 0) k_split_finish<<<a.nsets < 4096 ? a.nsets : 4096, NWARPS * 32, 0, st>>>(a);
 }
 
 size_t stream_smem_bytes() { return sizeof(Smem) + 1024; }

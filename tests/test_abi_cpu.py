@@ -34,13 +34,23 @@ def panel_height(m, n):
     return min(512, max(32, -(-m * -(-n // ITEM_COLS) // 2048)))
 
 
+SPLIT_ROWS = 256
+
+
 def expected_plan(sizes, n):
     """Panels by the packing rule of the plan (consecutive non-empty groups up
-    to the panel height; a larger group alone), items and stages from them."""
+    to the panel height; a group of more than 256 rows cut into pieces of 256
+    rows, each a panel), items and stages from them."""
     PANEL_ROWS = panel_height(int(np.sum(sizes)), n)
     panels, cur = [], 0
     for g in sizes:
         if g == 0:
+            continue
+        if g > SPLIT_ROWS:
+            if cur:
+                panels.append(cur)
+                cur = 0
+            panels += [min(SPLIT_ROWS, g - k) for k in range(0, g, SPLIT_ROWS)]
             continue
         if cur and cur + g > PANEL_ROWS:
             panels.append(cur)
