@@ -67,6 +67,9 @@ typedef struct {
     int32_t use_screening; /* 1: Alg. 1/2 screened evaluations in ot_gs_solve; 0: dense */
     int32_t use_lower_bound; /* 1: build the set N of Def. 3 every r iterations */
     double time_budget_ms; /* <= 0: none; else ot_gs_solve stops with OTGS_ETIMEOUT */
+    double ftol;           /* > 0: a solve (single or batched) also stops, with OTGS_OK, after an
+                              accepted iteration that raised D by at most ftol max(|D_old|, |D_new|)
+                              (objective stagnation); 0 (default): off */
 } ot_gs_params;
 
 /* Counters, cumulative since create (or since ot_gs_reset_stats). */
@@ -218,6 +221,116 @@ OTGS_API const char *ot_gs_version(void);
  */
 OTGS_API int ot_gs_plan_info(const int32_t *labels_host, int64_t m, int64_t n, int32_t L,
                     int64_t *n_panels, int64_t *n_items, int64_t *n_stages);
+
+/* ------------------------------------------------------------------------
+ * Batches: many independent problems in one handle.  The paper solves one
+ * problem at a time; a batch evaluates all of its problems with one launch of
+ * the evaluation kernel (each problem's rows only meet its own columns) and
+ * solves them with one L-BFGS state per problem, each following exactly the
+ * iteration ot_gs_solve would follow alone.
+ *
+ * Layout of batch vectors ("concatenated"): problem k's alpha occupies
+ * entries [row_off_k, row_off_k + m_k) in its caller row order, and its beta
+ * entries [col_off_k, col_off_k + n_k), where row_off_k = m_0 + ... + m_{k-1}
+ * and col_off_k = n_0 + ... + n_{k-1}.  A gradient vector holds the alpha
+ * part (sum m_k entries) followed by the beta part (sum n_k entries).
+ * ------------------------------------------------------------------------ */
+
+/*
+ * Create a batch of nprob >= 1 problems.  C, ldc, a, b, labels, m, n, L are
+ * HOST arrays of nprob entries; each C[k], a[k], b[k], labels[k] is a device
+ * pointer with the meaning, requirements and borrowing rule of ot_gs_create
+ * for problem k.  gamma, mu are shared.  A batch handle accepts the ot_gs_batch_*
+ * calls, the plan calls and the parameter, statistics and timing calls; the
+ * single-problem evaluation, screening and solve calls reject it with
+ * OTGS_EINVAL unless nprob == 1.  Synchronises the stream.  Errors as
+ * ot_gs_create (the message names the problem).
+ */
+OTGS_API int ot_gs_create_batch(ot_gs **h, int32_t nprob, const float *const *C, const int64_t *ldc,
+                                const double *const *a, const double *const *b, const int32_t *const *labels,
+                                const int64_t *m, const int64_t *n, const int32_t *L, double gamma, double mu,
+                                void *stream);
+
+/* Number of problems and total rows / columns (any pointer may be NULL; host).
+ * A handle from ot_gs_create is a batch of one. */
+OTGS_API int ot_gs_batch_size(const ot_gs *h, int32_t *nprob, int64_t *m_total, int64_t *n_total);
+
+/*
+ * Dense evaluation of every problem of the batch (Eq. 4, Eq. 5), one launch
+ * of the evaluation kernel for all of them:
+ *   alpha, beta  device FP64, concatenated layout
+ *   D            device FP64 [nprob]: D_k(alpha_k, beta_k)
+ *   grad         device FP64 [sum m + sum n] (may be NULL): dD_k/dalpha_k
+ *                then dD_k/dbeta_k in the concatenated layout
+ * Asynchronous.  Errors: OTGS_EINVAL, OTGS_ECUDA.
+ */
+OTGS_API int ot_gs_batch_grad(ot_gs *h, const double *alpha, const double *beta, double *D, double *grad);
+
+/*
+ * Solve every problem of the batch: per problem the L-BFGS iteration of
+ * ot_gs_solve (dense evaluations, memory lbfgs_m) from the batch iterate
+ * (zero after create, or the point given to ot_gs_batch_set_state).  Problem
+ * k stops when ||grad D_k||_inf <= tol, or (target_D != NULL) when D_k >=
+ * target_D[k] - target_rtol |target_D[k]|, or at maxit accepted iterations,
+ * or when its line search fails; stopped problems drop out of the following
+ * evaluations.  The trials run in CUDA graphs of 16 trials captured once per
+ * handle and relaunched until every problem has stopped; the host only reads
+ * the count of running problems between graph launches.
+ *   target_D  HOST FP64 [nprob] or NULL
+ * Returns OTGS_OK when every problem stopped on tol or its target, else the
+ * status of the first problem that did not (OTGS_ENOTCONV,
+ * OTGS_ELINESEARCH), or an error.  Synchronises.
+ */
+OTGS_API int ot_gs_batch_solve(ot_gs *h, double tol, int32_t maxit, const double *target_D, double target_rtol);
+
+/* Set the batch iterate used by the next ot_gs_batch_solve (warm start):
+ * device FP64, concatenated layout.  Clears each problem's L-BFGS memory. */
+OTGS_API int ot_gs_batch_set_state(ot_gs *h, const double *alpha, const double *beta);
+
+/*
+ * Results of the last ot_gs_batch_solve.  alpha, beta: device FP64
+ * (concatenated layout; both or neither).  HOST arrays of nprob entries (each
+ * may be NULL): D at the final iterate, ||grad D||_inf there, accepted
+ * iterations, status, evaluations (line-search trials included) and t_ms, the
+ * device time from the start of the solve to the problem's stop.
+ * Synchronises.
+ */
+OTGS_API int ot_gs_batch_result(ot_gs *h, double *alpha, double *beta, double *D, double *grad_inf,
+                                int32_t *iters, int32_t *status, int64_t *evals, double *t_ms);
+
+/*
+ * Plan shape.  panel_rows: rows of whole class groups per work item (an item
+ * is panel x 256 columns); split_rows: groups taller than this are cut into
+ * pieces of this height, summed by different CTAs.  ot_gs_set_plan rebuilds
+ * the handle's plan (0 = the default of each) and synchronises; valid ranges
+ * are [32, 4096] and [64, 8192].  ot_gs_get_plan reports the current shape
+ * and the number of work items (host pointers, each may be NULL).
+ */
+OTGS_API int ot_gs_set_plan(ot_gs *h, int32_t panel_rows, int32_t split_rows);
+OTGS_API int ot_gs_get_plan(const ot_gs *h, int32_t *panel_rows, int32_t *split_rows, int64_t *n_items);
+
+/*
+ * Autotuner of the plan shape: times `evals` dense evaluations of all the
+ * handle's problems at (alpha, beta) (device FP64, concatenated layout; the
+ * cost depends on how many blocks are positive there, so pass a point like
+ * those the solver visits) for each candidate (panel_rows in {32, ..., 1024},
+ * split_rows in {128, ..., 1024}), and keeps the fastest.  The choice is
+ * cached for the process under a key of the group-size histogram (share of
+ * rows per power-of-two size class) and the size classes of the column count
+ * per problem, the row count and the number of problems; a cached shape is
+ * applied without measuring (*best_ms = 0).  Outputs are host pointers (each
+ * may be NULL).  Synchronises.  ot_gs_autotune_clear_cache forgets all shapes.
+ */
+OTGS_API int ot_gs_autotune(ot_gs *h, const double *alpha, const double *beta, int32_t evals,
+                            int32_t *panel_rows, int32_t *split_rows, double *best_ms);
+OTGS_API int ot_gs_autotune_clear_cache(void);
+
+/* Host-only plan of a batch (no GPU needed), as ot_gs_plan_info: labels_host,
+ * m, n, L are host arrays of nprob entries (labels_host[k]: host int32 [m[k]]);
+ * panel_rows, split_rows as ot_gs_set_plan (0 = default). */
+OTGS_API int ot_gs_plan_info_batch(int32_t nprob, const int32_t *const *labels_host, const int64_t *m,
+                                   const int64_t *n, const int32_t *L, int32_t panel_rows, int32_t split_rows,
+                                   int64_t *n_panels, int64_t *n_items, int64_t *n_stages);
 
 /*
  * Allocation-free dense evaluation.  The paper has no counterpart: this entry

@@ -37,7 +37,8 @@ class OTGSError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("gamma", ctypes.c_double), ("mu", ctypes.c_double), ("r", ctypes.c_int32),
                 ("lbfgs_m", ctypes.c_int32), ("use_screening", ctypes.c_int32),
-                ("use_lower_bound", ctypes.c_int32), ("time_budget_ms", ctypes.c_double)]
+                ("use_lower_bound", ctypes.c_int32), ("time_budget_ms", ctypes.c_double),
+                ("ftol", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -87,6 +88,17 @@ def lib():
         "ot_gs_plan_info": ([P, i64, i64, i32, P, P, P], ctypes.c_int),
         "ot_gs_grad_noalloc": ([P, i64, P, P, P, i64, i64, i32, dbl, dbl, P, P, P, P], ctypes.c_int),
         "ot_gs_noalloc_last_error": ([], ctypes.c_char_p),
+        "ot_gs_create_batch": ([ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P, dbl, dbl, P], ctypes.c_int),
+        "ot_gs_batch_size": ([P, P, P, P], ctypes.c_int),
+        "ot_gs_batch_grad": ([P, P, P, P, P], ctypes.c_int),
+        "ot_gs_batch_solve": ([P, dbl, i32, P, dbl], ctypes.c_int),
+        "ot_gs_batch_set_state": ([P, P, P], ctypes.c_int),
+        "ot_gs_batch_result": ([P, P, P, P, P, P, P, P, P], ctypes.c_int),
+        "ot_gs_set_plan": ([P, i32, i32], ctypes.c_int),
+        "ot_gs_get_plan": ([P, P, P, P], ctypes.c_int),
+        "ot_gs_autotune": ([P, P, P, i32, P, P, P], ctypes.c_int),
+        "ot_gs_autotune_clear_cache": ([], ctypes.c_int),
+        "ot_gs_plan_info_batch": ([i32, P, P, P, P, i32, i32, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -299,6 +311,125 @@ def ot_gs_grad_noalloc(C, a, b, labels_host, L, gamma, mu, alpha, beta, out, str
     return rc
 
 
+def _host_array(vals, ctype):
+    arr = (ctype * len(vals))(*vals)
+    return arr, ctypes.cast(arr, ctypes.c_void_p)
+
+
+def ot_gs_create_batch(Cs, As, Bs, labels, Ls, gamma, mu, stream=None):
+    """Batch of independent problems: lists of CUDA tensors C_k (m_k, n_k)
+    float32 (unit column stride), a_k, b_k float64, labels_k int32, and class
+    counts L_k.  Returns the raw handle."""
+    import torch
+    k = len(Cs)
+    if not (len(As) == len(Bs) == len(labels) == len(Ls) == k) or k == 0:
+        raise ValueError("need equally long, non-empty lists")
+    cp, lp, ap, bp, lab, ms, ns = [], [], [], [], [], [], []
+    for q in range(k):
+        C = Cs[q]
+        if C.dim() != 2 or C.stride(1) != 1 or C.dtype != torch.float32 or not C.is_cuda:
+            raise ValueError(f"C[{q}] must be a 2-D float32 CUDA tensor with unit column stride")
+        m, n = C.shape
+        cp.append(C.data_ptr())
+        lp.append(C.stride(0))
+        ap.append(_ptr(As[q], torch.float64, m, f"a[{q}]").value)
+        bp.append(_ptr(Bs[q], torch.float64, n, f"b[{q}]").value)
+        lab.append(_ptr(labels[q], torch.int32, m, f"labels[{q}]").value)
+        ms.append(m)
+        ns.append(n)
+    keep = [_host_array(cp, ctypes.c_void_p), _host_array(lp, ctypes.c_int64), _host_array(ap, ctypes.c_void_p),
+            _host_array(bp, ctypes.c_void_p), _host_array(lab, ctypes.c_void_p), _host_array(ms, ctypes.c_int64),
+            _host_array(ns, ctypes.c_int64), _host_array([int(x) for x in Ls], ctypes.c_int32)]
+    h = ctypes.c_void_p()
+    rc = lib().ot_gs_create_batch(ctypes.byref(h), k, *[p for _, p in keep], float(gamma), float(mu),
+                                  _stream_ptr(stream))
+    if rc != OTGS_OK:
+        raise OTGSError(rc, lib().ot_gs_last_error(None).decode())
+    return h
+
+
+def ot_gs_batch_size(h):
+    k, m, n = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    _check(h, lib().ot_gs_batch_size(h, ctypes.byref(k), ctypes.byref(m), ctypes.byref(n)))
+    return k.value, m.value, n.value
+
+
+def ot_gs_batch_grad(h, alpha, beta, D, grad=None):
+    import torch
+    return _check(h, lib().ot_gs_batch_grad(h, _ptr(alpha, torch.float64, name="alpha"),
+                                            _ptr(beta, torch.float64, name="beta"),
+                                            _ptr(D, torch.float64, name="D"),
+                                            _ptr(grad, torch.float64, name="grad")))
+
+
+def ot_gs_batch_solve(h, tol, maxit, target_D=None, target_rtol=0.0):
+    tgt = None
+    if target_D is not None:
+        tgt = np.ascontiguousarray(target_D, dtype=np.float64)
+    return _check(h, lib().ot_gs_batch_solve(h, float(tol), int(maxit),
+                                             None if tgt is None else tgt.ctypes.data_as(ctypes.c_void_p),
+                                             float(target_rtol)))
+
+
+def ot_gs_batch_set_state(h, alpha, beta):
+    import torch
+    return _check(h, lib().ot_gs_batch_set_state(h, _ptr(alpha, torch.float64, name="alpha"),
+                                                 _ptr(beta, torch.float64, name="beta")))
+
+
+def ot_gs_batch_result(h, nprob, alpha=None, beta=None):
+    """Per-problem results of the last batch solve as numpy arrays (and the
+    iterate into alpha, beta when given)."""
+    import torch
+    D, gi, t = np.empty(nprob), np.empty(nprob), np.empty(nprob)
+    it, stt = np.empty(nprob, dtype=np.int32), np.empty(nprob, dtype=np.int32)
+    ev = np.empty(nprob, dtype=np.int64)
+    vp = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+    _check(h, lib().ot_gs_batch_result(h, _ptr(alpha, torch.float64, name="alpha"),
+                                       _ptr(beta, torch.float64, name="beta"), vp(D), vp(gi), vp(it), vp(stt),
+                                       vp(ev), vp(t)))
+    return dict(D=D, grad_inf=gi, iters=it, status=stt, evals=ev, t_ms=t)
+
+
+def ot_gs_set_plan(h, panel_rows=0, split_rows=0):
+    return _check(h, lib().ot_gs_set_plan(h, int(panel_rows), int(split_rows)))
+
+
+def ot_gs_get_plan(h):
+    pr, sr, ni = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(h, lib().ot_gs_get_plan(h, ctypes.byref(pr), ctypes.byref(sr), ctypes.byref(ni)))
+    return dict(panel_rows=pr.value, split_rows=sr.value, n_items=ni.value)
+
+
+def ot_gs_autotune(h, alpha, beta, evals=5):
+    import torch
+    pr, sr, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    _check(h, lib().ot_gs_autotune(h, _ptr(alpha, torch.float64, name="alpha"),
+                                   _ptr(beta, torch.float64, name="beta"), int(evals), ctypes.byref(pr),
+                                   ctypes.byref(sr), ctypes.byref(ms)))
+    return dict(panel_rows=pr.value, split_rows=sr.value, best_ms=ms.value)
+
+
+def ot_gs_autotune_clear_cache():
+    return lib().ot_gs_autotune_clear_cache()
+
+
+def ot_gs_plan_info_batch(labels_list, ns, Ls, panel_rows=0, split_rows=0):
+    """Host-only plan of a batch: counts of panels, work items and stages."""
+    k = len(labels_list)
+    labs = [np.ascontiguousarray(x, dtype=np.int32) for x in labels_list]
+    lp = _host_array([x.ctypes.data for x in labs], ctypes.c_void_p)
+    mp = _host_array([len(x) for x in labs], ctypes.c_int64)
+    npp = _host_array([int(x) for x in ns], ctypes.c_int64)
+    Lp = _host_array([int(x) for x in Ls], ctypes.c_int32)
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().ot_gs_plan_info_batch(k, lp[1], mp[1], npp[1], Lp[1], int(panel_rows), int(split_rows),
+                                     ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if rc != OTGS_OK:
+        raise OTGSError(rc, "invalid plan input")
+    return dict(n_panels=a.value, n_items=b.value, n_stages=c.value)
+
+
 # ------------------------------------------------------------ convenience
 class GroupSparseOT:
     """One problem on the current CUDA device.  Keeps references to the
@@ -368,3 +499,79 @@ class GroupSparseOT:
 
     def stats(self):
         return ot_gs_get_stats(self.h)
+
+
+class GroupSparseOTBatch:
+    """Independent problems solved together (one evaluation kernel for all,
+    one L-BFGS state per problem).  Vectors use the concatenated layout:
+    problem k's alpha at rows row_off[k]:row_off[k]+m_k, its beta at
+    col_off[k]:col_off[k]+n_k."""
+
+    def __init__(self, Cs, As, Bs, labels, Ls, gamma, mu, stream=None):
+        self._keep = (list(Cs), list(As), list(Bs), list(labels))
+        self.ms = [int(C.shape[0]) for C in Cs]
+        self.ns = [int(C.shape[1]) for C in Cs]
+        self.nprob = len(Cs)
+        self.row_off = np.concatenate([[0], np.cumsum(self.ms)]).astype(np.int64)
+        self.col_off = np.concatenate([[0], np.cumsum(self.ns)]).astype(np.int64)
+        self.m, self.n = int(self.row_off[-1]), int(self.col_off[-1])
+        self.device = Cs[0].device
+        self.h = ot_gs_create_batch(Cs, As, Bs, labels, Ls, gamma, mu, stream)
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            ot_gs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, **kw):
+        p = ot_gs_get_params(self.h)
+        for k, v in kw.items():
+            setattr(p, k, v)
+        ot_gs_set_params(self.h, p)
+
+    def grad(self, alpha, beta, with_grad=True):
+        import torch
+        D = torch.empty(self.nprob, dtype=torch.float64, device=self.device)
+        g = torch.empty(self.m + self.n, dtype=torch.float64, device=self.device) if with_grad else None
+        ot_gs_batch_grad(self.h, alpha, beta, D, g)
+        return D, g
+
+    def solve(self, tol=1e-8, maxit=1000, target_D=None, target_rtol=0.0):
+        return ot_gs_batch_solve(self.h, tol, maxit, target_D, target_rtol)
+
+    def set_state(self, alpha, beta):
+        ot_gs_batch_set_state(self.h, alpha, beta)
+
+    def result(self, with_iterate=True):
+        import torch
+        al = be = None
+        if with_iterate:
+            al = torch.empty(self.m, dtype=torch.float64, device=self.device)
+            be = torch.empty(self.n, dtype=torch.float64, device=self.device)
+        r = ot_gs_batch_result(self.h, self.nprob, al, be)
+        if with_iterate:
+            r["alpha"], r["beta"] = al, be
+        return r
+
+    def set_plan(self, panel_rows=0, split_rows=0):
+        ot_gs_set_plan(self.h, panel_rows, split_rows)
+
+    def plan(self):
+        return ot_gs_get_plan(self.h)
+
+    def autotune(self, alpha, beta, evals=5):
+        return ot_gs_autotune(self.h, alpha, beta, evals)
+
+    def split(self, vec, k, part):
+        """Problem k's alpha (part 'alpha') or beta (part 'beta') of a
+        concatenated vector; for a gradient vector the beta part starts at m."""
+        if part == "alpha":
+            return vec[self.row_off[k]:self.row_off[k + 1]]
+        base = self.m if vec.numel() == self.m + self.n else 0
+        return vec[base + self.col_off[k]:base + self.col_off[k + 1]]

@@ -15,6 +15,8 @@ static thread_local std::string g_create_error;
 
 namespace otgs {
 
+void set_create_error(const std::string& msg) { g_create_error = msg; }
+
 bool Handle::fail(int code, const std::string& msg)
 {
     err = msg;
@@ -49,8 +51,10 @@ Handle::~Handle()
 {
     if (st_synced_ok) cudaStreamSynchronize(st);
     delete solver;
+    destroy_batch(batch);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (void* p : allocs) cudaFree(p);
+    free_plan();
     if (host_scal) cudaFreeHost(host_scal);
 }
 
@@ -64,109 +68,207 @@ static T* upload(Handle* h, const std::vector<T>& v, const char* what)
     return d;
 }
 
-bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double* b_, const int32_t* labels_,
-                  int64_t m_, int64_t n_, int32_t L_, double gamma_, double mu_, cudaStream_t st_)
+void* Handle::plan_alloc(size_t bytes, const char* what)
+{
+    void* p = dalloc(bytes, what);
+    if (p) {
+        allocs.pop_back();
+        plan_allocs.push_back(p);
+    }
+    return p;
+}
+
+void Handle::free_plan()
+{
+    for (void* p : plan_allocs) cudaFree(p);
+    plan_allocs.clear();
+}
+
+template <class T>
+static T* plan_upload(Handle* h, const std::vector<T>& v, const char* what)
+{
+    T* d = (T*)h->plan_alloc(sizeof(T) * (v.empty() ? 1 : v.size()), what);
+    if (!d) return nullptr;
+    if (!v.empty() && !h->ck(cudaMemcpyAsync(d, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, h->st), what))
+        return nullptr;
+    return d;
+}
+
+bool Handle::init(int32_t np, const float* const* C_, const int64_t* ldc_, const double* const* a_,
+                  const double* const* b_, const int32_t* const* labels_, const int64_t* m_, const int64_t* n_,
+                  const int32_t* L_, double gamma_, double mu_, cudaStream_t st_)
 {
     st = st_;
-    m = m_; n = n_; L = L_;
+    nprob = np;
     prm.gamma = gamma_; prm.mu = mu_;
     prm.r = 10; prm.lbfgs_m = 10; prm.use_screening = 0; prm.use_lower_bound = 1;
     prm.time_budget_ms = 0.0;
-    std::vector<int32_t> lab(m);
-    if (!ck(cudaMemcpyAsync(lab.data(), labels_, sizeof(int32_t) * m, cudaMemcpyDeviceToHost, st), "labels D2H"))
-        return false;
+    prm.ftol = 0.0;
+    // labels to the host, one array for all problems
+    int64_t mtot = 0;
+    for (int32_t k = 0; k < np; k++) mtot += m_[k];
+    labels_h.resize(mtot);
+    pm_h.assign(m_, m_ + np);
+    pn_h.assign(n_, n_ + np);
+    pL_h.assign(L_, L_ + np);
+    {
+        int64_t off = 0;
+        for (int32_t k = 0; k < np; k++) {
+            if (!ck(cudaMemcpyAsync(labels_h.data() + off, labels_[k], sizeof(int32_t) * m_[k],
+                                    cudaMemcpyDeviceToHost, st),
+                    "labels D2H"))
+                return false;
+            off += m_[k];
+        }
+    }
     if (!ck(cudaStreamSynchronize(st), "labels sync")) return false;
     st_synced_ok = true;
-    std::string pe = build_plan(lab.data(), m, n, L, hp);
-    if (!pe.empty()) return fail(OTGS_EINVAL, pe);
+    {
+        std::vector<const int32_t*> lp(np);
+        int64_t off = 0;
+        for (int32_t k = 0; k < np; k++) {
+            lp[k] = labels_h.data() + off;
+            off += m_[k];
+        }
+        std::string pe = build_plan_batch(np, lp.data(), m_, n_, L_, PlanParams(), hp);
+        if (!pe.empty()) return fail(OTGS_EINVAL, pe);
+    }
+    m = hp.m; n = hp.n; L = hp.L;
     ntiles = hp.ntiles;
     unit_words = (ntiles + 31) / 32;
+    auto where = [&](int32_t k) { return np == 1 ? std::string() : " (problem " + std::to_string(k) + ")"; };
     // validation of C, a, b on the device
     {
-        double* sums = (double*)dalloc(2 * sizeof(double), "check sums");
-        int* flags = (int*)dalloc(4 * sizeof(int), "check flags");
+        double* sums = (double*)dalloc(2 * sizeof(double) * np, "check sums");
+        int* flags = (int*)dalloc(4 * sizeof(int) * np, "check flags");
         if (!sums || !flags) return false;
-        if (!ck(cudaMemsetAsync(sums, 0, 2 * sizeof(double), st), "memset")) return false;
-        if (!ck(cudaMemsetAsync(flags, 0, 4 * sizeof(int), st), "memset")) return false;
-        launch_check_finite(C_, ldc_, (int32_t)m, (int32_t)n, a_, b_, sums, flags, st);
-        double hs[2];
-        int hf[4];
-        if (!ck(cudaMemcpyAsync(hs, sums, sizeof(hs), cudaMemcpyDeviceToHost, st), "check D2H")) return false;
-        if (!ck(cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, st), "check D2H")) return false;
+        if (!ck(cudaMemsetAsync(sums, 0, 2 * sizeof(double) * np, st), "memset")) return false;
+        if (!ck(cudaMemsetAsync(flags, 0, 4 * sizeof(int) * np, st), "memset")) return false;
+        for (int32_t k = 0; k < np; k++)
+            launch_check_finite(C_[k], ldc_[k], (int32_t)m_[k], (int32_t)n_[k], a_[k], b_[k], sums + 2 * k,
+                                flags + 4 * k, st);
+        std::vector<double> hs(2 * (size_t)np);
+        std::vector<int> hf(4 * (size_t)np);
+        if (!ck(cudaMemcpyAsync(hs.data(), sums, sizeof(double) * hs.size(), cudaMemcpyDeviceToHost, st), "check D2H"))
+            return false;
+        if (!ck(cudaMemcpyAsync(hf.data(), flags, sizeof(int) * hf.size(), cudaMemcpyDeviceToHost, st), "check D2H"))
+            return false;
         if (!ck(cudaStreamSynchronize(st), "check sync")) return false;
-        if (hf[0]) return fail(OTGS_ENONFINITE, "C has a non-finite entry");
-        if (hf[1]) return fail(OTGS_EINVAL, "C has a negative entry");
-        if (hf[2]) return fail(OTGS_EINVAL, "a and b must be positive and finite");
-        if (!(std::fabs(hs[0] - hs[1]) <= 1e-12 * std::fmax(1.0, std::fmax(hs[0], hs[1]))))
-            return fail(OTGS_EINVAL, "sum(a) != sum(b)");
-        unsigned cbits = (unsigned)hf[3];
-        memcpy(&cmax, &cbits, sizeof(float));
+        for (int32_t k = 0; k < np; k++) {
+            const int* f = hf.data() + 4 * k;
+            const double* sm = hs.data() + 2 * k;
+            if (f[0]) return fail(OTGS_ENONFINITE, "C has a non-finite entry" + where(k));
+            if (f[1]) return fail(OTGS_EINVAL, "C has a negative entry" + where(k));
+            if (f[2]) return fail(OTGS_EINVAL, "a and b must be positive and finite" + where(k));
+            if (!(std::fabs(sm[0] - sm[1]) <= 1e-12 * std::fmax(1.0, std::fmax(sm[0], sm[1]))))
+                return fail(OTGS_EINVAL, "sum(a) != sum(b)" + where(k));
+            unsigned cbits = (unsigned)f[3];
+            float cm;
+            memcpy(&cm, &cbits, sizeof(float));
+            cmax = std::max(cmax, cm);
+        }
     }
-    // C: borrow when class-sorted and laid out as TMA needs (16-byte aligned
-    // base and row stride), else a sorted, padded copy
-    bool aligned = (reinterpret_cast<uintptr_t>(C_) % 16 == 0) && (ldc_ % 4 == 0);
     dp.perm = upload(this, hp.perm, "perm");
     if (!dp.perm) return false;
-    if (hp.sorted_identity && aligned) {
-        C = C_;
-        ldc = ldc_;
-        own_C = false;
-    } else {
-        ldc = (n + 3) / 4 * 4;
-        float* Cs = (float*)dalloc(sizeof(float) * (size_t)(m * ldc), "sorted C");
-        if (!Cs) return false;
-        launch_gather_rows(C_, ldc_, dp.perm, (int32_t)m, (int32_t)n, Cs, ldc, st);
-        C = Cs;
-        own_C = true;
+    // C of each problem: borrowed when class-sorted and laid out as TMA needs
+    // (16-byte aligned base and row stride), else a sorted, padded copy
+    probs_h.resize(np);
+    {
+        std::vector<char> copy(np, 0);
+        size_t copy_floats = 0;
+        int64_t off = 0;
+        for (int32_t k = 0; k < np; k++) {
+            bool sorted = true;
+            for (int64_t i = 1; i < m_[k] && sorted; i++) sorted = labels_h[off + i] >= labels_h[off + i - 1];
+            const bool aligned = (reinterpret_cast<uintptr_t>(C_[k]) % 16 == 0) && (ldc_[k] % 4 == 0);
+            copy[k] = !(sorted && aligned);
+            if (copy[k]) copy_floats += (size_t)m_[k] * (size_t)((n_[k] + 3) / 4 * 4);
+            off += m_[k];
+        }
+        float* Cs = nullptr;
+        if (copy_floats) {
+            Cs = (float*)dalloc(sizeof(float) * copy_floats, "sorted C");
+            if (!Cs) return false;
+        }
+        size_t at = 0;
+        for (int32_t k = 0; k < np; k++) {
+            ProbDesc& pd = probs_h[k];
+            memset(&pd, 0, sizeof(pd));
+            pd.m = (int32_t)m_[k];
+            pd.n = (int32_t)n_[k];
+            pd.roff = hp.proff[k];
+            pd.coff = hp.pcoff[k];
+            pd.bcoff = hp.pbcoff[k];
+            if (copy[k]) {
+                const int64_t ld = (n_[k] + 3) / 4 * 4;
+                launch_gather_rows(C_[k], ldc_[k], dp.perm + pd.roff, pd.roff, pd.m, pd.n, Cs + at, ld, st);
+                pd.C = Cs + at;
+                pd.ldc = ld;
+                at += (size_t)m_[k] * (size_t)ld;
+            } else {
+                pd.C = C_[k];
+                pd.ldc = ldc_[k];
+            }
+        }
     }
-    // plan arrays
+    probs = upload(this, probs_h, "problem table");
+    if (!probs) return false;
+    {
+        std::vector<TmaMaps> tm(np);
+        for (int32_t k = 0; k < np; k++) {
+            std::string te = make_tmaps(probs_h[k].C, probs_h[k].ldc, probs_h[k].m, probs_h[k].n, tm[k]);
+            if (!te.empty()) return fail(OTGS_ECUDA, te + where(k));
+        }
+        static_assert(sizeof(TmaMaps) == 2 * TMA_BOXES * sizeof(CUtensorMap), "maps are packed");
+        maps = (CUtensorMap*)upload(this, tm, "TMA descriptors");  // cudaMalloc: 256-byte aligned
+        if (!maps) return false;
+    }
+    // row groups (independent of the plan's parameters)
     dp.goff = upload(this, hp.goff, "goff");
     dp.rgroup = upload(this, hp.rgroup, "rgroup");
     dp.rowg = upload(this, hp.rowg, "row groups");
-    dp.prows = upload(this, hp.prows, "prows");
-    dp.pW = upload(this, hp.pW, "pW");
-    dp.pnch = upload(this, hp.pnch, "pnch");
-    dp.pitem = upload(this, hp.pitem, "pitem");
-    dp.psplit = upload(this, hp.psplit, "psplit");
-    dp.gpanel = upload(this, hp.gpanel, "gpanel");
-    dp.item_panel = upload(this, hp.item_panel, "item_panel");
-    dp.item_chunk = upload(this, hp.item_chunk, "item_chunk");
-    dp.exec_order = upload(this, hp.exec_order, "exec_order");
-    dp.desc = upload(this, hp.desc, "item descriptors");
-    if (!dp.goff || !dp.rgroup || !dp.rowg || !dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.psplit || !dp.gpanel ||
-        !dp.item_panel || !dp.item_chunk || !dp.exec_order || !dp.desc)
-        return false;
-    {
-        std::string te = make_tmaps(C, ldc, m, n, tmaps);
-        if (!te.empty()) return fail(OTGS_ECUDA, te);
-    }
-    // marginals (a in sorted order)
+    if (!dp.goff || !dp.rgroup || !dp.rowg) return false;
+    // marginals: a in sorted order, b concatenated
     a_sorted = (double*)dalloc(sizeof(double) * m, "a_sorted");
     b = (double*)dalloc(sizeof(double) * n, "b");
     if (!a_sorted || !b) return false;
-    launch_permute_f64(a_, dp.perm, (int32_t)m, a_sorted, true, st);
-    if (!ck(cudaMemcpyAsync(b, b_, sizeof(double) * n, cudaMemcpyDeviceToDevice, st), "b copy")) return false;
+    if (np == 1) {
+        launch_permute_f64(a_[0], dp.perm, (int32_t)m, a_sorted, true, st);
+    } else {
+        double* acat = (double*)dalloc(sizeof(double) * m, "a (concatenated)");
+        if (!acat) return false;
+        for (int32_t k = 0; k < np; k++)
+            if (!ck(cudaMemcpyAsync(acat + hp.proff[k], a_[k], sizeof(double) * m_[k], cudaMemcpyDeviceToDevice, st),
+                    "a copy"))
+                return false;
+        launch_permute_f64(acat, dp.perm, (int32_t)m, a_sorted, true, st);
+    }
+    for (int32_t k = 0; k < np; k++)
+        if (!ck(cudaMemcpyAsync(b + hp.pcoff[k], b_[k], sizeof(double) * n_[k], cudaMemcpyDeviceToDevice, st),
+                "b copy"))
+            return false;
     // evaluation buffers
     rowA = (float4*)dalloc(sizeof(float4) * (size_t)m, "rowA");
-    B2 = (float2*)dalloc(sizeof(float2) * (size_t)padded_cols(n), "B2");
+    B2 = (float2*)dalloc(sizeof(float2) * (size_t)hp.nb2, "B2");
     ctl = (EvalCtl*)dalloc(sizeof(EvalCtl), "evaluation control");
     kerr = (int*)dalloc(sizeof(int) * 4, "kernel error");
     alpha_eval = (double*)dalloc(sizeof(double) * m, "alpha_eval");
     rowfx = (unsigned long long*)dalloc(sizeof(unsigned long long) * (size_t)m, "row sums");
     colfx = (unsigned long long*)dalloc(sizeof(unsigned long long) * (size_t)n, "column sums");
-    psipart = (double*)dalloc(sizeof(double) * (size_t)hp.nitems() * NWARPS, "psipart");
+    pfx = (FxScale*)dalloc(sizeof(FxScale) * (size_t)np, "per-problem fixed-point scales");
+    if (!rowA || !B2 || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !pfx) return false;
+    if (!ck(cudaMemsetAsync(B2, 0, sizeof(float2) * (size_t)hp.nb2, st), "memset B2")) return false;
+    if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
     passb_cap = (int)std::min<int64_t>((int64_t)L * ntiles, 65536);
     passb = (PassB*)dalloc(sizeof(PassB) * (size_t)passb_cap, "pass-B list");
-    split_part = (float*)dalloc(sizeof(float) * 5 * ITEM_COLS * (size_t)hp.nsplit_slots, "split partial sums");
-    dp.sets = upload(this, hp.sets, "split block sets");
-    if (!passb || !split_part || !dp.sets) return false;
-    if (!rowA || !B2 || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !psipart) return false;
-    if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
+    if (!passb) return false;
     {
         int dev = 0;
         if (!ck(cudaGetDevice(&dev), "cudaGetDevice")) return false;
         if (!ck(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "SM count")) return false;
     }
+    if (!stream_prepare()) return fail(OTGS_ECUDA, "cudaFuncSetAttribute(evaluation kernel)");
+    if (!setup_plan(PlanParams())) return false;
     nred = reduce_blocks((int32_t)m, (int32_t)n);
     block_part = (double*)dalloc(sizeof(double) * 4 * (size_t)nred, "block_part");
     counter = (unsigned*)dalloc(sizeof(unsigned) * 4, "counter");
@@ -179,12 +281,78 @@ bool Handle::init(const float* C_, int64_t ldc_, const double* a_, const double*
     return true;
 }
 
+// The work decomposition for the given parameters (Sec. 2.3's blocks in
+// panels and column chunks) and every device buffer whose size depends on it.
+bool Handle::setup_plan(const PlanParams& pp)
+{
+    if (!plan_allocs.empty()) {
+        if (!ck(cudaStreamSynchronize(st), "re-plan sync")) return false;
+        free_plan();
+        std::vector<const int32_t*> lp(nprob);
+        int64_t off = 0;
+        for (int32_t k = 0; k < nprob; k++) {
+            lp[k] = labels_h.data() + off;
+            off += pm_h[k];
+        }
+        HostPlan nhp;
+        std::string pe = build_plan_batch(nprob, lp.data(), pm_h.data(), pn_h.data(), pL_h.data(), pp, nhp);
+        if (!pe.empty()) return fail(OTGS_EINVAL, pe);
+        hp = std::move(nhp);
+    }
+    plan_params = pp;
+    plan_gen++;
+    dp.prows = plan_upload(this, hp.prows, "prows");
+    dp.pW = plan_upload(this, hp.pW, "pW");
+    dp.pnch = plan_upload(this, hp.pnch, "pnch");
+    dp.pitem = plan_upload(this, hp.pitem, "pitem");
+    dp.psplit = plan_upload(this, hp.psplit, "psplit");
+    dp.gpanel = plan_upload(this, hp.gpanel, "gpanel");
+    dp.item_panel = plan_upload(this, hp.item_panel, "item_panel");
+    dp.item_chunk = plan_upload(this, hp.item_chunk, "item_chunk");
+    dp.exec_order = plan_upload(this, hp.exec_order, "exec_order");
+    dp.desc = plan_upload(this, hp.desc, "item descriptors");
+    dp.sets = plan_upload(this, hp.sets, "split block sets");
+    if (!dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.psplit || !dp.gpanel || !dp.item_panel ||
+        !dp.item_chunk || !dp.exec_order || !dp.desc || !dp.sets)
+        return false;
+    bprob_h.resize(nprob);
+    {
+        std::vector<int32_t> first(nprob + 1, hp.nitems());
+        for (int p = hp.npanels() - 1; p >= 0; p--) first[hp.pprob[p]] = hp.pitem[p];
+        for (int32_t k = 0; k < nprob; k++) {
+            BProb& b = bprob_h[k];
+            b.roff = hp.proff[k];
+            b.coff = hp.pcoff[k];
+            b.bcoff = hp.pbcoff[k];
+            b.m = hp.pm[k];
+            b.n = hp.pn[k];
+            b.voff = b.roff + b.coff;
+            b.item0 = first[k];
+            b.item1 = first[k + 1];
+        }
+    }
+    bprob = plan_upload(this, bprob_h, "batch problem table");
+    if (!bprob) return false;
+    psipart = (double*)plan_alloc(sizeof(double) * (size_t)hp.nitems() * NWARPS, "psipart");
+    split_part = (float*)plan_alloc(sizeof(float) * 5 * ITEM_COLS * (size_t)hp.nsplit_slots, "split partial sums");
+    if (!psipart || !split_part) return false;
+    if (screen_alloc) {
+        item_active = (uint8_t*)plan_alloc((size_t)hp.nitems(), "item_active");
+        stage_m8 = (uint8_t*)plan_alloc((size_t)hp.nstages * STAGE_ROWS, "stage masks");
+        if (!item_active || !stage_m8) return false;
+        invalidate_screen();
+    }
+    return ck(cudaGetLastError(), "plan upload");
+}
+
 EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool snap)
 {
     EvalArgs e;
     memset(&e, 0, sizeof(e));
-    e.C = C; e.ldc = ldc;
+    e.probs = probs;
+    e.maps = maps;
     e.m = (int32_t)m; e.n = (int32_t)n; e.L = L; e.ntiles = ntiles;
+    e.fx_m = (int32_t)hp.max_m; e.fx_n = (int32_t)hp.max_n;
     e.nitems = hp.nitems();
     e.rowA = rowA; e.rowg = dp.rowg;
     e.B2 = B2;
@@ -210,6 +378,8 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.th2_cut = fc;
     e.gamma = (float)prm.gamma;
     e.inv2g = 1.0 / (2.0 * prm.gamma);
+    e.inv2g_hi = (float)e.inv2g;
+    e.inv2g_lo = (float)(e.inv2g - (double)e.inv2g_hi);
     return e;
 }
 
@@ -219,6 +389,7 @@ ReduceArgs Handle::reduce_args(const uint8_t* active, double* out_caller, double
     ReduceArgs r;
     memset(&r, 0, sizeof(r));
     r.m = (int32_t)m; r.n = (int32_t)n; r.nitems = hp.nitems();
+    r.fx_m = (int32_t)hp.max_m; r.fx_n = (int32_t)hp.max_n;
     r.perm = dp.perm;
     r.item_active = active;
     r.rowfx = rowfx; r.colfx = colfx; r.psipart = psipart;
@@ -253,7 +424,7 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
         }
     }
     if (timing) cudaEventRecord(ev_pool[ev_used], st);
-    launch_stream(e, tmaps, n_ctas, st);
+    launch_stream(e, n_ctas, st);
     if (timing) {
         cudaEventRecord(ev_pool[ev_used + 1], st);
         ev_used += 2;
@@ -333,7 +504,7 @@ int ot_gs_create(ot_gs** out, const float* C, int64_t ldc, const double* a, cons
     }
     Handle* h = new (std::nothrow) Handle();
     if (!h) { g_create_error = "out of host memory"; return OTGS_ENOMEM; }
-    if (!h->init(C, ldc, a, b, labels, m, n, L, gamma, mu, (cudaStream_t)stream)) {
+    if (!h->init(1, &C, &ldc, &a, &b, &labels, &m, &n, &L, gamma, mu, (cudaStream_t)stream)) {
         g_create_error = h->err;
         int code = h->last_code ? h->last_code : OTGS_ECUDA;
         delete h;
@@ -363,8 +534,8 @@ int ot_gs_set_params(ot_gs* hh, const ot_gs_params* p)
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!p) { h->fail(OTGS_EINVAL, "params is NULL"); return OTGS_EINVAL; }
     if (!(p->gamma > 0.0) || !std::isfinite(p->gamma) || !(p->mu >= 0.0) || !std::isfinite(p->mu) || p->r < 1 ||
-        p->lbfgs_m < 1 || p->lbfgs_m > 32) {
-        h->fail(OTGS_EINVAL, "invalid params (gamma > 0, mu >= 0, r >= 1, 1 <= lbfgs_m <= 32)");
+        p->lbfgs_m < 1 || p->lbfgs_m > 32 || !(p->ftol >= 0.0)) {
+        h->fail(OTGS_EINVAL, "invalid params (gamma > 0, mu >= 0, r >= 1, 1 <= lbfgs_m <= 32, ftol >= 0)");
         return OTGS_EINVAL;
     }
     bool reg_changed = p->gamma != h->prm.gamma || p->mu != h->prm.mu;
@@ -385,6 +556,7 @@ int ot_gs_grad(ot_gs* hh, const double* alpha, const double* beta, double* out)
 {
     H_CHECK(hh);
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
     if (!alpha || !beta || !out) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
     if (!h->eval_dense(alpha, false, beta, out, nullptr, nullptr, false)) return h->last_code;
     return OTGS_OK;
@@ -451,6 +623,22 @@ int ot_gs_plan_info(const int32_t* labels_host, int64_t m, int64_t n, int32_t L,
     if (!labels_host) return OTGS_EINVAL;
     HostPlan hp;
     if (!build_plan(labels_host, m, n, L, hp).empty()) return OTGS_EINVAL;
+    if (n_panels) *n_panels = hp.npanels();
+    if (n_items) *n_items = hp.nitems();
+    if (n_stages) *n_stages = hp.nstages;
+    return OTGS_OK;
+}
+
+int ot_gs_plan_info_batch(int32_t nprob, const int32_t* const* labels_host, const int64_t* m, const int64_t* n,
+                          const int32_t* L, int32_t panel_rows, int32_t split_rows, int64_t* n_panels,
+                          int64_t* n_items, int64_t* n_stages)
+{
+    if (nprob <= 0 || !labels_host || !m || !n || !L || panel_rows < 0 || split_rows < 0) return OTGS_EINVAL;
+    HostPlan hp;
+    PlanParams pp;
+    pp.panel_rows = panel_rows;
+    pp.split_rows = split_rows;
+    if (!build_plan_batch(nprob, labels_host, m, n, L, pp, hp).empty()) return OTGS_EINVAL;
     if (n_panels) *n_panels = hp.npanels();
     if (n_items) *n_items = hp.nitems();
     if (n_stages) *n_stages = hp.nstages;

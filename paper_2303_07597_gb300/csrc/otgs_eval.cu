@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
     if (R.gate && !*R.gate) return;  // a skipped solver trial
     __shared__ double sh[4][RED_WARPS];
     __shared__ bool last;
-    const FxScale fx = fx_scale(R.ctl->amax, R.ctl->bmax, R.m, R.n, R.gamma);
+    const FxScale fx = fx_scale(R.ctl->amax, R.ctl->bmax, R.fx_m, R.fx_n, R.gamma);
     const int t = blockIdx.x * RED_THREADS + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double ab = 0.0, dt = 0.0, inf = 0.0, psi = 0.0;
@@ -164,24 +164,24 @@ void launch_reduce(const ReduceArgs& a, cudaStream_t st)
 
 // ---------------------------------------------------------- utilities
 __global__ void k_gather_rows(const float* __restrict__ C, int64_t ldc, const int32_t* __restrict__ perm,
-                              int32_t m, int32_t n, float* Cs, int64_t ldcs)
+                              int32_t base, int32_t m, int32_t n, float* Cs, int64_t ldcs)
 {
     const int r = blockIdx.y;
-    const float* src = C + (int64_t)perm[r] * ldc;
+    const float* src = C + (int64_t)(perm[r] - base) * ldc;
     float* dst = Cs + (int64_t)r * ldcs;
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < ldcs; j += (int64_t)gridDim.x * blockDim.x)
         dst[j] = j < n ? src[j] : 0.f;
 }
 
-void launch_gather_rows(const float* C, int64_t ldc, const int32_t* perm, int32_t m, int32_t n, float* Cs,
-                        int64_t ldcs, cudaStream_t st)
+void launch_gather_rows(const float* C, int64_t ldc, const int32_t* perm, int32_t base, int32_t m, int32_t n,
+                        float* Cs, int64_t ldcs, cudaStream_t st)
 {
     int bx = (int)((ldcs + 255) / 256);
     if (bx > 64) bx = 64;
     for (int32_t r0 = 0; r0 < m; r0 += 65535) {
         int32_t rows = m - r0 < 65535 ? m - r0 : 65535;
         dim3 grid(bx, rows);
-        k_gather_rows<<<grid, 256, 0, st>>>(C, ldc, perm + r0, rows, n, Cs + (int64_t)r0 * ldcs, ldcs);
+        k_gather_rows<<<grid, 256, 0, st>>>(C, ldc, perm + r0, base, rows, n, Cs + (int64_t)r0 * ldcs, ldcs);
     }
 }
 

@@ -9,6 +9,9 @@
 namespace otgs {
 
 struct Solver;
+struct Batch;
+void destroy_batch(Batch* b);
+void set_create_error(const std::string& msg);  // the message ot_gs_last_error(NULL) returns
 
 struct Handle {
     cudaStream_t st = nullptr;
@@ -22,18 +25,29 @@ struct Handle {
     int last_code = 0;
     bool st_synced_ok = false;
 
-    // problem
-    const float* C = nullptr;
-    int64_t ldc = 0;
-    bool own_C = false;
+    // problems: one, or a batch of independent ones concatenated (rows in
+    // problem order, class-sorted within a problem; columns in problem order)
+    int32_t nprob = 1;
+    std::vector<ProbDesc> probs_h;    // per problem: C (sorted rows), ldc, sizes, offsets
+    ProbDesc* probs = nullptr;        // device copy
+    std::vector<BProb> bprob_h;       // per problem: offsets and work-item range (plan-dependent)
+    BProb* bprob = nullptr;           // device copy
+    Batch* batch = nullptr;           // batched solver state (first ot_gs_batch_solve)
+    FxScale* pfx = nullptr;           // per problem: fixed-point scale of the last batch evaluation point
+    CUtensorMap* maps = nullptr;      // device: per problem, TMA descriptors (box[], then tile[])
+    PlanParams plan_params;           // the parameters of the current plan (0 = defaults)
+    int plan_gen = 0;                 // bumped by every (re)build of the plan
+    std::vector<int32_t> labels_h;    // all problems' labels (caller order), for re-planning
+    std::vector<int64_t> pm_h, pn_h;
+    std::vector<int32_t> pL_h;
+    std::vector<void*> plan_allocs;   // device buffers sized by the plan (replaced on re-planning)
     double* a_sorted = nullptr;
     double* b = nullptr;
     float cmax = 0.f;
 
     // one evaluation
     float4* rowA = nullptr;         // sorted rows: (alpha hi, lo, bound_up(hi), 0)
-    float2* B2 = nullptr;           // (beta hi, lo), padded columns
-    TmaMaps tmaps;                  // TMA descriptors of C
+    float2* B2 = nullptr;           // (beta hi, lo), per problem from probs_h[k].bcoff
     EvalCtl* ctl = nullptr;         // evaluation control word (work counter, scale maxima)
     int* kerr = nullptr;            // evaluation kernel error word
     int n_sm = 0;
@@ -78,8 +92,13 @@ struct Handle {
     void eval_launch(const EvalArgs& e, int n_ctas);
 
     ~Handle();
-    bool init(const float* C, int64_t ldc, const double* a, const double* b, const int32_t* labels, int64_t m,
-              int64_t n, int32_t L, double gamma, double mu, cudaStream_t st);
+    bool init(int32_t nprob, const float* const* C, const int64_t* ldc, const double* const* a,
+              const double* const* b, const int32_t* const* labels, const int64_t* m, const int64_t* n,
+              const int32_t* L, double gamma, double mu, cudaStream_t st);
+    // (re)builds the work decomposition with the given parameters and the buffers sized by it
+    bool setup_plan(const PlanParams& pp);
+    void* plan_alloc(size_t bytes, const char* what);
+    void free_plan();
     bool fail(int code, const std::string& msg);
     bool ck(cudaError_t e, const char* what);
     void* dalloc(size_t bytes, const char* what);
@@ -95,6 +114,9 @@ struct Handle {
     bool eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap);
     bool eval_screened_prepped(const double* beta, double* G_sorted, const double* dir,
                                double* out_caller = nullptr);
+    // every problem at (alpha, beta) in the caller's concatenated layout:
+    // D [nprob] and the gradient [m + n] (may be NULL), device
+    bool eval_batch(const double* alpha, const double* beta, double* D, double* grad);
     Solver* solver = nullptr;
     // While set (batched solver trials): evaluations are gated on this device
     // flag and are counted in the statistics by the solver afterwards.
@@ -114,5 +136,12 @@ struct Handle {
     bool collect_stats();
     void reset_device_stats();
 };
+
+// The calls that take one problem's vectors reject batch handles.
+inline bool single_problem(Handle* h)
+{
+    if (h->nprob == 1) return true;
+    return h->fail(OTGS_EINVAL, "a batch of problems: use the ot_gs_batch_* calls");
+}
 
 }  // namespace otgs

@@ -99,7 +99,32 @@ struct SplitSet {
     int item0;   // item id of piece 0 (holds the set's psi partials)
     int rstart;  // rows of the group
     int rend;
-    int pad;
+    int prob;    // problem of a batch
+};
+
+// Tunable plan parameters (0: the default rule).
+struct PlanParams {
+    int32_t panel_rows = 0;  // panel height (default: panel_rows(m, n))
+    int32_t split_rows = 0;  // groups taller than this are cut into pieces (default: SPLIT_ROWS)
+};
+
+// A problem of a batch as the kernels see it.
+struct ProbDesc {
+    const float* C;  // class-sorted rows of this problem, row stride ldc
+    int64_t ldc;
+    int32_t m, n;    // rows, columns
+    int32_t roff;    // first sorted row in the concatenation
+    int32_t coff;    // first column in the concatenation
+    int32_t bcoff;   // first entry in the beta pair array B2 (even: 16-byte aligned bulk copies)
+};
+
+// One problem of a batch as the per-problem kernels see it (the batched
+// preparation, reduction and L-BFGS step).
+struct BProb {
+    int32_t roff, coff, bcoff;  // first sorted row, first column, first B2 entry
+    int32_t m, n;
+    int32_t voff;               // first entry of the problem's solver vectors (roff + coff)
+    int32_t item0, item1;       // its work items [item0, item1)
 };
 
 // A work item as the evaluation kernel sees it, in execution order (64 B).
@@ -115,7 +140,8 @@ struct ItemDesc {
     int split;  // pieces of the item's group (1: not split)
     int sub;    // this item's piece
     int part;   // split groups: partial-sum slot of piece 0 of this block set (piece k: part + k)
-    int pad[5];
+    int prob;   // problem of a batch (0 for a single problem)
+    int pad[4];
 };
 
 // ------------------------------------------------------------------ host plan
@@ -124,13 +150,24 @@ struct ItemDesc {
 struct HostPlan {
     int64_t m = 0, n = 0;
     int32_t L = 0, ntiles = 0;
+    // a batch of independent problems: rows, columns and groups are the
+    // concatenation of the problems' (one problem: the trivial batch)
+    int32_t nprob = 1;
+    std::vector<int32_t> proff, pcoff, ploff;  // per problem: first row, column, group
+    std::vector<int32_t> pm, pn;               // per problem: rows, columns
+    std::vector<int32_t> pbcoff;               // per problem: first entry of B2 (columns rounded up to 4)
+    int64_t nb2 = 0;                           // entries of B2, with room for a full last column chunk
+    int64_t max_m = 0, max_n = 0;              // largest problem
+    std::vector<int32_t> gprob;                // group -> problem
+    int32_t panel_height = 0, split_height = 0;  // the parameters the plan was built with
     std::vector<int32_t> perm;    // sorted r -> caller row
     std::vector<int32_t> goff;    // L+1 offsets (sorted rows)
     std::vector<int32_t> rgroup;  // sorted r -> group
-    std::vector<int4> rowg;       // sorted r -> {group, first row, end row of the group, 0}
+    std::vector<int4> rowg;       // sorted r -> {group, first row, end row of the group, problem}
     // panels: row ranges of whole groups
     std::vector<int32_t> prow0;   // first sorted row
     std::vector<int32_t> prows;   // rows
+    std::vector<int32_t> pprob;   // problem
     std::vector<int32_t> pW;      // columns per work item (ITEM_COLS)
     std::vector<int32_t> pnch;    // work items (column chunks) of the panel
     std::vector<int32_t> pitem;   // first work-item id of the panel
@@ -153,6 +190,9 @@ struct HostPlan {
 
 // Returns an empty string on success, else an error message.
 std::string build_plan(const int32_t* labels, int64_t m, int64_t n, int32_t L, HostPlan& hp);
+// nprob problems (host label arrays of m[k] entries in [0, L[k]), n[k] columns).
+std::string build_plan_batch(int32_t nprob, const int32_t* const* labels, const int64_t* m, const int64_t* n,
+                             const int32_t* L, const PlanParams& pp, HostPlan& hp);
 
 // ---------------------------------------------------------------- device plan
 struct DevPlan {
@@ -177,8 +217,10 @@ struct EvalCtl {
 // whose pass B (row sums t_ij = s_j [f_ij]_+) is left to the pass-B kernel
 // because its rows have left the evaluation kernel's ring.
 struct PassB {
-    int gstart, gend, colg0, pad;  // rows [gstart, gend): a piece of at most PASSB_PIECE rows of the block
-    float s[TW];  // shrink factor of each column's block (0: none)
+    int gstart, gend;  // rows [gstart, gend): a piece of at most PASSB_PIECE rows of the block
+    int colg0;         // column (in the concatenation) of lane 0
+    int prob;          // problem of a batch
+    float s[TW];       // shrink factor of each column's block (0: none)
 };
 constexpr int PASSB_PIECE = 256;
 
@@ -202,14 +244,18 @@ __device__ __forceinline__ void record_max(EvalCtl* ctl, float apos, float bpos)
 struct FxScale {
     double to_r, from_r;  // row sums: value * to_r -> integer, integer * from_r -> value
     double to_c, from_c;  // column sums
+    float to_rf, to_cf;   // to_r, to_c as floats (exact: powers of two in FP32 range)
 };
 
+// k is kept in [-100, 100] so that 2^k is an FP32 number: a bound below
+// 2^-41 only gets a coarser grid than it could, and no finite FP32 input
+// gives a bound above 2^160.
 __host__ __device__ inline int fx_exponent(double bound)
 {
     if (!(bound > 0.0) || !(bound < 1e300)) return 0;
     const int e = ilogb(bound) + 2;  // bound < 2^(e-1): a factor 2 of slack for the FP32 split of alpha, beta
     const int k = 61 - e;
-    return k < -960 ? -960 : (k > 960 ? 960 : k);
+    return k < -100 ? -100 : (k > 100 ? 100 : k);
 }
 
 __host__ __device__ inline FxScale fx_scale(unsigned amax_bits, unsigned bmax_bits, int64_t m, int64_t n,
@@ -230,14 +276,17 @@ __host__ __device__ inline FxScale fx_scale(unsigned amax_bits, unsigned bmax_bi
     s.from_r = ldexp(1.0, -kr);
     s.to_c = ldexp(1.0, kc);
     s.from_c = ldexp(1.0, -kc);
+    s.to_rf = ldexpf(1.0f, kr);
+    s.to_cf = ldexpf(1.0f, kc);
     return s;
 }
 
 // -------------------------------------------------------------- kernel args
 struct EvalArgs {
-    const float* C;     // class-sorted rows, row stride ldc
-    int64_t ldc;
+    const ProbDesc* probs;      // [nprob]
+    const CUtensorMap* maps;    // [nprob][2 * TMA_BOXES] (box[], then tile[]); 64-byte aligned
     int32_t m, n, L, ntiles, nitems;
+    int32_t fx_m, fx_n;         // rows of the tallest problem, columns of the widest (fixed-point bounds)
     const float4* rowA;  // sorted rows: (alpha hi, alpha lo, bound_up(alpha hi), 0)
     const int4* rowg;    // sorted rows: (group, first row, end row of the group, 0)
     const float2* B2;    // columns padded to padded_cols(n): (hi, lo) split of beta
@@ -258,6 +307,9 @@ struct EvalArgs {
     const SplitSet* sets;  // block sets of split groups
     int32_t nsets;
     const int* gate;   // NULL, or a device flag: 0 = skip this evaluation (batched solver trials)
+    const int* prob_active;  // NULL, or per problem of a batch: 0 = its items are skipped
+    const FxScale* pfx;      // NULL, or per problem of a batch: its fixed-point scale (from its own
+                             // maxima and m, n); NULL: the scale of ctl's maxima with fx_m, fx_n
     float* zt;         // snapshot outputs (L x ntiles*TW) or NULL
     float* ot;
     // regularisation scalars
@@ -265,10 +317,12 @@ struct EvalArgs {
     float th2_cut;              // S_hi below this: block surely below threshold
     float gamma;
     double inv2g;               // 1 / (2 gamma)
+    float inv2g_hi, inv2g_lo;   // the same as a float pair
 };
 
 struct ReduceArgs {
     int32_t m, n, nitems;
+    int32_t fx_m, fx_n;
     const int32_t* perm;
     const uint8_t* item_active; // NULL = all items
     const unsigned long long* rowfx;
@@ -297,8 +351,8 @@ struct ReduceArgs {
 void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, const double* beta,
                  int32_t m, int32_t n, float4* rowA, float2* B2, double* alpha_s_out,
                  unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl, cudaStream_t st);
-// TMA descriptors of C: box[k] is 2^k rows x ITEM_COLS columns, tile[k] is
-// 2^k rows x TW columns (k = 0..TMA_BOXES-1).
+// TMA descriptors of one problem's C: box[k] is 2^k rows x ITEM_COLS columns,
+// tile[k] is 2^k rows x TW columns (k = 0..TMA_BOXES-1).
 constexpr int TMA_BOXES = 6;
 static_assert((1 << (TMA_BOXES - 1)) == STAGE_ROWS, "boxes must compose any stage height");
 struct TmaMaps {
@@ -308,7 +362,9 @@ struct TmaMaps {
 // Encodes the maps for C (m x n, row stride ldc floats); "" on success.
 std::string make_tmaps(const float* C, int64_t ldc, int64_t m, int64_t n, TmaMaps& T);
 // evaluation kernel (otgs_stream.cu): persistent, n_ctas CTAs; a.ctl zeroed by launch_prep
-void launch_stream(const EvalArgs& a, const TmaMaps& T, int n_ctas, cudaStream_t st);
+void launch_stream(const EvalArgs& a, int n_ctas, cudaStream_t st);
+// sets the evaluation kernel's shared-memory limit (once per device, before launches or capture)
+bool stream_prepare();
 // stage-mask kernel (otgs_stream.cu), screened evaluations: fills
 // a.stage_m8 from a.unit_need for the active items.  Launch before launch_stream.
 void launch_stage_masks(const EvalArgs& a, cudaStream_t st);
@@ -321,7 +377,8 @@ void launch_passb(const EvalArgs& a, int n_sm, cudaStream_t st);
 size_t stream_smem_bytes();
 void launch_reduce(const ReduceArgs& a, cudaStream_t st);
 int reduce_blocks(int32_t m, int32_t n);
-void launch_gather_rows(const float* C, int64_t ldc, const int32_t* perm, int32_t m, int32_t n,
+// Cs row r = C row perm[r] - base (columns [0, n), zero up to ldcs).
+void launch_gather_rows(const float* C, int64_t ldc, const int32_t* perm, int32_t base, int32_t m, int32_t n,
                         float* Cs, int64_t ldcs, cudaStream_t st);
 void launch_permute_f64(const double* src, const int32_t* perm, int32_t m, double* dst,
                         bool to_sorted, cudaStream_t st);

@@ -100,6 +100,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const size_t o_passb = cv.take(sizeof(PassB) * (size_t)passb_cap);
     const size_t o_spart = cv.take(sizeof(float) * 5 * ITEM_COLS * (size_t)hp.nsplit_slots);
     const size_t o_sets = cv.take(sizeof(SplitSet) * hp.sets.size());
+    const size_t o_maps = cv.take(sizeof(TmaMaps)), o_prob = cv.take(sizeof(ProbDesc));
     const int nred = reduce_blocks((int32_t)m, (int32_t)n);
     const size_t o_bpart = cv.take(8 * 4 * (size_t)nred), o_counter = cv.take(16), o_scal = cv.take(64);
     if (cv.off > OTGS_STATIC_SCRATCH_BYTES)
@@ -133,6 +134,16 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_counter, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_err, 0, 16, st);
     if (e == cudaSuccess) e = up(o_sets, hp.sets.data(), sizeof(SplitSet) * hp.sets.size());
+    TmaMaps tm;
+    {
+        const std::string te = make_tmaps(C, ldc, m, n, tm);
+        if (!te.empty()) return set_err(OTGS_ECUDA, te);
+    }
+    ProbDesc pd;
+    memset(&pd, 0, sizeof(pd));
+    pd.C = C; pd.ldc = ldc; pd.m = (int32_t)m; pd.n = (int32_t)n;
+    if (e == cudaSuccess) e = up(o_maps, &tm, sizeof(tm));
+    if (e == cudaSuccess) e = up(o_prob, &pd, sizeof(pd));
     int n_sm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return set_err(OTGS_ECUDA, std::string("scratch upload: ") + cudaGetErrorString(e));
@@ -147,8 +158,10 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     launch_prep(alpha, true, perm, beta, (int32_t)m, (int32_t)n, rowA, B2, aeval, rowfx, colfx, ctl, st);
     EvalArgs ea;
     memset(&ea, 0, sizeof(ea));
-    ea.C = C; ea.ldc = ldc;
+    ea.probs = (const ProbDesc*)(base + o_prob);
+    ea.maps = (const CUtensorMap*)(base + o_maps);
     ea.m = (int32_t)m; ea.n = (int32_t)n; ea.L = L; ea.ntiles = ntiles;
+    ea.fx_m = (int32_t)m; ea.fx_n = (int32_t)n;
     ea.nitems = hp.nitems();
     ea.rowA = rowA; ea.rowg = (const int4*)(base + o_rowg);
     ea.B2 = B2;
@@ -173,17 +186,16 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     ea.th2_cut = fc;
     ea.gamma = (float)gamma;
     ea.inv2g = 1.0 / (2.0 * gamma);
-    TmaMaps tm;
-    {
-        const std::string te = make_tmaps(C, ldc, m, n, tm);
-        if (!te.empty()) return set_err(OTGS_ECUDA, te);
-    }
-    launch_stream(ea, tm, std::min(CTAS_PER_SM * n_sm, hp.nitems()), st);
+    ea.inv2g_hi = (float)ea.inv2g;
+    ea.inv2g_lo = (float)(ea.inv2g - (double)ea.inv2g_hi);
+    if (!stream_prepare()) return set_err(OTGS_ECUDA, "cudaFuncSetAttribute(evaluation kernel)");
+    launch_stream(ea, std::min(CTAS_PER_SM * n_sm, hp.nitems()), st);
     launch_split_finish(ea, st);
     launch_passb(ea, n_sm, st);
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.m = (int32_t)m; ra.n = (int32_t)n; ra.nitems = hp.nitems();
+    ra.fx_m = (int32_t)m; ra.fx_n = (int32_t)n;
     ra.perm = perm; ra.item_active = nullptr;
     ra.rowfx = rowfx; ra.colfx = colfx; ra.psipart = ea.psipart;
     ra.ctl = ctl; ra.gamma = ea.gamma;

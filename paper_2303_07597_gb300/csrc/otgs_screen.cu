@@ -290,8 +290,8 @@ bool Handle::ensure_screen()
     Nmask = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * ntiles, "Nmask");
     skipmask = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * ntiles, "skipmask");
     unit_need = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * unit_words, "unit_need");
-    item_active = (uint8_t*)dalloc((size_t)hp.nitems(), "item_active");
-    stage_m8 = (uint8_t*)dalloc((size_t)hp.nstages * STAGE_ROWS, "stage masks");
+    item_active = (uint8_t*)plan_alloc((size_t)hp.nitems(), "item_active");
+    stage_m8 = (uint8_t*)plan_alloc((size_t)hp.nstages * STAGE_ROWS, "stage masks");
     if (!stage_m8) return false;
     gstat = (float*)dalloc(sizeof(float) * 4 * (size_t)L, "gstat");
     cstat = (float*)dalloc(sizeof(float) * 4 * ldz, "cstat");
@@ -426,6 +426,7 @@ int ot_gs_grad_screened(ot_gs* hh, const double* alpha, const double* beta, doub
 {
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
     if (!alpha || !beta || !out) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
     if (!h->eval_screened(alpha, false, beta, out, nullptr, nullptr)) return h->last_code;
     if (skip_mask &&
@@ -439,6 +440,7 @@ int ot_gs_snapshot(ot_gs* hh, const double* alpha, const double* beta, int build
 {
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
     if (!alpha || !beta) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
     if (!h->snapshot_at(alpha, false, beta, build_N != 0, out, nullptr, nullptr)) return h->last_code;
     return OTGS_OK;
@@ -448,6 +450,7 @@ int ot_gs_get_screen_state(ot_gs* hh, float* zt, float* ot, double* alpha_s, dou
 {
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
     if (!h->ensure_screen()) return h->last_code;
     if (!h->snap_valid) { h->fail(OTGS_EINVAL, "no snapshot yet"); return OTGS_EINVAL; }
     const size_t lz = (size_t)h->L * h->ntiles * TW;

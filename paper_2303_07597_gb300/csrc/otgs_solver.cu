@@ -50,20 +50,6 @@ __global__ void k_trial(SolverState* S, const double* __restrict__ x, const doub
     record_max(ctl, apos, bpos);
 }
 
-__device__ double bracket_step(double lo, double Flo, double dlo, double hi, double Fhi, double dhi)
-{
-    const double w = hi - lo;
-    double t = lo + 0.5 * w;
-    if (dlo < 0.0 && dhi > 0.0) {
-        t = lo - dlo * w / (dhi - dlo);
-    } else {
-        const double den = 2.0 * (Fhi - Flo - dlo * w);
-        if (den > 0.0) t = lo - dlo * w * w / den;
-    }
-    if (!(t >= lo + 0.1 * w && t <= hi - 0.1 * w)) t = lo + 0.5 * w;
-    return t;
-}
-
 __device__ __forceinline__ unsigned long long gtimer()
 {
     unsigned long long t;
@@ -90,35 +76,17 @@ __global__ void k_linesearch(SolverState* S, const double* scal)
     S->accepted = 0;
     S->refresh = 0;
     const double F = -scal[0], dphi = scal[1];
-    const double F0 = S->F0, d0 = S->dphi0, t = S->t;
-    const bool suff = (F <= F0 + LS_C1 * t * d0) || (F - F0 <= LS_EPS_F * fabs(F0) && dphi <= (2.0 * LS_C1 - 1.0) * d0);
-    S->ls_evals++;
-    bool accept = S->force_accept || (suff && fabs(dphi) <= -LS_C2 * d0);
-    if (!accept) {
-        if (!suff || dphi >= 0.0) {
-            S->hi = t; S->Fhi = F; S->dhi = dphi; S->have_hi = 1;
-        } else {
-            S->lo = t; S->Flo = F; S->dlo = dphi;
-        }
-        if (S->ls_evals >= LS_MAX_EVALS || (S->have_hi && S->hi - S->lo <= 1e-15 * S->hi)) {
-            if (S->lo > 0.0) {  // evaluate once more at the last sufficient-decrease step and take it
-                S->t = S->lo;
-                S->force_accept = 1;
-            } else {
-                S->status = OTGS_ELINESEARCH;
-                S->done = 1;
-            }
-        } else {
-            S->t = S->have_hi ? bracket_step(S->lo, S->Flo, S->dlo, S->hi, S->Fhi, S->dhi) : 2.0 * t;
-        }
-    } else {
+    const int r = ls_update(S, F, dphi);
+    if (r < 0) {
+        S->status = OTGS_ELINESEARCH;
+        S->done = 1;
+    } else if (r > 0) {
         S->accepted = 1;
-        S->force_accept = 0;
         S->F = F;
         S->ginf = scal[2];
         S->iter++;
         trace_put(S, F);
-        if (S->ginf <= S->tol) {
+        if (S->ginf <= S->tol || stalled(S->F0, F, S->ftol)) {
             S->status = OTGS_OK;
             S->done = 1;
         } else if (S->iter >= S->maxit) {
@@ -241,81 +209,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_direction(SolverState* S, co
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    if (!start) {
-        // curvature pair: keep it only with enough positive curvature
-        const int head = S->head;
-        const double sy = base[DOT_SY];
-        if (sy > 1e-12 * sqrt(base[DOT_SS] * base[DOT_YY])) {
-            for (int k = 0; k < M; k++) {
-                SY[head * M + k] = pd[k][PD_SNEW_Y];  // s_head . y_k
-                SY[k * M + head] = pd[k][PD_S_YNEW];  // s_k . y_head
-                YY[head * M + k] = pd[k][PD_YNEW_Y];
-                YY[k * M + head] = pd[k][PD_YNEW_Y];
-            }
-            SY[head * M + head] = sy;
-            YY[head * M + head] = base[DOT_YY];
-            for (int k = 0; k < M; k++) {
-                S->SY[head * M + k] = SY[head * M + k];
-                S->SY[k * M + head] = SY[k * M + head];
-                S->YY[head * M + k] = YY[head * M + k];
-                S->YY[k * M + head] = YY[k * M + head];
-            }
-            S->head = (head + 1) % M;
-            if (S->npairs < M) S->npairs++;
-        } else if (S->npairs == M) {
-            S->npairs = M - 1;  // the rejected pair overwrote the oldest slot
-        }
-    }
-    const int np = S->npairs, hd = S->head;
-    double a[MAX_LBFGS_M], b[MAX_LBFGS_M];
-    int idx[MAX_LBFGS_M];
-    for (int k = 0; k < np; k++) idx[k] = ((hd - np + k) % M + M) % M;  // oldest .. newest
-    // first loop, newest to oldest: a_i = rho_i s_i.q,  q = G - sum_{newer} a_k y_k
-    for (int u = np - 1; u >= 0; u--) {
-        const int i = idx[u];
-        double sq = pd[i][PD_G_S];
-        for (int v = u + 1; v < np; v++) sq -= a[v] * SY[i * M + idx[v]];
-        a[u] = sq / SY[i * M + i];
-    }
-    double h0 = 1.0;
-    if (np > 0) {
-        const int nw = idx[np - 1];
-        h0 = SY[nw * M + nw] / YY[nw * M + nw];
-    }
-    // second loop, oldest to newest: b_i = rho_i y_i.r, r = h0 q + sum_{older}(a_k - b_k) s_k
-    for (int u = 0; u < np; u++) {
-        const int i = idx[u];
-        double yq = pd[i][PD_G_Y];
-        for (int v = 0; v < np; v++) yq -= a[v] * YY[i * M + idx[v]];
-        double yr = h0 * yq;
-        for (int v = 0; v < u; v++) yr += (a[v] - b[v]) * SY[idx[v] * M + i];
-        b[u] = yr / SY[i * M + i];
-    }
-    // d = -(h0 q + sum (a - b) s) = -h0 G + h0 sum a y - sum (a - b) s
-    double cG = -h0;
-    double dphi0 = cG * base[DOT_GG];
-    for (int k = 0; k < MAX_LBFGS_M; k++) { S->cy[k] = 0.0; S->cs[k] = 0.0; }
-    for (int u = 0; u < np; u++) {
-        const int i = idx[u];
-        S->cy[i] = h0 * a[u];
-        S->cs[i] = -(a[u] - b[u]);
-        dphi0 += S->cy[i] * pd[i][PD_G_Y] + S->cs[i] * pd[i][PD_G_S];
-    }
-    if (!(dphi0 < 0.0)) {  // not a descent direction: restart from -G
-        for (int k = 0; k < MAX_LBFGS_M; k++) { S->cy[k] = 0.0; S->cs[k] = 0.0; }
-        S->npairs = 0;
-        cG = -1.0;
-        dphi0 = -base[DOT_GG];
-    }
-    S->cG = cG;
-    S->dphi0 = dphi0;
-    S->F0 = S->F;
-    const double ginf = S->ginf;
-    S->t = (S->iter == 0 && S->npairs == 0 && ginf > 0.0) ? 1.0 / ginf : 1.0;
-    S->lo = 0.0; S->Flo = S->F; S->dlo = dphi0;
-    S->hi = 0.0; S->Fhi = 0.0; S->dhi = 0.0; S->have_hi = 0;
-    S->ls_evals = 0;
-    S->force_accept = 0;
+    lbfgs_direction(S, SY, YY, base, pd, M, start != 0);
 }
 
 // d = cG G + sum_k cy_k y_k + sum_k cs_k s_k
@@ -419,6 +313,7 @@ int Solver::run(double tol, int maxit)
     init.r = h->prm.r;
     init.screening = h->prm.use_screening;
     init.budget_ns = h->prm.time_budget_ms > 0 ? h->prm.time_budget_ms * 1e6 : 0.0;
+    init.ftol = h->prm.ftol;
     init.npairs = 0;
     init.head = 0;
     init.status = OTGS_ENOTCONV;
@@ -520,6 +415,7 @@ int ot_gs_solve(ot_gs* hh, double tol, int32_t maxit)
 {
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
     if (!(tol >= 0.0) || maxit < 0) { h->fail(OTGS_EINVAL, "need tol >= 0 and maxit >= 0"); return OTGS_EINVAL; }
     if (!h->solver) {
         h->solver = new (std::nothrow) Solver();
@@ -540,6 +436,7 @@ int ot_gs_get_solution(ot_gs* hh, double* alpha, double* beta, double* D, double
 {
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
     if (!h->solver) { h->fail(OTGS_EINVAL, "no solve yet"); return OTGS_EINVAL; }
     Solver* s = h->solver;
     if (alpha) launch_permute_f64(s->x, h->dp.perm, (int32_t)h->m, alpha, false, h->st);
@@ -580,6 +477,7 @@ int ot_gs_set_state(ot_gs* hh, const double* alpha, const double* beta)
 {
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
     if (!alpha || !beta) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
     if (!h->solver) {
         h->solver = new (std::nothrow) Solver();

@@ -25,7 +25,7 @@ struct SolverState {
     int go;  // the current trial runs (set by the trial gate: not done, no refresh pending)
     long long evals;
     double tol, t, lo, Flo, dlo, hi, Fhi, dhi;
-    double F, F0, dphi0, ginf, cG, budget_ns;
+    double F, F0, dphi0, ginf, cG, budget_ns, ftol;
     unsigned long long t_start;
     unsigned long long t_begin;  // globaltimer when the solve was launched
     double* trace;               // [trace_cap][3]: D, ms since t_begin, evaluations
@@ -35,6 +35,147 @@ struct SolverState {
     double YY[MAX_LBFGS_M * MAX_LBFGS_M];
     double cy[MAX_LBFGS_M], cs[MAX_LBFGS_M];
 };
+
+// ------------------------------------------------ device steps of L-BFGS
+// Shared by the single-problem solver (SolverState) and the batched one (one
+// state per problem): any St with the fields used below.
+
+__device__ __forceinline__ double bracket_step(double lo, double Flo, double dlo, double hi, double Fhi, double dhi)
+{
+    const double w = hi - lo;
+    double t = lo + 0.5 * w;
+    if (dlo < 0.0 && dhi > 0.0) {
+        t = lo - dlo * w / (dhi - dlo);
+    } else {
+        const double den = 2.0 * (Fhi - Flo - dlo * w);
+        if (den > 0.0) t = lo - dlo * w * w / den;
+    }
+    if (!(t >= lo + 0.1 * w && t <= hi - 0.1 * w)) t = lo + 0.5 * w;
+    return t;
+}
+
+// Objective stagnation: the accepted step lowered F = -D by at most
+// ftol max(|F0|, |F|) (ftol = 0: never).
+__device__ __forceinline__ bool stalled(double F0, double F, double ftol)
+{
+    return ftol > 0.0 && F0 - F <= ftol * fmax(fabs(F0), fabs(F));
+}
+
+// One trial of the strong-Wolfe line search on F = -D at step t with slope
+// dphi = G(x + t d).d: 1 = accept, 0 = S->t holds the next trial, -1 = no
+// acceptable step.
+template <class St>
+__device__ __forceinline__ int ls_update(St* S, double F, double dphi)
+{
+    const double F0 = S->F0, d0 = S->dphi0, t = S->t;
+    const bool suff = (F <= F0 + LS_C1 * t * d0) || (F - F0 <= LS_EPS_F * fabs(F0) && dphi <= (2.0 * LS_C1 - 1.0) * d0);
+    S->ls_evals++;
+    if (S->force_accept || (suff && fabs(dphi) <= -LS_C2 * d0)) {
+        S->force_accept = 0;
+        return 1;
+    }
+    if (!suff || dphi >= 0.0) {
+        S->hi = t; S->Fhi = F; S->dhi = dphi; S->have_hi = 1;
+    } else {
+        S->lo = t; S->Flo = F; S->dlo = dphi;
+    }
+    if (S->ls_evals >= LS_MAX_EVALS || (S->have_hi && S->hi - S->lo <= 1e-15 * S->hi)) {
+        if (S->lo > 0.0) {  // evaluate once more at the last sufficient-decrease step and take it
+            S->t = S->lo;
+            S->force_accept = 1;
+            return 0;
+        }
+        return -1;
+    }
+    S->t = S->have_hi ? bracket_step(S->lo, S->Flo, S->dlo, S->hi, S->Fhi, S->dhi) : 2.0 * t;
+    return 0;
+}
+
+// One thread: keeps the new pair (slot S->head) when its curvature is
+// positive enough (unless start), then the two-loop recursion (Nocedal &
+// Wright, Alg. 7.4) on scalars, the descent check and the start of the next
+// line search.  SY, YY: the M x M curvature matrices (shared memory copies of
+// S->SY, S->YY, whose changed rows and columns are written back); base: s.y,
+// s.s, y.y, G.G; pd[k]: the NPAIR dots of slot k.
+template <class St>
+__device__ void lbfgs_direction(St* S, double* SY, double* YY, const double* base, const double (*pd)[NPAIR], int M,
+                                bool start)
+{
+    if (!start) {
+        const int head = S->head;
+        const double sy = base[DOT_SY];
+        if (sy > 1e-12 * sqrt(base[DOT_SS] * base[DOT_YY])) {
+            for (int k = 0; k < M; k++) {
+                SY[head * M + k] = pd[k][PD_SNEW_Y];  // s_head . y_k
+                SY[k * M + head] = pd[k][PD_S_YNEW];  // s_k . y_head
+                YY[head * M + k] = pd[k][PD_YNEW_Y];
+                YY[k * M + head] = pd[k][PD_YNEW_Y];
+            }
+            SY[head * M + head] = sy;
+            YY[head * M + head] = base[DOT_YY];
+            for (int k = 0; k < M; k++) {
+                S->SY[head * M + k] = SY[head * M + k];
+                S->SY[k * M + head] = SY[k * M + head];
+                S->YY[head * M + k] = YY[head * M + k];
+                S->YY[k * M + head] = YY[k * M + head];
+            }
+            S->head = (head + 1) % M;
+            if (S->npairs < M) S->npairs++;
+        } else if (S->npairs == M) {
+            S->npairs = M - 1;  // the rejected pair overwrote the oldest slot
+        }
+    }
+    const int np = S->npairs, hd = S->head;
+    double a[MAX_LBFGS_M], b[MAX_LBFGS_M];
+    int idx[MAX_LBFGS_M];
+    for (int k = 0; k < np; k++) idx[k] = ((hd - np + k) % M + M) % M;  // oldest .. newest
+    // first loop, newest to oldest: a_i = rho_i s_i.q,  q = G - sum_{newer} a_k y_k
+    for (int u = np - 1; u >= 0; u--) {
+        const int i = idx[u];
+        double sq = pd[i][PD_G_S];
+        for (int v = u + 1; v < np; v++) sq -= a[v] * SY[i * M + idx[v]];
+        a[u] = sq / SY[i * M + i];
+    }
+    double h0 = 1.0;
+    if (np > 0) {
+        const int nw = idx[np - 1];
+        h0 = SY[nw * M + nw] / YY[nw * M + nw];
+    }
+    // second loop, oldest to newest: b_i = rho_i y_i.r, r = h0 q + sum_{older}(a_k - b_k) s_k
+    for (int u = 0; u < np; u++) {
+        const int i = idx[u];
+        double yq = pd[i][PD_G_Y];
+        for (int v = 0; v < np; v++) yq -= a[v] * YY[i * M + idx[v]];
+        double yr = h0 * yq;
+        for (int v = 0; v < u; v++) yr += (a[v] - b[v]) * SY[idx[v] * M + i];
+        b[u] = yr / SY[i * M + i];
+    }
+    // d = -(h0 q + sum (a - b) s) = -h0 G + h0 sum a y - sum (a - b) s
+    double cG = -h0;
+    double dphi0 = cG * base[DOT_GG];
+    for (int k = 0; k < MAX_LBFGS_M; k++) { S->cy[k] = 0.0; S->cs[k] = 0.0; }
+    for (int u = 0; u < np; u++) {
+        const int i = idx[u];
+        S->cy[i] = h0 * a[u];
+        S->cs[i] = -(a[u] - b[u]);
+        dphi0 += S->cy[i] * pd[i][PD_G_Y] + S->cs[i] * pd[i][PD_G_S];
+    }
+    if (!(dphi0 < 0.0)) {  // not a descent direction: restart from -G
+        for (int k = 0; k < MAX_LBFGS_M; k++) { S->cy[k] = 0.0; S->cs[k] = 0.0; }
+        S->npairs = 0;
+        cG = -1.0;
+        dphi0 = -base[DOT_GG];
+    }
+    S->cG = cG;
+    S->dphi0 = dphi0;
+    S->F0 = S->F;
+    const double ginf = S->ginf;
+    S->t = (S->iter == 0 && S->npairs == 0 && ginf > 0.0) ? 1.0 / ginf : 1.0;
+    S->lo = 0.0; S->Flo = S->F; S->dlo = dphi0;
+    S->hi = 0.0; S->Fhi = 0.0; S->dhi = 0.0; S->have_hi = 0;
+    S->ls_evals = 0;
+    S->force_accept = 0;
+}
 
 struct Solver {
     Handle* h = nullptr;

@@ -144,30 +144,38 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t b
 }
 
 // One TMA box: rows [y, y + 2^k) x columns [x, x + IC) of C into dst.
-__device__ __forceinline__ void tma_box(const TmaMaps& T, int k, float* dst, int x, int y, uint64_t* bar)
+__device__ __forceinline__ void tma_box(const CUtensorMap* M, int k, float* dst, int x, int y, uint64_t* bar)
 {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
             "r"(su32(dst)),
-        "l"(reinterpret_cast<uint64_t>(&T.box[k])), "r"(x), "r"(y), "r"(su32(bar))
+        "l"(reinterpret_cast<uint64_t>(M + k)), "r"(x), "r"(y), "r"(su32(bar))
         : "memory");
+}
+
+// Orders this thread's later tensor copies after the descriptor's contents
+// (written to global memory before the launch).
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap* M)
+{
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(reinterpret_cast<uint64_t>(M))
+                 : "memory");
 }
 
 // Rows [y, y + rows) (rows <= STAGE_ROWS) into dst rows [0, rows): one box per
 // set bit of rows, so exactly the requested rows are read.
-__device__ __forceinline__ void tma_rows(const TmaMaps& T, float* dst, int x, int y, int rows, uint64_t* bar)
+__device__ __forceinline__ void tma_rows(const CUtensorMap* M, float* dst, int x, int y, int rows, uint64_t* bar)
 {
     int off = 0;
 #pragma unroll
     for (int k = TMA_BOXES - 1; k >= 0; k--)
         if (rows & (1 << k)) {
-            tma_box(T, k, dst + off * IC, x, y + off, bar);
+            tma_box(M, k, dst + off * IC, x, y + off, bar);
             off += 1 << k;
         }
 }
 
 // The same for one 32-column tile: rows of TW floats at dst + r * TW.
-__device__ __forceinline__ void tma_tile_rows(const TmaMaps& T, float* dst, int x, int y, int rows, uint64_t* bar)
+__device__ __forceinline__ void tma_tile_rows(const CUtensorMap* M, float* dst, int x, int y, int rows, uint64_t* bar)
 {
     int off = 0;
 #pragma unroll
@@ -176,7 +184,7 @@ __device__ __forceinline__ void tma_tile_rows(const TmaMaps& T, float* dst, int 
             asm volatile(
                 "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
                 "[%4];" ::"r"(su32(dst + off * TW)),
-                "l"(reinterpret_cast<uint64_t>(&T.tile[k])), "r"(x), "r"(y + off), "r"(su32(bar))
+                "l"(reinterpret_cast<uint64_t>(M + TMA_BOXES + k)), "r"(x), "r"(y + off), "r"(su32(bar))
                 : "memory");
             off += 1 << k;
         }
@@ -225,11 +233,22 @@ __device__ __forceinline__ void acc_p(float fh, float fl, Acc& a)
     df_add(a.Ph, a.Pl, fh, fl);
 }
 
-// Eq. 5 for one block from S = ||[f_[l]]_+||^2: the shrink factor
-// s = [z - theta]_+ / (gamma z); psi = [z - theta]_+^2 / (2 gamma).
-__device__ __forceinline__ float block_scale(float Sh, float Sl, const EvalArgs& A, double& psi)
+// (h, l) = (ah + al) * (bh + bl) to ~2^-46 relative.
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float& h, float& l)
 {
-    psi = 0.0;
+    h = __fmul_rn(ah, bh);
+    l = fmaf(ah, bh, -h);
+    l = fmaf(ah, bl, fmaf(al, bh, l));
+}
+
+// Eq. 5 for one block from S = ||[f_[l]]_+||^2: the shrink factor
+// s = [z - theta]_+ / (gamma z) and psi = [z - theta]_+^2 / (2 gamma) as a
+// float pair (psh, psl).  FP32 only: GB300's FP64 rate is a small fraction
+// of its FP32 rate, and this runs once per block.
+__device__ __forceinline__ float block_scale(float Sh, float Sl, const EvalArgs& A, float& psh, float& psl)
+{
+    psh = 0.f;
+    psl = 0.f;
     if (!(Sh > 0.f) || Sh < A.th2_cut) return 0.f;
     float sh = __fadd_rn(Sh, Sl);
     float sl = __fsub_rn(Sl, __fsub_rn(sh, Sh));
@@ -241,8 +260,9 @@ __device__ __forceinline__ float block_scale(float Sh, float Sl, const EvalArgs&
     float dl = __fadd_rn(de, __fsub_rn(zl, A.theta_lo));
     float ds = __fadd_rn(dh, dl);
     if (!(ds > 0.f)) return 0.f;
-    double d = (double)dh + (double)dl;
-    psi = d * d * A.inv2g;
+    float qh, ql;
+    df_mul(dh, dl, dh, dl, qh, ql);
+    df_mul(qh, ql, A.inv2g_hi, A.inv2g_lo, psh, psl);
     return __fdiv_rn(ds, __fmul_rn(A.gamma, __fadd_rn(zh, zl)));
 }
 
@@ -344,15 +364,49 @@ __device__ __forceinline__ uint32_t chunks_of_rows(uint32_t rows)
     return c;
 }
 
-__device__ __forceinline__ void red_fx(unsigned long long* p, double v, double to_fx)
+// The fixed-point scale of a problem's sums: from its own maxima in a batch
+// (so that one problem's large trial point costs the others no precision),
+// else from the evaluation's.
+__device__ __forceinline__ FxScale prob_fx(const EvalArgs& A, int prob)
 {
-    atomicAdd(p, (unsigned long long)__double2ll_rn(v * to_fx));
+    if (A.pfx) return A.pfx[prob];
+    return fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
 }
 
-// Snapshot values of block (l, col) (written only for col < n).
-__device__ __forceinline__ void put_snap(const EvalArgs& A, int l, int col, float zt, float ot)
+// t_ij = s f_ij (FP32) on the fixed-point grid: t * 2^k is exact in FP32
+// (below 2^61 by the choice of k), so this is the integer nearest to t 2^k.
+__device__ __forceinline__ unsigned long long t_q(float t, float to_fx)
 {
-    if (col < A.n) {
+    return (unsigned long long)__float2ll_rn(__fmul_rn(t, to_fx));
+}
+
+// Warp-wide: the lanes' terms q of one row (one column per lane) added into
+// the row's fixed-point sum with one atomic.  The row's total is below 2^61
+// (the grid's bound), so the three 32-bit partial sums cannot overflow:
+// bits 32.. sum below 2^29, the two 16-bit fields below 2^21.
+__device__ __forceinline__ void red_row(unsigned long long* p, unsigned long long q)
+{
+    if (!__any_sync(FULLMASK, q != 0ull)) return;
+    const unsigned hi = __reduce_add_sync(FULLMASK, (unsigned)(q >> 32));
+    const unsigned m1 = __reduce_add_sync(FULLMASK, (unsigned)(q >> 16) & 0xffffu);
+    const unsigned m0 = __reduce_add_sync(FULLMASK, (unsigned)q & 0xffffu);
+    if ((threadIdx.x & 31) == 0)
+        atomicAdd(p, ((unsigned long long)hi << 32) + ((unsigned long long)m1 << 16) + (unsigned long long)m0);
+}
+
+// A block's column-sum term s P (P = Ph + Pl) in fixed point: s P as a float
+// pair, each part rounded to the grid (an error below one grid step).
+__device__ __forceinline__ long long col_q(float s, float Ph, float Pl, float to_fx)
+{
+    const float ph = __fmul_rn(s, Ph);
+    const float pl = fmaf(s, Pl, fmaf(s, Ph, -ph));
+    return __float2ll_rn(__fmul_rn(ph, to_fx)) + __float2ll_rn(__fmul_rn(pl, to_fx));
+}
+
+// Snapshot values of block (l, col) (written only for a real column).
+__device__ __forceinline__ void put_snap(const EvalArgs& A, int l, int col, bool real, float zt, float ot)
+{
+    if (real) {
         const int64_t q = (int64_t)l * A.ntiles * TW + col;
         A.zt[q] = zt;
         A.ot[q] = ot;
@@ -377,12 +431,18 @@ struct Ctx {
     const float4* rA;  // stage's alpha records
     int ra, nr;        // first sorted row of the stage, rows in it
     float bh, bl, bp;  // beta hi, lo, B' of this lane's column
-    int colg;          // this lane's column of C
+    int colg;          // this lane's column in the concatenation of the problems' columns
+    bool real;         // the lane's column exists (the item's last chunk may be narrower)
+    const float* Cp;   // the item's problem: its C, row stride, first row
+    int64_t ldc;
+    int roff;
+    int lcol;          // this lane's column within its problem
     uint32_t U;        // chunks of the stage marked by some lane (dense path)
     int r0;            // first sorted row of the item
     int rend;          // end row of the item
     const uint8_t* marks;  // this warp's marked chunks of the item's stages
     int item, split, sub, part;  // the item; its group's pieces, its piece, the set's piece-0 slot
+    int prob;          // the item's problem
 };
 
 __device__ __forceinline__ void open_block(Block& b, const int4& g, bool need, const Ctx& x)
@@ -404,7 +464,8 @@ __device__ __forceinline__ void open_block(Block& b, const int4& g, bool need, c
 // PASSB_PIECE rows (so that one long block does not set that kernel's
 // duration); false when the list is full (the slots taken that fit are left
 // empty and the caller does pass B itself).
-__device__ __forceinline__ bool defer_passb(const EvalArgs& A, int gstart, int gend, int colg0, float s, int lane)
+__device__ __forceinline__ bool defer_passb(const EvalArgs& A, int gstart, int gend, int colg0, int prob, float s,
+                                            int lane)
 {
     const int npieces = (gend - gstart + PASSB_PIECE - 1) / PASSB_PIECE;
     int idx = 0;
@@ -418,6 +479,7 @@ __device__ __forceinline__ bool defer_passb(const EvalArgs& A, int gstart, int g
             e.gstart = fits ? gstart + k * PASSB_PIECE : 0;
             e.gend = fits ? min(gstart + (k + 1) * PASSB_PIECE, gend) : 0;
             e.colg0 = colg0;
+            e.prob = prob;
         }
     }
     return fits;
@@ -428,7 +490,7 @@ __device__ __forceinline__ bool defer_passb(const EvalArgs& A, int gstart, int g
 // pieces in order and finishes the block.
 template <bool SNAP>
 __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, const FxScale& fx,
-                                             int lane, bool marks, double& psi_acc, double& cacc)
+                                             int lane, bool marks, float (&psi_acc)[2], long long& cacc)
 {
     if (b.split) {
         float* q = A.split_part + ((int64_t)(x.part + x.sub) * ITEM_COLS + (threadIdx.x >> 5) * TW + lane) * 5;
@@ -442,13 +504,15 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
     float s = 0.f;
     if (__any_sync(FULLMASK, b.any)) {
         double psi;
-        s = block_scale(b.acc.Sh, b.acc.Sl, A, psi);
-        psi_acc += psi;
-        if (s > 0.f) cacc += (double)s * ((double)b.acc.Ph + (double)b.acc.Pl);
+        float psh, psl;
+        s = block_scale(b.acc.Sh, b.acc.Sl, A, psh, psl);
+        df_add(psi_acc[0], psi_acc[1], psh, psl);
+        if (s > 0.f) cacc += col_q(s, b.acc.Ph, b.acc.Pl, fx.to_cf);
     }
-    if (SNAP) put_snap(A, b.gl, x.colg, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
+    if (SNAP) put_snap(A, b.gl, x.colg, x.real, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
     if (!__any_sync(FULLMASK, s > 0.f)) return;
-    if (b.gstart < x.ra - PASSB_INLINE_ROWS && defer_passb(A, b.gstart, b.gend, x.colg - lane, s, lane)) return;
+    if (b.gstart < x.ra - PASSB_INLINE_ROWS && defer_passb(A, b.gstart, b.gend, x.colg - lane, x.prob, s, lane))
+        return;
     // pass B: t_ij = s [f_ij]_+ into the row sums, over the block's rows that
     // can hold an f > 0 (marked chunks; every row on the snapshot walk),
     // four rows at a time
@@ -472,16 +536,20 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
                     c[k] = x.st[(R - base) * x.rs];
                     a[k] = x.rA[R - base];
                 } else {  // the row's stage has left the ring: re-read it (from L2)
-                    c[k] = x.colg < A.n ? __ldg(A.C + (int64_t)R * A.ldc + x.colg) : 0.f;
+                    c[k] = x.real ? __ldg(x.Cp + (int64_t)(R - x.roff) * x.ldc + x.lcol) : 0.f;
                     a[k] = __ldg(A.rowA + R);
                 }
             }
 #pragma unroll
             for (int k = 0; k < 4; k++) {
-                if (R0 + k >= R1 || !(s > 0.f) || !maybe_pos(a[k].z, c[k], x.bp)) continue;
-                float fh, fl;
-                f_exact(a[k].x, a[k].y, x.bh, x.bl, c[k], fh, fl);
-                if (fh > 0.f) red_fx(A.rowfx + R0 + k, (double)__fmul_rn(s, fh), fx.to_r);
+                if (R0 + k >= R1) break;  // (uniform)
+                unsigned long long q = 0ull;
+                if (s > 0.f && maybe_pos(a[k].z, c[k], x.bp)) {
+                    float fh, fl;
+                    f_exact(a[k].x, a[k].y, x.bh, x.bl, c[k], fh, fl);
+                    if (fh > 0.f) q = t_q(__fmul_rn(s, fh), fx.to_rf);
+                }
+                red_row(A.rowfx + R0 + k, q);
             }
         }
     }
@@ -503,7 +571,7 @@ __device__ __forceinline__ void block_marked_rows(Block& b, const Ctx& x, int s,
 
 // ================================================================= kernel
 template <bool SNAP>
-__global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs A, const __grid_constant__ TmaMaps T)
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;  // a skipped solver trial
     extern __shared__ unsigned char smem_raw[];
@@ -539,11 +607,14 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             return (idx < A.nlist && lane < DESC_WORDS) ? __ldg(reinterpret_cast<const int*>(A.desc + idx) + lane) : 0;
         };
         auto load_act = [&](int idx, int w) -> int {
-            const int item = __shfl_sync(FULLMASK, w, 0);
+            const int item = __shfl_sync(FULLMASK, w, 0), prob = __shfl_sync(FULLMASK, w, 11);
             if (idx >= A.nlist) return 0;
-            if (!A.item_active) return 1;
-            return lane == 0 ? (int)__ldg(A.item_active + item) : 0;
+            int act = 1;  // lane 0's value is the one used
+            if (A.item_active && lane == 0) act = (int)__ldg(A.item_active + item);
+            if (A.prob_active && lane == 0 && !__ldg(A.prob_active + prob)) act = 0;
+            return act;
         };
+        int fenced = -1;  // the problem whose tensor maps were last acquired
         int i0 = bcast(fetch());
         int w0 = load_w(i0);
         int a0 = load_act(i0, w0);
@@ -569,6 +640,16 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int r0 = __shfl_sync(FULLMASK, w0, 2), rows = __shfl_sync(FULLMASK, w0, 3);
                 const int col0 = __shfl_sync(FULLMASK, w0, 4), nst = __shfl_sync(FULLMASK, w0, 6);
                 const int sbase = __shfl_sync(FULLMASK, w0, 7);
+                const int prob = __shfl_sync(FULLMASK, w0, 11);
+                const ProbDesc pd = A.probs[prob];
+                const CUtensorMap* maps = A.maps + (int64_t)prob * 2 * TMA_BOXES;
+                if (prob != fenced) {  // the descriptors live in global memory: acquire them for the tensor proxy
+                    if (lane == 0)
+                        for (int k = 0; k < TMA_BOXES; k++) tmap_acquire(maps + k);
+                    if (lane < CONSUMERS)
+                        for (int k = 0; k < TMA_BOXES; k++) tmap_acquire(maps + TMA_BOXES + k);
+                    fenced = prob;
+                }
                 // screened: this lane's row's needed tiles, one stage ahead
                 uint32_t m8n = screened ? (uint32_t)__ldg(A.stage_m8 + (int64_t)sbase * SR + lane) : 0xffu;
                 bool first = true;  // no stage of this item issued yet
@@ -605,7 +686,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                         mbar_expect(&S.full[slot], cdata + 2u * abytes + cbytes);
                         bulk_copy(S.rowA[slot], A.rowA + ra, abytes, &S.full[slot]);
                         bulk_copy(S.rowG[slot], A.rowg + ra, abytes, &S.full[slot]);
-                        if (first) bulk_copy(S.colB[slot], A.B2 + col0, IC * 8u, &S.full[slot]);
+                        if (first) bulk_copy(S.colB[slot], A.B2 + pd.bcoff + col0, IC * 8u, &S.full[slot]);
                         StageHdr& hh = S.hdr[slot];
                         hh.sidx = s;
                         hh.flags = first ? H_FIRST : 0;
@@ -616,7 +697,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                             const int a = __ffs(rem) - 1;
                             const uint32_t x = rem >> a;
                             const int len = x == FULLMASK ? 32 : __ffs(~x) - 1;
-                            tma_rows(T, S.stage[slot] + a * IC, col0, ra + a, len, &S.full[slot]);
+                            tma_rows(maps, S.stage[slot] + a * IC, col0, ra - pd.roff + a, len, &S.full[slot]);
                             rem &= a + len >= 32 ? 0u : ~((1u << (a + len)) - 1u);
                         }
                     }
@@ -628,7 +709,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                             const int a = __ffs(rem) - 1;
                             const uint32_t x = rem >> a;
                             const int len = x == FULLMASK ? 32 : __ffs(~x) - 1;
-                            tma_tile_rows(T, dst + a * TW, col0 + lane * TW, ra + a, len, &S.full[slot]);
+                            tma_tile_rows(maps, dst + a * TW, col0 + lane * TW, ra - pd.roff + a, len, &S.full[slot]);
                             rem &= a + len >= 32 ? 0u : ~((1u << (a + len)) - 1u);
                         }
                     }
@@ -653,12 +734,14 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
     }
 
     // ----------------------------------------------------------- consumers
-    const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);
+    FxScale fx = prob_fx(A, 0);  // the current item's problem's
     const int wc = warp * TW + lane;  // this lane's column within an item
     long long consumed = 0;
     Ctx x;
-    x.bh = 0.f; x.bl = 0.f; x.bp = -INFINITY; x.colg = 0; x.U = 0u;
-    double psi_acc = 0.0, cacc = 0.0;
+    x.bh = 0.f; x.bl = 0.f; x.bp = -INFINITY; x.colg = 0; x.U = 0u; x.real = false;
+    x.Cp = nullptr; x.ldc = 0; x.roff = 0; x.lcol = 0; x.prob = 0;
+    float psi_acc[2] = {0.f, 0.f};  // this lane's psi sum over the item's blocks, a float pair
+    long long cacc = 0;              // this lane's column sum over the item's blocks, fixed point
     int item = -1;  // the item being consumed; its sums are written when the next one starts
     Block blk;
     x.r0 = 0;
@@ -669,11 +752,11 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
     x.part = -1;
     open_block(blk, make_int4(0, 0, 0, 0), false, x);
     auto finish_item = [&]() {
-        double v = psi_acc;
+        double v = (double)psi_acc[0] + (double)psi_acc[1];
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
         if (lane == 0) A.psipart[(int64_t)item * NWARPS + warp] = v;
-        if (x.colg < A.n && cacc != 0.0) red_fx(A.colfx + x.colg, cacc, fx.to_c);
+        if (x.real && cacc != 0) atomicAdd(A.colfx + x.colg, (unsigned long long)cacc);
     };
     for (;;) {
         const int slot = (int)(consumed % NSTAGES);
@@ -698,10 +781,23 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             const float2 b2 = S.colB[slot][wc];
             x.bh = b2.x;
             x.bl = b2.y;
-            x.colg = hs.d.col0 + wc;
-            x.bp = x.colg < A.n ? bound_up(x.bh) : -INFINITY;  // B'; no element of a padding column passes
-            psi_acc = 0.0;
-            cacc = 0.0;
+            x.prob = hs.d.prob;
+            if (A.pfx) fx = A.pfx[x.prob];
+            const ProbDesc pd = A.probs[x.prob];
+            x.Cp = pd.C;
+            x.ldc = pd.ldc;
+            x.roff = pd.roff;
+            x.lcol = hs.d.col0 + wc;
+            x.colg = pd.coff + x.lcol;
+            x.real = wc < hs.d.ncols;
+            if (!x.real) {  // past the problem's last column (the pairs there may be another problem's)
+                x.bh = -1e30f;
+                x.bl = 0.f;
+            }
+            x.bp = x.real ? bound_up(x.bh) : -INFINITY;  // B'; no element of a missing column passes
+            psi_acc[0] = 0.f;
+            psi_acc[1] = 0.f;
+            cacc = 0;
             blk.gend = r0;  // no block continues into the item
         }
         x.r0 = r0;
@@ -800,10 +896,12 @@ void launch_stage_masks(const EvalArgs& a, cudaStream_t st)
 // row sums (integer adds: the total does not depend on their order).  Eight
 // rows' loads are issued together.
 __device__ __forceinline__ void passb_rows(const EvalArgs& A, const FxScale& fx, int R0, int R1, int step,
-                                           int colg, float s)
+                                           int prob, int colg, float s)
 {
-    const bool real = colg < A.n;
-    const float2 b2 = real ? __ldg(A.B2 + colg) : make_float2(0.f, 0.f);
+    const ProbDesc pd = A.probs[prob];
+    const int lcol = colg - pd.coff;
+    const bool real = lcol < pd.n;
+    const float2 b2 = real ? __ldg(A.B2 + pd.bcoff + lcol) : make_float2(0.f, 0.f);
     const float bp = real ? bound_up(b2.x) : -INFINITY;
     for (int R = R0; R < R1; R += step) {
         float c[8];
@@ -811,15 +909,19 @@ __device__ __forceinline__ void passb_rows(const EvalArgs& A, const FxScale& fx,
 #pragma unroll
         for (int q = 0; q < 8; q++) {
             const int Rq = min(R + q, R1 - 1);
-            c[q] = real ? __ldg(A.C + (int64_t)Rq * A.ldc + colg) : 0.f;
+            c[q] = real ? __ldg(pd.C + (int64_t)(Rq - pd.roff) * pd.ldc + lcol) : 0.f;
             a[q] = __ldg(A.rowA + Rq);
         }
 #pragma unroll
         for (int q = 0; q < 8; q++) {
-            if (R + q >= R1 || !(s > 0.f) || !maybe_pos(a[q].z, c[q], bp)) continue;
-            float fh, fl;
-            f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
-            if (fh > 0.f) red_fx(A.rowfx + R + q, (double)__fmul_rn(s, fh), fx.to_r);
+            if (R + q >= R1) break;  // (uniform)
+            unsigned long long tq = 0ull;
+            if (s > 0.f && maybe_pos(a[q].z, c[q], bp)) {
+                float fh, fl;
+                f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
+                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), fx.to_rf);
+            }
+            red_row(A.rowfx + R + q, tq);
         }
     }
 }
@@ -833,15 +935,15 @@ __global__ void __launch_bounds__(PASSB_THREADS) k_passb(const EvalArgs A)
     if (A.gate && !*A.gate) return;
     const int nb = min(A.ctl->npassb, A.passb_cap);
     if (nb == 0) return;
-    const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = PASSB_THREADS / 32;
     for (int eb = blockIdx.x; eb < nb; eb += gridDim.x) {
         const PassB& e = A.passb[eb];
         const float s = e.s[lane];
         if (!__any_sync(FULLMASK, s > 0.f)) continue;
+        const FxScale fx = prob_fx(A, e.prob);
         // warp w: 8-row batches w, w + nw, ... of the entry
         for (int R = e.gstart + 8 * warp; R < e.gend; R += 8 * nw)
-            passb_rows(A, fx, R, min(R + 8, e.gend), 8, e.colg0 + lane, s);
+            passb_rows(A, fx, R, min(R + 8, e.gend), 8, e.prob, e.colg0 + lane, s);
     }
 }
 
@@ -858,14 +960,18 @@ void launch_passb(const EvalArgs& a, int n_sm, cudaStream_t st)
 __global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
-    const FxScale fx = fx_scale(A.ctl->amax, A.ctl->bmax, A.m, A.n, A.gamma);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int si = blockIdx.x; si < A.nsets; si += gridDim.x) {
         const SplitSet st = A.sets[si];
+        if (A.prob_active && !A.prob_active[st.prob]) continue;  // a finished problem of a batch
         const int tile = st.col0 / TW + warp;
         if (A.unit_need && !((A.unit_need[(int64_t)st.l * A.unit_words + (tile >> 5)] >> (tile & 31)) & 1u))
             continue;  // a screened-out unit: its pieces wrote nothing this evaluation
-        const int colg = st.col0 + warp * TW + lane;
+        const ProbDesc pd = A.probs[st.prob];
+        const FxScale fx = prob_fx(A, st.prob);
+        const int lcol = st.col0 + warp * TW + lane;
+        const int colg = pd.coff + lcol;
+        const bool real = lcol < pd.n;
         Acc t = {0.f, 0.f, 0.f, 0.f};
         float o = 0.f;
         for (int k = 0; k < st.split; k++) {
@@ -877,17 +983,18 @@ __global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
         float s = 0.f;
         double psi = 0.0;
         if (__any_sync(FULLMASK, t.Ph > 0.f)) {
-            s = block_scale(t.Sh, t.Sl, A, psi);
-            if (s > 0.f && colg < A.n)
-                red_fx(A.colfx + colg, (double)s * ((double)t.Ph + (double)t.Pl), fx.to_c);
+            float psh, psl;
+            s = block_scale(t.Sh, t.Sl, A, psh, psl);
+            psi = (double)psh + (double)psl;
+            if (s > 0.f && real) atomicAdd(A.colfx + colg, (unsigned long long)col_q(s, t.Ph, t.Pl, fx.to_cf));
         }
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) psi += __shfl_xor_sync(FULLMASK, psi, off);
         if (lane == 0 && psi != 0.0) A.psipart[(int64_t)st.item0 * NWARPS + warp] += psi;
-        if (A.zt) put_snap(A, st.l, colg, z_up(t.Sh, t.Sl), __fsqrt_ru(o));
+        if (A.zt) put_snap(A, st.l, colg, real, z_up(t.Sh, t.Sl), __fsqrt_ru(o));
         if (!__any_sync(FULLMASK, s > 0.f)) continue;
-        if (!defer_passb(A, st.rstart, st.rend, st.col0 + warp * TW, s, lane))
-            passb_rows(A, fx, st.rstart, st.rend, 8, colg, s);  // the list is full
+        if (!defer_passb(A, st.rstart, st.rend, colg - lane, st.prob, s, lane))
+            passb_rows(A, fx, st.rstart, st.rend, 8, st.prob, colg, s);  // the list is full
     }
 }
 
@@ -898,16 +1005,18 @@ void launch_split_finish(const EvalArgs& a, cudaStream_t st)
 
 size_t stream_smem_bytes() { return sizeof(Smem) + 1024; }
 
-void launch_stream(const EvalArgs& a, const TmaMaps& T, int n_ctas, cudaStream_t st)
+bool stream_prepare()
 {
     const int sm = (int)stream_smem_bytes();
-    if (a.zt) {
-        cudaFuncSetAttribute(k_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        k_stream<true><<<n_ctas, THREADS, sm, st>>>(a, T);
-    } else {
-        cudaFuncSetAttribute(k_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
-        k_stream<false><<<n_ctas, THREADS, sm, st>>>(a, T);
-    }
+    return cudaFuncSetAttribute(k_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess &&
+           cudaFuncSetAttribute(k_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+}
+
+void launch_stream(const EvalArgs& a, int n_ctas, cudaStream_t st)
+{
+    const int sm = (int)stream_smem_bytes();
+    if (a.zt) k_stream<true><<<n_ctas, THREADS, sm, st>>>(a);
+    else k_stream<false><<<n_ctas, THREADS, sm, st>>>(a);
 }
 
 // ------------------------------------------------------------ TMA maps

@@ -16,6 +16,8 @@ Workloads (shapes follow the paper's domain-adaptation problems, Sec. 5.1):
 * :func:`tiny`   m=n=200, 10 classes x 20 rows, d=10
 * :func:`mid`    m=n=4000, 100 classes with Dirichlet(2) sizes, d=256
 * :func:`large`  m=n=20000, 1000 classes with Zipf(1.1) sizes (min 2), d=512
+* :func:`batch`  many independent problems, m, n ~ U[64, 2048], L ~ U[5, 100]
+  with Dirichlet(2) sizes, d=64
 * :func:`paper_synthetic` the paper's controlled-class data set (Sec. 5.1):
   d=2, g rows per class, class means (5l, -5) for sources and (5l, 5) for
   targets, unit Gaussian noise.
@@ -29,7 +31,7 @@ import numpy as np
 __all__ = [
     "Problem", "class_sizes_dirichlet", "class_sizes_zipf", "labels_from_sizes",
     "mixture_features", "cost_matrix", "make_problem", "tiny", "mid", "large",
-    "paper_synthetic", "random_duals", "random_instance",
+    "paper_synthetic", "random_duals", "random_instance", "batch",
 ]
 
 
@@ -213,6 +215,25 @@ def random_instance(m: int, n: int, L: int, seed: int = 0, d: int = 4,
     XS, XT, lab = mixture_features(sizes, n, d, rng)
     p = make_problem(XS, XT, lab, L, name=f"random_{m}x{n}_L{L}")
     return _maybe_shuffle(p, shuffle_rows, rng)
+
+
+def batch(seed: int = 0, nprob: int = 512, m_range=(64, 2048), n_range=(64, 2048), L_range=(5, 100),
+          d: int = 64, device=None) -> list:
+    """Independent problems of uneven shape: m, n uniform in the given
+    (inclusive) ranges, L uniform in L_range, class sizes 1 + largest-remainder
+    Dirichlet(2) (0 + Dirichlet when m < L), d-dimensional mixture features
+    as in :func:`mid`; labels sorted.  Problem k draws from its own stream
+    (seed, k), so a prefix of a batch does not depend on nprob."""
+    out = []
+    for k in range(nprob):
+        rng = np.random.default_rng([seed, k])
+        m = int(rng.integers(m_range[0], m_range[1] + 1))
+        n = int(rng.integers(n_range[0], n_range[1] + 1))
+        L = int(rng.integers(L_range[0], L_range[1] + 1))
+        sizes = class_sizes_dirichlet(m, L, 2.0, rng, min_size=1 if m >= L else 0)
+        XS, XT, lab = mixture_features(sizes, n, d, rng)
+        out.append(make_problem(XS, XT, lab, L, name=f"batch{k}_{m}x{n}_L{L}", device=device))
+    return out
 
 
 def random_duals(m: int, n: int, seed: int = 0, scale: float = 0.5, offset: float = 0.3):

@@ -97,3 +97,79 @@ def test_plan_zipf_large_shape():
 def test_plan_rejects_bad_labels():
     with pytest.raises(pk.OTGSError):
         pk.ot_gs_plan_info(np.array([0, 3, 1], np.int32), 5, 3)
+
+
+def expected_panels(sizes, panel_rows, split_rows):
+    panels, cur = [], 0
+    for g in sizes:
+        if g == 0:
+            continue
+        if g > split_rows:
+            if cur:
+                panels.append(cur)
+                cur = 0
+            panels += [min(split_rows, g - k) for k in range(0, g, split_rows)]
+            continue
+        if cur and cur + g > panel_rows:
+            panels.append(cur)
+            cur = 0
+        cur += g
+        if cur >= panel_rows:
+            panels.append(cur)
+            cur = 0
+    if cur:
+        panels.append(cur)
+    return panels
+
+
+def expected_plan_batch(sizes_list, ns, panel_rows=0, split_rows=0):
+    """A batch is planned problem by problem (a panel never holds rows of
+    two problems, an item never pairs rows with another problem's columns);
+    the default panel height comes from the batch's total rows and columns."""
+    m = sum(int(np.sum(s)) for s in sizes_list)
+    pr = panel_rows or panel_height(m, sum(ns))
+    sr = split_rows or SPLIT_ROWS
+    n_panels = n_items = n_stages = 0
+    for sizes, n in zip(sizes_list, ns):
+        panels = expected_panels(sizes, pr, sr)
+        assert sum(panels) == int(np.sum(sizes))
+        nch = -(-n // ITEM_COLS)
+        n_panels += len(panels)
+        n_items += len(panels) * nch
+        n_stages += sum(-(-r // STAGE_ROWS) for r in panels) * nch
+    return n_panels, n_items, n_stages
+
+
+@pytest.mark.parametrize("pr,sr", [(0, 0), (32, 128), (128, 256), (512, 1024), (1024, 64)])
+def test_batch_plan_is_per_problem(pr, sr):
+    rng = np.random.default_rng(5)
+    sizes_list, ns = [], []
+    for k in range(9):
+        L = int(rng.integers(1, 30))
+        sizes = rng.integers(0, 200, size=L)
+        if k == 3:
+            sizes[0] = 1300  # a tall group: pieces
+        sizes[-1] = max(sizes[-1], 1)
+        sizes_list.append(sizes)
+        ns.append(int(rng.integers(1, 700)))
+    labels = [synth.labels_from_sizes(s) for s in sizes_list]
+    info = pk.ot_gs_plan_info_batch(labels, ns, [len(s) for s in sizes_list], pr, sr)
+    assert (info["n_panels"], info["n_items"], info["n_stages"]) == expected_plan_batch(sizes_list, ns, pr, sr)
+
+
+def test_batch_of_one_plans_like_one_problem():
+    sizes = [1, 2, 3, 70, 5, 4100, 0, 9]
+    lab = synth.labels_from_sizes(np.array(sizes))
+    a = pk.ot_gs_plan_info(lab, 77, len(sizes))
+    b = pk.ot_gs_plan_info_batch([lab], [77], [len(sizes)])
+    assert a == b
+
+
+def test_batch_plan_rejects_bad_input():
+    with pytest.raises(pk.OTGSError):
+        pk.ot_gs_plan_info_batch([np.array([0, 1], np.int32), np.array([0, 5], np.int32)], [4, 4], [2, 2])
+    h = ctypes.c_void_p()
+    rc = pk.lib().ot_gs_create_batch(ctypes.byref(h), 0, None, None, None, None, None, None, None, None,
+                                     1.0, 0.1, None)
+    assert rc == pk.OTGS_EINVAL and not h.value
+    assert "nprob" in pk.ot_gs_last_error(None)
