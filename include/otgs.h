@@ -301,20 +301,26 @@ OTGS_API int ot_gs_batch_result(ot_gs *h, double *alpha, double *beta, double *D
 /*
  * Plan shape.  panel_rows: rows of whole class groups per work item (an item
  * is panel x 256 columns); split_rows: groups taller than this are cut into
- * pieces of this height, summed by different CTAs.  ot_gs_set_plan rebuilds
- * the handle's plan (0 = the default of each) and synchronises; valid ranges
- * are [32, 4096] and [64, 8192].  ot_gs_get_plan reports the current shape
- * and the number of work items (host pointers, each may be NULL).
+ * pieces of this height, summed by different CTAs; stage_fill: 0 = C streams
+ * in stages of 32 rows, k > 0 = a stage ends early, before a group of at most
+ * 32 rows that would straddle its end, when it keeps at least k rows (such a
+ * group's blocks then finish from shared memory, without the second pass of
+ * the pass-B kernel).  ot_gs_set_plan rebuilds the handle's plan (0 = the
+ * default of each) and synchronises; valid ranges are [32, 4096], [64, 8192]
+ * and [0, 32].  ot_gs_get_plan reports the current shape and the number of
+ * work items (host pointers, each may be NULL).
  */
-OTGS_API int ot_gs_set_plan(ot_gs *h, int32_t panel_rows, int32_t split_rows);
-OTGS_API int ot_gs_get_plan(const ot_gs *h, int32_t *panel_rows, int32_t *split_rows, int64_t *n_items);
+OTGS_API int ot_gs_set_plan(ot_gs *h, int32_t panel_rows, int32_t split_rows, int32_t stage_fill);
+OTGS_API int ot_gs_get_plan(const ot_gs *h, int32_t *panel_rows, int32_t *split_rows, int32_t *stage_fill,
+                            int64_t *n_items);
 
 /*
  * Autotuner of the plan shape: times `evals` dense evaluations of all the
  * handle's problems at (alpha, beta) (device FP64, concatenated layout; the
  * cost depends on how many blocks are positive there, so pass a point like
  * those the solver visits) for each candidate (panel_rows in {32, ..., 1024},
- * split_rows in {128, ..., 1024}), and keeps the fastest.  The choice is
+ * split_rows in {128, ..., 1024}, stage_fill in {0, 16}), and keeps the
+ * fastest.  The choice is
  * cached for the process under a key of the group-size histogram (share of
  * rows per power-of-two size class) and the size classes of the column count
  * per problem, the row count and the number of problems; a cached shape is
@@ -322,15 +328,15 @@ OTGS_API int ot_gs_get_plan(const ot_gs *h, int32_t *panel_rows, int32_t *split_
  * may be NULL).  Synchronises.  ot_gs_autotune_clear_cache forgets all shapes.
  */
 OTGS_API int ot_gs_autotune(ot_gs *h, const double *alpha, const double *beta, int32_t evals,
-                            int32_t *panel_rows, int32_t *split_rows, double *best_ms);
+                            int32_t *panel_rows, int32_t *split_rows, int32_t *stage_fill, double *best_ms);
 OTGS_API int ot_gs_autotune_clear_cache(void);
 
 /* Host-only plan of a batch (no GPU needed), as ot_gs_plan_info: labels_host,
  * m, n, L are host arrays of nprob entries (labels_host[k]: host int32 [m[k]]);
- * panel_rows, split_rows as ot_gs_set_plan (0 = default). */
+ * panel_rows, split_rows, stage_fill as ot_gs_set_plan (0 = default). */
 OTGS_API int ot_gs_plan_info_batch(int32_t nprob, const int32_t *const *labels_host, const int64_t *m,
                                    const int64_t *n, const int32_t *L, int32_t panel_rows, int32_t split_rows,
-                                   int64_t *n_panels, int64_t *n_items, int64_t *n_stages);
+                                   int32_t stage_fill, int64_t *n_panels, int64_t *n_items, int64_t *n_stages);
 
 /*
  * Allocation-free dense evaluation.  The paper has no counterpart: this entry

@@ -94,11 +94,11 @@ def lib():
         "ot_gs_batch_solve": ([P, dbl, i32, P, dbl], ctypes.c_int),
         "ot_gs_batch_set_state": ([P, P, P], ctypes.c_int),
         "ot_gs_batch_result": ([P, P, P, P, P, P, P, P, P], ctypes.c_int),
-        "ot_gs_set_plan": ([P, i32, i32], ctypes.c_int),
-        "ot_gs_get_plan": ([P, P, P, P], ctypes.c_int),
-        "ot_gs_autotune": ([P, P, P, i32, P, P, P], ctypes.c_int),
+        "ot_gs_set_plan": ([P, i32, i32, i32], ctypes.c_int),
+        "ot_gs_get_plan": ([P, P, P, P, P], ctypes.c_int),
+        "ot_gs_autotune": ([P, P, P, i32, P, P, P, P], ctypes.c_int),
         "ot_gs_autotune_clear_cache": ([], ctypes.c_int),
-        "ot_gs_plan_info_batch": ([i32, P, P, P, P, i32, i32, P, P, P], ctypes.c_int),
+        "ot_gs_plan_info_batch": ([i32, P, P, P, P, i32, i32, i32, P, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -391,30 +391,30 @@ def ot_gs_batch_result(h, nprob, alpha=None, beta=None):
     return dict(D=D, grad_inf=gi, iters=it, status=stt, evals=ev, t_ms=t)
 
 
-def ot_gs_set_plan(h, panel_rows=0, split_rows=0):
-    return _check(h, lib().ot_gs_set_plan(h, int(panel_rows), int(split_rows)))
+def ot_gs_set_plan(h, panel_rows=0, split_rows=0, stage_fill=0):
+    return _check(h, lib().ot_gs_set_plan(h, int(panel_rows), int(split_rows), int(stage_fill)))
 
 
 def ot_gs_get_plan(h):
-    pr, sr, ni = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
-    _check(h, lib().ot_gs_get_plan(h, ctypes.byref(pr), ctypes.byref(sr), ctypes.byref(ni)))
-    return dict(panel_rows=pr.value, split_rows=sr.value, n_items=ni.value)
+    pr, sr, sf, ni = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+    _check(h, lib().ot_gs_get_plan(h, ctypes.byref(pr), ctypes.byref(sr), ctypes.byref(sf), ctypes.byref(ni)))
+    return dict(panel_rows=pr.value, split_rows=sr.value, stage_fill=sf.value, n_items=ni.value)
 
 
 def ot_gs_autotune(h, alpha, beta, evals=5):
     import torch
-    pr, sr, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
+    pr, sr, sf, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_double()
     _check(h, lib().ot_gs_autotune(h, _ptr(alpha, torch.float64, name="alpha"),
                                    _ptr(beta, torch.float64, name="beta"), int(evals), ctypes.byref(pr),
-                                   ctypes.byref(sr), ctypes.byref(ms)))
-    return dict(panel_rows=pr.value, split_rows=sr.value, best_ms=ms.value)
+                                   ctypes.byref(sr), ctypes.byref(sf), ctypes.byref(ms)))
+    return dict(panel_rows=pr.value, split_rows=sr.value, stage_fill=sf.value, best_ms=ms.value)
 
 
 def ot_gs_autotune_clear_cache():
     return lib().ot_gs_autotune_clear_cache()
 
 
-def ot_gs_plan_info_batch(labels_list, ns, Ls, panel_rows=0, split_rows=0):
+def ot_gs_plan_info_batch(labels_list, ns, Ls, panel_rows=0, split_rows=0, stage_fill=0):
     """Host-only plan of a batch: counts of panels, work items and stages."""
     k = len(labels_list)
     labs = [np.ascontiguousarray(x, dtype=np.int32) for x in labels_list]
@@ -424,7 +424,7 @@ def ot_gs_plan_info_batch(labels_list, ns, Ls, panel_rows=0, split_rows=0):
     Lp = _host_array([int(x) for x in Ls], ctypes.c_int32)
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     rc = lib().ot_gs_plan_info_batch(k, lp[1], mp[1], npp[1], Lp[1], int(panel_rows), int(split_rows),
-                                     ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+                                     int(stage_fill), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
     if rc != OTGS_OK:
         raise OTGSError(rc, "invalid plan input")
     return dict(n_panels=a.value, n_items=b.value, n_stages=c.value)
@@ -559,8 +559,8 @@ class GroupSparseOTBatch:
             r["alpha"], r["beta"] = al, be
         return r
 
-    def set_plan(self, panel_rows=0, split_rows=0):
-        ot_gs_set_plan(self.h, panel_rows, split_rows)
+    def set_plan(self, panel_rows=0, split_rows=0, stage_fill=0):
+        ot_gs_set_plan(self.h, panel_rows, split_rows, stage_fill)
 
     def plan(self):
         return ot_gs_get_plan(self.h)

@@ -259,7 +259,7 @@ bool Handle::init(int32_t np, const float* const* C_, const int64_t* ldc_, const
     if (!rowA || !B2 || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !pfx) return false;
     if (!ck(cudaMemsetAsync(B2, 0, sizeof(float2) * (size_t)hp.nb2, st), "memset B2")) return false;
     if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
-    passb_cap = (int)std::min<int64_t>((int64_t)L * ntiles, 65536);
+    passb_cap = (int)std::min<int64_t>(2 * (int64_t)L * ntiles, 1 << 18);
     passb = (PassB*)dalloc(sizeof(PassB) * (size_t)passb_cap, "pass-B list");
     if (!passb) return false;
     {
@@ -312,8 +312,9 @@ bool Handle::setup_plan(const PlanParams& pp)
     dp.exec_order = plan_upload(this, hp.exec_order, "exec_order");
     dp.desc = plan_upload(this, hp.desc, "item descriptors");
     dp.sets = plan_upload(this, hp.sets, "split block sets");
+    dp.stage_row0 = plan_upload(this, hp.stage_row0, "stage rows");
     if (!dp.prows || !dp.pW || !dp.pnch || !dp.pitem || !dp.psplit || !dp.gpanel || !dp.item_panel ||
-        !dp.item_chunk || !dp.exec_order || !dp.desc || !dp.sets)
+        !dp.item_chunk || !dp.exec_order || !dp.desc || !dp.sets || !dp.stage_row0)
         return false;
     bprob_h.resize(nprob);
     {
@@ -359,6 +360,7 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.ctl = ctl; e.err = kerr;
     e.nlist = hp.nitems();
     e.desc = dp.desc;
+    e.stage_row0 = dp.stage_row0;
     e.item_active = active;
     e.unit_need = need;
     e.unit_words = unit_words;
@@ -630,14 +632,17 @@ int ot_gs_plan_info(const int32_t* labels_host, int64_t m, int64_t n, int32_t L,
 }
 
 int ot_gs_plan_info_batch(int32_t nprob, const int32_t* const* labels_host, const int64_t* m, const int64_t* n,
-                          const int32_t* L, int32_t panel_rows, int32_t split_rows, int64_t* n_panels,
-                          int64_t* n_items, int64_t* n_stages)
+                          const int32_t* L, int32_t panel_rows, int32_t split_rows, int32_t stage_fill,
+                          int64_t* n_panels, int64_t* n_items, int64_t* n_stages)
 {
-    if (nprob <= 0 || !labels_host || !m || !n || !L || panel_rows < 0 || split_rows < 0) return OTGS_EINVAL;
+    if (nprob <= 0 || !labels_host || !m || !n || !L || panel_rows < 0 || split_rows < 0 || stage_fill < 0 ||
+        stage_fill > STAGE_ROWS)
+        return OTGS_EINVAL;
     HostPlan hp;
     PlanParams pp;
     pp.panel_rows = panel_rows;
     pp.split_rows = split_rows;
+    pp.stage_fill = stage_fill;
     if (!build_plan_batch(nprob, labels_host, m, n, L, pp, hp).empty()) return OTGS_EINVAL;
     if (n_panels) *n_panels = hp.npanels();
     if (n_items) *n_items = hp.nitems();

@@ -26,6 +26,7 @@ constexpr int ITEM_COLS = NWARPS * TW;  // columns of a work item: 1 KB of each 
 // x ITEM_COLS columns (32 KB) per CTA, loaded by 2D TMA boxes.
 constexpr int STAGE_ROWS = 32;
 constexpr int NSTAGES = 3;
+
 // CTAs of the evaluation kernel per SM (each with its own ring).
 constexpr int CTAS_PER_SM = 2;
 // Consecutive groups are packed into "panels" of whole groups up to a panel
@@ -106,6 +107,11 @@ struct SplitSet {
 struct PlanParams {
     int32_t panel_rows = 0;  // panel height (default: panel_rows(m, n))
     int32_t split_rows = 0;  // groups taller than this are cut into pieces (default: SPLIT_ROWS)
+    // > 0: a stage ends early, before a group of at most STAGE_ROWS rows that
+    // would straddle its end (so that the group's blocks finish from shared
+    // memory instead of the pass-B kernel), when it keeps at least this many
+    // rows; 0 (default): stages of STAGE_ROWS rows
+    int32_t stage_fill = 0;
 };
 
 // A problem of a batch as the kernels see it.
@@ -135,13 +141,14 @@ struct ItemDesc {
     int rows;   // rows (whole groups, or one piece of a split group)
     int col0;   // first column (multiple of ITEM_COLS)
     int ncols;  // columns of C in the item (<= ITEM_COLS)
-    int nst;    // stages: ceil(rows / STAGE_ROWS)
+    int nst;    // stages of the item's panel (at most STAGE_ROWS rows each)
     int sbase;  // first stage of the item in execution order (index into per-stage tables)
     int split;  // pieces of the item's group (1: not split)
     int sub;    // this item's piece
     int part;   // split groups: partial-sum slot of piece 0 of this block set (piece k: part + k)
     int prob;   // problem of a batch (0 for a single problem)
-    int pad[4];
+    int st0;    // stage s spans sorted rows [stage_row0[st0 + s], stage_row0[st0 + s + 1])
+    int pad[3];
 };
 
 // ------------------------------------------------------------------ host plan
@@ -159,7 +166,7 @@ struct HostPlan {
     int64_t nb2 = 0;                           // entries of B2, with room for a full last column chunk
     int64_t max_m = 0, max_n = 0;              // largest problem
     std::vector<int32_t> gprob;                // group -> problem
-    int32_t panel_height = 0, split_height = 0;  // the parameters the plan was built with
+    int32_t panel_height = 0, split_height = 0, stage_fill = 0;  // the parameters the plan was built with
     std::vector<int32_t> perm;    // sorted r -> caller row
     std::vector<int32_t> goff;    // L+1 offsets (sorted rows)
     std::vector<int32_t> rgroup;  // sorted r -> group
@@ -175,6 +182,11 @@ struct HostPlan {
     std::vector<int32_t> psub;    // the panel's piece
     std::vector<int32_t> pslot;   // pieces of split groups before the panel's group (split panels)
     std::vector<int32_t> gpanel;  // group -> panel (-1 for empty groups; the first piece if split)
+    // stages: a panel's rows in runs of at most STAGE_ROWS, ended early (at
+    // a group's start) rather than cut a short group in two
+    std::vector<int32_t> pst0;        // panel -> its first entry of stage_row0
+    std::vector<int32_t> pnst;        // panel -> its number of stages
+    std::vector<int32_t> stage_row0;  // per panel: the stages' first rows, then the panel's end
     // work items, id = pitem[p] + chunk
     std::vector<int32_t> item_panel, item_chunk;
     std::vector<int32_t> exec_order;  // item ids, largest first
@@ -202,6 +214,7 @@ struct DevPlan {
     int32_t *prows, *pW, *pnch, *pitem, *psplit, *gpanel;
     int32_t *item_panel, *item_chunk, *exec_order;
     ItemDesc* desc;
+    int32_t* stage_row0;
 };
 
 // ------------------------------------------------- per-evaluation control word
@@ -294,6 +307,7 @@ struct EvalArgs {
     int* err;            // error word (0 = ok)
     int32_t nlist;       // entries of desc
     const ItemDesc* desc;
+    const int32_t* stage_row0;    // stage boundaries (ItemDesc::st0)
     const uint8_t* item_active;   // per item id: 1 if it has a unit to evaluate (screened), else NULL
     const uint32_t* unit_need;    // L x unit_words bitmask of units to evaluate, NULL = all
     const uint8_t* stage_m8;      // screened: [nstages][STAGE_ROWS] per row, bit w = tile w of its item needed

@@ -90,6 +90,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     Carve cv;
     const size_t o_perm = cv.take(4 * hp.perm.size()), o_rowg = cv.take(sizeof(int4) * hp.rowg.size());
     const size_t o_desc = cv.take(sizeof(ItemDesc) * hp.desc.size());
+    const size_t o_st = cv.take(sizeof(int32_t) * hp.stage_row0.size());
     const size_t o_rowA = cv.take(sizeof(float4) * (size_t)m);
     const size_t o_B2 = cv.take(8 * (size_t)padded_cols(n));
     const size_t o_ctl = cv.take(sizeof(EvalCtl)), o_err = cv.take(16);
@@ -131,6 +132,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     e = up(o_perm, hp.perm.data(), 4 * hp.perm.size());
     if (e == cudaSuccess) e = up(o_rowg, hp.rowg.data(), sizeof(int4) * hp.rowg.size());
     if (e == cudaSuccess) e = up(o_desc, hp.desc.data(), sizeof(ItemDesc) * hp.desc.size());
+    if (e == cudaSuccess) e = up(o_st, hp.stage_row0.data(), sizeof(int32_t) * hp.stage_row0.size());
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_counter, 0, 16, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(base + o_err, 0, 16, st);
     if (e == cudaSuccess) e = up(o_sets, hp.sets.data(), sizeof(SplitSet) * hp.sets.size());
@@ -168,6 +170,7 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     ea.ctl = ctl; ea.err = (int*)(base + o_err);
     ea.nlist = hp.nitems();
     ea.desc = (const ItemDesc*)(base + o_desc);
+    ea.stage_row0 = (const int32_t*)(base + o_st);
     ea.item_active = nullptr; ea.unit_need = nullptr;
     ea.unit_words = (ntiles + 31) / 32;
     ea.rowfx = rowfx; ea.colfx = colfx;

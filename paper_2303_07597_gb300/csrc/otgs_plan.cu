@@ -88,6 +88,7 @@ std::string build_plan_batch(int32_t nprob, const int32_t* const* labels, const 
     const int32_t SPLIT = pp.split_rows > 0 ? pp.split_rows : SPLIT_ROWS;
     hp.panel_height = PANEL_ROWS;
     hp.split_height = SPLIT;
+    hp.stage_fill = pp.stage_fill;
     hp.gpanel.assign(L, -1);
     int32_t cur0 = -1, cur_rows = 0, cur_prob = 0;
     int64_t slots = 0;
@@ -136,8 +137,31 @@ std::string build_plan_batch(int32_t nprob, const int32_t* const* labels, const 
     if (slots > INT32_MAX / (ITEM_COLS * 5)) return "too many pieces of tall groups";
     hp.nsplit_slots = slots;
 
-    // work items: (panel, column chunk of its problem)
+    // stages of each panel
     const int np = hp.npanels();
+    hp.pst0.resize(np);
+    hp.pnst.resize(np);
+    for (int p = 0; p < np; p++) {
+        hp.pst0[p] = (int32_t)hp.stage_row0.size();
+        const int32_t end = hp.prow0[p] + hp.prows[p];
+        int32_t ra = hp.prow0[p], cnt = 0;
+        while (ra < end) {
+            hp.stage_row0.push_back(ra);
+            cnt++;
+            int32_t nr = std::min<int32_t>(STAGE_ROWS, end - ra);
+            if (pp.stage_fill > 0 && ra + nr < end && hp.psplit[p] == 1) {
+                // the group holding the stage's last row: does it go on past the stage?
+                const int32_t l = hp.rgroup[ra + nr - 1], gs = hp.goff[l], ge = hp.goff[l + 1];
+                if (ge > ra + nr && ge - gs <= STAGE_ROWS && gs > ra && gs - ra >= pp.stage_fill) nr = gs - ra;
+            }
+            ra += nr;
+        }
+        hp.stage_row0.push_back(end);
+        hp.pnst[p] = cnt;
+    }
+    if (hp.stage_row0.size() > (size_t)INT32_MAX / 2) return "too many stages";
+
+    // work items: (panel, column chunk of its problem)
     hp.pW.assign(np, ITEM_COLS);
     hp.pnch.resize(np);
     hp.pitem.resize(np);
@@ -170,7 +194,8 @@ std::string build_plan_batch(int32_t nprob, const int32_t* const* labels, const 
         d.rows = hp.prows[p];
         d.col0 = cc * ITEM_COLS;
         d.ncols = (int)std::min<int64_t>(ITEM_COLS, hp.pn[k] - (int64_t)d.col0);
-        d.nst = (d.rows + STAGE_ROWS - 1) / STAGE_ROWS;
+        d.nst = hp.pnst[p];
+        d.st0 = hp.pst0[p];
         d.sbase = (int)hp.nstages;
         d.split = hp.psplit[p];
         d.sub = hp.psub[p];

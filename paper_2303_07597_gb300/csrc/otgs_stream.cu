@@ -53,23 +53,16 @@ constexpr int DESC_WORDS = (int)(sizeof(ItemDesc) / sizeof(int));
 static_assert(DESC_WORDS <= 32, "a descriptor is spread over the producer's lanes");
 static_assert(SR == 32, "the producer maps one lane to each row of a stage");
 
-// Stages of an item whose marked chunks a warp remembers for pass B (items of
-// up to MARK_STAGES * STAGE_ROWS rows; rows beyond are all visited).
-constexpr int MARK_STAGES = 256;
-// A block with s > 0 whose rows reach more than this many rows before the
-// current stage leaves its pass B to the pass-B kernel (re-reading them here
-// would hold the CTA's ring).
-constexpr int PASSB_INLINE_ROWS = 0;
 
 enum : int { H_FIRST = 1, H_TERM = 4 };
 
 // What the consumers need about a stage, written by the producer.
 struct StageHdr {
     ItemDesc d;
-    int sidx;     // stage index within the item
+    int ra;       // the stage's first sorted row
+    int nr;       // its rows (<= SR)
     int flags;
     int tiled;    // 0: rows of ITEM_COLS ([row][IC]); 1: per warp tile ([warp][row][TW])
-    int pad;
 };
 
 struct Smem {
@@ -78,7 +71,6 @@ struct Smem {
     int4 rowG[NSTAGES][SR];          // (group, first row, end row, 0) of the stage's rows
     float2 colB[NSTAGES][IC];        // item's first stage: (beta hi, lo) of its columns
     uint32_t rmaskw[NSTAGES][CONSUMERS];  // screened: bit r set = warp w evaluates row r's block
-    uint8_t marks[CONSUMERS][MARK_STAGES];  // per warp: marked chunks of each stage of the item
     StageHdr hdr[NSTAGES];
     uint64_t full[NSTAGES];
     uint64_t empty[NSTAGES];
@@ -403,6 +395,41 @@ __device__ __forceinline__ long long col_q(float s, float Ph, float Pl, float to
     return __float2ll_rn(__fmul_rn(ph, to_fx)) + __float2ll_rn(__fmul_rn(pl, to_fx));
 }
 
+// Rows [R0, R1) (stepping by `step` from R0) of a block for this lane's
+// column: re-form f and add the nonzero t_ij = s [f_ij]_+ to the fixed-point
+// row sums (integer adds: the total does not depend on their order).  Eight
+// rows' loads are issued together.
+__device__ __forceinline__ void passb_rows(const EvalArgs& A, const FxScale& fx, int R0, int R1, int step,
+                                           int prob, int colg, float s)
+{
+    const ProbDesc pd = A.probs[prob];
+    const int lcol = colg - pd.coff;
+    const bool real = lcol < pd.n;
+    const float2 b2 = real ? __ldg(A.B2 + pd.bcoff + lcol) : make_float2(0.f, 0.f);
+    const float bp = real ? bound_up(b2.x) : -INFINITY;
+    for (int R = R0; R < R1; R += step) {
+        float c[8];
+        float4 a[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const int Rq = min(R + q, R1 - 1);
+            c[q] = real ? __ldg(pd.C + (int64_t)(Rq - pd.roff) * pd.ldc + lcol) : 0.f;
+            a[q] = __ldg(A.rowA + Rq);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            if (R + q >= R1) break;  // (uniform)
+            unsigned long long tq = 0ull;
+            if (s > 0.f && maybe_pos(a[q].z, c[q], bp)) {
+                float fh, fl;
+                f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
+                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), fx.to_rf);
+            }
+            red_row(A.rowfx + R + q, tq);
+        }
+    }
+}
+
 // Snapshot values of block (l, col) (written only for a real column).
 __device__ __forceinline__ void put_snap(const EvalArgs& A, int l, int col, bool real, float zt, float ot)
 {
@@ -440,7 +467,6 @@ struct Ctx {
     uint32_t U;        // chunks of the stage marked by some lane (dense path)
     int r0;            // first sorted row of the item
     int rend;          // end row of the item
-    const uint8_t* marks;  // this warp's marked chunks of the item's stages
     int item, split, sub, part;  // the item; its group's pieces, its piece, the set's piece-0 slot
     int prob;          // the item's problem
 };
@@ -511,46 +537,35 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
     }
     if (SNAP) put_snap(A, b.gl, x.colg, x.real, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
     if (!__any_sync(FULLMASK, s > 0.f)) return;
-    if (b.gstart < x.ra - PASSB_INLINE_ROWS && defer_passb(A, b.gstart, b.gend, x.colg - lane, x.prob, s, lane))
-        return;
-    // pass B: t_ij = s [f_ij]_+ into the row sums, over the block's rows that
-    // can hold an f > 0 (marked chunks; every row on the snapshot walk),
-    // four rows at a time
-    const int sa = (b.gstart - x.r0) / SR, sb = (b.gend - 1 - x.r0) / SR;
-    for (int sg = sa; sg <= sb; sg++) {
-        const int base = x.r0 + sg * SR;
-        const bool here = base == x.ra;  // the stage being consumed is still in shared memory
-        uint32_t qm = 0xffu;  // rows past the record: all chunks
-        if (marks) qm = here ? x.U : (sg < MARK_STAGES ? (uint32_t)x.marks[sg] : 0xffu);
-        qm &= chunks_in(max(b.gstart - base, 0), min(b.gend - base, SR));
-        while (qm) {
-            const int q = __ffs(qm) - 1;
-            qm &= qm - 1u;
-            const int R0 = max(base + 4 * q, b.gstart), R1 = min(base + 4 * q + 4, b.gend);
-            float c[4];
-            float4 a[4];
+    if (b.gstart < x.ra) {
+        // the block began in an earlier stage, which has left the ring: its
+        // pass B goes to the pass-B kernel, or (that list is full) the
+        // earlier rows are re-read here
+        if (defer_passb(A, b.gstart, b.gend, x.colg - lane, x.prob, s, lane)) return;
+        passb_rows(A, fx, b.gstart, x.ra, 8, x.prob, x.colg, s);
+    }
+    // pass B over the block's rows in this stage: t_ij = s [f_ij]_+ into the
+    // row sums, over the chunks that can hold an f > 0 (every chunk on the
+    // snapshot walk), four rows at a time
+    uint32_t qm = marks ? x.U : 0xffu;
+    qm &= chunks_in(max(b.gstart - x.ra, 0), min(b.gend - x.ra, SR));
+    while (qm) {
+        const int q = __ffs(qm) - 1;
+        qm &= qm - 1u;
+        const int R0 = max(x.ra + 4 * q, b.gstart), R1 = min(x.ra + 4 * q + 4, b.gend);
 #pragma unroll
-            for (int k = 0; k < 4; k++) {
-                const int R = min(R0 + k, R1 - 1);
-                if (here) {
-                    c[k] = x.st[(R - base) * x.rs];
-                    a[k] = x.rA[R - base];
-                } else {  // the row's stage has left the ring: re-read it (from L2)
-                    c[k] = x.real ? __ldg(x.Cp + (int64_t)(R - x.roff) * x.ldc + x.lcol) : 0.f;
-                    a[k] = __ldg(A.rowA + R);
-                }
+        for (int k = 0; k < 4; k++) {
+            if (R0 + k >= R1) break;  // (uniform)
+            const int r = R0 + k - x.ra;
+            const float c = x.st[r * x.rs];
+            const float4 av = x.rA[r];
+            unsigned long long tq = 0ull;
+            if (s > 0.f && maybe_pos(av.z, c, x.bp)) {
+                float fh, fl;
+                f_exact(av.x, av.y, x.bh, x.bl, c, fh, fl);
+                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), fx.to_rf);
             }
-#pragma unroll
-            for (int k = 0; k < 4; k++) {
-                if (R0 + k >= R1) break;  // (uniform)
-                unsigned long long q = 0ull;
-                if (s > 0.f && maybe_pos(a[k].z, c[k], x.bp)) {
-                    float fh, fl;
-                    f_exact(a[k].x, a[k].y, x.bh, x.bl, c[k], fh, fl);
-                    if (fh > 0.f) q = t_q(__fmul_rn(s, fh), fx.to_rf);
-                }
-                red_row(A.rowfx + R0 + k, q);
-            }
+            red_row(A.rowfx + R0 + k, tq);
         }
     }
 }
@@ -614,10 +629,16 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             if (A.prob_active && lane == 0 && !__ldg(A.prob_active + prob)) act = 0;
             return act;
         };
+        // lane k: the item's stage boundary k (first rows, then the end), 32 at a time
+        auto load_st = [&](int idx, int w, int base) -> int {
+            const int st0 = __shfl_sync(FULLMASK, w, 12), nst = __shfl_sync(FULLMASK, w, 6);
+            return (idx < A.nlist && base + lane <= nst) ? __ldg(A.stage_row0 + st0 + base + lane) : 0;
+        };
         int fenced = -1;  // the problem whose tensor maps were last acquired
         int i0 = bcast(fetch());
         int w0 = load_w(i0);
         int a0 = load_act(i0, w0);
+        int v0 = load_st(i0, w0, 0);
         int i1 = bcast(fetch());
         int w1 = load_w(i1);
         int i2r = fetch();
@@ -633,11 +654,11 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 break;
             }
             const int a1 = load_act(i1, w1);
+            const int v1 = load_st(i1, w1, 0);
             const int i2 = bcast(i2r);
             const int w2 = load_w(i2);
             const int i3r = fetch();
             if (bcast(a0)) {
-                const int r0 = __shfl_sync(FULLMASK, w0, 2), rows = __shfl_sync(FULLMASK, w0, 3);
                 const int col0 = __shfl_sync(FULLMASK, w0, 4), nst = __shfl_sync(FULLMASK, w0, 6);
                 const int sbase = __shfl_sync(FULLMASK, w0, 7);
                 const int prob = __shfl_sync(FULLMASK, w0, 11);
@@ -653,9 +674,14 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 // screened: this lane's row's needed tiles, one stage ahead
                 uint32_t m8n = screened ? (uint32_t)__ldg(A.stage_m8 + (int64_t)sbase * SR + lane) : 0xffu;
                 bool first = true;  // no stage of this item issued yet
+                int wb = 0;         // first stage boundary held in v0
                 for (int s = 0; s < nst; s++) {
-                    const int ra = r0 + s * SR;
-                    const int nr = min(SR, rows - s * SR);
+                    if (s - wb >= 31) {  // a long item: the next 32 boundaries
+                        wb = s;
+                        v0 = load_st(i0, w0, wb);
+                    }
+                    const int ra = __shfl_sync(FULLMASK, v0, s - wb);
+                    const int nr = __shfl_sync(FULLMASK, v0, s - wb + 1) - ra;
                     uint32_t m8 = 0xffu;  // this lane's row: bit w = warp w evaluates its block
                     uint32_t need = nr == 32 ? FULLMASK : ((1u << nr) - 1u);
                     if (screened) {
@@ -688,7 +714,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                         bulk_copy(S.rowG[slot], A.rowg + ra, abytes, &S.full[slot]);
                         if (first) bulk_copy(S.colB[slot], A.B2 + pd.bcoff + col0, IC * 8u, &S.full[slot]);
                         StageHdr& hh = S.hdr[slot];
-                        hh.sidx = s;
+                        hh.ra = ra;
+                        hh.nr = nr;
                         hh.flags = first ? H_FIRST : 0;
                         hh.tiled = tiled ? 1 : 0;
                         // one run of consecutive needed rows at a time
@@ -720,7 +747,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 }
             }
             if (!ok) break;
-            i0 = i1; w0 = w1; a0 = a1;
+            i0 = i1; w0 = w1; a0 = a1; v0 = v1;
             i1 = i2; w1 = w2;
             i2r = i3r;
         }
@@ -802,9 +829,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
         }
         x.r0 = r0;
         x.rend = r0 + hs.d.rows;
-        x.ra = r0 + hs.sidx * SR;
-        x.marks = S.marks[warp];
-        x.nr = min(SR, hs.d.rows - hs.sidx * SR);
+        x.ra = hs.ra;
+        x.nr = hs.nr;
         const bool tiled = hs.tiled != 0;
         x.rs = tiled ? TW : IC;
         x.st = S.stage[slot] + (tiled ? warp * SR * TW + lane : wc);
@@ -826,8 +852,6 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             const uint32_t live = (x.nr >= SR ? 0xffu : (1u << ((x.nr + 3) >> 2)) - 1u) & chunks_of_rows(wrows);
             const uint32_t cm = tiled ? chunk_marks<TW>(x.st, x.rA, x.bp) : chunk_marks<IC>(x.st, x.rA, x.bp);
             x.U = __reduce_or_sync(FULLMASK, cm & live);
-            if (hs.sidx < MARK_STAGES && lane == 0) S.marks[warp][hs.sidx] = (uint8_t)x.U;
-            __syncwarp();
             int r = 0;
             if (blk.gend > x.ra) {  // the block open at the end of the last stage continues here
                 const int e = min(blk.gend - x.ra, x.nr);
@@ -875,13 +899,15 @@ __global__ void __launch_bounds__(256) k_stage_masks(const EvalArgs A)
     if (A.item_active && !A.item_active[d.item]) return;
     const int tile0 = d.col0 / TW;  // a multiple of NWARPS: the item's tiles share one mask word
     uint8_t* out = const_cast<uint8_t*>(A.stage_m8) + (int64_t)d.sbase * SR;
-    for (int r = threadIdx.x; r < d.nst * SR; r += blockDim.x) {
+    for (int q = threadIdx.x; q < d.nst * SR; q += blockDim.x) {
+        const int st = q / SR, i = q % SR;
+        const int ra = A.stage_row0[d.st0 + st], re = A.stage_row0[d.st0 + st + 1];
         uint32_t m8 = 0u;
-        if (r < d.rows) {
-            const int l = A.rowg[d.r0 + r].x;
+        if (ra + i < re) {
+            const int l = A.rowg[ra + i].x;
             m8 = (A.unit_need[(int64_t)l * A.unit_words + (tile0 >> 5)] >> (tile0 & 31)) & 0xffu;
         }
-        out[r] = (uint8_t)m8;
+        out[q] = (uint8_t)m8;
     }
 }
 
@@ -891,41 +917,6 @@ void launch_stage_masks(const EvalArgs& a, cudaStream_t st)
 }
 
 // ================================================================ pass B
-// Rows [R0, R1) (stepping by `step` from R0) of a block for this lane's
-// column: re-form f and add the nonzero t_ij = s [f_ij]_+ to the fixed-point
-// row sums (integer adds: the total does not depend on their order).  Eight
-// rows' loads are issued together.
-__device__ __forceinline__ void passb_rows(const EvalArgs& A, const FxScale& fx, int R0, int R1, int step,
-                                           int prob, int colg, float s)
-{
-    const ProbDesc pd = A.probs[prob];
-    const int lcol = colg - pd.coff;
-    const bool real = lcol < pd.n;
-    const float2 b2 = real ? __ldg(A.B2 + pd.bcoff + lcol) : make_float2(0.f, 0.f);
-    const float bp = real ? bound_up(b2.x) : -INFINITY;
-    for (int R = R0; R < R1; R += step) {
-        float c[8];
-        float4 a[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int Rq = min(R + q, R1 - 1);
-            c[q] = real ? __ldg(pd.C + (int64_t)(Rq - pd.roff) * pd.ldc + lcol) : 0.f;
-            a[q] = __ldg(A.rowA + Rq);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            if (R + q >= R1) break;  // (uniform)
-            unsigned long long tq = 0ull;
-            if (s > 0.f && maybe_pos(a[q].z, c[q], bp)) {
-                float fh, fl;
-                f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
-                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), fx.to_rf);
-            }
-            red_row(A.rowfx + R + q, tq);
-        }
-    }
-}
-
 // The deferred blocks, one CTA per list entry at a time: warp w takes rows
 // [gstart + 8 (w + NW t), + 8) for t = 0, 1, ...
 constexpr int PASSB_THREADS = 256;

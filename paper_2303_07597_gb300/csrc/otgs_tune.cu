@@ -1,14 +1,15 @@
 // otgs_tune.cu -- choice of the work decomposition by measurement.
 //
-// The plan's two shape parameters decide how the (class group x target
-// column) blocks of Sec. 2.3 are tiled over the evaluation kernel's CTAs:
-// the panel height (rows of whole groups per work item, times 256 columns)
-// and the split height (groups taller than it are cut into pieces summed by
-// several CTAs).  Which pair is fastest depends on the distribution of group
-// sizes and on the number of columns: short groups want tall panels (fewer,
-// larger items), a few huge groups want pieces (no single item sets the
-// kernel's duration).  The tuner times dense evaluations of the handle's own
-// problems at a given point for each candidate pair, keeps the fastest, and
+// The plan's shape parameters decide how the (class group x target column)
+// blocks of Sec. 2.3 are tiled over the evaluation kernel's CTAs: the panel
+// height (rows of whole groups per work item, times 256 columns), the split
+// height (groups taller than it are cut into pieces summed by several CTAs)
+// and the stage fill (stages end early rather than cut a short group).
+// Which shape is fastest depends on the distribution of group sizes and on
+// the number of columns: short groups want tall panels (fewer, larger
+// items), a few huge groups want pieces (no single item sets the kernel's
+// duration).  The tuner times dense evaluations of the handle's own problems
+// at a given point for each candidate shape, keeps the fastest, and
 // remembers it for the process under a key made of the group-size histogram
 // and the column and row counts, so handles of the same shape skip the
 // measurement.
@@ -61,33 +62,36 @@ using namespace otgs;
 
 extern "C" {
 
-int ot_gs_set_plan(ot_gs* hh, int32_t panel_rows, int32_t split_rows)
+int ot_gs_set_plan(ot_gs* hh, int32_t panel_rows, int32_t split_rows, int32_t stage_fill)
 {
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
     if ((panel_rows != 0 && (panel_rows < 32 || panel_rows > 4096)) ||
-        (split_rows != 0 && (split_rows < 64 || split_rows > 8192))) {
-        h->fail(OTGS_EINVAL, "need panel_rows in [32, 4096] and split_rows in [64, 8192] (or 0: default)");
+        (split_rows != 0 && (split_rows < 64 || split_rows > 8192)) || stage_fill < 0 || stage_fill > 32) {
+        h->fail(OTGS_EINVAL,
+                "need panel_rows in [32, 4096], split_rows in [64, 8192] (or 0: default), stage_fill in [0, 32]");
         return OTGS_EINVAL;
     }
     PlanParams pp;
     pp.panel_rows = panel_rows;
     pp.split_rows = split_rows;
+    pp.stage_fill = stage_fill;
     return h->setup_plan(pp) ? OTGS_OK : h->last_code;
 }
 
-int ot_gs_get_plan(const ot_gs* hh, int32_t* panel_rows, int32_t* split_rows, int64_t* n_items)
+int ot_gs_get_plan(const ot_gs* hh, int32_t* panel_rows, int32_t* split_rows, int32_t* stage_fill, int64_t* n_items)
 {
     if (!hh) return OTGS_EINVAL;
     const Handle* h = reinterpret_cast<const Handle*>(hh);
     if (panel_rows) *panel_rows = h->hp.panel_height;
     if (split_rows) *split_rows = h->hp.split_height;
+    if (stage_fill) *stage_fill = h->hp.stage_fill;
     if (n_items) *n_items = h->hp.nitems();
     return OTGS_OK;
 }
 
 int ot_gs_autotune(ot_gs* hh, const double* alpha, const double* beta, int32_t evals, int32_t* panel_rows,
-                   int32_t* split_rows, double* best_ms)
+                   int32_t* split_rows, int32_t* stage_fill, double* best_ms)
 {
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
@@ -118,18 +122,21 @@ int ot_gs_autotune(ot_gs* hh, const double* alpha, const double* beta, int32_t e
         }
         const int panels[] = {32, 64, 128, 256, 512, 1024};
         const int splits[] = {128, 256, 512, 1024};
+        const int fills[] = {0, 16};
         best_t = INFINITY;
         bool ok = true;
         for (int pr : panels) {
-            for (int sr : splits) {
+            for (int q = 0; q < 8; q++) {
+                const int sr = splits[q % 4], sf = fills[q / 4];
                 if (sr < pr / 2) continue;  // pieces much shorter than a panel only add items
                 PlanParams pp;
                 pp.panel_rows = pr;
                 pp.split_rows = sr;
+                pp.stage_fill = sf;
                 if (!h->setup_plan(pp)) { ok = false; break; }
                 ok = h->eval_batch(alpha, beta, D, nullptr);  // warm-up
                 ok = ok && h->ck(cudaEventRecord(e0, h->st), "cudaEventRecord");
-                for (int q = 0; ok && q < evals; q++) ok = h->eval_batch(alpha, beta, D, nullptr);
+                for (int e = 0; ok && e < evals; e++) ok = h->eval_batch(alpha, beta, D, nullptr);
                 ok = ok && h->ck(cudaEventRecord(e1, h->st), "cudaEventRecord") &&
                      h->ck(cudaEventSynchronize(e1), "cudaEventSynchronize");
                 float ms = 0.f;
@@ -152,6 +159,7 @@ int ot_gs_autotune(ot_gs* hh, const double* alpha, const double* beta, int32_t e
     if (!h->setup_plan(best)) return h->last_code;
     if (panel_rows) *panel_rows = h->hp.panel_height;
     if (split_rows) *split_rows = h->hp.split_height;
+    if (stage_fill) *stage_fill = h->hp.stage_fill;
     if (best_ms) *best_ms = cached ? 0.0 : best_t;
     return OTGS_OK;
 }

@@ -35,34 +35,60 @@ def panel_height(m, n):
 
 
 SPLIT_ROWS = 256
+def panel_stages(groups, piece, fill=0):
+    """Stages of a panel whose rows are the given groups (sizes, in order):
+    runs of at most 32 rows; with fill > 0 a run ends early at the start of a
+    group of at most 32 rows that would straddle its end when that keeps at
+    least fill rows (never inside a piece of a split group)."""
+    rows = int(sum(groups))
+    if piece or fill == 0:
+        return -(-rows // STAGE_ROWS)
+    starts = np.concatenate([[0], np.cumsum(groups)])
+    ra, cnt = 0, 0
+    while ra < rows:
+        cnt += 1
+        nr = min(STAGE_ROWS, rows - ra)
+        if ra + nr < rows:
+            k = int(np.searchsorted(starts, ra + nr - 1, side="right")) - 1  # group of row ra + nr - 1
+            gs, ge = int(starts[k]), int(starts[k + 1])
+            if ge > ra + nr and ge - gs <= STAGE_ROWS and gs > ra and gs - ra >= fill:
+                nr = gs - ra
+        ra += nr
+    return cnt
 
 
-def expected_plan(sizes, n):
+def plan_panels(sizes, panel_rows, split_rows):
     """Panels by the packing rule of the plan (consecutive non-empty groups up
-    to the panel height; a group of more than 256 rows cut into pieces of 256
-    rows, each a panel), items and stages from them."""
-    PANEL_ROWS = panel_height(int(np.sum(sizes)), n)
-    panels, cur = [], 0
+    to the panel height; a group of more than split_rows rows cut into pieces
+    of split_rows rows, each a panel) as (group sizes, is a piece)."""
+    panels, cur = [], []
     for g in sizes:
         if g == 0:
             continue
-        if g > SPLIT_ROWS:
+        if g > split_rows:
             if cur:
-                panels.append(cur)
-                cur = 0
-            panels += [min(SPLIT_ROWS, g - k) for k in range(0, g, SPLIT_ROWS)]
+                panels.append((cur, False))
+                cur = []
+            panels += [([min(split_rows, g - k)], True) for k in range(0, g, split_rows)]
             continue
-        if cur and cur + g > PANEL_ROWS:
-            panels.append(cur)
-            cur = 0
-        cur += g
-        if cur >= PANEL_ROWS:
-            panels.append(cur)
-            cur = 0
+        if cur and sum(cur) + g > panel_rows:
+            panels.append((cur, False))
+            cur = []
+        cur = cur + [g]
+        if sum(cur) >= panel_rows:
+            panels.append((cur, False))
+            cur = []
     if cur:
-        panels.append(cur)
+        panels.append((cur, False))
+    return panels
+
+
+def expected_plan(sizes, n):
+    """Panels, items and stages of one problem."""
+    panels = plan_panels(sizes, panel_height(int(np.sum(sizes)), n), SPLIT_ROWS)
     nch = -(-n // ITEM_COLS)
-    return len(panels), len(panels) * nch, sum(-(-r // STAGE_ROWS) for r in panels) * nch, panels
+    rows = [int(sum(g)) for g, _ in panels]
+    return len(panels), len(panels) * nch, sum(panel_stages(g, pc) for g, pc in panels) * nch, rows
 
 
 @pytest.mark.parametrize("sizes,n", [
@@ -99,30 +125,7 @@ def test_plan_rejects_bad_labels():
         pk.ot_gs_plan_info(np.array([0, 3, 1], np.int32), 5, 3)
 
 
-def expected_panels(sizes, panel_rows, split_rows):
-    panels, cur = [], 0
-    for g in sizes:
-        if g == 0:
-            continue
-        if g > split_rows:
-            if cur:
-                panels.append(cur)
-                cur = 0
-            panels += [min(split_rows, g - k) for k in range(0, g, split_rows)]
-            continue
-        if cur and cur + g > panel_rows:
-            panels.append(cur)
-            cur = 0
-        cur += g
-        if cur >= panel_rows:
-            panels.append(cur)
-            cur = 0
-    if cur:
-        panels.append(cur)
-    return panels
-
-
-def expected_plan_batch(sizes_list, ns, panel_rows=0, split_rows=0):
+def expected_plan_batch(sizes_list, ns, panel_rows=0, split_rows=0, fill=0):
     """A batch is planned problem by problem (a panel never holds rows of
     two problems, an item never pairs rows with another problem's columns);
     the default panel height comes from the batch's total rows and columns."""
@@ -131,17 +134,18 @@ def expected_plan_batch(sizes_list, ns, panel_rows=0, split_rows=0):
     sr = split_rows or SPLIT_ROWS
     n_panels = n_items = n_stages = 0
     for sizes, n in zip(sizes_list, ns):
-        panels = expected_panels(sizes, pr, sr)
-        assert sum(panels) == int(np.sum(sizes))
+        panels = plan_panels(sizes, pr, sr)
+        assert sum(int(sum(g)) for g, _ in panels) == int(np.sum(sizes))
         nch = -(-n // ITEM_COLS)
         n_panels += len(panels)
         n_items += len(panels) * nch
-        n_stages += sum(-(-r // STAGE_ROWS) for r in panels) * nch
+        n_stages += sum(panel_stages(g, pc, fill) for g, pc in panels) * nch
     return n_panels, n_items, n_stages
 
 
-@pytest.mark.parametrize("pr,sr", [(0, 0), (32, 128), (128, 256), (512, 1024), (1024, 64)])
-def test_batch_plan_is_per_problem(pr, sr):
+@pytest.mark.parametrize("pr,sr,sf", [(0, 0, 0), (32, 128, 0), (128, 256, 16), (512, 1024, 0), (1024, 64, 16),
+                                      (512, 256, 1), (512, 256, 31)])
+def test_batch_plan_is_per_problem(pr, sr, sf):
     rng = np.random.default_rng(5)
     sizes_list, ns = [], []
     for k in range(9):
@@ -153,8 +157,8 @@ def test_batch_plan_is_per_problem(pr, sr):
         sizes_list.append(sizes)
         ns.append(int(rng.integers(1, 700)))
     labels = [synth.labels_from_sizes(s) for s in sizes_list]
-    info = pk.ot_gs_plan_info_batch(labels, ns, [len(s) for s in sizes_list], pr, sr)
-    assert (info["n_panels"], info["n_items"], info["n_stages"]) == expected_plan_batch(sizes_list, ns, pr, sr)
+    info = pk.ot_gs_plan_info_batch(labels, ns, [len(s) for s in sizes_list], pr, sr, sf)
+    assert (info["n_panels"], info["n_items"], info["n_stages"]) == expected_plan_batch(sizes_list, ns, pr, sr, sf)
 
 
 def test_batch_of_one_plans_like_one_problem():

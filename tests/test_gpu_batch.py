@@ -74,12 +74,14 @@ def test_batch_plans_agree():
     D0, g0 = B.grad(at, bt)
     scale = torch.maximum(g0.abs(), torch.from_numpy(np.concatenate([p.a for p in problems] +
                                                                      [p.b for p in problems])).to(DEV))
-    for pr, sr in [(32, 256), (1024, 256), (32, 64), (64, 128), (512, 1024)]:
-        B.set_plan(pr, sr)
-        assert B.plan()["panel_rows"] == pr and B.plan()["split_rows"] == sr
+    for pr, sr, sf in [(32, 256, 0), (1024, 256, 0), (32, 64, 0), (64, 128, 16), (512, 1024, 0), (256, 256, 16),
+                       (512, 256, 1)]:
+        B.set_plan(pr, sr, sf)
+        pl = B.plan()
+        assert (pl["panel_rows"], pl["split_rows"], pl["stage_fill"]) == (pr, sr, sf)
         D1, g1 = B.grad(at, bt)
         if sr == 256:
-            assert torch.equal(g0[:B.m], g1[:B.m]), (pr, sr)
+            assert torch.equal(g0[:B.m], g1[:B.m]), (pr, sr, sf)
         assert ((g1 - g0).abs() / scale).max().item() <= 1e-11, (pr, sr)
         assert torch.allclose(D0, D1, rtol=1e-12, atol=0), (pr, sr, (D0 - D1).abs().max().item())
 
@@ -92,9 +94,11 @@ def test_autotune_picks_a_shape_and_caches():
     at, bt = torch.from_numpy(np.concatenate(al)).to(DEV), torch.from_numpy(np.concatenate(be)).to(DEV)
     r = B.autotune(at, bt, evals=2)
     assert r["best_ms"] > 0
-    assert B.plan()["panel_rows"] == r["panel_rows"] and B.plan()["split_rows"] == r["split_rows"]
+    pl = B.plan()
+    assert (pl["panel_rows"], pl["split_rows"], pl["stage_fill"]) == (r["panel_rows"], r["split_rows"], r["stage_fill"])
     r2 = B.autotune(at, bt, evals=2)
-    assert r2["best_ms"] == 0.0 and (r2["panel_rows"], r2["split_rows"]) == (r["panel_rows"], r["split_rows"])
+    assert r2["best_ms"] == 0.0
+    assert (r2["panel_rows"], r2["split_rows"], r2["stage_fill"]) == (r["panel_rows"], r["split_rows"], r["stage_fill"])
     check_batch(B, problems, 1.0, 0.1, al, be)
 
 
