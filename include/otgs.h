@@ -283,6 +283,17 @@ OTGS_API int ot_gs_batch_grad(ot_gs *h, const double *alpha, const double *beta,
  */
 OTGS_API int ot_gs_batch_solve(ot_gs *h, double tol, int32_t maxit, const double *target_D, double target_rtol);
 
+/*
+ * Best common shift of each problem's alpha: alpha_k += k_k, k_k the
+ * maximiser of the concave D_k(alpha_k + k 1, beta_k) (D is unchanged by
+ * alpha + k, beta - k, so this is the best point on that line through a
+ * predicted start).  A bracket is doubled from [-1, 1] until it holds the
+ * maximiser, then halved; each of the `iters` (1..200) steps is one batch
+ * evaluation.  alpha: device FP64, concatenated layout, updated in place;
+ * beta: device FP64.  Synchronises.
+ */
+OTGS_API int ot_gs_batch_shift(ot_gs *h, double *alpha, const double *beta, int32_t iters);
+
 /* Set the batch iterate used by the next ot_gs_batch_solve (warm start):
  * device FP64, concatenated layout.  Clears each problem's L-BFGS memory. */
 OTGS_API int ot_gs_batch_set_state(ot_gs *h, const double *alpha, const double *beta);
@@ -337,6 +348,56 @@ OTGS_API int ot_gs_autotune_clear_cache(void);
 OTGS_API int ot_gs_plan_info_batch(int32_t nprob, const int32_t *const *labels_host, const int64_t *m,
                                    const int64_t *n, const int32_t *L, int32_t panel_rows, int32_t split_rows,
                                    int32_t stage_fill, int64_t *n_panels, int64_t *n_items, int64_t *n_stages);
+
+/* ------------------------------------------------------------------------
+ * Learned warm start (no counterpart in the paper).  A 3-layer perceptron
+ * maps per-sample features of a problem to initial duals; the zero start
+ * stays the fallback and the judge (the solve from a warm start must reach
+ * the same objective).  Network, for in_dim K and width H (multiples of 16):
+ *   Z1 = q(X) q(W1)^T + b1, A1 = relu(Z1), Z2 = q(A1) q(W2)^T + b2,
+ *   A2 = relu(Z2), y = q(A2) q(w3) + b3,
+ * q = rounding to bfloat16 (the tensor-core operands; FP32 accumulation).
+ * Parameters are FP32 master copies in one flat array:
+ *   [W1 (H x K, row-major), b1 (H), W2 (H x H), b2 (H), w3 (H), b3 (1)].
+ * Training minimises mean (y - t)^2 with Adam.
+ * ------------------------------------------------------------------------ */
+typedef struct ot_gs_mlp ot_gs_mlp;
+
+/* New network with He-uniform weights from SplitMix64(seed) (biases 0) and
+ * buffers for batches of up to max_batch samples; work goes to `stream`.
+ * Synchronises once.  Errors: OTGS_EINVAL, OTGS_ENOMEM, OTGS_ECUDA. */
+OTGS_API int ot_gs_mlp_create(ot_gs_mlp **h, int32_t in_dim, int32_t width, int64_t max_batch, uint64_t seed,
+                              void *stream);
+OTGS_API int ot_gs_mlp_destroy(ot_gs_mlp *h);
+OTGS_API int ot_gs_mlp_num_params(const ot_gs_mlp *h, int64_t *n); /* host out */
+/* Copy the flat FP32 parameters in (device; clears Adam's moments and step)
+ * or out (device). */
+OTGS_API int ot_gs_mlp_set_params(ot_gs_mlp *h, const float *p);
+OTGS_API int ot_gs_mlp_get_params(ot_gs_mlp *h, float *p);
+/* y[b] for the B rows of X (device FP32, B x in_dim, row-major); 0 < B <= max_batch. */
+OTGS_API int ot_gs_mlp_forward(ot_gs_mlp *h, const float *X, int64_t B, float *y);
+/* Loss and gradient at targets t (device FP32 [B]): loss (device FP32 scalar,
+ * may be NULL) = mean (y - t)^2; grad (device FP32 flat, may be NULL) receives
+ * the gradient, which is also kept for ot_gs_mlp_adam. */
+OTGS_API int ot_gs_mlp_grad(ot_gs_mlp *h, const float *X, const float *t, int64_t B, float *loss, float *grad);
+/* One Adam step (Kingma & Ba) with the gradient of the last ot_gs_mlp_grad. */
+OTGS_API int ot_gs_mlp_adam(ot_gs_mlp *h, float lr, float beta1, float beta2, float eps);
+/*
+ * Input features of one problem: out (device FP32, (m + n) x in_dim) gets one
+ * row per source sample, then one per target sample:
+ *   source i of class l: [0, min_j c_ij, mean_j c_ij, sm_0.02, sm_0.1, g_l / m, x_i, mu_l]
+ *   target j:            [1, min_i c_ij, mean_i c_ij, sm_0.02, sm_0.1, g_k / m, y_j, mu_k]
+ * and zeros up to in_dim (>= 6 + 2 d).  mu_l = mean source feature of class l,
+ * g_l its size, k the non-empty class whose mean is nearest to y_j (FP32
+ * squared distance, terms in index order, ties to the lower class), sm_tau(v)
+ * = -tau log mean exp(-v / tau).  C: device FP32 m x n (row stride ldc); XS:
+ * device FP32 m x d; XT: device FP32 n x d; labels: device int32 [m] in [0, L).
+ */
+OTGS_API int ot_gs_mlp_features(const float *C, int64_t ldc, int64_t m, int64_t n, const float *XS, const float *XT,
+                                int32_t d, const int32_t *labels, int32_t L, int32_t in_dim, float *out,
+                                void *stream);
+/* Message of the last failure on h (NULL: of the last failed create or features call). */
+OTGS_API const char *ot_gs_mlp_last_error(const ot_gs_mlp *h);
 
 /*
  * Allocation-free dense evaluation.  The paper has no counterpart: this entry

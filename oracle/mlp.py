@@ -17,8 +17,8 @@ multiple of 16 by the caller's choice of ``kpad``):
   softmin_0.1, g_k / m, y_j (d), mu_k (d)]
 
 where mu_l is the mean of class l's source features, g_l its size, k the
-class whose mean is nearest to y_j (squared distance, decided in FP32, ties
-to the lower class), and softmin_tau over values v is
+class whose mean is nearest to y_j (squared distance in FP32, terms added
+in index order; ties to the lower class), and softmin_tau over values v is
 ``-tau log(mean exp(-v / tau))``.
 
 Network (width H): Z1 = q(X) q(W1)^T + b1, A1 = relu(Z1),
@@ -78,14 +78,18 @@ def features(C, XS, XT, labels, L, kpad=None):
     for l in range(L):
         if g[l] > 0:
             mu[l] = XS[lab == l].sum(0) / g[l]
-    # nearest class mean of each target sample, decided in FP32 (non-empty classes)
+    # nearest class mean of each target sample, decided in FP32: the squared
+    # differences of the single-precision values added in index order
     mu32 = mu.astype(np.float32)
     xt32 = np.asarray(XT, dtype=np.float32)
     dist = np.full((n, L), np.inf, dtype=np.float32)
     for l in range(L):
         if g[l] > 0:
-            diff = xt32 - mu32[l][None, :]
-            dist[:, l] = np.sum(diff * diff, axis=1, dtype=np.float32)
+            acc = np.zeros(n, dtype=np.float32)
+            for c in range(d):
+                df = xt32[:, c] - mu32[l, c]
+                acc = acc + df * df
+            dist[:, l] = acc
     near = np.argmin(dist, axis=1)
     S = np.zeros((m, kp))
     S[:, 0] = 0.0

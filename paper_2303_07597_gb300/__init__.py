@@ -93,12 +93,23 @@ def lib():
         "ot_gs_batch_grad": ([P, P, P, P, P], ctypes.c_int),
         "ot_gs_batch_solve": ([P, dbl, i32, P, dbl], ctypes.c_int),
         "ot_gs_batch_set_state": ([P, P, P], ctypes.c_int),
+        "ot_gs_batch_shift": ([P, P, P, i32], ctypes.c_int),
         "ot_gs_batch_result": ([P, P, P, P, P, P, P, P, P], ctypes.c_int),
         "ot_gs_set_plan": ([P, i32, i32, i32], ctypes.c_int),
         "ot_gs_get_plan": ([P, P, P, P, P], ctypes.c_int),
         "ot_gs_autotune": ([P, P, P, i32, P, P, P, P], ctypes.c_int),
         "ot_gs_autotune_clear_cache": ([], ctypes.c_int),
         "ot_gs_plan_info_batch": ([i32, P, P, P, P, i32, i32, i32, P, P, P], ctypes.c_int),
+        "ot_gs_mlp_create": ([ctypes.POINTER(P), i32, i32, i64, ctypes.c_uint64, P], ctypes.c_int),
+        "ot_gs_mlp_destroy": ([P], ctypes.c_int),
+        "ot_gs_mlp_num_params": ([P, P], ctypes.c_int),
+        "ot_gs_mlp_set_params": ([P, P], ctypes.c_int),
+        "ot_gs_mlp_get_params": ([P, P], ctypes.c_int),
+        "ot_gs_mlp_forward": ([P, P, i64, P], ctypes.c_int),
+        "ot_gs_mlp_grad": ([P, P, P, i64, P, P], ctypes.c_int),
+        "ot_gs_mlp_adam": ([P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
+        "ot_gs_mlp_features": ([P, i64, i64, i64, P, P, i32, P, i32, i32, P, P], ctypes.c_int),
+        "ot_gs_mlp_last_error": ([P], ctypes.c_char_p),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -377,6 +388,12 @@ def ot_gs_batch_set_state(h, alpha, beta):
                                                  _ptr(beta, torch.float64, name="beta")))
 
 
+def ot_gs_batch_shift(h, alpha, beta, iters=40):
+    import torch
+    return _check(h, lib().ot_gs_batch_shift(h, _ptr(alpha, torch.float64, name="alpha"),
+                                             _ptr(beta, torch.float64, name="beta"), int(iters)))
+
+
 def ot_gs_batch_result(h, nprob, alpha=None, beta=None):
     """Per-problem results of the last batch solve as numpy arrays (and the
     iterate into alpha, beta when given)."""
@@ -548,6 +565,11 @@ class GroupSparseOTBatch:
     def set_state(self, alpha, beta):
         ot_gs_batch_set_state(self.h, alpha, beta)
 
+    def shift(self, alpha, beta, iters=40):
+        """Best common shift of each problem's alpha, in place (see ot_gs_batch_shift)."""
+        ot_gs_batch_shift(self.h, alpha, beta, iters)
+        return alpha
+
     def result(self, with_iterate=True):
         import torch
         al = be = None
@@ -575,3 +597,102 @@ class GroupSparseOTBatch:
             return vec[self.row_off[k]:self.row_off[k + 1]]
         base = self.m if vec.numel() == self.m + self.n else 0
         return vec[base + self.col_off[k]:base + self.col_off[k + 1]]
+
+
+# ------------------------------------------------------------ warm start
+class MLPError(OTGSError):
+    pass
+
+
+def _mlp_check(h, rc):
+    if rc != OTGS_OK:
+        msg = lib().ot_gs_mlp_last_error(h)
+        raise MLPError(rc, msg.decode() if msg else "")
+    return rc
+
+
+def mlp_features(C, XS, XT, labels, L, in_dim, out=None, stream=None):
+    """Input features of one problem (device tensors): (m + n, in_dim) FP32,
+    source rows then target columns (see ot_gs_mlp_features)."""
+    import torch
+    m, n = C.shape
+    d = XS.shape[1]
+    if C.stride(1) != 1 or C.dtype != torch.float32:
+        raise ValueError("C must be float32 with unit column stride")
+    if out is None:
+        out = torch.empty(m + n, in_dim, dtype=torch.float32, device=C.device)
+    rc = lib().ot_gs_mlp_features(ctypes.c_void_p(C.data_ptr()), C.stride(0), m, n,
+                                  _ptr(XS, torch.float32, m * d, "XS"), _ptr(XT, torch.float32, n * d, "XT"),
+                                  d, _ptr(labels, torch.int32, m, "labels"), int(L), int(in_dim),
+                                  _ptr(out, torch.float32, (m + n) * in_dim, "out"), _stream_ptr(stream))
+    _mlp_check(None, rc)
+    return out
+
+
+class WarmStartMLP:
+    """The warm-start network on the current CUDA device (C ABI handle)."""
+
+    def __init__(self, in_dim, width=256, max_batch=8192, seed=0, stream=None):
+        import torch
+        self.in_dim, self.width, self.max_batch = int(in_dim), int(width), int(max_batch)
+        h = ctypes.c_void_p()
+        rc = lib().ot_gs_mlp_create(ctypes.byref(h), self.in_dim, self.width, self.max_batch, int(seed),
+                                    _stream_ptr(stream))
+        _mlp_check(None, rc)
+        self.h = h
+        n = ctypes.c_int64()
+        _mlp_check(h, lib().ot_gs_mlp_num_params(h, ctypes.byref(n)))
+        self.num_params = n.value
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lib().ot_gs_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import torch
+        p = torch.empty(self.num_params, dtype=torch.float32, device=self.device)
+        _mlp_check(self.h, lib().ot_gs_mlp_get_params(self.h, _ptr(p, torch.float32, self.num_params, "p")))
+        return p
+
+    def set_params(self, p):
+        import torch
+        _mlp_check(self.h, lib().ot_gs_mlp_set_params(self.h, _ptr(p, torch.float32, self.num_params, "p")))
+
+    def forward(self, X, out=None):
+        """Predictions for the rows of X (in chunks of max_batch)."""
+        import torch
+        B = X.shape[0]
+        if out is None:
+            out = torch.empty(B, dtype=torch.float32, device=X.device)
+        for s in range(0, B, self.max_batch):
+            e = min(B, s + self.max_batch)
+            xs, ys = X[s:e], out[s:e]
+            _mlp_check(self.h, lib().ot_gs_mlp_forward(self.h, _ptr(xs, torch.float32, (e - s) * self.in_dim, "X"),
+                                                       e - s, _ptr(ys, torch.float32, e - s, "y")))
+        return out
+
+    def grad(self, X, t, want_grad=False):
+        import torch
+        B = X.shape[0]
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+        g = torch.empty(self.num_params, dtype=torch.float32, device=X.device) if want_grad else None
+        _mlp_check(self.h, lib().ot_gs_mlp_grad(self.h, _ptr(X, torch.float32, B * self.in_dim, "X"),
+                                                _ptr(t, torch.float32, B, "t"), B, _ptr(loss, torch.float32, 1, "loss"),
+                                                _ptr(g, torch.float32, self.num_params, "grad")))
+        return loss, g
+
+    def adam(self, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        _mlp_check(self.h, lib().ot_gs_mlp_adam(self.h, float(lr), float(beta1), float(beta2), float(eps)))
+
+    def train_step(self, X, t, lr):
+        loss, _ = self.grad(X, t)
+        self.adam(lr)
+        return loss

@@ -591,6 +591,69 @@ __global__ void k_bscatter(const BProb* __restrict__ P, const int32_t* __restric
     }
 }
 
+// ------------------------------------------------------- shift search
+// D(alpha + k 1, beta) is concave in k with derivative 1' grad_alpha D =
+// sum a - sum T: per problem, a bracket [lo, hi] of the maximiser is grown
+// (doubling) until the derivative is > 0 at lo and < 0 at hi, then halved.
+struct ShiftState {
+    double lo, hi, x;
+    int lo_ok, hi_ok;
+};
+
+__global__ void __launch_bounds__(BT) k_shift_point(const BProb* __restrict__ P, ShiftState* S,
+                                                    const double* __restrict__ alpha, double* work, int first)
+{
+    __shared__ double xs;
+    const int k = blockIdx.x;
+    const BProb p = P[k];
+    if (threadIdx.x == 0) {
+        ShiftState& s = S[k];
+        if (first) {
+            s.lo = -1.0;
+            s.hi = 1.0;
+            s.lo_ok = 0;
+            s.hi_ok = 0;
+        }
+        s.x = !s.hi_ok ? s.hi : (!s.lo_ok ? s.lo : 0.5 * (s.lo + s.hi));
+        xs = s.x;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < p.m; e += BT) work[p.roff + e] = alpha[p.roff + e] + xs;
+}
+
+__global__ void __launch_bounds__(BT) k_shift_update(const BProb* __restrict__ P, ShiftState* S,
+                                                     const double* __restrict__ grad)
+{
+    __shared__ double sh[BW], tot[1];
+    const int k = blockIdx.x;
+    const BProb p = P[k];
+    double v[1] = {0.0};
+    for (int e = threadIdx.x; e < p.m; e += BT) v[0] += grad[p.roff + e];  // caller layout: rows of k contiguous
+    cta_sum<1>(v, sh, tot);
+    if (threadIdx.x != 0) return;
+    ShiftState& s = S[k];
+    const bool up = v[0] > 0.0;  // the maximiser lies above x
+    if (!s.hi_ok) {
+        if (up) { s.lo = s.hi; s.lo_ok = 1; s.hi *= 2.0; }
+        else s.hi_ok = 1;
+    } else if (!s.lo_ok) {
+        if (!up) { s.hi = s.lo; s.lo *= 2.0; }
+        else s.lo_ok = 1;
+    } else if (up) {
+        s.lo = s.x;
+    } else {
+        s.hi = s.x;
+    }
+}
+
+__global__ void __launch_bounds__(BT) k_shift_apply(const BProb* __restrict__ P, const ShiftState* S, double* alpha)
+{
+    const BProb p = P[blockIdx.x];
+    const ShiftState s = S[blockIdx.x];
+    const double x = (s.lo_ok && s.hi_ok) ? 0.5 * (s.lo + s.hi) : s.x;
+    for (int e = threadIdx.x; e < p.m; e += BT) alpha[p.roff + e] += x;
+}
+
 // ----------------------------------------------------------------- host
 static bool batch_init(Handle* h)
 {
@@ -853,6 +916,41 @@ int ot_gs_batch_solve(ot_gs* hh, double tol, int32_t maxit, const double* target
         return OTGS_EINVAL;
     }
     return batch_solve(h, tol, maxit, target_D, target_D ? target_rtol : 0.0);
+}
+
+int ot_gs_batch_shift(ot_gs* hh, double* alpha, const double* beta, int32_t iters)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!alpha || !beta || iters < 1 || iters > 200) {
+        h->fail(OTGS_EINVAL, "need alpha, beta and 1 <= iters <= 200");
+        return OTGS_EINVAL;
+    }
+    cudaStream_t st = h->st;
+    ShiftState* S = (ShiftState*)h->dalloc(sizeof(ShiftState) * (size_t)h->nprob, "shift search");
+    double* work = (double*)h->dalloc(sizeof(double) * (size_t)(2 * h->m + h->n) + sizeof(double) * h->nprob,
+                                      "shift search");
+    if (!S || !work) return h->last_code;
+    double* grad = work + h->m;
+    double* D = grad + h->m + h->n;
+    // (alpha is in the caller's layout: the rows of problem k are entries [roff_k, roff_k + m_k))
+    for (int it = 0; it < iters; it++) {
+        k_shift_point<<<h->nprob, BT, 0, st>>>(h->bprob, S, alpha, work, it == 0);
+        if (!h->eval_batch(work, beta, D, grad)) return h->last_code;
+        k_shift_update<<<h->nprob, BT, 0, st>>>(h->bprob, S, grad);
+    }
+    k_shift_apply<<<h->nprob, BT, 0, st>>>(h->bprob, S, alpha);
+    if (!h->ck(cudaStreamSynchronize(st), "shift search")) return OTGS_ECUDA;
+    // the scratch goes back (allocated per call: this runs once per warm start)
+    for (void* q : {(void*)S, (void*)work}) {
+        for (size_t i = 0; i < h->allocs.size(); i++)
+            if (h->allocs[i] == q) {
+                h->allocs.erase(h->allocs.begin() + (long)i);
+                break;
+            }
+        cudaFree(q);
+    }
+    return OTGS_OK;
 }
 
 int ot_gs_batch_set_state(ot_gs* hh, const double* alpha, const double* beta)

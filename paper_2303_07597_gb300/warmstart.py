@@ -1,0 +1,123 @@
+"""Learned warm start for the batched solver (no counterpart in the paper).
+
+The network (:class:`WarmStartMLP`, the library's own kernels) maps each
+sample's features (``mlp_features``: cost statistics, its features and its
+class-mean embedding) to its dual variable.  Targets are the solver's own
+solutions with the gauge fixed by mean(alpha) = mean(beta) (D is invariant
+under alpha + k, beta - k).  At solve time the prediction is used only when
+it is better than the zero start (D above D(0, 0) = 0); otherwise the solve
+starts from zero, so the zero-start solver stays the fallback.  Either way
+the solve runs to the same stopping rule and reaches the same objective.
+
+Tensors are PyTorch CUDA tensors (plumbing); features, network and solves
+run in the library's kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import GroupSparseOTBatch, WarmStartMLP, mlp_features
+
+NSTAT = 6
+
+
+def in_dim_for(d: int) -> int:
+    """Feature width for d-dimensional sample features, rounded up to 16."""
+    return (NSTAT + 2 * d + 15) // 16 * 16
+
+
+def gauge_fix(alpha, beta):
+    """alpha + k, beta - k with mean(alpha) = mean(beta) (tensors)."""
+    k = 0.5 * (beta.mean() - alpha.mean())
+    return alpha + k, beta - k
+
+
+def problem_features(p, device, in_dim):
+    """Features of a synth.Problem (with XS, XT) on the device: (m + n, in_dim)."""
+    import torch
+    C = torch.from_numpy(p.C).to(device)
+    XS = torch.from_numpy(np.ascontiguousarray(p.XS, dtype=np.float32)).to(device)
+    XT = torch.from_numpy(np.ascontiguousarray(p.XT, dtype=np.float32)).to(device)
+    lab = torch.from_numpy(p.labels).to(device)
+    return mlp_features(C, XS, XT, lab, p.L, in_dim)
+
+
+def batch_of(problems, device, gamma, mu):
+    import torch
+    Cs = [torch.from_numpy(p.C).to(device) for p in problems]
+    As = [torch.from_numpy(p.a).to(device) for p in problems]
+    Bs = [torch.from_numpy(p.b).to(device) for p in problems]
+    Ls = [torch.from_numpy(p.labels).to(device) for p in problems]
+    return GroupSparseOTBatch(Cs, As, Bs, Ls, [p.L for p in problems], gamma, mu)
+
+
+def solve_targets(problems, device, gamma, mu, tol=1e-9, maxit=20000, ftol=1e-14):
+    """Solve the problems together; returns the batch handle and per problem
+    (alpha, beta) as float64 tensors, gauge-fixed, and D."""
+    B = batch_of(problems, device, gamma, mu)
+    B.set_params(ftol=ftol)
+    B.solve(tol=tol, maxit=maxit)
+    r = B.result()
+    out = []
+    for k in range(len(problems)):
+        al, be = gauge_fix(B.split(r["alpha"], k, "alpha"), B.split(r["beta"], k, "beta"))
+        out.append((al, be))
+    return B, out, r
+
+
+def dataset(problems, targets, device, in_dim):
+    """Rows of features and their target duals for every sample of every problem."""
+    import torch
+    Xs, ts = [], []
+    for p, (al, be) in zip(problems, targets):
+        Xs.append(problem_features(p, device, in_dim))
+        ts.append(torch.cat([al, be]).float())
+    return torch.cat(Xs), torch.cat(ts)
+
+
+def train(net: WarmStartMLP, X, t, steps=2000, batch=4096, lr=1e-3, lr_end=1e-4, seed=0):
+    """Adam on random minibatches (learning rate decayed geometrically from lr
+    to lr_end); returns the loss trace (one value per 50 steps)."""
+    import torch
+    g = torch.Generator(device=X.device)
+    g.manual_seed(seed)
+    n = X.shape[0]
+    batch = min(batch, n, net.max_batch)
+    trace = []
+    for s in range(steps):
+        idx = torch.randint(0, n, (batch,), device=X.device, generator=g)
+        rate = lr * (lr_end / lr) ** (s / max(1, steps - 1))
+        loss = net.train_step(X[idx].contiguous(), t[idx].contiguous(), rate)
+        if s % 50 == 0 or s == steps - 1:
+            trace.append(float(loss.item()))
+    return trace
+
+
+def predict(net: WarmStartMLP, problems, device, in_dim):
+    """Predicted (alpha, beta) per problem, gauge-fixed, float64."""
+    out = []
+    for p in problems:
+        y = net.forward(problem_features(p, device, in_dim)).double()
+        out.append(gauge_fix(y[:p.m], y[p.m:]))
+    return out
+
+
+def warm_state(B: GroupSparseOTBatch, preds, shift_iters=40):
+    """Concatenated start point for the batch: each problem's prediction,
+    moved to the best point on its line (alpha + k, beta) by the library's
+    shift search, when its D then beats the zero start's D(0, 0) = 0; else
+    zero.  Returns (alpha, beta, used) with used[k] telling which problems
+    start warm."""
+    import torch
+    al = torch.cat([a for a, _ in preds]).contiguous()
+    be = torch.cat([b for _, b in preds]).contiguous()
+    if shift_iters > 0:
+        B.shift(al, be, shift_iters)
+    D, _ = B.grad(al, be, with_grad=False)
+    used = (D > 0.0).cpu().numpy()
+    for k in range(B.nprob):
+        if not used[k]:
+            B.split(al, k, "alpha").zero_()
+            bb = be[B.col_off[k]:B.col_off[k + 1]]
+            bb.zero_()
+    return al, be, used

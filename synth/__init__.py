@@ -170,13 +170,13 @@ def mid(seed: int = 0, m: int = 4000, n: int = 4000, L: int = 100, d: int = 256,
 
 
 def large(seed: int = 0, m: int = 20000, n: int = 20000, L: int = 1000, d: int = 512,
-          device=None, shuffle_rows: bool = False) -> Problem:
+          device=None, shuffle_rows: bool = False, keep_features: bool = False) -> Problem:
     """m=n=20000; 1000 classes with Zipf(1.1) sizes (min 2); d=512; C is
-    1.6 GB in float32."""
+    1.6 GB in float32.  Other sizes give smaller members of the same family."""
     rng = np.random.default_rng(seed)
     sizes = class_sizes_zipf(m, L, 1.1, min_size=2)
     XS, XT, lab = mixture_features(sizes, n, d, rng)
-    p = make_problem(XS, XT, lab, L, name="large", device=device)
+    p = make_problem(XS, XT, lab, L, name="large", device=device, keep_features=keep_features)
     return _maybe_shuffle(p, shuffle_rows, rng)
 
 
