@@ -335,6 +335,100 @@ def batch_report(args, dev):
     return out
 
 
+WARM = dict(m=256, L=13, d=64, gamma=1.0, mu=0.1)
+
+
+def warm_report(args, dev):
+    """Learned warm start: the network is trained (the library's kernels) on
+    solutions of args.warm_train problems of the Zipf-class generator family
+    (the large workload's generator at m = n = 256, 13 classes, d = 64), then
+    the args.warm_test held-out problems are solved together from zero and
+    from the network's prediction (features, forward pass, shift search
+    included in the warm time), both to D >= D* - 1e-6 |D*| with D* from a
+    longer run."""
+    import torch
+    import paper_2303_07597_gb300 as pk
+    from paper_2303_07597_gb300 import warmstart as ws
+    c = WARM
+    g, mu = c["gamma"], c["mu"]
+    K = ws.in_dim_for(c["d"])
+    out = {"workload": f"warm start: Zipf(1.1)-class problems m=n={c['m']}, L={c['L']}, d={c['d']}, gamma={g}, "
+                       f"mu={mu}; {args.warm_train} training / {args.warm_test} held-out problems",
+           "unit": "ms"}
+    t0 = time.perf_counter()
+    gen = lambda s: synth.large(seed=s, m=c["m"], n=c["m"], L=c["L"], d=c["d"], keep_features=True,
+                                device=str(dev))
+    train_p = [gen(1000 + s) for s in range(args.warm_train)]
+    test_p = [gen(10_000_000 + s) for s in range(args.warm_test)]
+    out["generate_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    targets = []
+    for c0 in range(0, len(train_p), 512):
+        Bt, tg, _ = ws.solve_targets(train_p[c0:c0 + 512], dev, g, mu)
+        targets += tg
+        Bt.close()
+    torch.cuda.synchronize()
+    out["solve_targets_s"] = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    X, t = ws.dataset(train_p, targets, dev, K, g)
+    del targets
+    net = pk.WarmStartMLP(K, 256, max_batch=8192, seed=1)
+    trace = ws.train(net, X, t, steps=args.warm_steps, batch=8192, lr=1e-3, lr_end=1e-4)
+    torch.cuda.synchronize()
+    out["train_s"] = time.perf_counter() - t0
+    out["train_samples"] = int(X.shape[0])
+    out["train_steps"] = args.warm_steps
+    out["train_loss_first_last"] = [trace[0], trace[-1]]
+    del X, t
+    # held out
+    B, tt, ref = ws.solve_targets(test_p, dev, g, mu)
+    Dstar = ref["D"].copy()
+    B.set_params(ftol=0.0)
+    devp = []
+    for p in test_p:
+        devp.append((torch.from_numpy(p.C).to(dev),
+                     torch.from_numpy(np.ascontiguousarray(p.XS, dtype=np.float32)).to(dev),
+                     torch.from_numpy(np.ascontiguousarray(p.XT, dtype=np.float32)).to(dev),
+                     torch.from_numpy(p.labels).to(dev)))
+    za = torch.zeros(B.m, dtype=torch.float64, device=dev)
+    zb = torch.zeros(B.n, dtype=torch.float64, device=dev)
+    B.set_state(za, zb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = B.solve(tol=0.0, maxit=20000, target_D=Dstar, target_rtol=1e-6)
+    cold_ms = (time.perf_counter() - t0) * 1000.0
+    cold = B.result(with_iterate=False)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pal, pbe = ws.predict_batch(net, devp, [p.L for p in test_p], K, g)
+    torch.cuda.synchronize()
+    tp = time.perf_counter()
+    al, be, used = ws.warm_state(B, (pal, pbe))
+    B.set_state(al, be)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    st2 = B.solve(tol=0.0, maxit=20000, target_D=Dstar, target_rtol=1e-6)
+    t2 = time.perf_counter()
+    warm = B.result(with_iterate=False)
+    rmse = []
+    for k, (ta, tb) in enumerate(tt):
+        a, b = ws.gauge_fix(B.split(pal, k, "alpha"), B.split(pbe, k, "beta"))
+        rmse.append(float(torch.cat([a - ta, b - tb]).pow(2).mean().sqrt().item()))
+    B.close()
+    net.close()
+    out.update({
+        "cold_ms": cold_ms, "cold_all_reached": bool(st == pk.OTGS_OK),
+        "cold_iters_mean": float(cold["iters"].mean()),
+        "warm_ms": (t2 - t0) * 1000.0, "warm_predict_ms": (tp - t0) * 1000.0,
+        "warm_shift_ms": (t1 - tp) * 1000.0, "warm_solve_ms": (t2 - t1) * 1000.0,
+        "warm_all_reached": bool(st2 == pk.OTGS_OK and np.all(warm["D"] >= Dstar - 1e-6 * np.abs(Dstar))),
+        "warm_iters_mean": float(warm["iters"].mean()), "warm_used_frac": float(np.mean(used)),
+        "heldout_rmse_mean": float(np.mean(rmse)),
+        "warm_vs_cold": cold_ms / ((t2 - t0) * 1000.0),
+    })
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -488,6 +582,8 @@ def run_gpu(args):
             line["solve"] = solve_report(args, dev)
         if world == 1 and not args.no_batch:
             line["batch"] = batch_report(args, dev)
+        if world == 1 and not args.no_warm:
+            line["warm_start"] = warm_report(args, dev)
         print(json.dumps(line))
     solver.close()
     if world > 1:
@@ -511,8 +607,12 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload solve measurement")
     ap.add_argument("--batch-problems", type=int, default=BATCH["nprob"])
     ap.add_argument("--batch-ref-iters", type=int, default=20000)
-    ap.add_argument("--batch-plain-sample", type=int, default=0,
+    ap.add_argument("--batch-plain-sample", type=int, default=64,
                     help="time the plain solver on this many problems and scale (0: all)")
+    ap.add_argument("--no-warm", action="store_true", help="skip the learned warm-start measurement")
+    ap.add_argument("--warm-train", type=int, default=4096)
+    ap.add_argument("--warm-test", type=int, default=512)
+    ap.add_argument("--warm-steps", type=int, default=8000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -287,9 +287,9 @@ OTGS_API int ot_gs_batch_solve(ot_gs *h, double tol, int32_t maxit, const double
  * Best common shift of each problem's alpha: alpha_k += k_k, k_k the
  * maximiser of the concave D_k(alpha_k + k 1, beta_k) (D is unchanged by
  * alpha + k, beta - k, so this is the best point on that line through a
- * predicted start).  A bracket is doubled from [-1, 1] until it holds the
- * maximiser, then halved; each of the `iters` (1..200) steps is one batch
- * evaluation.  alpha: device FP64, concatenated layout, updated in place;
+ * predicted start).  A bracket is doubled from [-1/16, 1/16] until it holds
+ * the maximiser, then halved; each of the `iters` (1..200) steps is one
+ * batch evaluation.  alpha: device FP64, concatenated layout, updated in place;
  * beta: device FP64.  Synchronises.
  */
 OTGS_API int ot_gs_batch_shift(ot_gs *h, double *alpha, const double *beta, int32_t iters);
@@ -385,17 +385,28 @@ OTGS_API int ot_gs_mlp_adam(ot_gs_mlp *h, float lr, float beta1, float beta2, fl
 /*
  * Input features of one problem: out (device FP32, (m + n) x in_dim) gets one
  * row per source sample, then one per target sample:
- *   source i of class l: [0, min_j c_ij, mean_j c_ij, sm_0.02, sm_0.1, g_l / m, x_i, mu_l]
- *   target j:            [1, min_i c_ij, mean_i c_ij, sm_0.02, sm_0.1, g_k / m, y_j, mu_k]
- * and zeros up to in_dim (>= 6 + 2 d).  mu_l = mean source feature of class l,
+ *   source i of class l: [0, min_j c_ij, mean_j c_ij, sm_0.02, sm_0.1, g_l / m, wl_0.5, wl_1, wl_2, x_i, mu_l]
+ *   target j:            [1, min_i c_ij, mean_i c_ij, sm_0.02, sm_0.1, g_k / m, wl_0.5, wl_1, wl_2, y_j, mu_k]
+ * and zeros up to in_dim (>= 9 + 2 d).  mu_l = mean source feature of class l,
  * g_l its size, k the non-empty class whose mean is nearest to y_j (FP32
  * squared distance, terms in index order, ties to the lower class), sm_tau(v)
- * = -tau log mean exp(-v / tau).  C: device FP32 m x n (row stride ldc); XS:
- * device FP32 m x d; XT: device FP32 n x d; labels: device int32 [m] in [0, L).
+ * = -tau log mean exp(-v / tau), wl_s = the level L with sum [L - v]_+ =
+ * s gamma / m over the row (s gamma / n over the column; by bisection).
+ * C: device FP32 m x n (row stride ldc); XS: device FP32 m x d; XT: device
+ * FP32 n x d; labels: device int32 [m] in [0, L); gamma > 0.
  */
 OTGS_API int ot_gs_mlp_features(const float *C, int64_t ldc, int64_t m, int64_t n, const float *XS, const float *XT,
-                                int32_t d, const int32_t *labels, int32_t L, int32_t in_dim, float *out,
+                                int32_t d, const int32_t *labels, int32_t L, float gamma, int32_t in_dim, float *out,
                                 void *stream);
+/* The same features for nprob problems in one launch: C, ldc, m, n, XS, XT,
+ * labels, L are HOST arrays of nprob entries (pointers to device data as
+ * above).  out (device FP32) gets the source rows of every problem in
+ * concatenated order (sum m rows), then the target rows (sum n rows): the
+ * network's output is then alpha, then beta, in the batch layout. */
+OTGS_API int ot_gs_mlp_features_batch(int32_t nprob, const float *const *C, const int64_t *ldc, const int64_t *m,
+                                      const int64_t *n, const float *const *XS, const float *const *XT, int32_t d,
+                                      const int32_t *const *labels, const int32_t *L, float gamma, int32_t in_dim,
+                                      float *out, void *stream);
 /* Message of the last failure on h (NULL: of the last failed create or features call). */
 OTGS_API const char *ot_gs_mlp_last_error(const ot_gs_mlp *h);
 

@@ -8,18 +8,21 @@ it.  It shares no code with the CUDA path.
 The paper has no learned component; this is the definition the project's
 own kernels implement (plain numpy, FP64, written for reading).
 
-Features (one row per sample; ``K = 6 + 2 d`` entries, zero-padded to a
+Features (one row per sample; ``K = 9 + 2 d`` entries, zero-padded to a
 multiple of 16 by the caller's choice of ``kpad``):
 
 * source row i of class l:  [0, min_j c_ij, mean_j c_ij, softmin_0.02,
-  softmin_0.1, g_l / m, x_i (d), mu_l (d)]
+  softmin_0.1, g_l / m, wl_0.5, wl_1, wl_2, x_i (d), mu_l (d)]
 * target column j:          [1, min_i c_ij, mean_i c_ij, softmin_0.02,
-  softmin_0.1, g_k / m, y_j (d), mu_k (d)]
+  softmin_0.1, g_k / m, wl_0.5, wl_1, wl_2, y_j (d), mu_k (d)]
 
 where mu_l is the mean of class l's source features, g_l its size, k the
 class whose mean is nearest to y_j (squared distance in FP32, terms added
-in index order; ties to the lower class), and softmin_tau over values v is
-``-tau log(mean exp(-v / tau))``.
+in index order; ties to the lower class), softmin_tau over values v is
+``-tau log(mean exp(-v / tau))`` and the water level wl_s over a row's
+(column's) costs v is the L with sum [L - v]_+ = s gamma / m (s gamma / n):
+with the other side's duals constant, the dual of a sample whose plan row
+sums to its marginal under the squared-L2 regulariser alone.
 
 Network (width H): Z1 = q(X) q(W1)^T + b1, A1 = relu(Z1),
 Z2 = q(A1) q(W2)^T + b2, A2 = relu(Z2), y = q(A2) q(w3) + b3, with q the
@@ -36,7 +39,8 @@ from __future__ import annotations
 
 import numpy as np
 
-NSTAT = 6  # flag, min, mean, two softmins, class fraction
+NSTAT = 9  # flag, min, mean, two softmins, class fraction, three water levels
+WL = (0.5, 1.0, 2.0)
 TAUS = (0.02, 0.1)
 
 
@@ -61,7 +65,20 @@ def softmin(v, tau, axis):
     return np.squeeze(lo - tau * np.log(s), axis=axis)
 
 
-def features(C, XS, XT, labels, L, kpad=None):
+def water_level(v, w):
+    """The L with sum_k [L - v_k]_+ = w (w > 0): with v sorted, the level over
+    the k smallest values, (w + v_1 + ... + v_k) / k, for the k where it falls
+    between v_k and v_(k+1)."""
+    v = np.sort(np.asarray(v, dtype=np.float64))
+    cs = np.cumsum(v)
+    for k in range(1, len(v) + 1):
+        lev = (w + cs[k - 1]) / k
+        if k == len(v) or lev <= v[k]:
+            return lev
+    raise AssertionError("unreachable")
+
+
+def features(C, XS, XT, labels, L, gamma, kpad=None):
     """Per-sample inputs (source rows, then target columns) as float64
     arrays of shape (m, K) and (n, K)."""
     C = np.asarray(C, dtype=np.float64)
@@ -98,6 +115,8 @@ def features(C, XS, XT, labels, L, kpad=None):
     S[:, 3] = softmin(C, TAUS[0], 1)
     S[:, 4] = softmin(C, TAUS[1], 1)
     S[:, 5] = g[lab] / m
+    for q, sc in enumerate(WL):
+        S[:, 6 + q] = [water_level(C[i], sc * gamma / m) for i in range(m)]
     S[:, NSTAT:NSTAT + d] = XS
     S[:, NSTAT + d:K] = mu[lab]
     T = np.zeros((n, kp))
@@ -107,6 +126,8 @@ def features(C, XS, XT, labels, L, kpad=None):
     T[:, 3] = softmin(C, TAUS[0], 0)
     T[:, 4] = softmin(C, TAUS[1], 0)
     T[:, 5] = g[near] / m
+    for q, sc in enumerate(WL):
+        T[:, 6 + q] = [water_level(C[:, j], sc * gamma / n) for j in range(n)]
     T[:, NSTAT:NSTAT + d] = XT
     T[:, NSTAT + d:K] = mu[near]
     return S, T

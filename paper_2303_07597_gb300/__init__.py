@@ -108,8 +108,9 @@ def lib():
         "ot_gs_mlp_forward": ([P, P, i64, P], ctypes.c_int),
         "ot_gs_mlp_grad": ([P, P, P, i64, P, P], ctypes.c_int),
         "ot_gs_mlp_adam": ([P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float], ctypes.c_int),
-        "ot_gs_mlp_features": ([P, i64, i64, i64, P, P, i32, P, i32, i32, P, P], ctypes.c_int),
+        "ot_gs_mlp_features": ([P, i64, i64, i64, P, P, i32, P, i32, ctypes.c_float, i32, P, P], ctypes.c_int),
         "ot_gs_mlp_last_error": ([P], ctypes.c_char_p),
+        "ot_gs_mlp_features_batch": ([i32, P, P, P, P, P, P, i32, P, P, ctypes.c_float, i32, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -611,7 +612,7 @@ def _mlp_check(h, rc):
     return rc
 
 
-def mlp_features(C, XS, XT, labels, L, in_dim, out=None, stream=None):
+def mlp_features(C, XS, XT, labels, L, gamma, in_dim, out=None, stream=None):
     """Input features of one problem (device tensors): (m + n, in_dim) FP32,
     source rows then target columns (see ot_gs_mlp_features)."""
     import torch
@@ -623,8 +624,36 @@ def mlp_features(C, XS, XT, labels, L, in_dim, out=None, stream=None):
         out = torch.empty(m + n, in_dim, dtype=torch.float32, device=C.device)
     rc = lib().ot_gs_mlp_features(ctypes.c_void_p(C.data_ptr()), C.stride(0), m, n,
                                   _ptr(XS, torch.float32, m * d, "XS"), _ptr(XT, torch.float32, n * d, "XT"),
-                                  d, _ptr(labels, torch.int32, m, "labels"), int(L), int(in_dim),
+                                  d, _ptr(labels, torch.int32, m, "labels"), int(L), float(gamma), int(in_dim),
                                   _ptr(out, torch.float32, (m + n) * in_dim, "out"), _stream_ptr(stream))
+    _mlp_check(None, rc)
+    return out
+
+
+def mlp_features_batch(Cs, XSs, XTs, labels, Ls, gamma, in_dim, out=None, stream=None):
+    """Features of many problems in one launch: rows of all source samples
+    (concatenated), then of all target samples."""
+    import torch
+    k = len(Cs)
+    d = XSs[0].shape[1]
+    ms = [int(C.shape[0]) for C in Cs]
+    ns = [int(C.shape[1]) for C in Cs]
+    for q in range(k):
+        if Cs[q].stride(1) != 1 or Cs[q].dtype != torch.float32:
+            raise ValueError(f"C[{q}] must be float32 with unit column stride")
+        _ptr(XSs[q], torch.float32, ms[q] * d, f"XS[{q}]")
+        _ptr(XTs[q], torch.float32, ns[q] * d, f"XT[{q}]")
+        _ptr(labels[q], torch.int32, ms[q], f"labels[{q}]")
+    if out is None:
+        out = torch.empty(sum(ms) + sum(ns), in_dim, dtype=torch.float32, device=Cs[0].device)
+    arrs = [_host_array([C.data_ptr() for C in Cs], ctypes.c_void_p),
+            _host_array([C.stride(0) for C in Cs], ctypes.c_int64), _host_array(ms, ctypes.c_int64),
+            _host_array(ns, ctypes.c_int64), _host_array([x.data_ptr() for x in XSs], ctypes.c_void_p),
+            _host_array([x.data_ptr() for x in XTs], ctypes.c_void_p)]
+    lp = _host_array([x.data_ptr() for x in labels], ctypes.c_void_p)
+    Lp = _host_array([int(x) for x in Ls], ctypes.c_int32)
+    rc = lib().ot_gs_mlp_features_batch(k, *[a[1] for a in arrs], d, lp[1], Lp[1], float(gamma), int(in_dim),
+                                        _ptr(out, torch.float32, out.numel(), "out"), _stream_ptr(stream))
     _mlp_check(None, rc)
     return out
 

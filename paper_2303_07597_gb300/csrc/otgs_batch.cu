@@ -593,8 +593,9 @@ __global__ void k_bscatter(const BProb* __restrict__ P, const int32_t* __restric
 
 // ------------------------------------------------------- shift search
 // D(alpha + k 1, beta) is concave in k with derivative 1' grad_alpha D =
-// sum a - sum T: per problem, a bracket [lo, hi] of the maximiser is grown
-// (doubling) until the derivative is > 0 at lo and < 0 at hi, then halved.
+// sum a - sum T: per problem, a bracket [lo, hi] of the maximiser (from
+// [-1/16, 1/16]) is grown (doubling) until the derivative is > 0 at lo and
+// < 0 at hi, then halved.
 struct ShiftState {
     double lo, hi, x;
     int lo_ok, hi_ok;
@@ -608,9 +609,9 @@ __global__ void __launch_bounds__(BT) k_shift_point(const BProb* __restrict__ P,
     const BProb p = P[k];
     if (threadIdx.x == 0) {
         ShiftState& s = S[k];
-        if (first) {
-            s.lo = -1.0;
-            s.hi = 1.0;
+        if (first) {  // a start of the usual size: far points make every f positive (slow evaluations)
+            s.lo = -0.0625;
+            s.hi = 0.0625;
             s.lo_ok = 0;
             s.hi_ok = 0;
         }

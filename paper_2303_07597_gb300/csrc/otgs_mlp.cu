@@ -3,13 +3,16 @@
 // them to initial duals, trained with Adam on solutions the solver produced.
 //
 // Features of a problem (one row of in_dim floats per sample, source rows
-// first, then target columns; entries past 6 + 2d are zero):
+// first, then target columns; entries past 9 + 2d are zero):
 //   source i of class l: [0, min_j c_ij, mean_j c_ij, softmin_0.02, softmin_0.1,
-//                         g_l / m, x_i (d), mu_l (d)]
+//                         g_l / m, wl_0.5, wl_1, wl_2, x_i (d), mu_l (d)]
 //   target j:            [1, min_i c_ij, mean_i c_ij, softmin_0.02, softmin_0.1,
-//                         g_k / m, y_j (d), mu_k (d)]
+//                         g_k / m, wl_0.5, wl_1, wl_2, y_j (d), mu_k (d)]
 // mu_l = mean source feature of class l, g_l its size, k = the non-empty
-// class whose mean is nearest to y_j, softmin_tau(v) = -tau log mean exp(-v/tau).
+// class whose mean is nearest to y_j, softmin_tau(v) = -tau log mean exp(-v/tau),
+// wl_s = the level L with sum [L - v]_+ = s gamma / m (rows; / n for columns):
+// the sample's dual when the other side's duals are constant and only the
+// squared-L2 part of the regulariser acts.
 //
 // Network (width H, in_dim K, both multiples of 16): Z1 = q(X) q(W1)^T + b1,
 // A1 = relu(Z1), Z2 = q(A1) q(W2)^T + b2, A2 = relu(Z2), y = q(A2) q(w3) + b3,
@@ -38,7 +41,8 @@ namespace {
 
 thread_local std::string g_mlp_err;
 
-constexpr int NSTAT = 6;
+constexpr int NSTAT = 9;
+constexpr int WL_STEPS = 30;  // bisection steps of a water level (bracket width 2^-30 of its mass)
 
 // ================================================================ GEMM
 // C[M x N] = A[M x K] . B[N x K]^T, A and B bf16 row-major with K
@@ -283,27 +287,10 @@ __global__ void k_init(float* p, int64_t n, int64_t w1, int64_t b1e, int64_t w2e
 }
 
 // ============================================================= features
-// Class sums (FP64, rows in order) -> means rounded to FP32, and sizes.
-__global__ void k_class_means(const float* __restrict__ XS, int m, int d, const int32_t* __restrict__ lab, int L,
-                              float* mu, int* gsz)
-{
-    const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= (int64_t)L * d) return;
-    const int l = (int)(q / d), c = (int)(q % d);
-    double s = 0.0;
-    int cnt = 0;
-    for (int i = 0; i < m; i++)
-        if (lab[i] == l) {
-            s += (double)XS[(int64_t)i * d + c];
-            cnt++;
-        }
-    mu[q] = cnt ? (float)(s / cnt) : 0.f;
-    if (c == 0) gsz[l] = cnt;
-}
-
-// Statistics of a cost row or column: min, mean and softmin for the two
-// temperatures, over `cnt` values at stride `stride` (FP32, in order).
-__device__ __forceinline__ void cost_stats(const float* v, int64_t stride, int cnt, float* out)
+// Statistics of a cost row or column: min, mean, softmin for the two
+// temperatures and the water levels of masses w * {0.5, 1, 2}, over `cnt`
+// values at stride `stride` (FP32, in order).
+__device__ __forceinline__ void cost_stats(const float* v, int64_t stride, int cnt, float w, float* out)
 {
     float mn = INFINITY;
     double sum = 0.0;
@@ -322,38 +309,173 @@ __device__ __forceinline__ void cost_stats(const float* v, int64_t stride, int c
     out[1] = (float)(sum / (double)cnt);
     out[2] = mn - 0.02f * logf(e1 / (float)cnt);
     out[3] = mn - 0.1f * logf(e2 / (float)cnt);
+    // sum [L - v]_+ grows with L from 0 at L = min past the mass at min + mass: bisection
+    const float mass[3] = {0.5f * w, w, 2.f * w};
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        float lo = mn, hi = mn + mass[q];
+        for (int it = 0; it < WL_STEPS; it++) {
+            const float mid = 0.5f * (lo + hi);
+            float sum = 0.f;
+            for (int k = 0; k < cnt; k++) sum += fmaxf(mid - v[(int64_t)k * stride], 0.f);
+            if (sum < mass[q]) lo = mid;
+            else hi = mid;
+        }
+        out[4 + q] = 0.5f * (lo + hi);
+    }
 }
 
-// One thread per sample (source rows, then target columns): the sample's row
-// of the feature matrix (in_dim floats).
-__global__ void k_features(const float* __restrict__ C, int64_t ldc, int m, int n, const float* __restrict__ XS,
-                           const float* __restrict__ XT, int d, const int32_t* __restrict__ lab, int L,
-                           const float* __restrict__ mu, const int* __restrict__ gsz, int in_dim, float* out)
+// Batched features: problem table entries.
+struct FeatProb {
+    const float* C;
+    const float* XS;
+    const float* XT;
+    const int32_t* lab;
+    int64_t ldc;
+    int32_t m, n, L;
+    int32_t roff, coff;  // first source row / target column in the concatenation
+    int32_t moff;        // first class of the problem in the class-mean table
+};
+
+// Class means of every problem: one CTA per problem, a thread per (class,
+// feature) pair walking the problem's rows in order (FP64 sums).
+__global__ void __launch_bounds__(256) k_class_means_b(const FeatProb* __restrict__ P, int d, float* mu, int* gsz)
 {
-    const int q = blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= m + n) return;
-    float* o = out + (int64_t)q * in_dim;
-    float st[4];
+    const FeatProb p = P[blockIdx.x];
+    for (int q = threadIdx.x; q < p.L * d; q += blockDim.x) {
+        const int l = q / d, c = q % d;
+        double s = 0.0;
+        int cnt = 0;
+        for (int i = 0; i < p.m; i++)
+            if (p.lab[i] == l) {
+                s += (double)p.XS[(int64_t)i * d + c];
+                cnt++;
+            }
+        mu[(int64_t)(p.moff + l) * d + c] = cnt ? (float)(s / cnt) : 0.f;
+        if (c == 0) gsz[p.moff + l] = cnt;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
+    return v;
+}
+
+// The statistics of cost_stats for one contiguous row, a warp at a time
+// (lanes take every 32nd value; the same in every lane on return).
+__device__ __forceinline__ void row_stats_warp(const float* v, int cnt, float w, float* out)
+{
+    const int lane = threadIdx.x & 31;
+    float mn = INFINITY;
+    double sum = 0.0;
+    for (int k = lane; k < cnt; k += 32) {
+        const float c = v[k];
+        mn = fminf(mn, c);
+        sum += (double)c;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        mn = fminf(mn, __shfl_xor_sync(FULLMASK, mn, off));
+        sum += __shfl_xor_sync(FULLMASK, sum, off);
+    }
+    float e1 = 0.f, e2 = 0.f;
+    for (int k = lane; k < cnt; k += 32) {
+        const float c = v[k] - mn;
+        e1 += expf(-c / 0.02f);
+        e2 += expf(-c / 0.1f);
+    }
+    e1 = warp_sum(e1);
+    e2 = warp_sum(e2);
+    out[0] = mn;
+    out[1] = (float)(sum / (double)cnt);
+    out[2] = mn - 0.02f * logf(e1 / (float)cnt);
+    out[3] = mn - 0.1f * logf(e2 / (float)cnt);
+    const float mass[3] = {0.5f * w, w, 2.f * w};
+#pragma unroll
+    for (int q = 0; q < 3; q++) {
+        float lo = mn, hi = mn + mass[q];
+        for (int it = 0; it < WL_STEPS; it++) {
+            const float mid = 0.5f * (lo + hi);
+            float part = 0.f;
+            for (int k = lane; k < cnt; k += 32) part += fmaxf(mid - v[k], 0.f);
+            if (warp_sum(part) < mass[q]) lo = mid;
+            else hi = mid;
+        }
+        out[4 + q] = 0.5f * (lo + hi);
+    }
+}
+
+// The problem holding global row (src) or column index g (offsets increase).
+__device__ __forceinline__ int find_prob(const FeatProb* __restrict__ P, int nprob, bool src, int64_t g)
+{
+    int lo = 0, hi = nprob - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if ((src ? P[mid].roff : P[mid].coff) <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Source samples, one warp each: rows [0, M) of the output.
+__global__ void k_features_src(const FeatProb* __restrict__ P, int nprob, int64_t Mtot, int d,
+                               const float* __restrict__ mu, const int* __restrict__ gsz, float gamma, int in_dim,
+                               float* out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= Mtot) return;
+    const FeatProb p = P[find_prob(P, nprob, true, g)];
+    const int i = (int)(g - p.roff);
+    float st[7];
+    row_stats_warp(p.C + (int64_t)i * p.ldc, p.n, gamma / (float)p.m, st);
+    int cls = p.lab[i];
+    if (cls < 0 || cls >= p.L) cls = -1;  // an invalid label: no class entries
+    float* o = out + g * in_dim;
+    const float* x = p.XS + (int64_t)i * d;
+    const float* mup = mu + (int64_t)(p.moff + (cls >= 0 ? cls : 0)) * d;
+    if (lane == 0) {
+        o[0] = 0.f;
+        for (int q = 0; q < 4; q++) o[1 + q] = st[q];
+        o[5] = cls >= 0 ? (float)gsz[p.moff + cls] / (float)p.m : 0.f;
+        for (int q = 0; q < 3; q++) o[6 + q] = st[4 + q];
+    }
+    for (int c = lane; c < d; c += 32) {
+        o[NSTAT + c] = x[c];
+        o[NSTAT + d + c] = cls >= 0 ? mup[c] : 0.f;
+    }
+    for (int c = NSTAT + 2 * d + lane; c < in_dim; c += 32) o[c] = 0.f;
+}
+
+// Target samples, one thread each (a column's values are read coalesced
+// across the threads): rows [M, M + N) of the output.
+__global__ void k_features_tgt(const FeatProb* __restrict__ P, int nprob, int64_t Mtot, int64_t Ntot, int d,
+                               const float* __restrict__ mu, const int* __restrict__ gsz, float gamma, int in_dim,
+                               float* out)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Ntot) return;
+    const int64_t q = Mtot + g;
+    const FeatProb p = P[find_prob(P, nprob, false, g)];
+    float* o = out + q * in_dim;
+    float st[7];
     int cls;
     const float* x;
-    if (q < m) {
-        cost_stats(C + (int64_t)q * ldc, 1, n, st);
-        cls = lab[q];
-        if (cls < 0 || cls >= L) cls = -1;  // an invalid label: no class entries
-        x = XS + (int64_t)q * d;
-        o[0] = 0.f;
-    } else {
-        const int j = q - m;
-        cost_stats(C + j, ldc, m, st);
-        x = XT + (int64_t)j * d;
-        // nearest non-empty class mean (FP32 squared distance summed in order; ties to the lower class)
+    const float* mup = mu + (int64_t)p.moff * d;
+    const int* gz = gsz + p.moff;
+    {
+        const int j = (int)(g - p.coff);
+        cost_stats(p.C + j, p.ldc, p.m, gamma / (float)p.n, st);
+        x = p.XT + (int64_t)j * d;
         float best = INFINITY;
         cls = -1;
-        for (int l = 0; l < L; l++) {
-            if (gsz[l] == 0) continue;
+        for (int l = 0; l < p.L; l++) {
+            if (gz[l] == 0) continue;
             float dist = 0.f;
             for (int c = 0; c < d; c++) {
-                const float df = __fsub_rn(x[c], mu[(int64_t)l * d + c]);
+                const float df = __fsub_rn(x[c], mup[(int64_t)l * d + c]);
                 dist = __fadd_rn(dist, __fmul_rn(df, df));
             }
             if (dist < best) {
@@ -367,10 +489,13 @@ __global__ void k_features(const float* __restrict__ C, int64_t ldc, int m, int 
     o[2] = st[1];
     o[3] = st[2];
     o[4] = st[3];
-    o[5] = cls >= 0 ? (float)gsz[cls] / (float)m : 0.f;
+    o[5] = cls >= 0 ? (float)gz[cls] / (float)p.m : 0.f;
+    o[6] = st[4];
+    o[7] = st[5];
+    o[8] = st[6];
     for (int c = 0; c < d; c++) {
         o[NSTAT + c] = x[c];
-        o[NSTAT + d + c] = cls >= 0 ? mu[(int64_t)cls * d + c] : 0.f;
+        o[NSTAT + d + c] = cls >= 0 ? mup[(int64_t)cls * d + c] : 0.f;
     }
     for (int c = NSTAT + 2 * d; c < in_dim; c++) o[c] = 0.f;
 }
@@ -644,33 +769,65 @@ int ot_gs_mlp_adam(ot_gs_mlp* h, float lr, float b1, float b2, float eps)
 }
 
 int ot_gs_mlp_features(const float* C, int64_t ldc, int64_t m, int64_t n, const float* XS, const float* XT,
-                       int32_t d, const int32_t* labels, int32_t L, int32_t in_dim, float* out, void* stream)
+                       int32_t d, const int32_t* labels, int32_t L, float gamma, int32_t in_dim, float* out,
+                       void* stream)
+{
+    return ot_gs_mlp_features_batch(1, &C, &ldc, &m, &n, &XS, &XT, d, &labels, &L, gamma, in_dim, out, stream);
+}
+
+int ot_gs_mlp_features_batch(int32_t nprob, const float* const* C, const int64_t* ldc, const int64_t* m,
+                             const int64_t* n, const float* const* XS, const float* const* XT, int32_t d,
+                             const int32_t* const* labels, const int32_t* L, float gamma, int32_t in_dim,
+                             float* out, void* stream)
 {
     g_mlp_err.clear();
-    if (!C || !XS || !XT || !labels || !out || m <= 0 || n <= 0 || d <= 0 || L <= 0 || ldc < n ||
-        in_dim < NSTAT + 2 * d || m > INT32_MAX / 2 || n > INT32_MAX / 2) {
-        g_mlp_err = "invalid features arguments (in_dim >= 6 + 2 d)";
+    if (nprob <= 0 || !C || !ldc || !m || !n || !XS || !XT || !labels || !L || !out || d <= 0 ||
+        in_dim < NSTAT + 2 * d || !(gamma > 0.f)) {
+        g_mlp_err = "invalid batched features arguments (in_dim >= 9 + 2 d, gamma > 0)";
         return OTGS_EINVAL;
     }
+    std::vector<FeatProb> tab(nprob);
+    int64_t M = 0, N = 0, LL = 0;
+    for (int32_t k = 0; k < nprob; k++) {
+        if (!C[k] || !XS[k] || !XT[k] || !labels[k] || m[k] <= 0 || n[k] <= 0 || L[k] <= 0 || ldc[k] < n[k]) {
+            g_mlp_err = "invalid problem " + std::to_string(k);
+            return OTGS_EINVAL;
+        }
+        FeatProb& p = tab[k];
+        p.C = C[k]; p.XS = XS[k]; p.XT = XT[k]; p.lab = labels[k]; p.ldc = ldc[k];
+        p.m = (int32_t)m[k]; p.n = (int32_t)n[k]; p.L = L[k];
+        p.roff = (int32_t)M; p.coff = (int32_t)N; p.moff = (int32_t)LL;
+        M += m[k];
+        N += n[k];
+        LL += L[k];
+        if (M > INT32_MAX / 2 || N > INT32_MAX / 2 || LL * d > INT32_MAX / 2) {
+            g_mlp_err = "batch too large";
+            return OTGS_EINVAL;
+        }
+    }
     cudaStream_t st = (cudaStream_t)stream;
+    FeatProb* dtab = nullptr;
     float* mu = nullptr;
     int* gsz = nullptr;
-    if (cudaMallocAsync(&mu, sizeof(float) * (size_t)L * d, st) != cudaSuccess ||
-        cudaMallocAsync(&gsz, sizeof(int) * (size_t)L, st) != cudaSuccess) {
+    if (cudaMallocAsync(&dtab, sizeof(FeatProb) * (size_t)nprob, st) != cudaSuccess ||
+        cudaMallocAsync(&mu, sizeof(float) * (size_t)(LL * d), st) != cudaSuccess ||
+        cudaMallocAsync(&gsz, sizeof(int) * (size_t)LL, st) != cudaSuccess) {
         cudaGetLastError();
+        if (dtab) cudaFreeAsync(dtab, st);
         if (mu) cudaFreeAsync(mu, st);
         g_mlp_err = "cudaMallocAsync failed";
         return OTGS_ENOMEM;
     }
-    const int64_t ld = (int64_t)L * d;
-    k_class_means<<<(int)((ld + 127) / 128), 128, 0, st>>>(XS, (int)m, d, labels, L, mu, gsz);
-    k_features<<<(int)((m + n + 127) / 128), 128, 0, st>>>(C, ldc, (int)m, (int)n, XS, XT, d, labels, L, mu, gsz,
-                                                          in_dim, out);
+    cudaMemcpyAsync(dtab, tab.data(), sizeof(FeatProb) * (size_t)nprob, cudaMemcpyHostToDevice, st);
+    k_class_means_b<<<nprob, 256, 0, st>>>(dtab, d, mu, gsz);
+    k_features_src<<<(int)((M + 7) / 8), 256, 0, st>>>(dtab, nprob, M, d, mu, gsz, gamma, in_dim, out);
+    k_features_tgt<<<(int)((N + 127) / 128), 128, 0, st>>>(dtab, nprob, M, N, d, mu, gsz, gamma, in_dim, out);
+    cudaFreeAsync(dtab, st);
     cudaFreeAsync(mu, st);
     cudaFreeAsync(gsz, st);
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
-        g_mlp_err = std::string("features: ") + cudaGetErrorString(e);
+        g_mlp_err = std::string("batched features: ") + cudaGetErrorString(e);
         return OTGS_ECUDA;
     }
     return OTGS_OK;

@@ -16,9 +16,9 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import GroupSparseOTBatch, WarmStartMLP, mlp_features
+from . import GroupSparseOTBatch, WarmStartMLP, mlp_features, mlp_features_batch
 
-NSTAT = 6
+NSTAT = 9
 
 
 def in_dim_for(d: int) -> int:
@@ -32,14 +32,14 @@ def gauge_fix(alpha, beta):
     return alpha + k, beta - k
 
 
-def problem_features(p, device, in_dim):
+def problem_features(p, device, in_dim, gamma):
     """Features of a synth.Problem (with XS, XT) on the device: (m + n, in_dim)."""
     import torch
     C = torch.from_numpy(p.C).to(device)
     XS = torch.from_numpy(np.ascontiguousarray(p.XS, dtype=np.float32)).to(device)
     XT = torch.from_numpy(np.ascontiguousarray(p.XT, dtype=np.float32)).to(device)
     lab = torch.from_numpy(p.labels).to(device)
-    return mlp_features(C, XS, XT, lab, p.L, in_dim)
+    return mlp_features(C, XS, XT, lab, p.L, gamma, in_dim)
 
 
 def batch_of(problems, device, gamma, mu):
@@ -65,13 +65,23 @@ def solve_targets(problems, device, gamma, mu, tol=1e-9, maxit=20000, ftol=1e-14
     return B, out, r
 
 
-def dataset(problems, targets, device, in_dim):
-    """Rows of features and their target duals for every sample of every problem."""
+WL1 = 7  # feature column of the water level wl_1
+
+
+def dataset(problems, targets, device, in_dim, gamma):
+    """Rows of features and their target duals for every sample of every
+    problem.  Only alpha + beta enters D, and the start point's common level
+    is set by the shift search, so each side's targets are anchored to a
+    level the features carry: mean(alpha) = mean of the rows' wl_1, mean(beta)
+    = mean of the columns' wl_1.  What is left to learn is each side's shape."""
     import torch
     Xs, ts = [], []
     for p, (al, be) in zip(problems, targets):
-        Xs.append(problem_features(p, device, in_dim))
-        ts.append(torch.cat([al, be]).float())
+        F = problem_features(p, device, in_dim, gamma)
+        Xs.append(F)
+        ta = al - al.mean() + F[:p.m, WL1].double().mean()
+        tb = be - be.mean() + F[p.m:, WL1].double().mean()
+        ts.append(torch.cat([ta, tb]).float())
     return torch.cat(Xs), torch.cat(ts)
 
 
@@ -93,27 +103,44 @@ def train(net: WarmStartMLP, X, t, steps=2000, batch=4096, lr=1e-3, lr_end=1e-4,
     return trace
 
 
-def predict(net: WarmStartMLP, problems, device, in_dim):
+def predict(net: WarmStartMLP, problems, device, in_dim, gamma):
     """Predicted (alpha, beta) per problem, gauge-fixed, float64."""
     out = []
     for p in problems:
-        y = net.forward(problem_features(p, device, in_dim)).double()
+        y = net.forward(problem_features(p, device, in_dim, gamma)).double()
         out.append(gauge_fix(y[:p.m], y[p.m:]))
     return out
 
 
-def warm_state(B: GroupSparseOTBatch, preds, shift_iters=40):
-    """Concatenated start point for the batch: each problem's prediction,
-    moved to the best point on its line (alpha + k, beta) by the library's
-    shift search, when its D then beats the zero start's D(0, 0) = 0; else
-    zero.  Returns (alpha, beta, used) with used[k] telling which problems
-    start warm."""
+def predict_batch(net: WarmStartMLP, dev_problems, Ls, in_dim, gamma):
+    """Predicted (alpha, beta) of many problems in the batch layout, from one
+    features launch and one pass of the network over all samples.
+    dev_problems: (C, XS, XT, labels) device tensors per problem."""
+    F = mlp_features_batch([q[0] for q in dev_problems], [q[1] for q in dev_problems],
+                           [q[2] for q in dev_problems], [q[3] for q in dev_problems], Ls, gamma, in_dim)
+    y = net.forward(F).double()
+    M = sum(int(q[0].shape[0]) for q in dev_problems)
+    return y[:M].contiguous(), y[M:].contiguous()
+
+
+def warm_state(B: GroupSparseOTBatch, preds, shift_iters=20):
+    """Concatenated start point for the batch: each problem's prediction
+    when its D beats the zero start's D(0, 0) = 0; if some problem's does
+    not, all predictions are first moved to the best point on their line
+    (alpha + k, beta) by the library's shift search; a problem whose D still
+    does not beat zero starts from zero.  preds: per problem (alpha, beta), or
+    the two concatenated vectors.  Returns (alpha, beta, used) with used[k]
+    telling which problems start warm."""
     import torch
-    al = torch.cat([a for a, _ in preds]).contiguous()
-    be = torch.cat([b for _, b in preds]).contiguous()
-    if shift_iters > 0:
-        B.shift(al, be, shift_iters)
+    if isinstance(preds, tuple) and len(preds) == 2 and preds[0].numel() == B.m:
+        al, be = preds[0].clone(), preds[1].clone()
+    else:
+        al = torch.cat([a for a, _ in preds]).contiguous()
+        be = torch.cat([b for _, b in preds]).contiguous()
     D, _ = B.grad(al, be, with_grad=False)
+    if shift_iters > 0 and not bool((D > 0.0).all()):
+        B.shift(al, be, shift_iters)
+        D, _ = B.grad(al, be, with_grad=False)
     used = (D > 0.0).cpu().numpy()
     for k in range(B.nprob):
         if not used[k]:

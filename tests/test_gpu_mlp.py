@@ -92,13 +92,33 @@ def test_features_match_oracle():
     XS, XT, lab = synth.mixture_features(sizes, n, d, rng)
     p = synth.make_problem(XS, XT, lab, L, keep_features=True)
     K = ws.in_dim_for(d)
-    F = ws.problem_features(p, DEV, K).cpu().numpy()
-    So, To = omlp.features(p.C, XS.astype(np.float32), XT.astype(np.float32), lab, L, kpad=K)
+    F = ws.problem_features(p, DEV, K, 0.8).cpu().numpy()
+    So, To = omlp.features(p.C, XS.astype(np.float32), XT.astype(np.float32), lab, L, 0.8, kpad=K)
     ref = np.concatenate([So, To])
     assert F.shape == ref.shape
-    # stats in FP32 (sums of C in FP64), class means rounded from FP64 sums
-    assert np.allclose(F[:, :omlp.NSTAT], ref[:, :omlp.NSTAT], rtol=2e-6, atol=1e-7)
+    # stats in FP32 (sums of C in FP64, water levels by 30 bisection steps),
+    # class means rounded from FP64 sums
+    assert np.allclose(F[:, :omlp.NSTAT], ref[:, :omlp.NSTAT], rtol=2e-6, atol=2e-7)
     assert np.allclose(F[:, omlp.NSTAT:], ref[:, omlp.NSTAT:], rtol=1e-6, atol=1e-7)
+
+
+def test_batched_features_equal_per_problem_features():
+    problems = [synth.large(seed=s, m=m, n=n, L=L, d=5, keep_features=True)
+                for s, (m, n, L) in enumerate([(40, 33, 4), (64, 64, 5), (17, 90, 3)])]
+    K = ws.in_dim_for(5)
+    devp = [(torch.from_numpy(p.C).to(DEV), torch.from_numpy(np.ascontiguousarray(p.XS, dtype=np.float32)).to(DEV),
+             torch.from_numpy(np.ascontiguousarray(p.XT, dtype=np.float32)).to(DEV),
+             torch.from_numpy(p.labels).to(DEV)) for p in problems]
+    F = pk.mlp_features_batch([q[0] for q in devp], [q[1] for q in devp], [q[2] for q in devp],
+                              [q[3] for q in devp], [p.L for p in problems], 1.0, K)
+    M = sum(p.m for p in problems)
+    ro, co = 0, M
+    for p, q in zip(problems, devp):
+        Fk = pk.mlp_features(q[0], q[1], q[2], q[3], p.L, 1.0, K)
+        assert torch.equal(F[ro:ro + p.m], Fk[:p.m])
+        assert torch.equal(F[co:co + p.n], Fk[p.m:])
+        ro += p.m
+        co += p.n
 
 
 def test_training_lowers_the_loss():
@@ -151,7 +171,7 @@ def test_warm_start_beats_zero_start_on_held_out_problems():
     for c0 in range(0, ntrain, 512):
         _, tg, _ = ws.solve_targets(train_p[c0:c0 + 512], DEV, gamma, mu)
         targets += tg
-    X, t = ws.dataset(train_p, targets, DEV, K)
+    X, t = ws.dataset(train_p, targets, DEV, K, gamma)
     net = pk.WarmStartMLP(K, 256, max_batch=4096, seed=1)
     trace = ws.train(net, X, t, steps=6000, batch=4096, lr=1e-3, lr_end=1e-4)
     assert trace[-1] < 0.5 * trace[0]
@@ -164,7 +184,7 @@ def test_warm_start_beats_zero_start_on_held_out_problems():
     B.set_state(za, zb)
     assert B.solve(tol=0.0, maxit=20000, target_D=Dstar, target_rtol=1e-6) == pk.OTGS_OK
     cold = B.result(with_iterate=False)
-    preds = ws.predict(net, test_p, DEV, K)
+    preds = ws.predict(net, test_p, DEV, K, gamma)
     al, be, used = ws.warm_state(B, preds)
     assert used.mean() >= 0.5
     B.set_state(al, be)

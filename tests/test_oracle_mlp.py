@@ -98,14 +98,16 @@ def test_features_by_brute_force():
     XT = rng.normal(size=(n, d))
     lab = np.array([0, 0, 2, 2, 2, 3, 0])  # class 1 empty
     C = rng.uniform(size=(m, n))
-    S, T = mlp.features(C, XS, XT, lab, L, kpad=16)
-    assert S.shape == (m, 16) and T.shape == (n, 16)
+    gamma = 0.7
+    S, T = mlp.features(C, XS, XT, lab, L, gamma, kpad=32)
+    assert S.shape == (m, 32) and T.shape == (n, 32)
     for i in range(m):
         l = lab[i]
         mu = XS[lab == l].mean(0)
         row = C[i]
         sm = [-tau * np.log(np.mean(np.exp(-row / tau))) for tau in mlp.TAUS]
-        ref = [0.0, row.min(), row.mean(), sm[0], sm[1], (lab == l).sum() / m, *XS[i], *mu]
+        wl = [_level_bisect(row, s * gamma / m) for s in mlp.WL]
+        ref = [0.0, row.min(), row.mean(), sm[0], sm[1], (lab == l).sum() / m, *wl, *XS[i], *mu]
         assert np.allclose(S[i, :len(ref)], ref, rtol=1e-12, atol=1e-12)
         assert np.all(S[i, len(ref):] == 0)
     for j in range(n):
@@ -114,8 +116,31 @@ def test_features_by_brute_force():
         k = cand[int(np.argmin(dist))]
         col = C[:, j]
         sm = [-tau * np.log(np.mean(np.exp(-col / tau))) for tau in mlp.TAUS]
-        ref = [1.0, col.min(), col.mean(), sm[0], sm[1], (lab == k).sum() / m, *XT[j], *XS[lab == k].mean(0)]
+        wl = [_level_bisect(col, s * gamma / n) for s in mlp.WL]
+        ref = [1.0, col.min(), col.mean(), sm[0], sm[1], (lab == k).sum() / m, *wl, *XT[j], *XS[lab == k].mean(0)]
         assert np.allclose(T[j, :len(ref)], ref, rtol=1e-12, atol=1e-12)
+
+
+def _level_bisect(v, w):
+    """sum [L - v]_+ = w by bisection (a method independent of the oracle's sort)."""
+    lo, hi = v.min(), v.min() + w
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if np.maximum(mid - v, 0).sum() < w:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+def test_water_level_closed_forms():
+    # one value: L = v + w; equal values: L = v + w / k; the level solves its equation
+    assert mlp.water_level([0.3], 0.2) == pytest.approx(0.5, abs=1e-15)
+    assert mlp.water_level([0.1] * 4, 0.2) == pytest.approx(0.15, abs=1e-15)
+    v = np.random.default_rng(9).uniform(size=37)
+    for w in (1e-4, 0.05, 3.0):
+        lev = mlp.water_level(v, w)
+        assert np.maximum(lev - v, 0).sum() == pytest.approx(w, rel=1e-12)
 
 
 def test_softmin_between_min_and_mean():
