@@ -222,6 +222,7 @@ bool Handle::init(int32_t np, const float* const* C_, const int64_t* ldc_, const
         static_assert(sizeof(TmaMaps) == 2 * TMA_BOXES * sizeof(CUtensorMap), "maps are packed");
         maps = (CUtensorMap*)upload(this, tm, "TMA descriptors");  // cudaMalloc: 256-byte aligned
         if (!maps) return false;
+        tm0 = tm[0];
     }
     // row groups (independent of the plan's parameters)
     dp.goff = upload(this, hp.goff, "goff");
@@ -352,6 +353,11 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     memset(&e, 0, sizeof(e));
     e.probs = probs;
     e.maps = maps;
+    if (nprob == 1) {
+        e.tm0 = tm0;
+        e.pd0 = probs_h[0];
+        e.inline_maps = 1;
+    }
     e.m = (int32_t)m; e.n = (int32_t)n; e.L = L; e.ntiles = ntiles;
     e.fx_m = (int32_t)hp.max_m; e.fx_n = (int32_t)hp.max_n;
     e.nitems = hp.nitems();

@@ -35,6 +35,7 @@ struct Handle {
     Batch* batch = nullptr;           // batched solver state (first ot_gs_batch_solve)
     FxScale* pfx = nullptr;           // per problem: fixed-point scale of the last batch evaluation point
     CUtensorMap* maps = nullptr;      // device: per problem, TMA descriptors (box[], then tile[])
+    TmaMaps tm0;                      // problem 0's descriptors (passed in the kernel's parameters when nprob == 1)
     PlanParams plan_params;           // the parameters of the current plan (0 = defaults)
     int plan_gen = 0;                 // bumped by every (re)build of the plan
     std::vector<int32_t> labels_h;    // all problems' labels (caller order), for re-planning

@@ -294,8 +294,19 @@ __host__ __device__ inline FxScale fx_scale(unsigned amax_bits, unsigned bmax_bi
     return s;
 }
 
+// TMA descriptors of one problem's C: box[k] is 2^k rows x ITEM_COLS columns,
+// tile[k] is 2^k rows x TW columns (k = 0..TMA_BOXES-1).
+constexpr int TMA_BOXES = 6;
+static_assert((1 << (TMA_BOXES - 1)) == STAGE_ROWS, "boxes must compose any stage height");
+struct TmaMaps {
+    CUtensorMap box[TMA_BOXES];
+    CUtensorMap tile[TMA_BOXES];
+};
 // -------------------------------------------------------------- kernel args
 struct EvalArgs {
+    TmaMaps tm0;                // one problem (inline_maps): its maps in the kernel's parameters
+    ProbDesc pd0;               //   and its descriptor
+    int32_t inline_maps;        // 1: use tm0, pd0 (parameter space: no fetch from global memory)
     const ProbDesc* probs;      // [nprob]
     const CUtensorMap* maps;    // [nprob][2 * TMA_BOXES] (box[], then tile[]); 64-byte aligned
     int32_t m, n, L, ntiles, nitems;
@@ -365,14 +376,6 @@ struct ReduceArgs {
 void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, const double* beta,
                  int32_t m, int32_t n, float4* rowA, float2* B2, double* alpha_s_out,
                  unsigned long long* rowfx, unsigned long long* colfx, EvalCtl* ctl, cudaStream_t st);
-// TMA descriptors of one problem's C: box[k] is 2^k rows x ITEM_COLS columns,
-// tile[k] is 2^k rows x TW columns (k = 0..TMA_BOXES-1).
-constexpr int TMA_BOXES = 6;
-static_assert((1 << (TMA_BOXES - 1)) == STAGE_ROWS, "boxes must compose any stage height");
-struct TmaMaps {
-    CUtensorMap box[TMA_BOXES];
-    CUtensorMap tile[TMA_BOXES];
-};
 // Encodes the maps for C (m x n, row stride ldc floats); "" on success.
 std::string make_tmaps(const float* C, int64_t ldc, int64_t m, int64_t n, TmaMaps& T);
 // evaluation kernel (otgs_stream.cu): persistent, n_ctas CTAs; a.ctl zeroed by launch_prep

@@ -162,6 +162,9 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     memset(&ea, 0, sizeof(ea));
     ea.probs = (const ProbDesc*)(base + o_prob);
     ea.maps = (const CUtensorMap*)(base + o_maps);
+    ea.tm0 = tm;
+    ea.pd0 = pd;
+    ea.inline_maps = 1;
     ea.m = (int32_t)m; ea.n = (int32_t)n; ea.L = L; ea.ntiles = ntiles;
     ea.fx_m = (int32_t)m; ea.fx_n = (int32_t)n;
     ea.nitems = hp.nitems();

@@ -373,12 +373,18 @@ __device__ __forceinline__ unsigned long long t_q(float t, float to_fx)
 }
 
 // Warp-wide: the lanes' terms q of one row (one column per lane) added into
-// the row's fixed-point sum with one atomic.  The row's total is below 2^61
+// the row's fixed-point sum with one atomic (or each lane's own, when at most
+// two lanes have a term).  The row's total is below 2^61
 // (the grid's bound), so the three 32-bit partial sums cannot overflow:
 // bits 32.. sum below 2^29, the two 16-bit fields below 2^21.
 __device__ __forceinline__ void red_row(unsigned long long* p, unsigned long long q)
 {
-    if (!__any_sync(FULLMASK, q != 0ull)) return;
+    const unsigned bal = __ballot_sync(FULLMASK, q != 0ull);
+    if (!bal) return;
+    if (__popc(bal) <= 2) {  // one or two columns: their own atomics are cheaper than the sums
+        if (q) atomicAdd(p, q);
+        return;
+    }
     const unsigned hi = __reduce_add_sync(FULLMASK, (unsigned)(q >> 32));
     const unsigned m1 = __reduce_add_sync(FULLMASK, (unsigned)(q >> 16) & 0xffffu);
     const unsigned m0 = __reduce_add_sync(FULLMASK, (unsigned)q & 0xffffu);
@@ -399,10 +405,10 @@ __device__ __forceinline__ long long col_q(float s, float Ph, float Pl, float to
 // column: re-form f and add the nonzero t_ij = s [f_ij]_+ to the fixed-point
 // row sums (integer adds: the total does not depend on their order).  Eight
 // rows' loads are issued together.
-__device__ __forceinline__ void passb_rows(const EvalArgs& A, const FxScale& fx, int R0, int R1, int step,
-                                           int prob, int colg, float s)
+__device__ __forceinline__ void passb_rows(const EvalArgs& A, float to_rf, int R0, int R1, int step, int prob,
+                                           int colg, float s)
 {
-    const ProbDesc pd = A.probs[prob];
+    const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[prob];
     const int lcol = colg - pd.coff;
     const bool real = lcol < pd.n;
     const float2 b2 = real ? __ldg(A.B2 + pd.bcoff + lcol) : make_float2(0.f, 0.f);
@@ -423,7 +429,7 @@ __device__ __forceinline__ void passb_rows(const EvalArgs& A, const FxScale& fx,
             if (s > 0.f && maybe_pos(a[q].z, c[q], bp)) {
                 float fh, fl;
                 f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
-                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), fx.to_rf);
+                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), to_rf);
             }
             red_row(A.rowfx + R + q, tq);
         }
@@ -469,6 +475,7 @@ struct Ctx {
     int rend;          // end row of the item
     int item, split, sub, part;  // the item; its group's pieces, its piece, the set's piece-0 slot
     int prob;          // the item's problem
+    float to_rf, to_cf;  // its fixed-point scales (row sums, column sums)
 };
 
 __device__ __forceinline__ void open_block(Block& b, const int4& g, bool need, const Ctx& x)
@@ -515,8 +522,8 @@ __device__ __forceinline__ bool defer_passb(const EvalArgs& A, int gstart, int g
 // split group only stores its partial sums; the split-finish kernel adds the
 // pieces in order and finishes the block.
 template <bool SNAP>
-__device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, const FxScale& fx,
-                                             int lane, bool marks, float (&psi_acc)[2], long long& cacc)
+__device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, int lane, bool marks,
+                                             float (&psi_acc)[2], long long& cacc)
 {
     if (b.split) {
         float* q = A.split_part + ((int64_t)(x.part + x.sub) * ITEM_COLS + (threadIdx.x >> 5) * TW + lane) * 5;
@@ -533,7 +540,7 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
         float psh, psl;
         s = block_scale(b.acc.Sh, b.acc.Sl, A, psh, psl);
         df_add(psi_acc[0], psi_acc[1], psh, psl);
-        if (s > 0.f) cacc += col_q(s, b.acc.Ph, b.acc.Pl, fx.to_cf);
+        if (s > 0.f) cacc += col_q(s, b.acc.Ph, b.acc.Pl, x.to_cf);
     }
     if (SNAP) put_snap(A, b.gl, x.colg, x.real, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
     if (!__any_sync(FULLMASK, s > 0.f)) return;
@@ -542,7 +549,17 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
         // pass B goes to the pass-B kernel, or (that list is full) the
         // earlier rows are re-read here
         if (defer_passb(A, b.gstart, b.gend, x.colg - lane, x.prob, s, lane)) return;
-        passb_rows(A, fx, b.gstart, x.ra, 8, x.prob, x.colg, s);
+        for (int R = b.gstart; R < x.ra; R++) {  // one row at a time: few registers for a rare path
+            const float c = x.real ? __ldg(x.Cp + (int64_t)(R - x.roff) * x.ldc + x.lcol) : 0.f;
+            const float4 av = __ldg(A.rowA + R);
+            unsigned long long tq = 0ull;
+            if (s > 0.f && maybe_pos(av.z, c, x.bp)) {
+                float fh, fl;
+                f_exact(av.x, av.y, x.bh, x.bl, c, fh, fl);
+                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), x.to_rf);
+            }
+            red_row(A.rowfx + R, tq);
+        }
     }
     // pass B over the block's rows in this stage: t_ij = s [f_ij]_+ into the
     // row sums, over the chunks that can hold an f > 0 (every chunk on the
@@ -563,7 +580,7 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
             if (s > 0.f && maybe_pos(av.z, c, x.bp)) {
                 float fh, fl;
                 f_exact(av.x, av.y, x.bh, x.bl, c, fh, fl);
-                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), fx.to_rf);
+                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), x.to_rf);
             }
             red_row(A.rowfx + R0 + k, tq);
         }
@@ -586,7 +603,7 @@ __device__ __forceinline__ void block_marked_rows(Block& b, const Ctx& x, int s,
 
 // ================================================================= kernel
 template <bool SNAP>
-__global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs A)
+__global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_constant__ EvalArgs A)
 {
     if (A.gate && !*A.gate) return;  // a skipped solver trial
     extern __shared__ unsigned char smem_raw[];
@@ -662,9 +679,10 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int col0 = __shfl_sync(FULLMASK, w0, 4), nst = __shfl_sync(FULLMASK, w0, 6);
                 const int sbase = __shfl_sync(FULLMASK, w0, 7);
                 const int prob = __shfl_sync(FULLMASK, w0, 11);
-                const ProbDesc pd = A.probs[prob];
-                const CUtensorMap* maps = A.maps + (int64_t)prob * 2 * TMA_BOXES;
-                if (prob != fenced) {  // the descriptors live in global memory: acquire them for the tensor proxy
+                const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[prob];
+                const CUtensorMap* maps =
+                    A.inline_maps ? &A.tm0.box[0] : A.maps + (int64_t)prob * 2 * TMA_BOXES;
+                if (!A.inline_maps && prob != fenced) {  // descriptors in global memory: acquire them for the tensor proxy
                     if (lane == 0)
                         for (int k = 0; k < TMA_BOXES; k++) tmap_acquire(maps + k);
                     if (lane < CONSUMERS)
@@ -761,12 +779,16 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
     }
 
     // ----------------------------------------------------------- consumers
-    FxScale fx = prob_fx(A, 0);  // the current item's problem's
     const int wc = warp * TW + lane;  // this lane's column within an item
     long long consumed = 0;
     Ctx x;
     x.bh = 0.f; x.bl = 0.f; x.bp = -INFINITY; x.colg = 0; x.U = 0u; x.real = false;
     x.Cp = nullptr; x.ldc = 0; x.roff = 0; x.lcol = 0; x.prob = 0;
+    {
+        const FxScale fx = prob_fx(A, 0);  // (batches: replaced by the item's problem's)
+        x.to_rf = fx.to_rf;
+        x.to_cf = fx.to_cf;
+    }
     float psi_acc[2] = {0.f, 0.f};  // this lane's psi sum over the item's blocks, a float pair
     long long cacc = 0;              // this lane's column sum over the item's blocks, fixed point
     int item = -1;  // the item being consumed; its sums are written when the next one starts
@@ -809,8 +831,11 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
             x.bh = b2.x;
             x.bl = b2.y;
             x.prob = hs.d.prob;
-            if (A.pfx) fx = A.pfx[x.prob];
-            const ProbDesc pd = A.probs[x.prob];
+            if (A.pfx) {
+                x.to_rf = A.pfx[x.prob].to_rf;
+                x.to_cf = A.pfx[x.prob].to_cf;
+            }
+            const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[x.prob];
             x.Cp = pd.C;
             x.ldc = pd.ldc;
             x.roff = pd.roff;
@@ -845,7 +870,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) scan_rows<true>(x.st, x.rA, r, e, x.bh, x.bl, x.bp, blk.acc, blk.O, blk.any);
                 r = e;
-                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, fx, lane, false, psi_acc, cacc);
+                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, lane, false, psi_acc, cacc);
             }
         } else {
             // only the groups with a marked chunk (and a block that ends here)
@@ -857,7 +882,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) block_marked_rows(blk, x, 0, e);
                 if (blk.gend <= x.ra + x.nr && blk.need)
-                    finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
+                    finish_block<false>(A, blk, x, lane, true, psi_acc, cacc);
                 r = e;
             }
             while (r < x.nr) {
@@ -869,7 +894,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                     const int last = x.nr - 1;
                     open_block(blk, rG[last], (wrows >> last) & 1u, x);
                     if (blk.split && blk.need && blk.gend <= x.ra + x.nr)
-                        finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
+                        finish_block<false>(A, blk, x, lane, true, psi_acc, cacc);
                     break;
                 }
                 const int rc = max(r, 4 * (__ffs(Ur) - 1));  // the group there starts at or after r
@@ -877,7 +902,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const EvalArgs 
                 const int e = min(blk.gend - x.ra, x.nr);
                 if (blk.need) block_marked_rows(blk, x, blk.gstart - x.ra, e);
                 if (blk.gend <= x.ra + x.nr && blk.need)
-                    finish_block<false>(A, blk, x, fx, lane, true, psi_acc, cacc);
+                    finish_block<false>(A, blk, x, lane, true, psi_acc, cacc);
                 r = e;
             }
         }
@@ -934,7 +959,7 @@ __global__ void __launch_bounds__(PASSB_THREADS) k_passb(const EvalArgs A)
         const FxScale fx = prob_fx(A, e.prob);
         // warp w: 8-row batches w, w + nw, ... of the entry
         for (int R = e.gstart + 8 * warp; R < e.gend; R += 8 * nw)
-            passb_rows(A, fx, R, min(R + 8, e.gend), 8, e.prob, e.colg0 + lane, s);
+            passb_rows(A, fx.to_rf, R, min(R + 8, e.gend), 8, e.prob, e.colg0 + lane, s);
     }
 }
 
@@ -958,7 +983,7 @@ __global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
         const int tile = st.col0 / TW + warp;
         if (A.unit_need && !((A.unit_need[(int64_t)st.l * A.unit_words + (tile >> 5)] >> (tile & 31)) & 1u))
             continue;  // a screened-out unit: its pieces wrote nothing this evaluation
-        const ProbDesc pd = A.probs[st.prob];
+        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[st.prob];
         const FxScale fx = prob_fx(A, st.prob);
         const int lcol = st.col0 + warp * TW + lane;
         const int colg = pd.coff + lcol;
@@ -985,7 +1010,7 @@ __global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
         if (A.zt) put_snap(A, st.l, colg, real, z_up(t.Sh, t.Sl), __fsqrt_ru(o));
         if (!__any_sync(FULLMASK, s > 0.f)) continue;
         if (!defer_passb(A, st.rstart, st.rend, colg - lane, st.prob, s, lane))
-            passb_rows(A, fx, st.rstart, st.rend, 8, st.prob, colg, s);  // the list is full
+            passb_rows(A, fx.to_rf, st.rstart, st.rend, 8, st.prob, colg, s);  // the list is full
     }
 }
 
