@@ -27,7 +27,7 @@ namespace otgs {
 
 #define FULLMASK 0xffffffffu
 
-constexpr int BT = 256;                // threads of the per-problem kernels
+constexpr int BT = 512;                // threads of the per-problem kernels
 constexpr int BW = BT / 32;
 constexpr int TRIALS_PER_GRAPH = 16;   // trials captured in one graph
 
@@ -72,7 +72,9 @@ struct BStepArgs {
     const int* kerr;
     const double* a_sorted;
     const double* b;
-    double *x, *G, *d, *xt, *Gt, *Sv, *Yv;
+    double *x, *G, *d, *xt, *Gt;
+    float2 *Sv, *Yv;  // history s_k, y_k as float pairs (hi, lo), slot-major
+    float2* Gp;       // the current G as float pairs
     int64_t Ntot;
     int M;
     float4* rowA;
@@ -89,7 +91,8 @@ struct Batch {
     BCtl* bc = nullptr;
     BCtl* hbc = nullptr;  // pinned: two slots of nactive read-backs
     int* pactive = nullptr;
-    double *x = nullptr, *G = nullptr, *d = nullptr, *xt = nullptr, *Gt = nullptr, *Sv = nullptr, *Yv = nullptr;
+    double *x = nullptr, *G = nullptr, *d = nullptr, *xt = nullptr, *Gt = nullptr;
+    float2 *Sv = nullptr, *Yv = nullptr, *Gp = nullptr;
     BResult* res = nullptr;
     cudaStream_t bst = nullptr;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -328,6 +331,55 @@ enum { ACT_RETRY = 0, ACT_ACCEPT = 1, ACT_START = 2 };
 
 constexpr int SLOT_GROUP = 4;  // history slots whose dot products one pass accumulates
 
+// Double-float arithmetic for the history's dot products and combinations:
+// FP64 runs at a small fraction of FP32's rate on GB300, and these are most
+// of a solver step's work.  A float pair (hi, lo) holds an FP64 value to
+// ~2^-48 relative; the product of two pairs and a running sum keep that
+// accuracy (Dekker's product by FMA, Knuth's TwoSum), so a dot of n terms is
+// within ~n 2^-48 of its FP64 value.
+__device__ __forceinline__ float2 dsplit(double x)
+{
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+}
+
+// (h, l) += a * b
+__device__ __forceinline__ void dd_fma(float2 a, float2 b, float& h, float& l)
+{
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    const float s = __fadd_rn(h, p);
+    const float bb = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+    h = s;
+    l = __fadd_rn(l, __fadd_rn(err, e));
+}
+
+__device__ __forceinline__ double dd_value(float h, float l) { return (double)h + (double)l; }
+
+// Warp sums of NV double-float values (a fixed xor tree, in FP32 pairs: an
+// FP64 tree of these would be most of the step's FP64 work); lane 0 writes
+// the totals, as FP64, to dst.
+template <int NV>
+__device__ __forceinline__ void warp_dd_sums_to(float (&h)[NV], float (&l)[NV], double* dst)
+{
+#pragma unroll
+    for (int c = 0; c < NV; c++) {
+        float hh = h[c], ll = l[c];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) {
+            const float oh = __shfl_xor_sync(FULLMASK, hh, off), ol = __shfl_xor_sync(FULLMASK, ll, off);
+            const float s = __fadd_rn(hh, oh);
+            const float bb = __fsub_rn(s, hh);
+            const float err = __fadd_rn(__fsub_rn(hh, __fsub_rn(s, bb)), __fsub_rn(oh, bb));
+            hh = s;
+            ll = __fadd_rn(__fadd_rn(ll, ol), err);
+        }
+        if ((threadIdx.x & 31) == 0) dst[c] = dd_value(hh, ll);
+    }
+}
+
 template <int NV>
 __device__ __forceinline__ void warp_sums_to(double (&v)[NV], double* dst /* [NV] of this warp */)
 {
@@ -343,7 +395,9 @@ __device__ __forceinline__ void warp_sums_to(double (&v)[NV], double* dst /* [NV
 // One problem per CTA: its trial's reduction, line-search step, L-BFGS
 // update and next trial point.  Three passes over the problem's vectors;
 // sums are per-warp partials in shared memory added in warp order (fixed
-// order: results do not depend on scheduling).
+// order: results do not depend on scheduling).  The iterate, gradients and
+// direction are FP64; the stored pairs (s_k, y_k) and the products with
+// them are in double-float (see dd_fma); the scalar recursion is FP64.
 __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
 {
     if (!A.bc->go) return;
@@ -354,32 +408,40 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
     __shared__ double red[NB];
     __shared__ double SYs[MAX_LBFGS_M * MAX_LBFGS_M], YYs[MAX_LBFGS_M * MAX_LBFGS_M];
     __shared__ double coef[2 * MAX_LBFGS_M + 2];  // cy[], cs[], cG, t
+    __shared__ float2 coefp[2 * MAX_LBFGS_M];     // cy[], cs[] as float pairs
     __shared__ int act, fin;
     __shared__ unsigned shm[2 * BW];
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const BProb p = A.P[k];
     BState* S = A.S + k;
     const int N = p.m + p.n, M = A.M;
-    double* x = A.x + p.voff;
-    double* G = A.G + p.voff;
-    double* d = A.d + p.voff;
-    double* xt = A.xt + p.voff;
-    double* Gt = A.Gt + p.voff;
+    // the problem's vectors: distinct arrays (restrict: loads of a later
+    // element may be issued before the stores of an earlier one)
+    double* __restrict__ x = A.x + p.voff;
+    double* __restrict__ G = A.G + p.voff;
+    double* __restrict__ d = A.d + p.voff;
+    double* __restrict__ xt = A.xt + p.voff;
+    double* __restrict__ Gt = A.Gt + p.voff;
+    unsigned long long* __restrict__ rowfx = A.rowfx;  // read in step 1, zeroed in step 5
+    unsigned long long* __restrict__ colfx = A.colfx;
+    const double* __restrict__ asorted = A.a_sorted;
+    const double* __restrict__ bv_ = A.b;
     const FxScale fx = A.pfx[k];
 
     // 1. D, Gt = -grad D, Gt.d and ||Gt||_inf at the trial point
     {
         double v[4] = {0.0, 0.0, 0.0, 0.0};  // alpha.a + beta.b, Gt.d, psi, ||.||_inf
+#pragma unroll 4
         for (int e = threadIdx.x; e < N; e += BT) {
             double g, wt;
             if (e < p.m) {
                 const int r = p.roff + e;
-                wt = A.a_sorted[r];
-                g = wt - (double)(long long)A.rowfx[r] * fx.from_r;
+                wt = asorted[r];
+                g = wt - (double)(long long)rowfx[r] * fx.from_r;
             } else {
                 const int c = p.coff + (e - p.m);
-                wt = A.b[c];
-                g = wt - (double)(long long)A.colfx[c] * fx.from_c;
+                wt = bv_[c];
+                g = wt - (double)(long long)colfx[c] * fx.from_c;
             }
             Gt[e] = -g;
             v[0] += xt[e] * wt;
@@ -451,22 +513,25 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
         // 3. accept: s = xt - x, y = Gt - G into the head slot, x = xt, G = Gt,
         // with the base dots and the NPAIR dots of every stored slot
         const int head = (int)coef[2 * MAX_LBFGS_M];
-        double* s_new = A.Sv + (int64_t)head * A.Ntot + p.voff;
-        double* y_new = A.Yv + (int64_t)head * A.Ntot + p.voff;
+        float2* __restrict__ s_new = A.Sv + (int64_t)head * A.Ntot + p.voff;
+        float2* __restrict__ y_new = A.Yv + (int64_t)head * A.Ntot + p.voff;
+        float2* __restrict__ gp = A.Gp + p.voff;
         {
             double bv[NBASE] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll 4
             for (int e = threadIdx.x; e < N; e += BT) {
                 const double g = Gt[e];
                 if (a == ACT_ACCEPT) {
                     const double sv = xt[e] - x[e], yv = g - G[e];
-                    s_new[e] = sv;
-                    y_new[e] = yv;
+                    s_new[e] = dsplit(sv);
+                    y_new[e] = dsplit(yv);
                     bv[DOT_SY] += sv * yv;
                     bv[DOT_SS] += sv * sv;
                     bv[DOT_YY] += yv * yv;
                 }
                 x[e] = xt[e];
                 G[e] = g;
+                gp[e] = dsplit(g);
                 bv[DOT_GG] += g * g;
             }
             warp_sums_to<NBASE>(bv, wpart[w]);
@@ -474,24 +539,27 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
         const bool need_dir = !fin;
         if (need_dir && a == ACT_ACCEPT) {
             for (int q0 = 0; q0 < M; q0 += SLOT_GROUP) {
-                double pv[SLOT_GROUP * NPAIR];
+                float ph[SLOT_GROUP * NPAIR], pl[SLOT_GROUP * NPAIR];
 #pragma unroll
-                for (int c = 0; c < SLOT_GROUP * NPAIR; c++) pv[c] = 0.0;
+                for (int c = 0; c < SLOT_GROUP * NPAIR; c++) ph[c] = pl[c] = 0.f;
+                const float2* __restrict__ Sb = A.Sv + (int64_t)q0 * A.Ntot + p.voff;
+                const float2* __restrict__ Yb = A.Yv + (int64_t)q0 * A.Ntot + p.voff;
+#pragma unroll 2
                 for (int e = threadIdx.x; e < N; e += BT) {
-                    const double sn = s_new[e], yn = y_new[e], g = G[e];
+                    const float2 sn = s_new[e], yn = y_new[e], g = gp[e];
 #pragma unroll
                     for (int u = 0; u < SLOT_GROUP; u++) {
                         if (q0 + u >= M) break;
-                        const double sk = A.Sv[(int64_t)(q0 + u) * A.Ntot + p.voff + e];
-                        const double yk = A.Yv[(int64_t)(q0 + u) * A.Ntot + p.voff + e];
-                        pv[u * NPAIR + PD_SNEW_Y] += sn * yk;
-                        pv[u * NPAIR + PD_S_YNEW] += sk * yn;
-                        pv[u * NPAIR + PD_YNEW_Y] += yn * yk;
-                        pv[u * NPAIR + PD_G_S] += g * sk;
-                        pv[u * NPAIR + PD_G_Y] += g * yk;
+                        const float2 sk = Sb[(int64_t)u * A.Ntot + e];
+                        const float2 yk = Yb[(int64_t)u * A.Ntot + e];
+                        dd_fma(sn, yk, ph[u * NPAIR + PD_SNEW_Y], pl[u * NPAIR + PD_SNEW_Y]);
+                        dd_fma(sk, yn, ph[u * NPAIR + PD_S_YNEW], pl[u * NPAIR + PD_S_YNEW]);
+                        dd_fma(yn, yk, ph[u * NPAIR + PD_YNEW_Y], pl[u * NPAIR + PD_YNEW_Y]);
+                        dd_fma(g, sk, ph[u * NPAIR + PD_G_S], pl[u * NPAIR + PD_G_S]);
+                        dd_fma(g, yk, ph[u * NPAIR + PD_G_Y], pl[u * NPAIR + PD_G_Y]);
                     }
                 }
-                warp_sums_to<SLOT_GROUP * NPAIR>(pv, wpart[w] + NBASE + q0 * NPAIR);
+                warp_dd_sums_to<SLOT_GROUP * NPAIR>(ph, pl, wpart[w] + NBASE + q0 * NPAIR);
             }
         }
         if (need_dir)
@@ -517,6 +585,8 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
             for (int q = 0; q < MAX_LBFGS_M; q++) {
                 coef[q] = S->cy[q];
                 coef[MAX_LBFGS_M + q] = S->cs[q];
+                coefp[q] = dsplit(S->cy[q]);
+                coefp[MAX_LBFGS_M + q] = dsplit(S->cs[q]);
             }
             coef[2 * MAX_LBFGS_M] = S->cG;
             coef[2 * MAX_LBFGS_M + 1] = S->t;
@@ -531,15 +601,18 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
     const bool newdir = a != ACT_RETRY;
     const double cG = coef[2 * MAX_LBFGS_M];
     float apos = 0.f, bpos = 0.f;
+    const float2* __restrict__ Sb = A.Sv + p.voff;
+    const float2* __restrict__ Yb = A.Yv + p.voff;
+#pragma unroll 2
     for (int e = threadIdx.x; e < N; e += BT) {
         double dv;
         if (newdir) {
-            dv = cG * G[e];
+            float h = 0.f, l = 0.f;
             for (int q = 0; q < M; q++) {
-                const double cy = coef[q], cs = coef[MAX_LBFGS_M + q];
-                if (cy != 0.0) dv += cy * A.Yv[(int64_t)q * A.Ntot + p.voff + e];
-                if (cs != 0.0) dv += cs * A.Sv[(int64_t)q * A.Ntot + p.voff + e];
+                if (coef[q] != 0.0) dd_fma(coefp[q], Yb[(int64_t)q * A.Ntot + e], h, l);
+                if (coef[MAX_LBFGS_M + q] != 0.0) dd_fma(coefp[MAX_LBFGS_M + q], Sb[(int64_t)q * A.Ntot + e], h, l);
             }
+            dv = fma(cG, G[e], dd_value(h, l));
             d[e] = dv;
         } else {
             dv = d[e];
@@ -548,10 +621,10 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
         xt[e] = vv;
         if (e < p.m) {
             apos = fmaxf(apos, prep_row(vv, A.rowA + p.roff + e));
-            A.rowfx[p.roff + e] = 0ull;
+            rowfx[p.roff + e] = 0ull;
         } else {
             bpos = fmaxf(bpos, prep_col(true, vv, A.B2 + p.bcoff + (e - p.m)));
-            A.colfx[p.coff + (e - p.m)] = 0ull;
+            colfx[p.coff + (e - p.m)] = 0ull;
         }
     }
     store_scale(apos, bpos, k, p, A.gamma, A.pfx, shm);
@@ -677,10 +750,11 @@ static bool batch_init(Handle* h)
     B->d = (double*)al(vb, "d");
     B->xt = (double*)al(vb, "xt");
     B->Gt = (double*)al(vb, "Gt");
-    B->Sv = (double*)al(vb * B->M, "S");
-    B->Yv = (double*)al(vb * B->M, "Y");
+    B->Sv = (float2*)al(vb * B->M, "S");  // 8 bytes per entry: a float pair
+    B->Yv = (float2*)al(vb * B->M, "Y");
+    B->Gp = (float2*)al(vb, "G pairs");
     if (!B->S || !B->bc || !B->pactive || !B->res || !B->x || !B->G || !B->d || !B->xt || !B->Gt || !B->Sv ||
-        !B->Yv)
+        !B->Yv || !B->Gp)
         return false;
     if (!h->ck(cudaMallocHost(&B->hbc, 2 * sizeof(BCtl)), "cudaMallocHost")) {
         B->hbc = nullptr;
@@ -713,7 +787,7 @@ static BStepArgs step_args(Handle* h, Batch* B, double tol, double rtol, int max
     a.kerr = h->kerr;
     a.a_sorted = h->a_sorted;
     a.b = h->b;
-    a.x = B->x; a.G = B->G; a.d = B->d; a.xt = B->xt; a.Gt = B->Gt; a.Sv = B->Sv; a.Yv = B->Yv;
+    a.x = B->x; a.G = B->G; a.d = B->d; a.xt = B->xt; a.Gt = B->Gt; a.Sv = B->Sv; a.Yv = B->Yv; a.Gp = B->Gp;
     a.Ntot = B->Ntot;
     a.M = B->M;
     a.rowA = h->rowA;

@@ -138,13 +138,14 @@ def warm_state(B: GroupSparseOTBatch, preds, shift_iters=20):
         al = torch.cat([a for a, _ in preds]).contiguous()
         be = torch.cat([b for _, b in preds]).contiguous()
     D, _ = B.grad(al, be, with_grad=False)
-    if shift_iters > 0 and not bool((D > 0.0).all()):
+    used = D.cpu().numpy() > 0.0
+    if shift_iters > 0 and not used.all():
         B.shift(al, be, shift_iters)
         D, _ = B.grad(al, be, with_grad=False)
-    used = (D > 0.0).cpu().numpy()
-    for k in range(B.nprob):
-        if not used[k]:
-            B.split(al, k, "alpha").zero_()
-            bb = be[B.col_off[k]:B.col_off[k + 1]]
-            bb.zero_()
+        used = D.cpu().numpy() > 0.0
+    if not used.all():
+        keep_r = torch.from_numpy(np.repeat(used, np.diff(B.row_off))).to(al.device)
+        keep_c = torch.from_numpy(np.repeat(used, np.diff(B.col_off))).to(be.device)
+        al = torch.where(keep_r, al, torch.zeros_like(al))
+        be = torch.where(keep_c, be, torch.zeros_like(be))
     return al, be, used
