@@ -431,6 +431,68 @@ def warm_report(args, dev):
     return out
 
 
+def sweep_report(args, dev):
+    """Paper-shaped trends (Sec. 5, synthetic set with controlled classes):
+    time of the screened solver (Alg. 1, with the set N) against the dense
+    one, both from zero to ||grad D||_inf <= tol, summed over rho for each
+    gamma (the paper's protocol), for growing numbers of classes |L| at g = 10
+    (Fig. 2), growing class sizes g at |L| = 10 (appendix), and with / without
+    the lower bound (appendix ablation)."""
+    import torch
+    import paper_2303_07597_gb300 as pk
+
+    def solve_time(p, gamma, rho, screening, lower):
+        g2, mu2 = pk.rho_to_gamma_mu(gamma, rho)
+        C = torch.from_numpy(p.C).to(dev)
+        a = torch.from_numpy(p.a).to(dev)
+        b = torch.from_numpy(p.b).to(dev)
+        lab = torch.from_numpy(p.labels).to(dev)
+        s = pk.GroupSparseOT(C, a, b, lab, p.L, g2, mu2)
+        s.set_params(use_screening=int(screening), use_lower_bound=int(lower))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = s.solve(tol=args.sweep_tol, maxit=args.sweep_maxit)
+        el = time.perf_counter() - t0
+        sol = s.solution()
+        stats = s.stats()
+        s.close()
+        return el, st, sol["D"], stats
+
+    def gain(p, gammas, rhos, lower=True):
+        rows = []
+        for gm in gammas:
+            td = ts = 0.0
+            same = True
+            skipped = total = 0
+            for rho in rhos:
+                e1, st1, D1, _ = solve_time(p, gm, rho, False, True)
+                e2, st2, D2, stt = solve_time(p, gm, rho, True, lower)
+                td += e1
+                ts += e2
+                same = same and abs(D1 - D2) <= 1e-9 * max(1.0, abs(D1))
+                skipped += stt["blocks_skipped"]
+                total += stt["blocks_total"]
+            rows.append({"gamma": gm, "dense_s": td, "screened_s": ts, "gain": td / ts, "same_D": same,
+                         "skipped_frac": skipped / max(1, total)})
+        return rows
+
+    gammas = [float(x) for x in args.sweep_gammas.split(",")]
+    rhos = [float(x) for x in args.sweep_rhos.split(",")]
+    out = {"protocol": f"tol {args.sweep_tol}, maxit {args.sweep_maxit}, time summed over rho in {rhos}",
+           "classes": [], "class_size": [], "lower_bound": []}
+    for L in [int(x) for x in args.sweep_classes.split(",")]:
+        p = synth.paper_synthetic(L, g=10, seed=args.seed)
+        out["classes"].append({"L": L, "m": p.m, "rows": gain(p, gammas, rhos)})
+    for gsz in [int(x) for x in args.sweep_sizes.split(",")]:
+        p = synth.paper_synthetic(10, g=gsz, seed=args.seed)
+        out["class_size"].append({"g": gsz, "m": p.m, "rows": gain(p, gammas, rhos)})
+    for L in [int(x) for x in args.sweep_ablation.split(",")]:
+        p = synth.paper_synthetic(L, g=10, seed=args.seed)
+        out["lower_bound"].append({"L": L, "with": gain(p, gammas, rhos, True),
+                                   "without": gain(p, gammas, rhos, False)})
+    return out
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -615,9 +677,23 @@ def main():
     ap.add_argument("--warm-train", type=int, default=4096)
     ap.add_argument("--warm-test", type=int, default=512)
     ap.add_argument("--warm-steps", type=int, default=8000)
+    ap.add_argument("--sweep", action="store_true",
+                    help="only the paper-shaped trends (screened vs dense over classes, class sizes, lower bound)")
+    ap.add_argument("--sweep-classes", default="10,40,160,640,1280")
+    ap.add_argument("--sweep-sizes", default="10,40,160")
+    ap.add_argument("--sweep-ablation", default="10,640")
+    ap.add_argument("--sweep-gammas", default="100,1,0.01")
+    ap.add_argument("--sweep-rhos", default="0.2,0.8")
+    ap.add_argument("--sweep-tol", type=float, default=1e-7)
+    ap.add_argument("--sweep-maxit", type=int, default=3000)
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.sweep:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"sweep": sweep_report(args, torch.device("cuda", 0))}))
+        return 0
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -222,6 +222,22 @@ OTGS_API const char *ot_gs_version(void);
 OTGS_API int ot_gs_plan_info(const int32_t *labels_host, int64_t m, int64_t n, int32_t L,
                     int64_t *n_panels, int64_t *n_items, int64_t *n_stages);
 
+/*
+ * Downstream use of a solution (single-problem handles).
+ * ot_gs_plan: the transport plan at (alpha, beta), t = grad psi (Sec. 2.3,
+ * Eq. 5): t_ij = s_lj [alpha_i + beta_j - c_ij]_+ with s_lj = [z - mu gamma]_+
+ * / (gamma z) of the block's positive part.  alpha: device FP64 [m] (caller
+ * order), beta: device FP64 [n]; T: device FP32, m x n, row i (caller order)
+ * at T + i*ldt (ldt >= n).  f is formed in FP64.
+ * ot_gs_barycentric: the mapping of Sec. 2.1, out = n T^T X_S (device FP32,
+ * n x d row-major): target sample j's image is n sum_i t_ij x_i; XS: device
+ * FP32 m x d row-major (caller row order).  Uses m x n FP32 of scratch.
+ * Both synchronise.  Errors: OTGS_EINVAL, OTGS_ENOMEM, OTGS_ECUDA.
+ */
+OTGS_API int ot_gs_plan(ot_gs *h, const double *alpha, const double *beta, float *T, int64_t ldt);
+OTGS_API int ot_gs_barycentric(ot_gs *h, const double *alpha, const double *beta, const float *XS, int32_t d,
+                               float *out);
+
 /* ------------------------------------------------------------------------
  * Batches: many independent problems in one handle.  The paper solves one
  * problem at a time; a batch evaluates all of its problems with one launch of

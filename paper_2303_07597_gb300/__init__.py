@@ -88,6 +88,8 @@ def lib():
         "ot_gs_plan_info": ([P, i64, i64, i32, P, P, P], ctypes.c_int),
         "ot_gs_grad_noalloc": ([P, i64, P, P, P, i64, i64, i32, dbl, dbl, P, P, P, P], ctypes.c_int),
         "ot_gs_noalloc_last_error": ([], ctypes.c_char_p),
+        "ot_gs_plan": ([P, P, P, P, i64], ctypes.c_int),
+        "ot_gs_barycentric": ([P, P, P, P, i32, P], ctypes.c_int),
         "ot_gs_create_batch": ([ctypes.POINTER(P), i32, P, P, P, P, P, P, P, P, dbl, dbl, P], ctypes.c_int),
         "ot_gs_batch_size": ([P, P, P, P], ctypes.c_int),
         "ot_gs_batch_grad": ([P, P, P, P, P], ctypes.c_int),
@@ -514,6 +516,27 @@ class GroupSparseOT:
 
     def trace(self):
         return ot_gs_get_trace(self.h)
+
+    def plan(self, alpha, beta, out=None):
+        """Transport plan t = grad psi at (alpha, beta): (m, n) FP32 (Sec. 2.3)."""
+        import torch
+        if out is None:
+            out = torch.empty(self.m, self.n, dtype=torch.float32, device=self.device)
+        _check(self.h, lib().ot_gs_plan(self.h, _ptr(alpha, torch.float64, self.m, "alpha"),
+                                        _ptr(beta, torch.float64, self.n, "beta"),
+                                        ctypes.c_void_p(out.data_ptr()), out.stride(0)))
+        return out
+
+    def barycentric(self, alpha, beta, XS):
+        """n T^T X_S (Sec. 2.1): (n, d) FP32 images of the target samples."""
+        import torch
+        d = XS.shape[1]
+        out = torch.empty(self.n, d, dtype=torch.float32, device=self.device)
+        _check(self.h, lib().ot_gs_barycentric(self.h, _ptr(alpha, torch.float64, self.m, "alpha"),
+                                               _ptr(beta, torch.float64, self.n, "beta"),
+                                               _ptr(XS, torch.float32, self.m * d, "XS"), d,
+                                               _ptr(out, torch.float32, self.n * d, "out")))
+        return out
 
     def stats(self):
         return ot_gs_get_stats(self.h)

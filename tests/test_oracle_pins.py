@@ -337,3 +337,17 @@ def test_screened_solve_matches_dense(use_lower):
         assert r1["iters"] == r0["iters"]
         assert np.array_equal(r1["trace"], r0["trace"])
     assert r1["skipped"] > 0.5 * r1["checked"]
+
+
+def test_barycentric_of_constant_features_is_the_constant():
+    """At an optimum the plan's column sums are b_j = 1/n, so n T^T X maps a
+    constant feature vector to itself (Sec. 2.1's mapping is a convex
+    combination per target sample)."""
+    p = synth.tiny(seed=1)
+    o = oracle.Oracle.from_problem(p, 1.0, 0.1)
+    r = o.solve(tol=1e-11, maxit=5000)
+    T = o.plan(r["alpha"], r["beta"])
+    v = np.array([0.3, -2.0, 5.0])
+    X = np.tile(v, (p.m, 1))
+    Xm = p.n * T.T @ X
+    assert np.allclose(Xm, v[None, :], rtol=1e-6, atol=1e-6)
