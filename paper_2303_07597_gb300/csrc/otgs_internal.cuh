@@ -25,10 +25,13 @@ constexpr int ITEM_COLS = NWARPS * TW;  // columns of a work item: 1 KB of each 
 // C streams through a ring of NSTAGES shared-memory stages of STAGE_ROWS rows
 // x ITEM_COLS columns (32 KB) per CTA, loaded by 2D TMA boxes.
 constexpr int STAGE_ROWS = 32;
-constexpr int NSTAGES = 3;
+constexpr int NSTAGES = 2;
 
-// CTAs of the evaluation kernel per SM (each with its own ring).
-constexpr int CTAS_PER_SM = 2;
+// CTAs of the evaluation kernel per SM (each with its own ring).  The
+// consumers' per-stage work, not the bytes in flight, sets the kernel's
+// speed: three CTAs of two stages (24 consumer warps, 72 registers each)
+// beat two of three (16 warps, 96 registers) by 6 %, one of six by 40 %.
+constexpr int CTAS_PER_SM = 3;
 // Consecutive groups are packed into "panels" of whole groups up to a panel
 // height; a larger group is a panel of its own.  A work item is (panel,
 // column chunk of ITEM_COLS).  The height is m * ceil(n / ITEM_COLS) /
