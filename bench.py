@@ -425,9 +425,83 @@ def warm_report(args, dev):
         "warm_shift_ms": (t1 - tp) * 1000.0, "warm_solve_ms": (t2 - t1) * 1000.0,
         "warm_all_reached": bool(st2 == pk.OTGS_OK and np.all(warm["D"] >= Dstar - 1e-6 * np.abs(Dstar))),
         "warm_iters_mean": float(warm["iters"].mean()), "warm_used_frac": float(np.mean(used)),
+        # spread over the problems: iterations and device time at which each stopped
+        "cold_iters_p50_p90_max": [float(np.percentile(cold["iters"], 50)), float(np.percentile(cold["iters"], 90)),
+                                   int(cold["iters"].max())],
+        "warm_iters_p50_p90_max": [float(np.percentile(warm["iters"], 50)), float(np.percentile(warm["iters"], 90)),
+                                   int(warm["iters"].max())],
+        "cold_stop_ms_p50_p90_max": [float(np.percentile(cold["t_ms"], 50)), float(np.percentile(cold["t_ms"], 90)),
+                                     float(cold["t_ms"].max())],
+        "warm_stop_ms_p50_p90_max": [float(np.percentile(warm["t_ms"], 50)), float(np.percentile(warm["t_ms"], 90)),
+                                     float(warm["t_ms"].max())],
         "heldout_rmse_mean": float(np.mean(rmse)),
         "warm_vs_cold": cold_ms / ((t2 - t0) * 1000.0),
     })
+    return out
+
+
+def case_report(args, dev):
+    """One kernel family in isolation, for profiling under ncu (``--case``).
+
+    batch: ``--case-n`` problems of the batched workload's generator solved
+    together from zero for ``--case-iters`` iterations (each trial: k_bgate,
+    k_stream, k_split_finish, k_passb, k_bstep), with one evaluation timed at
+    zero and one at the final iterate.
+    mlp: the warm-start network (input width 144, hidden 256) trained for
+    ``--case-iters`` Adam steps on 65536 random samples in batches of 8192,
+    then 50 more steps timed (three GEMM kernels forward and five backward
+    per step)."""
+    import torch
+    import paper_2303_07597_gb300 as pk
+    out = {"case": args.case}
+    ev = lambda: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+    if args.case == "batch":
+        probs, flat, Cs, As, Bs, Ls = _batch_on_device(args.seed, dev, args.case_n)
+        B = pk.GroupSparseOTBatch(Cs, As, Bs, Ls, [p.L for p in probs], BATCH["gamma"], BATCH["mu"])
+        out.update(problems=args.case_n, c_bytes=int(sum(4 * p.m * p.n for p in probs)), plan=B.plan())
+        za = torch.zeros(B.m, dtype=torch.float64, device=dev)
+        zb = torch.zeros(B.n, dtype=torch.float64, device=dev)
+
+        def eval_ms(a, b, k=10):
+            B.grad(a, b)
+            torch.cuda.synchronize()
+            e0, e1 = ev()
+            e0.record()
+            for _ in range(k):
+                B.grad(a, b, with_grad=False)
+            e1.record()
+            torch.cuda.synchronize()
+            return e0.elapsed_time(e1) / k
+
+        out["eval_at_zero_ms"] = eval_ms(za, zb)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        B.solve(tol=0.0, maxit=args.case_iters)
+        el = time.perf_counter() - t0
+        r = B.result()
+        out.update(iters=args.case_iters, solve_s=el, trials=int(r["evals"].max()),
+                   trial_ms=el * 1e3 / max(1, int(r["evals"].max())),
+                   eval_at_iterate_ms=eval_ms(r["alpha"], r["beta"]))
+        B.close()
+    else:
+        from paper_2303_07597_gb300 import warmstart as ws
+        K, H, nb = 144, 256, 8192
+        rng = np.random.default_rng(args.seed)
+        X = torch.from_numpy(rng.normal(size=(65536, K)).astype(np.float32)).to(dev)
+        t = torch.from_numpy(rng.normal(size=65536).astype(np.float32)).to(dev)
+        net = pk.WarmStartMLP(K, H, max_batch=nb, seed=1)
+        tr = ws.train(net, X, t, steps=args.case_iters, batch=nb)
+        e0, e1 = ev()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(50):
+            net.train_step(X[:nb], t[:nb], 1e-4)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 50
+        flops = 2 * nb * (K * H + H * H + H) * 3  # forward and the two backward products of each layer
+        out.update(steps=args.case_iters, train_step_ms=ms, tflops=flops / ms / 1e9, loss_last=tr[-1])
+        net.close()
     return out
 
 
@@ -686,9 +760,18 @@ def main():
     ap.add_argument("--sweep-rhos", default="0.2,0.8")
     ap.add_argument("--sweep-tol", type=float, default=1e-7)
     ap.add_argument("--sweep-maxit", type=int, default=3000)
+    ap.add_argument("--case", choices=["batch", "mlp"],
+                    help="only one kernel family in isolation (for profiling): the batched solver or the network")
+    ap.add_argument("--case-n", type=int, default=128, help="--case batch: problems")
+    ap.add_argument("--case-iters", type=int, default=300, help="--case batch: iterations; mlp: training steps")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.case:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps(case_report(args, torch.device("cuda", 0))))
+        return 0
     if args.sweep:
         import torch
         torch.cuda.set_device(0)

@@ -536,7 +536,6 @@ __device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, 
     }
     float s = 0.f;
     if (__any_sync(FULLMASK, b.any)) {
-        double psi;
         float psh, psl;
         s = block_scale(b.acc.Sh, b.acc.Sl, A, psh, psl);
         df_add(psi_acc[0], psi_acc[1], psh, psl);
@@ -708,26 +707,46 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
                         need = __ballot_sync(FULLMASK, m8 != 0u);
                         if (!need) continue;  // no row of this stage is needed: the stage is not sent
                     }
-                    uint32_t wmask = 0u;  // lane w < CONSUMERS: rows evaluated by warp w
+                    uint32_t wmask = 0u;   // lane w < CONSUMERS: rows evaluated by warp w (screened)
+                    uint32_t tiles = 0u;
+                    bool tiled = false;
+                    if (screened) {
 #pragma unroll
-                    for (int w = 0; w < CONSUMERS; w++) {
-                        const uint32_t bw = __ballot_sync(FULLMASK, (m8 >> w) & 1u);
-                        if (lane == w) wmask = bw;
+                        for (int w = 0; w < CONSUMERS; w++) {
+                            const uint32_t bw = __ballot_sync(FULLMASK, (m8 >> w) & 1u);
+                            if (lane == w) wmask = bw;
+                        }
+                        // When the needed (row, tile) pairs are sparse, load per 32-column
+                        // tile ([warp][row][TW]; 128-byte rows) instead of whole rows.
+                        tiles = __reduce_add_sync(FULLMASK, (uint32_t)__popc(wmask));
+                        tiled = tiles * 2u <= (uint32_t)__popc(need) * CONSUMERS;
                     }
-                    // When the needed (row, tile) pairs are sparse, load per 32-column
-                    // tile ([warp][row][TW]; 128-byte rows) instead of whole rows.
-                    const uint32_t tiles = __reduce_add_sync(FULLMASK, (uint32_t)__popc(wmask));
-                    const bool tiled = screened && tiles * 2u <= (uint32_t)__popc(need) * CONSUMERS;
+                    const uint32_t abytes = (uint32_t)nr * 16u;
+                    // the item's first stage sent (not necessarily s == 0) carries its beta pairs
+                    const uint32_t cbytes = first ? (uint32_t)IC * 8u : 0u;
+                    const uint32_t cdata = tiled ? tiles * (uint32_t)(TW * 4) : (uint32_t)__popc(need) * ROW_BYTES;
+                    const int y0 = ra - pd.roff;
                     int slot;
                     if (!next_slot(slot)) { ok = false; break; }
-                    if (lane < CONSUMERS) S.rmaskw[slot][lane] = wmask;
-                    if (lane < DESC_WORDS) reinterpret_cast<int*>(&S.hdr[slot].d)[lane] = w0;
+                    // The producer warp shares its SM's issue slots with 24 consumer
+                    // warps, so every instruction between the slot becoming free and
+                    // the tile's copy adds to the stage's latency: the long copy goes
+                    // first, the small ones and the header after it.
                     if (lane == 0) {
-                        const uint32_t abytes = (uint32_t)nr * 16u;
-                        // the item's first stage sent (not necessarily s == 0) carries its beta pairs
-                        const uint32_t cbytes = first ? (uint32_t)IC * 8u : 0u;
-                        const uint32_t cdata = tiled ? tiles * (uint32_t)(TW * 4) : (uint32_t)__popc(need) * ROW_BYTES;
                         mbar_expect(&S.full[slot], cdata + 2u * abytes + cbytes);
+                        if (!tiled && need == FULLMASK) {
+                            tma_box(maps, TMA_BOXES - 1, S.stage[slot], col0, y0, &S.full[slot]);
+                        } else {
+                            // one run of consecutive needed rows at a time
+                            uint32_t rem = tiled ? 0u : need;
+                            while (rem) {
+                                const int a = __ffs(rem) - 1;
+                                const uint32_t x = rem >> a;
+                                const int len = x == FULLMASK ? 32 : __ffs(~x) - 1;
+                                tma_rows(maps, S.stage[slot] + a * IC, col0, y0 + a, len, &S.full[slot]);
+                                rem &= a + len >= 32 ? 0u : ~((1u << (a + len)) - 1u);
+                            }
+                        }
                         bulk_copy(S.rowA[slot], A.rowA + ra, abytes, &S.full[slot]);
                         bulk_copy(S.rowG[slot], A.rowg + ra, abytes, &S.full[slot]);
                         if (first) bulk_copy(S.colB[slot], A.B2 + pd.bcoff + col0, IC * 8u, &S.full[slot]);
@@ -736,16 +755,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
                         hh.nr = nr;
                         hh.flags = first ? H_FIRST : 0;
                         hh.tiled = tiled ? 1 : 0;
-                        // one run of consecutive needed rows at a time
-                        uint32_t rem = tiled ? 0u : need;
-                        while (rem) {
-                            const int a = __ffs(rem) - 1;
-                            const uint32_t x = rem >> a;
-                            const int len = x == FULLMASK ? 32 : __ffs(~x) - 1;
-                            tma_rows(maps, S.stage[slot] + a * IC, col0, ra - pd.roff + a, len, &S.full[slot]);
-                            rem &= a + len >= 32 ? 0u : ~((1u << (a + len)) - 1u);
-                        }
                     }
+                    if (screened && lane < CONSUMERS) S.rmaskw[slot][lane] = wmask;
+                    if (lane < DESC_WORDS) reinterpret_cast<int*>(&S.hdr[slot].d)[lane] = w0;
                     __syncwarp();  // the transaction count is registered before the tiles' copies
                     if (tiled && lane < CONSUMERS) {
                         uint32_t rem = wmask;
@@ -754,7 +766,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
                             const int a = __ffs(rem) - 1;
                             const uint32_t x = rem >> a;
                             const int len = x == FULLMASK ? 32 : __ffs(~x) - 1;
-                            tma_tile_rows(maps, dst + a * TW, col0 + lane * TW, ra - pd.roff + a, len, &S.full[slot]);
+                            tma_tile_rows(maps, dst + a * TW, col0 + lane * TW, y0 + a, len, &S.full[slot]);
                             rem &= a + len >= 32 ? 0u : ~((1u << (a + len)) - 1u);
                         }
                     }
