@@ -537,7 +537,11 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
             warp_sums_to<NBASE>(bv, wpart[w]);
         }
         const bool need_dir = !fin;
-        if (need_dir && a == ACT_ACCEPT) {
+        // the pair dots: by enough warps that each lane sums at least two
+        // entries (on small problems the warp trees of 2 x 20 floats cost
+        // more than the entries)
+        const int nwd = min(BW, max(1, (N + 63) / 64));
+        if (need_dir && a == ACT_ACCEPT && w < nwd) {
             for (int q0 = 0; q0 < M; q0 += SLOT_GROUP) {
                 float ph[SLOT_GROUP * NPAIR], pl[SLOT_GROUP * NPAIR];
 #pragma unroll
@@ -545,7 +549,7 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
                 const float2* __restrict__ Sb = A.Sv + (int64_t)q0 * A.Ntot + p.voff;
                 const float2* __restrict__ Yb = A.Yv + (int64_t)q0 * A.Ntot + p.voff;
 #pragma unroll 2
-                for (int e = threadIdx.x; e < N; e += BT) {
+                for (int e = threadIdx.x; e < N; e += nwd * 32) {
                     const float2 sn = s_new[e], yn = y_new[e], g = gp[e];
 #pragma unroll
                     for (int u = 0; u < SLOT_GROUP; u++) {
@@ -573,23 +577,29 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
         const int nv = NBASE + (a == ACT_ACCEPT ? NPAIR * M : 0);
         for (int c = threadIdx.x; c < NBASE + NPAIR * MAX_LBFGS_M; c += BT) {
             double t = 0.0;
-            if (c < nv)
-                for (int q = 0; q < BW; q++) t += wpart[q][c];
+            if (c < nv) {
+                const int nq = c < NBASE ? BW : nwd;
+                for (int q = 0; q < nq; q++) t += wpart[q][c];
+            }
             red[c] = t;
         }
         __syncthreads();
-        // 4. the direction (one thread)
-        if (threadIdx.x == 0) {
+        // 4. the direction (one warp)
+        if (w == 0) {
             lbfgs_direction(S, SYs, YYs, red, reinterpret_cast<const double(*)[NPAIR]>(red + NBASE), M,
-                            a == ACT_START);
-            for (int q = 0; q < MAX_LBFGS_M; q++) {
-                coef[q] = S->cy[q];
-                coef[MAX_LBFGS_M + q] = S->cs[q];
-                coefp[q] = dsplit(S->cy[q]);
-                coefp[MAX_LBFGS_M + q] = dsplit(S->cs[q]);
+                            a == ACT_START, lane);
+            static_assert(MAX_LBFGS_M <= 32, "one lane per history slot");
+            if (lane < MAX_LBFGS_M) {
+                const double cy = S->cy[lane], cs = S->cs[lane];
+                coef[lane] = cy;
+                coef[MAX_LBFGS_M + lane] = cs;
+                coefp[lane] = dsplit(cy);
+                coefp[MAX_LBFGS_M + lane] = dsplit(cs);
             }
-            coef[2 * MAX_LBFGS_M] = S->cG;
-            coef[2 * MAX_LBFGS_M + 1] = S->t;
+            if (lane == 0) {
+                coef[2 * MAX_LBFGS_M] = S->cG;
+                coef[2 * MAX_LBFGS_M + 1] = S->t;
+            }
         }
         __syncthreads();
     } else if (fin) {

@@ -34,19 +34,21 @@ constexpr int NSTAGES = 2;
 constexpr int CTAS_PER_SM = 3;
 // Consecutive groups are packed into "panels" of whole groups up to a panel
 // height; a larger group is a panel of its own.  A work item is (panel,
-// column chunk of ITEM_COLS).  The height is m * ceil(n / ITEM_COLS) /
-// TARGET_ITEMS clamped to [MIN_PANEL_ROWS, MAX_PANEL_ROWS]: large problems get
-// tall panels (long TMA streams per item), small ones enough items to fill
-// every SM.
+// column chunk of ITEM_COLS).  The height is the number of (row, column
+// chunk) pairs -- m * ceil(n / ITEM_COLS) for one problem, the sum of that
+// over the problems of a batch -- divided by TARGET_ITEMS and clamped to
+// [MIN_PANEL_ROWS, MAX_PANEL_ROWS]: large problems get tall panels (long TMA
+// streams per item), small ones enough items to fill every SM.
 constexpr int MAX_PANEL_ROWS = 512;
 constexpr int MIN_PANEL_ROWS = 32;
 constexpr int64_t TARGET_ITEMS = 2048;
-inline int32_t panel_rows(int64_t m, int64_t n)
+inline int64_t row_chunks(int64_t m, int64_t n) { return m * ((n + ITEM_COLS - 1) / ITEM_COLS); }
+inline int32_t panel_rows_for(int64_t row_chunk_pairs)
 {
-    const int64_t nch = (n + ITEM_COLS - 1) / ITEM_COLS;
-    const int64_t h = (m * nch + TARGET_ITEMS - 1) / TARGET_ITEMS;
+    const int64_t h = (row_chunk_pairs + TARGET_ITEMS - 1) / TARGET_ITEMS;
     return (int32_t)(h < MIN_PANEL_ROWS ? MIN_PANEL_ROWS : (h > MAX_PANEL_ROWS ? MAX_PANEL_ROWS : h));
 }
+inline int32_t panel_rows(int64_t m, int64_t n) { return panel_rows_for(row_chunks(m, n)); }
 
 // Columns of the per-column float-pair split of beta, padded to whole items.
 inline int32_t padded_cols(int64_t n) { return (int32_t)((n + ITEM_COLS - 1) / ITEM_COLS * ITEM_COLS); }

@@ -84,7 +84,9 @@ std::string build_plan_batch(int32_t nprob, const int32_t* const* labels, const 
 
     // panels: runs of consecutive non-empty groups of one problem, closed
     // before they would exceed the panel height; tall groups in pieces
-    const int32_t PANEL_ROWS = pp.panel_rows > 0 ? pp.panel_rows : panel_rows(m, n);
+    int64_t pairs = 0;  // (row, column chunk) pairs of the problems
+    for (int32_t k = 0; k < nprob; k++) pairs += row_chunks(pm[k], hp.pn[k]);
+    const int32_t PANEL_ROWS = pp.panel_rows > 0 ? pp.panel_rows : panel_rows_for(pairs);
     const int32_t SPLIT = pp.split_rows > 0 ? pp.split_rows : SPLIT_ROWS;
     hp.panel_height = PANEL_ROWS;
     hp.split_height = SPLIT;

@@ -175,8 +175,8 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_pairdots(const SolverState* 
     block_sum<NPAIR>(acc, ppair + ((size_t)k * gridDim.x + blockIdx.x) * NPAIR);
 }
 
-// Sum block partials in block order; then the two-loop recursion on scalars,
-// the descent check, and the start of the next line search.
+// Sum block partials in block order; then (one warp) the two-loop recursion
+// on scalars, the descent check, and the start of the next line search.
 __global__ void __launch_bounds__(SOLVER_THREADS) k_direction(SolverState* S, const double* pbase, const double* ppair,
                                                              int nblocks, int start)
 {
@@ -208,8 +208,8 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_direction(SolverState* S, co
         }
     }
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    lbfgs_direction(S, SY, YY, base, pd, M, start != 0);
+    if (threadIdx.x >= 32) return;
+    lbfgs_direction(S, SY, YY, base, pd, M, start != 0, lane);
 }
 
 // d = cG G + sum_k cy_k y_k + sum_k cs_k s_k

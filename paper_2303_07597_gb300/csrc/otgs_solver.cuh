@@ -91,90 +91,126 @@ __device__ __forceinline__ int ls_update(St* S, double F, double dphi)
     return 0;
 }
 
-// One thread: keeps the new pair (slot S->head) when its curvature is
-// positive enough (unless start), then the two-loop recursion (Nocedal &
-// Wright, Alg. 7.4) on scalars, the descent check and the start of the next
-// line search.  SY, YY: the M x M curvature matrices (shared memory copies of
-// S->SY, S->YY, whose changed rows and columns are written back); base: s.y,
-// s.s, y.y, G.G; pd[k]: the NPAIR dots of slot k.
+// One warp (all 32 lanes): keeps the new pair (slot S->head) when its
+// curvature is positive enough (unless start), then the two-loop recursion
+// (Nocedal & Wright, Alg. 7.4) on scalars, the descent check and the start of
+// the next line search.  SY, YY: the M x M curvature matrices (shared memory
+// copies of S->SY, S->YY, whose changed rows and columns are written back);
+// base: s.y, s.s, y.y, G.G; pd[k]: the NPAIR dots of slot k.
+//
+// Lane u holds the u-th stored pair (oldest first).  Both loops of the
+// recursion are triangular solves: in the first, a_u = rho_u (s_u . G -
+// sum_{v > u} a_v s_u . y_v), newest first; in the second, b_u = rho_u (h0
+// (y_u . G - sum_v a_v y_u . y_v) + sum_{v < u} (a_v - b_v) s_v . y_u),
+// oldest first.  As each a_u (b_u) is found it is broadcast and every lane
+// still waiting takes its term, so the sequential chain is one multiply and
+// one fused multiply-add per pair instead of a whole row of them (the first
+// loop adds its terms newest first, and rho_u multiplies instead of s_u . y_u
+// dividing).
 template <class St>
 __device__ void lbfgs_direction(St* S, double* SY, double* YY, const double* base, const double (*pd)[NPAIR], int M,
-                                bool start)
+                                bool start, int lane)
 {
+    int np = S->npairs, hd = S->head;
     if (!start) {
-        const int head = S->head;
+        const int head = hd;
         const double sy = base[DOT_SY];
         if (sy > 1e-12 * sqrt(base[DOT_SS] * base[DOT_YY])) {
-            for (int k = 0; k < M; k++) {
-                SY[head * M + k] = pd[k][PD_SNEW_Y];  // s_head . y_k
-                SY[k * M + head] = pd[k][PD_S_YNEW];  // s_k . y_head
-                YY[head * M + k] = pd[k][PD_YNEW_Y];
-                YY[k * M + head] = pd[k][PD_YNEW_Y];
+            if (lane < M) {
+                SY[head * M + lane] = pd[lane][PD_SNEW_Y];  // s_head . y_k
+                SY[lane * M + head] = pd[lane][PD_S_YNEW];  // s_k . y_head
+                YY[head * M + lane] = pd[lane][PD_YNEW_Y];
+                YY[lane * M + head] = pd[lane][PD_YNEW_Y];
             }
-            SY[head * M + head] = sy;
-            YY[head * M + head] = base[DOT_YY];
-            for (int k = 0; k < M; k++) {
-                S->SY[head * M + k] = SY[head * M + k];
-                S->SY[k * M + head] = SY[k * M + head];
-                S->YY[head * M + k] = YY[head * M + k];
-                S->YY[k * M + head] = YY[k * M + head];
+            __syncwarp();
+            if (lane == 0) {
+                SY[head * M + head] = sy;
+                YY[head * M + head] = base[DOT_YY];
             }
-            S->head = (head + 1) % M;
-            if (S->npairs < M) S->npairs++;
-        } else if (S->npairs == M) {
-            S->npairs = M - 1;  // the rejected pair overwrote the oldest slot
+            __syncwarp();
+            if (lane < M) {
+                S->SY[head * M + lane] = SY[head * M + lane];
+                S->SY[lane * M + head] = SY[lane * M + head];
+                S->YY[head * M + lane] = YY[head * M + lane];
+                S->YY[lane * M + head] = YY[lane * M + head];
+            }
+            hd = (head + 1) % M;
+            if (np < M) np++;
+        } else if (np == M) {
+            np = M - 1;  // the rejected pair overwrote the oldest slot
         }
     }
-    const int np = S->npairs, hd = S->head;
-    double a[MAX_LBFGS_M], b[MAX_LBFGS_M];
-    int idx[MAX_LBFGS_M];
-    for (int k = 0; k < np; k++) idx[k] = ((hd - np + k) % M + M) % M;  // oldest .. newest
-    // first loop, newest to oldest: a_i = rho_i s_i.q,  q = G - sum_{newer} a_k y_k
+    const bool mine = lane < np;
+    const int i = mine ? ((hd - np + lane) % M + M) % M : 0;  // this lane's slot
+    // rho = 1 / s.y of the lane's pair: every lane's division at once, so that
+    // the chains below hold multiplications only (FP64 division is a long
+    // sequence on this GPU)
+    const double rho = mine ? 1.0 / SY[i * M + i] : 1.0;
+    // first loop, newest to oldest
+    double sq = mine ? pd[i][PD_G_S] : 0.0, a = 0.0;
     for (int u = np - 1; u >= 0; u--) {
-        const int i = idx[u];
-        double sq = pd[i][PD_G_S];
-        for (int v = u + 1; v < np; v++) sq -= a[v] * SY[i * M + idx[v]];
-        a[u] = sq / SY[i * M + i];
+        if (lane == u) a = sq * rho;
+        const double au = __shfl_sync(0xffffffffu, a, u);
+        const int iu = __shfl_sync(0xffffffffu, i, u);
+        if (lane < u) sq -= au * SY[i * M + iu];
     }
     double h0 = 1.0;
     if (np > 0) {
-        const int nw = idx[np - 1];
+        const int nw = ((hd - 1) % M + M) % M;
         h0 = SY[nw * M + nw] / YY[nw * M + nw];
     }
-    // second loop, oldest to newest: b_i = rho_i y_i.r, r = h0 q + sum_{older}(a_k - b_k) s_k
+    // second loop, oldest to newest
+    double yq = mine ? pd[i][PD_G_Y] : 0.0;
+    for (int v = 0; v < np; v++) {
+        const double av = __shfl_sync(0xffffffffu, a, v);
+        const int iv = __shfl_sync(0xffffffffu, i, v);
+        if (mine) yq -= av * YY[i * M + iv];
+    }
+    double yr = h0 * yq, b = 0.0;
     for (int u = 0; u < np; u++) {
-        const int i = idx[u];
-        double yq = pd[i][PD_G_Y];
-        for (int v = 0; v < np; v++) yq -= a[v] * YY[i * M + idx[v]];
-        double yr = h0 * yq;
-        for (int v = 0; v < u; v++) yr += (a[v] - b[v]) * SY[idx[v] * M + i];
-        b[u] = yr / SY[i * M + i];
+        if (lane == u) b = yr * rho;
+        const double cu = __shfl_sync(0xffffffffu, a - b, u);
+        const int iu = __shfl_sync(0xffffffffu, i, u);
+        if (mine && lane > u) yr += cu * SY[iu * M + i];
     }
     // d = -(h0 q + sum (a - b) s) = -h0 G + h0 sum a y - sum (a - b) s
     double cG = -h0;
     double dphi0 = cG * base[DOT_GG];
-    for (int k = 0; k < MAX_LBFGS_M; k++) { S->cy[k] = 0.0; S->cs[k] = 0.0; }
-    for (int u = 0; u < np; u++) {
-        const int i = idx[u];
-        S->cy[i] = h0 * a[u];
-        S->cs[i] = -(a[u] - b[u]);
-        dphi0 += S->cy[i] * pd[i][PD_G_Y] + S->cs[i] * pd[i][PD_G_S];
+    const double cy = h0 * a, cs = -(a - b);
+    for (int u = 0; u < np; u++) {  // every lane, the same sum in the same order
+        const double cyu = __shfl_sync(0xffffffffu, cy, u), csu = __shfl_sync(0xffffffffu, cs, u);
+        const int iu = __shfl_sync(0xffffffffu, i, u);
+        dphi0 += cyu * pd[iu][PD_G_Y] + csu * pd[iu][PD_G_S];
     }
-    if (!(dphi0 < 0.0)) {  // not a descent direction: restart from -G
-        for (int k = 0; k < MAX_LBFGS_M; k++) { S->cy[k] = 0.0; S->cs[k] = 0.0; }
-        S->npairs = 0;
+    const bool descent = dphi0 < 0.0;
+    if (!descent) {  // not a descent direction: restart from -G
+        np = 0;
         cG = -1.0;
         dphi0 = -base[DOT_GG];
     }
-    S->cG = cG;
-    S->dphi0 = dphi0;
-    S->F0 = S->F;
-    const double ginf = S->ginf;
-    S->t = (S->iter == 0 && S->npairs == 0 && ginf > 0.0) ? 1.0 / ginf : 1.0;
-    S->lo = 0.0; S->Flo = S->F; S->dlo = dphi0;
-    S->hi = 0.0; S->Fhi = 0.0; S->dhi = 0.0; S->have_hi = 0;
-    S->ls_evals = 0;
-    S->force_accept = 0;
+    // slot k's coefficients: from the lane that holds slot k, 0 for slots not stored
+    const int uk = ((lane - hd + np) % M + M) % M;  // the position slot k = lane would have
+    const bool held = descent && lane < M && uk < np;
+    const double cyk = __shfl_sync(0xffffffffu, cy, held ? uk : 0);
+    const double csk = __shfl_sync(0xffffffffu, cs, held ? uk : 0);
+    if (lane < MAX_LBFGS_M) {
+        S->cy[lane] = held ? cyk : 0.0;
+        S->cs[lane] = held ? csk : 0.0;
+    }
+    if (lane == 0) {
+        S->head = hd;
+        S->npairs = np;
+        S->cG = cG;
+        S->dphi0 = dphi0;
+        S->F0 = S->F;
+        const double ginf = S->ginf;
+        S->t = (S->iter == 0 && np == 0 && ginf > 0.0) ? 1.0 / ginf : 1.0;
+        S->lo = 0.0; S->Flo = S->F; S->dlo = dphi0;
+        S->hi = 0.0; S->Fhi = 0.0; S->dhi = 0.0; S->have_hi = 0;
+        S->ls_evals = 0;
+        S->force_accept = 0;
+    }
+    __syncwarp();
 }
 
 struct Solver {

@@ -128,9 +128,10 @@ def test_plan_rejects_bad_labels():
 def expected_plan_batch(sizes_list, ns, panel_rows=0, split_rows=0, fill=0):
     """A batch is planned problem by problem (a panel never holds rows of
     two problems, an item never pairs rows with another problem's columns);
-    the default panel height comes from the batch's total rows and columns."""
-    m = sum(int(np.sum(s)) for s in sizes_list)
-    pr = panel_rows or panel_height(m, sum(ns))
+    the default panel height comes from the (row, column chunk) pairs summed
+    over the problems."""
+    pairs = sum(int(np.sum(s)) * -(-n // ITEM_COLS) for s, n in zip(sizes_list, ns))
+    pr = panel_rows or min(512, max(32, -(-pairs // 2048)))
     sr = split_rows or SPLIT_ROWS
     n_panels = n_items = n_stages = 0
     for sizes, n in zip(sizes_list, ns):
