@@ -407,7 +407,7 @@ OTGS_API int ot_gs_mlp_adam(ot_gs_mlp *h, float lr, float beta1, float beta2, fl
  * g_l its size, k the non-empty class whose mean is nearest to y_j (FP32
  * squared distance, terms in index order, ties to the lower class), sm_tau(v)
  * = -tau log mean exp(-v / tau), wl_s = the level L with sum [L - v]_+ =
- * s gamma / m over the row (s gamma / n over the column; by bisection).
+ * s gamma / m over the row (s gamma / n over the column; by Newton steps).
  * C: device FP32 m x n (row stride ldc); XS: device FP32 m x d; XT: device
  * FP32 n x d; labels: device int32 [m] in [0, L); gamma > 0.
  */

@@ -42,7 +42,12 @@ namespace {
 thread_local std::string g_mlp_err;
 
 constexpr int NSTAT = 9;
-constexpr int WL_STEPS = 30;  // bisection steps of a water level (bracket width 2^-30 of its mass)
+// Water levels by Newton's method from the right: f(L) = sum_k [L - v_k]_+ - w
+// is convex, increasing and piecewise linear in L, and f(min + w) >= 0, so
+// from there each step L <- L - f(L) / #{v_k < L} stays at or right of the
+// root and lands on it once it reaches the linear piece that holds it (a few
+// passes over the values instead of a bisection's thirty).
+constexpr int WL_NEWTON_MAX = 32;
 
 // ================================================================ GEMM
 // C[M x N] = A[M x K] . B[N x K]^T, A and B bf16 row-major with K
@@ -309,19 +314,26 @@ __device__ __forceinline__ void cost_stats(const float* v, int64_t stride, int c
     out[1] = (float)(sum / (double)cnt);
     out[2] = mn - 0.02f * logf(e1 / (float)cnt);
     out[3] = mn - 0.1f * logf(e2 / (float)cnt);
-    // sum [L - v]_+ grows with L from 0 at L = min past the mass at min + mass: bisection
     const float mass[3] = {0.5f * w, w, 2.f * w};
 #pragma unroll
     for (int q = 0; q < 3; q++) {
-        float lo = mn, hi = mn + mass[q];
-        for (int it = 0; it < WL_STEPS; it++) {
-            const float mid = 0.5f * (lo + hi);
-            float sum = 0.f;
-            for (int k = 0; k < cnt; k++) sum += fmaxf(mid - v[(int64_t)k * stride], 0.f);
-            if (sum < mass[q]) lo = mid;
-            else hi = mid;
+        float L = mn + mass[q];
+        for (int it = 0; it < WL_NEWTON_MAX; it++) {
+            float sum = 0.f, below = 0.f;
+            for (int k = 0; k < cnt; k++) {
+                const float dl = L - v[(int64_t)k * stride];
+                if (dl > 0.f) {
+                    sum += dl;
+                    below += 1.f;
+                }
+            }
+            const float f = sum - mass[q];
+            if (!(f > 0.f)) break;  // at the root (or just left of it, by rounding)
+            const float Ln = L - f / below;
+            if (!(Ln < L)) break;
+            L = Ln;
         }
-        out[4 + q] = 0.5f * (lo + hi);
+        out[4 + q] = L;
     }
 }
 
@@ -395,15 +407,24 @@ __device__ __forceinline__ void row_stats_warp(const float* v, int cnt, float w,
     const float mass[3] = {0.5f * w, w, 2.f * w};
 #pragma unroll
     for (int q = 0; q < 3; q++) {
-        float lo = mn, hi = mn + mass[q];
-        for (int it = 0; it < WL_STEPS; it++) {
-            const float mid = 0.5f * (lo + hi);
-            float part = 0.f;
-            for (int k = lane; k < cnt; k += 32) part += fmaxf(mid - v[k], 0.f);
-            if (warp_sum(part) < mass[q]) lo = mid;
-            else hi = mid;
+        float L = mn + mass[q];  // Newton from the right, as in cost_stats (the same in every lane)
+        for (int it = 0; it < WL_NEWTON_MAX; it++) {
+            float part = 0.f, below = 0.f;
+            for (int k = lane; k < cnt; k += 32) {
+                const float dl = L - v[k];
+                if (dl > 0.f) {
+                    part += dl;
+                    below += 1.f;
+                }
+            }
+            const float f = warp_sum(part) - mass[q];
+            below = warp_sum(below);
+            if (!(f > 0.f)) break;
+            const float Ln = L - f / below;
+            if (!(Ln < L)) break;
+            L = Ln;
         }
-        out[4 + q] = 0.5f * (lo + hi);
+        out[4 + q] = L;
     }
 }
 

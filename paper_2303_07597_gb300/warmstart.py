@@ -112,13 +112,25 @@ def predict(net: WarmStartMLP, problems, device, in_dim, gamma):
     return out
 
 
-def predict_batch(net: WarmStartMLP, dev_problems, Ls, in_dim, gamma):
+def predict_batch(net: WarmStartMLP, dev_problems, Ls, in_dim, gamma, timings=None):
     """Predicted (alpha, beta) of many problems in the batch layout, from one
     features launch and one pass of the network over all samples.
-    dev_problems: (C, XS, XT, labels) device tensors per problem."""
+    dev_problems: (C, XS, XT, labels) device tensors per problem.  With a
+    dict ``timings``, the device is synchronised after each part and the
+    features and network times (ms) are recorded there."""
+    import time
+    import torch
+    t0 = time.perf_counter()
     F = mlp_features_batch([q[0] for q in dev_problems], [q[1] for q in dev_problems],
                            [q[2] for q in dev_problems], [q[3] for q in dev_problems], Ls, gamma, in_dim)
+    if timings is not None:
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        timings["features_ms"] = (t1 - t0) * 1e3
     y = net.forward(F).double()
+    if timings is not None:
+        torch.cuda.synchronize()
+        timings["network_ms"] = (time.perf_counter() - t1) * 1e3
     M = sum(int(q[0].shape[0]) for q in dev_problems)
     return y[:M].contiguous(), y[M:].contiguous()
 

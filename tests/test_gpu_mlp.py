@@ -96,7 +96,7 @@ def test_features_match_oracle():
     So, To = omlp.features(p.C, XS.astype(np.float32), XT.astype(np.float32), lab, L, 0.8, kpad=K)
     ref = np.concatenate([So, To])
     assert F.shape == ref.shape
-    # stats in FP32 (sums of C in FP64, water levels by 30 bisection steps),
+    # stats in FP32 (sums of C in FP64, water levels by Newton steps),
     # class means rounded from FP64 sums
     assert np.allclose(F[:, :omlp.NSTAT], ref[:, :omlp.NSTAT], rtol=2e-6, atol=2e-7)
     assert np.allclose(F[:, omlp.NSTAT:], ref[:, omlp.NSTAT:], rtol=1e-6, atol=1e-7)
