@@ -661,12 +661,17 @@ def mlp_features_batch(Cs, XSs, XTs, labels, Ls, gamma, in_dim, out=None, stream
     d = XSs[0].shape[1]
     ms = [int(C.shape[0]) for C in Cs]
     ns = [int(C.shape[1]) for C in Cs]
-    for q in range(k):
-        if Cs[q].stride(1) != 1 or Cs[q].dtype != torch.float32:
-            raise ValueError(f"C[{q}] must be float32 with unit column stride")
-        _ptr(XSs[q], torch.float32, ms[q] * d, f"XS[{q}]")
-        _ptr(XTs[q], torch.float32, ns[q] * d, f"XT[{q}]")
-        _ptr(labels[q], torch.int32, ms[q], f"labels[{q}]")
+    f32, i32 = torch.float32, torch.int32
+    for q in range(k):  # (inline checks: this runs for every problem of a batch)
+        C, xs, xt, lb = Cs[q], XSs[q], XTs[q], labels[q]
+        if C.dtype != f32 or C.stride(1) != 1 or not C.is_cuda:
+            raise ValueError(f"C[{q}] must be a CUDA float32 tensor with unit column stride")
+        if xs.dtype != f32 or not xs.is_cuda or not xs.is_contiguous() or xs.numel() != ms[q] * d:
+            raise ValueError(f"XS[{q}] must be a contiguous CUDA float32 tensor of {ms[q] * d} elements")
+        if xt.dtype != f32 or not xt.is_cuda or not xt.is_contiguous() or xt.numel() != ns[q] * d:
+            raise ValueError(f"XT[{q}] must be a contiguous CUDA float32 tensor of {ns[q] * d} elements")
+        if lb.dtype != i32 or not lb.is_cuda or not lb.is_contiguous() or lb.numel() != ms[q]:
+            raise ValueError(f"labels[{q}] must be a contiguous CUDA int32 tensor of {ms[q]} elements")
     if out is None:
         out = torch.empty(sum(ms) + sum(ns), in_dim, dtype=torch.float32, device=Cs[0].device)
     arrs = [_host_array([C.data_ptr() for C in Cs], ctypes.c_void_p),

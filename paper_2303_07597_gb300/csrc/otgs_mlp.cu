@@ -358,11 +358,21 @@ __global__ void __launch_bounds__(256) k_class_means_b(const FeatProb* __restric
         const int l = q / d, c = q % d;
         double s = 0.0;
         int cnt = 0;
-        for (int i = 0; i < p.m; i++)
-            if (p.lab[i] == l) {
-                s += (double)p.XS[(int64_t)i * d + c];
-                cnt++;
-            }
+        // rows in order, eight labels (and their rows' values) loaded ahead
+        for (int i0 = 0; i0 < p.m; i0 += 8) {
+            int lb[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) lb[u] = i0 + u < p.m ? __ldg(p.lab + i0 + u) : -1;
+            float xv[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) xv[u] = lb[u] == l ? __ldg(p.XS + (int64_t)(i0 + u) * d + c) : 0.f;
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+                if (lb[u] == l) {
+                    s += (double)xv[u];
+                    cnt++;
+                }
+        }
         mu[(int64_t)(p.moff + l) * d + c] = cnt ? (float)(s / cnt) : 0.f;
         if (c == 0) gsz[p.moff + l] = cnt;
     }

@@ -98,15 +98,15 @@ __device__ __forceinline__ int ls_update(St* S, double F, double dphi)
 // copies of S->SY, S->YY, whose changed rows and columns are written back);
 // base: s.y, s.s, y.y, G.G; pd[k]: the NPAIR dots of slot k.
 //
-// Lane u holds the u-th stored pair (oldest first).  Both loops of the
-// recursion are triangular solves: in the first, a_u = rho_u (s_u . G -
-// sum_{v > u} a_v s_u . y_v), newest first; in the second, b_u = rho_u (h0
-// (y_u . G - sum_v a_v y_u . y_v) + sum_{v < u} (a_v - b_v) s_v . y_u),
-// oldest first.  As each a_u (b_u) is found it is broadcast and every lane
-// still waiting takes its term, so the sequential chain is one multiply and
-// one fused multiply-add per pair instead of a whole row of them (the first
-// loop adds its terms newest first, and rho_u multiplies instead of s_u . y_u
-// dividing).
+// Lane u holds the u-th stored pair (oldest first).  The first loop, a_u =
+// (s_u . G - sum_{v > u} a_v s_u . y_v) / s_u . y_u newest first, runs on
+// lane 0 over shared-memory copies (each a_u needs every newer one, in that
+// order).  The second, b_u = (h0 (y_u . G - sum_v a_v y_u . y_v) + sum_{v <
+// u} (a_v - b_v) s_v . y_u) / s_u . y_u oldest first, is a triangular solve:
+// every lane forms its first sum at once, and as each b_u is found it is
+// broadcast and the lanes still waiting add their term.  The operations and
+// their order are those of the textbook recursion term by term, so the
+// result does not depend on how the work is spread over the lanes.
 template <class St>
 __device__ void lbfgs_direction(St* S, double* SY, double* YY, const double* base, const double (*pd)[NPAIR], int M,
                                 bool start, int lane)
@@ -142,18 +142,20 @@ __device__ void lbfgs_direction(St* S, double* SY, double* YY, const double* bas
     }
     const bool mine = lane < np;
     const int i = mine ? ((hd - np + lane) % M + M) % M : 0;  // this lane's slot
-    // rho = 1 / s.y of the lane's pair: every lane's division at once, so that
-    // the chains below hold multiplications only (FP64 division is a long
-    // sequence on this GPU)
-    const double rho = mine ? 1.0 / SY[i * M + i] : 1.0;
-    // first loop, newest to oldest
-    double sq = mine ? pd[i][PD_G_S] : 0.0, a = 0.0;
-    for (int u = np - 1; u >= 0; u--) {
-        if (lane == u) a = sq * rho;
-        const double au = __shfl_sync(0xffffffffu, a, u);
-        const int iu = __shfl_sync(0xffffffffu, i, u);
-        if (lane < u) sq -= au * SY[i * M + iu];
-    }
+    __shared__ double a_s[MAX_LBFGS_M];
+    __shared__ int idx_s[MAX_LBFGS_M];
+    if (mine) idx_s[lane] = i;
+    __syncwarp();
+    // first loop, newest to oldest (lane 0)
+    if (lane == 0)
+        for (int u = np - 1; u >= 0; u--) {
+            const int iu = idx_s[u];
+            double sq = pd[iu][PD_G_S];
+            for (int v = u + 1; v < np; v++) sq -= a_s[v] * SY[iu * M + idx_s[v]];
+            a_s[u] = sq / SY[iu * M + iu];
+        }
+    __syncwarp();
+    const double a = mine ? a_s[lane] : 0.0;
     double h0 = 1.0;
     if (np > 0) {
         const int nw = ((hd - 1) % M + M) % M;
@@ -168,7 +170,7 @@ __device__ void lbfgs_direction(St* S, double* SY, double* YY, const double* bas
     }
     double yr = h0 * yq, b = 0.0;
     for (int u = 0; u < np; u++) {
-        if (lane == u) b = yr * rho;
+        if (lane == u) b = yr / SY[i * M + i];
         const double cu = __shfl_sync(0xffffffffu, a - b, u);
         const int iu = __shfl_sync(0xffffffffu, i, u);
         if (mine && lane > u) yr += cu * SY[iu * M + i];
