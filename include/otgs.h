@@ -14,8 +14,8 @@
  *     z = ||[f_[l]]_+||,   psi_[l] = [z - mu gamma]_+^2 / (2 gamma),
  *
  * with the safe skipping of zero blocks (Def. 1, Eq. 6, Lemma 2), the set of
- * surely-nonzero blocks (Def. 2-3, Eq. 7-8) and the driver of Alg. 1 around an
- * L-BFGS loop that runs entirely on the device.
+ * surely-nonzero blocks (Def. 2-3, Eq. 7-8) and the outer loop of Alg. 1 around
+ * an L-BFGS loop that runs entirely on the device.
  *
  * Conventions for every entry point:
  *  - Pointers documented "device" must be device memory of the current CUDA
@@ -141,11 +141,11 @@ OTGS_API int ot_gs_grad_screened(ot_gs *h, const double *alpha, const double *be
                         uint32_t *skip_mask);
 
 /*
- * Refresh the snapshot at (alpha, beta) (Alg. 1, line 15): one dense pass that
+ * Refresh the snapshot at (alpha, beta) (Alg. 1's snapshot update): one dense pass that
  * also stores z~_{l,j} (rounded up to FP32) and o~_{l,j}, and alpha~ = alpha,
  * beta~ = beta.  When build_N != 0 the set N (Def. 3, Eq. 8) is first rebuilt
- * from the lower bound of Eq. 7 against the previous snapshot (Alg. 1, lines
- * 4-14).  Writes D and the gradient to out like ot_gs_grad when out != NULL.
+ * from the lower bound of Eq. 7 against the previous snapshot (Alg. 1's
+ * rebuild of N).  Writes D and the gradient to out like ot_gs_grad when out != NULL.
  */
 OTGS_API int ot_gs_snapshot(ot_gs *h, const double *alpha, const double *beta, int build_N, double *out);
 
@@ -160,7 +160,7 @@ OTGS_API int ot_gs_get_screen_state(ot_gs *h, float *zt, float *ot, double *alph
 
 /*
  * Solve max D with L-BFGS (memory lbfgs_m) and a strong-Wolfe line search,
- * from the handle's current iterate (zero after create, Alg. 1 line 1; or the
+ * from the handle's current iterate (zero after create, as Alg. 1 starts; or the
  * point given to ot_gs_set_state).  With use_screening = 1 each evaluation is
  * screened (Alg. 2) and every r accepted iterations N and the snapshot are
  * rebuilt (Alg. 1).  The whole iteration -- line search, evaluation, the
@@ -368,8 +368,8 @@ OTGS_API int ot_gs_plan_info_batch(int32_t nprob, const int32_t *const *labels_h
 /* ------------------------------------------------------------------------
  * Learned warm start (no counterpart in the paper).  A 3-layer perceptron
  * maps per-sample features of a problem to initial duals; the zero start
- * stays the fallback and the judge (the solve from a warm start must reach
- * the same objective).  Network, for in_dim K and width H (multiples of 16):
+ * stays the fallback and the yardstick (the solve from a warm start must
+ * reach the same objective).  Network, for in_dim K and width H (multiples of 16):
  *   Z1 = q(X) q(W1)^T + b1, A1 = relu(Z1), Z2 = q(A1) q(W2)^T + b2,
  *   A2 = relu(Z2), y = q(A2) q(w3) + b3,
  * q = rounding to bfloat16 (the tensor-core operands; FP32 accumulation).

@@ -339,8 +339,8 @@ static void gradpsi(const orc_t *h, screen_t *sc, const double *alpha, const dou
     free(rowacc); free(colacc); free(npos);
 }
 
-/* Alg. 1 lines 4-14: rebuild N from the lower bound (Eq. 7, Def. 3) against
- * the current snapshot; then line 15: refresh the snapshot at (alpha, beta). */
+/* Alg. 1, every r iterations: rebuild N from the lower bound (Eq. 7, Def. 3)
+ * against the current snapshot, then refresh the snapshot at (alpha, beta). */
 static void rebuild_N_and_snapshot(const orc_t *h, screen_t *sc, const double *alpha,
                                    const double *beta, int use_lower)
 {
@@ -491,8 +491,8 @@ static int line_search(solver_t *s, const double *x, double F0, double dphi0,
 }
 
 /*
- * Solve max D with L-BFGS from the given (alpha, beta) (zero start = Alg. 1
- * line 1).  screening = 1 runs Alg. 1: GradPsi for every evaluation, and
+ * Solve max D with L-BFGS from the given (alpha, beta) (zero start = the
+ * start of Alg. 1).  screening = 1 runs Alg. 1: GradPsi for every evaluation, and
  * every r accepted iterations the set N is rebuilt from Eq. 7 (use_lower = 1)
  * and the snapshot refreshed.  Stops when ||grad D||_inf <= tol.
  *
@@ -524,7 +524,7 @@ EXPORT int orc_solve(const orc_t *h, double *alpha, double *beta, double tol, in
         sc.zt = (double *)malloc(sizeof(double) * (size_t)LN);
         sc.ot = (double *)malloc(sizeof(double) * (size_t)LN);
         sc.inN = (unsigned char *)calloc((size_t)LN, 1);
-        /* Alg. 1 line 1: snapshot at the start point, N empty */
+        /* as Alg. 1 starts: snapshot at the start point, N empty */
         orc_dual(h, x, x + m, NULL, NULL, NULL, sc.zt, sc.ot);
         memcpy(sc.alpha_s, x, sizeof(double) * (size_t)m);
         memcpy(sc.beta_s, x + m, sizeof(double) * (size_t)n);

@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
     }
 }
 
-// Alg. 1 lines 4-14: N from the lower bound against the current snapshot.
+// Alg. 1, every r iterations: N from the lower bound against the current snapshot.
 __global__ void k_build_N(const ScreenArgs S)
 {
     const int64_t u = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
@@ -323,7 +323,7 @@ bool Handle::ensure_screen()
     return true;
 }
 
-// Alg. 1 line 1: the first snapshot is taken at alpha~ = beta~ = 0 with N empty.
+// As Alg. 1 starts: the first snapshot is taken at alpha~ = beta~ = 0 with N empty.
 bool Handle::zero_snapshot()
 {
     cudaMemsetAsync(alpha_snap, 0, sizeof(double) * m, st);

@@ -322,7 +322,7 @@ int Solver::run(double tol, int maxit)
     trace_len = 0;
     if (!h->ck(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st), "state H2D")) return h->last_code;
     k_begin<<<1, 1, 0, st>>>(state);
-    // Alg. 1 line 1: snapshot at the start point, N empty
+    // as Alg. 1 starts: snapshot at the start point, N empty
     if (h->prm.use_screening) {
         h->invalidate_screen();
         if (!h->ensure_screen()) return h->last_code;
