@@ -1,4 +1,4 @@
-// otgs_solver.cuh -- device L-BFGS state and host driver.
+// otgs_solver.cuh -- device L-BFGS state and the host side of the solve.
 #pragma once
 
 #include "otgs_handle.cuh"
