@@ -66,6 +66,24 @@ def _make_workload(name, seed, device):
     return p, C, cfg
 
 
+def max_over_ranks(x, device):
+    """The largest of the ranks' values x (every rank gets it); x itself
+    when no process group runs or it has one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, slowest_ms):
+    """Whole-job throughput: the units every rank processed over the slowest
+    rank's time (replicas of the same work on every rank)."""
+    return units_per_rank * world / (slowest_ms / 1000.0)
+
+
 def _eval_point(C, k):
     """A dual point like those met mid-solve: alpha = 0 and beta_j just above
     the k-th smallest cost of column j, so about k entries of f are positive
@@ -655,11 +673,8 @@ def run_gpu(args):
         torch.cuda.synchronize()
     pk.ot_gs_set_timing(solver.h, False)
     launches, kern_ms = pk.ot_gs_get_timing(solver.h)
-    el_ms = e0.elapsed_time(e1)
+    el_ms = max_over_ranks(e0.elapsed_time(e1), dev)
     if world > 1:
-        t = torch.tensor([el_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        el_ms = float(t.item())
         dist.barrier()
     clocks = cs.summary()
 
@@ -684,15 +699,11 @@ def run_gpu(args):
         step_e2e()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), dev)
 
     if rank == 0:
         m, n = p.m, p.n
-        value = args.steps * world / (el_ms / 1000.0)
+        value = job_throughput(args.steps, world, el_ms)
         kern_avg_s = kern_ms / max(1, launches) / 1000.0
         alg_bytes = 4.0 * m * n + 8.0 * (m + n)
         peak, peak_kind = _peaks()
@@ -718,7 +729,7 @@ def run_gpu(args):
                          "kernel_ms": kern_avg_s * 1000.0,
                          "traffic": _traffic_for(_src_hash(), args.workload)},
             "cpu_baseline": cb,
-            "e2e": {"value": k_e2e * world / (e2e_ms / 1000.0), "unit": UNIT,
+            "e2e": {"value": job_throughput(k_e2e, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (m + n), "d2h_bytes_per_step": 8 * (1 + m + n)},
             "gpu_launches": 5 * args.steps,  # prep, stream, split finish, pass B, reduce
             "clocks": clocks,
