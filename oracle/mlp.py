@@ -24,6 +24,10 @@ in index order; ties to the lower class), softmin_tau over values v is
 with the other side's duals constant, the dual of a sample whose plan row
 sums to its marginal under the squared-L2 regulariser alone.
 
+Second pass (``refine_features``): four more inputs per sample from a first
+prediction, the water levels against the other side's predicted duals and
+the sample's own prediction.
+
 Network (width H): Z1 = q(X) q(W1)^T + b1, A1 = relu(Z1),
 Z2 = q(A1) q(W2)^T + b2, A2 = relu(Z2), y = q(A2) q(w3) + b3, with q the
 round-to-nearest-even conversion to bfloat16 (the tensor-core operands) or
@@ -130,6 +134,36 @@ def features(C, XS, XT, labels, L, gamma, kpad=None):
         T[:, 6 + q] = [water_level(C[:, j], sc * gamma / n) for j in range(n)]
     T[:, NSTAT:NSTAT + d] = XT
     T[:, NSTAT + d:K] = mu[near]
+    return S, T
+
+
+NREF = 4  # second-pass inputs: three water levels against the other side's prediction, the own prediction
+
+
+def refine_features(C, alpha_hat, beta_hat, gamma):
+    """Second-pass inputs of the warm start, given a first prediction
+    (alpha_hat, beta_hat): for source row i, the water levels wl_s of the
+    values c_ij - beta_hat_j over j (masses s gamma / m, s in 0.5, 1, 2) and
+    alpha_hat_i; for target column j, those of c_ij - alpha_hat_i over i
+    (masses s gamma / n) and beta_hat_j.  With the other side's duals fixed
+    at the prediction and the squared-L2 regulariser alone, wl_1 is the dual
+    that makes the sample's plan row (column) sum to its marginal.  Returns
+    (m, 4) and (n, 4) float64 arrays.  The differences are formed from the
+    single-precision inputs (as the kernels read them) and rounded to single
+    precision, as the kernels form them."""
+    C32 = np.asarray(C, dtype=np.float32)
+    ah = np.asarray(alpha_hat, dtype=np.float32)
+    bh = np.asarray(beta_hat, dtype=np.float32)
+    m, n = C32.shape
+    S = np.zeros((m, NREF))
+    T = np.zeros((n, NREF))
+    VS = (C32 - bh[None, :]).astype(np.float64)  # FP32 differences, exactly widened
+    VT = (C32 - ah[:, None]).astype(np.float64)
+    for q, sc in enumerate(WL):
+        S[:, q] = [water_level(VS[i], sc * gamma / m) for i in range(m)]
+        T[:, q] = [water_level(VT[:, j], sc * gamma / n) for j in range(n)]
+    S[:, 3] = ah
+    T[:, 3] = bh
     return S, T
 
 

@@ -199,3 +199,23 @@ def test_gauge_fix_keeps_the_dual_objective():
     D1 = o.dual(al, be)[0]
     D2 = o.dual(a2, b2)[0]
     assert abs(D1 - D2) <= 1e-13 * abs(D1)
+
+
+def test_refine_features_reduce_to_the_base_levels_and_shift_with_the_prediction():
+    """Second-pass inputs: against zero predictions the water levels are the
+    first pass's (the same values, the same masses); a constant prediction k
+    on the other side moves every level by -k (sum [L - (v - k)]_+ = sum
+    [(L + k) - v]_+); the last column is the sample's own prediction."""
+    rng = np.random.default_rng(4)
+    m, n, d, L = 23, 17, 3, 4
+    sizes = np.array([8, 6, 0, 9])
+    XS, XT, lab = synth.mixture_features(sizes, n, d, rng)
+    p = synth.make_problem(XS, XT, lab, L, keep_features=True)
+    S0, T0 = mlp.features(p.C, XS, XT, lab, L, 0.7)
+    Sz, Tz = mlp.refine_features(p.C, np.zeros(m), np.zeros(n), 0.7)
+    assert np.array_equal(Sz[:, :3], S0[:, 6:9]) and np.array_equal(Tz[:, :3], T0[:, 6:9])
+    ah = rng.normal(size=m)
+    Sk, Tk = mlp.refine_features(p.C, ah, np.full(n, 0.375), 0.7)
+    assert np.allclose(Sk[:, :3], S0[:, 6:9] - 0.375, atol=1e-7)
+    assert np.array_equal(Sk[:, 3], ah.astype(np.float32).astype(np.float64))
+    assert np.array_equal(Tk[:, 3], np.full(n, 0.375))
