@@ -389,7 +389,8 @@ def warm_report(args, dev):
     out["solve_targets_s"] = time.perf_counter() - t0
     t0 = time.perf_counter()
     X, t = ws.dataset(train_p, targets, dev, K, g)
-    del targets
+    if args.warm_passes < 2:
+        del targets
     net = pk.WarmStartMLP(K, 256, max_batch=8192, seed=1)
     trace = ws.train(net, X, t, steps=args.warm_steps, batch=8192, lr=1e-3, lr_end=1e-4)
     torch.cuda.synchronize()
@@ -401,6 +402,21 @@ def warm_report(args, dev):
     # inference in chunks of 65536 samples (the training handle's buffers hold 8192)
     infer = pk.WarmStartMLP(K, 256, max_batch=65536, seed=1)
     infer.set_params(net.params())
+    infer2 = None
+    if args.warm_passes >= 2:
+        # a second network on the features plus the second-pass inputs from the first one's prediction
+        t0 = time.perf_counter()
+        X2, t2_ = ws.dataset_refine(train_p, targets, dev, K, g, infer)
+        del targets
+        net2 = pk.WarmStartMLP(K, 256, max_batch=8192, seed=2)
+        trace2 = ws.train(net2, X2, t2_, steps=args.warm_steps, batch=8192, lr=1e-3, lr_end=1e-4)
+        del X2, t2_
+        infer2 = pk.WarmStartMLP(K, 256, max_batch=65536, seed=2)
+        infer2.set_params(net2.params())
+        net2.close()
+        torch.cuda.synchronize()
+        out["train2_s"] = time.perf_counter() - t0
+        out["train2_loss_first_last"] = [trace2[0], trace2[-1]]
     # held out
     B, tt, ref = ws.solve_targets(test_p, dev, g, mu)
     Dstar = ref["D"].copy()
@@ -439,6 +455,33 @@ def warm_report(args, dev):
         rmse.append(float(torch.cat([a - ta, b - tb]).pow(2).mean().sqrt().item()))
     parts = {}
     ws.predict_batch(infer, devp, [p.L for p in test_p], K, g, timings=parts)  # the parts, timed apart
+    if infer2 is not None:
+        Ls = [p.L for p in test_p]
+        ws.warm_state(B, ws.predict_batch_refine(infer, infer2, devp, Ls, K, g))  # untimed first use
+        torch.cuda.synchronize()
+        t3 = time.perf_counter()
+        pal2, pbe2 = ws.predict_batch_refine(infer, infer2, devp, Ls, K, g)
+        al2, be2, used2 = ws.warm_state(B, (pal2, pbe2))
+        B.set_state(al2, be2)
+        torch.cuda.synchronize()
+        t4 = time.perf_counter()
+        st3 = B.solve(tol=0.0, maxit=20000, target_D=Dstar, target_rtol=1e-6)
+        t5 = time.perf_counter()
+        warm2 = B.result(with_iterate=False)
+        rmse2 = []
+        for k, (ta, tb) in enumerate(tt):
+            a, b = ws.gauge_fix(B.split(pal2, k, "alpha"), B.split(pbe2, k, "beta"))
+            rmse2.append(float(torch.cat([a - ta, b - tb]).pow(2).mean().sqrt().item()))
+        out.update({
+            "warm2_ms": (t5 - t3) * 1000.0, "warm2_prepare_ms": (t4 - t3) * 1000.0,
+            "warm2_all_reached": bool(st3 == pk.OTGS_OK and np.all(warm2["D"] >= Dstar - 1e-6 * np.abs(Dstar))),
+            "warm2_iters_mean": float(warm2["iters"].mean()), "warm2_used_frac": float(np.mean(used2)),
+            "warm2_iters_p50_p90_max": [float(np.percentile(warm2["iters"], 50)),
+                                        float(np.percentile(warm2["iters"], 90)), int(warm2["iters"].max())],
+            "heldout_rmse2_mean": float(np.mean(rmse2)),
+            "warm2_vs_cold": cold_ms / ((t5 - t3) * 1000.0),
+        })
+        infer2.close()
     B.close()
     net.close()
     infer.close()
@@ -769,6 +812,9 @@ def main():
     ap.add_argument("--warm-train", type=int, default=4096)
     ap.add_argument("--warm-test", type=int, default=512)
     ap.add_argument("--warm-steps", type=int, default=8000)
+    ap.add_argument("--warm-passes", type=int, default=1, choices=[1, 2],
+                    help="2: also a second network on the second-pass inputs (water levels against the first "
+                         "prediction), solved from its prediction as well")
     ap.add_argument("--sweep", action="store_true",
                     help="only the paper-shaped trends (screened vs dense over classes, class sizes, lower bound)")
     ap.add_argument("--sweep-classes", default="10,40,160,640,1280")

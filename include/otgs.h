@@ -423,6 +423,19 @@ OTGS_API int ot_gs_mlp_features_batch(int32_t nprob, const float *const *C, cons
                                       const int64_t *n, const float *const *XS, const float *const *XT, int32_t d,
                                       const int32_t *const *labels, const int32_t *L, float gamma, int32_t in_dim,
                                       float *out, void *stream);
+/* Second-pass inputs of the warm start (from a first prediction): for
+ * nprob problems (C, ldc, m, n HOST arrays as for ot_gs_mlp_features_batch)
+ * and the first pass's duals alpha_hat (device FP32, sum m, batch layout) and
+ * beta_hat (device FP32, sum n), writes columns [col0, col0 + 4) of every row
+ * of out (device FP32, (sum m + sum n) x in_dim, the layout of
+ * ot_gs_mlp_features_batch; other columns are left as they are): for source
+ * row i, wl_s of the values c_ij - beta_hat_j over the problem's columns
+ * (masses s gamma / m, s = 0.5, 1, 2; differences in FP32) and alpha_hat_i;
+ * for target column j, wl_s of c_ij - alpha_hat_i over its rows (masses
+ * s gamma / n) and beta_hat_j.  Needs 0 <= col0 <= in_dim - 4, gamma > 0. */
+OTGS_API int ot_gs_mlp_refine_features(int32_t nprob, const float *const *C, const int64_t *ldc, const int64_t *m,
+                                       const int64_t *n, const float *alpha_hat, const float *beta_hat, float gamma,
+                                       int32_t col0, int32_t in_dim, float *out, void *stream);
 /* Message of the last failure on h (NULL: of the last failed create or features call). */
 OTGS_API const char *ot_gs_mlp_last_error(const ot_gs_mlp *h);
 

@@ -113,6 +113,7 @@ def lib():
         "ot_gs_mlp_features": ([P, i64, i64, i64, P, P, i32, P, i32, ctypes.c_float, i32, P, P], ctypes.c_int),
         "ot_gs_mlp_last_error": ([P], ctypes.c_char_p),
         "ot_gs_mlp_features_batch": ([i32, P, P, P, P, P, P, i32, P, P, ctypes.c_float, i32, P, P], ctypes.c_int),
+        "ot_gs_mlp_refine_features": ([i32, P, P, P, P, P, P, ctypes.c_float, i32, i32, P, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -682,6 +683,31 @@ def mlp_features_batch(Cs, XSs, XTs, labels, Ls, gamma, in_dim, out=None, stream
     Lp = _host_array([int(x) for x in Ls], ctypes.c_int32)
     rc = lib().ot_gs_mlp_features_batch(k, *[a[1] for a in arrs], d, lp[1], Lp[1], float(gamma), int(in_dim),
                                         _ptr(out, torch.float32, out.numel(), "out"), _stream_ptr(stream))
+    _mlp_check(None, rc)
+    return out
+
+
+def mlp_refine_features(Cs, alpha_hat, beta_hat, gamma, col0, out, stream=None):
+    """Second-pass inputs (see ot_gs_mlp_refine_features): columns [col0,
+    col0 + 4) of out, the features of the problems Cs in the batch layout,
+    from a first prediction alpha_hat (sum m) and beta_hat (sum n), FP32."""
+    import torch
+    ms = [int(C.shape[0]) for C in Cs]
+    ns = [int(C.shape[1]) for C in Cs]
+    for q, C in enumerate(Cs):
+        if C.dtype != torch.float32 or C.stride(1) != 1 or not C.is_cuda:
+            raise ValueError(f"C[{q}] must be a CUDA float32 tensor with unit column stride")
+    M, N = sum(ms), sum(ns)
+    if out.dim() != 2 or out.shape[0] != M + N:
+        raise ValueError(f"out must have {M + N} rows")
+    arrs = [_host_array([C.data_ptr() for C in Cs], ctypes.c_void_p),
+            _host_array([C.stride(0) for C in Cs], ctypes.c_int64), _host_array(ms, ctypes.c_int64),
+            _host_array(ns, ctypes.c_int64)]
+    rc = lib().ot_gs_mlp_refine_features(len(Cs), *[a[1] for a in arrs],
+                                         _ptr(alpha_hat, torch.float32, M, "alpha_hat"),
+                                         _ptr(beta_hat, torch.float32, N, "beta_hat"), float(gamma), int(col0),
+                                         int(out.shape[1]), _ptr(out, torch.float32, out.numel(), "out"),
+                                         _stream_ptr(stream))
     _mlp_check(None, rc)
     return out
 

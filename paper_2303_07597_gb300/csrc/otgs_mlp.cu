@@ -47,6 +47,7 @@ constexpr int NSTAT = 9;
 // from there each step L <- L - f(L) / #{v_k < L} stays at or right of the
 // root and lands on it once it reaches the linear piece that holds it (a few
 // passes over the values instead of a bisection's thirty).
+constexpr int NREF = 4;  // second-pass inputs: three water levels and the own prediction
 constexpr int WL_NEWTON_MAX = 32;
 
 // ================================================================ GEMM
@@ -531,6 +532,107 @@ __global__ void k_features_tgt(const FeatProb* __restrict__ P, int nprob, int64_
     for (int c = NSTAT + 2 * d; c < in_dim; c++) o[c] = 0.f;
 }
 
+// ------------------------------------------------------- second pass
+// Water level of the values v_k - o_k (k < cnt; v at stride `stride`), by
+// the Newton steps of cost_stats, one thread.
+__device__ __forceinline__ float wl_shifted_thread(const float* v, int64_t stride, const float* o, int cnt, float mn,
+                                                   float mass)
+{
+    float L = mn + mass;
+    for (int it = 0; it < WL_NEWTON_MAX; it++) {
+        float sum = 0.f, below = 0.f;
+        for (int k = 0; k < cnt; k++) {
+            const float dl = L - __fsub_rn(v[(int64_t)k * stride], o[k]);
+            if (dl > 0.f) {
+                sum += dl;
+                below += 1.f;
+            }
+        }
+        const float f = sum - mass;
+        if (!(f > 0.f)) break;
+        const float Ln = L - f / below;
+        if (!(Ln < L)) break;
+        L = Ln;
+    }
+    return L;
+}
+
+// The same for one contiguous row, a warp at a time (the same in every lane).
+__device__ __forceinline__ float wl_shifted_warp(const float* v, const float* o, int cnt, float mn, float mass)
+{
+    const int lane = threadIdx.x & 31;
+    float L = mn + mass;
+    for (int it = 0; it < WL_NEWTON_MAX; it++) {
+        float part = 0.f, below = 0.f;
+        for (int k = lane; k < cnt; k += 32) {
+            const float dl = L - __fsub_rn(v[k], o[k]);
+            if (dl > 0.f) {
+                part += dl;
+                below += 1.f;
+            }
+        }
+        const float f = warp_sum(part) - mass;
+        below = warp_sum(below);
+        if (!(f > 0.f)) break;
+        const float Ln = L - f / below;
+        if (!(Ln < L)) break;
+        L = Ln;
+    }
+    return L;
+}
+
+// Second-pass inputs of source rows, one warp each: the water levels of
+// c_ij - beta_hat_j over the problem's columns, and alpha_hat_i, into
+// columns [col0, col0 + 4) of the row's features.
+__global__ void k_refine_src(const FeatProb* __restrict__ P, int nprob, int64_t Mtot, const float* __restrict__ ahat,
+                             const float* __restrict__ bhat, float gamma, int col0, int in_dim, float* out)
+{
+    const int lane = threadIdx.x & 31;
+    const int64_t g = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= Mtot) return;
+    const FeatProb p = P[find_prob(P, nprob, true, g)];
+    const int i = (int)(g - p.roff);
+    const float* v = p.C + (int64_t)i * p.ldc;
+    const float* o = bhat + p.coff;
+    float mn = INFINITY;
+    for (int k = lane; k < p.n; k += 32) mn = fminf(mn, __fsub_rn(v[k], o[k]));
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) mn = fminf(mn, __shfl_xor_sync(FULLMASK, mn, off));
+    const float w = gamma / (float)p.m;
+    const float l0 = wl_shifted_warp(v, o, p.n, mn, 0.5f * w);
+    const float l1 = wl_shifted_warp(v, o, p.n, mn, w);
+    const float l2 = wl_shifted_warp(v, o, p.n, mn, 2.f * w);
+    if (lane == 0) {
+        float* q = out + g * in_dim + col0;
+        q[0] = l0;
+        q[1] = l1;
+        q[2] = l2;
+        q[3] = ahat[g];
+    }
+}
+
+// Second-pass inputs of target columns, one thread each: the water levels
+// of c_ij - alpha_hat_i over the problem's rows, and beta_hat_j.
+__global__ void k_refine_tgt(const FeatProb* __restrict__ P, int nprob, int64_t Mtot, int64_t Ntot,
+                             const float* __restrict__ ahat, const float* __restrict__ bhat, float gamma, int col0,
+                             int in_dim, float* out)
+{
+    const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= Ntot) return;
+    const FeatProb p = P[find_prob(P, nprob, false, g)];
+    const int j = (int)(g - p.coff);
+    const float* v = p.C + j;
+    const float* o = ahat + p.roff;
+    float mn = INFINITY;
+    for (int k = 0; k < p.m; k++) mn = fminf(mn, __fsub_rn(v[(int64_t)k * p.ldc], o[k]));
+    const float w = gamma / (float)p.n;
+    float* q = out + (Mtot + g) * in_dim + col0;
+    q[0] = wl_shifted_thread(v, p.ldc, o, p.m, mn, 0.5f * w);
+    q[1] = wl_shifted_thread(v, p.ldc, o, p.m, mn, w);
+    q[2] = wl_shifted_thread(v, p.ldc, o, p.m, mn, 2.f * w);
+    q[3] = bhat[g];
+}
+
 }  // namespace
 
 // ================================================================ handle
@@ -859,6 +961,55 @@ int ot_gs_mlp_features_batch(int32_t nprob, const float* const* C, const int64_t
     const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         g_mlp_err = std::string("batched features: ") + cudaGetErrorString(e);
+        return OTGS_ECUDA;
+    }
+    return OTGS_OK;
+}
+
+int ot_gs_mlp_refine_features(int32_t nprob, const float* const* C, const int64_t* ldc, const int64_t* m,
+                              const int64_t* n, const float* alpha_hat, const float* beta_hat, float gamma,
+                              int32_t col0, int32_t in_dim, float* out, void* stream)
+{
+    g_mlp_err.clear();
+    if (nprob <= 0 || !C || !ldc || !m || !n || !alpha_hat || !beta_hat || !out || !(gamma > 0.f) || col0 < 0 ||
+        col0 > in_dim - NREF) {
+        g_mlp_err = "invalid second-pass features arguments (0 <= col0 <= in_dim - 4, gamma > 0)";
+        return OTGS_EINVAL;
+    }
+    std::vector<FeatProb> tab(nprob);
+    int64_t M = 0, N = 0;
+    for (int32_t k = 0; k < nprob; k++) {
+        if (!C[k] || m[k] <= 0 || n[k] <= 0 || ldc[k] < n[k]) {
+            g_mlp_err = "invalid problem " + std::to_string(k);
+            return OTGS_EINVAL;
+        }
+        FeatProb& p = tab[k];
+        p = FeatProb{};
+        p.C = C[k]; p.ldc = ldc[k];
+        p.m = (int32_t)m[k]; p.n = (int32_t)n[k];
+        p.roff = (int32_t)M; p.coff = (int32_t)N;
+        M += m[k];
+        N += n[k];
+        if (M > INT32_MAX / 2 || N > INT32_MAX / 2) {
+            g_mlp_err = "batch too large";
+            return OTGS_EINVAL;
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    FeatProb* dtab = nullptr;
+    if (cudaMallocAsync(&dtab, sizeof(FeatProb) * (size_t)nprob, st) != cudaSuccess) {
+        cudaGetLastError();
+        g_mlp_err = "cudaMallocAsync failed";
+        return OTGS_ENOMEM;
+    }
+    cudaMemcpyAsync(dtab, tab.data(), sizeof(FeatProb) * (size_t)nprob, cudaMemcpyHostToDevice, st);
+    k_refine_src<<<(int)((M + 7) / 8), 256, 0, st>>>(dtab, nprob, M, alpha_hat, beta_hat, gamma, col0, in_dim, out);
+    k_refine_tgt<<<(int)((N + 127) / 128), 128, 0, st>>>(dtab, nprob, M, N, alpha_hat, beta_hat, gamma, col0, in_dim,
+                                                          out);
+    cudaFreeAsync(dtab, st);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        g_mlp_err = std::string("second-pass features: ") + cudaGetErrorString(e);
         return OTGS_ECUDA;
     }
     return OTGS_OK;

@@ -16,7 +16,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import GroupSparseOTBatch, WarmStartMLP, mlp_features, mlp_features_batch
+from . import GroupSparseOTBatch, WarmStartMLP, mlp_features, mlp_features_batch, mlp_refine_features
 
 NSTAT = 9
 
@@ -24,6 +24,19 @@ NSTAT = 9
 def in_dim_for(d: int) -> int:
     """Feature width for d-dimensional sample features, rounded up to 16."""
     return (NSTAT + 2 * d + 15) // 16 * 16
+
+
+NREF = 4  # second-pass inputs per sample (three water levels, the own prediction)
+
+
+def col_refine(d: int) -> int:
+    """First feature column of the second-pass inputs."""
+    return NSTAT + 2 * d
+
+
+def in_dim_refine(d: int) -> int:
+    """Feature width with room for the second-pass inputs, rounded up to 16."""
+    return (NSTAT + 2 * d + NREF + 15) // 16 * 16
 
 
 def gauge_fix(alpha, beta):
@@ -85,6 +98,26 @@ def dataset(problems, targets, device, in_dim, gamma):
     return torch.cat(Xs), torch.cat(ts)
 
 
+def dataset_refine(problems, targets, device, in_dim, gamma, net1):
+    """Rows for a second network: each problem's features with the
+    second-pass inputs (water levels against the other side's prediction,
+    the own prediction) from net1's prediction, and the targets of
+    :func:`dataset`."""
+    import torch
+    d = problems[0].XS.shape[1]
+    Xs, ts = [], []
+    for p, (al, be) in zip(problems, targets):
+        F = problem_features(p, device, in_dim, gamma)
+        y = net1.forward(F)
+        C = torch.from_numpy(p.C).to(device)
+        mlp_refine_features([C], y[:p.m].contiguous(), y[p.m:].contiguous(), gamma, col_refine(d), F)
+        Xs.append(F)
+        ta = al - al.mean() + F[:p.m, WL1].double().mean()
+        tb = be - be.mean() + F[p.m:, WL1].double().mean()
+        ts.append(torch.cat([ta, tb]).float())
+    return torch.cat(Xs), torch.cat(ts)
+
+
 def train(net: WarmStartMLP, X, t, steps=2000, batch=4096, lr=1e-3, lr_end=1e-4, seed=0):
     """Adam on random minibatches (learning rate decayed geometrically from lr
     to lr_end); returns the loss trace (one value per 50 steps)."""
@@ -132,6 +165,21 @@ def predict_batch(net: WarmStartMLP, dev_problems, Ls, in_dim, gamma, timings=No
         torch.cuda.synchronize()
         timings["network_ms"] = (time.perf_counter() - t1) * 1e3
     M = sum(int(q[0].shape[0]) for q in dev_problems)
+    return y[:M].contiguous(), y[M:].contiguous()
+
+
+def predict_batch_refine(net1: WarmStartMLP, net2: WarmStartMLP, dev_problems, Ls, in_dim, gamma):
+    """Two passes: net1 on the features, then net2 on the features with the
+    second-pass inputs from net1's prediction (the feature width must leave
+    room for them: :func:`in_dim_refine`)."""
+    F = mlp_features_batch([q[0] for q in dev_problems], [q[1] for q in dev_problems],
+                           [q[2] for q in dev_problems], [q[3] for q in dev_problems], Ls, gamma, in_dim)
+    M = sum(int(q[0].shape[0]) for q in dev_problems)
+    y1 = net1.forward(F)
+    d = int(dev_problems[0][1].shape[1])
+    mlp_refine_features([q[0] for q in dev_problems], y1[:M].contiguous(), y1[M:].contiguous(), gamma,
+                        col_refine(d), F)
+    y = net2.forward(F).double()
     return y[:M].contiguous(), y[M:].contiguous()
 
 

@@ -121,6 +121,39 @@ def test_batched_features_equal_per_problem_features():
         co += p.n
 
 
+def test_refine_features_match_oracle_and_touch_only_their_columns():
+    """Second-pass inputs of a batch of two problems against the oracle, from
+    a random first prediction: water levels against the other side's
+    prediction (FP32 differences, Newton steps) and the own prediction; the
+    other columns of the features keep their values."""
+    problems = [synth.large(seed=s, m=m, n=n, L=L, d=4, keep_features=True)
+                for s, (m, n, L) in enumerate([(45, 38, 4), (30, 61, 3)])]
+    K = ws.in_dim_refine(4)
+    col0 = ws.col_refine(4)
+    devp = [(torch.from_numpy(p.C).to(DEV), torch.from_numpy(np.ascontiguousarray(p.XS, dtype=np.float32)).to(DEV),
+             torch.from_numpy(np.ascontiguousarray(p.XT, dtype=np.float32)).to(DEV),
+             torch.from_numpy(p.labels).to(DEV)) for p in problems]
+    F = pk.mlp_features_batch([q[0] for q in devp], [q[1] for q in devp], [q[2] for q in devp],
+                              [q[3] for q in devp], [p.L for p in problems], 0.9, K)
+    F0 = F.clone()
+    rng = np.random.default_rng(11)
+    M, N = sum(p.m for p in problems), sum(p.n for p in problems)
+    ah = rng.normal(0.2, 0.3, M).astype(np.float32)
+    bh = rng.normal(-0.1, 0.3, N).astype(np.float32)
+    pk.mlp_refine_features([q[0] for q in devp], torch.from_numpy(ah).to(DEV), torch.from_numpy(bh).to(DEV), 0.9,
+                           col0, F)
+    keep = [c for c in range(K) if not col0 <= c < col0 + omlp.NREF]
+    assert torch.equal(F[:, keep], F0[:, keep])
+    G = F.cpu().numpy()
+    ro, co = 0, M
+    for p in problems:
+        So, To = omlp.refine_features(p.C, ah[ro:ro + p.m], bh[co - M:co - M + p.n], 0.9)
+        assert np.allclose(G[ro:ro + p.m, col0:col0 + 4], So, rtol=2e-6, atol=2e-7)
+        assert np.allclose(G[co:co + p.n, col0:col0 + 4], To, rtol=2e-6, atol=2e-7)
+        ro += p.m
+        co += p.n
+
+
 def test_training_lowers_the_loss():
     K, H = 32, 64
     rng = np.random.default_rng(8)
