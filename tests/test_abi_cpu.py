@@ -26,6 +26,26 @@ def test_create_rejects_null_without_gpu():
     assert "NULL" in pk.ot_gs_last_error(None)
 
 
+def test_warm_start_entry_points_reject_bad_arguments_without_gpu():
+    """Argument checks of the warm-start entry points run before any device
+    call: they fail with OTGS_EINVAL and a message on a machine without a GPU."""
+    L = pk.lib()
+    P = ctypes.c_void_p
+    one = (ctypes.c_int64 * 1)(1)
+    ptrs = (P * 1)(P(16))
+    fake = P(16)  # never dereferenced: the checks fail first
+    # second-pass inputs: no problems; then columns past in_dim
+    rc = L.ot_gs_mlp_refine_features(0, ptrs, one, one, one, fake, fake, 1.0, 0, 16, fake, None)
+    assert rc == pk.OTGS_EINVAL
+    rc = L.ot_gs_mlp_refine_features(1, ptrs, one, one, one, fake, fake, 1.0, 13, 16, fake, None)
+    assert rc == pk.OTGS_EINVAL and "col0" in L.ot_gs_mlp_last_error(None).decode()
+    # batched features: in_dim below 9 + 2 d
+    lab = (P * 1)(P(16))
+    Ls = (ctypes.c_int32 * 1)(1)
+    rc = L.ot_gs_mlp_features_batch(1, ptrs, one, one, one, ptrs, ptrs, 8, lab, Ls, 1.0, 16, fake, None)
+    assert rc == pk.OTGS_EINVAL and "in_dim" in L.ot_gs_mlp_last_error(None).decode()
+
+
 ITEM_COLS, STAGE_ROWS = 256, 32
 
 
