@@ -46,6 +46,26 @@ def test_warm_start_entry_points_reject_bad_arguments_without_gpu():
     assert rc == pk.OTGS_EINVAL and "in_dim" in L.ot_gs_mlp_last_error(None).decode()
 
 
+def test_create_batch_rejects_bad_arguments_without_gpu():
+    """ot_gs_create_batch checks its host arrays and scalars before it
+    touches a device: no problems, a NULL array, an empty problem, ldc < n and
+    a non-positive gamma all fail with OTGS_EINVAL and a message."""
+    L = pk.lib()
+    P = ctypes.c_void_p
+    h = P()
+    ptr = (P * 1)(P(16))
+    i64 = lambda v: (ctypes.c_int64 * 1)(v)
+    i32 = (ctypes.c_int32 * 1)(2)
+
+    def create(nprob=1, C=ptr, ldc=i64(8), m=i64(4), n=i64(8), gamma=1.0):
+        return L.ot_gs_create_batch(ctypes.byref(h), nprob, C, ldc, ptr, ptr, ptr, m, n, i32, gamma, 0.1, None)
+
+    for kw, word in [(dict(nprob=0), "nprob"), (dict(C=None), "NULL"), (dict(m=i64(0)), "m, n"),
+                     (dict(ldc=i64(4)), "ldc"), (dict(gamma=0.0), "gamma")]:
+        assert create(**kw) == pk.OTGS_EINVAL and not h.value, kw
+        assert word in pk.ot_gs_last_error(None), (kw, pk.ot_gs_last_error(None))
+
+
 ITEM_COLS, STAGE_ROWS = 256, 32
 
 
