@@ -1,4 +1,4 @@
-"""The multi-process side of bench.py on CPU: two ranks over gloo (the
+"""Host logic of bench.py on CPU: the multi-process side over two gloo ranks (the
 benchmark runs one replica per GPU over NCCL; the timing reduction and the
 whole-job throughput are the same host logic)."""
 import os
@@ -55,3 +55,20 @@ def test_single_process_is_its_own_maximum():
     import bench
     assert bench.max_over_ranks(3.5, "cpu") == 3.5
     assert bench.job_throughput(10, 1, 500.0) == pytest.approx(20.0)
+
+
+def test_clock_summary_reads_the_samples_and_the_throttle_reasons(tmp_path):
+    """The clocks record of a bench line: median SM clock of the samples, the
+    largest max clock seen, and every throttle reason that was Active."""
+    sys.path.insert(0, ROOT)
+    import bench
+    path = tmp_path / "clocks.csv"
+    path.write_text("2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "1950, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+                    "2070, 2070, 1200.5, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+                    "garbage line\n")
+    cs = bench.ClockSampler()
+    cs.f = open(path)
+    got = cs.summary()
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
+    assert not path.exists()  # the sample file is removed once read
