@@ -1,6 +1,6 @@
-"""Host logic of bench.py on CPU: the multi-process side over two gloo ranks (the
-benchmark runs one replica per GPU over NCCL; the timing reduction and the
-whole-job throughput are the same host logic)."""
+"""Host logic of bench.py on CPU: the multi-process side over two gloo ranks
+(the benchmark runs one replica per GPU over NCCL; the timing reduction and
+the whole-job throughput are the same host logic), and the clock record."""
 import os
 import socket
 import sys
