@@ -3,11 +3,14 @@
 The network (:class:`WarmStartMLP`, the library's own kernels) maps each
 sample's features (``mlp_features``: cost statistics, its features and its
 class-mean embedding) to its dual variable.  Targets are the solver's own
-solutions with the gauge fixed by mean(alpha) = mean(beta) (D is invariant
-under alpha + k, beta - k).  At solve time the prediction is used only when
-it is better than the zero start (D above D(0, 0) = 0); otherwise the solve
-starts from zero, so the zero-start solver stays the fallback.  Either way
-the solve runs to the same stopping rule and reaches the same objective.
+solutions, each side anchored to the mean of its samples' water levels (D
+depends on alpha_i + beta_j only, so a common level is not learnable; the
+shift search sets it at solve time).  An optional second network also sees
+water levels against the first one's prediction (``mlp_refine_features``).
+At solve time the prediction is used only when it is better than the zero
+start (D above D(0, 0) = 0); otherwise the solve starts from zero, so the
+zero-start solver stays the fallback.  Either way the solve runs to the
+same stopping rule and reaches the same objective.
 
 Tensors are PyTorch CUDA tensors (plumbing); features, network and solves
 run in the library's kernels.
