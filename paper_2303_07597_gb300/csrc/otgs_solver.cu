@@ -4,7 +4,7 @@
 // The two-loop recursion (Nocedal & Wright, Alg. 7.4) only needs dot products
 // of the current gradient G with the stored pairs and of the pairs with each
 // other.  Those come from one multi-dot pass per accepted step; the scalar
-// recursion then runs in one thread and one more pass forms the direction
+// recursion then runs on one warp and one more pass forms the direction
 //   d = cG G + sum_k cy_k y_k + sum_k cs_k s_k.
 // The line search is a state machine in one thread: it reads D and the slope
 // of the trial evaluation, and sets the next trial step, or accepts.  Alg. 1's
