@@ -456,16 +456,22 @@ OTGS_API const char *ot_gs_mlp_last_error(const ot_gs_mlp *h);
  *   labels_host  HOST int32 [m], non-decreasing, values in [0, L)
  *   alpha, beta  device FP64 [m], [n];  out: device FP64 [1 + m + n] as ot_gs_grad
  *   stream       cudaStream_t as void*
- * Inputs are not otherwise validated.  Sizes whose scratch would exceed the
- * static array (about 44 bytes per row, 20 per column, 64 per work item of up
- * to 512 rows x 256 columns, and 5 KB per 256 rows x 256 columns of classes of
- * more than 256 rows: m = n = 2 x 10^4 fits) are
+ * Inputs are not otherwise validated.  The scratch a problem needs is 52
+ * bytes per row, 16 per column (rounded up to a multiple of 256 columns), 128
+ * per work item (a panel of whole classes, up to 512 rows, x 256 columns), 5
+ * KB per 256-row piece x 256 columns of every class taller than 256 rows,
+ * and about 0.6 MB fixed (the list of deferred row-sum passes); the Zipf-class
+ * workload at m = n = 2 x 10^4 needs about 20 MB.  Larger problems are
  * rejected with OTGS_EINVAL before any GPU work; the message says how many
  * bytes were needed.  The first call made on a device looks up the array's
- * device address there (once per device), so that first call should come
- * before any stream capture.  Every call shares the array and leaves the last
- * call's contents in it (the values that must start at zero are cleared by
- * each call); calls that overlap on the GPU race with each other.
+ * device address there (once per device).  Each call uploads its plan with
+ * cudaMemcpyAsync from pageable host memory, which the runtime stages
+ * synchronously: the call returns once its inputs are staged, the host waits
+ * for work already queued on the stream before the copy, and the call must
+ * not be made while the stream is being captured into a CUDA graph.  Every
+ * call shares the array and leaves the last call's contents in it (the values
+ * that must start at zero are cleared by each call); calls that overlap on
+ * the GPU race with each other.
  * Asynchronous with respect to the host.  Errors: OTGS_EINVAL, OTGS_ECUDA;
  * message from ot_gs_noalloc_last_error().
  */

@@ -631,22 +631,22 @@ EXPORT int orc_solve(const orc_t *h, double *alpha, double *beta, double tol, in
  *   skip_out (optional)             L x ntiles words: blocks skipped by Eq. 6
  *   N_out (optional)                L x ntiles words: N rebuilt from Eq. 7
  *   counts[3] (optional)            += in N, checked, skipped
+ *
+ * Pinned against the paper's rule in FP64 (orc_bounds) by
+ * tests/test_oracle_screen_rule.py: every block this rule skips has an FP64
+ * upper bound below theta by at least half the margin, every block whose FP64
+ * bound is below theta by more than the FP32 error bound is skipped, the set
+ * N differs from the FP64 one only within the rounding band of theta, and on
+ * dyadic inputs (every FP32 operation exact) the decisions equal the FP64
+ * rule's except on ties zbar == theta.
  */
-static void xor_tree_f(float *v, int up)
+static void xor_tree_f(float *v)
 {
     float w[32];
     for (int off = 16; off >= 1; off >>= 1) {
         for (int x = 0; x < 32; x++) w[x] = v[x] + v[x ^ off];
         for (int x = 0; x < 32; x++) v[x] = w[x];
     }
-    (void)up;
-}
-
-static float maxf_tree(const float *v)
-{
-    float r = 0.f;
-    for (int x = 0; x < 32; x++) if (v[x] > r) r = v[x];
-    return r;
 }
 
 EXPORT void orc_gpu_screen(const orc_t *h, const double *alpha, const double *beta,
@@ -692,12 +692,12 @@ EXPORT void orc_gpu_screen(const orc_t *h, const double *alpha, const double *be
         fesetround(FE_TONEAREST);
         double sg = sqrt((double)g);
         fesetround(FE_UPWARD);
-        xor_tree_f(pu, 1);
+        xor_tree_f(pu);
         npos[l] = sqrtf(pu[0]);
         sgru[l] = (float)sg;
         fesetround(FE_TONEAREST);
-        xor_tree_f(a2, 0);
-        xor_tree_f(n2, 0);
+        xor_tree_f(a2);
+        xor_tree_f(n2);
         nabs[l] = sqrtf(a2[0]);
         nneg[l] = sqrtf(n2[0]);
         sgrn[l] = (float)sqrt((double)g);

@@ -311,6 +311,10 @@ def ot_gs_grad_noalloc(C, a, b, labels_host, L, gamma, mu, alpha, beta, out, str
     (for callers that cannot allocate); labels_host is a host int32 array of
     non-decreasing labels.  Raises OTGSError on a non-zero status."""
     import torch
+    if not isinstance(C, torch.Tensor) or not C.is_cuda or C.dtype != torch.float32:
+        raise TypeError("C must be a float32 CUDA tensor")
+    if C.dim() != 2 or C.stride(1) != 1:
+        raise ValueError("C must be 2-D with unit column stride")
     m, n = C.shape
     lab = np.ascontiguousarray(labels_host, dtype=np.int32)
     if lab.shape != (m,):

@@ -99,6 +99,7 @@ struct Batch {
     cudaGraphExec_t gexec = nullptr;
     int g_plan = -1;  // generation of the plan the graph was captured with
     double g_tol = -1.0, g_rtol = -1.0, g_ftol = -1.0;
+    double g_gamma = -1.0, g_mu = -1.0;  // regularisation baked into the captured kernels' arguments
     int g_maxit = -1;
     ~Batch();
 };
@@ -829,8 +830,10 @@ static bool enqueue_trials(Handle* h, Batch* B, const BStepArgs& sa, int trials,
 
 static bool capture_graph(Handle* h, Batch* B, double tol, double rtol, int maxit)
 {
+    // the captured arguments hold gamma and mu (theta, 1 / (2 gamma), the
+    // fixed-point bounds), so a change of either needs a new graph
     if (B->gexec && B->g_plan == h->plan_gen && B->g_tol == tol && B->g_rtol == rtol &&
-        B->g_maxit == maxit && B->g_ftol == h->prm.ftol)
+        B->g_maxit == maxit && B->g_ftol == h->prm.ftol && B->g_gamma == h->prm.gamma && B->g_mu == h->prm.mu)
         return true;
     if (B->gexec) {
         cudaGraphExecDestroy(B->gexec);
@@ -858,6 +861,8 @@ static bool capture_graph(Handle* h, Batch* B, double tol, double rtol, int maxi
     B->g_rtol = rtol;
     B->g_maxit = maxit;
     B->g_ftol = h->prm.ftol;
+    B->g_gamma = h->prm.gamma;
+    B->g_mu = h->prm.mu;
     return true;
 }
 

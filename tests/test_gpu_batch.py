@@ -192,3 +192,25 @@ def test_batch_rejects_single_problem_calls():
     assert e.value.code == pk.OTGS_EINVAL
     with pytest.raises(pk.OTGSError):
         pk.ot_gs_solve(B.h, 1e-6, 10)
+
+
+def test_batch_solve_after_changing_mu():
+    """The batched solver's captured trials hold theta = mu gamma and 1 / (2
+    gamma): after set_params changes mu (or gamma) the next solve must use the
+    new values.  Solve, change mu, solve again from zero: D* is the oracle's
+    at the new mu, for every problem."""
+    problems = [synth.random_instance(m, n, L, seed=s, d=3) for m, n, L, s in SOLVE_SHAPES[:3]]
+    gamma, tol = 1.0, 1e-8
+    B = make_batch(problems, gamma, 0.1)
+    assert B.solve(tol=tol, maxit=5000) == pk.OTGS_OK
+    zero_a = torch.zeros(B.m, dtype=torch.float64, device=DEV)
+    zero_b = torch.zeros(B.n, dtype=torch.float64, device=DEV)
+    for g2, mu2 in [(gamma, 0.4), (0.5, 0.4)]:
+        B.set_params(gamma=g2, mu=mu2)
+        B.set_state(zero_a, zero_b)
+        assert B.solve(tol=tol, maxit=5000) == pk.OTGS_OK
+        r = B.result()
+        for k, p in enumerate(problems):
+            ro = oracle.Oracle.from_problem(p, g2, mu2).solve(tol=tol, maxit=5000)
+            assert ro["status"] == "ok"
+            assert abs(r["D"][k] - ro["D"]) <= 1e-9 * abs(ro["D"]), (g2, mu2, k, r["D"][k], ro["D"])

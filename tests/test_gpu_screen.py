@@ -1,7 +1,9 @@
 """Screening on the GPU (Alg. 2, Eq. 6-8) against the oracle: the skip set and
-the set N bit for bit (given the GPU's stored snapshot), skipped blocks safe
-(zero gradient in exact FP64), and screened evaluation == dense evaluation bit
-for bit (Thm. 2)."""
+the set N bit for bit against the oracle's FP32 rule (given the GPU's stored
+snapshot), and against the paper's rule in FP64: every block the GPU skips the
+paper's rule skips, the rest differs only within the FP32 rounding band;
+skipped blocks safe (zero gradient in exact FP64), and screened evaluation ==
+dense evaluation bit for bit (Thm. 2)."""
 import numpy as np
 import pytest
 import torch
@@ -67,8 +69,23 @@ def test_screened_equals_dense_and_skip_set_matches_oracle(name, mk, gamma, mu):
     assert cnt[2] > 0, "expected some skipped blocks"
     # safety (Lemma 2): every skipped block has z <= theta in exact FP64
     _, _, _, z, _ = o.dual(x1[0], x1[1], want_norms=True)
-    bits = np.unpackbits(sk_gpu.view(np.uint8), bitorder="little").reshape(p.L, nt * 32)[:, :p.n]
-    assert (z[bits.astype(bool)] <= o.theta).all()
+    bits = np.unpackbits(sk_gpu.view(np.uint8), bitorder="little").reshape(p.L, nt * 32)[:, :p.n].astype(bool)
+    assert (z[bits] <= o.theta).all()
+    # the paper's rule (Eq. 6 and Alg. 2 in FP64) on the same snapshot: every
+    # block the GPU skips, it skips too; the blocks it skips and the GPU keeps
+    # lie within the FP32 rule's rounding band (directed rounding and margin)
+    zt64 = zt[:, :p.n].astype(np.float64)
+    inN = np.unpackbits(Nm.view(np.uint8), bitorder="little").reshape(p.L, nt * 32)[:, :p.n].astype(bool)
+    D64, ga64, gb64, sk64, _ = o.gradpsi(x1[0], x1[1], als, bes, zt64, inN.astype(np.uint8))
+    assert not (bits & ~sk64).any()
+    missed = sk64 & ~bits
+    zbar, _ = o.bounds(x1[0], x1[1], als, bes, zt64, ot[:, :p.n].astype(np.float64))
+    g = np.bincount(p.labels, minlength=p.L).astype(np.float64)
+    band = np.ldexp(zbar, -21) + np.ldexp(g * zbar.max(), -23)[:, None] + np.ldexp(g, -20)[:, None]
+    assert (zbar[missed] >= o.theta - band[missed]).all()
+    print(f"{name}: paper rule skips {int(sk64.sum())} blocks, GPU {int(bits.sum())}, missed {int(missed.sum())}")
+    # Alg. 2 in FP64 gives the dense result (Thm. 2), which the GPU matches
+    check_grad(out_s, (D64, ga64, gb64), x1[0], x1[1], p.a, p.b, name + " (paper rule)")
 
 
 @pytest.mark.parametrize("name,mk,gamma,mu", CASES[:3])
@@ -83,9 +100,18 @@ def test_N_rebuild_matches_oracle(name, mk, gamma, mu):
     _, _, _, _, Nm = _state(s, p)
     _, N_ref, _ = o.gpu_screen_rule(x1[0], x1[1], als, bes, zt0, ot0, None)
     assert np.array_equal(Nm, N_ref)
+    # against the paper's Eq. 7 in FP64 on the same snapshot: differences only
+    # where the FP64 lower bound is within the FP32 rounding band of theta
+    nt = (p.n + 31) // 32
+    N_gpu = np.unpackbits(Nm.view(np.uint8), bitorder="little").reshape(p.L, nt * 32)[:, :p.n].astype(bool)
+    _, zlow = o.bounds(x1[0], x1[1], als, bes, zt0[:, :p.n].astype(np.float64), ot0[:, :p.n].astype(np.float64))
+    g = np.bincount(p.labels, minlength=p.L).astype(np.float64)
+    diff = N_gpu != (zlow > o.theta)
+    band = np.ldexp(np.abs(zlow) + 4.0, -19) + np.ldexp(g, -18)[:, None]
+    assert (np.abs(zlow[diff] - o.theta) <= band[diff]).all()
+    print(f"{name}: |N| GPU {int(N_gpu.sum())}, FP64 {int((zlow > o.theta).sum())}, differ {int(diff.sum())}")
     # Lemma 4: every block of N has a nonzero gradient block (z > theta)
     _, _, _, z, _ = o.dual(x1[0], x1[1], want_norms=True)
-    nt = (p.n + 31) // 32
     bits = np.unpackbits(Nm.view(np.uint8), bitorder="little").reshape(p.L, nt * 32)[:, :p.n]
     assert (z[bits.astype(bool)] > o.theta).all()
 
