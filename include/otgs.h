@@ -331,8 +331,7 @@ OTGS_API int ot_gs_batch_result(ot_gs *h, double *alpha, double *beta, double *D
  * pieces of this height, summed by different CTAs; stage_fill: 0 = C streams
  * in stages of 32 rows, k > 0 = a stage ends early, before a group of at most
  * 32 rows that would straddle its end, when it keeps at least k rows (such a
- * group's blocks then finish from shared memory, without the second pass of
- * the pass-B kernel).  ot_gs_set_plan rebuilds the handle's plan (0 = the
+ * group's blocks are then bounded within one stage).  ot_gs_set_plan rebuilds the handle's plan (0 = the
  * default of each) and synchronises; valid ranges are [32, 4096], [64, 8192]
  * and [0, 32].  ot_gs_get_plan reports the current shape and the number of
  * work items (host pointers, each may be NULL).
@@ -457,12 +456,12 @@ OTGS_API const char *ot_gs_mlp_last_error(const ot_gs_mlp *h);
  *   alpha, beta  device FP64 [m], [n];  out: device FP64 [1 + m + n] as ot_gs_grad
  *   stream       cudaStream_t as void*
  * Inputs are not otherwise validated.  The scratch a problem needs is 52
- * bytes per row, 16 per column (rounded up to a multiple of 256 columns), 128
- * per work item (a panel of whole classes, up to 512 rows, x 256 columns), 5
- * KB per 256-row piece x 256 columns of every class taller than 256 rows,
- * and about 0.6 MB fixed (the list of deferred row-sum passes); the Zipf-class
- * workload at m = n = 2 x 10^4 needs about 20 MB.  Larger problems are
- * rejected with OTGS_EINVAL before any GPU work; the message says how many
+ * bytes per row, 16 per column (rounded up to a multiple of 256 columns), 64
+ * per work item (a panel of whole classes, up to 512 rows, x 256 columns), 32
+ * per (non-empty class, 32-column tile), and 2 KB per 256-row piece x 256
+ * columns of every class taller than 256 rows; the Zipf-class workload at m
+ * = n = 2 x 10^4 needs about 30 MB.  Larger problems are rejected with
+ * OTGS_EINVAL before any GPU work; the message says how many
  * bytes were needed.  The first call made on a device looks up the array's
  * device address there (once per device).  Each call uploads its plan with
  * cudaMemcpyAsync from pageable host memory, which the runtime stages

@@ -260,9 +260,9 @@ bool Handle::init(int32_t np, const float* const* C_, const int64_t* ldc_, const
     if (!rowA || !B2 || !ctl || !kerr || !alpha_eval || !rowfx || !colfx || !pfx) return false;
     if (!ck(cudaMemsetAsync(B2, 0, sizeof(float2) * (size_t)hp.nb2, st), "memset B2")) return false;
     if (!ck(cudaMemsetAsync(kerr, 0, sizeof(int) * 4, st), "memset err")) return false;
-    passb_cap = (int)std::min<int64_t>(2 * (int64_t)L * ntiles, 1 << 18);
-    passb = (PassB*)dalloc(sizeof(PassB) * (size_t)passb_cap, "pass-B list");
-    if (!passb) return false;
+    psix = (unsigned long long*)dalloc(sizeof(unsigned long long) * 2 * (size_t)np, "psi of the exact-sum kernel");
+    if (!psix) return false;
+    if (!ck(cudaMemsetAsync(psix, 0, sizeof(unsigned long long) * 2 * (size_t)np, st), "memset psix")) return false;
     {
         int dev = 0;
         if (!ck(cudaGetDevice(&dev), "cudaGetDevice")) return false;
@@ -271,7 +271,7 @@ bool Handle::init(int32_t np, const float* const* C_, const int64_t* ldc_, const
     if (!stream_prepare()) return fail(OTGS_ECUDA, "cudaFuncSetAttribute(evaluation kernel)");
     if (!setup_plan(PlanParams())) return false;
     nred = reduce_blocks((int32_t)m, (int32_t)n);
-    block_part = (double*)dalloc(sizeof(double) * 4 * (size_t)nred, "block_part");
+    block_part = (double*)dalloc(sizeof(double) * REDUCE_PARTS * (size_t)nred, "block_part");
     counter = (unsigned*)dalloc(sizeof(unsigned) * 4, "counter");
     scal = (double*)dalloc(sizeof(double) * 8, "scal");
     if (!block_part || !counter || !scal) return false;
@@ -335,9 +335,19 @@ bool Handle::setup_plan(const PlanParams& pp)
     }
     bprob = plan_upload(this, bprob_h, "batch problem table");
     if (!bprob) return false;
-    psipart = (double*)plan_alloc(sizeof(double) * (size_t)hp.nitems() * NWARPS, "psipart");
-    split_part = (float*)plan_alloc(sizeof(float) * 5 * ITEM_COLS * (size_t)hp.nsplit_slots, "split partial sums");
-    if (!psipart || !split_part) return false;
+    split_part =
+        (float*)plan_alloc(sizeof(float) * SPLIT_VALS * ITEM_COLS * (size_t)hp.nsplit_slots, "split partial sums");
+    if (!split_part) return false;
+    {
+        int64_t ce = 0, ct = 0;
+        exact_caps(hp, ce, ct);
+        if (ce > INT32_MAX || ct > INT32_MAX) return fail(OTGS_EINVAL, "too many blocks");
+        xent_cap = (int32_t)ce;
+        xtall_cap = (int32_t)ct;
+        xent = (XEntry*)plan_alloc(sizeof(XEntry) * (size_t)ce, "flagged block sets");
+        xtall = (XEntry*)plan_alloc(sizeof(XEntry) * (size_t)ct, "flagged block sets of tall classes");
+        if (!xent || !xtall) return false;
+    }
     if (screen_alloc) {
         item_active = (uint8_t*)plan_alloc((size_t)hp.nitems(), "item_active");
         stage_m8 = (uint8_t*)plan_alloc((size_t)hp.nstages * STAGE_ROWS, "stage masks");
@@ -370,8 +380,12 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.item_active = active;
     e.unit_need = need;
     e.unit_words = unit_words;
-    e.rowfx = rowfx; e.colfx = colfx; e.psipart = psipart;
-    e.passb = passb; e.passb_cap = passb_cap;
+    e.rowfx = rowfx; e.colfx = colfx;
+    // psi goes to the control word (cleared with it) on the single-problem
+    // paths; the batch paths point it to their per-problem array
+    e.psix = ctl_psi(ctl);
+    e.xent = xent; e.xent_cap = xent_cap;
+    e.xtall = xtall; e.xtall_cap = xtall_cap;
     e.split_part = split_part;
     e.sets = dp.sets; e.nsets = (int32_t)hp.sets.size();
     e.gate = eval_gate;
@@ -384,6 +398,12 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     float fc = (float)cut;
     if ((double)fc > cut) fc = std::nextafter(fc, 0.f);
     e.th2_cut = fc;
+    {
+        const double t2 = theta * theta * (1.0 - std::ldexp(1.0, -21));
+        float ft = (float)t2;
+        if ((double)ft > t2) ft = std::nextafter(ft, 0.f);
+        e.thr_flag = ft;
+    }
     e.gamma = (float)prm.gamma;
     e.inv2g = 1.0 / (2.0 * prm.gamma);
     e.inv2g_hi = (float)e.inv2g;
@@ -400,7 +420,8 @@ ReduceArgs Handle::reduce_args(const uint8_t* active, double* out_caller, double
     r.fx_m = (int32_t)hp.max_m; r.fx_n = (int32_t)hp.max_n;
     r.perm = dp.perm;
     r.item_active = active;
-    r.rowfx = rowfx; r.colfx = colfx; r.psipart = psipart;
+    r.rowfx = rowfx; r.colfx = colfx;
+    r.psix = ctl_psi(ctl);
     r.ctl = ctl;
     r.gamma = (float)prm.gamma;
     r.a_sorted = a_sorted; r.b = b;
@@ -438,7 +459,7 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
         ev_used += 2;
     }
     launch_split_finish(e, st);
-    launch_passb(e, n_sm, st);
+    launch_exact(e, n_sm, st);
 }
 
 // Dense evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.

@@ -10,7 +10,7 @@
 //   k_bgate        opens the trial when some problem is still running,
 //   k_stream       the evaluation of every running problem (finished
 //                  problems' work items are skipped),
-//   k_split_finish, k_passb   as for one problem,
+//   k_split_finish, k_exact   as for one problem,
 //   k_bstep        per problem: the reduction to D, Gt.d and ||Gt||_inf, the
 //                  line-search step, on acceptance the L-BFGS update and the
 //                  new direction (the recursion of Nocedal & Wright, Alg. 7.4),
@@ -68,7 +68,7 @@ struct BStepArgs {
     float gamma;
     unsigned long long* rowfx;
     unsigned long long* colfx;
-    const double* psipart;
+    unsigned long long* psix;        // [nprob][2]: psi of the problem's flagged blocks, fixed point
     const int* kerr;
     const double* a_sorted;
     const double* b;
@@ -146,6 +146,29 @@ __device__ __forceinline__ void cta_sum(double (&v)[NV], double* sh /* [BW * NV]
     for (int k = 0; k < NV; k++) v[k] = out[k];
 }
 
+// The same for integers (exact: the order of the additions does not matter).
+template <int NV>
+__device__ __forceinline__ void cta_sum_ll(long long (&v)[NV], long long* sh /* [BW * NV] */, long long* out)
+{
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < NV; k++) {
+        long long x = v[k];
+#pragma unroll
+        for (int off = 16; off >= 1; off >>= 1) x += __shfl_xor_sync(FULLMASK, x, off);
+        if (lane == 0) sh[w * NV + k] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < NV) {
+        long long s = 0;
+        for (int q = 0; q < BW; q++) s += sh[q * NV + threadIdx.x];
+        out[threadIdx.x] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < NV; k++) v[k] = out[k];
+}
+
 __device__ __forceinline__ double cta_max(double v, double* sh /* [BW] */)
 {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -189,10 +212,12 @@ __device__ __forceinline__ void store_scale(float apos, float bpos, int k, const
 __global__ void __launch_bounds__(BT) k_bprep(const BProb* __restrict__ P, const double* __restrict__ alpha,
                                               const int32_t* __restrict__ perm, const double* __restrict__ beta,
                                               float4* rowA, float2* B2, double* alpha_eval, unsigned long long* rowfx,
-                                              unsigned long long* colfx, FxScale* pfx, float gamma)
+                                              unsigned long long* colfx, FxScale* pfx, float gamma,
+                                              unsigned long long* psix)
 {
     __shared__ unsigned shm[2 * BW];
     const BProb p = P[blockIdx.x];
+    if (threadIdx.x < 2) psix[2 * blockIdx.x + threadIdx.x] = 0ull;
     float apos = 0.f, bpos = 0.f;
     for (int e = threadIdx.x; e < p.m; e += BT) {
         const int r = p.roff + e;
@@ -213,7 +238,7 @@ __global__ void __launch_bounds__(BT) k_breduce(const BProb* __restrict__ P, con
                                                 const FxScale* pfx,
                                                 const unsigned long long* __restrict__ rowfx,
                                                 const unsigned long long* __restrict__ colfx,
-                                                const double* __restrict__ psipart, const int* kerr,
+                                                const unsigned long long* __restrict__ psix, const int* kerr,
                                                 const double* __restrict__ a_sorted, const double* __restrict__ b,
                                                 const double* __restrict__ alpha_eval,
                                                 const double* __restrict__ beta, int64_t m_tot, double* Dout,
@@ -222,7 +247,7 @@ __global__ void __launch_bounds__(BT) k_breduce(const BProb* __restrict__ P, con
     __shared__ double sh[BW * 2], tot[2];
     const BProb p = P[blockIdx.x];
     const FxScale fx = pfx[blockIdx.x];
-    double v[2] = {0.0, 0.0};  // alpha.a + beta.b, psi
+    double v[1] = {0.0};  // alpha.a + beta.b
     for (int e = threadIdx.x; e < p.m; e += BT) {
         const int r = p.roff + e;
         const double ga = a_sorted[r] - (double)(long long)rowfx[r] * fx.from_r;
@@ -235,25 +260,26 @@ __global__ void __launch_bounds__(BT) k_breduce(const BProb* __restrict__ P, con
         if (grad) grad[m_tot + c] = gb;
         v[0] += beta[c] * b[c];
     }
-    for (int64_t q = (int64_t)p.item0 * NWARPS + threadIdx.x; q < (int64_t)p.item1 * NWARPS; q += BT)
-        v[1] += psipart[q];
-    cta_sum<2>(v, sh, tot);
-    if (threadIdx.x == 0 && Dout)
+    cta_sum<1>(v, sh, tot);
+    if (threadIdx.x == 0 && Dout) {
+        const double psi = psi_from_fx((long long)psix[2 * blockIdx.x], (long long)psix[2 * blockIdx.x + 1], fx.from_p);
         Dout[blockIdx.x] = (kerr && *(volatile const int*)kerr) ? __longlong_as_double(0x7ff8000000000000ll)
-                                                                 : v[0] - v[1];
+                                                                 : v[0] - psi;
+    }
 }
 
 bool Handle::eval_batch(const double* alpha, const double* beta, double* D, double* grad)
 {
     if (!ck(cudaMemsetAsync(ctl, 0, sizeof(EvalCtl), st), "memset")) return false;
     k_bprep<<<nprob, BT, 0, st>>>(bprob, alpha, dp.perm, beta, rowA, B2, alpha_eval, rowfx, colfx, pfx,
-                                  (float)prm.gamma);
+                                  (float)prm.gamma, psix);
     EvalArgs e = eval_args(nullptr, nullptr, false);
     e.gate = nullptr;
     e.pfx = pfx;
+    e.psix = psix;  // per problem (k_breduce reads them), even for a batch of one
     eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
-    k_breduce<<<nprob, BT, 0, st>>>(bprob, dp.perm, pfx, rowfx, colfx, psipart, kerr, a_sorted, b, alpha_eval, beta,
-                                    m, D, grad);
+    k_breduce<<<nprob, BT, 0, st>>>(bprob, dp.perm, pfx, rowfx, colfx, psix, kerr, a_sorted, b, alpha_eval,
+                                    beta, m, D, grad);
     count_dense_evals(1);
     return ck(cudaGetLastError(), "batch evaluation launch");
 }
@@ -262,8 +288,9 @@ bool Handle::eval_batch(const double* alpha, const double* beta, double* D, doub
 __global__ void __launch_bounds__(BT) k_binit(const BProb* __restrict__ P, BState* S, int* pactive, const double* x,
                                               double* xt, float4* rowA, float2* B2, unsigned long long* rowfx,
                                               unsigned long long* colfx, FxScale* pfx, float gamma, int M,
-                                              const double* target)
+                                              const double* target, unsigned long long* psix)
 {
+    if (threadIdx.x < 2) psix[2 * blockIdx.x + threadIdx.x] = 0ull;
     __shared__ unsigned shm[2 * BW];
     const int k = blockIdx.x;
     const BProb p = P[k];
@@ -317,10 +344,7 @@ __global__ void k_bgate(BCtl* bc, EvalCtl* ctl)
     const int go = bc->nactive > 0;
     bc->go = go;
     if (!go) return;
-    ctl->work = 0;
-    ctl->amax = 0u;
-    ctl->bmax = 0u;
-    ctl->npassb = 0;
+    ctl_clear(ctl);
 }
 
 __device__ __forceinline__ bool reached(const BState* s, double D, double rtol)
@@ -431,7 +455,7 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
 
     // 1. D, Gt = -grad D, Gt.d and ||Gt||_inf at the trial point
     {
-        double v[4] = {0.0, 0.0, 0.0, 0.0};  // alpha.a + beta.b, Gt.d, psi, ||.||_inf
+        double v[4] = {0.0, 0.0, 0.0, 0.0};  // alpha.a + beta.b, Gt.d, (unused), ||.||_inf
 #pragma unroll 4
         for (int e = threadIdx.x; e < N; e += BT) {
             double g, wt;
@@ -449,24 +473,22 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
             v[1] += -g * d[e];
             v[3] = fmax(v[3], fabs(g));
         }
-        for (int64_t q = (int64_t)p.item0 * NWARPS + threadIdx.x; q < (int64_t)p.item1 * NWARPS; q += BT)
-            v[2] += A.psipart[q];
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) v[3] = fmax(v[3], __shfl_xor_sync(FULLMASK, v[3], off));
-        double sv[3] = {v[0], v[1], v[2]};
-        warp_sums_to<3>(sv, wpart[w]);
+        double sv[2] = {v[0], v[1]};
+        warp_sums_to<2>(sv, wpart[w]);
         if (lane == 0) wpart[w][3] = v[3];
     }
     __syncthreads();
     // 2. the line search (or the start of the solve), one thread
     if (threadIdx.x == 0) {
-        double ab = 0.0, dphi = 0.0, psi = 0.0, inf = 0.0;
+        double ab = 0.0, dphi = 0.0, inf = 0.0;
         for (int q = 0; q < BW; q++) {
             ab += wpart[q][0];
             dphi += wpart[q][1];
-            psi += wpart[q][2];
             inf = fmax(inf, wpart[q][3]);
         }
+        const double psi = psi_from_fx((long long)A.psix[2 * k], (long long)A.psix[2 * k + 1], fx.from_p);
         const double D = (A.kerr && *(volatile const int*)A.kerr) ? __longlong_as_double(0x7ff8000000000000ll)
                                                                   : ab - psi;
         const double F = -D;
@@ -638,6 +660,7 @@ __global__ void __launch_bounds__(BT) k_bstep(const BStepArgs A)
             colfx[p.coff + (e - p.m)] = 0ull;
         }
     }
+    if (threadIdx.x < 2) A.psix[2 * k + threadIdx.x] = 0ull;  // read in step 1 (before the syncs since)
     store_scale(apos, bpos, k, p, A.gamma, A.pfx, shm);
 }
 
@@ -794,7 +817,7 @@ static BStepArgs step_args(Handle* h, Batch* B, double tol, double rtol, int max
     a.gamma = (float)h->prm.gamma;
     a.rowfx = h->rowfx;
     a.colfx = h->colfx;
-    a.psipart = h->psipart;
+    a.psix = h->psix;
     a.kerr = h->kerr;
     a.a_sorted = h->a_sorted;
     a.b = h->b;
@@ -814,6 +837,7 @@ static BStepArgs step_args(Handle* h, Batch* B, double tol, double rtol, int max
 static bool enqueue_trials(Handle* h, Batch* B, const BStepArgs& sa, int trials, cudaStream_t st)
 {
     EvalArgs e = h->eval_args(nullptr, nullptr, false);
+    e.psix = h->psix;  // per problem (k_bstep reads them), even for a batch of one
     e.gate = &B->bc->go;
     e.prob_active = B->pactive;
     e.pfx = h->pfx;
@@ -822,7 +846,7 @@ static bool enqueue_trials(Handle* h, Batch* B, const BStepArgs& sa, int trials,
         k_bgate<<<1, 1, 0, st>>>(B->bc, h->ctl);
         launch_stream(e, n_ctas, st);
         launch_split_finish(e, st);
-        launch_passb(e, h->n_sm, st);
+        launch_exact(e, h->n_sm, st);
         k_bstep<<<B->nprob, BT, 0, st>>>(sa);
     }
     return h->ck(cudaGetLastError(), "batch trial launch");
@@ -892,7 +916,7 @@ static int batch_solve(Handle* h, double tol, int maxit, const double* target_ho
     if (!h->ck(cudaMemcpyAsync(B->bc, &c0, sizeof(c0), cudaMemcpyHostToDevice, st), "control H2D")) return h->last_code;
     if (!h->ck(cudaMemsetAsync(h->kerr, 0, sizeof(int) * 4, st), "memset err")) return h->last_code;
     k_binit<<<B->nprob, BT, 0, st>>>(h->bprob, B->S, B->pactive, B->x, B->xt, h->rowA, h->B2, h->rowfx, h->colfx,
-                                     h->pfx, (float)h->prm.gamma, B->M, dtarget);
+                                     h->pfx, (float)h->prm.gamma, B->M, dtarget, h->psix);
     k_bbegin<<<1, 1, 0, st>>>(B->bc);
     if (!h->ck(cudaGetLastError(), "batch start")) return h->last_code;
     if (!capture_graph(h, B, tol, rtol, maxit)) return h->last_code;

@@ -5,11 +5,11 @@
 // Precision (the evaluation kernel is in otgs_stream.cu): near the optimum
 // z - theta is tiny next to z, so z must be exact to ~1e-13 relative.  alpha
 // and beta reach the kernel as FP32 (hi, lo) pairs plus an upper bound of each
-// (bound_up) for the cheap rejection test; f is formed with error-free
-// transformations where it may be positive.  Row and column sums of T arrive
-// as fixed-point integers and psi as per-(item, warp) partials added here in
-// a fixed order, so results are deterministic and screened evaluations
-// (skipped units are exact zeros) equal dense ones bit for bit.
+// (bound_up) for the cheap bound and rejection tests; f is formed with
+// error-free transformations where it may be positive.  Row and column sums
+// of T and psi arrive as fixed-point integers, so results are deterministic
+// whatever kernel formed a block and in whatever order, and screened
+// evaluations (skipped units are exact zeros) equal dense ones bit for bit.
 #include "otgs_internal.cuh"
 
 namespace otgs {
@@ -54,6 +54,7 @@ void launch_prep(const double* alpha, bool alpha_sorted, const int32_t* perm, co
 // not depend on scheduling.
 constexpr int RED_THREADS = 256;
 constexpr int RED_WARPS = RED_THREADS / 32;
+constexpr int BP = REDUCE_PARTS;  // values per block in block_part
 
 int reduce_blocks(int32_t m, int32_t n)
 {
@@ -64,12 +65,12 @@ int reduce_blocks(int32_t m, int32_t n)
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
 {
     if (R.gate && !*R.gate) return;  // a skipped solver trial
-    __shared__ double sh[4][RED_WARPS];
+    __shared__ double sh[3][RED_WARPS];
     __shared__ bool last;
     const FxScale fx = fx_scale(R.ctl->amax, R.ctl->bmax, R.fx_m, R.fx_n, R.gamma);
     const int t = blockIdx.x * RED_THREADS + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double ab = 0.0, dt = 0.0, inf = 0.0, psi = 0.0;
+    double ab = 0.0, dt = 0.0, inf = 0.0;
     if (t < R.m) {
         const double rs = (double)(long long)R.rowfx[t] * fx.from_r;
         const double ga = R.a_sorted[t] - rs;
@@ -88,39 +89,28 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
         inf = fmax(inf, fabs(gb));
         ab += R.beta[t] * R.b[t];
     }
-    {
-        const int64_t E = (int64_t)R.nitems * NWARPS;
-        const int64_t per = (E + gridDim.x - 1) / gridDim.x;
-        const int64_t e0 = (int64_t)blockIdx.x * per, e1 = e0 + per < E ? e0 + per : E;
-        for (int64_t e = e0 + threadIdx.x; e < e1; e += RED_THREADS)
-            if (!R.item_active || R.item_active[e / NWARPS]) psi += R.psipart[e];
-    }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
         ab += __shfl_xor_sync(FULLMASK, ab, off);
         dt += __shfl_xor_sync(FULLMASK, dt, off);
-        psi += __shfl_xor_sync(FULLMASK, psi, off);
         inf = fmax(inf, __shfl_xor_sync(FULLMASK, inf, off));
     }
     if (lane == 0) {
         sh[0][warp] = ab;
         sh[1][warp] = dt;
         sh[2][warp] = inf;
-        sh[3][warp] = psi;
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+        double v0 = 0.0, v1 = 0.0, v2 = 0.0;
         for (int w = 0; w < RED_WARPS; w++) {
             v0 += sh[0][w];
             v1 += sh[1][w];
             v2 = fmax(v2, sh[2][w]);
-            v3 += sh[3][w];
         }
-        R.block_part[4 * blockIdx.x + 0] = v0;
-        R.block_part[4 * blockIdx.x + 1] = v1;
-        R.block_part[4 * blockIdx.x + 2] = v2;
-        R.block_part[4 * blockIdx.x + 3] = v3;
+        R.block_part[BP * blockIdx.x + 0] = v0;
+        R.block_part[BP * blockIdx.x + 1] = v1;
+        R.block_part[BP * blockIdx.x + 2] = v2;
         __threadfence();
         const unsigned ticket = atomicAdd(R.counter, 1u);
         last = ticket == gridDim.x - 1;
@@ -130,20 +120,20 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
     __threadfence();
     // last block, first warp: fixed-order sums over blocks
     const volatile double* bp = R.block_part;
-    double s_ab = 0.0, s_dt = 0.0, s_inf = 0.0, s_psi = 0.0;
+    double s_ab = 0.0, s_dt = 0.0, s_inf = 0.0;
     for (int b = lane; b < (int)gridDim.x; b += 32) {
-        s_ab += bp[4 * b];
-        s_dt += bp[4 * b + 1];
-        s_inf = fmax(s_inf, bp[4 * b + 2]);
-        s_psi += bp[4 * b + 3];
+        s_ab += bp[BP * b];
+        s_dt += bp[BP * b + 1];
+        s_inf = fmax(s_inf, bp[BP * b + 2]);
     }
     for (int off = 16; off >= 1; off >>= 1) {
         s_ab += __shfl_xor_sync(FULLMASK, s_ab, off);
         s_dt += __shfl_xor_sync(FULLMASK, s_dt, off);
         s_inf = fmax(s_inf, __shfl_xor_sync(FULLMASK, s_inf, off));
-        s_psi += __shfl_xor_sync(FULLMASK, s_psi, off);
     }
     if (lane == 0) {
+        // psi: the exact-sum kernel's fixed-point sums
+        const double s_psi = psi_from_fx((long long)R.psix[0], (long long)R.psix[1], fx.from_p);
         const double D = (R.err && *(volatile const int*)R.err) ? __longlong_as_double(0x7ff8000000000000ll)
                                                                   : s_ab - s_psi;
         if (R.out_caller) R.out_caller[0] = D;

@@ -55,9 +55,10 @@ struct Handle {
     double* alpha_eval = nullptr;   // sorted alpha of the last evaluation
     unsigned long long* rowfx = nullptr;  // fixed-point row sums of T
     unsigned long long* colfx = nullptr;  // fixed-point column sums of T
-    double* psipart = nullptr;      // per (item, consumer warp) psi sums
-    PassB* passb = nullptr;         // blocks whose pass B the pass-B kernel does
-    int passb_cap = 0;
+    unsigned long long* psix = nullptr;  // per problem of a batch: psi of the exact-sum kernel (hi, lo)
+    XEntry* xent = nullptr;         // flagged block sets for the exact-sum kernel (sized by the plan):
+    XEntry* xtall = nullptr;        // classes of at most XTALL_ROWS rows, taller classes
+    int32_t xent_cap = 0, xtall_cap = 0;
     float* split_part = nullptr;    // partial block sums of the pieces of split groups
     int nred = 0;
     double* block_part = nullptr;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -53,12 +54,14 @@ inline int32_t panel_rows(int64_t m, int64_t n) { return panel_rows_for(row_chun
 // Columns of the per-column float-pair split of beta, padded to whole items.
 inline int32_t padded_cols(int64_t n) { return (int32_t)((n + ITEM_COLS - 1) / ITEM_COLS * ITEM_COLS); }
 
-// alpha_i (resp. beta_j) rounded up by a relative 2^-22: with A' and B' so
-// rounded, fl(fl(A'_i - c_ij) + B'_j) > 0 whenever alpha_i + beta_j - c_ij >= 0
-// (the FP32 representation and rounding errors are below 2^-23 of |alpha| +
-// |beta| + c <= 2 (|alpha| + |beta|)), so the test rejects only elements
-// whose f is certainly <= 0.
-__device__ __forceinline__ float bound_up(float h) { return __fadd_ru(h, __fmul_ru(fabsf(h), 0x1p-22f)); }
+// alpha_i (resp. beta_j) rounded up by a relative 2^-20: with A' and B' so
+// rounded, y_ij = fl(fl(A'_i - c_ij) + B'_j) >= f_ij = alpha_i + beta_j - c_ij
+// whenever f_ij > 0 (then c_ij < |alpha| + |beta|, and the representation and
+// rounding errors, below 6 2^-24 (|alpha| + |beta|), are covered by the 16
+// 2^-24 (|alpha| + |beta|) the rounding up adds).  So [y]_+ >= [f]_+ for every
+// element: y <= 0 rejects only elements whose f is certainly <= 0, and the
+// FP32 sum of [y]_+^2 bounds ||[f_[l]]_+||^2 from above.
+__device__ __forceinline__ float bound_up(float h) { return __fadd_ru(h, __fmul_ru(fabsf(h), 0x1p-20f)); }
 
 // FP32 (hi, lo) split of an FP64 value: hi + lo = x to ~2^-48 relative.
 __device__ __forceinline__ float2 split2(double x)
@@ -108,14 +111,18 @@ struct SplitSet {
     int prob;    // problem of a batch
 };
 
+// Values a piece of a split group stores per column: the FP32 bound sum S'
+// of [y]_+^2 and the snapshot's sum of [y]_-^2.
+constexpr int SPLIT_VALS = 2;
+
 // Tunable plan parameters (0: the default rule).
 struct PlanParams {
     int32_t panel_rows = 0;  // panel height (default: panel_rows(m, n))
     int32_t split_rows = 0;  // groups taller than this are cut into pieces (default: SPLIT_ROWS)
     // > 0: a stage ends early, before a group of at most STAGE_ROWS rows that
-    // would straddle its end (so that the group's blocks finish from shared
-    // memory instead of the pass-B kernel), when it keeps at least this many
-    // rows; 0 (default): stages of STAGE_ROWS rows
+    // would straddle its end (so that the group's blocks are bounded within
+    // one stage), when it keeps at least this many rows; 0 (default): stages
+    // of STAGE_ROWS rows
     int32_t stage_fill = 0;
 };
 
@@ -140,7 +147,7 @@ struct BProb {
 
 // A work item as the evaluation kernel sees it, in execution order (64 B).
 struct ItemDesc {
-    int item;   // item id (index of its psi partials and active flag)
+    int item;   // item id (index of its active flag)
     int p;      // panel
     int r0;     // first sorted row
     int rows;   // rows (whole groups, or one piece of a split group)
@@ -228,19 +235,49 @@ struct EvalCtl {
     int work;           // work-item counter of the evaluation kernel
     unsigned amax;      // float bits of max_i [alpha_i hi]_+
     unsigned bmax;      // float bits of max_j [beta_j hi]_+
-    int npassb;         // deferred pass-B blocks recorded (may exceed the list's capacity)
+    int nxent;          // flagged block sets of classes of at most XTALL_ROWS rows
+    int nxtall;         // flagged block sets of taller classes
+    unsigned long long psi[2];  // one problem: psi summed by the exact-sum kernel (fixed point, hi and lo)
 };
 
-// A block (group rows [gstart, gend) x the 32 columns [colg0, colg0 + 32))
-// whose pass B (row sums t_ij = s_j [f_ij]_+) is left to the pass-B kernel
-// because its rows have left the evaluation kernel's ring.
-struct PassB {
-    int gstart, gend;  // rows [gstart, gend): a piece of at most PASSB_PIECE rows of the block
-    int colg0;         // column (in the concatenation) of lane 0
+// Device address of the control word's psi accumulators (host side: plain
+// address arithmetic on the device pointer).
+inline unsigned long long* ctl_psi(EvalCtl* c)
+{
+    return reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(c) + offsetof(EvalCtl, psi));
+}
+
+// Clears a control word (every field starts each evaluation at zero).
+__device__ __forceinline__ void ctl_clear(EvalCtl* c)
+{
+    c->work = 0;
+    c->amax = 0u;
+    c->bmax = 0u;
+    c->nxent = 0;
+    c->nxtall = 0;
+    c->psi[0] = 0ull;
+    c->psi[1] = 0ull;
+}
+
+// A flagged block set for the exact-sum kernel: the blocks (group l, column
+// j) of one 32-column tile whose FP32 bound does not rule out z > theta.  The
+// kernel re-reads the rows [gstart, gend) for the columns in mask, forms S =
+// ||[f]_+||^2 and P = sum [f]_+ in double-float, and finishes the blocks
+// (Eq. 5) with their row sums.
+// A flagged block set of a class taller than this goes to the exact-sum
+// kernel's CTA-wide path (a warp per set for the others).
+constexpr int XTALL_ROWS = 256;
+
+struct XEntry {
+    int gstart, gend;  // rows of the group
+    int colg0;         // first column (in the concatenation) of the tile
     int prob;          // problem of a batch
-    float s[TW];       // shrink factor of each column's block (0: none)
+    int l;             // group
+    uint32_t mask;     // columns (bit k: column colg0 + k) to evaluate
+    int pad[2];
 };
-constexpr int PASSB_PIECE = 256;
+
+
 
 // Adds this warp's maxima of [alpha hi]_+ and [beta hi]_+ into ctl (all
 // lanes of the warp must call it).  Non-negative floats order as their bits.
@@ -262,6 +299,7 @@ __device__ __forceinline__ void record_max(EvalCtl* ctl, float apos, float bpos)
 struct FxScale {
     double to_r, from_r;  // row sums: value * to_r -> integer, integer * from_r -> value
     double to_c, from_c;  // column sums
+    double to_p, from_p;  // psi: the coarse grid (its remainders go to a grid 2^30 times finer)
     float to_rf, to_cf;   // to_r, to_c as floats (exact: powers of two in FP32 range)
 };
 
@@ -289,7 +327,13 @@ __host__ __device__ inline FxScale fx_scale(unsigned amax_bits, unsigned bmax_bi
 #endif
     const double F = ((double)am + (double)bm) / (double)gamma;
     const int kr = fx_exponent(F * (double)n), kc = fx_exponent(F * (double)m);
+    // sum psi <= sum_ij [f_ij]_+^2 / (2 gamma) <= m n F'^2 / (2 gamma), F' = (max [alpha]_+ + max [beta]_+)
+    // with the 2^-20 of the bounds' rounding (a 1.01 factor of slack)
+    const double Fp = ((double)am + (double)bm) * 1.01;
+    const int kp = fx_exponent(Fp * Fp * (double)m * (double)n / (2.0 * (double)gamma));
     FxScale s;
+    s.to_p = ldexp(1.0, kp);
+    s.from_p = ldexp(1.0, -kp);
     s.to_r = ldexp(1.0, kr);
     s.from_r = ldexp(1.0, -kr);
     s.to_c = ldexp(1.0, kc);
@@ -297,6 +341,25 @@ __host__ __device__ inline FxScale fx_scale(unsigned amax_bits, unsigned bmax_bi
     s.to_rf = ldexpf(1.0f, kr);
     s.to_cf = ldexpf(1.0f, kc);
     return s;
+}
+
+// psi of one block (as the float pair of Eq. 5's evaluation) to the
+// two-level fixed point of the scale: the value on the coarse grid and its
+// remainder on a grid 2^30 times finer.  Each part is an exact integer
+// function of the block, so sums of them do not depend on the order of the
+// additions (or on which kernel formed the block).
+__device__ __forceinline__ void psi_to_fx(float psh, float psl, double to_p, long long& hi, long long& lo)
+{
+    const double x = ((double)psh + (double)psl) * to_p;  // exact: a pair of floats, times a power of two
+    const double q = rint(x);
+    hi += (long long)q;
+    lo += __double2ll_rn((x - q) * 1073741824.0);         // x - q is exact; |.| <= 1/2
+}
+
+// D's psi term from the fixed-point sums.
+__host__ __device__ inline double psi_from_fx(long long hi, long long lo, double from_p)
+{
+    return (double)hi * from_p + (double)lo * (from_p * (1.0 / 1073741824.0));
 }
 
 // TMA descriptors of one problem's C: box[k] is 2^k rows x ITEM_COLS columns,
@@ -330,10 +393,12 @@ struct EvalArgs {
     int32_t unit_words;           // ceil(ntiles / 32)
     unsigned long long* rowfx;    // [m] fixed-point row sums of T (zeroed by the preparation kernel)
     unsigned long long* colfx;    // [n] fixed-point column sums of T
-    double* psipart;   // [nitems * NWARPS]: per item and consumer warp, sum of psi
-    PassB* passb;      // deferred pass-B blocks (capacity passb_cap)
-    int32_t passb_cap;
-    float* split_part; // [slots][ITEM_COLS][5]: a piece's (S hi, S lo, P hi, P lo, O) per column
+    unsigned long long* psix;  // [nprob][2]: psi of the exact-sum kernel's blocks (fixed point, hi, lo)
+    XEntry* xent;      // flagged block sets of classes of at most XTALL_ROWS rows (capacity xent_cap)
+    XEntry* xtall;     // those of taller classes (capacity xtall_cap)
+    int32_t xent_cap, xtall_cap;
+    float thr_flag;    // RD(theta^2 (1 - 2^-21)): a block whose FP32 bound stays at or below it has s = 0
+    float* split_part; // [slots][ITEM_COLS][SPLIT_VALS]: a piece's (S', O) per column
     const SplitSet* sets;  // block sets of split groups
     int32_t nsets;
     const int* gate;   // NULL, or a device flag: 0 = skip this evaluation (batched solver trials)
@@ -350,6 +415,10 @@ struct EvalArgs {
     float inv2g_hi, inv2g_lo;   // the same as a float pair
 };
 
+// Values per block of the reduction kernel's scratch (D's terms, the slope,
+// the gradient's max norm).
+constexpr int REDUCE_PARTS = 3;
+
 struct ReduceArgs {
     int32_t m, n, nitems;
     int32_t fx_m, fx_n;
@@ -357,7 +426,7 @@ struct ReduceArgs {
     const uint8_t* item_active; // NULL = all items
     const unsigned long long* rowfx;
     const unsigned long long* colfx;
-    const double* psipart;
+    const unsigned long long* psix;  // [2]: psi of the exact-sum kernel's blocks
     const EvalCtl* ctl;
     float gamma;
     const double* a_sorted;     // FP64 [m] sorted order
@@ -369,7 +438,7 @@ struct ReduceArgs {
     double* G_sorted;     // [m + n] minus gradient (sorted rows, then columns)
     const double* dir;    // [m + n] direction for dot(G, dir), or NULL
     double* scal;         // [4]: D, dot(G, dir), ||G||_inf, psi
-    double* block_part;   // scratch [4 * nblocks]
+    double* block_part;   // scratch [REDUCE_PARTS * nblocks]
     unsigned int* counter;// scratch, zero on entry, reset by the last block
     const int* err;       // evaluation error word: non-zero makes D NaN
     const int* gate;      // NULL, or a device flag: 0 = skip (batched solver trials)
@@ -393,9 +462,14 @@ void launch_stage_masks(const EvalArgs& a, cudaStream_t st);
 // split-finish kernel (otgs_stream.cu): adds the pieces' partial sums of the
 // split groups' blocks and finishes them.  Launch right after launch_stream.
 void launch_split_finish(const EvalArgs& a, cudaStream_t st);
-// pass-B kernel (otgs_stream.cu): the blocks k_stream and the split-finish
-// kernel deferred.  Launch after them with the same arguments.
-void launch_passb(const EvalArgs& a, int n_sm, cudaStream_t st);
+// exact-sum kernel (otgs_stream.cu): the exact sums, Eq. 5 and the row sums
+// of the blocks the evaluation kernel and the split-finish kernel flagged.
+// Launch after the split-finish kernel with the same arguments.
+void launch_exact(const EvalArgs& a, int n_sm, cudaStream_t st);
+// Capacities of the flagged-block lists (host): one entry per (non-empty
+// group, 32-column tile of its problem), each recorded at most once per
+// evaluation; groups of at most XTALL_ROWS rows, and taller ones.
+void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall);
 size_t stream_smem_bytes();
 void launch_reduce(const ReduceArgs& a, cudaStream_t st);
 int reduce_blocks(int32_t m, int32_t n);

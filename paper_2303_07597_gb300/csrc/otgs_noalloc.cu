@@ -96,14 +96,15 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const size_t o_ctl = cv.take(sizeof(EvalCtl)), o_err = cv.take(16);
     const size_t o_aeval = cv.take(8 * (size_t)m);
     const size_t o_rowfx = cv.take(8 * (size_t)m), o_colfx = cv.take(8 * (size_t)n);
-    const size_t o_psipart = cv.take(8 * (size_t)hp.nitems() * NWARPS);
-    const int passb_cap = 4096;
-    const size_t o_passb = cv.take(sizeof(PassB) * (size_t)passb_cap);
-    const size_t o_spart = cv.take(sizeof(float) * 5 * ITEM_COLS * (size_t)hp.nsplit_slots);
+    const size_t o_spart = cv.take(sizeof(float) * SPLIT_VALS * ITEM_COLS * (size_t)hp.nsplit_slots);
+    int64_t xe_cap = 0, xt_cap = 0;
+    exact_caps(hp, xe_cap, xt_cap);
+    const size_t o_xent = cv.take(sizeof(XEntry) * (size_t)xe_cap);
+    const size_t o_xtall = cv.take(sizeof(XEntry) * (size_t)xt_cap);
     const size_t o_sets = cv.take(sizeof(SplitSet) * hp.sets.size());
     const size_t o_maps = cv.take(sizeof(TmaMaps)), o_prob = cv.take(sizeof(ProbDesc));
     const int nred = reduce_blocks((int32_t)m, (int32_t)n);
-    const size_t o_bpart = cv.take(8 * 4 * (size_t)nred), o_counter = cv.take(16), o_scal = cv.take(64);
+    const size_t o_bpart = cv.take(8 * REDUCE_PARTS * (size_t)nred), o_counter = cv.take(16), o_scal = cv.take(64);
     if (cv.off > OTGS_STATIC_SCRATCH_BYTES)
         return set_err(OTGS_EINVAL, "problem needs " + std::to_string(cv.off) + " bytes of scratch, above the " +
                                         std::to_string((size_t)OTGS_STATIC_SCRATCH_BYTES) +
@@ -177,9 +178,11 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     ea.item_active = nullptr; ea.unit_need = nullptr;
     ea.unit_words = (ntiles + 31) / 32;
     ea.rowfx = rowfx; ea.colfx = colfx;
-    ea.psipart = (double*)(base + o_psipart);
-    ea.passb = (PassB*)(base + o_passb);
-    ea.passb_cap = passb_cap;
+    ea.psix = ctl_psi(ctl);  // cleared with the control word by the preparation
+    ea.xent = (XEntry*)(base + o_xent);
+    ea.xent_cap = (int32_t)xe_cap;
+    ea.xtall = (XEntry*)(base + o_xtall);
+    ea.xtall_cap = (int32_t)xt_cap;
     ea.split_part = (float*)(base + o_spart);
     ea.sets = (const SplitSet*)(base + o_sets);
     ea.nsets = (int32_t)hp.sets.size();
@@ -190,6 +193,12 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     float fc = (float)cut;
     if ((double)fc > cut) fc = std::nextafter(fc, 0.f);
     ea.th2_cut = fc;
+    {
+        const double t2 = theta * theta * (1.0 - std::ldexp(1.0, -21));
+        float ft = (float)t2;
+        if ((double)ft > t2) ft = std::nextafter(ft, 0.f);
+        ea.thr_flag = ft;
+    }
     ea.gamma = (float)gamma;
     ea.inv2g = 1.0 / (2.0 * gamma);
     ea.inv2g_hi = (float)ea.inv2g;
@@ -197,13 +206,13 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     if (!stream_prepare()) return set_err(OTGS_ECUDA, "cudaFuncSetAttribute(evaluation kernel)");
     launch_stream(ea, std::min(CTAS_PER_SM * n_sm, hp.nitems()), st);
     launch_split_finish(ea, st);
-    launch_passb(ea, n_sm, st);
+    launch_exact(ea, n_sm, st);
     ReduceArgs ra;
     memset(&ra, 0, sizeof(ra));
     ra.m = (int32_t)m; ra.n = (int32_t)n; ra.nitems = hp.nitems();
     ra.fx_m = (int32_t)m; ra.fx_n = (int32_t)n;
     ra.perm = perm; ra.item_active = nullptr;
-    ra.rowfx = rowfx; ra.colfx = colfx; ra.psipart = ea.psipart;
+    ra.rowfx = rowfx; ra.colfx = colfx; ra.psix = ea.psix;
     ra.ctl = ctl; ra.gamma = ea.gamma;
     ra.a_sorted = a; ra.b = b; ra.alpha_sorted = aeval; ra.beta = beta;
     ra.out_caller = out; ra.scal = (double*)(base + o_scal);

@@ -136,7 +136,7 @@ std::string build_plan_batch(int32_t nprob, const int32_t* const* labels, const 
         }
         flush();  // panels never span two problems
     }
-    if (slots > INT32_MAX / (ITEM_COLS * 5)) return "too many pieces of tall groups";
+    if (slots > INT32_MAX / (ITEM_COLS * SPLIT_VALS)) return "too many pieces of tall groups";
     hp.nsplit_slots = slots;
 
     // stages of each panel

@@ -256,10 +256,7 @@ __global__ void k_gate(SolverState* S, EvalCtl* ctl, unsigned* gmax)
     const int go = !S->done && !S->refresh;
     S->go = go;
     if (!go) return;
-    ctl->work = 0;
-    ctl->amax = 0u;
-    ctl->bmax = 0u;
-    ctl->npassb = 0;
+    ctl_clear(ctl);
     if (gmax)
         for (int k = 0; k < 4; k++) gmax[k] = 0u;
 }

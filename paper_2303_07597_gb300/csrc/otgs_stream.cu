@@ -1,7 +1,8 @@
-// otgs_stream.cu -- the evaluation kernel: one pass over C per evaluation of
-// the dual (Eq. 4) and its gradient (Eq. 5), fed by TMA.
+// otgs_stream.cu -- the evaluation of the dual (Eq. 4) and its gradient
+// (Eq. 5): one pass over C that bounds every block, then the exact sums of
+// the blocks the bound does not rule out.
 //
-// Persistent, one CTA per SM, warp-specialised:
+// k_stream, persistent, CTAS_PER_SM CTAs per SM, warp-specialised:
 //  * a producer warp takes work items (a panel of whole groups x ITEM_COLS
 //    columns; host-built descriptors fetched three items ahead) from a global
 //    counter and streams each item's rows, STAGE_ROWS at a time, into a ring
@@ -10,24 +11,27 @@
 //    and on an item's first stage its columns' beta constants.  Stages
 //    complete on mbarrier transaction counts;
 //  * NWARPS consumer warps: warp w owns the item's columns [32 w, 32 w + 32),
-//    one per lane, and walks every row of every stage, so each block (l, j)
-//    is evaluated start to end by one thread and the warps' work is the same
-//    whatever the group sizes.
+//    one per lane, and walks every row of every stage.  For each element the
+//    lane forms y = fl(fl(A'_i - c_ij) + B'_j) (A', B' alpha, beta rounded up,
+//    so y >= f_ij where f_ij > 0) and adds [y]_+^2 to its block's FP32 sum S',
+//    an upper bound of z^2 = ||[f_[l]]_+||^2 within a stated relative error.
+//    4-row chunks where no y can be positive (the max over the chunk) are
+//    skipped, and so are groups with no such chunk.  At a block's last row
+//    a bound at or below theta^2 (with its error) means s = 0 (Eq. 5): the
+//    block adds nothing.  The other ("flagged") blocks of a 32-column tile
+//    are recorded for the exact-sum kernel.  The work per element is the same
+//    in every lane and warp whatever the iterate.  Pieces of a split group
+//    store their partial bound sums; the split-finish kernel adds them.  A
+//    snapshot evaluation also needs z~ (an upper bound: the bound itself) and
+//    o~ (Def. 1-2) of every block, so it walks every group.
 //
-// Per block (group l, column j), dense evaluation: each lane first marks the
-// 4-row chunks of a stage where f may be positive -- fl(fl(A'_i - c_ij) + B'_j)
-// > 0 for the max over the chunk, with A', B' alpha, beta rounded up by a
-// relative 2^-22 -- and only groups with a marked chunk (in any lane of the
-// warp) are visited: f is formed there in double-float with TwoSum, and S =
-// ||[f_[l]]_+||^2 and P = sum [f_[l]]_+ are summed.  At the group's last row:
-// the shrink s = [z - theta]_+ / (gamma z) and psi = [z - theta]_+^2 /
-// (2 gamma) of Eq. 5, and, where s > 0, pass B adds s [f]_+ into the row sums
-// (each lane adds its nonzero t_ij; only rows in chunks marked in pass A;
-// rows of earlier stages are re-read from L2).  A
-// snapshot evaluation also needs z~ and o~ (Def. 1) of every block, so it
-// walks every group.  Row and column sums go to int64 fixed-point accumulators
-// by atomic adds, whose total does not depend on their order; psi goes to
-// per-(item, warp) partials that the reduction kernel adds in a fixed order.
+// k_exact, k_exact_tall: the flagged blocks.  f is formed in double-float
+// with TwoSum, S = sum [f]_+^2 and P = sum [f]_+ are summed in a fixed
+// order, Eq. 5 gives the shrink s and psi, and a second sweep adds t_ij =
+// s [f_ij]_+ into the row sums.  Row and column sums and psi are int64 fixed
+// point (atomic adds whose total does not depend on their order), so the
+// results are deterministic, and a screened evaluation (skipped blocks
+// contribute exact zeros) equals a dense one bit for bit.
 //
 // Every wait is on an mbarrier and gives up after WAIT_NS; on timeout the
 // kernel records an error in A.err, the producer waits (bounded) for the
@@ -267,56 +271,33 @@ __device__ __forceinline__ bool maybe_pos(float ap, float c, float bp)
     return __fadd_rn(__fsub_rn(ap, c), bp) > 0.f;
 }
 
-// One element of pass A.
-__device__ __forceinline__ void elem_exact(const float4& a, float c, float bh, float bl, float bp, Acc& acc,
-                                           bool& any)
+// Whether a block may have s > 0 (Eq. 5), from the FP32 bound S' = sum of
+// [y]_+^2 over its rows (y as bound_up describes, [y]_+ >= [f]_+ for every
+// element): S' summed by k fused multiply-adds and additions of non-negative
+// terms is at least (1 - 2^-24)^k of the exact sum, so ||[f]_+||^2 <= S' (1 +
+// (k + 4) 2^-23) holds, and a block at or below thr_flag = RD(theta^2 (1 -
+// 2^-21)) has z < theta by far more than the exact sums' rounding: its s is 0.
+// k counts the rows and the partial sums added.  theta = 0: every block with
+// some [y]_+ > 0.
+__device__ __forceinline__ float sp_bound(float Sp, int k) { return fmaf(Sp, (float)(k + 4) * 0x1p-23f, Sp); }
+__device__ __forceinline__ bool flag_block(float Sp, int k, float thr) { return sp_bound(Sp, k) > thr; }
+// The same bound rounded up, as a snapshot value z~ >= z (Def. 1).
+__device__ __forceinline__ float sp_up(float Sp, int k)
 {
-    if (maybe_pos(a.z, c, bp)) {
-        float fh, fl;
-        f_exact(a.x, a.y, bh, bl, c, fh, fl);
-        if (fh > 0.f) {
-            acc_p(fh, fl, acc);
-            any = true;
-        }
-    }
+    return __fsqrt_ru(__fmaf_ru(Sp, __fmul_ru((float)(k + 4), 0x1p-23f), Sp));
 }
 
-// o~^2 term of Def. 1: [f]_-^2, f in plain FP32 (the snapshot keeps o~ rounded up).
-__device__ __forceinline__ void acc_neg(const float4& a, float c, float bh, float& O)
-{
-    const float x = fminf(__fsub_rn(__fadd_rn(a.x, bh), c), 0.f);
-    O = fmaf(x, x, O);
-}
-
-// Pass A over rows [r, e) of a stage for this lane's column (snapshot walk).
+// One element of the stream's pass: y = fl(fl(A' - c) + B') (>= f where
+// f > 0); S' += [y]_+^2, and for a snapshot the sum of [y]_-^2.
 template <bool SNAP>
-__device__ __forceinline__ void scan_rows(const float* st, const float4* rA, int r, int e, float bh, float bl,
-                                          float bp, Acc& acc, float& O, bool& any)
+__device__ __forceinline__ void elem_pass(float ap, float c, float bp, float& Sp, float& O)
 {
-    for (; r + 4 <= e; r += 4) {
-        const float c0 = st[(r + 0) * IC], c1 = st[(r + 1) * IC], c2 = st[(r + 2) * IC], c3 = st[(r + 3) * IC];
-        const float4 a0 = rA[r + 0], a1 = rA[r + 1], a2 = rA[r + 2], a3 = rA[r + 3];
-        if (SNAP) {
-            acc_neg(a0, c0, bh, O);
-            acc_neg(a1, c1, bh, O);
-            acc_neg(a2, c2, bh, O);
-            acc_neg(a3, c3, bh, O);
-        }
-        // rounding is monotonic, so fl(max(x) + B') > 0 iff some fl(x + B') > 0
-        const float mx = fmaxf(fmaxf(__fsub_rn(a0.z, c0), __fsub_rn(a1.z, c1)),
-                               fmaxf(__fsub_rn(a2.z, c2), __fsub_rn(a3.z, c3)));
-        if (__fadd_rn(mx, bp) > 0.f) {
-            elem_exact(a0, c0, bh, bl, bp, acc, any);
-            elem_exact(a1, c1, bh, bl, bp, acc, any);
-            elem_exact(a2, c2, bh, bl, bp, acc, any);
-            elem_exact(a3, c3, bh, bl, bp, acc, any);
-        }
-    }
-    for (; r < e; r++) {
-        const float c = st[r * IC];
-        const float4 a = rA[r];
-        if (SNAP) acc_neg(a, c, bh, O);
-        elem_exact(a, c, bh, bl, bp, acc, any);
+    const float y = __fadd_rn(__fsub_rn(ap, c), bp);
+    const float p = fmaxf(y, 0.f);  // a NaN y counts as 0
+    Sp = fmaf(p, p, Sp);
+    if (SNAP) {
+        const float q = fminf(y, 0.f);
+        O = fmaf(q, q, O);
     }
 }
 
@@ -372,26 +353,6 @@ __device__ __forceinline__ unsigned long long t_q(float t, float to_fx)
     return (unsigned long long)__float2ll_rn(__fmul_rn(t, to_fx));
 }
 
-// Warp-wide: the lanes' terms q of one row (one column per lane) added into
-// the row's fixed-point sum with one atomic (or each lane's own, when at most
-// two lanes have a term).  The row's total is below 2^61
-// (the grid's bound), so the three 32-bit partial sums cannot overflow:
-// bits 32.. sum below 2^29, the two 16-bit fields below 2^21.
-__device__ __forceinline__ void red_row(unsigned long long* p, unsigned long long q)
-{
-    const unsigned bal = __ballot_sync(FULLMASK, q != 0ull);
-    if (!bal) return;
-    if (__popc(bal) <= 2) {  // one or two columns: their own atomics are cheaper than the sums
-        if (q) atomicAdd(p, q);
-        return;
-    }
-    const unsigned hi = __reduce_add_sync(FULLMASK, (unsigned)(q >> 32));
-    const unsigned m1 = __reduce_add_sync(FULLMASK, (unsigned)(q >> 16) & 0xffffu);
-    const unsigned m0 = __reduce_add_sync(FULLMASK, (unsigned)q & 0xffffu);
-    if ((threadIdx.x & 31) == 0)
-        atomicAdd(p, ((unsigned long long)hi << 32) + ((unsigned long long)m1 << 16) + (unsigned long long)m0);
-}
-
 // A block's column-sum term s P (P = Ph + Pl) in fixed point: s P as a float
 // pair, each part rounded to the grid (an error below one grid step).
 __device__ __forceinline__ long long col_q(float s, float Ph, float Pl, float to_fx)
@@ -399,41 +360,6 @@ __device__ __forceinline__ long long col_q(float s, float Ph, float Pl, float to
     const float ph = __fmul_rn(s, Ph);
     const float pl = fmaf(s, Pl, fmaf(s, Ph, -ph));
     return __float2ll_rn(__fmul_rn(ph, to_fx)) + __float2ll_rn(__fmul_rn(pl, to_fx));
-}
-
-// Rows [R0, R1) (stepping by `step` from R0) of a block for this lane's
-// column: re-form f and add the nonzero t_ij = s [f_ij]_+ to the fixed-point
-// row sums (integer adds: the total does not depend on their order).  Eight
-// rows' loads are issued together.
-__device__ __forceinline__ void passb_rows(const EvalArgs& A, float to_rf, int R0, int R1, int step, int prob,
-                                           int colg, float s)
-{
-    const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[prob];
-    const int lcol = colg - pd.coff;
-    const bool real = lcol < pd.n;
-    const float2 b2 = real ? __ldg(A.B2 + pd.bcoff + lcol) : make_float2(0.f, 0.f);
-    const float bp = real ? bound_up(b2.x) : -INFINITY;
-    for (int R = R0; R < R1; R += step) {
-        float c[8];
-        float4 a[8];
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const int Rq = min(R + q, R1 - 1);
-            c[q] = real ? __ldg(pd.C + (int64_t)(Rq - pd.roff) * pd.ldc + lcol) : 0.f;
-            a[q] = __ldg(A.rowA + Rq);
-        }
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            if (R + q >= R1) break;  // (uniform)
-            unsigned long long tq = 0ull;
-            if (s > 0.f && maybe_pos(a[q].z, c[q], bp)) {
-                float fh, fl;
-                f_exact(a[q].x, a[q].y, b2.x, b2.y, c[q], fh, fl);
-                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), to_rf);
-            }
-            red_row(A.rowfx + R + q, tq);
-        }
-    }
 }
 
 // Snapshot values of block (l, col) (written only for a real column).
@@ -449,12 +375,10 @@ __device__ __forceinline__ void put_snap(const EvalArgs& A, int l, int col, bool
 // The block of this lane's column that is being accumulated.
 struct Block {
     int gl, gstart, gend;  // group and the sorted rows [gstart, gend) summed in this item
-    int rstart, rend;      // all rows of the group (wider than [gstart, gend) for a piece of a split group)
     bool split;            // a piece of a group cut over several items
     bool need;             // evaluated by this warp (always, unless screened)
-    bool any;              // some f > 0 seen
-    Acc acc;
-    float O;               // sum of [f]_-^2 (snapshot evaluations)
+    float Sp;              // FP32 bound sum of [y]_+^2
+    float O;               // sum of [y]_-^2 (snapshot evaluations)
 };
 
 // Per-lane constants of the current item and the stage being consumed.
@@ -463,139 +387,103 @@ struct Ctx {
     int rs;            // the stage's row stride (floats)
     const float4* rA;  // stage's alpha records
     int ra, nr;        // first sorted row of the stage, rows in it
-    float bh, bl, bp;  // beta hi, lo, B' of this lane's column
+    float bp;          // B' of this lane's column (-inf past the problem's last column)
     int colg;          // this lane's column in the concatenation of the problems' columns
     bool real;         // the lane's column exists (the item's last chunk may be narrower)
-    const float* Cp;   // the item's problem: its C, row stride, first row
-    int64_t ldc;
-    int roff;
-    int lcol;          // this lane's column within its problem
     uint32_t U;        // chunks of the stage marked by some lane (dense path)
     int r0;            // first sorted row of the item
     int rend;          // end row of the item
-    int item, split, sub, part;  // the item; its group's pieces, its piece, the set's piece-0 slot
+    int pslot;         // a piece of a split group: its partial-sum slot
     int prob;          // the item's problem
-    float to_rf, to_cf;  // its fixed-point scales (row sums, column sums)
 };
 
 __device__ __forceinline__ void open_block(Block& b, const int4& g, bool need, const Ctx& x)
 {
     b.gl = g.x;
-    b.rstart = g.y;
-    b.rend = g.z;
     b.split = g.y < x.r0 || g.z > x.rend;  // a group cut into pieces: this item sums one
     b.gstart = max(g.y, x.r0);
     b.gend = min(g.z, x.rend);
     b.need = need;
-    b.any = false;
-    b.acc = Acc{0.f, 0.f, 0.f, 0.f};
+    b.Sp = 0.f;
     b.O = 0.f;
 }
 
-// Leaves pass B of a block (rows [gstart, gend) x the warp's 32 columns from
-// colg0, shrink factor s per lane) to the pass-B kernel, in pieces of at most
-// PASSB_PIECE rows (so that one long block does not set that kernel's
-// duration); false when the list is full (the slots taken that fit are left
-// empty and the caller does pass B itself).
-__device__ __forceinline__ bool defer_passb(const EvalArgs& A, int gstart, int gend, int colg0, int prob, float s,
-                                            int lane)
+// A block set for the exact-sum kernel (lane 0 of the calling warp records
+// it): rows [gstart, gend) of group l x the columns colg0 + k, k in mask.
+__device__ __forceinline__ void add_xentry(const EvalArgs& A, int gstart, int gend, int colg0, int prob, int l,
+                                           uint32_t mask, int lane)
 {
-    const int npieces = (gend - gstart + PASSB_PIECE - 1) / PASSB_PIECE;
-    int idx = 0;
-    if (lane == 0) idx = atomicAdd(&A.ctl->npassb, npieces);
-    idx = __shfl_sync(FULLMASK, idx, 0);
-    const bool fits = idx + npieces <= A.passb_cap;
-    for (int k = 0; k < npieces && idx + k < A.passb_cap; k++) {
-        PassB& e = A.passb[idx + k];
-        e.s[lane] = fits ? s : 0.f;
-        if (lane == 0) {
-            e.gstart = fits ? gstart + k * PASSB_PIECE : 0;
-            e.gend = fits ? min(gstart + (k + 1) * PASSB_PIECE, gend) : 0;
-            e.colg0 = colg0;
-            e.prob = prob;
-        }
+    if (lane != 0) return;
+    const bool tall = gend - gstart > XTALL_ROWS;
+    const int e = atomicAdd(tall ? &A.ctl->nxtall : &A.ctl->nxent, 1);
+    if (e < (tall ? A.xtall_cap : A.xent_cap)) {
+        XEntry& x = (tall ? A.xtall : A.xent)[e];
+        x.gstart = gstart;
+        x.gend = gend;
+        x.colg0 = colg0;
+        x.prob = prob;
+        x.l = l;
+        x.mask = mask;
+    } else {
+        atomicOr(A.err, 4);  // the capacity holds every (group, tile) once: not reached
     }
-    return fits;
 }
 
-// The block is complete: Eq. 5 for it, and pass B where s > 0.  A piece of a
-// split group only stores its partial sums; the split-finish kernel adds the
-// pieces in order and finishes the block.
+// The block is complete: flagged (its FP32 bound does not rule out z > theta)
+// it goes to the exact-sum kernel, which finishes it; otherwise its s is 0
+// and it adds nothing.  A snapshot stores the bound as z~ (the exact-sum
+// kernel replaces it for the flagged blocks) and o~.  A piece of a split
+// group only stores its partial sums; the split-finish kernel adds the
+// pieces in order and decides.
 template <bool SNAP>
-__device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, int lane, bool marks,
-                                             float (&psi_acc)[2], long long& cacc)
+__device__ __forceinline__ void finish_block(const EvalArgs& A, const Block& b, const Ctx& x, int lane)
 {
     if (b.split) {
-        float* q = A.split_part + ((int64_t)(x.part + x.sub) * ITEM_COLS + (threadIdx.x >> 5) * TW + lane) * 5;
-        q[0] = b.acc.Sh;
-        q[1] = b.acc.Sl;
-        q[2] = b.acc.Ph;
-        q[3] = b.acc.Pl;
-        q[4] = b.O;
+        float* q = A.split_part + ((int64_t)x.pslot * ITEM_COLS + (threadIdx.x >> 5) * TW + lane) * SPLIT_VALS;
+        q[0] = b.Sp;
+        q[1] = b.O;
         return;
     }
-    float s = 0.f;
-    if (__any_sync(FULLMASK, b.any)) {
-        float psh, psl;
-        s = block_scale(b.acc.Sh, b.acc.Sl, A, psh, psl);
-        df_add(psi_acc[0], psi_acc[1], psh, psl);
-        if (s > 0.f) cacc += col_q(s, b.acc.Ph, b.acc.Pl, x.to_cf);
-    }
-    if (SNAP) put_snap(A, b.gl, x.colg, x.real, z_up(b.acc.Sh, b.acc.Sl), __fsqrt_ru(b.O));
-    if (!__any_sync(FULLMASK, s > 0.f)) return;
-    if (b.gstart < x.ra) {
-        // the block began in an earlier stage, which has left the ring: its
-        // pass B goes to the pass-B kernel, or (that list is full) the
-        // earlier rows are re-read here
-        if (defer_passb(A, b.gstart, b.gend, x.colg - lane, x.prob, s, lane)) return;
-        for (int R = b.gstart; R < x.ra; R++) {  // one row at a time: few registers for a rare path
-            const float c = x.real ? __ldg(x.Cp + (int64_t)(R - x.roff) * x.ldc + x.lcol) : 0.f;
-            const float4 av = __ldg(A.rowA + R);
-            unsigned long long tq = 0ull;
-            if (s > 0.f && maybe_pos(av.z, c, x.bp)) {
-                float fh, fl;
-                f_exact(av.x, av.y, x.bh, x.bl, c, fh, fl);
-                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), x.to_rf);
-            }
-            red_row(A.rowfx + R, tq);
-        }
-    }
-    // pass B over the block's rows in this stage: t_ij = s [f_ij]_+ into the
-    // row sums, over the chunks that can hold an f > 0 (every chunk on the
-    // snapshot walk), four rows at a time
-    uint32_t qm = marks ? x.U : 0xffu;
-    qm &= chunks_in(max(b.gstart - x.ra, 0), min(b.gend - x.ra, SR));
-    while (qm) {
-        const int q = __ffs(qm) - 1;
-        qm &= qm - 1u;
-        const int R0 = max(x.ra + 4 * q, b.gstart), R1 = min(x.ra + 4 * q + 4, b.gend);
-#pragma unroll
-        for (int k = 0; k < 4; k++) {
-            if (R0 + k >= R1) break;  // (uniform)
-            const int r = R0 + k - x.ra;
-            const float c = x.st[r * x.rs];
-            const float4 av = x.rA[r];
-            unsigned long long tq = 0ull;
-            if (s > 0.f && maybe_pos(av.z, c, x.bp)) {
-                float fh, fl;
-                f_exact(av.x, av.y, x.bh, x.bl, c, fh, fl);
-                if (fh > 0.f) tq = t_q(__fmul_rn(s, fh), x.to_rf);
-            }
-            red_row(A.rowfx + R0 + k, tq);
-        }
-    }
+    const int k = b.gend - b.gstart;
+    const uint32_t fw = __ballot_sync(FULLMASK, x.real && flag_block(b.Sp, k, A.thr_flag));
+    if (fw) add_xentry(A, b.gstart, b.gend, x.colg - lane, x.prob, b.gl, fw, lane);
+    if (SNAP) put_snap(A, b.gl, x.colg, x.real, sp_up(b.Sp, k), __fsqrt_ru(b.O));
 }
 
 // Dense path: the marked chunks of rows [s, e) of the block's group.
 __device__ __forceinline__ void block_marked_rows(Block& b, const Ctx& x, int s, int e)
 {
     uint32_t qm = x.U & chunks_in(s, e);
+    float O = 0.f;
     while (qm) {
         const int q = __ffs(qm) - 1;
         qm &= qm - 1u;
-        const int r1 = min(4 * q + 4, e);
-        for (int r = max(4 * q, s); r < r1; r++) elem_exact(x.rA[r], x.st[r * x.rs], x.bh, x.bl, x.bp, b.acc, b.any);
+        const int r0 = max(4 * q, s), r1 = min(4 * q + 4, e);
+        if (r0 == 4 * q && r1 == 4 * q + 4) {
+            const float c0 = x.st[(r0 + 0) * x.rs], c1 = x.st[(r0 + 1) * x.rs], c2 = x.st[(r0 + 2) * x.rs],
+                        c3 = x.st[(r0 + 3) * x.rs];
+            elem_pass<false>(x.rA[r0 + 0].z, c0, x.bp, b.Sp, O);
+            elem_pass<false>(x.rA[r0 + 1].z, c1, x.bp, b.Sp, O);
+            elem_pass<false>(x.rA[r0 + 2].z, c2, x.bp, b.Sp, O);
+            elem_pass<false>(x.rA[r0 + 3].z, c3, x.bp, b.Sp, O);
+        } else {
+            for (int r = r0; r < r1; r++) elem_pass<false>(x.rA[r].z, x.st[r * x.rs], x.bp, b.Sp, O);
+        }
     }
+}
+
+// Snapshot path: every row of [r, e).
+__device__ __forceinline__ void scan_rows(Block& b, const Ctx& x, int r, int e)
+{
+    for (; r + 4 <= e; r += 4) {
+        const float c0 = x.st[(r + 0) * x.rs], c1 = x.st[(r + 1) * x.rs], c2 = x.st[(r + 2) * x.rs],
+                    c3 = x.st[(r + 3) * x.rs];
+        elem_pass<true>(x.rA[r + 0].z, c0, x.bp, b.Sp, b.O);
+        elem_pass<true>(x.rA[r + 1].z, c1, x.bp, b.Sp, b.O);
+        elem_pass<true>(x.rA[r + 2].z, c2, x.bp, b.Sp, b.O);
+        elem_pass<true>(x.rA[r + 3].z, c3, x.bp, b.Sp, b.O);
+    }
+    for (; r < e; r++) elem_pass<true>(x.rA[r].z, x.st[r * x.rs], x.bp, b.Sp, b.O);
 }
 
 }  // namespace
@@ -654,6 +542,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
         int i0 = bcast(fetch());
         int w0 = load_w(i0);
         int a0 = load_act(i0, w0);
+
         int v0 = load_st(i0, w0, 0);
         int i1 = bcast(fetch());
         int w1 = load_w(i1);
@@ -794,31 +683,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
     const int wc = warp * TW + lane;  // this lane's column within an item
     long long consumed = 0;
     Ctx x;
-    x.bh = 0.f; x.bl = 0.f; x.bp = -INFINITY; x.colg = 0; x.U = 0u; x.real = false;
-    x.Cp = nullptr; x.ldc = 0; x.roff = 0; x.lcol = 0; x.prob = 0;
-    {
-        const FxScale fx = prob_fx(A, 0);  // (batches: replaced by the item's problem's)
-        x.to_rf = fx.to_rf;
-        x.to_cf = fx.to_cf;
-    }
-    float psi_acc[2] = {0.f, 0.f};  // this lane's psi sum over the item's blocks, a float pair
-    long long cacc = 0;              // this lane's column sum over the item's blocks, fixed point
-    int item = -1;  // the item being consumed; its sums are written when the next one starts
-    Block blk;
+    x.bp = -INFINITY; x.colg = 0; x.U = 0u; x.real = false; x.prob = 0;
     x.r0 = 0;
     x.rend = 0;
-    x.item = 0;
-    x.split = 1;
-    x.sub = 0;
-    x.part = -1;
+    x.pslot = 0;
+    Block blk;
     open_block(blk, make_int4(0, 0, 0, 0), false, x);
-    auto finish_item = [&]() {
-        double v = (double)psi_acc[0] + (double)psi_acc[1];
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(FULLMASK, v, off);
-        if (lane == 0) A.psipart[(int64_t)item * NWARPS + warp] = v;
-        if (x.real && cacc != 0) atomicAdd(A.colfx + x.colg, (unsigned long long)cacc);
-    };
     for (;;) {
         const int slot = (int)(consumed % NSTAGES);
         if (!mbar_wait(&S.full[slot], (uint32_t)((consumed / NSTAGES) & 1))) {
@@ -827,41 +697,17 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
         }
         const StageHdr& hs = S.hdr[slot];
         const int flags = hs.flags;
-        if (flags & H_TERM) {
-            if (item >= 0) finish_item();
-            return;
-        }
+        if (flags & H_TERM) return;
         const int r0 = hs.d.r0;
         if (flags & H_FIRST) {
-            if (item >= 0) finish_item();
-            item = hs.d.item;
-            x.item = item;
-            x.split = hs.d.split;
-            x.sub = hs.d.sub;
-            x.part = hs.d.part;
-            const float2 b2 = S.colB[slot][wc];
-            x.bh = b2.x;
-            x.bl = b2.y;
+            x.pslot = hs.d.part + hs.d.sub;
             x.prob = hs.d.prob;
-            if (A.pfx) {
-                x.to_rf = A.pfx[x.prob].to_rf;
-                x.to_cf = A.pfx[x.prob].to_cf;
-            }
             const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[x.prob];
-            x.Cp = pd.C;
-            x.ldc = pd.ldc;
-            x.roff = pd.roff;
-            x.lcol = hs.d.col0 + wc;
-            x.colg = pd.coff + x.lcol;
+            x.colg = pd.coff + hs.d.col0 + wc;
             x.real = wc < hs.d.ncols;
-            if (!x.real) {  // past the problem's last column (the pairs there may be another problem's)
-                x.bh = -1e30f;
-                x.bl = 0.f;
-            }
-            x.bp = x.real ? bound_up(x.bh) : -INFINITY;  // B'; no element of a missing column passes
-            psi_acc[0] = 0.f;
-            psi_acc[1] = 0.f;
-            cacc = 0;
+            // B'; no element of a missing column (past the problem's last one, where the
+            // pairs may be another problem's) passes
+            x.bp = x.real ? bound_up(S.colB[slot][wc].x) : -INFINITY;
             blk.gend = r0;  // no block continues into the item
         }
         x.r0 = r0;
@@ -880,41 +726,34 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
             while (r < x.nr) {
                 if (x.ra + r == blk.gend) open_block(blk, rG[r], (wrows >> r) & 1u, x);
                 const int e = min(blk.gend - x.ra, x.nr);
-                if (blk.need) scan_rows<true>(x.st, x.rA, r, e, x.bh, x.bl, x.bp, blk.acc, blk.O, blk.any);
+                if (blk.need) scan_rows(blk, x, r, e);
                 r = e;
-                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, lane, false, psi_acc, cacc);
+                if (x.ra + r == blk.gend && blk.need) finish_block<true>(A, blk, x, lane);
             }
         } else {
-            // only the groups with a marked chunk (and a block that ends here)
+            // only the groups with a marked chunk (and a block that ends here):
+            // an unmarked chunk has y <= 0 in every row, so it adds nothing
             const uint32_t live = (x.nr >= SR ? 0xffu : (1u << ((x.nr + 3) >> 2)) - 1u) & chunks_of_rows(wrows);
             const uint32_t cm = tiled ? chunk_marks<TW>(x.st, x.rA, x.bp) : chunk_marks<IC>(x.st, x.rA, x.bp);
             x.U = __reduce_or_sync(FULLMASK, cm & live);
             int r = 0;
-            if (blk.gend > x.ra) {  // the block open at the end of the last stage continues here
-                const int e = min(blk.gend - x.ra, x.nr);
-                if (blk.need) block_marked_rows(blk, x, 0, e);
-                if (blk.gend <= x.ra + x.nr && blk.need)
-                    finish_block<false>(A, blk, x, lane, true, psi_acc, cacc);
-                r = e;
-            }
-            while (r < x.nr) {
-                const uint32_t Ur = x.U & ~((1u << (r >> 2)) - 1u);
-                if (!Ur) {
-                    // no f > 0 in rows [r, nr): the stage's last group stays open
-                    // (with nothing accumulated) in case it continues; a piece of a
-                    // split group still reports (zero) partial sums at its end
-                    const int last = x.nr - 1;
-                    open_block(blk, rG[last], (wrows >> last) & 1u, x);
-                    if (blk.split && blk.need && blk.gend <= x.ra + x.nr)
-                        finish_block<false>(A, blk, x, lane, true, psi_acc, cacc);
-                    break;
+            bool cont = blk.gend > x.ra;  // the block open at the end of the last stage continues here
+            while (cont || r < x.nr) {
+                int s0 = 0;
+                if (!cont) {
+                    // the group of the first marked chunk at or after r (it starts at or
+                    // after r); with none, the stage's last group, which stays open (with
+                    // nothing summed) in case it continues -- a piece of a split group
+                    // still reports (zero) partial sums at its end
+                    const uint32_t Ur = x.U & ~((1u << (r >> 2)) - 1u);
+                    const int rc = Ur ? max(r, 4 * (__ffs(Ur) - 1)) : x.nr - 1;
+                    open_block(blk, rG[rc], (wrows >> rc) & 1u, x);
+                    s0 = blk.gstart - x.ra;
                 }
-                const int rc = max(r, 4 * (__ffs(Ur) - 1));  // the group there starts at or after r
-                open_block(blk, rG[rc], (wrows >> rc) & 1u, x);
+                cont = false;
                 const int e = min(blk.gend - x.ra, x.nr);
-                if (blk.need) block_marked_rows(blk, x, blk.gstart - x.ra, e);
-                if (blk.gend <= x.ra + x.nr && blk.need)
-                    finish_block<false>(A, blk, x, lane, true, psi_acc, cacc);
+                if (blk.need) block_marked_rows(blk, x, s0, e);
+                if (blk.gend <= x.ra + x.nr && blk.need) finish_block<false>(A, blk, x, lane);
                 r = e;
             }
         }
@@ -953,38 +792,12 @@ void launch_stage_masks(const EvalArgs& a, cudaStream_t st)
     k_stage_masks<<<a.nlist, 256, 0, st>>>(a);
 }
 
-// ================================================================ pass B
-// The deferred blocks, one CTA per list entry at a time: warp w takes rows
-// [gstart + 8 (w + NW t), + 8) for t = 0, 1, ...
-constexpr int PASSB_THREADS = 256;
-
-__global__ void __launch_bounds__(PASSB_THREADS) k_passb(const EvalArgs A)
-{
-    if (A.gate && !*A.gate) return;
-    const int nb = min(A.ctl->npassb, A.passb_cap);
-    if (nb == 0) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = PASSB_THREADS / 32;
-    for (int eb = blockIdx.x; eb < nb; eb += gridDim.x) {
-        const PassB& e = A.passb[eb];
-        const float s = e.s[lane];
-        if (!__any_sync(FULLMASK, s > 0.f)) continue;
-        const FxScale fx = prob_fx(A, e.prob);
-        // warp w: 8-row batches w, w + nw, ... of the entry
-        for (int R = e.gstart + 8 * warp; R < e.gend; R += 8 * nw)
-            passb_rows(A, fx.to_rf, R, min(R + 8, e.gend), 8, e.prob, e.colg0 + lane, s);
-    }
-}
-
-void launch_passb(const EvalArgs& a, int n_sm, cudaStream_t st)
-{
-    k_passb<<<4 * n_sm, PASSB_THREADS, 0, st>>>(a);
-}
-
 // ========================================================== split finish
 // One CTA per block set at a time, warp w = tile w of the set's 256 columns:
-// add the pieces' partial sums in piece order, then Eq. 5 for the block as
-// in the evaluation kernel (psi into piece 0's partials, the column sum, the
-// snapshot values, pass B to the pass-B kernel).
+// add the pieces' FP32 bound sums (and the snapshot's [y]_-^2 sums) in piece
+// order, then, as the evaluation kernel does for a block that ends in its
+// ring: the flagged blocks go to the exact-sum kernel, and a snapshot stores
+// the bound as z~ (replaced by the exact value for flagged blocks) and o~.
 __global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
@@ -992,43 +805,359 @@ __global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
     for (int si = blockIdx.x; si < A.nsets; si += gridDim.x) {
         const SplitSet st = A.sets[si];
         if (A.prob_active && !A.prob_active[st.prob]) continue;  // a finished problem of a batch
-        const int tile = st.col0 / TW + warp;
+        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[st.prob];
+        const int tile = st.col0 / TW + warp;  // within the problem
         if (A.unit_need && !((A.unit_need[(int64_t)st.l * A.unit_words + (tile >> 5)] >> (tile & 31)) & 1u))
             continue;  // a screened-out unit: its pieces wrote nothing this evaluation
-        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[st.prob];
-        const FxScale fx = prob_fx(A, st.prob);
         const int lcol = st.col0 + warp * TW + lane;
         const int colg = pd.coff + lcol;
         const bool real = lcol < pd.n;
-        Acc t = {0.f, 0.f, 0.f, 0.f};
-        float o = 0.f;
+        float sp = 0.f, o = 0.f;
         for (int k = 0; k < st.split; k++) {
-            const float* q = A.split_part + ((int64_t)(st.part + k) * ITEM_COLS + warp * TW + lane) * 5;
-            df_add(t.Sh, t.Sl, q[0], q[1]);
-            df_add(t.Ph, t.Pl, q[2], q[3]);
-            o = __fadd_rn(o, q[4]);
+            const float* q = A.split_part + ((int64_t)(st.part + k) * ITEM_COLS + warp * TW + lane) * SPLIT_VALS;
+            sp = __fadd_rn(sp, q[0]);
+            o = __fadd_rn(o, q[1]);
         }
-        float s = 0.f;
-        double psi = 0.0;
-        if (__any_sync(FULLMASK, t.Ph > 0.f)) {
-            float psh, psl;
-            s = block_scale(t.Sh, t.Sl, A, psh, psl);
-            psi = (double)psh + (double)psl;
-            if (s > 0.f && real) atomicAdd(A.colfx + colg, (unsigned long long)col_q(s, t.Ph, t.Pl, fx.to_cf));
-        }
-#pragma unroll
-        for (int off = 16; off >= 1; off >>= 1) psi += __shfl_xor_sync(FULLMASK, psi, off);
-        if (lane == 0 && psi != 0.0) A.psipart[(int64_t)st.item0 * NWARPS + warp] += psi;
-        if (A.zt) put_snap(A, st.l, colg, real, z_up(t.Sh, t.Sl), __fsqrt_ru(o));
-        if (!__any_sync(FULLMASK, s > 0.f)) continue;
-        if (!defer_passb(A, st.rstart, st.rend, colg - lane, st.prob, s, lane))
-            passb_rows(A, fx.to_rf, st.rstart, st.rend, 8, st.prob, colg, s);  // the list is full
+        const int k = st.rend - st.rstart + st.split;
+        const uint32_t fw = __ballot_sync(FULLMASK, real && flag_block(sp, k, A.thr_flag));
+        if (fw) add_xentry(A, st.rstart, st.rend, colg - lane, st.prob, st.l, fw, lane);
+        if (A.zt) put_snap(A, st.l, colg, real, sp_up(sp, k), __fsqrt_ru(o));
     }
 }
 
 void launch_split_finish(const EvalArgs& a, cudaStream_t st)
 {
     if (a.nsets > 0) k_split_finish<<<a.nsets < 4096 ? a.nsets : 4096, NWARPS * 32, 0, st>>>(a);
+}
+
+// ============================================================ exact sums
+// The flagged blocks of classes of at most XTALL_ROWS rows: one warp per
+// entry (a group's rows x up to 32 columns of a tile), up to XCOLS of its
+// columns per sweep, one row per lane (rows gstart + lane + 32 u).  First sweep: each lane sums S = sum [f]_+^2 and
+// P = sum [f]_+ over its rows in double-float (f formed with TwoSum where the
+// bound y > 0), the warp adds the lanes' sums in a fixed xor tree, and Eq. 5
+// gives s and psi (psi in fixed point into the problem's accumulators, the
+// column sum s P in fixed point, the snapshot's z~).  Second sweep, where
+// some s > 0, over the same rows (now in L1/L2): the nonzero t_ij = s
+// [f_ij]_+ of the row, summed over the sweep's columns, to the row's
+// fixed-point sum (consecutive rows: one coalesced atomic per 32 rows).  C is
+// read in 32-byte sectors of the active columns only; the alpha records are
+// coalesced; XUNROLL rows per lane are in flight.  The block decomposition
+// and the order of every floating-point sum are fixed, so results do not
+// depend on scheduling.
+constexpr int EXACT_THREADS = 256;
+constexpr int XCOLS = 2;
+constexpr int XUNROLL = 4;
+
+// The warp's sum of a double-float value, in a fixed xor tree; lane 0's result.
+__device__ __forceinline__ void warp_df_sum(float& h, float& l)
+{
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const float oh = __shfl_xor_sync(FULLMASK, h, off), ol = __shfl_xor_sync(FULLMASK, l, off);
+        df_add(h, l, oh, ol);
+    }
+    h = __shfl_sync(FULLMASK, h, 0);
+    l = __shfl_sync(FULLMASK, l, 0);
+}
+
+__global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact(const EvalArgs A)
+{
+    if (A.gate && !*A.gate) return;
+    const int ne = min(A.ctl->nxent, A.xent_cap);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = EXACT_THREADS / 32;
+    int pprob = -1;          // the problem of the psi sums held by lane 0
+    long long ph = 0, pl = 0;
+    for (int t = blockIdx.x * nw + warp; t < ne; t += gridDim.x * nw) {
+        const XEntry E = A.xent[t];
+        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
+        const FxScale fx = prob_fx(A, E.prob);
+        if (E.prob != pprob) {  // psi of another problem: flush the held sums
+            if (lane == 0 && (ph | pl) != 0) {
+                atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
+                atomicAdd(A.psix + 2 * pprob + 1, (unsigned long long)pl);
+            }
+            ph = pl = 0;
+            pprob = E.prob;
+        }
+        uint32_t rem = E.mask;  // columns of the problem only
+        while (rem) {
+            int kc[XCOLS];
+            float bh[XCOLS], bl[XCOLS], bp[XCOLS];
+            const float* cp[XCOLS];
+#pragma unroll
+            for (int q = 0; q < XCOLS; q++) {
+                kc[q] = rem ? __ffs(rem) - 1 : -1;
+                rem &= rem - 1u;
+                const int lcol = E.colg0 + max(kc[q], 0) - pd.coff;
+                const float2 b2 = kc[q] >= 0 ? __ldg(A.B2 + pd.bcoff + lcol) : make_float2(0.f, 0.f);
+                bh[q] = b2.x;
+                bl[q] = b2.y;
+                bp[q] = kc[q] >= 0 ? bound_up(b2.x) : -INFINITY;
+                cp[q] = pd.C + lcol - (int64_t)pd.roff * pd.ldc;  // row R of the problem at cp + R ldc
+            }
+            Acc acc[XCOLS];
+#pragma unroll
+            for (int q = 0; q < XCOLS; q++) acc[q] = Acc{0.f, 0.f, 0.f, 0.f};
+            for (int R0 = E.gstart; R0 < E.gend; R0 += 32 * XUNROLL) {
+                float c[XUNROLL][XCOLS];
+                float4 a[XUNROLL];
+#pragma unroll
+                for (int u = 0; u < XUNROLL; u++) {
+                    const int R = R0 + 32 * u + lane;
+                    const bool in = R < E.gend;
+                    a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+#pragma unroll
+                    for (int q = 0; q < XCOLS; q++) c[u][q] = (in && kc[q] >= 0) ? __ldg(cp[q] + (int64_t)R * pd.ldc) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < XUNROLL; u++)
+#pragma unroll
+                    for (int q = 0; q < XCOLS; q++)
+                        if (maybe_pos(a[u].z, c[u][q], bp[q])) {
+                            float fh, fl;
+                            f_exact(a[u].x, a[u].y, bh[q], bl[q], c[u][q], fh, fl);
+                            if (fh > 0.f) acc_p(fh, fl, acc[q]);
+                        }
+            }
+            float s[XCOLS];
+            bool anys = false;
+#pragma unroll
+            for (int q = 0; q < XCOLS; q++) {
+                s[q] = 0.f;
+                if (kc[q] < 0) continue;  // (uniform)
+                warp_df_sum(acc[q].Sh, acc[q].Sl);
+                warp_df_sum(acc[q].Ph, acc[q].Pl);
+                float psh, psl;
+                s[q] = block_scale(acc[q].Sh, acc[q].Sl, A, psh, psl);
+                anys = anys || s[q] > 0.f;
+                if (lane == 0) {
+                    const int colg = E.colg0 + kc[q];
+                    if (s[q] > 0.f) {
+                        psi_to_fx(psh, psl, fx.to_p, ph, pl);
+                        atomicAdd(A.colfx + colg, (unsigned long long)col_q(s[q], acc[q].Ph, acc[q].Pl, fx.to_cf));
+                    }
+                    if (A.zt) A.zt[(int64_t)E.l * A.ntiles * TW + colg] = z_up(acc[q].Sh, acc[q].Sl);
+                }
+            }
+            if (!anys) continue;  // (uniform)
+            for (int R0 = E.gstart; R0 < E.gend; R0 += 32 * XUNROLL) {
+                float c[XUNROLL][XCOLS];
+                float4 a[XUNROLL];
+#pragma unroll
+                for (int u = 0; u < XUNROLL; u++) {
+                    const int R = R0 + 32 * u + lane;
+                    const bool in = R < E.gend;
+                    a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+#pragma unroll
+                    for (int q = 0; q < XCOLS; q++)
+                        c[u][q] = (in && s[q] > 0.f) ? __ldg(cp[q] + (int64_t)R * pd.ldc) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < XUNROLL; u++) {
+                    unsigned long long tq = 0ull;
+#pragma unroll
+                    for (int q = 0; q < XCOLS; q++)
+                        if (s[q] > 0.f && maybe_pos(a[u].z, c[u][q], bp[q])) {
+                            float fh, fl;
+                            f_exact(a[u].x, a[u].y, bh[q], bl[q], c[u][q], fh, fl);
+                            if (fh > 0.f) tq += t_q(__fmul_rn(s[q], fh), fx.to_rf);
+                        }
+                    if (tq) atomicAdd(A.rowfx + R0 + 32 * u + lane, tq);
+                }
+            }
+        }
+    }
+    if (lane == 0 && pprob >= 0 && (ph | pl) != 0) {
+        atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
+        atomicAdd(A.psix + 2 * pprob + 1, (unsigned long long)pl);
+    }
+}
+
+// Classes taller than XTALL_ROWS: one CTA per block set at a time, thread t
+// taking rows gstart + t + EXACT_THREADS u.  The CTA's sums: each warp's
+// fixed xor tree, then the warps' sums in warp order.  The first sweep keeps
+// the positive parts [f]_+ (hi) of its first XT_CACHED_ROWS rows in shared
+// memory, so the second sweep reads C again only for rows past them.
+constexpr int XT_CACHED_ROWS = 4096;
+constexpr int XT_SLOTS = XT_CACHED_ROWS / EXACT_THREADS;  // rows per thread kept
+
+__global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact_tall(const EvalArgs A)
+{
+    if (A.gate && !*A.gate) return;
+    const int ne = min(A.ctl->nxtall, A.xtall_cap);
+    constexpr int NW = EXACT_THREADS / 32;
+    __shared__ float red[NW][XCOLS][4];
+    __shared__ float sv[XCOLS];
+    __shared__ float fkeep[XT_SLOTS][XCOLS][EXACT_THREADS];  // [row slot][column][thread]: [f]_+ hi
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int pprob = -1;  // the problem of the psi sums held by thread 0
+    long long ph = 0, pl = 0;
+    for (int t = blockIdx.x; t < ne; t += gridDim.x) {
+        const XEntry E = A.xtall[t];
+        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
+        const FxScale fx = prob_fx(A, E.prob);
+        if (E.prob != pprob) {
+            if (tid == 0 && (ph | pl) != 0) {
+                atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
+                atomicAdd(A.psix + 2 * pprob + 1, (unsigned long long)pl);
+            }
+            ph = pl = 0;
+            pprob = E.prob;
+        }
+        uint32_t rem = E.mask;
+        while (rem) {
+            int kc[XCOLS];
+            float bh[XCOLS], bl[XCOLS], bp[XCOLS];
+            const float* cp[XCOLS];
+#pragma unroll
+            for (int q = 0; q < XCOLS; q++) {
+                kc[q] = rem ? __ffs(rem) - 1 : -1;
+                rem &= rem - 1u;
+                const int lcol = E.colg0 + max(kc[q], 0) - pd.coff;
+                const float2 b2 = kc[q] >= 0 ? __ldg(A.B2 + pd.bcoff + lcol) : make_float2(0.f, 0.f);
+                bh[q] = b2.x;
+                bl[q] = b2.y;
+                bp[q] = kc[q] >= 0 ? bound_up(b2.x) : -INFINITY;
+                cp[q] = pd.C + lcol - (int64_t)pd.roff * pd.ldc;
+            }
+            Acc acc[XCOLS];
+#pragma unroll
+            for (int q = 0; q < XCOLS; q++) acc[q] = Acc{0.f, 0.f, 0.f, 0.f};
+            for (int R0 = E.gstart; R0 < E.gend; R0 += EXACT_THREADS * XUNROLL) {
+                float c[XUNROLL][XCOLS];
+                float4 a[XUNROLL];
+#pragma unroll
+                for (int u = 0; u < XUNROLL; u++) {
+                    const int R = R0 + EXACT_THREADS * u + tid;
+                    const bool in = R < E.gend;
+                    a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+#pragma unroll
+                    for (int q = 0; q < XCOLS; q++) c[u][q] = (in && kc[q] >= 0) ? __ldg(cp[q] + (int64_t)R * pd.ldc) : 0.f;
+                }
+#pragma unroll
+                for (int u = 0; u < XUNROLL; u++) {
+                    const int slot = (R0 - E.gstart) / EXACT_THREADS + u;  // the same for the whole CTA
+#pragma unroll
+                    for (int q = 0; q < XCOLS; q++) {
+                        float fk = 0.f;
+                        if (maybe_pos(a[u].z, c[u][q], bp[q])) {
+                            float fh, fl;
+                            f_exact(a[u].x, a[u].y, bh[q], bl[q], c[u][q], fh, fl);
+                            if (fh > 0.f) {
+                                acc_p(fh, fl, acc[q]);
+                                fk = fh;
+                            }
+                        }
+                        if (slot < XT_SLOTS) fkeep[slot][q][tid] = fk;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < XCOLS; q++) {
+                if (kc[q] < 0) continue;  // (uniform)
+                warp_df_sum(acc[q].Sh, acc[q].Sl);
+                warp_df_sum(acc[q].Ph, acc[q].Pl);
+                if (lane == 0) {
+                    red[warp][q][0] = acc[q].Sh;
+                    red[warp][q][1] = acc[q].Sl;
+                    red[warp][q][2] = acc[q].Ph;
+                    red[warp][q][3] = acc[q].Pl;
+                }
+            }
+            __syncthreads();
+            if (tid == 0) {
+#pragma unroll
+                for (int q = 0; q < XCOLS; q++) {
+                    sv[q] = 0.f;
+                    if (kc[q] < 0) continue;
+                    Acc T = {0.f, 0.f, 0.f, 0.f};
+                    for (int w = 0; w < NW; w++) {  // in warp order
+                        df_add(T.Sh, T.Sl, red[w][q][0], red[w][q][1]);
+                        df_add(T.Ph, T.Pl, red[w][q][2], red[w][q][3]);
+                    }
+                    float psh, psl;
+                    const float sq = block_scale(T.Sh, T.Sl, A, psh, psl);
+                    const int colg = E.colg0 + kc[q];
+                    if (sq > 0.f) {
+                        psi_to_fx(psh, psl, fx.to_p, ph, pl);
+                        atomicAdd(A.colfx + colg, (unsigned long long)col_q(sq, T.Ph, T.Pl, fx.to_cf));
+                    }
+                    if (A.zt) A.zt[(int64_t)E.l * A.ntiles * TW + colg] = z_up(T.Sh, T.Sl);
+                    sv[q] = sq;
+                }
+            }
+            __syncthreads();
+            float s[XCOLS];
+            bool anys = false;
+#pragma unroll
+            for (int q = 0; q < XCOLS; q++) {
+                s[q] = sv[q];
+                anys = anys || s[q] > 0.f;
+            }
+            if (anys) {  // (uniform)
+                // the kept rows: [f]_+ from shared memory
+                const int kept = min(E.gend - E.gstart, XT_CACHED_ROWS);
+                for (int k = 0; k < XT_SLOTS && k * EXACT_THREADS < kept; k++) {
+                    const int R = E.gstart + EXACT_THREADS * k + tid;
+                    unsigned long long tq = 0ull;
+#pragma unroll
+                    for (int q = 0; q < XCOLS; q++) {
+                        const float fh = fkeep[k][q][tid];
+                        if (s[q] > 0.f && fh > 0.f) tq += t_q(__fmul_rn(s[q], fh), fx.to_rf);
+                    }
+                    if (tq) atomicAdd(A.rowfx + R, tq);  // (fh > 0 only for rows of the set)
+                }
+                // the rows past them: C again
+                for (int R0 = E.gstart + XT_CACHED_ROWS; R0 < E.gend; R0 += EXACT_THREADS * XUNROLL) {
+                    float c[XUNROLL][XCOLS];
+                    float4 a[XUNROLL];
+#pragma unroll
+                    for (int u = 0; u < XUNROLL; u++) {
+                        const int R = R0 + EXACT_THREADS * u + tid;
+                        const bool in = R < E.gend;
+                        a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+#pragma unroll
+                        for (int q = 0; q < XCOLS; q++)
+                            c[u][q] = (in && s[q] > 0.f) ? __ldg(cp[q] + (int64_t)R * pd.ldc) : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < XUNROLL; u++) {
+                        unsigned long long tq = 0ull;
+#pragma unroll
+                        for (int q = 0; q < XCOLS; q++)
+                            if (s[q] > 0.f && maybe_pos(a[u].z, c[u][q], bp[q])) {
+                                float fh, fl;
+                                f_exact(a[u].x, a[u].y, bh[q], bl[q], c[u][q], fh, fl);
+                                if (fh > 0.f) tq += t_q(__fmul_rn(s[q], fh), fx.to_rf);
+                            }
+                        if (tq) atomicAdd(A.rowfx + R0 + EXACT_THREADS * u + tid, tq);
+                    }
+                }
+            }
+            __syncthreads();  // red and sv are reused by the next columns
+        }
+    }
+    if (tid == 0 && pprob >= 0 && (ph | pl) != 0) {
+        atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
+        atomicAdd(A.psix + 2 * pprob + 1, (unsigned long long)pl);
+    }
+}
+
+void launch_exact(const EvalArgs& a, int n_sm, cudaStream_t st)
+{
+    k_exact<<<4 * n_sm, EXACT_THREADS, 0, st>>>(a);
+    k_exact_tall<<<2 * n_sm, EXACT_THREADS, 0, st>>>(a);
+}
+
+void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall)
+{
+    xent = xtall = 0;
+    for (int64_t l = 0; l < hp.L; l++) {
+        const int64_t g = hp.goff[l + 1] - hp.goff[l];
+        if (g == 0) continue;
+        (g > XTALL_ROWS ? xtall : xent) += (hp.pn[hp.gprob[l]] + TW - 1) / TW;
+    }
 }
 
 size_t stream_smem_bytes() { return sizeof(Smem) + 1024; }

@@ -12,11 +12,18 @@ pytestmark = pytest.mark.gpu
 
 
 def _run(p, gamma, mu, alpha, beta):
+    """Two evaluations at the point, both against the oracle and equal bit
+    for bit (the kernels' sums have a fixed order or are exact integers)."""
     s = solver(p, gamma, mu)
-    out = s.grad(torch.from_numpy(alpha).to(DEV), torch.from_numpy(beta).to(DEV))
+    a_t, b_t = torch.from_numpy(alpha).to(DEV), torch.from_numpy(beta).to(DEV)
+    cold = s.grad(a_t, b_t).clone()
+    warm = s.grad(a_t, b_t)
     torch.cuda.synchronize()
     o = oracle.Oracle.from_problem(p, gamma, mu)
-    return check_grad(out, o.dual(alpha, beta), alpha, beta, p.a, p.b)
+    ref = o.dual(alpha, beta)
+    check_grad(cold, ref, alpha, beta, p.a, p.b)
+    assert torch.equal(cold, warm)
+    return check_grad(warm, ref, alpha, beta, p.a, p.b)
 
 
 def test_zero_start_is_exact():
@@ -77,3 +84,25 @@ def test_deterministic_repeat():
     o1 = s.grad(a_t, b_t).clone()
     o2 = s.grad(a_t, b_t)
     assert torch.equal(o1, o2)
+
+
+def test_result_does_not_depend_on_earlier_evaluations():
+    """An evaluation leaves no state that changes the next one: at x1 the
+    result is the same bit for bit whether it follows nothing, an evaluation
+    at x1, or one at a far point x2, and the snapshot pass gives it too."""
+    p = synth.random_instance(700, 300, 9, seed=11)
+    gamma, mu = 1.0, 0.3
+    o = oracle.Oracle.from_problem(p, gamma, mu)
+    x1 = synth.random_duals(p.m, p.n, seed=12, scale=0.6, offset=0.35)
+    x2 = synth.random_duals(p.m, p.n, seed=13, scale=0.6, offset=0.2)
+    t = lambda v: torch.from_numpy(v).to(DEV)
+    s = solver(p, gamma, mu)
+    first = s.grad(t(x1[0]), t(x1[1])).clone()
+    again = s.grad(t(x1[0]), t(x1[1])).clone()
+    s.grad(t(x2[0]), t(x2[1]))
+    after_x2 = s.grad(t(x1[0]), t(x1[1])).clone()
+    snap = torch.empty_like(first)
+    s.snapshot(t(x1[0]), t(x1[1]), build_N=False, out=snap)
+    torch.cuda.synchronize()
+    assert torch.equal(first, again) and torch.equal(first, after_x2) and torch.equal(first, snap)
+    check_grad(first, o.dual(*x1), x1[0], x1[1], p.a, p.b)

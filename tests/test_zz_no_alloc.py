@@ -4,11 +4,10 @@ It serves callers that cannot allocate device memory; its scratch lives in a
 static device array.  Its results must match the FP64 oracle and the
 handle-based ot_gs_grad within the tolerances the other parity tests use, on
 two calls in a row (the second call reuses the array the first one left
-behind).  The cases reach the kernel's two special paths: a class taller
-than the split height (its pieces' partial sums and their finishing kernel)
-and more deferred row-sum passes than the fixed list holds (the evaluation
-kernel then re-reads those rows itself).  This file is collected last on
-purpose."""
+behind).  The cases reach the path of a class taller than the split height
+(its pieces' partial sums and their finishing kernel) and many flagged
+blocks (thousands of block sets for the exact-sum kernel).  This file is
+collected last on purpose."""
 import ctypes
 
 import numpy as np
@@ -39,10 +38,9 @@ def _sized(sizes, n, seed, d=4):
 
 
 def _many_deferred():
-    """100 classes of 40 rows: each is a panel of its own whose blocks end in
-    the panel's second stage, so every active (class, 32-column tile) pair is
-    left to the deferred row-sum pass; with 4096 columns and the duals of the
-    test there are far more such pairs than the 4096 entries of the list."""
+    """100 classes of 40 rows (each a panel of its own, its blocks spanning
+    two stages) x 4096 columns: with the duals of the test several thousand
+    (class, 32-column tile) block sets hold active blocks."""
     return _sized(np.full(100, 40), 4096, seed=7)
 
 
@@ -68,7 +66,7 @@ def test_noalloc_matches_oracle_and_handle_twice(name, mk, gamma, mu):
         al, be = synth.random_duals(p.m, p.n, seed=10 + call)
         ref = o.dual(al, be)
         if name == "many_deferred":
-            # (class, 32-column tile) pairs with a nonzero plan entry: each is one deferred entry
+            # (class, 32-column tile) block sets with a nonzero plan entry
             T = o.plan(al, be)
             act = (T.reshape(p.L, 40, p.n // 32, 32) != 0).any(axis=(1, 3))
             assert int(act.sum()) > 4096
