@@ -192,6 +192,34 @@ OTGS_API int ot_gs_get_trace(ot_gs *h, double *D, double *t_ms, int64_t *evals, 
  * clear the L-BFGS memory.  alpha, beta: device FP64 [m], [n], caller order. */
 OTGS_API int ot_gs_set_state(ot_gs *h, const double *alpha, const double *beta);
 
+/*
+ * Checkpoint and resume of ot_gs_solve (Alg. 1's loop state).  A saved state
+ * holds everything an unfinished solve goes on with: the L-BFGS state (the
+ * iterate x = (alpha, beta), the gradient, the next search direction, the
+ * stored pairs (s_k, y_k) and their curvature matrices, the line search's
+ * scalars, the iteration and evaluation counters) and, when the handle holds
+ * a snapshot, the screening state of Alg. 1 (z~, o~, alpha~, beta~ and the
+ * set N).
+ *   ot_gs_state_size     *bytes (host) = size of the state of h, for a buffer
+ *   ot_gs_get_state      copies the state of h into dst (device, >= that
+ *                        size); needs a solver (after ot_gs_solve or
+ *                        ot_gs_set_state); synchronises
+ *   ot_gs_restore_state  loads a state saved from a handle of the same problem
+ *                        (same m, n, classes, lbfgs_m, gamma and mu; the
+ *                        caller keeps C, a, b the same) into h; the next
+ *                        ot_gs_solve continues it: maxit then counts the
+ *                        iterations of the whole solve, the restored ones
+ *                        included, and the iterates are bit for bit those of
+ *                        a solve that was never stopped (dense or screened,
+ *                        with the same parameters).  Its trace starts at the
+ *                        restored iterate.  Synchronises.
+ * ot_gs_set_state (a warm start) drops a restored state.  Errors: OTGS_EINVAL
+ * (no solver, short buffer, a state of another problem), OTGS_ECUDA.
+ */
+OTGS_API int ot_gs_state_size(ot_gs *h, int64_t *bytes);
+OTGS_API int ot_gs_get_state(ot_gs *h, void *dst, int64_t bytes);
+OTGS_API int ot_gs_restore_state(ot_gs *h, const void *src, int64_t bytes);
+
 OTGS_API int ot_gs_get_stats(ot_gs *h, ot_gs_stats *s); /* host struct; synchronises */
 OTGS_API int ot_gs_reset_stats(ot_gs *h);
 

@@ -80,6 +80,9 @@ def lib():
         "ot_gs_set_state": ([P, P, P], ctypes.c_int),
         "ot_gs_get_trace": ([P, P, P, P, i32, P], ctypes.c_int),
         "ot_gs_get_stats": ([P, ctypes.POINTER(Stats)], ctypes.c_int),
+        "ot_gs_state_size": ([P, P], ctypes.c_int),
+        "ot_gs_get_state": ([P, P, i64], ctypes.c_int),
+        "ot_gs_restore_state": ([P, P, i64], ctypes.c_int),
         "ot_gs_reset_stats": ([P], ctypes.c_int),
         "ot_gs_set_timing": ([P, ctypes.c_int], ctypes.c_int),
         "ot_gs_get_timing": ([P, P, P], ctypes.c_int),
@@ -265,6 +268,26 @@ def ot_gs_set_state(h, alpha, beta):
     import torch
     return _check(h, lib().ot_gs_set_state(h, _ptr(alpha, torch.float64, name="alpha"),
                                            _ptr(beta, torch.float64, name="beta")))
+
+
+def ot_gs_state_size(h) -> int:
+    n = ctypes.c_int64()
+    _check(h, lib().ot_gs_state_size(h, ctypes.byref(n)))
+    return n.value
+
+
+def ot_gs_get_state(h, buf):
+    """Copies the solver state into buf (a CUDA uint8 tensor of at least
+    ot_gs_state_size(h) bytes)."""
+    import torch
+    _ptr(buf, torch.uint8, name="buf")
+    return _check(h, lib().ot_gs_get_state(h, ctypes.c_void_p(buf.data_ptr()), buf.numel()))
+
+
+def ot_gs_restore_state(h, buf):
+    import torch
+    _ptr(buf, torch.uint8, name="buf")
+    return _check(h, lib().ot_gs_restore_state(h, ctypes.c_void_p(buf.data_ptr()), buf.numel()))
 
 
 def ot_gs_get_stats(h) -> dict:
@@ -521,6 +544,18 @@ class GroupSparseOT:
 
     def trace(self):
         return ot_gs_get_trace(self.h)
+
+    def save_state(self):
+        """The solver's full state (a CUDA uint8 tensor) for restore_state."""
+        import torch
+        buf = torch.empty(ot_gs_state_size(self.h), dtype=torch.uint8, device=self.device)
+        ot_gs_get_state(self.h, buf)
+        return buf
+
+    def restore_state(self, buf):
+        """Loads a saved state; the next solve continues it (maxit counts the
+        whole solve's iterations)."""
+        ot_gs_restore_state(self.h, buf)
 
     def plan(self, alpha, beta, out=None):
         """Transport plan t = grad psi at (alpha, beta): (m, n) FP32 (Sec. 2.3)."""

@@ -351,7 +351,8 @@ bool Handle::setup_plan(const PlanParams& pp)
     if (screen_alloc) {
         item_active = (uint8_t*)plan_alloc((size_t)hp.nitems(), "item_active");
         stage_m8 = (uint8_t*)plan_alloc((size_t)hp.nstages * STAGE_ROWS, "stage masks");
-        if (!item_active || !stage_m8) return false;
+        stage_need = (uint32_t*)plan_alloc(sizeof(uint32_t) * (size_t)((hp.nstages + 31) / 32), "stages needed");
+        if (!item_active || !stage_m8 || !stage_need) return false;
         invalidate_screen();
     }
     return ck(cudaGetLastError(), "plan upload");
@@ -492,7 +493,8 @@ void Handle::count_dense_evals(int64_t k)
     stats_host.units_total += k * (int64_t)L * ntiles;
     dense_units += k * nonempty_units();
     stats_host.units_computed = dense_units;
-    stats_host.c_bytes += (double)k * 4.0 * (double)m * (double)n;
+    dense_cbytes += (double)k * 4.0 * (double)m * (double)n;
+    stats_host.c_bytes = dense_cbytes;
 }
 
 void Handle::count_screened_evals(int64_t k)

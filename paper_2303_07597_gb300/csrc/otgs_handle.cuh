@@ -78,13 +78,16 @@ struct Handle {
     uint32_t* unit_need = nullptr;// L x unit_words
     uint8_t* item_active = nullptr;
     uint8_t* stage_m8 = nullptr;  // [nstages][STAGE_ROWS]: per row, the needed tiles of its item
+    uint32_t* stage_need = nullptr; // [ceil(nstages / 32)]: stages with a needed row
     float* gstat = nullptr;       // per group: npos, nabs, nneg, theta_skip
+    float2* drow = nullptr;       // per sorted row: RU([alpha - alpha~]_+), RN(alpha - alpha~) as FP32
     float* cstat = nullptr;       // per column: dbp, dbabs, dbneg
     unsigned* gmax = nullptr;     // float bits: max|alpha|, max|beta|, max|alpha~|, max|beta~|
     unsigned long long* dcount = nullptr; // device counters: in_N, checked, skipped, units
     float* sg_ru = nullptr;       // sqrt(g_l) rounded up
     float* sg_rn = nullptr;       // sqrt(g_l) rounded to nearest
     int64_t dense_units = 0;      // units streamed by dense passes
+    double dense_cbytes = 0.0;    // bytes of C streamed by dense passes
     ot_gs_stats stats_host;
 
     // optional event timing of evaluation-kernel launches

@@ -390,6 +390,8 @@ struct EvalArgs {
     const uint8_t* item_active;   // per item id: 1 if it has a unit to evaluate (screened), else NULL
     const uint32_t* unit_need;    // L x unit_words bitmask of units to evaluate, NULL = all
     const uint8_t* stage_m8;      // screened: [nstages][STAGE_ROWS] per row, bit w = tile w of its item needed
+    uint32_t* stage_need;         // screened: bit s of word s / 32 set when stage s has a needed row
+    unsigned long long* c_streamed; // NULL, or a counter: bytes of C the copies brought in (screened)
     int32_t unit_words;           // ceil(ntiles / 32)
     unsigned long long* rowfx;    // [m] fixed-point row sums of T (zeroed by the preparation kernel)
     unsigned long long* colfx;    // [n] fixed-point column sums of T

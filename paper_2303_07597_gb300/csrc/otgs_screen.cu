@@ -64,8 +64,34 @@ __device__ __forceinline__ void atomic_max_pos(unsigned* addr, float v)
     atomicMax(addr, __float_as_uint(v));  // v >= 0: integer order == float order
 }
 
-// Blocks [0, ceil(L/8)) take one group per warp; the rest take columns.
-__global__ void k_delta(const ScreenArgs S, int group_blocks)
+// Per sorted row (the FP64 part of the group statistics, spread over the
+// whole grid): (RU(RU(alpha - alpha~)) clamped at 0, RN(RN(alpha - alpha~)))
+// as FP32, and the maxima of |alpha|, |alpha~| rounded up.
+__global__ void k_delta_rows(const ScreenArgs S, float2* drow)
+{
+    if (S.gate && !*S.gate) return;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    float amax = 0.f, asmax = 0.f;
+    if (r < S.m) {
+        const double al = S.alpha[r], as = S.alpha_s[r];
+        const float du = __double2float_ru(__dsub_ru(al, as));
+        drow[r] = make_float2(fmaxf(du, 0.f), __double2float_rn(__dsub_rn(al, as)));
+        amax = __double2float_ru(fabs(al));
+        asmax = __double2float_ru(fabs(as));
+    }
+    for (int off = 16; off >= 1; off >>= 1) {
+        amax = fmaxf(amax, __shfl_xor_sync(FULLMASK, amax, off));
+        asmax = fmaxf(asmax, __shfl_xor_sync(FULLMASK, asmax, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_pos(S.gmax + 0, amax);
+        atomic_max_pos(S.gmax + 2, asmax);
+    }
+}
+
+// Blocks [0, ceil(L/8)) take one group per warp (the sums, from the rows'
+// FP32 values); the rest take columns.
+__global__ void k_delta(const ScreenArgs S, int group_blocks, const float2* drow)
 {
     if (S.gate && !*S.gate) return;
     if ((int)blockIdx.x < group_blocks) {
@@ -73,47 +99,36 @@ __global__ void k_delta(const ScreenArgs S, int group_blocks)
         const int lane = threadIdx.x & 31;
         if (l >= S.L) return;
         const int r0 = S.goff[l], r1 = S.goff[l + 1];
-        float pu = 0.f, a2 = 0.f, n2 = 0.f, amax = 0.f, asmax = 0.f;
+        float pu = 0.f, a2 = 0.f, n2 = 0.f;
         // each lane visits rows r0 + lane, r0 + lane + 32, ... in that order
-        // (the order the sums are defined in); loads four at a time
-        auto add = [&](double al, double as) {
-            const float du = __double2float_ru(__dsub_ru(al, as));
-            const float dp = fmaxf(du, 0.f);
+        // (the order the sums are defined in); loads sixteen rows ahead
+        auto add = [&](float2 v) {
+            const float dp = v.x, d = v.y;
             pu = __fadd_ru(pu, __fmul_ru(dp, dp));
-            const float d = __double2float_rn(__dsub_rn(al, as));
             a2 = __fadd_rn(a2, __fmul_rn(d, d));
             const float dn = fminf(d, 0.f);
             n2 = __fadd_rn(n2, __fmul_rn(dn, dn));
-            amax = fmaxf(amax, __double2float_ru(fabs(al)));
-            asmax = fmaxf(asmax, __double2float_ru(fabs(as)));
         };
         int r = r0 + lane;
-        for (; r + 96 < r1; r += 128) {
-            double al[4], as[4];
+        for (; r + 32 * 15 < r1; r += 32 * 16) {
+            float2 v[16];
 #pragma unroll
-            for (int q = 0; q < 4; q++) {
-                al[q] = S.alpha[r + 32 * q];
-                as[q] = S.alpha_s[r + 32 * q];
-            }
+            for (int q = 0; q < 16; q++) v[q] = drow[r + 32 * q];
 #pragma unroll
-            for (int q = 0; q < 4; q++) add(al[q], as[q]);
+            for (int q = 0; q < 16; q++) add(v[q]);
         }
-        for (; r < r1; r += 32) add(S.alpha[r], S.alpha_s[r]);
+        for (; r < r1; r += 32) add(drow[r]);
 #pragma unroll
         for (int off = 16; off >= 1; off >>= 1) {
             pu = __fadd_ru(pu, __shfl_xor_sync(FULLMASK, pu, off));
             a2 = __fadd_rn(a2, __shfl_xor_sync(FULLMASK, a2, off));
             n2 = __fadd_rn(n2, __shfl_xor_sync(FULLMASK, n2, off));
-            amax = fmaxf(amax, __shfl_xor_sync(FULLMASK, amax, off));
-            asmax = fmaxf(asmax, __shfl_xor_sync(FULLMASK, asmax, off));
         }
         if (lane == 0) {
             S.gstat[4 * l + 0] = __fsqrt_ru(pu);
             S.gstat[4 * l + 1] = __fsqrt_rn(a2);
             S.gstat[4 * l + 2] = __fsqrt_rn(n2);
             S.gstat[4 * l + 3] = 0.f;
-            atomic_max_pos(S.gmax + 0, amax);
-            atomic_max_pos(S.gmax + 2, asmax);
         }
         return;
     }
@@ -170,6 +185,7 @@ __global__ void k_theta(const ScreenArgs S)
 // in the tile, so each need word is written whole; statistics are summed per
 // block before one atomic add each.
 constexpr int SCREEN_WARPS = 8;
+constexpr int SCREEN_TB = 8;  // tiles whose loads a warp issues together
 
 __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S)
 {
@@ -186,32 +202,48 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
         const int p = g > 0 ? S.gpanel[l] : 0;
         uint32_t needword = 0u;
         const int jt1 = min(32 * w + 32, S.ntiles);
-        for (int jt = 32 * w; jt < jt1; jt++) {
-            const int64_t u = (int64_t)l * S.ntiles + jt;
-            const int j = jt * TW + lane;
-            const bool valid = j < S.n && g > 0;
-            const uint32_t Nw = S.Nmask[u];
-            const bool inN = valid && ((Nw >> lane) & 1u);
-            bool skip = false;
-            if (valid && !inN) {
-                const float zbar =
-                    __fadd_ru(__fadd_ru(S.zt[(int64_t)l * S.ntiles * TW + j], npos), __fmul_ru(sg, S.cstat[4 * j]));
-                skip = zbar <= th;
+        // tiles in batches of SCREEN_TB, their loads issued together
+        for (int jb = 32 * w; jb < jt1; jb += SCREEN_TB) {
+            float zv[SCREEN_TB], dv[SCREEN_TB];
+            uint32_t Nv[SCREEN_TB];
+#pragma unroll
+            for (int q = 0; q < SCREEN_TB; q++) {
+                const int jt = jb + q;
+                const int j = jt * TW + lane;
+                const bool ok = jt < jt1 && j < S.n && g > 0;
+                zv[q] = ok ? __ldg(S.zt + (int64_t)l * S.ntiles * TW + j) : 0.f;
+                dv[q] = ok ? __ldg(S.cstat + 4 * j) : 0.f;
+                Nv[q] = jt < jt1 ? __ldg(S.Nmask + (int64_t)l * S.ntiles + jt) : 0u;
             }
-            const uint32_t skipw = __ballot_sync(FULLMASK, skip);
-            const uint32_t needw = __ballot_sync(FULLMASK, valid && !skip);
-            const uint32_t validw = __ballot_sync(FULLMASK, valid);
-            if (lane == 0) {
-                S.skipmask[u] = skipw;
-                if (needw) {
-                    needword |= 1u << (jt & 31);
-                    // the item of (l, tile) in every piece of the group (same value from every writer)
-                    for (int k = 0; k < S.psplit[p]; k++) S.item_active[S.pitem[p + k] + (jt * TW) / S.pW[p]] = 1;
+#pragma unroll
+            for (int q = 0; q < SCREEN_TB; q++) {
+                const int jt = jb + q;
+                if (jt >= jt1) break;  // (uniform)
+                const int64_t u = (int64_t)l * S.ntiles + jt;
+                const int j = jt * TW + lane;
+                const bool valid = j < S.n && g > 0;
+                const uint32_t Nw = Nv[q];
+                const bool inN = valid && ((Nw >> lane) & 1u);
+                bool skip = false;
+                if (valid && !inN) {
+                    const float zbar = __fadd_ru(__fadd_ru(zv[q], npos), __fmul_ru(sg, dv[q]));
+                    skip = zbar <= th;
                 }
-                c0 += __popc(Nw & validw);
-                c1 += __popc(~Nw & validw);
-                c2 += __popc(skipw);
-                c3 += needw ? 1ull : 0ull;
+                const uint32_t skipw = __ballot_sync(FULLMASK, skip);
+                const uint32_t needw = __ballot_sync(FULLMASK, valid && !skip);
+                const uint32_t validw = __ballot_sync(FULLMASK, valid);
+                if (lane == 0) {
+                    S.skipmask[u] = skipw;
+                    if (needw) {
+                        needword |= 1u << (jt & 31);
+                        // the item of (l, tile) in every piece of the group (same value from every writer)
+                        for (int k = 0; k < S.psplit[p]; k++) S.item_active[S.pitem[p + k] + (jt * TW) / S.pW[p]] = 1;
+                    }
+                    c0 += __popc(Nw & validw);
+                    c1 += __popc(~Nw & validw);
+                    c2 += __popc(skipw);
+                    c3 += needw ? 1ull : 0ull;
+                }
             }
         }
         if (lane == 0) S.unit_need[(int64_t)l * S.unit_words + w] = needword;
@@ -292,8 +324,11 @@ bool Handle::ensure_screen()
     unit_need = (uint32_t*)dalloc(sizeof(uint32_t) * (size_t)L * unit_words, "unit_need");
     item_active = (uint8_t*)plan_alloc((size_t)hp.nitems(), "item_active");
     stage_m8 = (uint8_t*)plan_alloc((size_t)hp.nstages * STAGE_ROWS, "stage masks");
-    if (!stage_m8) return false;
+    stage_need = (uint32_t*)plan_alloc(sizeof(uint32_t) * (size_t)((hp.nstages + 31) / 32), "stages needed");
+    if (!stage_m8 || !stage_need) return false;
     gstat = (float*)dalloc(sizeof(float) * 4 * (size_t)L, "gstat");
+    drow = (float2*)dalloc(sizeof(float2) * (size_t)m, "per-row changes of alpha");
+    if (!drow) return false;
     cstat = (float*)dalloc(sizeof(float) * 4 * ldz, "cstat");
     gmax = (unsigned*)dalloc(sizeof(unsigned) * 8, "gmax");
     dcount = (unsigned long long*)dalloc(sizeof(unsigned long long) * 8, "dcount");
@@ -343,7 +378,8 @@ static void launch_delta(Handle* h, const double* beta)
     if (!h->eval_gate) cudaMemsetAsync(h->gmax, 0, sizeof(unsigned) * 4, h->st);  // else cleared by the trial gate
     const int gblocks = (h->L + 7) / 8;
     const int cblocks = (h->ntiles * TW + 255) / 256;
-    k_delta<<<gblocks + cblocks, 256, 0, h->st>>>(s, gblocks);
+    k_delta_rows<<<(unsigned)((h->m + 255) / 256), 256, 0, h->st>>>(s, h->drow);
+    k_delta<<<gblocks + cblocks, 256, 0, h->st>>>(s, gblocks, h->drow);
 }
 
 bool Handle::snapshot_at(const double* alpha, bool alpha_sorted, const double* beta, bool build_N,
@@ -390,6 +426,8 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s);
     EvalArgs e = eval_args(item_active, unit_need, false);
     e.stage_m8 = stage_m8;
+    e.stage_need = stage_need;
+    e.c_streamed = dcount + 4;
     launch_stage_masks(e, st);
     eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
@@ -407,12 +445,14 @@ bool Handle::collect_stats()
     stats_host.blocks_checked = (int64_t)c[1];
     stats_host.blocks_skipped = (int64_t)c[2];
     stats_host.units_computed = dense_units + (int64_t)c[3];
+    stats_host.c_bytes = dense_cbytes + (double)c[4];
     return true;
 }
 
 void Handle::reset_device_stats()
 {
     dense_units = 0;
+    dense_cbytes = 0.0;
     if (screen_alloc) cudaMemsetAsync(dcount, 0, sizeof(unsigned long long) * 8, st);
 }
 

@@ -61,8 +61,9 @@ __device__ __forceinline__ unsigned long long gtimer()
 // the solve, evaluations so far.
 __device__ __forceinline__ void trace_put(SolverState* S, double F)
 {
-    if (!S->trace || S->iter >= S->trace_cap) return;
-    double* e = S->trace + 3 * (size_t)S->iter;
+    const int k = S->iter - S->iter0;
+    if (!S->trace || k >= S->trace_cap) return;
+    double* e = S->trace + 3 * (size_t)k;
     e[0] = -F;
     e[1] = (double)(gtimer() - S->t_begin) * 1e-6;
     e[2] = (double)S->evals;
@@ -176,11 +177,14 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_pairdots(const SolverState* 
 }
 
 // Sum block partials in block order; then (one warp) the two-loop recursion
-// on scalars, the descent check, and the start of the next line search.
+// on scalars, the descent check, and the start of the next line search.  It
+// also runs after the iteration that ends a solve, so that the state a solve
+// stops in is the one an unfinished solve goes on from (a saved state then
+// resumes exactly).
 __global__ void __launch_bounds__(SOLVER_THREADS) k_direction(SolverState* S, const double* pbase, const double* ppair,
                                                              int nblocks, int start)
 {
-    if (S->done || (!start && (!S->go || !S->accepted))) return;
+    if (start ? S->done : (!S->go || !S->accepted)) return;
     const int M = S->M;
     __shared__ double base[NBASE];
     __shared__ double pd[MAX_LBFGS_M][NPAIR];
@@ -216,7 +220,7 @@ __global__ void __launch_bounds__(SOLVER_THREADS) k_direction(SolverState* S, co
 __global__ void k_combine(const SolverState* S, const double* G, const double* Sv, const double* Yv, double* d,
                           int N, int M, int start)
 {
-    if (S->done || (!start && (!S->go || !S->accepted))) return;
+    if (start ? S->done : (!S->go || !S->accepted)) return;
     const double cG = S->cG;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
         double v = cG * G[i];
@@ -247,6 +251,31 @@ __global__ void k_start(SolverState* S, const double* scal)
 }
 
 __global__ void k_begin(SolverState* S) { S->t_begin = gtimer(); }
+
+// Continues a restored state: the stopping rule of this solve, its trace
+// (entry 0 = the restored iterate), and Alg. 1's snapshot refresh that an
+// unfinished solve would take after the restored iteration.
+__global__ void k_resume(SolverState* S, double tol, int maxit, double budget_ns, double ftol, double* trace,
+                         int trace_cap, int r, int screening)
+{
+    S->tol = tol;
+    S->maxit = maxit;
+    S->budget_ns = budget_ns;
+    S->ftol = ftol;
+    S->trace = trace;
+    S->trace_cap = trace_cap;
+    S->r = r;
+    S->screening = screening;
+    S->iter0 = S->iter;
+    S->status = OTGS_ENOTCONV;
+    S->done = 0;
+    S->go = 0;
+    S->accepted = 0;
+    S->refresh = screening && S->iter > 0 && S->iter % r == 0;
+    if (S->iter >= maxit) S->done = 1;
+    S->t_start = gtimer();
+    trace_put(S, S->F);
+}
 
 // Opens a line-search trial: it runs only while the solve is not done and no
 // snapshot refresh is waiting for the host.  A running trial starts with a
@@ -317,10 +346,24 @@ int Solver::run(double tol, int maxit)
     init.trace = trace;
     init.trace_cap = TRACE_CAP;
     trace_len = 0;
-    if (!h->ck(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st), "state H2D")) return h->last_code;
-    k_begin<<<1, 1, 0, st>>>(state);
+    const bool resumed = resume;
+    resume = false;
+    if (resumed) {
+        if (h->prm.use_screening && !h->snap_valid) {
+            h->fail(OTGS_EINVAL, "the restored state has no snapshot: resume with use_screening = 0");
+            return OTGS_EINVAL;
+        }
+        k_begin<<<1, 1, 0, st>>>(state);
+        k_resume<<<1, 1, 0, st>>>(state, tol, maxit, init.budget_ns, init.ftol, trace, TRACE_CAP, h->prm.r,
+                                  h->prm.use_screening);
+    } else {
+        if (!h->ck(cudaMemcpyAsync(state, &init, sizeof(init), cudaMemcpyHostToDevice, st), "state H2D"))
+            return h->last_code;
+        k_begin<<<1, 1, 0, st>>>(state);
+    }
     // as Alg. 1 starts: snapshot at the start point, N empty
-    if (h->prm.use_screening) {
+    if (resumed) {
+    } else if (h->prm.use_screening) {
         h->invalidate_screen();
         if (!h->ensure_screen()) return h->last_code;
         cudaMemsetAsync(h->Nmask, 0, sizeof(uint32_t) * (size_t)h->L * h->ntiles, st);
@@ -329,10 +372,12 @@ int Solver::run(double tol, int maxit)
     } else {
         if (!h->eval_dense(x, true, x + h->m, nullptr, G, nullptr, false)) return h->last_code;
     }
-    k_start<<<1, 1, 0, st>>>(state, h->scal);
-    k_gg<<<nblk, SOLVER_THREADS, 0, st>>>(G, N, pbase);
-    k_direction<<<1, SOLVER_THREADS, 0, st>>>(state, pbase, ppair, nblk, 1);
-    k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 1);
+    if (!resumed) {
+        k_start<<<1, 1, 0, st>>>(state, h->scal);
+        k_gg<<<nblk, SOLVER_THREADS, 0, st>>>(G, N, pbase);
+        k_direction<<<1, SOLVER_THREADS, 0, st>>>(state, pbase, ppair, nblk, 1);
+        k_combine<<<nblk, SOLVER_THREADS, 0, st>>>(state, G, Sv, Yv, d, N, M, 1);
+    }
     const int npad = padded_cols(h->n);
     const int tb = (std::max((int)h->m, npad) + 255) / 256;
     const size_t hdr = offsetof(SolverState, tol);  // the int fields and the eval counter
@@ -381,9 +426,9 @@ int Solver::run(double tol, int maxit)
         !h->ck(cudaStreamSynchronize(st), "solver sync"))
         return h->last_code;
     h->stats_host.iters = hstate->iter;
-    trace_len = std::min(hstate->iter + 1, TRACE_CAP);
+    trace_len = std::min(hstate->iter - hstate->iter0 + 1, TRACE_CAP);
     // the trial evaluations (all but the first, counted when it was made)
-    const long long trials = hstate->evals - 1;
+    const long long trials = resumed ? hstate->evals - evals0 : hstate->evals - 1;
     if (trials > 0) {
         if (h->prm.use_screening) h->count_screened_evals(trials);
         else h->count_dense_evals(trials);
@@ -402,11 +447,175 @@ bool Solver::eval_trial()
     return h->eval_dense_prepped(beta, Gt, d);
 }
 
+// ---------------------------------------------------------- saved states
+// A saved solver state is one device buffer: a header, then the L-BFGS state
+// (the struct, x, G, the direction, the stored pairs), then, when the handle
+// holds a snapshot, Alg. 1's screening state (z~, o~, alpha~, beta~, N).
+namespace {
+constexpr uint64_t STATE_MAGIC = 0x5441545347544f31ull;
+constexpr int32_t STATE_VERSION = 1;
+struct StateHeader {
+    uint64_t magic;
+    int32_t version, M;
+    int64_t m, n;
+    int32_t L, ntiles;
+    int32_t has_snap, pad;
+    double gamma, mu;
+    int64_t bytes;
+};
+struct StateLayout {
+    size_t st, x, G, d, S, Y, zt, ot, as, bs, Nm, total;
+};
+inline size_t a16(size_t v) { return (v + 15) / 16 * 16; }
+StateLayout state_layout(const Handle* h, int M, bool snap)
+{
+    const size_t N = (size_t)(h->m + h->n), lz = (size_t)h->L * h->ntiles * TW, lu = (size_t)h->L * h->ntiles;
+    StateLayout o;
+    size_t at = a16(sizeof(StateHeader));
+    auto take = [&](size_t bytes) {
+        const size_t p = at;
+        at = a16(at + bytes);
+        return p;
+    };
+    o.st = take(sizeof(SolverState));
+    o.x = take(8 * N);
+    o.G = take(8 * N);
+    o.d = take(8 * N);
+    o.S = take(8 * N * M);
+    o.Y = take(8 * N * M);
+    o.zt = o.ot = o.as = o.bs = o.Nm = 0;
+    if (snap) {
+        o.zt = take(4 * lz);
+        o.ot = take(4 * lz);
+        o.as = take(8 * (size_t)h->m);
+        o.bs = take(8 * (size_t)h->n);
+        o.Nm = take(4 * lu);
+    }
+    o.total = at;
+    return o;
+}
+}  // namespace
+
 }  // namespace otgs
 
 using namespace otgs;
 
 extern "C" {
+
+int ot_gs_state_size(ot_gs* hh, int64_t* bytes)
+{
+    if (!hh || !bytes) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
+    const int M = h->solver ? h->solver->M : h->prm.lbfgs_m;
+    *bytes = (int64_t)state_layout(h, M, h->screen_alloc && h->snap_valid).total;
+    return OTGS_OK;
+}
+
+int ot_gs_get_state(ot_gs* hh, void* dst, int64_t bytes)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
+    if (!dst) { h->fail(OTGS_EINVAL, "NULL pointer"); return OTGS_EINVAL; }
+    if (!h->solver) { h->fail(OTGS_EINVAL, "no solver state yet (solve or set_state first)"); return OTGS_EINVAL; }
+    Solver* s = h->solver;
+    const bool snap = h->screen_alloc && h->snap_valid;
+    const StateLayout o = state_layout(h, s->M, snap);
+    if (bytes < (int64_t)o.total) { h->fail(OTGS_EINVAL, "buffer smaller than ot_gs_state_size"); return OTGS_EINVAL; }
+    StateHeader hd;
+    memset(&hd, 0, sizeof(hd));
+    hd.magic = STATE_MAGIC;
+    hd.version = STATE_VERSION;
+    hd.M = s->M;
+    hd.m = h->m;
+    hd.n = h->n;
+    hd.L = h->L;
+    hd.ntiles = h->ntiles;
+    hd.has_snap = snap ? 1 : 0;
+    hd.gamma = h->prm.gamma;
+    hd.mu = h->prm.mu;
+    hd.bytes = (int64_t)o.total;
+    char* b = static_cast<char*>(dst);
+    const size_t N = (size_t)(h->m + h->n), lz = (size_t)h->L * h->ntiles * TW, lu = (size_t)h->L * h->ntiles;
+    cudaStream_t st = h->st;
+    auto cp = [&](size_t off, const void* src, size_t n, cudaMemcpyKind k) {
+        return h->ck(cudaMemcpyAsync(b + off, src, n, k, st), "state copy");
+    };
+    bool ok = cp(0, &hd, sizeof(hd), cudaMemcpyHostToDevice) &&
+              cp(o.st, s->state, sizeof(SolverState), cudaMemcpyDeviceToDevice) &&
+              cp(o.x, s->x, 8 * N, cudaMemcpyDeviceToDevice) && cp(o.G, s->G, 8 * N, cudaMemcpyDeviceToDevice) &&
+              cp(o.d, s->d, 8 * N, cudaMemcpyDeviceToDevice) &&
+              cp(o.S, s->Sv, 8 * N * s->M, cudaMemcpyDeviceToDevice) &&
+              cp(o.Y, s->Yv, 8 * N * s->M, cudaMemcpyDeviceToDevice);
+    if (ok && snap)
+        ok = cp(o.zt, h->zt, 4 * lz, cudaMemcpyDeviceToDevice) && cp(o.ot, h->ot, 4 * lz, cudaMemcpyDeviceToDevice) &&
+             cp(o.as, h->alpha_snap, 8 * (size_t)h->m, cudaMemcpyDeviceToDevice) &&
+             cp(o.bs, h->beta_snap, 8 * (size_t)h->n, cudaMemcpyDeviceToDevice) &&
+             cp(o.Nm, h->Nmask, 4 * lu, cudaMemcpyDeviceToDevice);
+    if (!ok || !h->ck(cudaStreamSynchronize(st), "state sync")) return h->last_code;
+    return OTGS_OK;
+}
+
+int ot_gs_restore_state(ot_gs* hh, const void* src, int64_t bytes)
+{
+    if (!hh) return OTGS_EINVAL;
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (!single_problem(h)) return OTGS_EINVAL;
+    if (!src || bytes < (int64_t)sizeof(StateHeader)) { h->fail(OTGS_EINVAL, "NULL or short state"); return OTGS_EINVAL; }
+    StateHeader hd;
+    if (!h->ck(cudaMemcpyAsync(&hd, src, sizeof(hd), cudaMemcpyDeviceToHost, h->st), "state header") ||
+        !h->ck(cudaStreamSynchronize(h->st), "state sync"))
+        return h->last_code;
+    if (hd.magic != STATE_MAGIC || hd.version != STATE_VERSION) {
+        h->fail(OTGS_EINVAL, "not a saved solver state");
+        return OTGS_EINVAL;
+    }
+    if (hd.m != h->m || hd.n != h->n || hd.L != h->L || hd.ntiles != h->ntiles || hd.M != h->prm.lbfgs_m ||
+        hd.gamma != h->prm.gamma || hd.mu != h->prm.mu) {
+        h->fail(OTGS_EINVAL, "the saved state belongs to another problem (sizes, classes, lbfgs_m, gamma or mu)");
+        return OTGS_EINVAL;
+    }
+    const StateLayout o = state_layout(h, hd.M, hd.has_snap != 0);
+    if (hd.bytes != (int64_t)o.total || bytes < hd.bytes) { h->fail(OTGS_EINVAL, "state size mismatch"); return OTGS_EINVAL; }
+    if (!h->solver) {
+        h->solver = new (std::nothrow) Solver();
+        if (!h->solver || !h->solver->init(h)) {
+            delete h->solver;
+            h->solver = nullptr;
+            return h->last_code ? h->last_code : OTGS_ENOMEM;
+        }
+    }
+    Solver* s = h->solver;
+    if (s->M != hd.M) { h->fail(OTGS_EINVAL, "lbfgs_m changed after the first solve"); return OTGS_EINVAL; }
+    const char* b = static_cast<const char*>(src);
+    const size_t N = (size_t)(h->m + h->n), lz = (size_t)h->L * h->ntiles * TW, lu = (size_t)h->L * h->ntiles;
+    cudaStream_t st = h->st;
+    auto cp = [&](void* dst, size_t off, size_t n) {
+        return h->ck(cudaMemcpyAsync(dst, b + off, n, cudaMemcpyDeviceToDevice, st), "state copy");
+    };
+    bool ok = cp(s->state, o.st, sizeof(SolverState)) && cp(s->x, o.x, 8 * N) && cp(s->G, o.G, 8 * N) &&
+              cp(s->d, o.d, 8 * N) && cp(s->Sv, o.S, 8 * N * s->M) && cp(s->Yv, o.Y, 8 * N * s->M);
+    if (!ok) return h->last_code;
+    if (hd.has_snap) {
+        if (!h->ensure_screen()) return h->last_code;
+        ok = cp(h->zt, o.zt, 4 * lz) && cp(h->ot, o.ot, 4 * lz) && cp(h->alpha_snap, o.as, 8 * (size_t)h->m) &&
+             cp(h->beta_snap, o.bs, 8 * (size_t)h->n) && cp(h->Nmask, o.Nm, 4 * lu);
+        if (!ok) return h->last_code;
+        h->snap_valid = true;
+    } else {
+        h->invalidate_screen();
+    }
+    if (!h->ck(cudaMemcpyAsync(s->hstate, s->state, sizeof(SolverState), cudaMemcpyDeviceToHost, st), "state D2H") ||
+        !h->ck(cudaStreamSynchronize(st), "state sync"))
+        return h->last_code;
+    s->evals0 = s->hstate->evals;
+    s->iters = s->hstate->iter;
+    s->D = -s->hstate->F;
+    s->ginf = s->hstate->ginf;
+    s->resume = true;
+    return OTGS_OK;
+}
 
 int ot_gs_solve(ot_gs* hh, double tol, int32_t maxit)
 {
@@ -485,6 +694,7 @@ int ot_gs_set_state(ot_gs* hh, const double* alpha, const double* beta)
         }
     }
     Solver* s = h->solver;
+    s->resume = false;
     launch_permute_f64(alpha, h->dp.perm, (int32_t)h->m, s->x, true, h->st);
     if (!h->ck(cudaMemcpyAsync(s->x + h->m, beta, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, h->st), "copy"))
         return OTGS_ECUDA;

@@ -23,6 +23,8 @@ struct SolverState {
     int status, done, iter, npairs, head, accepted, refresh, force_accept;
     int ls_evals, have_hi, M, r, screening, maxit;
     int go;  // the current trial runs (set by the trial gate: not done, no refresh pending)
+    int iter0;  // accepted iterations before this solve (a solve resumed from a saved state)
+    int pad_i;
     long long evals;
     double tol, t, lo, Flo, dlo, hi, Fhi, dhi;
     double F, F0, dphi0, ginf, cG, budget_ns, ftol;
@@ -230,6 +232,8 @@ struct Solver {
     ~Solver();
     bool init(Handle* h);
     int run(double tol, int maxit);
+    bool resume = false;  // the next run continues the state restored by ot_gs_restore_state
+    long long evals0 = 0; // evaluations of the restored state
     bool eval_trial();
     void launch_dots(bool start);
 };

@@ -348,9 +348,22 @@ __device__ __forceinline__ FxScale prob_fx(const EvalArgs& A, int prob)
 
 // t_ij = s f_ij (FP32) on the fixed-point grid: t * 2^k is exact in FP32
 // (below 2^61 by the choice of k), so this is the integer nearest to t 2^k.
+// The integer nearest to x (ties to even) for |x| < 2^63, with 32-bit
+// conversions only (a 64-bit one runs on GB300's narrow FP64 pipe): x =
+// h 2^32 + r with h = floor(|x| 2^-32) and r = |x| - h 2^32 both exact in FP32
+// (r holds the low bits of |x|'s 24-bit significand).
+__device__ __forceinline__ long long f2ll_rn(float x)
+{
+    const float ax = fabsf(x);
+    const float h = floorf(__fmul_rn(ax, 0x1p-32f));
+    const float r = fmaf(-h, 0x1p32f, ax);
+    const long long q = ((long long)__float2int_rz(h) << 32) + (long long)__float2uint_rn(r);
+    return x < 0.f ? -q : q;
+}
+
 __device__ __forceinline__ unsigned long long t_q(float t, float to_fx)
 {
-    return (unsigned long long)__float2ll_rn(__fmul_rn(t, to_fx));
+    return (unsigned long long)f2ll_rn(__fmul_rn(t, to_fx));
 }
 
 // A block's column-sum term s P (P = Ph + Pl) in fixed point: s P as a float
@@ -359,7 +372,7 @@ __device__ __forceinline__ long long col_q(float s, float Ph, float Pl, float to
 {
     const float ph = __fmul_rn(s, Ph);
     const float pl = fmaf(s, Pl, fmaf(s, Ph, -ph));
-    return __float2ll_rn(__fmul_rn(ph, to_fx)) + __float2ll_rn(__fmul_rn(pl, to_fx));
+    return f2ll_rn(__fmul_rn(ph, to_fx)) + f2ll_rn(__fmul_rn(pl, to_fx));
 }
 
 // Snapshot values of block (l, col) (written only for a real column).
@@ -510,6 +523,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
     if (warp == CONSUMERS) {
         const bool screened = A.unit_need != nullptr;
         long long issued = 0;  // stages issued so far
+        unsigned long long cstreamed = 0;  // bytes of C requested (lane 0)
         bool ok = true;
         auto next_slot = [&](int& slot) -> bool {
             slot = (int)(issued % NSTAGES);
@@ -577,8 +591,25 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
                         for (int k = 0; k < TMA_BOXES; k++) tmap_acquire(maps + TMA_BOXES + k);
                     fenced = prob;
                 }
-                // screened: this lane's row's needed tiles, one stage ahead
-                uint32_t m8n = screened ? (uint32_t)__ldg(A.stage_m8 + (int64_t)sbase * SR + lane) : 0xffu;
+                // screened: the stages with a needed row (one bit per stage, read a
+                // word at a time), and this lane's row's needed tiles for the next
+                // such stage, loaded one needed stage ahead
+                int need_wi = -1;
+                uint32_t need_w = 0u;
+                auto next_on = [&](int s0) -> int {
+                    for (int q = s0; q < nst; q++) {
+                        const int gs = sbase + q;
+                        if ((gs >> 5) != need_wi) {
+                            need_wi = gs >> 5;
+                            need_w = __ldg(A.stage_need + need_wi);
+                        }
+                        if ((need_w >> (gs & 31)) & 1u) return q;
+                    }
+                    return nst;
+                };
+                int snext = screened ? next_on(0) : 0;
+                uint32_t m8n = (screened && snext < nst) ? (uint32_t)__ldg(A.stage_m8 + (int64_t)(sbase + snext) * SR + lane)
+                                                        : 0xffu;
                 bool first = true;  // no stage of this item issued yet
                 int wb = 0;         // first stage boundary held in v0
                 for (int s = 0; s < nst; s++) {
@@ -586,15 +617,17 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
                         wb = s;
                         v0 = load_st(i0, w0, wb);
                     }
+                    if (screened && s != snext) continue;  // no row of this stage is needed: not sent
                     const int ra = __shfl_sync(FULLMASK, v0, s - wb);
                     const int nr = __shfl_sync(FULLMASK, v0, s - wb + 1) - ra;
                     uint32_t m8 = 0xffu;  // this lane's row: bit w = warp w evaluates its block
                     uint32_t need = nr == 32 ? FULLMASK : ((1u << nr) - 1u);
                     if (screened) {
                         m8 = m8n;
-                        if (s + 1 < nst) m8n = __ldg(A.stage_m8 + (int64_t)(sbase + s + 1) * SR + lane);
+                        snext = next_on(s + 1);
+                        if (snext < nst) m8n = __ldg(A.stage_m8 + (int64_t)(sbase + snext) * SR + lane);
                         need = __ballot_sync(FULLMASK, m8 != 0u);
-                        if (!need) continue;  // no row of this stage is needed: the stage is not sent
+                        if (!need) continue;  // (not reached: the stage's bit says some row is needed)
                     }
                     uint32_t wmask = 0u;   // lane w < CONSUMERS: rows evaluated by warp w (screened)
                     uint32_t tiles = 0u;
@@ -623,6 +656,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
                     // first, the small ones and the header after it.
                     if (lane == 0) {
                         mbar_expect(&S.full[slot], cdata + 2u * abytes + cbytes);
+                        cstreamed += cdata;
                         if (!tiled && need == FULLMASK) {
                             tma_box(maps, TMA_BOXES - 1, S.stage[slot], col0, y0, &S.full[slot]);
                         } else {
@@ -670,6 +704,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
             i1 = i2; w1 = w2;
             i2r = i3r;
         }
+        if (lane == 0 && A.c_streamed) atomicAdd(A.c_streamed, cstreamed);
         if (!ok) {
             if (lane == 0) atomicOr(A.err, 1);
             // wait (bounded) for the copies already issued into the ring
@@ -720,7 +755,12 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
         x.rA = S.rowA[slot];
         const int4* rG = S.rowG[slot];
         const uint32_t wrows = A.unit_need ? S.rmaskw[slot][warp] : FULLMASK;  // rows this warp evaluates
-        if (SNAP) {
+        if (wrows == 0u) {
+            // screened, and no block of this warp's tile in the stage is needed: a
+            // needed block that continued here or started here would have rows in
+            // wrows, so nothing is open for this warp past the stage
+            blk.gend = x.ra + x.nr;
+        } else if (SNAP) {
             // every block: z~ and o~ of Def. 1 for the snapshot
             int r = 0;
             while (r < x.nr) {
@@ -768,6 +808,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
 // for the row's group (bit w = tile w of the item's 256 columns), from the
 // unit bitmask, so that the evaluation kernel's producer reads them without
 // a chain of dependent loads.  One block per active item.
+static_assert(SR == 32, "k_stage_masks: a warp covers one stage");
 __global__ void __launch_bounds__(256) k_stage_masks(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
@@ -775,6 +816,8 @@ __global__ void __launch_bounds__(256) k_stage_masks(const EvalArgs A)
     if (A.item_active && !A.item_active[d.item]) return;
     const int tile0 = d.col0 / TW;  // a multiple of NWARPS: the item's tiles share one mask word
     uint8_t* out = const_cast<uint8_t*>(A.stage_m8) + (int64_t)d.sbase * SR;
+    // a warp's 32 entries are one stage's rows (SR == 32): the stage's bit in
+    // stage_need is set when some row is needed, else cleared
     for (int q = threadIdx.x; q < d.nst * SR; q += blockDim.x) {
         const int st = q / SR, i = q % SR;
         const int ra = A.stage_row0[d.st0 + st], re = A.stage_row0[d.st0 + st + 1];
@@ -784,6 +827,12 @@ __global__ void __launch_bounds__(256) k_stage_masks(const EvalArgs A)
             m8 = (A.unit_need[(int64_t)l * A.unit_words + (tile0 >> 5)] >> (tile0 & 31)) & 0xffu;
         }
         out[q] = (uint8_t)m8;
+        const bool any = __ballot_sync(FULLMASK, m8 != 0u) != 0u;
+        if ((threadIdx.x & 31) == 0) {
+            const int gs = d.sbase + st;
+            if (any) atomicOr(A.stage_need + (gs >> 5), 1u << (gs & 31));
+            else atomicAnd(A.stage_need + (gs >> 5), ~(1u << (gs & 31)));
+        }
     }
 }
 
@@ -847,6 +896,7 @@ void launch_split_finish(const EvalArgs& a, cudaStream_t st)
 // depend on scheduling.
 constexpr int EXACT_THREADS = 256;
 constexpr int XCOLS = 2;
+static_assert(XCOLS == 2, "the tall-class kernel finishes column q on thread q");
 constexpr int XUNROLL = 4;
 
 // The warp's sum of a double-float value, in a fixed xor tree; lane 0's result.
@@ -866,12 +916,15 @@ __global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact(const EvalArgs A)
     if (A.gate && !*A.gate) return;
     const int ne = min(A.ctl->nxent, A.xent_cap);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = EXACT_THREADS / 32;
+    __shared__ FxScale fx1;  // one problem: the evaluation's scale
+    if (threadIdx.x == 0 && !A.pfx && ne > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
+    __syncthreads();
     int pprob = -1;          // the problem of the psi sums held by lane 0
     long long ph = 0, pl = 0;
     for (int t = blockIdx.x * nw + warp; t < ne; t += gridDim.x * nw) {
         const XEntry E = A.xent[t];
         const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
-        const FxScale fx = prob_fx(A, E.prob);
+        const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
         if (E.prob != pprob) {  // psi of another problem: flush the held sums
             if (lane == 0 && (ph | pl) != 0) {
                 atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
@@ -974,31 +1027,38 @@ __global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact(const EvalArgs A)
     }
 }
 
-// Classes taller than XTALL_ROWS: one CTA per block set at a time, thread t
-// taking rows gstart + t + EXACT_THREADS u.  The CTA's sums: each warp's
-// fixed xor tree, then the warps' sums in warp order.  The first sweep keeps
-// the positive parts [f]_+ (hi) of its first XT_CACHED_ROWS rows in shared
-// memory, so the second sweep reads C again only for rows past them.
-constexpr int XT_CACHED_ROWS = 4096;
-constexpr int XT_SLOTS = XT_CACHED_ROWS / EXACT_THREADS;  // rows per thread kept
+// Classes taller than XTALL_ROWS: one CTA of TALL_THREADS per block set at a
+// time, thread t taking rows gstart + t + TALL_THREADS u; all of a class's
+// loads of a sweep (up to XT_CACHED_ROWS rows) are in flight together.  The
+// CTA's sums: each warp's fixed xor tree, then the warps' sums in warp order
+// (thread q finishes column q).  The first sweep keeps the positive parts
+// [f]_+ (hi) of its first XT_CACHED_ROWS rows in shared memory, so the second
+// sweep reads C again only for rows past them.
+constexpr int TALL_THREADS = 256;
+constexpr int XT_UNROLL = 8;
+constexpr int XT_SLOTS = 16;  // rows per thread kept
+constexpr int XT_CACHED_ROWS = TALL_THREADS * XT_SLOTS;
 
-__global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact_tall(const EvalArgs A)
+__global__ void __launch_bounds__(TALL_THREADS, 2) k_exact_tall(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
     const int ne = min(A.ctl->nxtall, A.xtall_cap);
-    constexpr int NW = EXACT_THREADS / 32;
+    constexpr int NW = TALL_THREADS / 32;
     __shared__ float red[NW][XCOLS][4];
     __shared__ float sv[XCOLS];
-    __shared__ float fkeep[XT_SLOTS][XCOLS][EXACT_THREADS];  // [row slot][column][thread]: [f]_+ hi
+    __shared__ float fkeep[XT_SLOTS][XCOLS][TALL_THREADS];  // [row slot][column][thread]: [f]_+ hi
+    __shared__ FxScale fx1;  // one problem: the evaluation's scale
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    int pprob = -1;  // the problem of the psi sums held by thread 0
+    if (tid == 0 && !A.pfx && ne > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
+    __syncthreads();
+    int pprob = -1;  // thread q < XCOLS: the problem of the psi sums it holds
     long long ph = 0, pl = 0;
     for (int t = blockIdx.x; t < ne; t += gridDim.x) {
         const XEntry E = A.xtall[t];
         const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
-        const FxScale fx = prob_fx(A, E.prob);
+        const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
         if (E.prob != pprob) {
-            if (tid == 0 && (ph | pl) != 0) {
+            if (tid < XCOLS && (ph | pl) != 0) {
                 atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
                 atomicAdd(A.psix + 2 * pprob + 1, (unsigned long long)pl);
             }
@@ -1024,32 +1084,35 @@ __global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact_tall(const EvalArgs 
             Acc acc[XCOLS];
 #pragma unroll
             for (int q = 0; q < XCOLS; q++) acc[q] = Acc{0.f, 0.f, 0.f, 0.f};
-            for (int R0 = E.gstart; R0 < E.gend; R0 += EXACT_THREADS * XUNROLL) {
-                float c[XUNROLL][XCOLS];
-                float4 a[XUNROLL];
+            for (int R0 = E.gstart; R0 < E.gend; R0 += TALL_THREADS * XT_UNROLL) {
+                float c[XT_UNROLL][XCOLS];
+                float ax[XT_UNROLL], ay[XT_UNROLL], az[XT_UNROLL];
 #pragma unroll
-                for (int u = 0; u < XUNROLL; u++) {
-                    const int R = R0 + EXACT_THREADS * u + tid;
+                for (int u = 0; u < XT_UNROLL; u++) {
+                    const int R = R0 + TALL_THREADS * u + tid;
                     const bool in = R < E.gend;
-                    a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+                    const float4 a = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+                    ax[u] = a.x;
+                    ay[u] = a.y;
+                    az[u] = a.z;
 #pragma unroll
                     for (int q = 0; q < XCOLS; q++) c[u][q] = (in && kc[q] >= 0) ? __ldg(cp[q] + (int64_t)R * pd.ldc) : 0.f;
                 }
+                const int slot0 = (R0 - E.gstart) / TALL_THREADS;  // the same for the whole CTA
 #pragma unroll
-                for (int u = 0; u < XUNROLL; u++) {
-                    const int slot = (R0 - E.gstart) / EXACT_THREADS + u;  // the same for the whole CTA
+                for (int u = 0; u < XT_UNROLL; u++) {
 #pragma unroll
                     for (int q = 0; q < XCOLS; q++) {
                         float fk = 0.f;
-                        if (maybe_pos(a[u].z, c[u][q], bp[q])) {
+                        if (maybe_pos(az[u], c[u][q], bp[q])) {
                             float fh, fl;
-                            f_exact(a[u].x, a[u].y, bh[q], bl[q], c[u][q], fh, fl);
+                            f_exact(ax[u], ay[u], bh[q], bl[q], c[u][q], fh, fl);
                             if (fh > 0.f) {
                                 acc_p(fh, fl, acc[q]);
                                 fk = fh;
                             }
                         }
-                        if (slot < XT_SLOTS) fkeep[slot][q][tid] = fk;
+                        if (slot0 + u < XT_SLOTS) fkeep[slot0 + u][q][tid] = fk;
                     }
                 }
             }
@@ -1066,26 +1129,26 @@ __global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact_tall(const EvalArgs 
                 }
             }
             __syncthreads();
-            if (tid == 0) {
-#pragma unroll
-                for (int q = 0; q < XCOLS; q++) {
-                    sv[q] = 0.f;
-                    if (kc[q] < 0) continue;
+            if (tid < XCOLS) {  // thread q: column q
+                const int q = tid;
+                const int kq = q == 0 ? kc[0] : kc[XCOLS - 1];
+                float sq = 0.f;
+                if (kq >= 0) {
                     Acc T = {0.f, 0.f, 0.f, 0.f};
                     for (int w = 0; w < NW; w++) {  // in warp order
                         df_add(T.Sh, T.Sl, red[w][q][0], red[w][q][1]);
                         df_add(T.Ph, T.Pl, red[w][q][2], red[w][q][3]);
                     }
                     float psh, psl;
-                    const float sq = block_scale(T.Sh, T.Sl, A, psh, psl);
-                    const int colg = E.colg0 + kc[q];
+                    sq = block_scale(T.Sh, T.Sl, A, psh, psl);
+                    const int colg = E.colg0 + kq;
                     if (sq > 0.f) {
                         psi_to_fx(psh, psl, fx.to_p, ph, pl);
                         atomicAdd(A.colfx + colg, (unsigned long long)col_q(sq, T.Ph, T.Pl, fx.to_cf));
                     }
                     if (A.zt) A.zt[(int64_t)E.l * A.ntiles * TW + colg] = z_up(T.Sh, T.Sl);
-                    sv[q] = sq;
                 }
+                sv[q] = sq;
             }
             __syncthreads();
             float s[XCOLS];
@@ -1098,8 +1161,8 @@ __global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact_tall(const EvalArgs 
             if (anys) {  // (uniform)
                 // the kept rows: [f]_+ from shared memory
                 const int kept = min(E.gend - E.gstart, XT_CACHED_ROWS);
-                for (int k = 0; k < XT_SLOTS && k * EXACT_THREADS < kept; k++) {
-                    const int R = E.gstart + EXACT_THREADS * k + tid;
+                for (int k = 0; k < XT_SLOTS && k * TALL_THREADS < kept; k++) {
+                    const int R = E.gstart + TALL_THREADS * k + tid;
                     unsigned long long tq = 0ull;
 #pragma unroll
                     for (int q = 0; q < XCOLS; q++) {
@@ -1109,36 +1172,31 @@ __global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact_tall(const EvalArgs 
                     if (tq) atomicAdd(A.rowfx + R, tq);  // (fh > 0 only for rows of the set)
                 }
                 // the rows past them: C again
-                for (int R0 = E.gstart + XT_CACHED_ROWS; R0 < E.gend; R0 += EXACT_THREADS * XUNROLL) {
-                    float c[XUNROLL][XCOLS];
-                    float4 a[XUNROLL];
+                for (int R0 = E.gstart + XT_CACHED_ROWS; R0 < E.gend; R0 += TALL_THREADS * XT_UNROLL) {
 #pragma unroll
-                    for (int u = 0; u < XUNROLL; u++) {
-                        const int R = R0 + EXACT_THREADS * u + tid;
-                        const bool in = R < E.gend;
-                        a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
-#pragma unroll
-                        for (int q = 0; q < XCOLS; q++)
-                            c[u][q] = (in && s[q] > 0.f) ? __ldg(cp[q] + (int64_t)R * pd.ldc) : 0.f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < XUNROLL; u++) {
+                    for (int u = 0; u < XT_UNROLL; u++) {
+                        const int R = R0 + TALL_THREADS * u + tid;
+                        if (R >= E.gend) break;
+                        const float4 a = __ldg(A.rowA + R);
                         unsigned long long tq = 0ull;
 #pragma unroll
-                        for (int q = 0; q < XCOLS; q++)
-                            if (s[q] > 0.f && maybe_pos(a[u].z, c[u][q], bp[q])) {
+                        for (int q = 0; q < XCOLS; q++) {
+                            if (!(s[q] > 0.f)) continue;
+                            const float cq = __ldg(cp[q] + (int64_t)R * pd.ldc);
+                            if (maybe_pos(a.z, cq, bp[q])) {
                                 float fh, fl;
-                                f_exact(a[u].x, a[u].y, bh[q], bl[q], c[u][q], fh, fl);
+                                f_exact(a.x, a.y, bh[q], bl[q], cq, fh, fl);
                                 if (fh > 0.f) tq += t_q(__fmul_rn(s[q], fh), fx.to_rf);
                             }
-                        if (tq) atomicAdd(A.rowfx + R0 + EXACT_THREADS * u + tid, tq);
+                        }
+                        if (tq) atomicAdd(A.rowfx + R, tq);
                     }
                 }
             }
-            __syncthreads();  // red and sv are reused by the next columns
+            __syncthreads();  // red, sv and fkeep are reused by the next columns
         }
     }
-    if (tid == 0 && pprob >= 0 && (ph | pl) != 0) {
+    if (tid < XCOLS && pprob >= 0 && (ph | pl) != 0) {
         atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
         atomicAdd(A.psix + 2 * pprob + 1, (unsigned long long)pl);
     }
@@ -1147,7 +1205,7 @@ __global__ void __launch_bounds__(EXACT_THREADS, 2) k_exact_tall(const EvalArgs 
 void launch_exact(const EvalArgs& a, int n_sm, cudaStream_t st)
 {
     k_exact<<<4 * n_sm, EXACT_THREADS, 0, st>>>(a);
-    k_exact_tall<<<2 * n_sm, EXACT_THREADS, 0, st>>>(a);
+    k_exact_tall<<<2 * n_sm, TALL_THREADS, 0, st>>>(a);
 }
 
 void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall)
