@@ -6,6 +6,11 @@ over the whole workload, through the library's C ABI.  Default workload: m = n
 features, C FP32 (1.6 GB) squared-Euclidean scaled to max 1, gamma = 1,
 mu = 0.5, synthetic and seeded.  C is larger than L2, so no flush is needed.
 
+Beside the step (1 GPU): the same workload solved from zero to a relative
+objective error of 1e-6, dense and screened (Alg. 1), with one dense and one
+screened evaluation timed at the iterate where the solve gets there; the
+batched workload; the learned warm start.
+
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
 of the workload on its GPU (the single-problem path is not sharded).
 ``--impl reference`` times the FP64 CPU oracle on host cores instead.
@@ -94,18 +99,92 @@ def _eval_point(C, k):
     return alpha, beta.contiguous()
 
 
+class _Nvml:
+    """Read-only NVML queries through ctypes: SM clock, its maximum, power
+    draw and the active clock event reasons of one GPU (by UUID)."""
+
+    # clock event reason bits (nvml.h)
+    REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown"}
+
+    def __init__(self, uuid):
+        import ctypes
+        self.c = ctypes
+        self.lib = ctypes.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise RuntimeError("nvmlInit failed")
+        self.dev = ctypes.c_void_p()
+        if self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), ctypes.byref(self.dev)) != 0:
+            raise RuntimeError("no NVML device for " + uuid)
+        self.reasons_fn = getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+            self.lib.nvmlDeviceGetCurrentClocksThrottleReasons
+        v = ctypes.c_uint()
+        if self.lib.nvmlDeviceGetMaxClockInfo(self.dev, 1, ctypes.byref(v)) != 0:
+            raise RuntimeError("nvmlDeviceGetMaxClockInfo failed")
+        self.max_sm = float(v.value)
+
+    def sample(self):
+        c = self.c
+        sm, mw, rs = c.c_uint(), c.c_uint(), c.c_ulonglong()
+        if self.lib.nvmlDeviceGetClockInfo(self.dev, 1, c.byref(sm)) != 0:  # NVML_CLOCK_SM
+            return None
+        self.lib.nvmlDeviceGetPowerUsage(self.dev, c.byref(mw))
+        self.reasons_fn(self.dev, c.byref(rs))
+        return float(sm.value), self.max_sm, mw.value / 1000.0, int(rs.value)
+
+    def close(self):
+        try:
+            self.lib.nvmlShutdown()
+        except Exception:
+            pass
+
+
 class ClockSampler:
-    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    """SM clock and throttle reasons sampled during a region.
+
+    With NVML (read through ctypes), a thread samples every 2 ms and the
+    region is marked by ``mark(True)`` / ``mark(False)`` around the timed
+    work: the summary keeps the samples inside the marks (at least the three
+    nearest to the region when it is shorter than that).  Without NVML,
+    ``nvidia-smi -lms 100`` writes the samples to a file that the summary
+    reads (CSV: sm, max sm, power, reasons bitmask, then the four reasons
+    hw_slowdown, hw_thermal_slowdown, sw_thermal_slowdown, sw_power_cap)."""
 
     Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    PERIOD_S = 0.002
 
     def __init__(self, uuid=None):
         self.uuid = uuid
         self.proc = None
+        self.nvml = None
+        self.samples = []   # (host time, sm MHz, max sm MHz, W, reasons bitmask)
+        self.window = None  # host times of the marks
+        self._t0 = None
+        self._stop = None
+        self.thread = None
 
     def __enter__(self):
+        import threading
+        if self.uuid:
+            try:
+                self.nvml = _Nvml(self.uuid)
+            except Exception:
+                self.nvml = None
+        if self.nvml is not None:
+            self._stop = threading.Event()
+
+            def run():
+                while not self._stop.is_set():
+                    r = self.nvml.sample()
+                    if r is not None:
+                        self.samples.append((time.perf_counter(),) + r)
+                    time.sleep(self.PERIOD_S)
+
+            self.thread = threading.Thread(target=run, daemon=True)
+            self.thread.start()
+            time.sleep(0.02)
+            return self
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         cmd = ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "100"]
         if self.uuid:
@@ -117,7 +196,20 @@ class ClockSampler:
         time.sleep(0.3)
         return self
 
+    def mark(self, start):
+        t = time.perf_counter()
+        if start:
+            self._t0 = t
+        else:
+            self.window = (self._t0, t)
+
     def __exit__(self, *a):
+        if self.thread is not None:
+            time.sleep(0.01)
+            self._stop.set()
+            self.thread.join(timeout=5)
+            self.nvml.close()
+            return
         if self.proc is not None:
             self.proc.terminate()
             try:
@@ -126,7 +218,32 @@ class ClockSampler:
                 self.proc.kill()
         self.f.flush()
 
+    def _summary_nvml(self):
+        rows = self.samples
+        where = "all samples"
+        if self.window:
+            t0, t1 = self.window
+            inside = [r for r in rows if t0 <= r[0] <= t1]
+            if len(inside) >= 3:
+                rows, where = inside, "inside the timed region"
+            else:
+                mid = 0.5 * (t0 + t1)
+                rows = sorted(rows, key=lambda r: abs(r[0] - mid))[:3]
+                where = f"{len(inside)} inside the timed region, nearest 3 used"
+        if not rows:
+            return None
+        reasons = set()
+        for r in rows:
+            for bit, nm in _Nvml.REASONS.items():
+                if r[4] & bit:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[1] for r in rows), "sm_max_mhz": max(r[2] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows), "source": "nvml, every 2 ms",
+                "window": where, "power_w_median": statistics.median(r[3] for r in rows)}
+
     def summary(self):
+        if self.samples:
+            return self._summary_nvml()
         try:
             rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
             os.unlink(self.f.name)
@@ -194,13 +311,58 @@ def cpu_baseline(p, alpha, beta, gamma, mu, budget_s=10.0, ncols=None):
                       f"({el:.1f} s), scaled by n/{ncols}"}
 
 
+def _timed(fn, k, stream):
+    """Mean device time (ms) of k calls of fn, CUDA events on the launching
+    stream, after three untimed calls."""
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(k):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / k
+
+
+def _stream_timed(h, fn, k, stream):
+    """(mean ms of a whole call, mean ms of its k_stream launch)."""
+    import paper_2303_07597_gb300 as pk
+    fn()
+    pk.ot_gs_set_timing(h, True)
+    ms = _timed(fn, k, stream)
+    pk.ot_gs_set_timing(h, False)
+    nl, kms = pk.ot_gs_get_timing(h)
+    return ms, kms / max(1, nl)
+
+
+def screened_needed_bytes(skip_mask, sizes, n, L):
+    """Bytes one screened evaluation (Alg. 2) must read at least: C of every
+    block (l, j) it does not skip (g_l rows x 4 bytes), the snapshot's
+    z~ and o~ of every block (FP32 each), alpha and beta.  skip_mask: L x
+    ceil(n/32) words, bit j % 32 of word (l, j / 32) set when block (l, j) is
+    skipped; sizes: rows per class."""
+    words = np.asarray(skip_mask, dtype=np.uint32).reshape(L, -1)
+    bits = np.unpackbits(words.view(np.uint8), bitorder="little").reshape(L, -1)[:, :n]
+    skipped = bits.sum(axis=1).astype(np.int64)
+    c_needed = int(np.sum(np.asarray(sizes, dtype=np.int64) * (n - skipped))) * 4
+    m = int(np.sum(sizes))
+    return c_needed + 8 * L * n + 8 * (m + n), c_needed, int(skipped.sum())
+
+
 def solve_report(args, dev):
     """Time to a relative objective error of 1e-6 (|D_k - D*| <= 1e-6 |D*|)
     for the plain (dense) and the screened device solver from the zero start
     (Alg. 1), read from the solver's device-time objective trace.  D* is the
-    objective after a longer dense run.  The screened solver visits the same
-    iterates bit for bit (each screened evaluation equals the dense one), so
-    both reach the threshold at the same iteration; only the time differs."""
+    objective of a dense run to stagnation (ftol 1e-14).  The screened solver
+    visits the same iterates bit for bit (each screened evaluation equals the
+    dense one), so both reach the threshold at the same iteration; only the
+    time differs.  At that iterate, with the screened run's own snapshot and
+    set N, one dense and one screened evaluation are timed apart (roofline of
+    each: the dense one against 4mn + 8(m+n) bytes, the screened one against
+    the bytes Alg. 2 must read there)."""
     import torch
     import paper_2303_07597_gb300 as pk
     name = args.solve_workload
@@ -209,9 +371,12 @@ def solve_report(args, dev):
     a = torch.from_numpy(p.a).to(dev)
     b = torch.from_numpy(p.b).to(dev)
     lab = torch.from_numpy(p.labels).to(dev)
+    stream = torch.cuda.current_stream()
     ref = pk.GroupSparseOT(C, a, b, lab, p.L, cfg["gamma"], cfg["mu"])
-    ref.set_params(use_screening=0)
+    ref.set_params(use_screening=0, ftol=1e-14)
+    t0 = time.perf_counter()
     ref.solve(0.0, args.solve_ref_iters)
+    ref_s = time.perf_counter() - t0
     D, t, ev = ref.trace()
     sol = ref.solution()
     ref.close()
@@ -219,24 +384,60 @@ def solve_report(args, dev):
     rel = np.abs(D - Dstar) / abs(Dstar)
     hit = np.nonzero(rel <= 1e-6)[0]
     k = int(hit[0]) if len(hit) and hit[0] < len(D) - 1 else -1
-    out = {"workload": f"{name}: m=n={cfg['m']}, L={cfg['L']}, gamma={cfg['gamma']}, mu={cfg['mu']}",
+    out = {"workload": f"{name}: m=n={cfg['m']}, L={cfg['L']}, gamma={cfg['gamma']}, mu={cfg['mu']}, from zero",
            "D_star": Dstar, "D_star_iters": int(len(D) - 1), "D_star_grad_inf": sol["grad_inf"],
-           "iters_to_1e-6": k, "unit": "ms"}
+           "D_star_run_s": ref_s, "iters_to_1e-6": k, "unit": "ms"}
     if k < 0:
         out["note"] = "the reference run did not reach the threshold before its last iterate"
         return out
     out["dense_ms"] = float(t[k])
     out["dense_evals"] = int(ev[k])
     scr = pk.GroupSparseOT(C, a, b, lab, p.L, cfg["gamma"], cfg["mu"])
-    scr.set_params(use_screening=1)
+    scr.set_params(use_screening=1, ftol=0.0)
     scr.solve(0.0, k)
     Ds, ts, evs = scr.trace()
     st = scr.stats()
-    scr.close()
     out["screened_ms"] = float(ts[k])
-    out["screened_same_iterates"] = bool(len(Ds) > k and Ds[k] == D[k])
+    out["screened_evals"] = int(evs[k])
+    out["screened_same_iterates"] = bool(len(Ds) > k and np.array_equal(Ds[:k + 1], D[:k + 1]))
     out["screened_units_computed_frac"] = st["units_computed"] / max(1, st["units_total"])
+    out["screened_c_bytes_frac"] = st["c_bytes"] / max(1.0, 4.0 * p.m * p.n * st["evals"])
     out["screened_vs_dense"] = out["dense_ms"] / out["screened_ms"]
+    # per-iteration time over the last fifth of the run, where the iterates move least
+    k0 = int(0.8 * k)
+    out["last_fifth_ms_per_iter"] = {"dense": float(t[k] - t[k0]) / (k - k0),
+                                     "screened": float(ts[k] - ts[k0]) / (k - k0)}
+    # evaluations at the iterate of the crossing
+    it = scr.solution()
+    al, be = it["alpha"], it["beta"]
+    outv = torch.empty(1 + p.m + p.n, dtype=torch.float64, device=dev)
+    peak, peak_kind = _peaks()
+    reps = args.solve_eval_reps
+    dense_bytes = 4.0 * p.m * p.n + 8.0 * (p.m + p.n)
+    ms, kms = _stream_timed(scr.h, lambda: pk.ot_gs_grad(scr.h, al, be, outv), reps, stream)
+    out["dense_eval_at_iterate"] = {
+        "iterate": k, "step_ms": ms, "k_stream_ms": kms, "alg_bytes": dense_bytes,
+        "roofline": {"bound": "hbm", "kernel": "k_stream", "achieved": dense_bytes / kms / 1e6, "peak": peak,
+                     "unit": "GB/s", "frac": dense_bytes / kms / 1e6 / peak, "peak_kind": peak_kind},
+        "step_frac": dense_bytes / ms / 1e6 / peak}
+    Dd = float(outv[0].item())
+    skip = torch.empty(p.L * ((p.n + 31) // 32), dtype=torch.int32, device=dev)
+    pk.ot_gs_grad_screened(scr.h, al, be, outv, skip)
+    sizes = np.bincount(p.labels, minlength=p.L)
+    need, c_need, nskip = screened_needed_bytes(skip.cpu().numpy().view(np.uint32), sizes, p.n, p.L)
+    pk.ot_gs_reset_stats(scr.h)
+    ms_s, kms_s = _stream_timed(scr.h, lambda: pk.ot_gs_grad_screened(scr.h, al, be, outv), reps, stream)
+    st2 = scr.stats()
+    per = max(1, st2["evals"])
+    out["screened_eval_at_iterate"] = {
+        "iterate": k, "snapshot_iterate": k - (k % scr.params().r or scr.params().r), "step_ms": ms_s, "k_stream_ms": kms_s,
+        "blocks_skipped_frac": nskip / (p.L * p.n), "needed_bytes": need, "needed_c_bytes": c_need,
+        "streamed_c_bytes": st2["c_bytes"] / per,
+        "roofline": {"bound": "hbm", "kernel": "whole screened evaluation", "achieved": need / ms_s / 1e6,
+                     "peak": peak, "unit": "GB/s", "frac": need / ms_s / 1e6 / peak, "peak_kind": peak_kind},
+        "same_D_as_dense": float(outv[0].item()) == Dd,
+        "vs_dense_eval": ms / ms_s}
+    scr.close()
     return out
 
 
@@ -705,16 +906,20 @@ def run_gpu(args):
         uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
     except Exception:
         pass
+    kernels0 = solver.stats()["kernels"]
     pk.ot_gs_set_timing(solver.h, True)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(uuid) as cs:
         torch.cuda.synchronize()
+        cs.mark(True)
         e0.record(stream)
         for _ in range(args.steps):
             step()
         e1.record(stream)
         torch.cuda.synchronize()
+        cs.mark(False)
     pk.ot_gs_set_timing(solver.h, False)
+    kernels = solver.stats()["kernels"] - kernels0
     launches, kern_ms = pk.ot_gs_get_timing(solver.h)
     el_ms = max_over_ranks(e0.elapsed_time(e1), dev)
     if world > 1:
@@ -774,7 +979,9 @@ def run_gpu(args):
             "cpu_baseline": cb,
             "e2e": {"value": job_throughput(k_e2e, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (m + n), "d2h_bytes_per_step": 8 * (1 + m + n)},
-            "gpu_launches": 5 * args.steps,  # prep, stream, split finish, pass B, reduce
+            # the library's own count: prep, k_stream, the two exact-sum kernels, k_reduce
+            # (and k_split_finish when a class is split across items) per evaluation
+            "gpu_launches": kernels,
             "clocks": clocks,
         }
         if world == 1 and not args.no_solve:
@@ -801,8 +1008,10 @@ def main():
     ap.add_argument("--cpu-budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true", help="skip the time-to-1e-6 solve measurement")
-    ap.add_argument("--solve-workload", choices=sorted(WORKLOADS), default="mid")
-    ap.add_argument("--solve-ref-iters", type=int, default=20000)
+    ap.add_argument("--solve-workload", choices=sorted(WORKLOADS), default="large")
+    ap.add_argument("--solve-ref-iters", type=int, default=65000)
+    ap.add_argument("--solve-eval-reps", type=int, default=50,
+                    help="evaluations timed at the iterate where the solve reaches 1e-6")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-workload solve measurement")
     ap.add_argument("--batch-problems", type=int, default=BATCH["nprob"])
     ap.add_argument("--batch-ref-iters", type=int, default=20000)

@@ -84,6 +84,7 @@ typedef struct {
     int64_t units_computed;   /* units whose C tile was streamed */
     int64_t snapshots;        /* snapshot refreshes (dense passes) */
     double  c_bytes;          /* bytes of C streamed by evaluation kernels */
+    int64_t kernels;          /* kernels launched by ot_gs_grad / ot_gs_grad_screened calls */
 } ot_gs_stats;
 
 /*

@@ -46,7 +46,8 @@ class Stats(ctypes.Structure):
                 ("blocks_total", ctypes.c_int64), ("blocks_in_N", ctypes.c_int64),
                 ("blocks_skipped", ctypes.c_int64), ("blocks_checked", ctypes.c_int64),
                 ("units_total", ctypes.c_int64), ("units_computed", ctypes.c_int64),
-                ("snapshots", ctypes.c_int64), ("c_bytes", ctypes.c_double)]
+                ("snapshots", ctypes.c_int64), ("c_bytes", ctypes.c_double),
+                ("kernels", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -468,6 +468,7 @@ bool Handle::eval_dense(const double* alpha, bool alpha_sorted, const double* be
                         double* G_sorted, const double* dir, bool snap)
 {
     prep(alpha, alpha_sorted, beta);
+    if (!eval_gate) stats_host.kernels += 1;
     return eval_dense_core(beta, out_caller, G_sorted, dir, snap);
 }
 
@@ -482,7 +483,10 @@ bool Handle::eval_dense_core(const double* beta, double* out_caller, double* G_s
     eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(nullptr, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
-    if (!eval_gate) count_dense_evals(1);
+    if (!eval_gate) {
+        count_dense_evals(1);
+        stats_host.kernels += 4 + (e.nsets > 0);  // stream, exact (2), reduce, split finish
+    }
     return ck(cudaGetLastError(), "eval launch");
 }
 

@@ -410,6 +410,7 @@ bool Handle::eval_screened(const double* alpha, bool alpha_sorted, const double*
     if (!ensure_screen()) return false;
     if (!snap_valid && !zero_snapshot()) return false;
     prep(alpha, alpha_sorted, beta);
+    if (!eval_gate) stats_host.kernels += 1;
     return eval_screened_prepped(beta, G_sorted, dir, out_caller);
 }
 
@@ -432,7 +433,11 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
-    if (!eval_gate) count_screened_evals(1);
+    if (!eval_gate) {
+        count_screened_evals(1);
+        // deltas (2), theta, screen, stage masks, stream, exact (2), reduce, split finish
+        stats_host.kernels += 9 + (e.nsets > 0);
+    }
     return ck(cudaGetLastError(), "screened eval launch");
 }
 

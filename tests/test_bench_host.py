@@ -72,3 +72,40 @@ def test_clock_summary_reads_the_samples_and_the_throttle_reasons(tmp_path):
     got = cs.summary()
     assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"], "samples": 3}
     assert not path.exists()  # the sample file is removed once read
+
+
+def test_clock_summary_keeps_the_samples_inside_the_timed_region():
+    """NVML samples: only those between the marks count; the reason bits map
+    to their names (sw_power_cap 0x4, hw_slowdown 0x8)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    cs = bench.ClockSampler()
+    cs.samples = [(0.0, 1000.0, 2070.0, 500.0, 0x8)] + \
+        [(1.0 + 0.001 * k, 2070.0 - k, 2070.0, 1200.0, 0x4 if k == 2 else 0) for k in range(5)] + \
+        [(9.0, 500.0, 2070.0, 300.0, 0x40)]
+    cs.window = (0.9, 1.1)
+    got = cs.summary()
+    assert got["samples"] == 5 and got["sm_mhz"] == 2068.0 and got["reasons"] == ["sw_power_cap"]
+    assert got["window"] == "inside the timed region"
+    cs.window = (5.0, 5.0001)  # shorter than a sample period: the three nearest
+    got = cs.summary()
+    assert got["samples"] == 3 and "nearest 3" in got["window"]
+
+
+def test_screened_needed_bytes_counts_the_unskipped_blocks():
+    """C bytes of every block not skipped (rows of its class x 4 bytes), the
+    snapshot (8 bytes a block) and the duals, from a skip mask of L x
+    ceil(n/32) words (bit j % 32 of word j / 32)."""
+    np = pytest.importorskip("numpy")
+    sys.path.insert(0, ROOT)
+    import bench
+    L, n = 3, 40
+    sizes = [5, 0, 7]
+    mask = np.zeros((L, 2), dtype=np.uint32)
+    mask[0, 0] = 0xFFFFFFFF          # class 0: columns 0..31 skipped
+    mask[0, 1] = 0b101               # and 32, 34
+    mask[2, 1] = 0xFFFFFFFF          # class 2: 32..39 skipped (bits past n ignored)
+    need, c_need, nskip = bench.screened_needed_bytes(mask.ravel(), sizes, n, L)
+    assert nskip == 34 + 8
+    assert c_need == 4 * (5 * (40 - 34) + 7 * (40 - 8))
+    assert need == c_need + 8 * L * n + 8 * (12 + 40)
