@@ -85,6 +85,7 @@ typedef struct {
     int64_t snapshots;        /* snapshot refreshes (dense passes) */
     double  c_bytes;          /* bytes of C streamed by evaluation kernels */
     int64_t kernels;          /* kernels launched by ot_gs_grad / ot_gs_grad_screened calls */
+    int64_t blocks_flagged;   /* blocks whose FP32 bound left s > 0 possible (Eq. 5 formed exactly) */
 } ot_gs_stats;
 
 /*
@@ -167,8 +168,10 @@ OTGS_API int ot_gs_get_screen_state(ot_gs *h, float *zt, float *ot, double *alph
  * rebuilt (Alg. 1).  The whole iteration -- line search, evaluation, the
  * L-BFGS update and the convergence test -- runs on the device; the host
  * waits once at the end.  Stops when ||grad D||_inf <= tol.
- * Returns OTGS_OK, OTGS_ENOTCONV (maxit), OTGS_ETIMEOUT, OTGS_ELINESEARCH, or
- * an error.  Synchronises the stream.
+ * Returns OTGS_OK, OTGS_ENOTCONV (maxit), OTGS_ETIMEOUT, OTGS_ELINESEARCH,
+ * OTGS_ENONFINITE (D or the gradient at the start point is not finite, e.g.
+ * a NaN in the state set by ot_gs_set_state), or an error.  Synchronises the
+ * stream.
  */
 OTGS_API int ot_gs_solve(ot_gs *h, double tol, int32_t maxit);
 
@@ -223,6 +226,27 @@ OTGS_API int ot_gs_restore_state(ot_gs *h, const void *src, int64_t bytes);
 
 OTGS_API int ot_gs_get_stats(ot_gs *h, ot_gs_stats *s); /* host struct; synchronises */
 OTGS_API int ot_gs_reset_stats(ot_gs *h);
+
+/*
+ * Test hooks: each changes the evaluations issued after it on this handle
+ * (ot_gs_grad, ot_gs_grad_screened, ot_gs_snapshot, ot_gs_solve).
+ *   OTGS_DEBUG_STALL: value in (0, 1e10] makes the evaluation kernel's
+ *     consumer warps stop releasing their stages and its ring waits give up
+ *     after value ns: the producer then waits (at the normal 2 s limit) for
+ *     the copies it issued, the kernel records an error and returns, and D
+ *     comes out NaN.  The handle's error word stays set: later evaluations
+ *     of this handle give NaN too.  value <= 0 restores normal operation.
+ *   OTGS_DEBUG_NAN_EVAL: value > 0 makes ot_gs_solve read the objective of
+ *     its value-th evaluation and of every later one as NaN (a fake of a
+ *     failing evaluation): the line search finds no acceptable step and the
+ *     solve returns OTGS_ELINESEARCH (value 1, the start point: ENONFINITE).
+ *     value <= 0: off.
+ * Host only, no synchronisation.  Errors: OTGS_EINVAL (unknown switch, a
+ * limit above 10 s).
+ */
+#define OTGS_DEBUG_STALL 2
+#define OTGS_DEBUG_NAN_EVAL 3
+OTGS_API int ot_gs_debug(ot_gs *h, int what, int64_t value);
 
 /*
  * Kernel timing for benchmarks: while enabled (enable != 0), every launch of

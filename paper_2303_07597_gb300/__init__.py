@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("blocks_skipped", ctypes.c_int64), ("blocks_checked", ctypes.c_int64),
                 ("units_total", ctypes.c_int64), ("units_computed", ctypes.c_int64),
                 ("snapshots", ctypes.c_int64), ("c_bytes", ctypes.c_double),
-                ("kernels", ctypes.c_int64)]
+                ("kernels", ctypes.c_int64), ("blocks_flagged", ctypes.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -86,6 +86,7 @@ def lib():
         "ot_gs_restore_state": ([P, P, i64], ctypes.c_int),
         "ot_gs_reset_stats": ([P], ctypes.c_int),
         "ot_gs_set_timing": ([P, ctypes.c_int], ctypes.c_int),
+        "ot_gs_debug": ([P, ctypes.c_int, ctypes.c_int64], ctypes.c_int),
         "ot_gs_get_timing": ([P, P, P], ctypes.c_int),
         "ot_gs_last_error": ([P], ctypes.c_char_p),
         "ot_gs_version": ([], ctypes.c_char_p),
@@ -299,6 +300,15 @@ def ot_gs_get_stats(h) -> dict:
 
 def ot_gs_reset_stats(h):
     return _check(h, lib().ot_gs_reset_stats(h))
+
+
+OTGS_DEBUG_STALL = 2
+OTGS_DEBUG_NAN_EVAL = 3
+
+
+def ot_gs_debug(h, what: int, value: int):
+    """Test hooks of later evaluations (see include/otgs.h)."""
+    return _check(h, lib().ot_gs_debug(h, ctypes.c_int(what), ctypes.c_int64(value)))
 
 
 def ot_gs_set_timing(h, enable: bool):

@@ -268,6 +268,9 @@ bool Handle::init(int32_t np, const float* const* C_, const int64_t* ldc_, const
         if (!ck(cudaGetDevice(&dev), "cudaGetDevice")) return false;
         if (!ck(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev), "SM count")) return false;
     }
+    fcount = (unsigned long long*)dalloc(sizeof(unsigned long long) * 2, "flagged block counters");
+    if (!fcount) return false;
+    if (!ck(cudaMemsetAsync(fcount, 0, sizeof(unsigned long long) * 2, st), "memset counters")) return false;
     if (!stream_prepare()) return fail(OTGS_ECUDA, "cudaFuncSetAttribute(evaluation kernel)");
     if (!setup_plan(PlanParams())) return false;
     nred = reduce_blocks((int32_t)m, (int32_t)n);
@@ -387,6 +390,9 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.psix = ctl_psi(ctl);
     e.xent = xent; e.xent_cap = xent_cap;
     e.xtall = xtall; e.xtall_cap = xtall_cap;
+    e.fcount = fcount;
+    e.wait_ns = (unsigned long long)std::max<int64_t>(dbg_stall_ns, 0);
+    e.stall = dbg_stall_ns > 0;
     e.split_part = split_part;
     e.sets = dp.sets; e.nsets = (int32_t)hp.sets.size();
     e.gate = eval_gate;
@@ -444,7 +450,7 @@ void Handle::prep(const double* alpha, bool alpha_sorted, const double* beta)
 }
 
 // Launch of the evaluation kernel, optionally bracketed by timing events.
-void Handle::eval_launch(const EvalArgs& e, int n_ctas)
+int Handle::eval_launch(const EvalArgs& e, int n_ctas)
 {
     if (timing) {
         while (ev_pool.size() < ev_used + 2) {
@@ -461,6 +467,7 @@ void Handle::eval_launch(const EvalArgs& e, int n_ctas)
     }
     launch_split_finish(e, st);
     launch_exact(e, n_sm, st);
+    return 3 + (e.nsets > 0);  // stream, exact (2), split finish
 }
 
 // Dense evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.
@@ -480,12 +487,12 @@ bool Handle::eval_dense_prepped(const double* beta, double* G_sorted, const doub
 bool Handle::eval_dense_core(const double* beta, double* out_caller, double* G_sorted, const double* dir, bool snap)
 {
     EvalArgs e = eval_args(nullptr, nullptr, snap);
-    eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
+    const int nk = eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(nullptr, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     if (!eval_gate) {
         count_dense_evals(1);
-        stats_host.kernels += 4 + (e.nsets > 0);  // stream, exact (2), reduce, split finish
+        stats_host.kernels += nk + 1;  // and the reduction
     }
     return ck(cudaGetLastError(), "eval launch");
 }
@@ -604,6 +611,9 @@ int ot_gs_get_stats(ot_gs* hh, ot_gs_stats* s)
     if (!s) return OTGS_EINVAL;
     if (!h->ck(cudaStreamSynchronize(h->st), "stats sync")) return OTGS_ECUDA;
     if (!h->collect_stats()) return h->last_code;
+    unsigned long long fc[2] = {0, 0};
+    if (!h->ck(cudaMemcpy(fc, h->fcount, sizeof(fc), cudaMemcpyDeviceToHost), "stats D2H")) return OTGS_ECUDA;
+    h->stats_host.blocks_flagged = (int64_t)fc[0];
     *s = h->stats_host;
     return OTGS_OK;
 }
@@ -615,7 +625,29 @@ int ot_gs_reset_stats(ot_gs* hh)
     if (!h->ck(cudaStreamSynchronize(h->st), "stats sync")) return OTGS_ECUDA;
     h->stats_host = ot_gs_stats();
     h->reset_device_stats();
+    if (!h->ck(cudaMemsetAsync(h->fcount, 0, sizeof(unsigned long long) * 2, h->st), "memset counters"))
+        return OTGS_ECUDA;
     return OTGS_OK;
+}
+
+int ot_gs_debug(ot_gs* hh, int what, int64_t value)
+{
+    H_CHECK(hh);
+    Handle* h = reinterpret_cast<Handle*>(hh);
+    if (what == OTGS_DEBUG_STALL) {
+        if (value > 10000000000LL) {
+            h->fail(OTGS_EINVAL, "stall wait limit above 10 s");
+            return OTGS_EINVAL;
+        }
+        h->dbg_stall_ns = value > 0 ? value : 0;
+        return OTGS_OK;
+    }
+    if (what == OTGS_DEBUG_NAN_EVAL) {
+        h->dbg_nan_eval = value > 0 ? value : 0;
+        return OTGS_OK;
+    }
+    h->fail(OTGS_EINVAL, "unknown debug switch");
+    return OTGS_EINVAL;
 }
 
 int ot_gs_set_timing(ot_gs* hh, int enable)

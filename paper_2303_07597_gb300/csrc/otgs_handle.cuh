@@ -59,6 +59,9 @@ struct Handle {
     XEntry* xent = nullptr;         // flagged block sets for the exact-sum kernel (sized by the plan):
     XEntry* xtall = nullptr;        // classes of at most XTALL_ROWS rows, taller classes
     int32_t xent_cap = 0, xtall_cap = 0;
+    unsigned long long* fcount = nullptr;  // flagged blocks (statistics)
+    int64_t dbg_stall_ns = 0;       // test hooks (ot_gs_debug): a stalled ring with this wait limit,
+    int64_t dbg_nan_eval = 0;       //   a solve's objective NaN from this evaluation on
     float* split_part = nullptr;    // partial block sums of the pieces of split groups
     int nred = 0;
     double* block_part = nullptr;
@@ -94,7 +97,7 @@ struct Handle {
     bool timing = false;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
-    void eval_launch(const EvalArgs& e, int n_ctas);
+    int eval_launch(const EvalArgs& e, int n_ctas);  // returns the kernels launched
 
     ~Handle();
     bool init(int32_t nprob, const float* const* C, const int64_t* ldc, const double* const* a,

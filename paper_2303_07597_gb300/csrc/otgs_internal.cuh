@@ -400,6 +400,9 @@ struct EvalArgs {
     XEntry* xtall;     // those of taller classes (capacity xtall_cap)
     int32_t xent_cap, xtall_cap;
     float thr_flag;    // RD(theta^2 (1 - 2^-21)): a block whose FP32 bound stays at or below it has s = 0
+    unsigned long long* fcount;  // NULL, or a counter of the flagged blocks (statistics)
+    unsigned long long wait_ns;  // 0: the default limit of the evaluation kernel's waits; else this one
+    int32_t stall;     // test hook: the consumer warps do not release stages (the waits run out)
     float* split_part; // [slots][ITEM_COLS][SPLIT_VALS]: a piece's (S', O) per column
     const SplitSet* sets;  // block sets of split groups
     int32_t nsets;

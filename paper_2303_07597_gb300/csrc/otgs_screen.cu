@@ -430,13 +430,12 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     e.stage_need = stage_need;
     e.c_streamed = dcount + 4;
     launch_stage_masks(e, st);
-    eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
+    const int nk = eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     if (!eval_gate) {
         count_screened_evals(1);
-        // deltas (2), theta, screen, stage masks, stream, exact (2), reduce, split finish
-        stats_host.kernels += 9 + (e.nsets > 0);
+        stats_host.kernels += nk + 6;  // and deltas (2), theta, screen, stage masks, reduction
     }
     return ck(cudaGetLastError(), "screened eval launch");
 }

@@ -76,7 +76,9 @@ __global__ void k_linesearch(SolverState* S, const double* scal)
     S->evals++;
     S->accepted = 0;
     S->refresh = 0;
-    const double F = -scal[0], dphi = scal[1];
+    const double F = (S->nan_eval > 0 && S->evals >= S->nan_eval) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                                    : -scal[0];
+    const double dphi = scal[1];
     const int r = ls_update(S, F, dphi);
     if (r < 0) {
         S->status = OTGS_ELINESEARCH;
@@ -239,7 +241,10 @@ __global__ void k_start(SolverState* S, const double* scal)
     S->F = -scal[0];
     S->ginf = scal[2];
     S->evals++;
-    if (S->ginf <= S->tol) {
+    if (!isfinite(S->F) || !isfinite(S->ginf)) {  // a non-finite start point (or a failed evaluation)
+        S->status = OTGS_ENONFINITE;
+        S->done = 1;
+    } else if (S->ginf <= S->tol) {
         S->status = OTGS_OK;
         S->done = 1;
     } else if (S->maxit <= 0) {
@@ -345,6 +350,7 @@ int Solver::run(double tol, int maxit)
     init.status = OTGS_ENOTCONV;
     init.trace = trace;
     init.trace_cap = TRACE_CAP;
+    init.nan_eval = (int)std::min<int64_t>(std::max<int64_t>(h->dbg_nan_eval, 0), INT32_MAX);
     trace_len = 0;
     const bool resumed = resume;
     resume = false;

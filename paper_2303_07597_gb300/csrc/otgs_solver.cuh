@@ -24,7 +24,7 @@ struct SolverState {
     int ls_evals, have_hi, M, r, screening, maxit;
     int go;  // the current trial runs (set by the trial gate: not done, no refresh pending)
     int iter0;  // accepted iterations before this solve (a solve resumed from a saved state)
-    int pad_i;
+    int nan_eval;  // test hook: > 0, evaluations from this count on read D = NaN (0: off)
     long long evals;
     double tol, t, lo, Flo, dlo, hi, Fhi, dhi;
     double F, F0, dphi0, ginf, cG, budget_ns, ftol;

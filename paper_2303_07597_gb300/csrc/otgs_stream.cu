@@ -118,15 +118,15 @@ __device__ __forceinline__ unsigned long long gtime()
     return t;
 }
 
-// Wait for the phase with the given parity to complete; false after WAIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity)
+// Wait for the phase with the given parity to complete; false after limit ns.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, unsigned long long limit)
 {
     if (mbar_try(b, parity)) return true;
     const unsigned long long t0 = gtime();
     for (;;) {
         for (int i = 0; i < 64; i++)
             if (mbar_try(b, parity)) return true;
-        if (gtime() - t0 > WAIT_NS) return false;
+        if (gtime() - t0 > limit) return false;
     }
 }
 
@@ -429,6 +429,7 @@ __device__ __forceinline__ void add_xentry(const EvalArgs& A, int gstart, int ge
     if (lane != 0) return;
     const bool tall = gend - gstart > XTALL_ROWS;
     const int e = atomicAdd(tall ? &A.ctl->nxtall : &A.ctl->nxent, 1);
+    if (A.fcount) atomicAdd(A.fcount, (unsigned long long)__popc(mask));
     if (e < (tall ? A.xtall_cap : A.xent_cap)) {
         XEntry& x = (tall ? A.xtall : A.xent)[e];
         x.gstart = gstart;
@@ -519,6 +520,8 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
     }
     __syncthreads();
 
+    const unsigned long long wlim = A.wait_ns ? A.wait_ns : WAIT_NS;  // limit of the ring's waits
+
     // ------------------------------------------------------------ producer
     if (warp == CONSUMERS) {
         const bool screened = A.unit_need != nullptr;
@@ -528,7 +531,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
         auto next_slot = [&](int& slot) -> bool {
             slot = (int)(issued % NSTAGES);
             const long long use = issued / NSTAGES;
-            return use == 0 || mbar_wait(&S.empty[slot], (uint32_t)((use - 1) & 1));
+            return use == 0 || mbar_wait(&S.empty[slot], (uint32_t)((use - 1) & 1), wlim);
         };
         // Items flow through a software pipeline so that no load is waited on
         // right after it is issued: at the start of item k the counter is bumped
@@ -707,9 +710,9 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
         if (lane == 0 && A.c_streamed) atomicAdd(A.c_streamed, cstreamed);
         if (!ok) {
             if (lane == 0) atomicOr(A.err, 1);
-            // wait (bounded) for the copies already issued into the ring
+            // wait (bounded, at the default limit) for the copies already issued into the ring
             for (long long k = (issued > NSTAGES ? issued - NSTAGES : 0); k < issued; k++)
-                mbar_wait(&S.full[k % NSTAGES], (uint32_t)((k / NSTAGES) & 1));
+                mbar_wait(&S.full[k % NSTAGES], (uint32_t)((k / NSTAGES) & 1), WAIT_NS);
         }
         return;
     }
@@ -726,7 +729,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
     open_block(blk, make_int4(0, 0, 0, 0), false, x);
     for (;;) {
         const int slot = (int)(consumed % NSTAGES);
-        if (!mbar_wait(&S.full[slot], (uint32_t)((consumed / NSTAGES) & 1))) {
+        if (!mbar_wait(&S.full[slot], (uint32_t)((consumed / NSTAGES) & 1), wlim)) {
             if (lane == 0) atomicOr(A.err, 2);
             return;
         }
@@ -798,7 +801,7 @@ __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_co
             }
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(&S.empty[slot]);
+        if (lane == 0 && !A.stall) mbar_arrive(&S.empty[slot]);
         consumed++;
     }
 }
