@@ -241,11 +241,16 @@ OTGS_API int ot_gs_reset_stats(ot_gs *h);
  *     failing evaluation): the line search finds no acceptable step and the
  *     solve returns OTGS_ELINESEARCH (value 1, the start point: ENONFINITE).
  *     value <= 0: off.
+ *   OTGS_DEBUG_SCREEN_ROUTE: the route of screened evaluations: 0 (the
+ *     default) lets each evaluation choose, 1 always runs the bound pass over
+ *     the needed tiles, 2 always reads the blocks the screen left from the
+ *     transposed copy.  Both routes give the same bits.
  * Host only, no synchronisation.  Errors: OTGS_EINVAL (unknown switch, a
  * limit above 10 s).
  */
 #define OTGS_DEBUG_STALL 2
 #define OTGS_DEBUG_NAN_EVAL 3
+#define OTGS_DEBUG_SCREEN_ROUTE 4
 OTGS_API int ot_gs_debug(ot_gs *h, int what, int64_t value);
 
 /*

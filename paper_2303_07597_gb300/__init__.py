@@ -304,6 +304,7 @@ def ot_gs_reset_stats(h):
 
 OTGS_DEBUG_STALL = 2
 OTGS_DEBUG_NAN_EVAL = 3
+OTGS_DEBUG_SCREEN_ROUTE = 4
 
 
 def ot_gs_debug(h, what: int, value: int):

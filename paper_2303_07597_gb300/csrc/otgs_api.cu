@@ -211,6 +211,22 @@ bool Handle::init(int32_t np, const float* const* C_, const int64_t* ldc_, const
             }
         }
     }
+    {
+        // the transposed copy: each block (l, j) is one contiguous run of rows
+        size_t ct_floats = 0;
+        for (int32_t k = 0; k < np; k++) ct_floats += (size_t)n_[k] * (size_t)((m_[k] + 3) / 4 * 4);
+        float* CT = (float*)dalloc(sizeof(float) * std::max<size_t>(ct_floats, 1), "transposed C");
+        if (!CT) return false;
+        size_t at = 0;
+        for (int32_t k = 0; k < np; k++) {
+            ProbDesc& pd = probs_h[k];
+            pd.ldct = (m_[k] + 3) / 4 * 4;
+            pd.CT = CT + at;
+            launch_transpose(pd.C, pd.ldc, pd.m, pd.n, CT + at, pd.ldct, st);
+            at += (size_t)n_[k] * (size_t)pd.ldct;
+        }
+        if (!ck(cudaGetLastError(), "transpose")) return false;
+    }
     probs = upload(this, probs_h, "problem table");
     if (!probs) return false;
     {
@@ -342,14 +358,21 @@ bool Handle::setup_plan(const PlanParams& pp)
         (float*)plan_alloc(sizeof(float) * SPLIT_VALS * ITEM_COLS * (size_t)hp.nsplit_slots, "split partial sums");
     if (!split_part) return false;
     {
-        int64_t ce = 0, ct = 0;
-        exact_caps(hp, ce, ct);
-        if (ce > INT32_MAX || ct > INT32_MAX) return fail(OTGS_EINVAL, "too many blocks");
+        int64_t ce = 0, ct = 0, cu = 0, cc = 0;
+        exact_caps(hp, ce, ct, cu, cc);
+        if (ce > INT32_MAX || ct > INT32_MAX || cu > INT32_MAX || cc > INT32_MAX)
+            return fail(OTGS_EINVAL, "too many blocks");
         xent_cap = (int32_t)ce;
         xtall_cap = (int32_t)ct;
+        xunit_cap = (int32_t)cu;
+        xtcol_cap = (int32_t)cc;
         xent = (XEntry*)plan_alloc(sizeof(XEntry) * (size_t)ce, "flagged block sets");
         xtall = (XEntry*)plan_alloc(sizeof(XEntry) * (size_t)ct, "flagged block sets of tall classes");
-        if (!xent || !xtall) return false;
+        xpart = (float4*)plan_alloc(sizeof(float4) * (size_t)std::max<int64_t>(cu, 1), "slice sums");
+        xwmap = (uint32_t*)plan_alloc(sizeof(uint32_t) * (size_t)std::max<int64_t>(cu, 1), "slice sets");
+        xtcnt = (int*)plan_alloc(sizeof(int) * (size_t)std::max<int64_t>(cc, 1), "column slices done");
+        xtsv = (float*)plan_alloc(sizeof(float) * (size_t)std::max<int64_t>(cc, 1), "column shrink");
+        if (!xent || !xtall || !xpart || !xwmap || !xtcnt || !xtsv) return false;
     }
     if (screen_alloc) {
         item_active = (uint8_t*)plan_alloc((size_t)hp.nitems(), "item_active");
@@ -390,7 +413,10 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.psix = ctl_psi(ctl);
     e.xent = xent; e.xent_cap = xent_cap;
     e.xtall = xtall; e.xtall_cap = xtall_cap;
+    e.xpart = xpart; e.xwmap = xwmap; e.xtcnt = xtcnt; e.xtsv = xtsv;
+    e.xunit_cap = xunit_cap; e.xtcol_cap = xtcol_cap;
     e.fcount = fcount;
+    e.use_ct = 1;
     e.wait_ns = (unsigned long long)std::max<int64_t>(dbg_stall_ns, 0);
     e.stall = dbg_stall_ns > 0;
     e.split_part = split_part;
@@ -467,7 +493,7 @@ int Handle::eval_launch(const EvalArgs& e, int n_ctas)
     }
     launch_split_finish(e, st);
     launch_exact(e, n_sm, st);
-    return 3 + (e.nsets > 0);  // stream, exact (2), split finish
+    return 4 + (e.nsets > 0);  // stream, exact (2), split finish
 }
 
 // Dense evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.
@@ -640,6 +666,14 @@ int ot_gs_debug(ot_gs* hh, int what, int64_t value)
             return OTGS_EINVAL;
         }
         h->dbg_stall_ns = value > 0 ? value : 0;
+        return OTGS_OK;
+    }
+    if (what == OTGS_DEBUG_SCREEN_ROUTE) {
+        if (value < 0 || value > 2) {
+            h->fail(OTGS_EINVAL, "screen route is 0, 1 or 2");
+            return OTGS_EINVAL;
+        }
+        h->dbg_route = value;
         return OTGS_OK;
     }
     if (what == OTGS_DEBUG_NAN_EVAL) {

@@ -175,6 +175,34 @@ void launch_gather_rows(const float* C, int64_t ldc, const int32_t* perm, int32_
     }
 }
 
+// CT[j * ldct + i] = C[i * ldc + j], i < m, j < n: 32 x 32 tiles through shared
+// memory (reads along C's rows, writes along CT's rows, both coalesced).
+__global__ void __launch_bounds__(256) k_transpose(const float* __restrict__ C, int64_t ldc, int32_t m, int32_t n,
+                                                   float* __restrict__ CT, int64_t ldct)
+{
+    __shared__ float t[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, j = j0 + tx;
+        t[r][tx] = (i < m && j < n) ? C[(int64_t)i * ldc + j] : 0.f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = j0 + r, i = i0 + tx;
+        if (j < n && i < m) CT[(int64_t)j * ldct + i] = t[tx][r];
+    }
+}
+
+void launch_transpose(const float* C, int64_t ldc, int32_t m, int32_t n, float* CT, int64_t ldct, cudaStream_t st)
+{
+    for (int32_t i0 = 0; i0 < m; i0 += 32 * 65535) {
+        const int32_t rows = m - i0 < 32 * 65535 ? m - i0 : 32 * 65535;
+        dim3 grid((unsigned)((n + 31) / 32), (unsigned)((rows + 31) / 32));
+        k_transpose<<<grid, 256, 0, st>>>(C + (int64_t)i0 * ldc, ldc, rows, n, CT + i0, ldct);
+    }
+}
+
 __global__ void k_permute(const double* __restrict__ src, const int32_t* __restrict__ perm, int32_t m,
                           double* dst, int to_sorted)
 {

@@ -59,9 +59,15 @@ struct Handle {
     XEntry* xent = nullptr;         // flagged block sets for the exact-sum kernel (sized by the plan):
     XEntry* xtall = nullptr;        // classes of at most XTALL_ROWS rows, taller classes
     int32_t xent_cap = 0, xtall_cap = 0;
+    float4* xpart = nullptr;        // transposed route of the taller classes: slice sums,
+    uint32_t* xwmap = nullptr;      //   unit -> set,
+    int* xtcnt = nullptr;           //   slices done per column,
+    float* xtsv = nullptr;          //   s per column
+    int32_t xunit_cap = 0, xtcol_cap = 0;
     unsigned long long* fcount = nullptr;  // flagged blocks (statistics)
     int64_t dbg_stall_ns = 0;       // test hooks (ot_gs_debug): a stalled ring with this wait limit,
-    int64_t dbg_nan_eval = 0;       //   a solve's objective NaN from this evaluation on
+    int64_t dbg_nan_eval = 0;       //   a solve's objective NaN from this evaluation on,
+    int64_t dbg_route = 0;          //   a screened evaluation's route (0: chosen, 1: bound pass, 2: block sets)
     float* split_part = nullptr;    // partial block sums of the pieces of split groups
     int nred = 0;
     double* block_part = nullptr;

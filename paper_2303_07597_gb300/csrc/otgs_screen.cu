@@ -54,9 +54,12 @@ struct ScreenArgs {
     const int32_t* pitem;
     const int32_t* pW;
     const int32_t* psplit;      // pieces of a panel's group (1: not split)
-    unsigned long long* count;  // [0] in N, [1] checked, [2] skipped, [3] units needed
+    unsigned long long* count;  // [0] in N, [1] checked, [2] skipped, [3] units needed, [4] C bytes read
     int32_t nitems;
     const int* gate;            // NULL, or a device flag: 0 = skip (batched solver trials)
+    int32_t wl_build;           // 1: record each needed unit as a block set for the exact-sum kernels
+    int32_t route;              // 0: k_route decides, 1: the bound pass, 2: the screen's block sets
+    double wl_max;              // k_route takes the screen's sets when their rows x columns are at most this
 };
 
 __device__ __forceinline__ void atomic_max_pos(unsigned* addr, float v)
@@ -187,13 +190,13 @@ __global__ void k_theta(const ScreenArgs S)
 constexpr int SCREEN_WARPS = 8;
 constexpr int SCREEN_TB = 8;  // tiles whose loads a warp issues together
 
-__global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S)
+__global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S, const EvalArgs E)
 {
     if (S.gate && !*S.gate) return;
     __shared__ unsigned long long csum[SCREEN_WARPS][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t ntask = (int64_t)S.L * S.unit_words;
-    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
+    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, wk = 0;
     for (int64_t task = (int64_t)blockIdx.x * SCREEN_WARPS + warp; task < ntask;
          task += (int64_t)gridDim.x * SCREEN_WARPS) {
         const int l = (int)(task / S.unit_words), w = (int)(task % S.unit_words);
@@ -232,6 +235,10 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
                 const uint32_t skipw = __ballot_sync(FULLMASK, skip);
                 const uint32_t needw = __ballot_sync(FULLMASK, valid && !skip);
                 const uint32_t validw = __ballot_sync(FULLMASK, valid);
+                if (needw && S.wl_build) {  // (uniform) the unit as a block set: its group's rows x needed columns
+                    add_xentry(E, S.goff[l], S.goff[l + 1], jt * TW, 0, l, needw, lane);
+                    wk += (unsigned long long)g * (unsigned long long)__popc(needw);
+                }
                 if (lane == 0) {
                     S.skipmask[u] = skipw;
                     if (needw) {
@@ -253,12 +260,37 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
         csum[warp][1] = c1;
         csum[warp][2] = c2;
         csum[warp][3] = c3;
+        if (wk) atomicAdd(&E.ctl->wl_work, wk);
     }
     __syncthreads();
     if (threadIdx.x < 4) {
         unsigned long long v = 0;
         for (int q = 0; q < SCREEN_WARPS; q++) v += csum[q][threadIdx.x];
         if (v) atomicAdd(S.count + threadIdx.x, v);
+    }
+}
+
+// The route of a screened evaluation.  The screen recorded every needed unit
+// as a block set for the exact-sum kernels; when their rows x columns are few
+// (at most wl_max: then reading just those blocks from the transposed copy
+// costs less than a bound pass over every needed tile) the evaluation takes
+// them as they are and the bound pass and its kernels stand down (ctl->wl).
+// Otherwise the sets are dropped and the bound pass flags its own.  Either
+// way every block with s > 0 is formed by the same exact-sum kernels, so the
+// route changes no result.
+__global__ void k_route(const ScreenArgs S, EvalCtl* ctl)
+{
+    if (S.gate && !*S.gate) return;
+    const double w = (double)ctl->wl_work;
+    const bool wl = S.wl_build && (S.route == 2 || (S.route == 0 && w <= S.wl_max));
+    ctl->wl = wl ? 1 : 0;
+    if (wl) {
+        S.count[4] += (unsigned long long)(4.0 * w);  // the blocks' bytes of C
+    } else {
+        ctl->nxent = 0;
+        ctl->nxtall = 0;
+        ctl->nunit = 0;
+        ctl->ntcol = 0;
     }
 }
 
@@ -421,21 +453,25 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     launch_delta(this, beta);
     ScreenArgs s = make_screen_args(this);
     s.beta = beta;
-    k_theta<<<(std::max<int>(L, hp.nitems()) + 255) / 256, 256, 0, st>>>(s);
-    const int64_t tasks = (int64_t)L * unit_words;
-    const int sblocks = (int)std::min<int64_t>((tasks + SCREEN_WARPS - 1) / SCREEN_WARPS, 16LL * n_sm);
-    k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s);
     EvalArgs e = eval_args(item_active, unit_need, false);
     e.stage_m8 = stage_m8;
     e.stage_need = stage_need;
     e.c_streamed = dcount + 4;
+    s.wl_build = e.use_ct && dbg_route != 1;
+    s.route = (int32_t)dbg_route;
+    s.wl_max = WL_FRACTION * (double)m * (double)n;
+    k_theta<<<(std::max<int>(L, hp.nitems()) + 255) / 256, 256, 0, st>>>(s);
+    const int64_t tasks = (int64_t)L * unit_words;
+    const int sblocks = (int)std::min<int64_t>((tasks + SCREEN_WARPS - 1) / SCREEN_WARPS, 16LL * n_sm);
+    k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s, e);
+    k_route<<<1, 1, 0, st>>>(s, ctl);
     launch_stage_masks(e, st);
     const int nk = eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     if (!eval_gate) {
         count_screened_evals(1);
-        stats_host.kernels += nk + 6;  // and deltas (2), theta, screen, stage masks, reduction
+        stats_host.kernels += nk + 7;  // and deltas (2), theta, screen, route, stage masks, reduction
     }
     return ck(cudaGetLastError(), "screened eval launch");
 }

@@ -337,15 +337,6 @@ __device__ __forceinline__ uint32_t chunks_of_rows(uint32_t rows)
     return c;
 }
 
-// The fixed-point scale of a problem's sums: from its own maxima in a batch
-// (so that one problem's large trial point costs the others no precision),
-// else from the evaluation's.
-__device__ __forceinline__ FxScale prob_fx(const EvalArgs& A, int prob)
-{
-    if (A.pfx) return A.pfx[prob];
-    return fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
-}
-
 // t_ij = s f_ij (FP32) on the fixed-point grid: t * 2^k is exact in FP32
 // (below 2^61 by the choice of k), so this is the integer nearest to t 2^k.
 // The integer nearest to x (ties to even) for |x| < 2^63, with 32-bit
@@ -421,28 +412,6 @@ __device__ __forceinline__ void open_block(Block& b, const int4& g, bool need, c
     b.O = 0.f;
 }
 
-// A block set for the exact-sum kernel (lane 0 of the calling warp records
-// it): rows [gstart, gend) of group l x the columns colg0 + k, k in mask.
-__device__ __forceinline__ void add_xentry(const EvalArgs& A, int gstart, int gend, int colg0, int prob, int l,
-                                           uint32_t mask, int lane)
-{
-    if (lane != 0) return;
-    const bool tall = gend - gstart > XTALL_ROWS;
-    const int e = atomicAdd(tall ? &A.ctl->nxtall : &A.ctl->nxent, 1);
-    if (A.fcount) atomicAdd(A.fcount, (unsigned long long)__popc(mask));
-    if (e < (tall ? A.xtall_cap : A.xent_cap)) {
-        XEntry& x = (tall ? A.xtall : A.xent)[e];
-        x.gstart = gstart;
-        x.gend = gend;
-        x.colg0 = colg0;
-        x.prob = prob;
-        x.l = l;
-        x.mask = mask;
-    } else {
-        atomicOr(A.err, 4);  // the capacity holds every (group, tile) once: not reached
-    }
-}
-
 // The block is complete: flagged (its FP32 bound does not rule out z > theta)
 // it goes to the exact-sum kernel, which finishes it; otherwise its s is 0
 // and it adds nothing.  A snapshot stores the bound as z~ (the exact-sum
@@ -507,6 +476,7 @@ template <bool SNAP>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_constant__ EvalArgs A)
 {
     if (A.gate && !*A.gate) return;  // a skipped solver trial
+    if (A.ctl->wl) return;           // screened, and the screen's block sets are the work (k_route)
     extern __shared__ unsigned char smem_raw[];
     // TMA destinations must be 128-byte aligned: align the layout to 1 KB
     Smem& S = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -815,6 +785,7 @@ static_assert(SR == 32, "k_stage_masks: a warp covers one stage");
 __global__ void __launch_bounds__(256) k_stage_masks(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
+    if (A.ctl->wl) return;
     const ItemDesc d = A.desc[blockIdx.x];
     if (A.item_active && !A.item_active[d.item]) return;
     const int tile0 = d.col0 / TW;  // a multiple of NWARPS: the item's tiles share one mask word
@@ -853,6 +824,7 @@ void launch_stage_masks(const EvalArgs& a, cudaStream_t st)
 __global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
+    if (A.ctl->wl) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int si = blockIdx.x; si < A.nsets; si += gridDim.x) {
         const SplitSet st = A.sets[si];
@@ -1205,19 +1177,253 @@ __global__ void __launch_bounds__(TALL_THREADS, 2) k_exact_tall(const EvalArgs A
     }
 }
 
+// The flagged block sets read from the transposed copy of C, where block
+// (l, j) is the contiguous run CT[j][gstart, gend) of its problem: warps read
+// it with coalesced loads, one row per lane, and only the flagged columns'
+// bytes are read.
+//  * A shorter class's set (at most XTALL_ROWS rows): one warp, taken from a
+//    counter.  Per column: S = sum [f]_+^2 and P = sum [f]_+ in double-float
+//    per lane (rows gstart + lane + 32 u in order), the fixed xor tree, Eq. 5
+//    (psi in fixed point, the column sum s P, a snapshot's z~).  Then its rows
+//    once more, every column with s > 0 per row: t_ij = s [f_ij]_+ into the
+//    row's fixed-point sum.
+//  * A taller class's column: one warp per slice of XSLICE rows (a unit),
+//    units of every such column taken from a counter first.  Each slice's
+//    sums (the same per-lane order and tree) go to its unit's partial; the
+//    warp that completes a column adds the partials in slice order and
+//    finishes it (Eq. 5).  k_exact_t_rows then adds each slice's t_ij.
+// Every floating-point sum has a fixed order, so a block's results do not
+// depend on its set, on scheduling or on the evaluation being screened.
+constexpr int XTC_THREADS = 256;
+constexpr int XTC_UNROLL = 8;
+static_assert(XSLICE == 32 * XTC_UNROLL, "a slice is one load round of a warp");
+
+// The sums over rows [r0, r1) (r1 - r0 <= 32 XTC_UNROLL) of one column; every
+// lane gets them.
+__device__ __forceinline__ Acc slice_sums(const EvalArgs& A, const float* col, int r0, int r1, float bp, float bh,
+                                          float bl, int lane)
+{
+    float c[XTC_UNROLL];
+    float4 a[XTC_UNROLL];
+#pragma unroll
+    for (int u = 0; u < XTC_UNROLL; u++) {
+        const int R = r0 + 32 * u + lane;
+        const bool in = R < r1;
+        a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+        c[u] = in ? __ldg(col + R) : 0.f;
+    }
+    Acc acc = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < XTC_UNROLL; u++)
+        if (maybe_pos(a[u].z, c[u], bp)) {
+            float fh, fl;
+            f_exact(a[u].x, a[u].y, bh, bl, c[u], fh, fl);
+            if (fh > 0.f) acc_p(fh, fl, acc);
+        }
+    warp_df_sum(acc.Sh, acc.Sl);
+    warp_df_sum(acc.Ph, acc.Pl);
+    return acc;
+}
+
+// Eq. 5 for one block from its sums (lane 0's work): psi into (ph, pl), s P
+// into the column sum, a snapshot's z~.  Returns s.
+__device__ __forceinline__ float finish_block_exact(const EvalArgs& A, const FxScale& fx, const Acc& T, int l,
+                                                    int colg, long long& ph, long long& pl)
+{
+    float psh, psl;
+    const float s = block_scale(T.Sh, T.Sl, A, psh, psl);
+    if (s > 0.f) {
+        psi_to_fx(psh, psl, fx.to_p, ph, pl);
+        atomicAdd(A.colfx + colg, (unsigned long long)col_q(s, T.Ph, T.Pl, fx.to_cf));
+    }
+    if (A.zt) A.zt[(int64_t)l * A.ntiles * TW + colg] = z_up(T.Sh, T.Sl);
+    return s;
+}
+
+__device__ __forceinline__ void hold_psi(const EvalArgs& A, int prob, int& pprob, long long& ph, long long& pl)
+{
+    if (prob != pprob) {
+        if (pprob >= 0 && (ph | pl) != 0) {
+            atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
+            atomicAdd(A.psix + 2 * pprob + 1, (unsigned long long)pl);
+        }
+        ph = pl = 0;
+        pprob = prob;
+    }
+}
+
+__global__ void __launch_bounds__(XTC_THREADS, 2) k_exact_t(const EvalArgs A)
+{
+    if (A.gate && !*A.gate) return;
+    const int nx = min(A.ctl->nxent, A.xent_cap);
+    const int nu = min(A.ctl->nunit, A.xunit_cap);
+    const int lane = threadIdx.x & 31;
+    __shared__ FxScale fx1;  // one problem: the evaluation's scale
+    if (threadIdx.x == 0 && !A.pfx && nx + nu > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
+    __syncthreads();
+    int pprob = -1;  // lane 0: the problem of the psi sums it holds
+    long long ph = 0, pl = 0;
+    // the taller classes' units
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(&A.ctl->unext, 1);
+        u = __shfl_sync(FULLMASK, u, 0);
+        if (u >= nu) break;
+        const XEntry E = A.xtall[A.xwmap[u]];
+        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
+        const int ns = (E.gend - E.gstart + XSLICE - 1) / XSLICE;
+        const int q = (u - E.ubase) / ns, sl = (u - E.ubase) % ns;
+        const int k = __fns(E.mask, 0, q + 1);  // the set's q-th column
+        const int lcol = E.colg0 + k - pd.coff;
+        const float2 b2 = __ldg(A.B2 + pd.bcoff + lcol);
+        const float* col = pd.CT + (int64_t)lcol * pd.ldct - pd.roff;
+        const int r0 = E.gstart + sl * XSLICE;
+        const Acc p = slice_sums(A, col, r0, min(E.gend, r0 + XSLICE), bound_up(b2.x), b2.x, b2.y, lane);
+        int done = 0;
+        if (lane == 0) {
+            A.xpart[u] = make_float4(p.Sh, p.Sl, p.Ph, p.Pl);
+            __threadfence();
+            done = atomicAdd(A.xtcnt + E.tbase + q, 1) == ns - 1;
+        }
+        done = __shfl_sync(FULLMASK, done, 0);
+        if (!done) continue;  // (uniform)
+        if (lane == 0) {  // the column's last slice: add the slices in order and finish it
+            __threadfence();
+            Acc T = {0.f, 0.f, 0.f, 0.f};
+            const int u0 = E.ubase + q * ns;
+            for (int i = 0; i < ns; i++) {
+                const float4 v = __ldcg(A.xpart + u0 + i);
+                df_add(T.Sh, T.Sl, v.x, v.y);
+                df_add(T.Ph, T.Pl, v.z, v.w);
+            }
+            const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
+            hold_psi(A, E.prob, pprob, ph, pl);
+            A.xtsv[E.tbase + q] = finish_block_exact(A, fx, T, E.l, E.colg0 + k, ph, pl);
+        }
+    }
+    // the shorter classes' sets
+    for (;;) {
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&A.ctl->xnext, 1);
+        t = __shfl_sync(FULLMASK, t, 0);
+        if (t >= nx) break;
+        const XEntry E = A.xent[t];
+        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
+        const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
+        if (lane == 0) hold_psi(A, E.prob, pprob, ph, pl);
+        const float* ct0 = pd.CT + (int64_t)(E.colg0 - pd.coff) * pd.ldct - pd.roff;  // + k ldct + R
+        float sk = 0.f;  // lane k: s of column k
+        uint32_t rem = E.mask;
+        while (rem) {
+            const int k = __ffs(rem) - 1;
+            rem &= rem - 1u;
+            const float2 b2 = __ldg(A.B2 + pd.bcoff + E.colg0 + k - pd.coff);
+            const Acc T = slice_sums(A, ct0 + (int64_t)k * pd.ldct, E.gstart, E.gend, bound_up(b2.x), b2.x, b2.y, lane);
+            float s = 0.f;
+            if (lane == 0) s = finish_block_exact(A, fx, T, E.l, E.colg0 + k, ph, pl);
+            s = __shfl_sync(FULLMASK, s, 0);
+            if (lane == k) sk = s;
+        }
+        uint32_t srem = __ballot_sync(FULLMASK, sk > 0.f);
+        if (!srem) continue;  // (uniform)
+        unsigned long long tq[XTC_UNROLL];
+#pragma unroll
+        for (int u = 0; u < XTC_UNROLL; u++) tq[u] = 0ull;
+        while (srem) {
+            const int k = __ffs(srem) - 1;
+            srem &= srem - 1u;
+            const float s = __shfl_sync(FULLMASK, sk, k);
+            const float2 b2 = __ldg(A.B2 + pd.bcoff + E.colg0 + k - pd.coff);
+            const float bp = bound_up(b2.x);
+            const float* col = ct0 + (int64_t)k * pd.ldct;
+            float c[XTC_UNROLL];
+            float4 a[XTC_UNROLL];  // (the rows' records again: in L1)
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++) {
+                const int R = E.gstart + 32 * u + lane;
+                const bool in = R < E.gend;
+                a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+                c[u] = in ? __ldg(col + R) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++)
+                if (maybe_pos(a[u].z, c[u], bp)) {
+                    float fh, fl;
+                    f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
+                    if (fh > 0.f) tq[u] += t_q(__fmul_rn(s, fh), fx.to_rf);
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < XTC_UNROLL; u++)
+            if (tq[u]) atomicAdd(A.rowfx + E.gstart + 32 * u + lane, tq[u]);
+    }
+    if (lane == 0 && pprob >= 0 && (ph | pl) != 0) {
+        atomicAdd(A.psix + 2 * pprob, (unsigned long long)ph);
+        atomicAdd(A.psix + 2 * pprob + 1, (unsigned long long)pl);
+    }
+}
+
+// Row sums of the taller classes' columns with s > 0: one warp per unit.
+__global__ void __launch_bounds__(XTC_THREADS) k_exact_t_rows(const EvalArgs A)
+{
+    if (A.gate && !*A.gate) return;
+    const int nu = min(A.ctl->nunit, A.xunit_cap);
+    const int lane = threadIdx.x & 31, nw = XTC_THREADS / 32;
+    __shared__ FxScale fx1;
+    if (threadIdx.x == 0 && !A.pfx && nu > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
+    __syncthreads();
+    for (int u = blockIdx.x * nw + (threadIdx.x >> 5); u < nu; u += gridDim.x * nw) {
+        const XEntry& E = A.xtall[A.xwmap[u]];
+        const int ns = (E.gend - E.gstart + XSLICE - 1) / XSLICE;
+        const int q = (u - E.ubase) / ns, sl = (u - E.ubase) % ns;
+        const float s = A.xtsv[E.tbase + q];
+        if (!(s > 0.f)) continue;  // (uniform)
+        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
+        const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
+        const int k = __fns(E.mask, 0, q + 1);
+        const int lcol = E.colg0 + k - pd.coff;
+        const float2 b2 = __ldg(A.B2 + pd.bcoff + lcol);
+        const float bp = bound_up(b2.x);
+        const float* col = pd.CT + (int64_t)lcol * pd.ldct - pd.roff;
+        const int r0 = E.gstart + sl * XSLICE, r1 = min(E.gend, r0 + XSLICE);
+#pragma unroll
+        for (int uu = 0; uu < XTC_UNROLL; uu++) {
+            const int R = r0 + 32 * uu + lane;
+            if (R >= r1) break;
+            const float4 a = __ldg(A.rowA + R);
+            const float c = __ldg(col + R);
+            if (maybe_pos(a.z, c, bp)) {
+                float fh, fl;
+                f_exact(a.x, a.y, b2.x, b2.y, c, fh, fl);
+                if (fh > 0.f) atomicAdd(A.rowfx + R, t_q(__fmul_rn(s, fh), fx.to_rf));
+            }
+        }
+    }
+}
+
 void launch_exact(const EvalArgs& a, int n_sm, cudaStream_t st)
 {
+    if (a.use_ct) {
+        k_exact_t<<<2 * n_sm, XTC_THREADS, 0, st>>>(a);
+        k_exact_t_rows<<<4 * n_sm, XTC_THREADS, 0, st>>>(a);
+        return;
+    }
     k_exact<<<4 * n_sm, EXACT_THREADS, 0, st>>>(a);
     k_exact_tall<<<2 * n_sm, TALL_THREADS, 0, st>>>(a);
 }
 
-void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall)
+void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall, int64_t& units, int64_t& tcols)
 {
-    xent = xtall = 0;
+    xent = xtall = units = tcols = 0;
     for (int64_t l = 0; l < hp.L; l++) {
         const int64_t g = hp.goff[l + 1] - hp.goff[l];
         if (g == 0) continue;
-        (g > XTALL_ROWS ? xtall : xent) += (hp.pn[hp.gprob[l]] + TW - 1) / TW;
+        const int64_t n = hp.pn[hp.gprob[l]];
+        (g > XTALL_ROWS ? xtall : xent) += (n + TW - 1) / TW;
+        if (g > XTALL_ROWS) {
+            tcols += n;
+            units += n * ((g + XSLICE - 1) / XSLICE);
+        }
     }
 }
 
