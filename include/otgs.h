@@ -85,7 +85,9 @@ typedef struct {
     int64_t snapshots;        /* snapshot refreshes (dense passes) */
     double  c_bytes;          /* bytes of C streamed by evaluation kernels */
     int64_t kernels;          /* kernels launched by ot_gs_grad / ot_gs_grad_screened calls */
-    int64_t blocks_flagged;   /* blocks whose FP32 bound left s > 0 possible (Eq. 5 formed exactly) */
+    int64_t blocks_flagged;   /* blocks formed exactly (Eq. 5): those whose FP32 bound left s > 0
+                                 possible, or, on a screened evaluation's block-set route, those the
+                                 screen left */
 } ot_gs_stats;
 
 /*

@@ -371,8 +371,7 @@ bool Handle::setup_plan(const PlanParams& pp)
         xpart = (float4*)plan_alloc(sizeof(float4) * (size_t)std::max<int64_t>(cu, 1), "slice sums");
         xwmap = (uint32_t*)plan_alloc(sizeof(uint32_t) * (size_t)std::max<int64_t>(cu, 1), "slice sets");
         xtcnt = (int*)plan_alloc(sizeof(int) * (size_t)std::max<int64_t>(cc, 1), "column slices done");
-        xtsv = (float*)plan_alloc(sizeof(float) * (size_t)std::max<int64_t>(cc, 1), "column shrink");
-        if (!xent || !xtall || !xpart || !xwmap || !xtcnt || !xtsv) return false;
+        if (!xent || !xtall || !xpart || !xwmap || !xtcnt) return false;
     }
     if (screen_alloc) {
         item_active = (uint8_t*)plan_alloc((size_t)hp.nitems(), "item_active");
@@ -413,7 +412,8 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.psix = ctl_psi(ctl);
     e.xent = xent; e.xent_cap = xent_cap;
     e.xtall = xtall; e.xtall_cap = xtall_cap;
-    e.xpart = xpart; e.xwmap = xwmap; e.xtcnt = xtcnt; e.xtsv = xtsv;
+    e.xpart = xpart; e.xwmap = xwmap; e.xtcnt = xtcnt;
+    e.nprob = nprob;
     e.xunit_cap = xunit_cap; e.xtcol_cap = xtcol_cap;
     e.fcount = fcount;
     e.use_ct = 1;

@@ -61,8 +61,7 @@ struct Handle {
     int32_t xent_cap = 0, xtall_cap = 0;
     float4* xpart = nullptr;        // transposed route of the taller classes: slice sums,
     uint32_t* xwmap = nullptr;      //   unit -> set,
-    int* xtcnt = nullptr;           //   slices done per column,
-    float* xtsv = nullptr;          //   s per column
+    int* xtcnt = nullptr;           //   slices done per column
     int32_t xunit_cap = 0, xtcol_cap = 0;
     unsigned long long* fcount = nullptr;  // flagged blocks (statistics)
     int64_t dbg_stall_ns = 0;       // test hooks (ot_gs_debug): a stalled ring with this wait limit,

@@ -246,6 +246,7 @@ struct EvalCtl {
     int wl;             // screened: 1 = the screen built the sets itself (no bound pass; see k_route)
     unsigned long long psi[2];  // one problem: psi summed by the exact-sum kernel (fixed point, hi and lo)
     unsigned long long wl_work;  // screened: rows x columns of the blocks the screen left (see k_route)
+    unsigned long long wl_cols;  //   and their number
 };
 
 // Device address of the control word's psi accumulators (host side: plain
@@ -269,6 +270,7 @@ __device__ __forceinline__ void ctl_clear(EvalCtl* c)
     c->ntcol = 0;
     c->wl = 0;
     c->wl_work = 0ull;
+    c->wl_cols = 0ull;
     c->psi[0] = 0ull;
     c->psi[1] = 0ull;
 }
@@ -426,11 +428,11 @@ struct EvalArgs {
     float thr_flag;    // RD(theta^2 (1 - 2^-21)): a block whose FP32 bound stays at or below it has s = 0
     unsigned long long* fcount;  // NULL, or a counter of the flagged blocks (statistics)
     int32_t use_ct;    // 1: every problem has its transposed copy (ProbDesc::CT) for the exact sums
-    float4* xpart;     // transposed route: per unit, its slice's (S hi, S lo, P hi, P lo)
+    float4* xpart;     // transposed route: per unit, its slice's (S hi, S lo, P hi, P lo), then its row-sum record
     uint32_t* xwmap;   //   per unit, its set in the taller classes' list
     int* xtcnt;        //   per column task, slices done
-    float* xtsv;       //   per column task, s (Eq. 5) once finished
     int32_t xunit_cap, xtcol_cap;
+    int32_t nprob;     // problems
     unsigned long long wait_ns;  // 0: the default limit of the evaluation kernel's waits; else this one
     int32_t stall;     // test hook: the consumer warps do not release stages (the waits run out)
     float* split_part; // [slots][ITEM_COLS][SPLIT_VALS]: a piece's (S', O) per column

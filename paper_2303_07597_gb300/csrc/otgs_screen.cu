@@ -185,26 +185,27 @@ __global__ void k_theta(const ScreenArgs S)
 
 // Alg. 2's skip test (Eq. 6, Lemma 2) for every block outside N.  A warp
 // takes the 32 units (l, 32-column tile) of one unit_need word, lane = column
-// in the tile, so each need word is written whole; statistics are summed per
-// block before one atomic add each.
+// in the tile; lane t keeps tile t's ballots and, after the word, writes that
+// tile's skip word and marks its items, so no lane works through the tiles
+// alone.  Statistics are summed per block before one atomic add each.
 constexpr int SCREEN_WARPS = 8;
 constexpr int SCREEN_TB = 8;  // tiles whose loads a warp issues together
 
-__global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S, const EvalArgs E)
+__global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S)
 {
     if (S.gate && !*S.gate) return;
     __shared__ unsigned long long csum[SCREEN_WARPS][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t ntask = (int64_t)S.L * S.unit_words;
-    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, wk = 0;
+    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
     for (int64_t task = (int64_t)blockIdx.x * SCREEN_WARPS + warp; task < ntask;
          task += (int64_t)gridDim.x * SCREEN_WARPS) {
         const int l = (int)(task / S.unit_words), w = (int)(task % S.unit_words);
         const int g = S.goff[l + 1] - S.goff[l];
         const float th = S.gstat[4 * l + 3], npos = S.gstat[4 * l], sg = S.sg_ru[l];
-        const int p = g > 0 ? S.gpanel[l] : 0;
-        uint32_t needword = 0u;
         const int jt1 = min(32 * w + 32, S.ntiles);
+        // lane t keeps the ballots of tile 32 w + t
+        uint32_t my_skip = 0u, my_need = 0u, my_valid = 0u, my_N = 0u;
         // tiles in batches of SCREEN_TB, their loads issued together
         for (int jb = 32 * w; jb < jt1; jb += SCREEN_TB) {
             float zv[SCREEN_TB], dv[SCREEN_TB];
@@ -222,11 +223,9 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
             for (int q = 0; q < SCREEN_TB; q++) {
                 const int jt = jb + q;
                 if (jt >= jt1) break;  // (uniform)
-                const int64_t u = (int64_t)l * S.ntiles + jt;
                 const int j = jt * TW + lane;
                 const bool valid = j < S.n && g > 0;
-                const uint32_t Nw = Nv[q];
-                const bool inN = valid && ((Nw >> lane) & 1u);
+                const bool inN = valid && ((Nv[q] >> lane) & 1u);
                 bool skip = false;
                 if (valid && !inN) {
                     const float zbar = __fadd_ru(__fadd_ru(zv[q], npos), __fmul_ru(sg, dv[q]));
@@ -235,32 +234,43 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
                 const uint32_t skipw = __ballot_sync(FULLMASK, skip);
                 const uint32_t needw = __ballot_sync(FULLMASK, valid && !skip);
                 const uint32_t validw = __ballot_sync(FULLMASK, valid);
-                if (needw && S.wl_build) {  // (uniform) the unit as a block set: its group's rows x needed columns
-                    add_xentry(E, S.goff[l], S.goff[l + 1], jt * TW, 0, l, needw, lane);
-                    wk += (unsigned long long)g * (unsigned long long)__popc(needw);
-                }
-                if (lane == 0) {
-                    S.skipmask[u] = skipw;
-                    if (needw) {
-                        needword |= 1u << (jt & 31);
-                        // the item of (l, tile) in every piece of the group (same value from every writer)
-                        for (int k = 0; k < S.psplit[p]; k++) S.item_active[S.pitem[p + k] + (jt * TW) / S.pW[p]] = 1;
-                    }
-                    c0 += __popc(Nw & validw);
-                    c1 += __popc(~Nw & validw);
-                    c2 += __popc(skipw);
-                    c3 += needw ? 1ull : 0ull;
+                if (lane == (jt & 31)) {
+                    my_skip = skipw;
+                    my_need = needw;
+                    my_valid = validw;
+                    my_N = Nv[q];
                 }
             }
         }
+        // every lane its own tile: the skip word, the items that hold it, the statistics
+        const int jt = 32 * w + lane;
+        if (jt < jt1) {
+            S.skipmask[(int64_t)l * S.ntiles + jt] = my_skip;
+            if (my_need) {
+                // the item of (l, tile) in every piece of the group (same value from every writer)
+                const int p = S.gpanel[l];
+                for (int k = 0; k < S.psplit[p]; k++) S.item_active[S.pitem[p + k] + (jt * TW) / S.pW[p]] = 1;
+            }
+            c0 += __popc(my_N & my_valid);
+            c1 += __popc(~my_N & my_valid);
+            c2 += __popc(my_skip);
+            c3 += my_need ? 1ull : 0ull;
+        }
+        const uint32_t needword = __ballot_sync(FULLMASK, my_need != 0u);
         if (lane == 0) S.unit_need[(int64_t)l * S.unit_words + w] = needword;
+    }
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        c0 += __shfl_xor_sync(FULLMASK, c0, off);
+        c1 += __shfl_xor_sync(FULLMASK, c1, off);
+        c2 += __shfl_xor_sync(FULLMASK, c2, off);
+        c3 += __shfl_xor_sync(FULLMASK, c3, off);
     }
     if (lane == 0) {
         csum[warp][0] = c0;
         csum[warp][1] = c1;
         csum[warp][2] = c2;
         csum[warp][3] = c3;
-        if (wk) atomicAdd(&E.ctl->wl_work, wk);
     }
     __syncthreads();
     if (threadIdx.x < 4) {
@@ -270,7 +280,85 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
     }
 }
 
-// The route of a screened evaluation.  The screen recorded every needed unit
+// Every needed unit (l, tile) as a block set for the exact-sum kernels: its
+// group's rows x the tile's columns the screen did not skip.  A warp per mask
+// word of a group, lane t for tile 32 w + t: one atomic per counter and warp
+// (warp scans give each lane its place), then every lane writes its own set
+// (and a taller class's slice units and column tasks).  Also sums the sets'
+// rows x columns for k_route.
+__global__ void __launch_bounds__(256) k_wlist(const ScreenArgs S, const EvalArgs E)
+{
+    if (S.gate && !*S.gate) return;
+    if (!S.wl_build) return;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    const int64_t ntask = (int64_t)S.L * S.unit_words;
+    unsigned long long work = 0, flagged = 0;
+    for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; task < ntask;
+         task += (int64_t)gridDim.x * blockDim.x / 32) {
+        const int l = (int)(task / S.unit_words), w = (int)(task % S.unit_words);
+        const int gs = S.goff[l], ge = S.goff[l + 1], g = ge - gs;
+        if (g == 0) continue;  // (uniform)
+        const int jt = 32 * w + lane;
+        uint32_t need = 0u;
+        if (jt < S.ntiles) {
+            const int left = S.n - jt * TW;  // columns of the tile that exist
+            const uint32_t valid = left >= 32 ? FULLMASK : ((1u << left) - 1u);
+            need = valid & ~__ldg(S.skipmask + (int64_t)l * S.ntiles + jt);
+        }
+        const uint32_t hb = __ballot_sync(FULLMASK, need != 0u);
+        if (!hb) continue;  // (uniform)
+        const bool tall = g > XTALL_ROWS;
+        const int nc = __popc(need), ns = (g + XSLICE - 1) / XSLICE;
+        // inclusive scan of the columns over the lanes
+        int cs = nc;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULLMASK, cs, off);
+            if (lane >= off) cs += v;
+        }
+        const int ctot = __shfl_sync(FULLMASK, cs, 31);
+        int e0 = 0, ub = 0, tb = 0;
+        if (lane == 0) {
+            e0 = atomicAdd(tall ? &E.ctl->nxtall : &E.ctl->nxent, __popc(hb));
+            if (tall && E.use_ct) {
+                ub = atomicAdd(&E.ctl->nunit, ctot * ns);
+                tb = atomicAdd(&E.ctl->ntcol, ctot);
+            }
+        }
+        e0 = __shfl_sync(FULLMASK, e0, 0);
+        ub = __shfl_sync(FULLMASK, ub, 0) + (cs - nc) * ns;
+        tb = __shfl_sync(FULLMASK, tb, 0) + (cs - nc);
+        work += (unsigned long long)g * (unsigned long long)ctot;
+        flagged += (unsigned long long)ctot;
+        if (!need) continue;
+        const int e = e0 + __popc(hb & lt);
+        if (e >= (tall ? E.xtall_cap : E.xent_cap) ||
+            (tall && E.use_ct && (ub + nc * ns > E.xunit_cap || tb + nc > E.xtcol_cap))) {
+            atomicOr(E.err, 4);  // the capacities hold every (group, column) once: not reached
+            continue;
+        }
+        XEntry& x = (tall ? E.xtall : E.xent)[e];
+        x.gstart = gs;
+        x.gend = ge;
+        x.colg0 = jt * TW;
+        x.prob = 0;
+        x.l = l;
+        x.mask = need;
+        x.ubase = ub;
+        x.tbase = tb;
+        if (tall && E.use_ct) {
+            for (int i = 0; i < nc * ns; i++) E.xwmap[ub + i] = (uint32_t)e;
+            for (int i = 0; i < nc; i++) E.xtcnt[tb + i] = 0;
+        }
+    }
+    if (lane == 0 && work) {
+        atomicAdd(&E.ctl->wl_work, work);
+        atomicAdd(&E.ctl->wl_cols, flagged);
+    }
+}
+
+// The route of a screened evaluation.  k_wlist recorded every needed unit
 // as a block set for the exact-sum kernels; when their rows x columns are few
 // (at most wl_max: then reading just those blocks from the transposed copy
 // costs less than a bound pass over every needed tile) the evaluation takes
@@ -278,7 +366,7 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
 // Otherwise the sets are dropped and the bound pass flags its own.  Either
 // way every block with s > 0 is formed by the same exact-sum kernels, so the
 // route changes no result.
-__global__ void k_route(const ScreenArgs S, EvalCtl* ctl)
+__global__ void k_route(const ScreenArgs S, EvalCtl* ctl, unsigned long long* fcount)
 {
     if (S.gate && !*S.gate) return;
     const double w = (double)ctl->wl_work;
@@ -286,6 +374,7 @@ __global__ void k_route(const ScreenArgs S, EvalCtl* ctl)
     ctl->wl = wl ? 1 : 0;
     if (wl) {
         S.count[4] += (unsigned long long)(4.0 * w);  // the blocks' bytes of C
+        if (fcount) *fcount += ctl->wl_cols;
     } else {
         ctl->nxent = 0;
         ctl->nxtall = 0;
@@ -463,15 +552,18 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     k_theta<<<(std::max<int>(L, hp.nitems()) + 255) / 256, 256, 0, st>>>(s);
     const int64_t tasks = (int64_t)L * unit_words;
     const int sblocks = (int)std::min<int64_t>((tasks + SCREEN_WARPS - 1) / SCREEN_WARPS, 16LL * n_sm);
-    k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s, e);
-    k_route<<<1, 1, 0, st>>>(s, ctl);
+    k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s);
+    if (s.wl_build)
+        k_wlist<<<(unsigned)std::min<int64_t>((tasks * 32 + 255) / 256, 8LL * n_sm), 256, 0, st>>>(s, e);
+    k_route<<<1, 1, 0, st>>>(s, ctl, fcount);
     launch_stage_masks(e, st);
     const int nk = eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     if (!eval_gate) {
         count_screened_evals(1);
-        stats_host.kernels += nk + 7;  // and deltas (2), theta, screen, route, stage masks, reduction
+        // and deltas (2), theta, screen, block sets, route, stage masks, reduction
+        stats_host.kernels += nk + 7 + (s.wl_build ? 1 : 0);
     }
     return ck(cudaGetLastError(), "screened eval launch");
 }

@@ -1287,10 +1287,12 @@ __global__ void __launch_bounds__(XTC_THREADS, 2) k_exact_t(const EvalArgs A)
         }
         done = __shfl_sync(FULLMASK, done, 0);
         if (!done) continue;  // (uniform)
-        if (lane == 0) {  // the column's last slice: add the slices in order and finish it
+        // the column's last slice: add the slices in order and finish it
+        const int u0 = E.ubase + q * ns;
+        float sv = 0.f;
+        if (lane == 0) {
             __threadfence();
             Acc T = {0.f, 0.f, 0.f, 0.f};
-            const int u0 = E.ubase + q * ns;
             for (int i = 0; i < ns; i++) {
                 const float4 v = __ldcg(A.xpart + u0 + i);
                 df_add(T.Sh, T.Sl, v.x, v.y);
@@ -1298,7 +1300,15 @@ __global__ void __launch_bounds__(XTC_THREADS, 2) k_exact_t(const EvalArgs A)
             }
             const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
             hold_psi(A, E.prob, pprob, ph, pl);
-            A.xtsv[E.tbase + q] = finish_block_exact(A, fx, T, E.l, E.colg0 + k, ph, pl);
+            sv = finish_block_exact(A, fx, T, E.l, E.colg0 + k, ph, pl);
+        }
+        sv = __shfl_sync(FULLMASK, sv, 0);
+        // the slices' row-sum records over their partials (read above): first
+        // row, column, s, rows | problem << 9
+        for (int i = lane; i < ns; i += 32) {
+            const int ri = E.gstart + i * XSLICE;
+            reinterpret_cast<int4*>(A.xpart)[u0 + i] =
+                make_int4(ri, lcol, __float_as_int(sv), min(XSLICE, E.gend - ri) | (E.prob << 9));
         }
     }
     // the shorter classes' sets
@@ -1363,7 +1373,9 @@ __global__ void __launch_bounds__(XTC_THREADS, 2) k_exact_t(const EvalArgs A)
     }
 }
 
-// Row sums of the taller classes' columns with s > 0: one warp per unit.
+// Row sums of the taller classes' columns with s > 0: one warp per unit, from
+// the record k_exact_t left in the unit's slot (no other lookup before the
+// data loads).
 __global__ void __launch_bounds__(XTC_THREADS) k_exact_t_rows(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
@@ -1372,24 +1384,29 @@ __global__ void __launch_bounds__(XTC_THREADS) k_exact_t_rows(const EvalArgs A)
     __shared__ FxScale fx1;
     if (threadIdx.x == 0 && !A.pfx && nu > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
     __syncthreads();
-    for (int u = blockIdx.x * nw + (threadIdx.x >> 5); u < nu; u += gridDim.x * nw) {
-        const XEntry& E = A.xtall[A.xwmap[u]];
-        const int ns = (E.gend - E.gstart + XSLICE - 1) / XSLICE;
-        const int q = (u - E.ubase) / ns, sl = (u - E.ubase) % ns;
-        const float s = A.xtsv[E.tbase + q];
+    const int4* rec = reinterpret_cast<const int4*>(A.xpart);
+    const int step = gridDim.x * nw;
+    int u = blockIdx.x * nw + (threadIdx.x >> 5);
+    int4 rn = u < nu ? __ldcg(rec + u) : make_int4(0, 0, 0, 0);  // the next unit's record, loaded ahead
+    for (; u < nu; u += step) {
+        const int4 r = rn;
+        if (u + step < nu) rn = __ldcg(rec + u + step);
+        const float s = __int_as_float(r.z);
         if (!(s > 0.f)) continue;  // (uniform)
-        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
-        const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
-        const int k = __fns(E.mask, 0, q + 1);
-        const int lcol = E.colg0 + k - pd.coff;
-        const float2 b2 = __ldg(A.B2 + pd.bcoff + lcol);
+        const int prob = r.w >> 9, cnt = r.w & 511;
+        if (prob >= A.nprob || (A.inline_maps && prob != 0) || cnt > XSLICE || r.x < 0 || r.x + cnt > A.m)
+            continue;  // (not reached: every unit's column is finished before this kernel)
+        const ProbDesc& pd = A.inline_maps ? A.pd0 : A.probs[prob];
+        if (r.y < 0 || r.y >= pd.n) continue;
+        const FxScale& fx = A.pfx ? A.pfx[prob] : fx1;
+        const float2 b2 = __ldg(A.B2 + pd.bcoff + r.y);
         const float bp = bound_up(b2.x);
-        const float* col = pd.CT + (int64_t)lcol * pd.ldct - pd.roff;
-        const int r0 = E.gstart + sl * XSLICE, r1 = min(E.gend, r0 + XSLICE);
+        const float* col = pd.CT + (int64_t)r.y * pd.ldct - pd.roff;
 #pragma unroll
         for (int uu = 0; uu < XTC_UNROLL; uu++) {
-            const int R = r0 + 32 * uu + lane;
-            if (R >= r1) break;
+            const int i = 32 * uu + lane;
+            if (i >= cnt) break;
+            const int R = r.x + i;
             const float4 a = __ldg(A.rowA + R);
             const float c = __ldg(col + R);
             if (maybe_pos(a.z, c, bp)) {
@@ -1405,7 +1422,7 @@ void launch_exact(const EvalArgs& a, int n_sm, cudaStream_t st)
 {
     if (a.use_ct) {
         k_exact_t<<<2 * n_sm, XTC_THREADS, 0, st>>>(a);
-        k_exact_t_rows<<<4 * n_sm, XTC_THREADS, 0, st>>>(a);
+        k_exact_t_rows<<<8 * n_sm, XTC_THREADS, 0, st>>>(a);
         return;
     }
     k_exact<<<4 * n_sm, EXACT_THREADS, 0, st>>>(a);
