@@ -111,6 +111,22 @@ OTGS_API int ot_gs_create(ot_gs **h, const float *C, int64_t ldc, const double *
                  const int32_t *labels, int64_t m, int64_t n, int32_t L, double gamma,
                  double mu, void *stream);
 
+/*
+ * A column shard of a problem (the multi-GPU split of the dual over target
+ * columns, Eq. 4-5): C holds the columns J of the full cost matrix (m x |J|),
+ * b the marginal b_J of those columns, a the whole a; everything else as
+ * ot_gs_create, except that sum b_J need not equal sum a.  Its evaluations
+ * (ot_gs_grad, ot_gs_grad_screened) give D_J = alpha.a + beta_J.b_J - sum
+ * over j in J of psi, the alpha gradient a - sum_{j in J} t_.j and the beta_J
+ * gradient.  Over shards J_1..J_P of all columns: D = sum_p D_Jp - (P - 1)
+ * alpha.a and grad_alpha = sum_p grad_alpha_p - (P - 1) a (one sum across the
+ * GPUs per evaluation); the beta gradients are the shards' own.  ot_gs_solve
+ * rejects a shard handle (OTGS_EINVAL): its objective is partial.
+ */
+OTGS_API int ot_gs_create_shard(ot_gs **h, const float *C, int64_t ldc, const double *a, const double *b,
+                 const int32_t *labels, int64_t m, int64_t n, int32_t L, double gamma,
+                 double mu, void *stream);
+
 /* Release every resource of the handle (synchronises its stream).  NULL is a no-op. */
 OTGS_API int ot_gs_destroy(ot_gs *h);
 

@@ -68,6 +68,7 @@ def lib():
     P, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     sig = {
         "ot_gs_create": ([ctypes.POINTER(P), P, i64, P, P, P, i64, i64, i32, dbl, dbl, P], ctypes.c_int),
+        "ot_gs_create_shard": ([ctypes.POINTER(P), P, i64, P, P, P, i64, i64, i32, dbl, dbl, P], ctypes.c_int),
         "ot_gs_destroy": ([P], ctypes.c_int),
         "ot_gs_set_stream": ([P, P], ctypes.c_int),
         "ot_gs_set_params": ([P, ctypes.POINTER(Params)], ctypes.c_int),
@@ -174,15 +175,17 @@ def rho_to_gamma_mu(gamma: float, rho: float):
 
 
 # ---------------------------------------------------------- ABI wrappers
-def ot_gs_create(C, a, b, labels, L, gamma, mu, stream=None):
+def ot_gs_create(C, a, b, labels, L, gamma, mu, stream=None, shard=False):
     """C: (m, n) float32 CUDA (row stride C.stride(0)); a (m,), b (n,) float64;
-    labels (m,) int32 in [0, L).  Returns the raw handle (ctypes.c_void_p)."""
+    labels (m,) int32 in [0, L).  shard: C and b are a column shard of a
+    larger problem (ot_gs_create_shard).  Returns the raw handle (ctypes.c_void_p)."""
     import torch
     if C.dim() != 2 or C.stride(1) != 1:
         raise ValueError("C must be 2-D with unit column stride")
     m, n = C.shape
     h = ctypes.c_void_p()
-    rc = lib().ot_gs_create(ctypes.byref(h), _ptr(C, torch.float32, name="C") if C.is_contiguous()
+    fn = lib().ot_gs_create_shard if shard else lib().ot_gs_create
+    rc = fn(ctypes.byref(h), _ptr(C, torch.float32, name="C") if C.is_contiguous()
                             else ctypes.c_void_p(C.data_ptr()), C.stride(0),
                             _ptr(a, torch.float64, m, "a"), _ptr(b, torch.float64, n, "b"),
                             _ptr(labels, torch.int32, m, "labels"), m, n, int(L), float(gamma),
@@ -495,13 +498,13 @@ class GroupSparseOT:
     """One problem on the current CUDA device.  Keeps references to the
     borrowed input tensors for the handle's lifetime."""
 
-    def __init__(self, C, a, b, labels, L, gamma, mu, stream=None):
+    def __init__(self, C, a, b, labels, L, gamma, mu, stream=None, shard=False):
         import torch
         self._keep = (C, a, b, labels)
         self.m, self.n = C.shape
         self.L = int(L)
         self.device = C.device
-        self.h = ot_gs_create(C, a, b, labels, L, gamma, mu, stream)
+        self.h = ot_gs_create(C, a, b, labels, L, gamma, mu, stream, shard=shard)
 
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:

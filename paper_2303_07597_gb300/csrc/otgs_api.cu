@@ -160,7 +160,7 @@ bool Handle::init(int32_t np, const float* const* C_, const int64_t* ldc_, const
             if (f[0]) return fail(OTGS_ENONFINITE, "C has a non-finite entry" + where(k));
             if (f[1]) return fail(OTGS_EINVAL, "C has a negative entry" + where(k));
             if (f[2]) return fail(OTGS_EINVAL, "a and b must be positive and finite" + where(k));
-            if (!(std::fabs(sm[0] - sm[1]) <= 1e-12 * std::fmax(1.0, std::fmax(sm[0], sm[1]))))
+            if (!shard && !(std::fabs(sm[0] - sm[1]) <= 1e-12 * std::fmax(1.0, std::fmax(sm[0], sm[1]))))
                 return fail(OTGS_EINVAL, "sum(a) != sum(b)" + where(k));
             unsigned cbits = (unsigned)f[3];
             float cm;
@@ -558,8 +558,9 @@ int64_t Handle::nonempty_units() const
 
 extern "C" {
 
-int ot_gs_create(ot_gs** out, const float* C, int64_t ldc, const double* a, const double* b,
-                 const int32_t* labels, int64_t m, int64_t n, int32_t L, double gamma, double mu, void* stream)
+static int create_single(ot_gs** out, const float* C, int64_t ldc, const double* a, const double* b,
+                         const int32_t* labels, int64_t m, int64_t n, int32_t L, double gamma, double mu, void* stream,
+                         bool shard)
 {
     g_create_error.clear();
     if (!out) { g_create_error = "h is NULL"; return OTGS_EINVAL; }
@@ -572,6 +573,7 @@ int ot_gs_create(ot_gs** out, const float* C, int64_t ldc, const double* a, cons
     }
     Handle* h = new (std::nothrow) Handle();
     if (!h) { g_create_error = "out of host memory"; return OTGS_ENOMEM; }
+    h->shard = shard;
     if (!h->init(1, &C, &ldc, &a, &b, &labels, &m, &n, &L, gamma, mu, (cudaStream_t)stream)) {
         g_create_error = h->err;
         int code = h->last_code ? h->last_code : OTGS_ECUDA;
@@ -580,6 +582,18 @@ int ot_gs_create(ot_gs** out, const float* C, int64_t ldc, const double* a, cons
     }
     *out = reinterpret_cast<ot_gs*>(h);
     return OTGS_OK;
+}
+
+int ot_gs_create(ot_gs** out, const float* C, int64_t ldc, const double* a, const double* b,
+                 const int32_t* labels, int64_t m, int64_t n, int32_t L, double gamma, double mu, void* stream)
+{
+    return create_single(out, C, ldc, a, b, labels, m, n, L, gamma, mu, stream, false);
+}
+
+int ot_gs_create_shard(ot_gs** out, const float* C, int64_t ldc, const double* a, const double* b,
+                       const int32_t* labels, int64_t m, int64_t n, int32_t L, double gamma, double mu, void* stream)
+{
+    return create_single(out, C, ldc, a, b, labels, m, n, L, gamma, mu, stream, true);
 }
 
 int ot_gs_destroy(ot_gs* hh)

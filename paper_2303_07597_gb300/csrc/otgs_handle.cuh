@@ -28,6 +28,7 @@ struct Handle {
     // problems: one, or a batch of independent ones concatenated (rows in
     // problem order, class-sorted within a problem; columns in problem order)
     int32_t nprob = 1;
+    bool shard = false;               // a column shard: b is a slice of the marginal (no solve)
     std::vector<ProbDesc> probs_h;    // per problem: C (sorted rows), ldc, sizes, offsets
     ProbDesc* probs = nullptr;        // device copy
     std::vector<BProb> bprob_h;       // per problem: offsets and work-item range (plan-dependent)

@@ -628,6 +628,10 @@ int ot_gs_solve(ot_gs* hh, double tol, int32_t maxit)
     if (!hh) return OTGS_EINVAL;
     Handle* h = reinterpret_cast<Handle*>(hh);
     if (!single_problem(h)) return OTGS_EINVAL;
+    if (h->shard) {
+        h->fail(OTGS_EINVAL, "a column shard's objective is partial: combine the shards' evaluations");
+        return OTGS_EINVAL;
+    }
     if (!(tol >= 0.0) || maxit < 0) { h->fail(OTGS_EINVAL, "need tol >= 0 and maxit >= 0"); return OTGS_EINVAL; }
     if (!h->solver) {
         h->solver = new (std::nothrow) Solver();
