@@ -719,7 +719,12 @@ def case_report(args, dev):
     mlp: the warm-start network (input width 144, hidden 256) trained for
     ``--case-iters`` Adam steps on 65536 random samples in batches of 8192,
     then 50 more steps timed (three GEMM kernels forward and five backward
-    per step)."""
+    per step).
+    late: the 10k member of the large family (m = n = 10^4, 500 classes,
+    400 MB of C) solved from zero for ``--case-iters`` iterations (snapshot
+    and N taken there, as Alg. 1's refresh), then 10 iterations more (the
+    saved state restored and continued); at that iterate 20 dense and 20
+    screened evaluations are timed (CUDA events) after 3 of each untimed."""
     import torch
     import paper_2303_07597_gb300 as pk
     out = {"case": args.case}
@@ -752,6 +757,36 @@ def case_report(args, dev):
                    trial_ms=el * 1e3 / max(1, int(r["evals"].max())),
                    eval_at_iterate_ms=eval_ms(r["alpha"], r["beta"]))
         B.close()
+    elif args.case == "late":
+        cfg = WORKLOADS["large10k"]
+        p, C, _ = _make_workload("large10k", args.seed, str(dev))
+        s = pk.GroupSparseOT(C, torch.from_numpy(p.a).to(dev), torch.from_numpy(p.b).to(dev),
+                             torch.from_numpy(p.labels).to(dev), p.L, cfg["gamma"], cfg["mu"])
+        s.solve(0.0, args.case_iters)
+        it0 = s.solution()
+        s.restore_state(s.save_state())
+        s.solve(0.0, args.case_iters + 10)
+        it1 = s.solution()
+        s.snapshot(it0["alpha"], it0["beta"], build_N=False)
+        s.snapshot(it0["alpha"], it0["beta"], build_N=True)
+        outv = torch.empty(1 + p.m + p.n, dtype=torch.float64, device=dev)
+        stream = torch.cuda.current_stream()
+        al, be = it1["alpha"], it1["beta"]
+        torch.cuda.synchronize()
+        torch.cuda.profiler.start()  # (ncu --profile-from-start off captures from here)
+        dense_ms = _timed(lambda: pk.ot_gs_grad(s.h, al, be, outv), 20, stream)
+        Dd = float(outv[0].item())
+        pk.ot_gs_reset_stats(s.h)
+        scr_ms = _timed(lambda: pk.ot_gs_grad_screened(s.h, al, be, outv), 20, stream)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        st = s.stats()
+        out.update(workload="large10k: m=n=10000, L=500, gamma=1.0, mu=0.5", iterate=args.case_iters + 10,
+                   snapshot_iterate=args.case_iters, dense_ms=dense_ms, screened_ms=scr_ms,
+                   same_D=float(outv[0].item()) == Dd,
+                   screened_units_frac=st["units_computed"] / max(1, st["units_total"]),
+                   screened_blocks_skipped_frac=st["blocks_skipped"] / max(1, st["blocks_total"]))
+        s.close()
     else:
         from paper_2303_07597_gb300 import warmstart as ws
         K, H, nb = 144, 256, 8192
@@ -1033,8 +1068,9 @@ def main():
     ap.add_argument("--sweep-rhos", default="0.2,0.8")
     ap.add_argument("--sweep-tol", type=float, default=1e-7)
     ap.add_argument("--sweep-maxit", type=int, default=3000)
-    ap.add_argument("--case", choices=["batch", "mlp"],
-                    help="only one kernel family in isolation (for profiling): the batched solver or the network")
+    ap.add_argument("--case", choices=["batch", "mlp", "late"],
+                    help="only one kernel family in isolation (for profiling): the batched solver, the network, "
+                         "or the evaluations at a late solve iterate")
     ap.add_argument("--case-n", type=int, default=128, help="--case batch: problems")
     ap.add_argument("--case-iters", type=int, default=300, help="--case batch: iterations; mlp: training steps")
     args = ap.parse_args()
