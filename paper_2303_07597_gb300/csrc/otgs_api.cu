@@ -358,20 +358,17 @@ bool Handle::setup_plan(const PlanParams& pp)
         (float*)plan_alloc(sizeof(float) * SPLIT_VALS * ITEM_COLS * (size_t)hp.nsplit_slots, "split partial sums");
     if (!split_part) return false;
     {
-        int64_t ce = 0, ct = 0, cu = 0, cc = 0;
-        exact_caps(hp, ce, ct, cu, cc);
-        if (ce > INT32_MAX || ct > INT32_MAX || cu > INT32_MAX || cc > INT32_MAX)
+        int64_t ce = 0, ct = 0, cc = 0;
+        exact_caps(hp, ce, ct, cc);
+        if (ce > INT32_MAX || ct > INT32_MAX || cc > INT32_MAX)
             return fail(OTGS_EINVAL, "too many blocks");
         xent_cap = (int32_t)ce;
         xtall_cap = (int32_t)ct;
-        xunit_cap = (int32_t)cu;
         xtcol_cap = (int32_t)cc;
         xent = (XEntry*)plan_alloc(sizeof(XEntry) * (size_t)ce, "flagged block sets");
         xtall = (XEntry*)plan_alloc(sizeof(XEntry) * (size_t)ct, "flagged block sets of tall classes");
-        xpart = (float4*)plan_alloc(sizeof(float4) * (size_t)std::max<int64_t>(cu, 1), "slice sums");
-        xwmap = (uint32_t*)plan_alloc(sizeof(uint32_t) * (size_t)std::max<int64_t>(cu, 1), "slice sets");
-        xtcnt = (int*)plan_alloc(sizeof(int) * (size_t)std::max<int64_t>(cc, 1), "column slices done");
-        if (!xent || !xtall || !xpart || !xwmap || !xtcnt) return false;
+        xtmap = (uint32_t*)plan_alloc(sizeof(uint32_t) * (size_t)std::max<int64_t>(cc, 1), "column tasks");
+        if (!xent || !xtall || !xtmap) return false;
     }
     if (screen_alloc) {
         item_active = (uint8_t*)plan_alloc((size_t)hp.nitems(), "item_active");
@@ -412,9 +409,9 @@ EvalArgs Handle::eval_args(const uint8_t* active, const uint32_t* need, bool sna
     e.psix = ctl_psi(ctl);
     e.xent = xent; e.xent_cap = xent_cap;
     e.xtall = xtall; e.xtall_cap = xtall_cap;
-    e.xpart = xpart; e.xwmap = xwmap; e.xtcnt = xtcnt;
+    e.xtmap = xtmap;
     e.nprob = nprob;
-    e.xunit_cap = xunit_cap; e.xtcol_cap = xtcol_cap;
+    e.xtcol_cap = xtcol_cap;
     e.fcount = fcount;
     e.use_ct = 1;
     e.wait_ns = (unsigned long long)std::max<int64_t>(dbg_stall_ns, 0);
@@ -493,7 +490,7 @@ int Handle::eval_launch(const EvalArgs& e, int n_ctas)
     }
     launch_split_finish(e, st);
     launch_exact(e, n_sm, st);
-    return 4 + (e.nsets > 0);  // stream, exact (2), split finish
+    return 2 + (e.use_ct ? 1 : 2) + (e.nsets > 0);  // stream, exact, split finish
 }
 
 // Dense evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.

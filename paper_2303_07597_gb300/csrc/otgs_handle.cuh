@@ -60,10 +60,8 @@ struct Handle {
     XEntry* xent = nullptr;         // flagged block sets for the exact-sum kernel (sized by the plan):
     XEntry* xtall = nullptr;        // classes of at most XTALL_ROWS rows, taller classes
     int32_t xent_cap = 0, xtall_cap = 0;
-    float4* xpart = nullptr;        // transposed route of the taller classes: slice sums,
-    uint32_t* xwmap = nullptr;      //   unit -> set,
-    int* xtcnt = nullptr;           //   slices done per column
-    int32_t xunit_cap = 0, xtcol_cap = 0;
+    uint32_t* xtmap = nullptr;      // transposed route: column task of a taller class -> its set
+    int32_t xtcol_cap = 0;
     unsigned long long* fcount = nullptr;  // flagged blocks (statistics)
     int64_t dbg_stall_ns = 0;       // test hooks (ot_gs_debug): a stalled ring with this wait limit,
     int64_t dbg_nan_eval = 0;       //   a solve's objective NaN from this evaluation on,

@@ -240,8 +240,7 @@ struct EvalCtl {
     int nxent;          // flagged block sets of classes of at most XTALL_ROWS rows
     int nxtall;         // flagged block sets of taller classes
     int xnext;          // the next flagged block set of shorter classes for the exact-sum kernel
-    int unext;          // the next (column, slice) unit of the taller classes' sets
-    int nunit;          // units handed out
+    int tnext;          // the next column task of the taller classes' sets
     int ntcol;          // column tasks handed out
     int wl;             // screened: 1 = the screen built the sets itself (no bound pass; see k_route)
     unsigned long long psi[2];  // one problem: psi summed by the exact-sum kernel (fixed point, hi and lo)
@@ -265,8 +264,7 @@ __device__ __forceinline__ void ctl_clear(EvalCtl* c)
     c->nxent = 0;
     c->nxtall = 0;
     c->xnext = 0;
-    c->unext = 0;
-    c->nunit = 0;
+    c->tnext = 0;
     c->ntcol = 0;
     c->wl = 0;
     c->wl_work = 0ull;
@@ -290,8 +288,8 @@ struct XEntry {
     int prob;          // problem of a batch
     int l;             // group
     uint32_t mask;     // columns (bit k: column colg0 + k) to evaluate
-    int ubase;         // taller classes, transposed copy: first (column, slice) unit of the set
-    int tbase;         //   and first column task
+    int tbase;         // taller classes, transposed copy: the set's first column task
+    int pad_;
 };
 
 // A screened evaluation reads the blocks the screen left straight from the
@@ -300,7 +298,7 @@ struct XEntry {
 constexpr double WL_FRACTION = 0.25;
 
 // Rows of a slice of a taller class's column (the transposed copy's exact
-// sums: one warp per slice, partial sums added in slice order).
+// sums: one warp per slice, slice sums added in slice order).
 constexpr int XSLICE = 256;
 
 
@@ -428,10 +426,8 @@ struct EvalArgs {
     float thr_flag;    // RD(theta^2 (1 - 2^-21)): a block whose FP32 bound stays at or below it has s = 0
     unsigned long long* fcount;  // NULL, or a counter of the flagged blocks (statistics)
     int32_t use_ct;    // 1: every problem has its transposed copy (ProbDesc::CT) for the exact sums
-    float4* xpart;     // transposed route: per unit, its slice's (S hi, S lo, P hi, P lo), then its row-sum record
-    uint32_t* xwmap;   //   per unit, its set in the taller classes' list
-    int* xtcnt;        //   per column task, slices done
-    int32_t xunit_cap, xtcol_cap;
+    uint32_t* xtmap;   // transposed route: per column task of a taller class, its set
+    int32_t xtcol_cap;
     int32_t nprob;     // problems
     unsigned long long wait_ns;  // 0: the default limit of the evaluation kernel's waits; else this one
     int32_t stall;     // test hook: the consumer warps do not release stages (the waits run out)
@@ -483,27 +479,22 @@ struct ReduceArgs {
 
 // A block set for the exact-sum kernels (all lanes of the calling warp; lane
 // 0 records it): rows [gstart, gend) of group l x the columns colg0 + k, k in
-// mask.  With the transposed copy, a taller class's set also gets its (column,
-// slice) units and column tasks (capacities hold every (group, column) once).
+// mask.  With the transposed copy, a taller class's set also gets a column
+// task per column (capacities hold every (group, column) once).
 __device__ __forceinline__ void add_xentry(const EvalArgs& A, int gstart, int gend, int colg0, int prob, int l,
                                            uint32_t mask, int lane)
 {
     const bool tall = gend - gstart > XTALL_ROWS;
-    const int nc = __popc(mask), ns = (gend - gstart + XSLICE - 1) / XSLICE;
-    int e = 0, ub = 0, tb = 0;
+    const int nc = __popc(mask);
+    int e = 0, tb = 0;
     if (lane == 0) {
         e = atomicAdd(tall ? &A.ctl->nxtall : &A.ctl->nxent, 1);
-        if (tall && A.use_ct) {
-            ub = atomicAdd(&A.ctl->nunit, nc * ns);
-            tb = atomicAdd(&A.ctl->ntcol, nc);
-        }
+        if (tall && A.use_ct) tb = atomicAdd(&A.ctl->ntcol, nc);
         if (A.fcount) atomicAdd(A.fcount, (unsigned long long)nc);
     }
     e = __shfl_sync(0xffffffffu, e, 0);
-    ub = __shfl_sync(0xffffffffu, ub, 0);
     tb = __shfl_sync(0xffffffffu, tb, 0);
-    if (e >= (tall ? A.xtall_cap : A.xent_cap) ||
-        (tall && A.use_ct && (ub + nc * ns > A.xunit_cap || tb + nc > A.xtcol_cap))) {
+    if (e >= (tall ? A.xtall_cap : A.xent_cap) || (tall && A.use_ct && tb + nc > A.xtcol_cap)) {
         if (lane == 0) atomicOr(A.err, 4);  // the capacities hold every (group, column) once: not reached
         return;
     }
@@ -515,13 +506,9 @@ __device__ __forceinline__ void add_xentry(const EvalArgs& A, int gstart, int ge
         x.prob = prob;
         x.l = l;
         x.mask = mask;
-        x.ubase = ub;
         x.tbase = tb;
     }
-    if (tall && A.use_ct) {
-        for (int i = lane; i < nc * ns; i += 32) A.xwmap[ub + i] = (uint32_t)e;
-        if (lane < nc) A.xtcnt[tb + lane] = 0;
-    }
+    if (tall && A.use_ct && lane < nc) A.xtmap[tb + lane] = (uint32_t)e;
 }
 
 // launchers (otgs_eval.cu)
@@ -549,7 +536,7 @@ void launch_exact(const EvalArgs& a, int n_sm, cudaStream_t st);
 // Capacities of the flagged-block lists (host): one entry per (non-empty
 // group, 32-column tile of its problem), each recorded at most once per
 // evaluation; groups of at most XTALL_ROWS rows, and taller ones.
-void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall, int64_t& units, int64_t& tcols);
+void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall, int64_t& tcols);
 size_t stream_smem_bytes();
 void launch_reduce(const ReduceArgs& a, cudaStream_t st);
 int reduce_blocks(int32_t m, int32_t n);

@@ -98,8 +98,8 @@ int ot_gs_grad_noalloc(const float* C, int64_t ldc, const double* a, const doubl
     const size_t o_rowfx = cv.take(8 * (size_t)m), o_colfx = cv.take(8 * (size_t)n);
     const size_t o_spart = cv.take(sizeof(float) * SPLIT_VALS * ITEM_COLS * (size_t)hp.nsplit_slots);
     int64_t xe_cap = 0, xt_cap = 0;
-    int64_t xu_cap = 0, xc_cap = 0;  // (the transposed route's; not used here)
-    exact_caps(hp, xe_cap, xt_cap, xu_cap, xc_cap);
+    int64_t xc_cap = 0;  // (the transposed route's; not used here)
+    exact_caps(hp, xe_cap, xt_cap, xc_cap);
     const size_t o_xent = cv.take(sizeof(XEntry) * (size_t)xe_cap);
     const size_t o_xtall = cv.take(sizeof(XEntry) * (size_t)xt_cap);
     const size_t o_sets = cv.take(sizeof(SplitSet) * hp.sets.size());

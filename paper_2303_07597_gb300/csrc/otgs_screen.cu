@@ -284,7 +284,7 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
 // group's rows x the tile's columns the screen did not skip.  A warp per mask
 // word of a group, lane t for tile 32 w + t: one atomic per counter and warp
 // (warp scans give each lane its place), then every lane writes its own set
-// (and a taller class's slice units and column tasks).  Also sums the sets'
+// (and a taller class's column tasks).  Also sums the sets'
 // rows x columns for k_route.
 __global__ void __launch_bounds__(256) k_wlist(const ScreenArgs S, const EvalArgs E)
 {
@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(256) k_wlist(const ScreenArgs S, const EvalArg
         const uint32_t hb = __ballot_sync(FULLMASK, need != 0u);
         if (!hb) continue;  // (uniform)
         const bool tall = g > XTALL_ROWS;
-        const int nc = __popc(need), ns = (g + XSLICE - 1) / XSLICE;
+        const int nc = __popc(need);
         // inclusive scan of the columns over the lanes
         int cs = nc;
 #pragma unroll
@@ -318,23 +318,18 @@ __global__ void __launch_bounds__(256) k_wlist(const ScreenArgs S, const EvalArg
             if (lane >= off) cs += v;
         }
         const int ctot = __shfl_sync(FULLMASK, cs, 31);
-        int e0 = 0, ub = 0, tb = 0;
+        int e0 = 0, tb = 0;
         if (lane == 0) {
             e0 = atomicAdd(tall ? &E.ctl->nxtall : &E.ctl->nxent, __popc(hb));
-            if (tall && E.use_ct) {
-                ub = atomicAdd(&E.ctl->nunit, ctot * ns);
-                tb = atomicAdd(&E.ctl->ntcol, ctot);
-            }
+            if (tall && E.use_ct) tb = atomicAdd(&E.ctl->ntcol, ctot);
         }
         e0 = __shfl_sync(FULLMASK, e0, 0);
-        ub = __shfl_sync(FULLMASK, ub, 0) + (cs - nc) * ns;
         tb = __shfl_sync(FULLMASK, tb, 0) + (cs - nc);
         work += (unsigned long long)g * (unsigned long long)ctot;
         flagged += (unsigned long long)ctot;
         if (!need) continue;
         const int e = e0 + __popc(hb & lt);
-        if (e >= (tall ? E.xtall_cap : E.xent_cap) ||
-            (tall && E.use_ct && (ub + nc * ns > E.xunit_cap || tb + nc > E.xtcol_cap))) {
+        if (e >= (tall ? E.xtall_cap : E.xent_cap) || (tall && E.use_ct && tb + nc > E.xtcol_cap)) {
             atomicOr(E.err, 4);  // the capacities hold every (group, column) once: not reached
             continue;
         }
@@ -345,12 +340,9 @@ __global__ void __launch_bounds__(256) k_wlist(const ScreenArgs S, const EvalArg
         x.prob = 0;
         x.l = l;
         x.mask = need;
-        x.ubase = ub;
         x.tbase = tb;
-        if (tall && E.use_ct) {
-            for (int i = 0; i < nc * ns; i++) E.xwmap[ub + i] = (uint32_t)e;
-            for (int i = 0; i < nc; i++) E.xtcnt[tb + i] = 0;
-        }
+        if (tall && E.use_ct)
+            for (int i = 0; i < nc; i++) E.xtmap[tb + i] = (uint32_t)e;
     }
     if (lane == 0 && work) {
         atomicAdd(&E.ctl->wl_work, work);
@@ -378,7 +370,6 @@ __global__ void k_route(const ScreenArgs S, EvalCtl* ctl, unsigned long long* fc
     } else {
         ctl->nxent = 0;
         ctl->nxtall = 0;
-        ctl->nunit = 0;
         ctl->ntcol = 0;
     }
 }

@@ -1181,17 +1181,17 @@ __global__ void __launch_bounds__(TALL_THREADS, 2) k_exact_tall(const EvalArgs A
 // (l, j) is the contiguous run CT[j][gstart, gend) of its problem: warps read
 // it with coalesced loads, one row per lane, and only the flagged columns'
 // bytes are read.
+//  * A taller class's column (a column task): one CTA, taken from a counter
+//    before the shorter sets (the longest work goes out first).  Its slices of
+//    XSLICE rows go to the eight warps in rounds (slice 8 r + w to warp w);
+//    each warp sums its slice (S = sum [f]_+^2 and P = sum [f]_+ in
+//    double-float per lane in row order, the fixed xor tree), one thread adds
+//    the slices in slice order and finishes the block (Eq. 5: psi in fixed
+//    point, the column sum s P, a snapshot's z~), then the warps add their
+//    slices' t_ij = s [f_ij]_+ to the row sums (the rows again, from L1).
 //  * A shorter class's set (at most XTALL_ROWS rows): one warp, taken from a
-//    counter.  Per column: S = sum [f]_+^2 and P = sum [f]_+ in double-float
-//    per lane (rows gstart + lane + 32 u in order), the fixed xor tree, Eq. 5
-//    (psi in fixed point, the column sum s P, a snapshot's z~).  Then its rows
-//    once more, every column with s > 0 per row: t_ij = s [f_ij]_+ into the
-//    row's fixed-point sum.
-//  * A taller class's column: one warp per slice of XSLICE rows (a unit),
-//    units of every such column taken from a counter first.  Each slice's
-//    sums (the same per-lane order and tree) go to its unit's partial; the
-//    warp that completes a column adds the partials in slice order and
-//    finishes it (Eq. 5).  k_exact_t_rows then adds each slice's t_ij.
+//    counter.  Per column the same sums over its rows (one slice), Eq. 5; then
+//    its rows once more, every column with s > 0 per row, one atomic per row.
 // Every floating-point sum has a fixed order, so a block's results do not
 // depend on its set, on scheduling or on the evaluation being screened.
 constexpr int XTC_THREADS = 256;
@@ -1252,73 +1252,83 @@ __device__ __forceinline__ void hold_psi(const EvalArgs& A, int prob, int& pprob
     }
 }
 
-__global__ void __launch_bounds__(XTC_THREADS, 2) k_exact_t(const EvalArgs A)
+__global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
     const int nx = min(A.ctl->nxent, A.xent_cap);
-    const int nu = min(A.ctl->nunit, A.xunit_cap);
-    const int lane = threadIdx.x & 31;
+    const int ntc = min(A.ctl->ntcol, A.xtcol_cap);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = XTC_THREADS / 32;
     __shared__ FxScale fx1;  // one problem: the evaluation's scale
-    if (threadIdx.x == 0 && !A.pfx && nx + nu > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
-    __syncthreads();
-    int pprob = -1;  // lane 0: the problem of the psi sums it holds
+    __shared__ Acc spart[NW];
+    __shared__ int sh_t;
+    __shared__ float sh_s;
+    if (tid == 0 && !A.pfx && nx + ntc > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
+    int pprob = -1;  // lane 0 of each warp: the problem of the psi sums it holds
     long long ph = 0, pl = 0;
-    // the taller classes' units
+    // the taller classes' columns, a CTA each
     for (;;) {
-        int u = 0;
-        if (lane == 0) u = atomicAdd(&A.ctl->unext, 1);
-        u = __shfl_sync(FULLMASK, u, 0);
-        if (u >= nu) break;
-        const XEntry E = A.xtall[A.xwmap[u]];
-        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
-        const int ns = (E.gend - E.gstart + XSLICE - 1) / XSLICE;
-        const int q = (u - E.ubase) / ns, sl = (u - E.ubase) % ns;
-        const int k = __fns(E.mask, 0, q + 1);  // the set's q-th column
+        if (tid == 0) sh_t = atomicAdd(&A.ctl->tnext, 1);
+        __syncthreads();
+        const int t = sh_t;
+        if (t >= ntc) break;  // (uniform)
+        const XEntry E = A.xtall[A.xtmap[t]];
+        const ProbDesc& pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
+        const int k = __fns(E.mask, 0, t - E.tbase + 1);  // the column of this task
         const int lcol = E.colg0 + k - pd.coff;
         const float2 b2 = __ldg(A.B2 + pd.bcoff + lcol);
+        const float bp = bound_up(b2.x);
         const float* col = pd.CT + (int64_t)lcol * pd.ldct - pd.roff;
-        const int r0 = E.gstart + sl * XSLICE;
-        const Acc p = slice_sums(A, col, r0, min(E.gend, r0 + XSLICE), bound_up(b2.x), b2.x, b2.y, lane);
-        int done = 0;
-        if (lane == 0) {
-            A.xpart[u] = make_float4(p.Sh, p.Sl, p.Ph, p.Pl);
-            __threadfence();
-            done = atomicAdd(A.xtcnt + E.tbase + q, 1) == ns - 1;
-        }
-        done = __shfl_sync(FULLMASK, done, 0);
-        if (!done) continue;  // (uniform)
-        // the column's last slice: add the slices in order and finish it
-        const int u0 = E.ubase + q * ns;
-        float sv = 0.f;
-        if (lane == 0) {
-            __threadfence();
-            Acc T = {0.f, 0.f, 0.f, 0.f};
-            for (int i = 0; i < ns; i++) {
-                const float4 v = __ldcg(A.xpart + u0 + i);
-                df_add(T.Sh, T.Sl, v.x, v.y);
-                df_add(T.Ph, T.Pl, v.z, v.w);
+        const int ns = (E.gend - E.gstart + XSLICE - 1) / XSLICE;
+        Acc T = {0.f, 0.f, 0.f, 0.f};  // thread 0
+        for (int r0 = 0; r0 < ns; r0 += NW) {
+            const int sl = r0 + warp;
+            if (sl < ns) {
+                const int a0 = E.gstart + sl * XSLICE;
+                const Acc p = slice_sums(A, col, a0, min(E.gend, a0 + XSLICE), bp, b2.x, b2.y, lane);
+                if (lane == 0) spart[warp] = p;
             }
-            const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
+            __syncthreads();
+            if (tid == 0)
+                for (int w = 0; w < NW && r0 + w < ns; w++) {
+                    df_add(T.Sh, T.Sl, spart[w].Sh, spart[w].Sl);
+                    df_add(T.Ph, T.Pl, spart[w].Ph, spart[w].Pl);
+                }
+            __syncthreads();  // spart is refilled by the next round
+        }
+        if (tid == 0) {
             hold_psi(A, E.prob, pprob, ph, pl);
-            sv = finish_block_exact(A, fx, T, E.l, E.colg0 + k, ph, pl);
+            sh_s = finish_block_exact(A, A.pfx ? A.pfx[E.prob] : fx1, T, E.l, E.colg0 + k, ph, pl);
         }
-        sv = __shfl_sync(FULLMASK, sv, 0);
-        // the slices' row-sum records over their partials (read above): first
-        // row, column, s, rows | problem << 9
-        for (int i = lane; i < ns; i += 32) {
-            const int ri = E.gstart + i * XSLICE;
-            reinterpret_cast<int4*>(A.xpart)[u0 + i] =
-                make_int4(ri, lcol, __float_as_int(sv), min(XSLICE, E.gend - ri) | (E.prob << 9));
+        __syncthreads();
+        const float s = sh_s;
+        if (s > 0.f) {  // (uniform)
+            const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
+            for (int sl = warp; sl < ns; sl += NW) {
+#pragma unroll
+                for (int u = 0; u < XTC_UNROLL; u++) {
+                    const int R = E.gstart + sl * XSLICE + 32 * u + lane;
+                    if (R >= E.gend) break;
+                    const float4 a = __ldg(A.rowA + R);
+                    const float c = __ldg(col + R);
+                    if (maybe_pos(a.z, c, bp)) {
+                        float fh, fl;
+                        f_exact(a.x, a.y, b2.x, b2.y, c, fh, fl);
+                        if (fh > 0.f) atomicAdd(A.rowfx + R, t_q(__fmul_rn(s, fh), fx.to_rf));
+                    }
+                }
+            }
         }
+        __syncthreads();  // sh_t, sh_s are rewritten by the next column
     }
-    // the shorter classes' sets
+    // the shorter classes' sets, a warp each
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(&A.ctl->xnext, 1);
         t = __shfl_sync(FULLMASK, t, 0);
         if (t >= nx) break;
         const XEntry E = A.xent[t];
-        const ProbDesc pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
+        const ProbDesc& pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
         const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
         if (lane == 0) hold_psi(A, E.prob, pprob, ph, pl);
         const float* ct0 = pd.CT + (int64_t)(E.colg0 - pd.coff) * pd.ldct - pd.roff;  // + k ldct + R
@@ -1373,74 +1383,25 @@ __global__ void __launch_bounds__(XTC_THREADS, 2) k_exact_t(const EvalArgs A)
     }
 }
 
-// Row sums of the taller classes' columns with s > 0: one warp per unit, from
-// the record k_exact_t left in the unit's slot (no other lookup before the
-// data loads).
-__global__ void __launch_bounds__(XTC_THREADS) k_exact_t_rows(const EvalArgs A)
-{
-    if (A.gate && !*A.gate) return;
-    const int nu = min(A.ctl->nunit, A.xunit_cap);
-    const int lane = threadIdx.x & 31, nw = XTC_THREADS / 32;
-    __shared__ FxScale fx1;
-    if (threadIdx.x == 0 && !A.pfx && nu > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
-    __syncthreads();
-    const int4* rec = reinterpret_cast<const int4*>(A.xpart);
-    const int step = gridDim.x * nw;
-    int u = blockIdx.x * nw + (threadIdx.x >> 5);
-    int4 rn = u < nu ? __ldcg(rec + u) : make_int4(0, 0, 0, 0);  // the next unit's record, loaded ahead
-    for (; u < nu; u += step) {
-        const int4 r = rn;
-        if (u + step < nu) rn = __ldcg(rec + u + step);
-        const float s = __int_as_float(r.z);
-        if (!(s > 0.f)) continue;  // (uniform)
-        const int prob = r.w >> 9, cnt = r.w & 511;
-        if (prob >= A.nprob || (A.inline_maps && prob != 0) || cnt > XSLICE || r.x < 0 || r.x + cnt > A.m)
-            continue;  // (not reached: every unit's column is finished before this kernel)
-        const ProbDesc& pd = A.inline_maps ? A.pd0 : A.probs[prob];
-        if (r.y < 0 || r.y >= pd.n) continue;
-        const FxScale& fx = A.pfx ? A.pfx[prob] : fx1;
-        const float2 b2 = __ldg(A.B2 + pd.bcoff + r.y);
-        const float bp = bound_up(b2.x);
-        const float* col = pd.CT + (int64_t)r.y * pd.ldct - pd.roff;
-#pragma unroll
-        for (int uu = 0; uu < XTC_UNROLL; uu++) {
-            const int i = 32 * uu + lane;
-            if (i >= cnt) break;
-            const int R = r.x + i;
-            const float4 a = __ldg(A.rowA + R);
-            const float c = __ldg(col + R);
-            if (maybe_pos(a.z, c, bp)) {
-                float fh, fl;
-                f_exact(a.x, a.y, b2.x, b2.y, c, fh, fl);
-                if (fh > 0.f) atomicAdd(A.rowfx + R, t_q(__fmul_rn(s, fh), fx.to_rf));
-            }
-        }
-    }
-}
-
 void launch_exact(const EvalArgs& a, int n_sm, cudaStream_t st)
 {
     if (a.use_ct) {
-        k_exact_t<<<2 * n_sm, XTC_THREADS, 0, st>>>(a);
-        k_exact_t_rows<<<8 * n_sm, XTC_THREADS, 0, st>>>(a);
+        k_exact_t<<<3 * n_sm, XTC_THREADS, 0, st>>>(a);
         return;
     }
     k_exact<<<4 * n_sm, EXACT_THREADS, 0, st>>>(a);
     k_exact_tall<<<2 * n_sm, TALL_THREADS, 0, st>>>(a);
 }
 
-void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall, int64_t& units, int64_t& tcols)
+void exact_caps(const HostPlan& hp, int64_t& xent, int64_t& xtall, int64_t& tcols)
 {
-    xent = xtall = units = tcols = 0;
+    xent = xtall = tcols = 0;
     for (int64_t l = 0; l < hp.L; l++) {
         const int64_t g = hp.goff[l + 1] - hp.goff[l];
         if (g == 0) continue;
         const int64_t n = hp.pn[hp.gprob[l]];
         (g > XTALL_ROWS ? xtall : xent) += (n + TW - 1) / TW;
-        if (g > XTALL_ROWS) {
-            tcols += n;
-            units += n * ((g + XSLICE - 1) / XSLICE);
-        }
+        if (g > XTALL_ROWS) tcols += n;
     }
 }
 
