@@ -720,8 +720,8 @@ def case_report(args, dev):
     ``--case-iters`` Adam steps on 65536 random samples in batches of 8192,
     then 50 more steps timed (three GEMM kernels forward and five backward
     per step).
-    late: the 10k member of the large family (m = n = 10^4, 500 classes,
-    400 MB of C) solved from zero for ``--case-iters`` iterations (snapshot
+    late: a member of the large family (``--case-workload``: the 10k one, m =
+    n = 10^4, 500 classes, 400 MB of C, or the full one) solved from zero for ``--case-iters`` iterations (snapshot
     and N taken there, as Alg. 1's refresh), then 10 iterations more (the
     saved state restored and continued); at that iterate 20 dense and 20
     screened evaluations are timed (CUDA events) after 3 of each untimed."""
@@ -758,8 +758,9 @@ def case_report(args, dev):
                    eval_at_iterate_ms=eval_ms(r["alpha"], r["beta"]))
         B.close()
     elif args.case == "late":
-        cfg = WORKLOADS["large10k"]
-        p, C, _ = _make_workload("large10k", args.seed, str(dev))
+        wl = args.case_workload
+        cfg = WORKLOADS[wl]
+        p, C, _ = _make_workload(wl, args.seed, str(dev))
         s = pk.GroupSparseOT(C, torch.from_numpy(p.a).to(dev), torch.from_numpy(p.b).to(dev),
                              torch.from_numpy(p.labels).to(dev), p.L, cfg["gamma"], cfg["mu"])
         s.solve(0.0, args.case_iters)
@@ -781,7 +782,8 @@ def case_report(args, dev):
         torch.cuda.synchronize()
         torch.cuda.profiler.stop()
         st = s.stats()
-        out.update(workload="large10k: m=n=10000, L=500, gamma=1.0, mu=0.5", iterate=args.case_iters + 10,
+        out.update(workload=f"{wl}: m=n={cfg['m']}, L={cfg['L']}, gamma={cfg['gamma']}, mu={cfg['mu']}",
+                   iterate=args.case_iters + 10,
                    snapshot_iterate=args.case_iters, dense_ms=dense_ms, screened_ms=scr_ms,
                    same_D=float(outv[0].item()) == Dd,
                    screened_units_frac=st["units_computed"] / max(1, st["units_total"]),
@@ -1072,6 +1074,8 @@ def main():
                     help="only one kernel family in isolation (for profiling): the batched solver, the network, "
                          "or the evaluations at a late solve iterate")
     ap.add_argument("--case-n", type=int, default=128, help="--case batch: problems")
+    ap.add_argument("--case-workload", choices=["large10k", "large"], default="large10k",
+                    help="--case late: the member of the large family")
     ap.add_argument("--case-iters", type=int, default=300, help="--case batch: iterations; mlp: training steps")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -1181,14 +1181,13 @@ __global__ void __launch_bounds__(TALL_THREADS, 2) k_exact_tall(const EvalArgs A
 // (l, j) is the contiguous run CT[j][gstart, gend) of its problem: warps read
 // it with coalesced loads, one row per lane, and only the flagged columns'
 // bytes are read.
-//  * A taller class's column (a column task): one CTA, taken from a counter
-//    before the shorter sets (the longest work goes out first).  Its slices of
-//    XSLICE rows go to the eight warps in rounds (slice 8 r + w to warp w);
-//    each warp sums its slice (S = sum [f]_+^2 and P = sum [f]_+ in
-//    double-float per lane in row order, the fixed xor tree), one thread adds
-//    the slices in slice order and finishes the block (Eq. 5: psi in fixed
-//    point, the column sum s P, a snapshot's z~), then the warps add their
-//    slices' t_ij = s [f_ij]_+ to the row sums (the rows again, from L1).
+//  * A taller class's column (a column task): one warp, taken from a counter
+//    before the shorter sets (the longest work goes out first).  It sums its
+//    slices of XSLICE rows one after the other (S = sum [f]_+^2 and P = sum
+//    [f]_+ in double-float per lane in row order, the fixed xor tree per
+//    slice, the slices added in slice order), finishes the block (Eq. 5: psi
+//    in fixed point, the column sum s P, a snapshot's z~), then adds the
+//    rows' t_ij = s [f_ij]_+ to the row sums (the rows again, from L1/L2).
 //  * A shorter class's set (at most XTALL_ROWS rows): one warp, taken from a
 //    counter.  Per column the same sums over its rows (one slice), Eq. 5; then
 //    its rows once more, every column with s > 0 per row, one atomic per row.
@@ -1257,69 +1256,57 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
     if (A.gate && !*A.gate) return;
     const int nx = min(A.ctl->nxent, A.xent_cap);
     const int ntc = min(A.ctl->ntcol, A.xtcol_cap);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = XTC_THREADS / 32;
+    const int tid = threadIdx.x, lane = tid & 31;
     __shared__ FxScale fx1;  // one problem: the evaluation's scale
-    __shared__ Acc spart[NW];
-    __shared__ int sh_t;
-    __shared__ float sh_s;
     if (tid == 0 && !A.pfx && nx + ntc > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
+    __syncthreads();
     int pprob = -1;  // lane 0 of each warp: the problem of the psi sums it holds
     long long ph = 0, pl = 0;
-    // the taller classes' columns, a CTA each
+    // the taller classes' columns, a warp each
     for (;;) {
-        if (tid == 0) sh_t = atomicAdd(&A.ctl->tnext, 1);
-        __syncthreads();
-        const int t = sh_t;
-        if (t >= ntc) break;  // (uniform)
+        int t = 0;
+        if (lane == 0) t = atomicAdd(&A.ctl->tnext, 1);
+        t = __shfl_sync(FULLMASK, t, 0);
+        if (t >= ntc) break;
         const XEntry E = A.xtall[A.xtmap[t]];
         const ProbDesc& pd = A.inline_maps ? A.pd0 : A.probs[E.prob];
+        const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
         const int k = __fns(E.mask, 0, t - E.tbase + 1);  // the column of this task
         const int lcol = E.colg0 + k - pd.coff;
         const float2 b2 = __ldg(A.B2 + pd.bcoff + lcol);
         const float bp = bound_up(b2.x);
         const float* col = pd.CT + (int64_t)lcol * pd.ldct - pd.roff;
-        const int ns = (E.gend - E.gstart + XSLICE - 1) / XSLICE;
-        Acc T = {0.f, 0.f, 0.f, 0.f};  // thread 0
-        for (int r0 = 0; r0 < ns; r0 += NW) {
-            const int sl = r0 + warp;
-            if (sl < ns) {
-                const int a0 = E.gstart + sl * XSLICE;
-                const Acc p = slice_sums(A, col, a0, min(E.gend, a0 + XSLICE), bp, b2.x, b2.y, lane);
-                if (lane == 0) spart[warp] = p;
-            }
-            __syncthreads();
-            if (tid == 0)
-                for (int w = 0; w < NW && r0 + w < ns; w++) {
-                    df_add(T.Sh, T.Sl, spart[w].Sh, spart[w].Sl);
-                    df_add(T.Ph, T.Pl, spart[w].Ph, spart[w].Pl);
-                }
-            __syncthreads();  // spart is refilled by the next round
+        Acc T = {0.f, 0.f, 0.f, 0.f};  // the slices' sums, added in slice order
+        for (int a0 = E.gstart; a0 < E.gend; a0 += XSLICE) {
+            const Acc p = slice_sums(A, col, a0, min(E.gend, a0 + XSLICE), bp, b2.x, b2.y, lane);
+            df_add(T.Sh, T.Sl, p.Sh, p.Sl);
+            df_add(T.Ph, T.Pl, p.Ph, p.Pl);
         }
-        if (tid == 0) {
+        float s = 0.f;
+        if (lane == 0) {
             hold_psi(A, E.prob, pprob, ph, pl);
-            sh_s = finish_block_exact(A, A.pfx ? A.pfx[E.prob] : fx1, T, E.l, E.colg0 + k, ph, pl);
+            s = finish_block_exact(A, fx, T, E.l, E.colg0 + k, ph, pl);
         }
-        __syncthreads();
-        const float s = sh_s;
-        if (s > 0.f) {  // (uniform)
-            const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
-            for (int sl = warp; sl < ns; sl += NW) {
+        s = __shfl_sync(FULLMASK, s, 0);
+        if (!(s > 0.f)) continue;  // (uniform)
+        for (int a0 = E.gstart; a0 < E.gend; a0 += XSLICE) {
+            float c[XTC_UNROLL];
+            float4 a[XTC_UNROLL];
 #pragma unroll
-                for (int u = 0; u < XTC_UNROLL; u++) {
-                    const int R = E.gstart + sl * XSLICE + 32 * u + lane;
-                    if (R >= E.gend) break;
-                    const float4 a = __ldg(A.rowA + R);
-                    const float c = __ldg(col + R);
-                    if (maybe_pos(a.z, c, bp)) {
-                        float fh, fl;
-                        f_exact(a.x, a.y, b2.x, b2.y, c, fh, fl);
-                        if (fh > 0.f) atomicAdd(A.rowfx + R, t_q(__fmul_rn(s, fh), fx.to_rf));
-                    }
-                }
+            for (int u = 0; u < XTC_UNROLL; u++) {
+                const int R = a0 + 32 * u + lane;
+                const bool in = R < E.gend;
+                a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+                c[u] = in ? __ldg(col + R) : 0.f;
             }
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++)
+                if (maybe_pos(a[u].z, c[u], bp)) {
+                    float fh, fl;
+                    f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
+                    if (fh > 0.f) atomicAdd(A.rowfx + a0 + 32 * u + lane, t_q(__fmul_rn(s, fh), fx.to_rf));
+                }
         }
-        __syncthreads();  // sh_t, sh_s are rewritten by the next column
     }
     // the shorter classes' sets, a warp each
     for (;;) {
