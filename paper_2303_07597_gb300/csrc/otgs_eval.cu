@@ -67,7 +67,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const ReduceArgs R)
     if (R.gate && !*R.gate) return;  // a skipped solver trial
     __shared__ double sh[3][RED_WARPS];
     __shared__ bool last;
-    const FxScale fx = fx_scale(R.ctl->amax, R.ctl->bmax, R.fx_m, R.fx_n, R.gamma);
+    __shared__ FxScale fxs;  // once per block (FP64 scale arithmetic)
+    if (threadIdx.x == 0) fxs = fx_scale(R.ctl->amax, R.ctl->bmax, R.fx_m, R.fx_n, R.gamma);
+    __syncthreads();
+    const FxScale& fx = fxs;
     const int t = blockIdx.x * RED_THREADS + threadIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     double ab = 0.0, dt = 0.0, inf = 0.0;

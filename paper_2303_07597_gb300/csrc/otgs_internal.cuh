@@ -246,6 +246,7 @@ struct EvalCtl {
     unsigned long long psi[2];  // one problem: psi summed by the exact-sum kernel (fixed point, hi and lo)
     unsigned long long wl_work;  // screened: rows x columns of the blocks the screen left (see k_route)
     unsigned long long wl_cols;  //   and their number
+    unsigned wl_done;            //   blocks of the list kernel done (its last one picks the route)
 };
 
 // Device address of the control word's psi accumulators (host side: plain
@@ -269,6 +270,7 @@ __device__ __forceinline__ void ctl_clear(EvalCtl* c)
     c->wl = 0;
     c->wl_work = 0ull;
     c->wl_cols = 0ull;
+    c->wl_done = 0u;
     c->psi[0] = 0ull;
     c->psi[1] = 0ull;
 }
@@ -525,7 +527,7 @@ void launch_stream(const EvalArgs& a, int n_ctas, cudaStream_t st);
 bool stream_prepare();
 // stage-mask kernel (otgs_stream.cu), screened evaluations: fills
 // a.stage_m8 from a.unit_need for the active items.  Launch before launch_stream.
-void launch_stage_masks(const EvalArgs& a, cudaStream_t st);
+void launch_stage_masks(const EvalArgs& a, int n_sm, cudaStream_t st);
 // split-finish kernel (otgs_stream.cu): adds the pieces' partial sums of the
 // split groups' blocks and finishes them.  Launch right after launch_stream.
 void launch_split_finish(const EvalArgs& a, cudaStream_t st);

@@ -58,8 +58,8 @@ struct ScreenArgs {
     int32_t nitems;
     const int* gate;            // NULL, or a device flag: 0 = skip (batched solver trials)
     int32_t wl_build;           // 1: record each needed unit as a block set for the exact-sum kernels
-    int32_t route;              // 0: k_route decides, 1: the bound pass, 2: the screen's block sets
-    double wl_max;              // k_route takes the screen's sets when their rows x columns are at most this
+    int32_t route;              // 0: chosen by size, 1: the bound pass, 2: the screen's block sets
+    double wl_max;              // the screen's sets are taken when their rows x columns are at most this
 };
 
 __device__ __forceinline__ void atomic_max_pos(unsigned* addr, float v)
@@ -74,7 +74,12 @@ __global__ void k_delta_rows(const ScreenArgs S, float2* drow)
 {
     if (S.gate && !*S.gate) return;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
-    float amax = 0.f, asmax = 0.f;
+    if (S.item_active && r < S.nitems) S.item_active[r] = 0;  // k_screen marks the items it needs
+    float amax = 0.f, asmax = 0.f, bmax = 0.f, bsmax = 0.f;
+    if (r < S.n) {  // the columns' maxima too, so that k_delta has M for theta_skip
+        bmax = __double2float_ru(fabs(S.beta[r]));
+        bsmax = __double2float_ru(fabs(S.beta_s[r]));
+    }
     if (r < S.m) {
         const double al = S.alpha[r], as = S.alpha_s[r];
         const float du = __double2float_ru(__dsub_ru(al, as));
@@ -85,15 +90,31 @@ __global__ void k_delta_rows(const ScreenArgs S, float2* drow)
     for (int off = 16; off >= 1; off >>= 1) {
         amax = fmaxf(amax, __shfl_xor_sync(FULLMASK, amax, off));
         asmax = fmaxf(asmax, __shfl_xor_sync(FULLMASK, asmax, off));
+        bmax = fmaxf(bmax, __shfl_xor_sync(FULLMASK, bmax, off));
+        bsmax = fmaxf(bsmax, __shfl_xor_sync(FULLMASK, bsmax, off));
     }
     if ((threadIdx.x & 31) == 0) {
         atomic_max_pos(S.gmax + 0, amax);
+        atomic_max_pos(S.gmax + 1, bmax);
         atomic_max_pos(S.gmax + 2, asmax);
+        atomic_max_pos(S.gmax + 3, bsmax);
     }
 }
 
+// theta_skip_l = RD(theta - 2^-36 (sqrt(g) M + g theta)), FP64 round-to-nearest inside.
+__device__ __forceinline__ float theta_skip(const ScreenArgs& S, int g)
+{
+    const double M = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn((double)__uint_as_float(S.gmax[0]),
+                                                             (double)__uint_as_float(S.gmax[1])),
+                                                    (double)__uint_as_float(S.gmax[2])),
+                                           (double)__uint_as_float(S.gmax[3])),
+                                  (double)S.cmax);
+    const double tau = ldexp(__dadd_rn(__dmul_rn(__dsqrt_rn((double)g), M), __dmul_rn((double)g, S.theta)), -36);
+    return __double2float_rd(__dsub_rn(S.theta, tau));
+}
+
 // Blocks [0, ceil(L/8)) take one group per warp (the sums, from the rows'
-// FP32 values); the rest take columns.
+// FP32 values, and the group's theta_skip, once: FP64); the rest take columns.
 __global__ void k_delta(const ScreenArgs S, int group_blocks, const float2* drow)
 {
     if (S.gate && !*S.gate) return;
@@ -131,57 +152,26 @@ __global__ void k_delta(const ScreenArgs S, int group_blocks, const float2* drow
             S.gstat[4 * l + 0] = __fsqrt_ru(pu);
             S.gstat[4 * l + 1] = __fsqrt_rn(a2);
             S.gstat[4 * l + 2] = __fsqrt_rn(n2);
-            S.gstat[4 * l + 3] = 0.f;
+            S.gstat[4 * l + 3] = theta_skip(S, r1 - r0);  // (the maxima are complete: k_delta_rows)
         }
         return;
     }
     const int j = (blockIdx.x - group_blocks) * blockDim.x + threadIdx.x;
     if (j >= S.ntiles * TW) return;
-    float dbp = 0.f, dba = 0.f, dbn = 0.f, bmax = 0.f, bsmax = 0.f;
+    float dbp = 0.f, dba = 0.f, dbn = 0.f;
     if (j < S.n) {
         const double be = S.beta[j], bs = S.beta_s[j];
         dbp = fmaxf(__double2float_ru(__dsub_ru(be, bs)), 0.f);
         const float d = __double2float_rn(__dsub_rn(be, bs));
         dba = fabsf(d);
         dbn = fabsf(fminf(d, 0.f));
-        bmax = __double2float_ru(fabs(be));
-        bsmax = __double2float_ru(fabs(bs));
     }
     S.cstat[4 * j + 0] = dbp;
     S.cstat[4 * j + 1] = dba;
     S.cstat[4 * j + 2] = dbn;
     S.cstat[4 * j + 3] = 0.f;
-    for (int off = 16; off >= 1; off >>= 1) {
-        bmax = fmaxf(bmax, __shfl_xor_sync(FULLMASK, bmax, off));
-        bsmax = fmaxf(bsmax, __shfl_xor_sync(FULLMASK, bsmax, off));
-    }
-    if ((threadIdx.x & 31) == 0) {
-        atomic_max_pos(S.gmax + 1, bmax);
-        atomic_max_pos(S.gmax + 3, bsmax);
-    }
 }
 
-// theta_skip_l = RD(theta - 2^-36 (sqrt(g) M + g theta)), FP64 round-to-nearest inside.
-__device__ __forceinline__ float theta_skip(const ScreenArgs& S, int g)
-{
-    const double M = __dadd_rn(__dadd_rn(__dadd_rn(__dadd_rn((double)__uint_as_float(S.gmax[0]),
-                                                             (double)__uint_as_float(S.gmax[1])),
-                                                    (double)__uint_as_float(S.gmax[2])),
-                                           (double)__uint_as_float(S.gmax[3])),
-                                  (double)S.cmax);
-    const double tau = ldexp(__dadd_rn(__dmul_rn(__dsqrt_rn((double)g), M), __dmul_rn((double)g, S.theta)), -36);
-    return __double2float_rd(__dsub_rn(S.theta, tau));
-}
-
-// theta_skip of every group (it depends on g_l and on the maxima from
-// k_delta); also clears the item-active flags that k_screen sets.
-__global__ void k_theta(const ScreenArgs S)
-{
-    if (S.gate && !*S.gate) return;
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < S.L) S.gstat[4 * t + 3] = theta_skip(S, S.goff[t + 1] - S.goff[t]);
-    if (t < S.nitems) S.item_active[t] = 0;
-}
 
 // Alg. 2's skip test (Eq. 6, Lemma 2) for every block outside N.  A warp
 // takes the 32 units (l, 32-column tile) of one unit_need word, lane = column
@@ -280,12 +270,36 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
     }
 }
 
+// The route of a screened evaluation (the last block of k_wlist, which
+// recorded every needed unit
+// as a block set for the exact-sum kernels): when their rows x columns are few
+// (at most wl_max: then reading just those blocks from the transposed copy
+// costs less than a bound pass over every needed tile) the evaluation takes
+// them as they are and the bound pass and its kernels stand down (ctl->wl).
+// Otherwise the sets are dropped and the bound pass flags its own.  Either
+// way every block with s > 0 is formed by the same exact-sum kernels, so the
+// route changes no result.
+__device__ void pick_route(const ScreenArgs& S, EvalCtl* ctl, unsigned long long* fcount)
+{
+    const double w = (double)ctl->wl_work;
+    const bool wl = S.wl_build && (S.route == 2 || (S.route == 0 && w <= S.wl_max));
+    ctl->wl = wl ? 1 : 0;
+    if (wl) {
+        S.count[4] += (unsigned long long)(4.0 * w);  // the blocks' bytes of C
+        if (fcount) *fcount += ctl->wl_cols;
+    } else {
+        ctl->nxent = 0;
+        ctl->nxtall = 0;
+        ctl->ntcol = 0;
+    }
+}
+
 // Every needed unit (l, tile) as a block set for the exact-sum kernels: its
 // group's rows x the tile's columns the screen did not skip.  A warp per mask
 // word of a group, lane t for tile 32 w + t: one atomic per counter and warp
 // (warp scans give each lane its place), then every lane writes its own set
 // (and a taller class's column tasks).  Also sums the sets'
-// rows x columns for k_route.
+// rows x columns, and its last block picks the route.
 __global__ void __launch_bounds__(256) k_wlist(const ScreenArgs S, const EvalArgs E)
 {
     if (S.gate && !*S.gate) return;
@@ -348,29 +362,17 @@ __global__ void __launch_bounds__(256) k_wlist(const ScreenArgs S, const EvalArg
         atomicAdd(&E.ctl->wl_work, work);
         atomicAdd(&E.ctl->wl_cols, flagged);
     }
-}
-
-// The route of a screened evaluation.  k_wlist recorded every needed unit
-// as a block set for the exact-sum kernels; when their rows x columns are few
-// (at most wl_max: then reading just those blocks from the transposed copy
-// costs less than a bound pass over every needed tile) the evaluation takes
-// them as they are and the bound pass and its kernels stand down (ctl->wl).
-// Otherwise the sets are dropped and the bound pass flags its own.  Either
-// way every block with s > 0 is formed by the same exact-sum kernels, so the
-// route changes no result.
-__global__ void k_route(const ScreenArgs S, EvalCtl* ctl, unsigned long long* fcount)
-{
-    if (S.gate && !*S.gate) return;
-    const double w = (double)ctl->wl_work;
-    const bool wl = S.wl_build && (S.route == 2 || (S.route == 0 && w <= S.wl_max));
-    ctl->wl = wl ? 1 : 0;
-    if (wl) {
-        S.count[4] += (unsigned long long)(4.0 * w);  // the blocks' bytes of C
-        if (fcount) *fcount += ctl->wl_cols;
-    } else {
-        ctl->nxent = 0;
-        ctl->nxtall = 0;
-        ctl->ntcol = 0;
+    // the last block to finish picks the route (every block's sums are in)
+    __shared__ bool last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&E.ctl->wl_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        pick_route(S, E.ctl, E.fcount);
     }
 }
 
@@ -490,7 +492,8 @@ static void launch_delta(Handle* h, const double* beta)
     if (!h->eval_gate) cudaMemsetAsync(h->gmax, 0, sizeof(unsigned) * 4, h->st);  // else cleared by the trial gate
     const int gblocks = (h->L + 7) / 8;
     const int cblocks = (h->ntiles * TW + 255) / 256;
-    k_delta_rows<<<(unsigned)((h->m + 255) / 256), 256, 0, h->st>>>(s, h->drow);
+    const int64_t nt = std::max<int64_t>(std::max<int64_t>(h->m, h->n), h->hp.nitems());
+    k_delta_rows<<<(unsigned)((nt + 255) / 256), 256, 0, h->st>>>(s, h->drow);
     k_delta<<<gblocks + cblocks, 256, 0, h->st>>>(s, gblocks, h->drow);
 }
 
@@ -540,21 +543,20 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     s.wl_build = e.use_ct && dbg_route != 1;
     s.route = (int32_t)dbg_route;
     s.wl_max = WL_FRACTION * (double)m * (double)n;
-    k_theta<<<(std::max<int>(L, hp.nitems()) + 255) / 256, 256, 0, st>>>(s);
     const int64_t tasks = (int64_t)L * unit_words;
     const int sblocks = (int)std::min<int64_t>((tasks + SCREEN_WARPS - 1) / SCREEN_WARPS, 16LL * n_sm);
     k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s);
+    // (without the block sets the control word's zero route is the bound pass)
     if (s.wl_build)
         k_wlist<<<(unsigned)std::min<int64_t>((tasks * 32 + 255) / 256, 8LL * n_sm), 256, 0, st>>>(s, e);
-    k_route<<<1, 1, 0, st>>>(s, ctl, fcount);
-    launch_stage_masks(e, st);
+    launch_stage_masks(e, n_sm, st);
     const int nk = eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     if (!eval_gate) {
         count_screened_evals(1);
-        // and deltas (2), theta, screen, block sets, route, stage masks, reduction
-        stats_host.kernels += nk + 7 + (s.wl_build ? 1 : 0);
+        // and deltas (2), screen, block sets, stage masks, reduction
+        stats_host.kernels += nk + 5 + (s.wl_build ? 1 : 0);
     }
     return ck(cudaGetLastError(), "screened eval launch");
 }

@@ -476,7 +476,7 @@ template <bool SNAP>
 __global__ void __launch_bounds__(THREADS, CTAS_PER_SM) k_stream(const __grid_constant__ EvalArgs A)
 {
     if (A.gate && !*A.gate) return;  // a skipped solver trial
-    if (A.ctl->wl) return;           // screened, and the screen's block sets are the work (k_route)
+    if (A.ctl->wl) return;           // screened, and the screen's block sets are the work
     extern __shared__ unsigned char smem_raw[];
     // TMA destinations must be 128-byte aligned: align the layout to 1 KB
     Smem& S = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -786,33 +786,37 @@ __global__ void __launch_bounds__(256) k_stage_masks(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
     if (A.ctl->wl) return;
-    const ItemDesc d = A.desc[blockIdx.x];
-    if (A.item_active && !A.item_active[d.item]) return;
-    const int tile0 = d.col0 / TW;  // a multiple of NWARPS: the item's tiles share one mask word
-    uint8_t* out = const_cast<uint8_t*>(A.stage_m8) + (int64_t)d.sbase * SR;
-    // a warp's 32 entries are one stage's rows (SR == 32): the stage's bit in
-    // stage_need is set when some row is needed, else cleared
-    for (int q = threadIdx.x; q < d.nst * SR; q += blockDim.x) {
-        const int st = q / SR, i = q % SR;
-        const int ra = A.stage_row0[d.st0 + st], re = A.stage_row0[d.st0 + st + 1];
-        uint32_t m8 = 0u;
-        if (ra + i < re) {
-            const int l = A.rowg[ra + i].x;
-            m8 = (A.unit_need[(int64_t)l * A.unit_words + (tile0 >> 5)] >> (tile0 & 31)) & 0xffu;
-        }
-        out[q] = (uint8_t)m8;
-        const bool any = __ballot_sync(FULLMASK, m8 != 0u) != 0u;
-        if ((threadIdx.x & 31) == 0) {
-            const int gs = d.sbase + st;
-            if (any) atomicOr(A.stage_need + (gs >> 5), 1u << (gs & 31));
-            else atomicAnd(A.stage_need + (gs >> 5), ~(1u << (gs & 31)));
+    for (int it = blockIdx.x; it < A.nlist; it += gridDim.x) {
+        const ItemDesc d = A.desc[it];
+        if (A.item_active && !A.item_active[d.item]) continue;  // (uniform)
+        const int tile0 = d.col0 / TW;  // a multiple of NWARPS: the item's tiles share one mask word
+        uint8_t* out = const_cast<uint8_t*>(A.stage_m8) + (int64_t)d.sbase * SR;
+        // a warp's 32 entries are one stage's rows (SR == 32): the stage's bit in
+        // stage_need is set when some row is needed, else cleared
+        for (int q = threadIdx.x; q < d.nst * SR; q += blockDim.x) {
+            const int st = q / SR, i = q % SR;
+            const int ra = A.stage_row0[d.st0 + st], re = A.stage_row0[d.st0 + st + 1];
+            uint32_t m8 = 0u;
+            if (ra + i < re) {
+                const int l = A.rowg[ra + i].x;
+                m8 = (A.unit_need[(int64_t)l * A.unit_words + (tile0 >> 5)] >> (tile0 & 31)) & 0xffu;
+            }
+            out[q] = (uint8_t)m8;
+            const bool any = __ballot_sync(FULLMASK, m8 != 0u) != 0u;
+            if ((threadIdx.x & 31) == 0) {
+                const int gs = d.sbase + st;
+                if (any) atomicOr(A.stage_need + (gs >> 5), 1u << (gs & 31));
+                else atomicAnd(A.stage_need + (gs >> 5), ~(1u << (gs & 31)));
+            }
         }
     }
 }
 
-void launch_stage_masks(const EvalArgs& a, cudaStream_t st)
+void launch_stage_masks(const EvalArgs& a, int n_sm, cudaStream_t st)
 {
-    k_stage_masks<<<a.nlist, 256, 0, st>>>(a);
+    // a grid of a few CTAs per SM: when the screen took the block-set route
+    // the kernel returns at once, and few CTAs return sooner than thousands
+    k_stage_masks<<<std::min(a.nlist, 4 * n_sm), 256, 0, st>>>(a);
 }
 
 // ========================================================== split finish
@@ -849,9 +853,13 @@ __global__ void __launch_bounds__(NWARPS * 32) k_split_finish(const EvalArgs A)
     }
 }
 
+// (a screened evaluation on the block-set route returns from it at once: a
+// grid of hundreds of CTAs, not thousands, keeps that short)
+constexpr int SPLIT_FINISH_CTAS = 608;
+
 void launch_split_finish(const EvalArgs& a, cudaStream_t st)
 {
-    if (a.nsets > 0) k_split_finish<<<a.nsets < 4096 ? a.nsets : 4096, NWARPS * 32, 0, st>>>(a);
+    if (a.nsets > 0) k_split_finish<<<a.nsets < SPLIT_FINISH_CTAS ? a.nsets : SPLIT_FINISH_CTAS, NWARPS * 32, 0, st>>>(a);
 }
 
 // ============================================================ exact sums
