@@ -811,6 +811,46 @@ def case_report(args, dev):
     return out
 
 
+def grid_report(args, dev):
+    """The mid workload (m = n = 4000, 100 Dirichlet(2) classes, d = 256)
+    over gamma in {0.1, 1, 10} x mu in {0.01, 0.1, 1}, screening off and on:
+    for each pair a dense solve from zero to stagnation (ftol 1e-14) gives D*
+    and the dense time to a relative objective error of 1e-6 (from its
+    device-time trace); a screened solve (Alg. 1) runs to the same iteration
+    and must visit the same iterates bit for bit."""
+    import torch
+    import paper_2303_07597_gb300 as pk
+    p, C, _ = _make_workload("mid", args.seed, str(dev))
+    a = torch.from_numpy(p.a).to(dev)
+    b = torch.from_numpy(p.b).to(dev)
+    lab = torch.from_numpy(p.labels).to(dev)
+    rows = []
+    for gamma in [0.1, 1.0, 10.0]:
+        for mu in [0.01, 0.1, 1.0]:
+            ref = pk.GroupSparseOT(C, a, b, lab, p.L, gamma, mu)
+            ref.set_params(use_screening=0, ftol=1e-14)
+            ref.solve(0.0, args.grid_iters)
+            D, t, ev = ref.trace()
+            ref.close()
+            Dstar = float(D[-1])
+            hit = np.nonzero(np.abs(D - Dstar) <= 1e-6 * abs(Dstar))[0]
+            k = int(hit[0]) if len(hit) else -1
+            row = {"gamma": gamma, "mu": mu, "D_star": Dstar, "D_star_iters": int(len(D) - 1), "iters_to_1e-6": k}
+            if k > 0:
+                scr = pk.GroupSparseOT(C, a, b, lab, p.L, gamma, mu)
+                scr.set_params(use_screening=1, ftol=0.0)
+                scr.solve(0.0, k)
+                Ds, ts, evs = scr.trace()
+                st = scr.stats()
+                scr.close()
+                row.update(dense_ms=float(t[k]), screened_ms=float(ts[k]),
+                           screened_vs_dense=float(t[k]) / float(ts[k]),
+                           same_iterates=bool(len(Ds) > k and np.array_equal(Ds[:k + 1], D[:k + 1])),
+                           blocks_skipped_frac=st["blocks_skipped"] / max(1, st["blocks_total"]))
+            rows.append(row)
+    return {"workload": "mid: m=n=4000, L=100 (Dirichlet(2) sizes), d=256, from zero", "unit": "ms", "rows": rows}
+
+
 def sweep_report(args, dev):
     """Paper-shaped trends (Sec. 5, synthetic set with controlled classes):
     time of the screened solver (Alg. 1, with the set N) against the dense
@@ -1061,6 +1101,9 @@ def main():
     ap.add_argument("--warm-passes", type=int, default=1, choices=[1, 2],
                     help="2: also a second network on the second-pass inputs (water levels against the first "
                          "prediction), solved from its prediction as well")
+    ap.add_argument("--grid", action="store_true",
+                    help="only the mid workload over the (gamma, mu) grid, dense and screened time to 1e-6")
+    ap.add_argument("--grid-iters", type=int, default=30000)
     ap.add_argument("--sweep", action="store_true",
                     help="only the paper-shaped trends (screened vs dense over classes, class sizes, lower bound)")
     ap.add_argument("--sweep-classes", default="10,40,160,640,1280")
@@ -1084,6 +1127,11 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps(case_report(args, torch.device("cuda", 0))))
+        return 0
+    if args.grid:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"grid": grid_report(args, torch.device("cuda", 0))}))
         return 0
     if args.sweep:
         import torch
