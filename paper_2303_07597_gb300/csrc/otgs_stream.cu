@@ -1327,13 +1327,45 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
         const FxScale& fx = A.pfx ? A.pfx[E.prob] : fx1;
         if (lane == 0) hold_psi(A, E.prob, pprob, ph, pl);
         const float* ct0 = pd.CT + (int64_t)(E.colg0 - pd.coff) * pd.ldct - pd.roff;  // + k ldct + R
+        // the set's rows (at most XTALL_ROWS = 32 XTC_UNROLL): their records once, and
+        // each column's values loaded one column ahead of its sums
+        float4 a[XTC_UNROLL];
+#pragma unroll
+        for (int u = 0; u < XTC_UNROLL; u++) {
+            const int R = E.gstart + 32 * u + lane;
+            a[u] = R < E.gend ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+        }
+        auto load_col = [&](int k, float (&c)[XTC_UNROLL]) {
+            const float* col = ct0 + (int64_t)k * pd.ldct;
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++) {
+                const int R = E.gstart + 32 * u + lane;
+                c[u] = R < E.gend ? __ldg(col + R) : 0.f;
+            }
+        };
         float sk = 0.f;  // lane k: s of column k
         uint32_t rem = E.mask;
+        float cn[XTC_UNROLL];
+        if (rem) load_col(__ffs(rem) - 1, cn);
         while (rem) {
             const int k = __ffs(rem) - 1;
             rem &= rem - 1u;
+            float c[XTC_UNROLL];
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++) c[u] = cn[u];
+            if (rem) load_col(__ffs(rem) - 1, cn);
             const float2 b2 = __ldg(A.B2 + pd.bcoff + E.colg0 + k - pd.coff);
-            const Acc T = slice_sums(A, ct0 + (int64_t)k * pd.ldct, E.gstart, E.gend, bound_up(b2.x), b2.x, b2.y, lane);
+            const float bp = bound_up(b2.x);
+            Acc T = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++)
+                if (maybe_pos(a[u].z, c[u], bp)) {
+                    float fh, fl;
+                    f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
+                    if (fh > 0.f) acc_p(fh, fl, T);
+                }
+            warp_df_sum(T.Sh, T.Sl);
+            warp_df_sum(T.Ph, T.Pl);
             float s = 0.f;
             if (lane == 0) s = finish_block_exact(A, fx, T, E.l, E.colg0 + k, ph, pl);
             s = __shfl_sync(FULLMASK, s, 0);
@@ -1344,22 +1376,17 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
         unsigned long long tq[XTC_UNROLL];
 #pragma unroll
         for (int u = 0; u < XTC_UNROLL; u++) tq[u] = 0ull;
+        load_col(__ffs(srem) - 1, cn);
         while (srem) {
             const int k = __ffs(srem) - 1;
             srem &= srem - 1u;
+            float c[XTC_UNROLL];
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++) c[u] = cn[u];
+            if (srem) load_col(__ffs(srem) - 1, cn);
             const float s = __shfl_sync(FULLMASK, sk, k);
             const float2 b2 = __ldg(A.B2 + pd.bcoff + E.colg0 + k - pd.coff);
             const float bp = bound_up(b2.x);
-            const float* col = ct0 + (int64_t)k * pd.ldct;
-            float c[XTC_UNROLL];
-            float4 a[XTC_UNROLL];  // (the rows' records again: in L1)
-#pragma unroll
-            for (int u = 0; u < XTC_UNROLL; u++) {
-                const int R = E.gstart + 32 * u + lane;
-                const bool in = R < E.gend;
-                a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
-                c[u] = in ? __ldg(col + R) : 0.f;
-            }
 #pragma unroll
             for (int u = 0; u < XTC_UNROLL; u++)
                 if (maybe_pos(a[u].z, c[u], bp)) {
