@@ -88,7 +88,7 @@ struct Handle {
     uint32_t* stage_need = nullptr; // [ceil(nstages / 32)]: stages with a needed row
     float* gstat = nullptr;       // per group: npos, nabs, nneg, theta_skip
     float2* drow = nullptr;       // per sorted row: RU([alpha - alpha~]_+), RN(alpha - alpha~) as FP32
-    float* cstat = nullptr;       // per column: dbp, dbabs, dbneg
+    float* cstat = nullptr;       // per column: dbp, dbabs, dbneg (an array each)
     unsigned* gmax = nullptr;     // float bits: max|alpha|, max|beta|, max|alpha~|, max|beta~|
     unsigned long long* dcount = nullptr; // device counters: in_N, checked, skipped, units
     float* sg_ru = nullptr;       // sqrt(g_l) rounded up

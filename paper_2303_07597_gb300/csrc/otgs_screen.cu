@@ -41,7 +41,7 @@ struct ScreenArgs {
     const float* sg_ru;      // RU(sqrt(g_l))
     const float* sg_rn;      // RN(sqrt(g_l))
     float* gstat;            // [L][4]: npos (RU), nabs, nneg (RN)
-    float* cstat;            // [ntiles*TW][4]: dbp (RU), |dbeta|, |[dbeta]_-| (RN)
+    float* cstat;            // [3][ntiles*TW]: dbp (RU), |dbeta|, |[dbeta]_-| (RN), one array each
     unsigned* gmax;          // [4] float bits, zeroed before the delta kernel
     float cmax;
     double theta;
@@ -166,10 +166,10 @@ __global__ void k_delta(const ScreenArgs S, int group_blocks, const float2* drow
         dba = fabsf(d);
         dbn = fabsf(fminf(d, 0.f));
     }
-    S.cstat[4 * j + 0] = dbp;
-    S.cstat[4 * j + 1] = dba;
-    S.cstat[4 * j + 2] = dbn;
-    S.cstat[4 * j + 3] = 0.f;
+    const int ldz = S.ntiles * TW;
+    S.cstat[j] = dbp;
+    S.cstat[ldz + j] = dba;
+    S.cstat[2 * ldz + j] = dbn;
 }
 
 
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
                 const int j = jt * TW + lane;
                 const bool ok = jt < jt1 && j < S.n && g > 0;
                 zv[q] = ok ? __ldg(S.zt + (int64_t)l * S.ntiles * TW + j) : 0.f;
-                dv[q] = ok ? __ldg(S.cstat + 4 * j) : 0.f;
+                dv[q] = ok ? __ldg(S.cstat + j) : 0.f;
                 Nv[q] = jt < jt1 ? __ldg(S.Nmask + (int64_t)l * S.ntiles + jt) : 0u;
             }
 #pragma unroll
@@ -392,10 +392,10 @@ __global__ void k_build_N(const ScreenArgs S)
         const float kt = __fsqrt_rn(__fadd_rn(__fmul_rn(z, z), __fmul_rn(o, o)));
         const float sg = S.sg_rn[l];
         float zl = __fsub_rn(kt, S.gstat[4 * l + 1]);
-        zl = __fsub_rn(zl, __fmul_rn(sg, S.cstat[4 * j + 1]));
+        zl = __fsub_rn(zl, __fmul_rn(sg, S.cstat[S.ntiles * TW + j]));
         zl = __fsub_rn(zl, o);
         zl = __fsub_rn(zl, S.gstat[4 * l + 2]);
-        zl = __fsub_rn(zl, __fmul_rn(sg, S.cstat[4 * j + 2]));
+        zl = __fsub_rn(zl, __fmul_rn(sg, S.cstat[2 * S.ntiles * TW + j]));
         inN = zl > S.theta_f;
     }
     const uint32_t w = __ballot_sync(FULLMASK, inN);
