@@ -705,6 +705,12 @@ def warm_report(args, dev):
                                      float(warm["t_ms"].max())],
         "heldout_rmse_mean": float(np.mean(rmse)),
         "warm_vs_cold": cold_ms / ((t2 - t0) * 1000.0),
+        # per problem: the median problem's time to the target, cold over warm
+        # (the warm one including the preparation), and the slowest problem's
+        # iterations if each problem took the better of its two starts
+        "warm_vs_cold_median_problem": float(np.percentile(cold["t_ms"], 50))
+        / (float(np.percentile(warm["t_ms"], 50)) + (t1 - t0) * 1000.0),
+        "min_of_starts_iters_max": int(np.max(np.minimum(cold["iters"], warm["iters"]))),
     })
     return out
 
