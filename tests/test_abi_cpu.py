@@ -70,8 +70,8 @@ ITEM_COLS, STAGE_ROWS = 256, 32
 
 
 def panel_height(m, n):
-    """m * ceil(n / 256) / 2048 rows, clamped to [32, 512]."""
-    return min(512, max(32, -(-m * -(-n // ITEM_COLS) // 2048)))
+    """m * ceil(n / 256) / 2048 rows, clamped to [32, 128]."""
+    return min(128, max(32, -(-m * -(-n // ITEM_COLS) // 2048)))
 
 
 SPLIT_ROWS = 256
@@ -152,8 +152,8 @@ def test_plan_zipf_large_shape():
     info = pk.ot_gs_plan_info(lab, 20000, 1000)
     n_panels, n_items, n_stages, _ = expected_plan(list(sizes), 20000)
     assert (info["n_panels"], info["n_items"], info["n_stages"]) == (n_panels, n_items, n_stages)
-    assert panel_height(20000, 20000) == 512
-    assert int((np.asarray(sizes) > 512).sum()) < info["n_panels"] < 200
+    assert panel_height(20000, 20000) == 128
+    assert int((np.asarray(sizes) > 128).sum()) < info["n_panels"] < 200
     # streaming one evaluation touches every row once per column chunk, in
     # 32-row stages: at most one partial stage per panel and chunk
     nch = -(-20000 // ITEM_COLS)
@@ -171,7 +171,7 @@ def expected_plan_batch(sizes_list, ns, panel_rows=0, split_rows=0, fill=0):
     the default panel height comes from the (row, column chunk) pairs summed
     over the problems."""
     pairs = sum(int(np.sum(s)) * -(-n // ITEM_COLS) for s, n in zip(sizes_list, ns))
-    pr = panel_rows or min(512, max(32, -(-pairs // 2048)))
+    pr = panel_rows or min(128, max(32, -(-pairs // 2048)))
     sr = split_rows or SPLIT_ROWS
     n_panels = n_items = n_stages = 0
     for sizes, n in zip(sizes_list, ns):
