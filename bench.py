@@ -339,17 +339,27 @@ def _stream_timed(h, fn, k, stream):
 
 
 def screened_needed_bytes(skip_mask, sizes, n, L):
-    """Bytes one screened evaluation (Alg. 2) must read at least: C of every
-    block (l, j) it does not skip (g_l rows x 4 bytes), the snapshot's
-    z~ and o~ of every block (FP32 each), alpha and beta.  skip_mask: L x
-    ceil(n/32) words, bit j % 32 of word (l, j / 32) set when block (l, j) is
-    skipped; sizes: rows per class."""
+    """Bytes one screened evaluation (Alg. 2 with the tile-level test) must
+    read at least: C of every block (l, j) it does not skip (g_l rows x 4
+    bytes); per unit (class, 32-column tile) the tile's largest z~ and its
+    word of N (4 bytes each); z~ (4 bytes) of every column of the units that
+    hold a block it does not skip (the tile test cannot pass there); alpha,
+    beta and their snapshot values (FP64).  skip_mask: L x ceil(n/32) words,
+    bit j % 32 of word (l, j / 32) set when block (l, j) is skipped; sizes:
+    rows per class (an empty class needs nothing)."""
     words = np.asarray(skip_mask, dtype=np.uint32).reshape(L, -1)
+    ntiles = words.shape[1]
     bits = np.unpackbits(words.view(np.uint8), bitorder="little").reshape(L, -1)[:, :n]
+    sizes = np.asarray(sizes, dtype=np.int64)
     skipped = bits.sum(axis=1).astype(np.int64)
-    c_needed = int(np.sum(np.asarray(sizes, dtype=np.int64) * (n - skipped))) * 4
+    c_needed = int(np.sum(sizes * (n - skipped))) * 4
+    pad = np.ones((L, ntiles * 32), dtype=np.uint8)
+    pad[:, :n] = bits
+    unit_open = (pad.reshape(L, ntiles, 32) == 0).any(axis=2) & (sizes > 0)[:, None]
+    tile_cols = np.minimum(32, n - 32 * np.arange(ntiles))
+    z_bytes = 4 * int(np.sum(unit_open * tile_cols[None, :]))
     m = int(np.sum(sizes))
-    return c_needed + 8 * L * n + 8 * (m + n), c_needed, int(skipped.sum())
+    return c_needed + z_bytes + 8 * L * ntiles + 16 * (m + n), c_needed, int(skipped.sum())
 
 
 def solve_report(args, dev):

@@ -513,9 +513,10 @@ bool Handle::eval_dense_core(const double* beta, double* out_caller, double* G_s
     const int nk = eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(nullptr, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
+    if (snap && !zt_tiles()) return false;  // z~ is complete: its tile maxima
     if (!eval_gate) {
         count_dense_evals(1);
-        stats_host.kernels += nk + 1;  // and the reduction
+        stats_host.kernels += nk + 1 + (snap ? 1 : 0);  // and the reduction, the tile maxima
     }
     return ck(cudaGetLastError(), "eval launch");
 }

@@ -77,6 +77,7 @@ struct Handle {
     bool screen_alloc = false;
     bool snap_valid = false;      // zt/ot/alpha_snap/beta_snap describe a snapshot
     float* zt = nullptr;          // z~ (rounded up), L x ntiles*TW
+    float* zt_tile = nullptr;     // L x ntiles: the largest z~ of each 32-column tile (+inf with a NaN)
     float* ot = nullptr;          // o~, L x ntiles*TW
     double* alpha_snap = nullptr; // sorted
     double* beta_snap = nullptr;
@@ -88,7 +89,7 @@ struct Handle {
     uint32_t* stage_need = nullptr; // [ceil(nstages / 32)]: stages with a needed row
     float* gstat = nullptr;       // per group: npos, nabs, nneg, theta_skip
     float2* drow = nullptr;       // per sorted row: RU([alpha - alpha~]_+), RN(alpha - alpha~) as FP32
-    float* cstat = nullptr;       // per column: dbp, dbabs, dbneg (an array each)
+    float* cstat = nullptr;       // per column: dbp, dbabs, dbneg (an array each); per tile: max dbp
     unsigned* gmax = nullptr;     // float bits: max|alpha|, max|beta|, max|alpha~|, max|beta~|
     unsigned long long* dcount = nullptr; // device counters: in_N, checked, skipped, units
     float* sg_ru = nullptr;       // sqrt(g_l) rounded up
@@ -141,6 +142,7 @@ struct Handle {
     bool ensure_screen();
     bool zero_snapshot();
     void invalidate_screen() { snap_valid = false; }
+    bool zt_tiles();  // zt_tile from zt (after every write of zt)
     bool snapshot_at(const double* alpha, bool alpha_sorted, const double* beta, bool build_N,
                      double* out_caller, double* G_sorted, const double* dir);
     bool eval_screened(const double* alpha, bool alpha_sorted, const double* beta, double* out_caller,

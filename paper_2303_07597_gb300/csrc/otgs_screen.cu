@@ -13,6 +13,11 @@
 //    max|alpha~| + max|beta~| + max c.  tau_l exceeds the rounding error of
 //    the evaluation kernel's z (double-float f and S), so a skipped block also
 //    evaluates to exactly zero there and screened == dense bit for bit.
+//    The screen first applies the same formula to a whole 32-column tile with
+//    the tile's largest z~ (formed once per snapshot) and largest dbp: every
+//    step rounds up, so the tile's zbar bounds each column's, and a tile that
+//    passes skips its columns outside N with no per-column read.  Only the
+//    other tiles read z~ column by column; the skip decisions are the same.
 //  * lower bound (Def. 2, Eq. 7), round-to-nearest (N only decides which
 //    blocks are computed without a check, never a result):
 //      zlow = k~ - ||dalpha_[l]|| - sqrt(g_l)|dbeta_j| - o~ - ||[dalpha_[l]]_-|| - sqrt(g_l)|[dbeta_j]_-|
@@ -37,11 +42,13 @@ struct ScreenArgs {
     const double* beta;
     const double* beta_s;
     const float* zt;         // L x ntiles*TW
+    const float* zt_tile;    // L x ntiles: max of zt over each tile's columns (+inf with a NaN)
     const float* ot;
     const float* sg_ru;      // RU(sqrt(g_l))
     const float* sg_rn;      // RN(sqrt(g_l))
     float* gstat;            // [L][4]: npos (RU), nabs, nneg (RN)
-    float* cstat;            // [3][ntiles*TW]: dbp (RU), |dbeta|, |[dbeta]_-| (RN), one array each
+    float* cstat;            // [3][ntiles*TW]: dbp (RU), |dbeta|, |[dbeta]_-| (RN), one array each;
+                             // then [ntiles]: the largest dbp of each tile
     unsigned* gmax;          // [4] float bits, zeroed before the delta kernel
     float cmax;
     double theta;
@@ -170,6 +177,28 @@ __global__ void k_delta(const ScreenArgs S, int group_blocks, const float2* drow
     S.cstat[j] = dbp;
     S.cstat[ldz + j] = dba;
     S.cstat[2 * ldz + j] = dbn;
+    // a warp holds one tile's columns (whole warps return above): the tile's largest dbp
+    float tm = dbp;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) tm = fmaxf(tm, __shfl_xor_sync(FULLMASK, tm, off));
+    if ((threadIdx.x & 31) == 0) S.cstat[3 * ldz + (j >> 5)] = tm;
+}
+
+// After a snapshot: per unit (group l, tile jt) the largest z~ over the
+// tile's columns (columns past n count as 0; a NaN makes it +inf), for the
+// screen's tile-level test.  One warp per unit.
+__global__ void k_zt_tiles(const float* zt, float* zt_tile, int64_t units, int ntiles, int n, const int* gate)
+{
+    if (gate && !*gate) return;
+    const int64_t u = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (u >= units) return;
+    const int lane = threadIdx.x & 31;
+    const int j = (int)(u % ntiles) * TW + lane;
+    float z = j < n ? zt[u * TW + lane] : 0.f;
+    if (z != z) z = INFINITY;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) z = fmaxf(z, __shfl_xor_sync(FULLMASK, z, off));
+    if (lane == 0) zt_tile[u] = z;
 }
 
 
@@ -194,47 +223,57 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
         const int g = S.goff[l + 1] - S.goff[l];
         const float th = S.gstat[4 * l + 3], npos = S.gstat[4 * l], sg = S.sg_ru[l];
         const int jt1 = min(32 * w + 32, S.ntiles);
-        // lane t keeps the ballots of tile 32 w + t
-        uint32_t my_skip = 0u, my_need = 0u, my_valid = 0u, my_N = 0u;
-        // tiles in batches of SCREEN_TB, their loads issued together
-        for (int jb = 32 * w; jb < jt1; jb += SCREEN_TB) {
+        const int ldz = S.ntiles * TW;
+        // lane t: tile jt = 32 w + t; its word of N, its existing columns (none
+        // in an empty group) and the tile-level test: with z~max and dbpmax the
+        // tile's largest z~ and dbp, RU((z~max + npos) + sg dbpmax) <= theta_skip
+        // implies the block test below for each of its columns (every operation
+        // rounds up, so the bound grows with each operand), so the tile's skip
+        // word is then its columns outside N without reading their z~
+        const int jt = 32 * w + lane;
+        const bool tv = jt < jt1;
+        const int64_t tq = (int64_t)l * S.ntiles + jt;
+        const uint32_t my_N = tv ? __ldg(S.Nmask + tq) : 0u;
+        const int cols = min(TW, S.n - jt * TW);
+        const uint32_t my_valid = (tv && g > 0) ? (cols >= TW ? FULLMASK : (1u << cols) - 1u) : 0u;
+        bool pass = false;
+        if (my_valid) {
+            const float zb = __fadd_ru(__fadd_ru(__ldg(S.zt_tile + tq), npos), __fmul_ru(sg, __ldg(S.cstat + 3 * ldz + jt)));
+            pass = zb <= th;
+        }
+        uint32_t my_skip = pass ? my_valid & ~my_N : 0u;
+        // the other tiles column by column (Eq. 6), lane = column, SCREEN_TB
+        // tiles' loads issued together
+        uint32_t todo = __ballot_sync(FULLMASK, my_valid != 0u && !pass);
+        while (todo) {
+            int tl[SCREEN_TB];
             float zv[SCREEN_TB], dv[SCREEN_TB];
-            uint32_t Nv[SCREEN_TB];
 #pragma unroll
             for (int q = 0; q < SCREEN_TB; q++) {
-                const int jt = jb + q;
-                const int j = jt * TW + lane;
-                const bool ok = jt < jt1 && j < S.n && g > 0;
-                zv[q] = ok ? __ldg(S.zt + (int64_t)l * S.ntiles * TW + j) : 0.f;
+                tl[q] = todo ? __ffs(todo) - 1 : -1;
+                todo &= todo - 1u;
+                const int j = (32 * w + tl[q]) * TW + lane;
+                const bool ok = tl[q] >= 0 && j < S.n;
+                zv[q] = ok ? __ldg(S.zt + (int64_t)l * ldz + j) : 0.f;
                 dv[q] = ok ? __ldg(S.cstat + j) : 0.f;
-                Nv[q] = jt < jt1 ? __ldg(S.Nmask + (int64_t)l * S.ntiles + jt) : 0u;
             }
 #pragma unroll
             for (int q = 0; q < SCREEN_TB; q++) {
-                const int jt = jb + q;
-                if (jt >= jt1) break;  // (uniform)
-                const int j = jt * TW + lane;
-                const bool valid = j < S.n && g > 0;
-                const bool inN = valid && ((Nv[q] >> lane) & 1u);
+                if (tl[q] < 0) break;  // (uniform)
+                const uint32_t Nv = __shfl_sync(FULLMASK, my_N, tl[q]);
+                const int j = (32 * w + tl[q]) * TW + lane;
                 bool skip = false;
-                if (valid && !inN) {
+                if (j < S.n && !((Nv >> lane) & 1u)) {
                     const float zbar = __fadd_ru(__fadd_ru(zv[q], npos), __fmul_ru(sg, dv[q]));
                     skip = zbar <= th;
                 }
                 const uint32_t skipw = __ballot_sync(FULLMASK, skip);
-                const uint32_t needw = __ballot_sync(FULLMASK, valid && !skip);
-                const uint32_t validw = __ballot_sync(FULLMASK, valid);
-                if (lane == (jt & 31)) {
-                    my_skip = skipw;
-                    my_need = needw;
-                    my_valid = validw;
-                    my_N = Nv[q];
-                }
+                if (lane == tl[q]) my_skip = skipw;
             }
         }
+        const uint32_t my_need = my_valid & ~my_skip;
         // every lane its own tile: the skip word, the items that hold it, the statistics
-        const int jt = 32 * w + lane;
-        if (jt < jt1) {
+        if (tv) {
             S.skipmask[(int64_t)l * S.ntiles + jt] = my_skip;
             if (my_need) {
                 // the item of (l, tile) in every piece of the group (same value from every writer)
@@ -411,7 +450,7 @@ ScreenArgs make_screen_args(Handle* h)
     s.goff = h->dp.goff;
     s.alpha = h->alpha_eval; s.alpha_s = h->alpha_snap;
     s.beta = nullptr; s.beta_s = h->beta_snap;
-    s.zt = h->zt; s.ot = h->ot;
+    s.zt = h->zt; s.ot = h->ot; s.zt_tile = h->zt_tile;
     s.sg_ru = h->sg_ru; s.sg_rn = h->sg_rn;
     s.gstat = h->gstat; s.cstat = h->cstat; s.gmax = h->gmax;
     s.cmax = h->cmax;
@@ -430,6 +469,7 @@ bool Handle::ensure_screen()
     if (screen_alloc) return true;
     const size_t ldz = (size_t)ntiles * TW;
     zt = (float*)dalloc(sizeof(float) * (size_t)L * ldz, "zt");
+    zt_tile = (float*)dalloc(sizeof(float) * (size_t)L * ntiles, "zt_tile");
     ot = (float*)dalloc(sizeof(float) * (size_t)L * ldz, "ot");
     alpha_snap = (double*)dalloc(sizeof(double) * m, "alpha_snap");
     beta_snap = (double*)dalloc(sizeof(double) * n, "beta_snap");
@@ -446,7 +486,7 @@ bool Handle::ensure_screen()
     cstat = (float*)dalloc(sizeof(float) * 4 * ldz, "cstat");
     gmax = (unsigned*)dalloc(sizeof(unsigned) * 8, "gmax");
     dcount = (unsigned long long*)dalloc(sizeof(unsigned long long) * 8, "dcount");
-    if (!zt || !ot || !alpha_snap || !beta_snap || !Nmask || !skipmask || !unit_need || !item_active || !gstat ||
+    if (!zt || !zt_tile || !ot || !alpha_snap || !beta_snap || !Nmask || !skipmask || !unit_need || !item_active || !gstat ||
         !cstat || !gmax || !dcount)
         return false;
     std::vector<float> ru(L), rn(L);
@@ -470,6 +510,14 @@ bool Handle::ensure_screen()
     if (!ck(cudaStreamSynchronize(st), "screen alloc sync")) return false;
     screen_alloc = true;
     return true;
+}
+
+// The tile maxima of z~ (k_screen's tile-level test) from the current z~.
+bool Handle::zt_tiles()
+{
+    const int64_t units = (int64_t)L * ntiles;
+    k_zt_tiles<<<(unsigned)((units + 7) / 8), 256, 0, st>>>(zt, zt_tile, units, ntiles, (int)n, eval_gate);
+    return ck(cudaGetLastError(), "zt tiles launch");
 }
 
 // As Alg. 1 starts: the first snapshot is taken at alpha~ = beta~ = 0 with N empty.

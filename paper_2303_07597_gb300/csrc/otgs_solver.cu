@@ -606,7 +606,7 @@ int ot_gs_restore_state(ot_gs* hh, const void* src, int64_t bytes)
     if (hd.has_snap) {
         if (!h->ensure_screen()) return h->last_code;
         ok = cp(h->zt, o.zt, 4 * lz) && cp(h->ot, o.ot, 4 * lz) && cp(h->alpha_snap, o.as, 8 * (size_t)h->m) &&
-             cp(h->beta_snap, o.bs, 8 * (size_t)h->n) && cp(h->Nmask, o.Nm, 4 * lu);
+             cp(h->beta_snap, o.bs, 8 * (size_t)h->n) && cp(h->Nmask, o.Nm, 4 * lu) && h->zt_tiles();
         if (!ok) return h->last_code;
         h->snap_valid = true;
     } else {

@@ -93,9 +93,10 @@ def test_clock_summary_keeps_the_samples_inside_the_timed_region():
 
 
 def test_screened_needed_bytes_counts_the_unskipped_blocks():
-    """C bytes of every block not skipped (rows of its class x 4 bytes), the
-    snapshot (8 bytes a block) and the duals, from a skip mask of L x
-    ceil(n/32) words (bit j % 32 of word j / 32)."""
+    """C bytes of every block not skipped (rows of its class x 4 bytes), two
+    words per unit (tile maximum of z~, word of N), z~ of the columns of the
+    units with a block not skipped, and the duals with their snapshot values,
+    from a skip mask of L x ceil(n/32) words (bit j % 32 of word j / 32)."""
     np = pytest.importorskip("numpy")
     sys.path.insert(0, ROOT)
     import bench
@@ -108,4 +109,5 @@ def test_screened_needed_bytes_counts_the_unskipped_blocks():
     need, c_need, nskip = bench.screened_needed_bytes(mask.ravel(), sizes, n, L)
     assert nskip == 34 + 8
     assert c_need == 4 * (5 * (40 - 34) + 7 * (40 - 8))
-    assert need == c_need + 8 * L * n + 8 * (12 + 40)
+    # units with a block not skipped: (0, tile 1: 8 columns), (2, tile 0: 32)
+    assert need == c_need + 4 * (8 + 32) + 8 * L * 2 + 16 * (12 + 40)
