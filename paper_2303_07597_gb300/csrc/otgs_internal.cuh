@@ -245,11 +245,11 @@ struct EvalCtl {
     int xnext;          // the next flagged block set of shorter classes for the exact-sum kernel
     int tnext;          // the next column task of the taller classes' sets
     int ntcol;          // column tasks handed out
-    int wl;             // screened: 1 = the screen built the sets itself (no bound pass; see k_route)
+    int wl;             // screened: 1 = the screen built the sets itself (no bound pass; see pick_route)
     unsigned long long psi[2];  // one problem: psi summed by the exact-sum kernel (fixed point, hi and lo)
-    unsigned long long wl_work;  // screened: rows x columns of the blocks the screen left (see k_route)
+    unsigned long long wl_work;  // screened: rows x columns of the blocks the screen left (see pick_route)
     unsigned long long wl_cols;  //   and their number
-    unsigned wl_done;            //   blocks of the list kernel done (its last one picks the route)
+    unsigned wl_done;            //   CTAs of the screen kernel done (its last one picks the route)
 };
 
 // Device address of the control word's psi accumulators (host side: plain

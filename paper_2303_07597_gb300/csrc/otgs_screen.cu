@@ -203,24 +203,40 @@ __global__ void k_zt_tiles(const float* zt, float* zt_tile, int64_t units, int n
 
 
 // Alg. 2's skip test (Eq. 6, Lemma 2) for every block outside N.  A warp
-// takes the 32 units (l, 32-column tile) of one unit_need word, lane = column
-// in the tile; lane t keeps tile t's ballots and, after the word, writes that
-// tile's skip word and marks its items, so no lane works through the tiles
-// alone.  Statistics are summed per block before one atomic add each.
+// takes the 32 units (l, 32-column tile) of one unit_need word, lane t tile
+// t; a tile that fails the tile-level test is screened column by column
+// (lane = column), and lane t keeps tile t's skip word, writes it and marks
+// its items.  With wl_build, every unit with a block left is also recorded
+// as a block set for the exact-sum kernels (its group's rows x the tile's
+// columns not skipped): the warps of a CTA count their sets and column tasks,
+// one atomic per counter and CTA hands out their places, and each lane
+// writes its tile's set; the rows x columns of the sets are summed, and the
+// last CTA to finish picks the route.  Statistics are summed per CTA before
+// one atomic add each.
 constexpr int SCREEN_WARPS = 8;
 constexpr int SCREEN_TB = 8;  // tiles whose loads a warp issues together
 
-__global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S)
+__device__ void pick_route(const ScreenArgs& S, EvalCtl* ctl, unsigned long long* fcount);
+
+__global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S, const EvalArgs E)
 {
     if (S.gate && !*S.gate) return;
     __shared__ unsigned long long csum[SCREEN_WARPS][4];
+    __shared__ int wcnt[3][SCREEN_WARPS];  // a round's short sets, tall sets, tall column tasks per warp
+    __shared__ int wbase[3][SCREEN_WARPS]; // the index of each warp's first one
+    __shared__ bool last;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lt = (1u << lane) - 1u;
     const int64_t ntask = (int64_t)S.L * S.unit_words;
-    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0;
-    for (int64_t task = (int64_t)blockIdx.x * SCREEN_WARPS + warp; task < ntask;
-         task += (int64_t)gridDim.x * SCREEN_WARPS) {
-        const int l = (int)(task / S.unit_words), w = (int)(task % S.unit_words);
-        const int g = S.goff[l + 1] - S.goff[l];
+    unsigned long long c0 = 0, c1 = 0, c2 = 0, c3 = 0, work = 0, wcols = 0;
+    // rounds of SCREEN_WARPS tasks, the same count in every warp of the CTA
+    for (int64_t base = (int64_t)blockIdx.x * SCREEN_WARPS; base < ntask;
+         base += (int64_t)gridDim.x * SCREEN_WARPS) {
+        const int64_t task = base + warp;
+        const bool have = task < ntask;  // (uniform in the warp)
+        const int l = have ? (int)(task / S.unit_words) : 0, w = have ? (int)(task % S.unit_words) : 0;
+        const int gs = S.goff[l], ge = S.goff[l + 1];
+        const int g = have ? ge - gs : 0;
         const float th = S.gstat[4 * l + 3], npos = S.gstat[4 * l], sg = S.sg_ru[l];
         const int jt1 = min(32 * w + 32, S.ntiles);
         const int ldz = S.ntiles * TW;
@@ -231,7 +247,7 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
         // rounds up, so the bound grows with each operand), so the tile's skip
         // word is then its columns outside N without reading their z~
         const int jt = 32 * w + lane;
-        const bool tv = jt < jt1;
+        const bool tv = have && jt < jt1;
         const int64_t tq = (int64_t)l * S.ntiles + jt;
         const uint32_t my_N = tv ? __ldg(S.Nmask + tq) : 0u;
         const int cols = min(TW, S.n - jt * TW);
@@ -286,7 +302,57 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
             c3 += my_need ? 1ull : 0ull;
         }
         const uint32_t needword = __ballot_sync(FULLMASK, my_need != 0u);
-        if (lane == 0) S.unit_need[(int64_t)l * S.unit_words + w] = needword;
+        if (lane == 0 && have) S.unit_need[(int64_t)l * S.unit_words + w] = needword;
+        if (!S.wl_build) continue;  // (uniform in the kernel)
+        // the units with a block left as block sets
+        const bool tall = g > XTALL_ROWS;
+        const int nc = __popc(my_need);
+        int cs = nc;  // inclusive scan of the columns over the lanes
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const int v = __shfl_up_sync(FULLMASK, cs, off);
+            if (lane >= off) cs += v;
+        }
+        const int ctot = __shfl_sync(FULLMASK, cs, 31);
+        if (lane == 0) {
+            wcnt[0][warp] = tall ? 0 : __popc(needword);
+            wcnt[1][warp] = tall ? __popc(needword) : 0;
+            wcnt[2][warp] = tall && E.use_ct ? ctot : 0;
+        }
+        work += (unsigned long long)g * (unsigned long long)ctot;
+        wcols += (unsigned long long)ctot;
+        __syncthreads();
+        if (threadIdx.x < 3) {
+            const int k = threadIdx.x;
+            int tot = 0;
+            for (int q = 0; q < SCREEN_WARPS; q++) {
+                wbase[k][q] = tot;
+                tot += wcnt[k][q];
+            }
+            if (tot) {
+                const int b0 = atomicAdd(k == 0 ? &E.ctl->nxent : (k == 1 ? &E.ctl->nxtall : &E.ctl->ntcol), tot);
+                for (int q = 0; q < SCREEN_WARPS; q++) wbase[k][q] += b0;
+            }
+        }
+        __syncthreads();
+        if (my_need) {
+            const int e = wbase[tall ? 1 : 0][warp] + __popc(needword & lt);
+            const int tb = wbase[2][warp] + (cs - nc);
+            if (e >= (tall ? E.xtall_cap : E.xent_cap) || (tall && E.use_ct && tb + nc > E.xtcol_cap)) {
+                atomicOr(E.err, 4);  // the capacities hold every (group, column) once: not reached
+                continue;
+            }
+            XEntry& x = (tall ? E.xtall : E.xent)[e];
+            x.gstart = gs;
+            x.gend = ge;
+            x.colg0 = jt * TW;
+            x.prob = 0;
+            x.l = l;
+            x.mask = my_need;
+            x.tbase = tb;
+            if (tall && E.use_ct)
+                for (int i = 0; i < nc; i++) E.xtmap[tb + i] = (uint32_t)e;
+        }
     }
 #pragma unroll
     for (int off = 16; off >= 1; off >>= 1) {
@@ -307,9 +373,25 @@ __global__ void __launch_bounds__(SCREEN_WARPS * 32) k_screen(const ScreenArgs S
         for (int q = 0; q < SCREEN_WARPS; q++) v += csum[q][threadIdx.x];
         if (v) atomicAdd(S.count + threadIdx.x, v);
     }
+    if (!S.wl_build) return;
+    if (lane == 0 && work) {
+        atomicAdd(&E.ctl->wl_work, work);
+        atomicAdd(&E.ctl->wl_cols, wcols);
+    }
+    // the last CTA to finish picks the route (every CTA's sums are in)
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        last = atomicAdd(&E.ctl->wl_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        pick_route(S, E.ctl, E.fcount);
+    }
 }
 
-// The route of a screened evaluation (the last block of k_wlist, which
+// The route of a screened evaluation (the last CTA of k_screen, which
 // recorded every needed unit
 // as a block set for the exact-sum kernels): when their rows x columns are few
 // (at most wl_max: then reading just those blocks from the transposed copy
@@ -330,88 +412,6 @@ __device__ void pick_route(const ScreenArgs& S, EvalCtl* ctl, unsigned long long
         ctl->nxent = 0;
         ctl->nxtall = 0;
         ctl->ntcol = 0;
-    }
-}
-
-// Every needed unit (l, tile) as a block set for the exact-sum kernels: its
-// group's rows x the tile's columns the screen did not skip.  A warp per mask
-// word of a group, lane t for tile 32 w + t: one atomic per counter and warp
-// (warp scans give each lane its place), then every lane writes its own set
-// (and a taller class's column tasks).  Also sums the sets'
-// rows x columns, and its last block picks the route.
-__global__ void __launch_bounds__(256) k_wlist(const ScreenArgs S, const EvalArgs E)
-{
-    if (S.gate && !*S.gate) return;
-    if (!S.wl_build) return;
-    const int lane = threadIdx.x & 31;
-    const uint32_t lt = (1u << lane) - 1u;
-    const int64_t ntask = (int64_t)S.L * S.unit_words;
-    unsigned long long work = 0, flagged = 0;
-    for (int64_t task = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32; task < ntask;
-         task += (int64_t)gridDim.x * blockDim.x / 32) {
-        const int l = (int)(task / S.unit_words), w = (int)(task % S.unit_words);
-        const int gs = S.goff[l], ge = S.goff[l + 1], g = ge - gs;
-        if (g == 0) continue;  // (uniform)
-        const int jt = 32 * w + lane;
-        uint32_t need = 0u;
-        if (jt < S.ntiles) {
-            const int left = S.n - jt * TW;  // columns of the tile that exist
-            const uint32_t valid = left >= 32 ? FULLMASK : ((1u << left) - 1u);
-            need = valid & ~__ldg(S.skipmask + (int64_t)l * S.ntiles + jt);
-        }
-        const uint32_t hb = __ballot_sync(FULLMASK, need != 0u);
-        if (!hb) continue;  // (uniform)
-        const bool tall = g > XTALL_ROWS;
-        const int nc = __popc(need);
-        // inclusive scan of the columns over the lanes
-        int cs = nc;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const int v = __shfl_up_sync(FULLMASK, cs, off);
-            if (lane >= off) cs += v;
-        }
-        const int ctot = __shfl_sync(FULLMASK, cs, 31);
-        int e0 = 0, tb = 0;
-        if (lane == 0) {
-            e0 = atomicAdd(tall ? &E.ctl->nxtall : &E.ctl->nxent, __popc(hb));
-            if (tall && E.use_ct) tb = atomicAdd(&E.ctl->ntcol, ctot);
-        }
-        e0 = __shfl_sync(FULLMASK, e0, 0);
-        tb = __shfl_sync(FULLMASK, tb, 0) + (cs - nc);
-        work += (unsigned long long)g * (unsigned long long)ctot;
-        flagged += (unsigned long long)ctot;
-        if (!need) continue;
-        const int e = e0 + __popc(hb & lt);
-        if (e >= (tall ? E.xtall_cap : E.xent_cap) || (tall && E.use_ct && tb + nc > E.xtcol_cap)) {
-            atomicOr(E.err, 4);  // the capacities hold every (group, column) once: not reached
-            continue;
-        }
-        XEntry& x = (tall ? E.xtall : E.xent)[e];
-        x.gstart = gs;
-        x.gend = ge;
-        x.colg0 = jt * TW;
-        x.prob = 0;
-        x.l = l;
-        x.mask = need;
-        x.tbase = tb;
-        if (tall && E.use_ct)
-            for (int i = 0; i < nc; i++) E.xtmap[tb + i] = (uint32_t)e;
-    }
-    if (lane == 0 && work) {
-        atomicAdd(&E.ctl->wl_work, work);
-        atomicAdd(&E.ctl->wl_cols, flagged);
-    }
-    // the last block to finish picks the route (every block's sums are in)
-    __shared__ bool last;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        last = atomicAdd(&E.ctl->wl_done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (last && threadIdx.x == 0) {
-        __threadfence();
-        pick_route(S, E.ctl, E.fcount);
     }
 }
 
@@ -593,18 +593,16 @@ bool Handle::eval_screened_prepped(const double* beta, double* G_sorted, const d
     s.wl_max = WL_FRACTION * (double)m * (double)n;
     const int64_t tasks = (int64_t)L * unit_words;
     const int sblocks = (int)std::min<int64_t>((tasks + SCREEN_WARPS - 1) / SCREEN_WARPS, 16LL * n_sm);
-    k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s);
     // (without the block sets the control word's zero route is the bound pass)
-    if (s.wl_build)
-        k_wlist<<<(unsigned)std::min<int64_t>((tasks * 32 + 255) / 256, 8LL * n_sm), 256, 0, st>>>(s, e);
+    k_screen<<<sblocks, SCREEN_WARPS * 32, 0, st>>>(s, e);
     launch_stage_masks(e, n_sm, st);
     const int nk = eval_launch(e, std::min(CTAS_PER_SM * n_sm, hp.nitems()));
     ReduceArgs r = reduce_args(item_active, out_caller, G_sorted, dir, beta);
     launch_reduce(r, st);
     if (!eval_gate) {
         count_screened_evals(1);
-        // and deltas (2), screen, block sets, stage masks, reduction
-        stats_host.kernels += nk + 5 + (s.wl_build ? 1 : 0);
+        // and deltas (2), screen, stage masks, reduction
+        stats_host.kernels += nk + 5;
     }
     return ck(cudaGetLastError(), "screened eval launch");
 }
