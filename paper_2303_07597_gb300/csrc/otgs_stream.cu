@@ -1190,12 +1190,15 @@ __global__ void __launch_bounds__(TALL_THREADS, 2) k_exact_tall(const EvalArgs A
 // it with coalesced loads, one row per lane, and only the flagged columns'
 // bytes are read.
 //  * A taller class's column (a column task): one warp, taken from a counter
-//    before the shorter sets (the longest work goes out first).  It sums its
-//    slices of XSLICE rows one after the other (S = sum [f]_+^2 and P = sum
-//    [f]_+ in double-float per lane in row order, the fixed xor tree per
-//    slice, the slices added in slice order), finishes the block (Eq. 5: psi
-//    in fixed point, the column sum s P, a snapshot's z~), then adds the
-//    rows' t_ij = s [f_ij]_+ to the row sums (the rows again, from L1/L2).
+//    before the shorter sets (the longest work goes out first).  Lane k takes
+//    rows gstart + k, gstart + k + 32, ... in that order, XSLICE rows a load
+//    round, and sums S = sum [f]_+^2 and P = sum [f]_+ in double-float; the
+//    lanes' sums are then added in the fixed xor tree, and the block is
+//    finished (Eq. 5: psi in fixed point, the column sum s P, a snapshot's
+//    z~).  Each lane also keeps its rows' [f]_+ (the float pair's high part,
+//    which is all t_ij = s [f_ij]_+ uses) in the warp's XT_CACHE floats of
+//    shared memory, so the rows' t_ij go to the row sums without a second
+//    read of C; rows past the cache are formed again from C.
 //  * A shorter class's set (at most XTALL_ROWS rows): one warp, taken from a
 //    counter.  Per column the same sums over its rows (one slice), Eq. 5; then
 //    its rows once more, every column with s > 0 per row, one atomic per row.
@@ -1203,34 +1206,10 @@ __global__ void __launch_bounds__(TALL_THREADS, 2) k_exact_tall(const EvalArgs A
 // depend on its set, on scheduling or on the evaluation being screened.
 constexpr int XTC_THREADS = 256;
 constexpr int XTC_UNROLL = 8;
+constexpr int XT_CACHE = 2048;  // rows of a taller class's column whose [f]_+ a warp keeps (8 KB)
 static_assert(XSLICE == 32 * XTC_UNROLL, "a slice is one load round of a warp");
-
-// The sums over rows [r0, r1) (r1 - r0 <= 32 XTC_UNROLL) of one column; every
-// lane gets them.
-__device__ __forceinline__ Acc slice_sums(const EvalArgs& A, const float* col, int r0, int r1, float bp, float bh,
-                                          float bl, int lane)
-{
-    float c[XTC_UNROLL];
-    float4 a[XTC_UNROLL];
-#pragma unroll
-    for (int u = 0; u < XTC_UNROLL; u++) {
-        const int R = r0 + 32 * u + lane;
-        const bool in = R < r1;
-        a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
-        c[u] = in ? __ldg(col + R) : 0.f;
-    }
-    Acc acc = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-    for (int u = 0; u < XTC_UNROLL; u++)
-        if (maybe_pos(a[u].z, c[u], bp)) {
-            float fh, fl;
-            f_exact(a[u].x, a[u].y, bh, bl, c[u], fh, fl);
-            if (fh > 0.f) acc_p(fh, fl, acc);
-        }
-    warp_df_sum(acc.Sh, acc.Sl);
-    warp_df_sum(acc.Ph, acc.Pl);
-    return acc;
-}
+static_assert(XT_CACHE % XSLICE == 0, "the cache ends at a slice boundary");
+constexpr size_t exact_t_smem_bytes() { return sizeof(float) * XT_CACHE * (XTC_THREADS / 32); }
 
 // Eq. 5 for one block from its sums (lane 0's work): psi into (ph, pl), s P
 // into the column sum, a snapshot's z~.  Returns s.
@@ -1266,6 +1245,8 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
     const int ntc = min(A.ctl->ntcol, A.xtcol_cap);
     const int tid = threadIdx.x, lane = tid & 31;
     __shared__ FxScale fx1;  // one problem: the evaluation's scale
+    extern __shared__ float xcache[];                // XT_CACHE floats per warp
+    float* fk = xcache + (tid >> 5) * XT_CACHE;      // this warp's: [f]_+ of a column's rows, by row
     if (tid == 0 && !A.pfx && nx + ntc > 0) fx1 = fx_scale(A.ctl->amax, A.ctl->bmax, A.fx_m, A.fx_n, A.gamma);
     __syncthreads();
     int pprob = -1;  // lane 0 of each warp: the problem of the psi sums it holds
@@ -1284,12 +1265,34 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
         const float2 b2 = __ldg(A.B2 + pd.bcoff + lcol);
         const float bp = bound_up(b2.x);
         const float* col = pd.CT + (int64_t)lcol * pd.ldct - pd.roff;
-        Acc T = {0.f, 0.f, 0.f, 0.f};  // the slices' sums, added in slice order
+        Acc T = {0.f, 0.f, 0.f, 0.f};  // this lane's rows, in row order
         for (int a0 = E.gstart; a0 < E.gend; a0 += XSLICE) {
-            const Acc p = slice_sums(A, col, a0, min(E.gend, a0 + XSLICE), bp, b2.x, b2.y, lane);
-            df_add(T.Sh, T.Sl, p.Sh, p.Sl);
-            df_add(T.Ph, T.Pl, p.Ph, p.Pl);
+            float c[XTC_UNROLL];
+            float4 a[XTC_UNROLL];
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++) {
+                const int R = a0 + 32 * u + lane;
+                const bool in = R < E.gend;
+                a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+                c[u] = in ? __ldg(col + R) : 0.f;
+            }
+            const bool keep = a0 - E.gstart < XT_CACHE;  // (uniform)
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++) {
+                float fp = 0.f;
+                if (maybe_pos(a[u].z, c[u], bp)) {
+                    float fh, fl;
+                    f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
+                    if (fh > 0.f) {
+                        acc_p(fh, fl, T);
+                        fp = fh;
+                    }
+                }
+                if (keep) fk[a0 - E.gstart + 32 * u + lane] = fp;
+            }
         }
+        warp_df_sum(T.Sh, T.Sl);
+        warp_df_sum(T.Ph, T.Pl);
         float s = 0.f;
         if (lane == 0) {
             hold_psi(A, E.prob, pprob, ph, pl);
@@ -1297,7 +1300,17 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
         }
         s = __shfl_sync(FULLMASK, s, 0);
         if (!(s > 0.f)) continue;  // (uniform)
-        for (int a0 = E.gstart; a0 < E.gend; a0 += XSLICE) {
+        // t_ij = s [f_ij]_+ into the row sums: each lane reads back the rows it kept
+        const int kept = min(E.gend, E.gstart + XT_CACHE);
+        for (int a0 = E.gstart; a0 < kept; a0 += XSLICE) {
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++) {
+                const int R = a0 + 32 * u + lane;
+                const float fh = fk[R - E.gstart];
+                if (R < E.gend && fh > 0.f) atomicAdd(A.rowfx + R, t_q(__fmul_rn(s, fh), fx.to_rf));
+            }
+        }
+        for (int a0 = kept; a0 < E.gend; a0 += XSLICE) {
             float c[XTC_UNROLL];
             float4 a[XTC_UNROLL];
 #pragma unroll
@@ -1408,7 +1421,7 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
 void launch_exact(const EvalArgs& a, int n_sm, cudaStream_t st)
 {
     if (a.use_ct) {
-        k_exact_t<<<3 * n_sm, XTC_THREADS, 0, st>>>(a);
+        k_exact_t<<<3 * n_sm, XTC_THREADS, exact_t_smem_bytes(), st>>>(a);
         return;
     }
     k_exact<<<4 * n_sm, EXACT_THREADS, 0, st>>>(a);
@@ -1433,7 +1446,9 @@ bool stream_prepare()
 {
     const int sm = (int)stream_smem_bytes();
     return cudaFuncSetAttribute(k_stream<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess &&
-           cudaFuncSetAttribute(k_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess;
+           cudaFuncSetAttribute(k_stream<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm) == cudaSuccess &&
+           cudaFuncSetAttribute(k_exact_t, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)exact_t_smem_bytes()) == cudaSuccess;
 }
 
 void launch_stream(const EvalArgs& a, int n_ctas, cudaStream_t st)
