@@ -1238,6 +1238,21 @@ __device__ __forceinline__ void hold_psi(const EvalArgs& A, int prob, int& pprob
     }
 }
 
+// One load round of a column of CT: rows a0 + 32 u + lane (below r1) of the
+// column and their (alpha hi, lo); A' = bound_up(alpha hi) is formed where
+// it is used (it is the row record's third field, bit for bit).
+__device__ __forceinline__ void load_rows(const EvalArgs& A, const float* col, int a0, int r1, int lane,
+                                          float2 (&a)[XTC_UNROLL], float (&c)[XTC_UNROLL])
+{
+#pragma unroll
+    for (int u = 0; u < XTC_UNROLL; u++) {
+        const int R = a0 + 32 * u + lane;
+        const bool in = R < r1;
+        a[u] = in ? __ldg(reinterpret_cast<const float2*>(A.rowA + R)) : make_float2(0.f, 0.f);
+        c[u] = in ? __ldg(col + R) : 0.f;
+    }
+}
+
 __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
 {
     if (A.gate && !*A.gate) return;
@@ -1266,21 +1281,24 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
         const float bp = bound_up(b2.x);
         const float* col = pd.CT + (int64_t)lcol * pd.ldct - pd.roff;
         Acc T = {0.f, 0.f, 0.f, 0.f};  // this lane's rows, in row order
+        // each round's loads go out before the previous round is summed
+        float2 an[XTC_UNROLL];
+        float cn[XTC_UNROLL];
+        load_rows(A, col, E.gstart, E.gend, lane, an, cn);
         for (int a0 = E.gstart; a0 < E.gend; a0 += XSLICE) {
+            float2 a[XTC_UNROLL];
             float c[XTC_UNROLL];
-            float4 a[XTC_UNROLL];
 #pragma unroll
             for (int u = 0; u < XTC_UNROLL; u++) {
-                const int R = a0 + 32 * u + lane;
-                const bool in = R < E.gend;
-                a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
-                c[u] = in ? __ldg(col + R) : 0.f;
+                a[u] = an[u];
+                c[u] = cn[u];
             }
+            if (a0 + XSLICE < E.gend) load_rows(A, col, a0 + XSLICE, E.gend, lane, an, cn);
             const bool keep = a0 - E.gstart < XT_CACHE;  // (uniform)
 #pragma unroll
             for (int u = 0; u < XTC_UNROLL; u++) {
                 float fp = 0.f;
-                if (maybe_pos(a[u].z, c[u], bp)) {
+                if (a0 + 32 * u + lane < E.gend && maybe_pos(bound_up(a[u].x), c[u], bp)) {
                     float fh, fl;
                     f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
                     if (fh > 0.f) {
@@ -1311,18 +1329,12 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
             }
         }
         for (int a0 = kept; a0 < E.gend; a0 += XSLICE) {
+            float2 a[XTC_UNROLL];
             float c[XTC_UNROLL];
-            float4 a[XTC_UNROLL];
-#pragma unroll
-            for (int u = 0; u < XTC_UNROLL; u++) {
-                const int R = a0 + 32 * u + lane;
-                const bool in = R < E.gend;
-                a[u] = in ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
-                c[u] = in ? __ldg(col + R) : 0.f;
-            }
+            load_rows(A, col, a0, E.gend, lane, a, c);
 #pragma unroll
             for (int u = 0; u < XTC_UNROLL; u++)
-                if (maybe_pos(a[u].z, c[u], bp)) {
+                if (a0 + 32 * u + lane < E.gend && maybe_pos(bound_up(a[u].x), c[u], bp)) {
                     float fh, fl;
                     f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
                     if (fh > 0.f) atomicAdd(A.rowfx + a0 + 32 * u + lane, t_q(__fmul_rn(s, fh), fx.to_rf));
@@ -1342,11 +1354,13 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
         const float* ct0 = pd.CT + (int64_t)(E.colg0 - pd.coff) * pd.ldct - pd.roff;  // + k ldct + R
         // the set's rows (at most XTALL_ROWS = 32 XTC_UNROLL): their records once, and
         // each column's values loaded one column ahead of its sums
-        float4 a[XTC_UNROLL];
+        float2 a[XTC_UNROLL];
+        float ap[XTC_UNROLL];  // A' of the rows (-inf past the set)
 #pragma unroll
         for (int u = 0; u < XTC_UNROLL; u++) {
             const int R = E.gstart + 32 * u + lane;
-            a[u] = R < E.gend ? __ldg(A.rowA + R) : make_float4(0.f, 0.f, -INFINITY, 0.f);
+            a[u] = R < E.gend ? __ldg(reinterpret_cast<const float2*>(A.rowA + R)) : make_float2(0.f, 0.f);
+            ap[u] = R < E.gend ? bound_up(a[u].x) : -INFINITY;
         }
         auto load_col = [&](int k, float (&c)[XTC_UNROLL]) {
             const float* col = ct0 + (int64_t)k * pd.ldct;
@@ -1372,7 +1386,7 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
             Acc T = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
             for (int u = 0; u < XTC_UNROLL; u++)
-                if (maybe_pos(a[u].z, c[u], bp)) {
+                if (maybe_pos(ap[u], c[u], bp)) {
                     float fh, fl;
                     f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
                     if (fh > 0.f) acc_p(fh, fl, T);
@@ -1402,7 +1416,7 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
             const float bp = bound_up(b2.x);
 #pragma unroll
             for (int u = 0; u < XTC_UNROLL; u++)
-                if (maybe_pos(a[u].z, c[u], bp)) {
+                if (maybe_pos(ap[u], c[u], bp)) {
                     float fh, fl;
                     f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
                     if (fh > 0.f) tq[u] += t_q(__fmul_rn(s, fh), fx.to_rf);
