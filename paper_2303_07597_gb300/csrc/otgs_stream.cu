@@ -1200,8 +1200,10 @@ __global__ void __launch_bounds__(TALL_THREADS, 2) k_exact_tall(const EvalArgs A
 //    shared memory, so the rows' t_ij go to the row sums without a second
 //    read of C; rows past the cache are formed again from C.
 //  * A shorter class's set (at most XTALL_ROWS rows): one warp, taken from a
-//    counter.  Per column the same sums over its rows (one slice), Eq. 5; then
-//    its rows once more, every column with s > 0 per row, one atomic per row.
+//    counter.  Per column the same sums over its rows (one slice), Eq. 5, the
+//    first XS_CACHED columns' [f]_+ kept in the warp's cache; then per row the
+//    t_ij of every column with s > 0 (kept ones from the cache, the others
+//    formed again from C), one atomic per row.
 // Every floating-point sum has a fixed order, so a block's results do not
 // depend on its set, on scheduling or on the evaluation being screened.
 constexpr int XTC_THREADS = 256;
@@ -1210,6 +1212,8 @@ constexpr int XT_CACHE = 2048;  // rows of a taller class's column whose [f]_+ a
 static_assert(XSLICE == 32 * XTC_UNROLL, "a slice is one load round of a warp");
 static_assert(XT_CACHE % XSLICE == 0, "the cache ends at a slice boundary");
 constexpr size_t exact_t_smem_bytes() { return sizeof(float) * XT_CACHE * (XTC_THREADS / 32); }
+constexpr int XS_CACHED = XT_CACHE / XSLICE;  // columns of a shorter class's set whose [f]_+ a warp keeps
+static_assert(XTALL_ROWS <= XSLICE, "a shorter class's column fits one cache slot");
 
 // Eq. 5 for one block from its sums (lane 0's work): psi into (ph, pl), s P
 // into the column sum, a snapshot's z~.  Returns s.
@@ -1370,13 +1374,16 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
                 c[u] = R < E.gend ? __ldg(col + R) : 0.f;
             }
         };
-        float sk = 0.f;  // lane k: s of column k
+        float sk = 0.f;         // lane k: s of column k
+        int sq = XS_CACHED;     // lane k: column k's slot in the warp's cache (XS_CACHED: none)
+        int q = 0;              // columns summed so far
         uint32_t rem = E.mask;
         float cn[XTC_UNROLL];
         if (rem) load_col(__ffs(rem) - 1, cn);
         while (rem) {
             const int k = __ffs(rem) - 1;
             rem &= rem - 1u;
+            const bool keep = q < XS_CACHED;  // (uniform)
             float c[XTC_UNROLL];
 #pragma unroll
             for (int u = 0; u < XTC_UNROLL; u++) c[u] = cn[u];
@@ -1385,25 +1392,50 @@ __global__ void __launch_bounds__(XTC_THREADS, 3) k_exact_t(const EvalArgs A)
             const float bp = bound_up(b2.x);
             Acc T = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int u = 0; u < XTC_UNROLL; u++)
+            for (int u = 0; u < XTC_UNROLL; u++) {
+                float fp = 0.f;
                 if (maybe_pos(ap[u], c[u], bp)) {
                     float fh, fl;
                     f_exact(a[u].x, a[u].y, b2.x, b2.y, c[u], fh, fl);
-                    if (fh > 0.f) acc_p(fh, fl, T);
+                    if (fh > 0.f) {
+                        acc_p(fh, fl, T);
+                        fp = fh;
+                    }
                 }
+                if (keep) fk[q * XSLICE + 32 * u + lane] = fp;
+            }
             warp_df_sum(T.Sh, T.Sl);
             warp_df_sum(T.Ph, T.Pl);
             float s = 0.f;
             if (lane == 0) s = finish_block_exact(A, fx, T, E.l, E.colg0 + k, ph, pl);
             s = __shfl_sync(FULLMASK, s, 0);
-            if (lane == k) sk = s;
+            if (lane == k) {
+                sk = s;
+                if (keep) sq = q;
+            }
+            q++;
         }
         uint32_t srem = __ballot_sync(FULLMASK, sk > 0.f);
         if (!srem) continue;  // (uniform)
         unsigned long long tq[XTC_UNROLL];
 #pragma unroll
         for (int u = 0; u < XTC_UNROLL; u++) tq[u] = 0ull;
-        load_col(__ffs(srem) - 1, cn);
+        // the columns whose [f]_+ the lanes kept: t_ij from the cache
+        uint32_t crem = srem & __ballot_sync(FULLMASK, sq < XS_CACHED);
+        srem &= ~crem;
+        while (crem) {
+            const int k = __ffs(crem) - 1;
+            crem &= crem - 1u;
+            const float s = __shfl_sync(FULLMASK, sk, k);
+            const int qk = __shfl_sync(FULLMASK, sq, k);
+#pragma unroll
+            for (int u = 0; u < XTC_UNROLL; u++) {
+                const float fh = fk[qk * XSLICE + 32 * u + lane];
+                if (fh > 0.f) tq[u] += t_q(__fmul_rn(s, fh), fx.to_rf);
+            }
+        }
+        // the others from C again
+        if (srem) load_col(__ffs(srem) - 1, cn);
         while (srem) {
             const int k = __ffs(srem) - 1;
             srem &= srem - 1u;
