@@ -302,8 +302,8 @@ struct XEntry {
 // fraction of m n.
 constexpr double WL_FRACTION = 0.25;
 
-// Rows of a slice of a taller class's column (the transposed copy's exact
-// sums: one warp per slice, slice sums added in slice order).
+// Rows of one load round of a warp over a column of the transposed copy
+// (eight rows a lane) in the exact-sum kernel.
 constexpr int XSLICE = 256;
 
 
