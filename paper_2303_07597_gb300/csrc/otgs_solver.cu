@@ -388,7 +388,7 @@ int Solver::run(double tol, int maxit)
     const int tb = (std::max((int)h->m, npad) + 255) / 256;
     const size_t hdr = offsetof(SolverState, tol);  // the int fields and the eval counter
     const long long max_trials = (long long)maxit * (LS_MAX_EVALS + 2) + 16;
-    // Trials are queued TRIALS_PER_SYNC at a time; each opens with k_gate, so
+    // Trials are queued up to TRIALS_PER_SYNC at a time; each opens with k_gate, so
     // the ones queued after the solve ended, or after an iteration that asks
     // for a snapshot refresh (Alg. 1, every r accepted iterations), do
     // nothing.  The host then takes the snapshot at the accepted iterate and
@@ -413,7 +413,14 @@ int Solver::run(double tol, int maxit)
             h->fail(OTGS_ENOTCONV, "solver exceeded its trial budget");
             break;
         }
-        for (int q = 0; q < TRIALS_PER_SYNC; q++) {
+        // with screening, trials up to the next refresh (every r accepted
+        // iterations, each taking at least one trial) and two more for line
+        // searches that need a second one: the trials queued after the refresh
+        // point only pass through the gate
+        int nq = TRIALS_PER_SYNC;
+        if (hstate->screening && hstate->r > 0)
+            nq = std::min(nq, hstate->r - hstate->iter % hstate->r + 2);
+        for (int q = 0; q < nq; q++) {
             k_gate<<<1, 1, 0, st>>>(state, h->ctl, h->prm.use_screening ? h->gmax : nullptr);
             k_trial<<<tb, 256, 0, st>>>(state, x, d, xt, h->rowA, h->B2, h->alpha_eval, h->rowfx, h->colfx,
                                         h->ctl, (int)h->m, (int)h->n, npad);
