@@ -1100,8 +1100,8 @@ def run_gpu(args):
             "l2_flushed": flushed,
             "e2e": {"value": job_throughput(k_e2e, world, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (m + n), "d2h_bytes_per_step": 8 * (1 + m + n)},
-            # the library's own count: prep, k_stream, the two exact-sum kernels, k_reduce
-            # (and k_split_finish when a class is split across items) per evaluation
+            # the library's own count per evaluation: k_prep, k_stream, k_exact_t,
+            # k_reduce, and k_split_finish when a class is split across items
             "gpu_launches": kernels,
             "clocks": clocks,
         }

@@ -490,7 +490,9 @@ int Handle::eval_launch(const EvalArgs& e, int n_ctas)
     }
     launch_split_finish(e, st);
     launch_exact(e, n_sm, st);
-    return 2 + (e.use_ct ? 1 : 2) + (e.nsets > 0);  // stream, exact, split finish
+    // k_stream, k_split_finish (when a class is split over items), and the
+    // exact sums: k_exact_t, or k_exact and k_exact_tall without the transposed copy
+    return 1 + (e.nsets > 0 ? 1 : 0) + (e.use_ct ? 1 : 2);
 }
 
 // Dense evaluation at (alpha, beta); alpha in caller order unless alpha_sorted.
