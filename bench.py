@@ -829,6 +829,30 @@ def case_report(args, dev):
     return out
 
 
+def panel_sweep_report(args, dev):
+    """Dense evaluations of --workload at the bench point for several panel
+    heights (rows of whole class groups per work item): whole step and
+    k_stream per launch, CUDA events on the launch stream.  The plan only
+    changes how the blocks are tiled, so D is the same for every height."""
+    import torch
+    import paper_2303_07597_gb300 as pk
+    p, C, cfg = _make_workload(args.workload, args.seed, str(dev))
+    s = pk.GroupSparseOT(C, torch.from_numpy(p.a).to(dev), torch.from_numpy(p.b).to(dev),
+                         torch.from_numpy(p.labels).to(dev), p.L, cfg["gamma"], cfg["mu"])
+    alpha, beta = _eval_point(C, 20)
+    out = torch.empty(1 + p.m + p.n, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    rows = []
+    for pr in [int(x) for x in args.panel_sweep.split(",")]:
+        pk.ot_gs_set_plan(s.h, pr, 0, 0)
+        plan = pk.ot_gs_get_plan(s.h)
+        ms, kms = _stream_timed(s.h, lambda: pk.ot_gs_grad(s.h, alpha, beta, out), args.steps, stream)
+        rows.append({"panel_rows": plan["panel_rows"], "n_items": plan["n_items"], "step_ms": ms,
+                     "k_stream_ms": kms, "D": float(out[0].item())})
+    s.close()
+    return {"workload": args.workload, "rows": rows, "same_D": len({r["D"] for r in rows}) == 1}
+
+
 def grid_report(args, dev):
     """The mid workload (m = n = 4000, 100 Dirichlet(2) classes, d = 256)
     over gamma in {0.1, 1, 10} x mu in {0.01, 0.1, 1}, screening off and on:
@@ -1148,6 +1172,8 @@ def main():
     ap.add_argument("--grid", action="store_true",
                     help="only the mid workload over the (gamma, mu) grid, dense and screened time to 1e-6")
     ap.add_argument("--grid-iters", type=int, default=30000)
+    ap.add_argument("--panel-sweep", default="",
+                    help="only dense evaluations of --workload at these panel heights (comma-separated)")
     ap.add_argument("--sweep", action="store_true",
                     help="only the paper-shaped trends (screened vs dense over classes, class sizes, lower bound)")
     ap.add_argument("--sweep-classes", default="10,40,160,640,1280")
@@ -1181,6 +1207,11 @@ def main():
         import torch
         torch.cuda.set_device(0)
         print(json.dumps({"sweep": sweep_report(args, torch.device("cuda", 0))}))
+        return 0
+    if args.panel_sweep:
+        import torch
+        torch.cuda.set_device(0)
+        print(json.dumps({"panel_sweep": panel_sweep_report(args, torch.device("cuda", 0))}))
         return 0
     if args.impl == "reference":
         return run_reference(args)
