@@ -163,7 +163,9 @@ OTGS_API int ot_gs_grad_screened(ot_gs *h, const double *alpha, const double *be
 /*
  * Refresh the snapshot at (alpha, beta) (Alg. 1's snapshot update): one dense pass that
  * also stores z~_{l,j} (rounded up to FP32) and o~_{l,j}, and alpha~ = alpha,
- * beta~ = beta.  When build_N != 0 the set N (Def. 3, Eq. 8) is first rebuilt
+ * beta~ = beta; then one pass over z~ forms each 32-column tile's largest
+ * z~, with which the screened evaluation first tests whole tiles (the same
+ * skip decisions as block by block, fewer bytes read).  When build_N != 0 the set N (Def. 3, Eq. 8) is first rebuilt
  * from the lower bound of Eq. 7 against the previous snapshot (Alg. 1's
  * rebuild of N).  Writes D and the gradient to out like ot_gs_grad when out != NULL.
  */
